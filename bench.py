@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Benchmark of the hot path: one step = forward Monte Carlo polarization trace
+of the representative waveguide (3D slab n=1.71, 1.5 mm, 6 PRMA mirrors x 40
+SiO2/TiO2/Ta2O5 layers, 460/532/630 nm, 32x18 fields over 30x17 deg, random
+linear polarization, 1e7 rays, 64x48 eyebox bins) + loss (Eq. 1) + adjoint
+with respect to the 240 layer thicknesses. Metric: ray-mirror interactions/s
+(forward interactions per step / step time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank traces its own 1e7 rays (seed offset by rank, no
+data-path collective: weak scaling); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ray-mirror interactions/s fwd & fwd+bwd at <=1e-4 rel err; p50/p99 eval latency"
+UNIT = "interactions/s"
+# algorithmic FP32 flops per transfer-matrix layer step (counting an FMA as 2):
+#   forward: phase 1 mul + per polarization (2 mul for the layer matrix,
+#   4 mul + 4 fma for the 2x2 product) = 29;
+#   adjoint: reverse sweep per polarization (2 mul + 4 mul + 4 fma) and the
+#   layer gradient (q21 (p2 z1 + p4 z3) - q12 (p1 z2 + p3 z4): 2 fma + 2 mul
+#   + 2 mul + 1 fma = 9) = 2*(14+9) + 3 to combine = 49.
+FLOPS_FWD_LAYER = 29
+FLOPS_ADJ_LAYER = 49
+L2_FLUSH_BYTES = 256 << 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_count, sm_mhz):
+    """FP32 FMA-pipe peak: SMs x 128 lanes x 2 flops x SM clock."""
+    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def src_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2601_04370_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel):
+    """DRAM bytes per launch from profiles/traffic.json if it was taken on the
+    current kernel sources, else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        with open(p) as f:
+            t = json.load(f)
+        e = t.get(kernel)
+        if e and e.get("src_hash") == src_hash():
+            return e.get("dram_bytes_per_launch")
+    except Exception:
+        return None
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.device), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            v = [x.strip() for x in line.split(",")]
+            if len(v) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(v[1]), smax=float(v[2]), power=float(v[3]), hw=v[5], hwt=v[6], swt=v[7],
+                                 swp=v[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return None
+        smax = max(r["smax"] for r in rows)
+        load = [r for r in rows if r["power"] > 200.0] or rows
+        reasons = []
+        for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
+                          ("swp", "sw_power_cap")):
+            if any(r[key].lower().startswith("active") for r in rows):
+                reasons.append(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows), "samples_under_load": len(load)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        if device is not None:
+            pg.barrier(device_ids=[device])
+        else:
+            pg.barrier()
+
+
+def allmax(pg, x, device=None):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=("cuda" if device is not None else "cpu"))
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(pg, x, device=None):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=("cuda" if device is not None else "cpu"))
+    pg.all_reduce(t)
+    return float(t.item())
+
+
+def workload(rank, n_rays=None):
+    from paper_2601_04370_gb300 import workloads as W
+    D, C = W.representative() if n_rays is None else W.representative(n_rays=n_rays)
+    return D, C.replace(seed=C.seed + 1000003 * rank)
+
+
+WORKLOAD_NAME = ("representative fwd+loss+adjoint: 3D slab n=1.71 t=1.5mm, 6 PRMA mirrors x 40 layers "
+                 "(SiO2/TiO2/Ta2O5, d~U[10,200] nm), 460/532/630 nm, 32x18 fields over 30x17 deg, "
+                 "random linear pol, 1e7 rays per GPU, 64x48 eyebox bins, max 100 events")
+
+
+def cpu_oracle_rate(D, C, G, budget_s=12.0, max_rays=None):
+    """Oracle (FP64 CPU) forward + adjoint on a bounded sample of the same
+    workload: rays spread over all cells (blocks of 16 rays per cell stride)."""
+    from oracle import oracle as O
+    nthreads = O.hardware_threads()
+
+    cells = list(range(0, C.n_cells, max(1, C.n_cells // 64)))
+
+    def run(k):
+        # sample: the first k rays of each of 64 cells spread over the grid
+        hits = 0
+        t0 = time.perf_counter()
+        for cell in cells:
+            r0 = cell * C.n_cell
+            o = O.trace(D, C, rays=(r0, r0 + k), nthreads=nthreads)
+            hits += o["stats"]["n_hits"]
+            O.trace_grad(D, C, G, rays=(r0, r0 + k), nthreads=nthreads)
+        return hits, time.perf_counter() - t0
+
+    k = 8
+    h, t = run(k)
+    k = int(min(C.n_cell, max(k, k * budget_s / max(t, 1e-3))))
+    if max_rays:
+        k = min(k, max(1, max_rays // len(cells)))
+    h, t = run(k)
+    return dict(value=h / t, unit=UNIT, cores=nthreads, kind="oracle",
+                sample=f"{k * len(cells)} rays ({k} per cell from {len(cells)} of {C.n_cells} cells), "
+                       f"FP64 forward + adjoint, {t:.1f} s wall on {nthreads} host threads"), h, t
+
+
+def run_reference(args):
+    ws, rank, local, pg = dist_setup(args)
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import oracle as O
+    D, C = workload(0)
+    rng = np.random.default_rng(0)
+    G = rng.normal(size=C.tally_shape) / C.n_cell
+    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    base, h, t = cpu_oracle_rate(D, C, G, budget_s=per_step)
+    rates = []
+    for i in range(args.warmup + args.steps):
+        b, h, t = cpu_oracle_rate(D, C, G, budget_s=per_step)
+        if i >= args.warmup:
+            rates.append((h, t))
+    H = sum(h for h, _ in rates)
+    T = sum(t for _, t in rates)
+    value = H / T
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * T / len(rates),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD_NAME, "reference": "FP64 CPU oracle (oracle/wg_oracle.cpp), "
+                                                             "bounded sample per step"},
+           "cpu_baseline": dict(base, value=value),
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local, pg = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    dev = local
+    torch.cuda.set_device(dev)
+    from paper_2601_04370_gb300 import wg
+    pk, pk_kind = peaks()
+    D, C = workload(rank)
+    ctx = wg.Context(dev)
+    dh = ctx.create_design(D)
+    tally = torch.zeros(C.tally_shape, dtype=torch.float64, device="cuda")
+    G = torch.zeros_like(tally)
+    grad = torch.zeros(D.total_layers, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    # work counts of one step (the same keys every step)
+    st_f = ctx.trace_forward(dh, C, tally)
+    loss = ctx.loss(dh, C, tally, G)
+    st_b = ctx.trace_backward(dh, C, G, grad)
+    hits = st_f["n_hits"]
+    flops_fwd = FLOPS_FWD_LAYER * st_f["n_layer_steps"]
+    flops_bwd = FLOPS_FWD_LAYER * st_b["n_layer_steps"] + FLOPS_ADJ_LAYER * st_b["n_adjoint_steps"]
+
+    def step(evs):
+        flush.zero_()
+        evs[0].record(stream)
+        ctx.trace_forward(dh, C, tally, stats=False)
+        evs[1].record(stream)
+        ctx.loss(dh, C, tally, G)
+        evs[2].record(stream)
+        ctx.trace_backward(dh, C, G, grad, stats=False)
+        evs[3].record(stream)
+
+    for _ in range(args.warmup):
+        step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
+    torch.cuda.synchronize()
+    barrier(pg, dev)
+    torch.cuda.synchronize()
+    clocks = Clocks(dev)
+    clocks.start()
+    n0 = wg.kernel_launches()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        step(evs[i])
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    barrier(pg, dev)
+    torch.cuda.synchronize()
+    launches = wg.kernel_launches() - n0
+    ck = clocks.stop()
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]
+    fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    bwd_ms = [e[2].elapsed_time(e[3]) for e in evs]
+    t_dev = sum(step_ms) / 1e3
+    t_max = allmax(pg, t_dev, dev)
+    hits_all = allsum(pg, hits * args.steps, dev)
+    value = hits_all / t_max
+    fwd_rate = allsum(pg, hits * args.steps, dev) / allmax(pg, sum(fwd_ms) / 1e3, dev)
+
+    # end to end through the C ABI with host buffers: thickness from pinned
+    # host memory in, loss and gradient out, every step
+    th_host = torch.tensor(D.layer_d_nm, dtype=torch.float32).pin_memory().numpy()
+    g_host = np.zeros(D.total_layers)
+    cfg_bytes = 4 * (len(C.lam_nm) + len(C.fx_deg) + len(C.fy_deg))
+    h2d = th_host.nbytes + 2 * cfg_bytes
+    d2h = 4 * 8 + g_host.nbytes
+    e2e_t = []
+    barrier(pg, dev)
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dh.set_params(thickness_nm=th_host)
+        ctx.trace_forward(dh, C, tally, stats=False)
+        ctx.loss(dh, C, tally, G)
+        ctx.trace_backward(dh, C, G, g_host, stats=False)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_max = allmax(pg, sum(e2e_t), dev)
+    e2e_value = hits_all / e2e_max
+
+    out = None
+    if rank == 0:
+        sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        smax = float(pk.get("sm_max_mhz", 2070.0))
+        peak = fp32_peak_tflops(sm, smax)
+        bwd_s = statistics.mean(bwd_ms) / 1e3
+        fwd_s = statistics.mean(fwd_ms) / 1e3
+        ach_b = flops_bwd / bwd_s / 1e12
+        ach_f = flops_fwd / fwd_s / 1e12
+        roof = {"bound": "alu", "kernel": "k_trace_bwd", "achieved": ach_b, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach_b / peak, "traffic": profile_traffic("k_trace_bwd"),
+                "peak_source": f"derived: {sm} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz "
+                               f"(sm_max_mhz of {pk_kind} peaks)"}
+        roof_f = {"bound": "alu", "kernel": "k_trace_fwd", "achieved": ach_f, "peak": peak, "unit": "TFLOP/s",
+                  "frac": ach_f / peak, "traffic": profile_traffic("k_trace_fwd")}
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            cpu, _, _ = cpu_oracle_rate(D, C, G.cpu().numpy(), budget_s=args.cpu_budget)
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": WORKLOAD_NAME, "rays_per_gpu": C.total_rays,
+                          "interactions_per_step_per_gpu": hits, "l2": "flushed between steps (256 MiB write)",
+                          "parallelism": f"replicas x{ws} (rays sharded by seed, no collective)"},
+               "fwd_interactions_per_s": fwd_rate, "fwd_ms": statistics.mean(fwd_ms),
+               "bwd_ms": statistics.mean(bwd_ms), "loss": loss[0], "wall_s": t_wall,
+               "roofline": roof, "roofline_fwd": roof_f, "cpu_baseline": cpu,
+               "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+               "gpu_launches": launches, "clocks": ck}
+        print(json.dumps(out))
+    dh.destroy()
+    ctx.close()
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,272 @@
+/*
+ * wg.h - C ABI of the GB300 waveguide ray-trace library (libwg.so).
+ *
+ * The library evaluates the hot path of "End-to-end differentiable design of
+ * geometric waveguide displays" (arXiv 2601.04370): Monte Carlo
+ * non-sequential polarization ray tracing through a slab waveguide with a
+ * partially reflective mirror array (PRMA), a multilayer thin-film
+ * transfer-matrix evaluation at every ray-mirror hit, the eyebox tally, the
+ * loss of Eq. 1 and the adjoint of the whole chain with respect to the layer
+ * thicknesses. All arithmetic runs in hand-written CUDA kernels for sm_103a.
+ *
+ * Conventions (every entry point):
+ *  - Every call returns a wg_status (0 = WG_OK, negative = error) and never
+ *    aborts the process; wg_last_error() returns a message for the calling
+ *    thread's last failure.
+ *  - Lengths are mm, layer thicknesses and wavelengths nm, angles degrees.
+ *  - A `stream` argument is a cudaStream_t passed as void*; NULL means the
+ *    legacy default stream. Calls are stream-ordered unless stated otherwise.
+ *  - Pointers documented as "host or device" are inspected with
+ *    cudaPointerGetAttributes: device pointers are used in place; host
+ *    pointers are staged through device memory inside the call (the call then
+ *    synchronizes its stream before returning).
+ *  - Tally layout: row-major [lambda][field_y][field_x][eyebox_y][eyebox_x],
+ *    FP64. Thickness-gradient layout: the design's layers, mirror by mirror,
+ *    layer 1 first (the order of wg_design_desc.layer_thickness_nm).
+ *  - Inputs are FP32 at the boundary except tallies and gradients (FP64);
+ *    the kernels compute in FP32 and accumulate tallies/gradients in FP64.
+ */
+#ifndef WG_H_
+#define WG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t wg_status;
+#define WG_OK 0
+#define WG_EINVAL (-1)      /* invalid argument or design */
+#define WG_ENOMEM (-2)      /* device allocation failed / admission refused */
+#define WG_EBUSY (-3)       /* request queue full */
+#define WG_ENOTREADY (-4)   /* poll timed out; request still running */
+#define WG_ETIMEOUT (-5)    /* a bounded device wait ran out */
+#define WG_ECANCELED (-6)   /* request was cancelled */
+#define WG_EDEVICE (-7)     /* CUDA runtime error */
+#define WG_ENOTFOUND (-8)   /* unknown ticket */
+
+#define WG_MAX_MIRRORS 64
+#define WG_MAX_MATERIALS 4
+#define WG_MAX_EVENTS 128   /* upper bound of wg_trace_cfg.max_events */
+
+/* polarization of the launched light */
+#define WG_POL_PAIR 0          /* unpolarized: s and p Jones pair, I = (I_s+I_p)/2 */
+#define WG_POL_RANDOM_LINEAR 1 /* linear at angle pi*u per ray */
+#define WG_POL_S 2
+#define WG_POL_P 3
+
+/* energy ledger slots (wg_stats.ledger) */
+#define WG_LEDGER_EYEBOX 0     /* tallied intensity */
+#define WG_LEDGER_MISSED 1     /* left through the eye-side face outside the eyebox */
+#define WG_LEDGER_EXIT_REFL 2  /* Fresnel-reflected remainder at eye-side exits */
+#define WG_LEDGER_LEAKED 3     /* left through the back face */
+#define WG_LEDGER_ABSORBED 4   /* hit the input mirror side, the far end or a lateral side */
+#define WG_LEDGER_TRUNCATED 5  /* still alive after max_events surface events */
+
+typedef struct wg_ctx wg_ctx;
+typedef struct wg_design wg_design;
+
+typedef struct wg_init_opts {
+  int32_t device;              /* CUDA device ordinal */
+  int32_t max_slots;           /* serving: requests admitted at once (0 = 64) */
+  size_t hbm_budget_bytes;     /* serving: admission budget (0 = 80% of free HBM) */
+  const char* autotune_cache;  /* serving: file for autotuned launch shapes, or NULL */
+} wg_init_opts;
+
+/*
+ * Waveguide design (Results, "System Architecture"): a glass slab
+ * 0 <= z <= thickness with TIR faces, an input mirror (plane through the
+ * origin tilted by ic_tilt_deg about y) that couples the panel's rays in, and
+ * K partially reflective mirrors, mirror k a plane through
+ * (mirror_x_mm[k], 0, thickness/2) with normal (-sin a, 0, cos a),
+ * a = mirror_tilt_deg[k]. Each mirror carries a lossless multilayer stack;
+ * layer 1 faces the +normal side. A pruned layer has zero thickness and is
+ * skipped. mirror_omega[k] is the Monte Carlo reflection probability
+ * (Methods, "Differentiable Monte Carlo ...", Eq. 5), 0 < omega < 1.
+ * All arrays are host memory owned by the caller; wg_create_design copies
+ * them.
+ */
+typedef struct wg_design_desc {
+  int32_t dims;         /* 2 (x-z plane) or 3 */
+  int32_t n_materials;  /* <= WG_MAX_MATERIALS */
+  int32_t n_mirrors;    /* 1..WG_MAX_MIRRORS */
+  int32_t reserved;
+  float n_slab, thickness_mm, width_mm, x_end_mm, eye_relief_mm, ic_tilt_deg;
+  const float* material_n;          /* [n_materials] refractive index */
+  const float* mirror_x_mm;         /* [n_mirrors] */
+  const float* mirror_tilt_deg;     /* [n_mirrors] */
+  const float* mirror_omega;        /* [n_mirrors] */
+  const int32_t* n_layers;          /* [n_mirrors] */
+  const int32_t* layer_material;    /* [sum n_layers] material index */
+  const float* layer_thickness_nm;  /* [sum n_layers] */
+  const uint8_t* layer_pruned;      /* [sum n_layers] 1 = pruned, or NULL */
+} wg_design_desc;
+
+/*
+ * Trace configuration (Results, "System Architecture": parallel rays per
+ * field-of-view sample from the panel, several wavelengths, an eyebox grid at
+ * the eye relief). Ray r belongs to cell r / N_cell, N_cell =
+ * ceil(n_rays / (n_lambda * n_fx * n_fy)); cell = (lambda * n_fy + fy) * n_fx
+ * + fx. Its random numbers are Philox4x32-10 with key = seed and counter
+ * (r_lo, r_hi, 0, "GEN0") for the launch, (r_lo, r_hi, m >> 2, "EVT0") word
+ * m & 3 for the decision at its m-th mirror hit.
+ */
+typedef struct wg_trace_cfg {
+  int32_t n_lambda, n_fx, n_fy, pol;
+  const float* lambda_nm;     /* host [n_lambda] */
+  const float* field_x_deg;   /* host [n_fx] field angle about y, in air */
+  const float* field_y_deg;   /* host [n_fy] field angle about x, in air (2D: one value, 0) */
+  int64_t n_rays;             /* requested rays (rounded up to whole cells) */
+  uint64_t seed;
+  int32_t max_events;         /* surface events per ray, <= WG_MAX_EVENTS */
+  int32_t eb_nx, eb_ny;       /* eyebox bins (2D: eb_ny = 1) */
+  int32_t flags;              /* reserved, 0 */
+  float pupil_y_mm;           /* 3D: lateral extent of the launch region */
+  float eb_cx_mm, eb_cy_mm, eb_w_mm, eb_h_mm;  /* eyebox centre and size */
+  void* stream;               /* cudaStream_t or NULL */
+  int64_t ray_begin, ray_end; /* traced ray ids [begin, end); end <= 0: all */
+  void* ray_records;          /* NULL or device wg_ray_record[end - begin] */
+} wg_trace_cfg;
+
+/* per-ray record written when wg_trace_cfg.ray_records != NULL */
+typedef struct wg_ray_record {
+  uint32_t hash;     /* FNV-1a over (surface id | 0x80 if reflected at a mirror) per event */
+  int32_t n_events;  /* surface events */
+  int32_t n_hits;    /* ray-mirror (PRMA) interactions */
+  int32_t cat;       /* WG_LEDGER_* category of the ray's end */
+  int32_t bin;       /* flat tally index, -1 if not tallied */
+  float intensity;   /* tallied intensity (0 if not tallied) */
+  float weight;      /* |E|^2 at the ray's end (pair-averaged) */
+  int32_t pad;
+} wg_ray_record;
+
+typedef struct wg_stats {
+  int64_t n_rays;         /* rays traced */
+  int64_t n_hits;         /* ray-mirror (PRMA) interactions: the throughput unit */
+  int64_t n_events;       /* all surface events */
+  int64_t n_tir;          /* total internal reflections */
+  int64_t n_layer_steps;  /* transfer-matrix layer steps (sum of layers over hits) */
+  double ledger[6];       /* energy by WG_LEDGER_* slot, in units of launched power */
+  float kernel_ms;        /* device time of the main kernel (CUDA events) */
+  int32_t overflow;       /* backward: rays with more than 64 mirror hits (gradient skipped) */
+  int64_t n_tallied;      /* backward: rays that ended in the eyebox */
+  int64_t n_adjoint_steps;/* backward: layer steps of the thin-film adjoint */
+  int64_t n_nonfinite;    /* backward: non-finite per-layer terms dropped (expected 0) */
+} wg_stats;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Creates a context on opts->device (NULL opts: device 0, defaults).
+ * Errors: WG_EINVAL (bad device), WG_EDEVICE. Owns no caller memory. */
+wg_status wg_init(wg_ctx** ctx, const wg_init_opts* opts);
+
+/* Stops the serving thread, frees every device buffer of the context and of
+ * designs still alive. Safe on NULL. */
+void wg_shutdown(wg_ctx* ctx);
+
+/* Message of the calling thread's last failed call (static storage). */
+const char* wg_last_error(void);
+
+/* Library version string. */
+const char* wg_version(void);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * entry points, all contexts). Lets a caller count the kernels of a timed
+ * region. */
+uint64_t wg_kernel_launches(void);
+
+/* ---- designs ---------------------------------------------------------- */
+
+/* Validates and uploads a design (deep copy; the caller keeps its arrays).
+ * Errors: WG_EINVAL (dims, counts, NaN or negative thickness, omega outside
+ * (0,1), index out of range), WG_ENOMEM. */
+wg_status wg_create_design(wg_ctx* ctx, const wg_design_desc* desc, wg_design** out);
+
+/* Optimizer step: replaces thicknesses ([sum n_layers], host or device, FP32;
+ * NULL keeps them) and tilts ([n_mirrors], host, degrees; NULL keeps them).
+ * Pruned layers keep zero thickness. Stream-ordered on `stream`.
+ * Errors: WG_EINVAL on size mismatch or invalid values. */
+wg_status wg_set_params(wg_design* d, const float* thickness_nm, int64_t n_thickness,
+                        const float* tilt_deg, int32_t n_tilt, void* stream);
+
+/* Frees the design's device memory (after its stream work completes). */
+void wg_destroy_design(wg_design* d);
+
+/* ---- thin-film coating (Methods, "Multilayer thin-film solver") ------- */
+
+/*
+ * Effective coefficients of mirror `mirror`'s stack between two half-spaces
+ * of slab glass, by the characteristic-matrix method (Heavens): per layer
+ * delta = 2 pi n d cos(theta)/lambda and M = [[cos d, i sin d/eta],
+ * [i eta sin d, cos d]], eta_s = n cos, eta_p = n / cos. Results use the
+ * paper's Fresnel sign convention (r_p = -r_s at normal incidence).
+ * side = 0: light arrives on the +normal side (layer 1 first); 1: reversed.
+ * cos_theta, lambda_nm: device [n]; out_rt: device [n][8] =
+ * Re/Im of r_s, r_p, t_s, t_p. Errors: WG_EINVAL.
+ */
+wg_status wg_eval_coating(wg_ctx* ctx, const wg_design* d, int32_t mirror, int32_t side, int64_t n,
+                          const float* cos_theta, const float* lambda_nm, float* out_rt, void* stream);
+
+/*
+ * Gradient of f = 2 Re(A_s c_s + A_p c_p) (c = r if which == 0, t if 1) with
+ * respect to each non-pruned layer thickness of the mirror's stack, in
+ * traversal order, by the checkpointed reverse sweep the adjoint kernel uses.
+ * weights: device [n][4] = Re A_s, Im A_s, Re A_p, Im A_p. grad: device
+ * [n][L] (L = non-pruned layers of the mirror, per nm, FP32).
+ */
+wg_status wg_eval_coating_grad(wg_ctx* ctx, const wg_design* d, int32_t mirror, int32_t side, int64_t n,
+                               const float* cos_theta, const float* lambda_nm, const float* weights,
+                               int32_t which, float* grad, void* stream);
+
+/* ---- trace, loss, adjoint --------------------------------------------- */
+
+/*
+ * Forward Monte Carlo trace (Methods, "Polarization ray tracing" Eq. 4 and
+ * "Differentiable Monte Carlo ..." Eq. 5; intensity I = sum |E|^2).
+ * Per ray: launch on the input mirror, TIR at the slab faces (Fresnel with an
+ * evanescent transmitted wave), at every mirror hit the stack's (r_s, r_p,
+ * t_s, t_p), projection onto the local s/p basis, reflect with probability
+ * omega and rescale the field by 1/sqrt(omega) or 1/sqrt(1-omega); at the
+ * eye-side face the Fresnel power transmission into air, propagation to the
+ * eye plane and an FP64 tally.
+ * tally: host or device, FP64, tally layout, overwritten for the traced cells
+ * (zeroed first). stats: host, optional (NULL: no synchronization).
+ * Errors: WG_EINVAL, WG_ENOMEM, WG_EDEVICE.
+ */
+wg_status wg_trace_forward(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cfg, double* tally,
+                           wg_stats* stats);
+
+/*
+ * Loss of Results Eq. 1 on a tally: L = -I_mean + w_f U_FoV + w_e U_eyebox,
+ * with pupil images I[lambda, field, pupil] = sum of the tally over 3x3
+ * discs of 4 mm diameter spanning the eyebox (3 intervals in 2D), divided by
+ * rays per cell; U = coefficient of variation (kind 0, paper) or variance
+ * (kind 1), averaged over the other axes. tally: device FP64. out: host
+ * double[4] = L, I_mean, U_FoV, U_eyebox (the call synchronizes). dL_dtally:
+ * device FP64, tally layout, or NULL.
+ */
+wg_status wg_loss(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cfg, int32_t kind, double w_f,
+                  double w_e, const double* tally, double* out, double* dL_dtally);
+
+/*
+ * Adjoint of the trace with respect to layer thicknesses: replays every ray
+ * from its Philox key (nothing is stored by the forward pass), propagates
+ * G[bin] dI/dE backwards through the ray's Jones maps, and back-propagates
+ * each hit's coefficient sensitivity through the characteristic-matrix chain
+ * (checkpointed forward products, no matrix inversion). The sampled path is
+ * held fixed (the sampling does not depend on the thicknesses).
+ * dL_dtally: host or device FP64 in tally layout. grad_thickness: host or
+ * device FP64 [sum n_layers] (pruned layers get 0), overwritten. grad_tilt:
+ * reserved, must be NULL. Errors: WG_EINVAL, WG_ENOMEM, WG_EDEVICE.
+ */
+wg_status wg_trace_backward(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cfg,
+                            const double* dL_dtally, double* grad_thickness, double* grad_tilt,
+                            wg_stats* stats);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WG_H_ */

@@ -1,0 +1,697 @@
+// C ABI of libwg.so: contexts, designs, and the trace / loss / adjoint entry
+// points declared in include/wg.h. Host code here validates arguments, lays
+// out device buffers and launches the kernels; every step of the hot path's
+// arithmetic runs in the kernels of wg_trace.cu and wg_loss.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "wg.h"
+#include "wg_device.cuh"
+#include "wg_internal.h"
+
+using namespace wgk;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+
+static wg_status fail(wg_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return st;
+}
+
+#define CU(call)                                                                                       \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess) return fail(WG_EDEVICE, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+extern "C" const char* wg_last_error(void) { return g_err.c_str(); }
+extern "C" const char* wg_version(void) { return "wg 0.1 (sm_103a)"; }
+extern "C" uint64_t wg_kernel_launches(void) { return (uint64_t)launches(); }
+
+// ---------------------------------------------------------------------------
+// objects
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= n) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e == cudaSuccess) n = bytes;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+struct wg_ctx {
+  int device = 0;
+  int sm_count = 0;
+  std::mutex mu;
+  DevBuf ws;      // small per-call workspace (counters, cfg arrays, fields)
+  DevBuf bwd;     // adjoint scratch (hit records, per-CTA rows)
+  DevBuf loss;    // loss workspace
+  cudaEvent_t ws_free = nullptr;  // last use of the workspaces
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  int max_slots = 64;
+  size_t hbm_budget = 0;
+  std::vector<wg_design*> designs;
+};
+
+struct wg_design {
+  wg_ctx* ctx = nullptr;
+  int dims = 3, n_mat = 0, K = 0, n_orig = 0, n_dev = 0;
+  float n_slab = 0, thick = 0, width = 0, x_end = 0, eye_relief = 0, ic_tilt = 0;
+  std::vector<float> mat_n, mir_x, mir_tilt, omega, layer_d;
+  std::vector<int> n_layers, layer_mat, orig_to_dev, dev_to_orig;
+  std::vector<uint8_t> pruned;
+  uint8_t* blob = nullptr;
+  int blob_bytes = 0;
+  float* d_mir = nullptr;      // [3][K]: x, tilt, omega
+  int* d_orig_to_dev = nullptr;
+  int* d_dev_to_orig = nullptr;
+  float* d_stage = nullptr;    // [n_orig] thickness staging for set_params
+};
+
+static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" wg_status wg_init(wg_ctx** out, const wg_init_opts* opts) {
+  if (!out) return fail(WG_EINVAL, "wg_init: out is NULL");
+  *out = nullptr;
+  int dev = opts ? opts->device : 0;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return fail(WG_EDEVICE, "wg_init: no CUDA device");
+  }
+  if (dev < 0 || dev >= n) return fail(WG_EINVAL, "wg_init: device %d out of range [0,%d)", dev, n);
+  CU(cudaSetDevice(dev));
+  cudaDeviceProp prop;
+  CU(cudaGetDeviceProperties(&prop, dev));
+  wg_ctx* c = new wg_ctx();
+  c->device = dev;
+  c->sm_count = prop.multiProcessorCount;
+  if (opts && opts->max_slots > 0) c->max_slots = opts->max_slots;
+  if (opts) c->hbm_budget = opts->hbm_budget_bytes;
+  if (cudaEventCreateWithFlags(&c->ws_free, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&c->t0) != cudaSuccess || cudaEventCreate(&c->t1) != cudaSuccess) {
+    delete c;
+    return fail(WG_EDEVICE, "wg_init: event creation failed");
+  }
+  *out = c;
+  return WG_OK;
+}
+
+static void destroy_design_dev(wg_design* d) {
+  if (d->blob) cudaFree(d->blob);
+  if (d->d_mir) cudaFree(d->d_mir);
+  if (d->d_orig_to_dev) cudaFree(d->d_orig_to_dev);
+  if (d->d_dev_to_orig) cudaFree(d->d_dev_to_orig);
+  if (d->d_stage) cudaFree(d->d_stage);
+  d->blob = nullptr;
+}
+
+extern "C" void wg_shutdown(wg_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  for (wg_design* d : c->designs) {
+    destroy_design_dev(d);
+    delete d;
+  }
+  c->ws.release();
+  c->bwd.release();
+  c->loss.release();
+  if (c->ws_free) cudaEventDestroy(c->ws_free);
+  if (c->t0) cudaEventDestroy(c->t0);
+  if (c->t1) cudaEventDestroy(c->t1);
+  delete c;
+}
+
+// ---------------------------------------------------------------------------
+// designs
+// ---------------------------------------------------------------------------
+static wg_status validate_desc(const wg_design_desc* s) {
+  if (!s) return fail(WG_EINVAL, "design: desc is NULL");
+  if (s->dims != 2 && s->dims != 3) return fail(WG_EINVAL, "design: dims must be 2 or 3 (got %d)", s->dims);
+  if (s->n_materials < 1 || s->n_materials > WG_MAX_MATERIALS)
+    return fail(WG_EINVAL, "design: n_materials must be in [1,%d]", WG_MAX_MATERIALS);
+  if (s->n_mirrors < 1 || s->n_mirrors > WG_MAX_MIRRORS)
+    return fail(WG_EINVAL, "design: n_mirrors must be in [1,%d]", WG_MAX_MIRRORS);
+  if (!s->material_n || !s->mirror_x_mm || !s->mirror_tilt_deg || !s->mirror_omega || !s->n_layers ||
+      !s->layer_material || !s->layer_thickness_nm)
+    return fail(WG_EINVAL, "design: NULL array");
+  if (!(s->n_slab > 1.0f) || !(s->thickness_mm > 0.0f) || !(s->eye_relief_mm > 0.0f) || !(s->width_mm > 0.0f))
+    return fail(WG_EINVAL, "design: n_slab > 1, thickness, width and eye relief > 0 required");
+  if (!(s->ic_tilt_deg > 0.0f && s->ic_tilt_deg < 90.0f)) return fail(WG_EINVAL, "design: ic_tilt_deg in (0,90)");
+  for (int i = 0; i < s->n_materials; ++i)
+    if (!(s->material_n[i] >= 1.0f) || !std::isfinite(s->material_n[i]))
+      return fail(WG_EINVAL, "design: material %d index must be finite and >= 1", i);
+  long long total = 0;
+  for (int k = 0; k < s->n_mirrors; ++k) {
+    if (s->n_layers[k] < 0 || s->n_layers[k] > MAX_LAYERS_MIRROR)
+      return fail(WG_EINVAL, "design: mirror %d layer count must be in [0,%d]", k, MAX_LAYERS_MIRROR);
+    if (!(s->mirror_omega[k] > 0.0f && s->mirror_omega[k] < 1.0f))
+      return fail(WG_EINVAL, "design: mirror %d omega must be in (0,1)", k);
+    if (!std::isfinite(s->mirror_x_mm[k]) || !std::isfinite(s->mirror_tilt_deg[k]) ||
+        !(std::fabs(s->mirror_tilt_deg[k]) < 89.0f))
+      return fail(WG_EINVAL, "design: mirror %d position/tilt invalid", k);
+    total += s->n_layers[k];
+  }
+  for (long long i = 0; i < total; ++i) {
+    if (s->layer_material[i] < 0 || s->layer_material[i] >= s->n_materials)
+      return fail(WG_EINVAL, "design: layer %lld material out of range", i);
+    const float d = s->layer_thickness_nm[i];
+    if (!std::isfinite(d) || d < 0.0f) return fail(WG_EINVAL, "design: layer %lld thickness must be finite and >= 0", i);
+  }
+  return WG_OK;
+}
+
+// host layout of the blob; geometry-derived fields are filled by k_prep_design
+static std::vector<uint8_t> build_blob(const wg_design& d) {
+  const size_t off_mir = sizeof(BlobHeader);
+  const size_t off_d = align16(off_mir + sizeof(MirrorRec) * d.K);
+  const size_t off_m = align16(off_d + sizeof(float) * d.n_dev);
+  const size_t bytes = align16(off_m + (size_t)d.n_dev + 1);
+  std::vector<uint8_t> b(bytes, 0);
+  BlobHeader h;
+  memset(&h, 0, sizeof(h));
+  h.dims = d.dims;
+  h.n_mat = d.n_mat;
+  h.n_mir = d.K;
+  h.n_layers = d.n_dev;
+  h.n_slab = d.n_slab;
+  h.thick = d.thick;
+  h.half_w = 0.5f * d.width;
+  h.x_end = d.x_end;
+  h.eye_relief = d.eye_relief;
+  for (int i = 0; i < d.n_mat; ++i) h.mat_n[i] = d.mat_n[i];
+  h.off_mir = (int)off_mir;
+  h.off_d = (int)off_d;
+  h.off_m = (int)off_m;
+  h.bytes = (int)bytes;
+  memcpy(b.data(), &h, sizeof(h));
+  MirrorRec* mir = reinterpret_cast<MirrorRec*>(b.data() + off_mir);
+  float* dd = reinterpret_cast<float*>(b.data() + off_d);
+  uint8_t* mm = b.data() + off_m;
+  int orig = 0, dev = 0;
+  for (int k = 0; k < d.K; ++k) {
+    MirrorRec r;
+    memset(&r, 0, sizeof(r));
+    r.layer_off = dev;
+    for (int l = 0; l < d.n_layers[k]; ++l, ++orig) {
+      if (d.pruned[orig]) continue;
+      dd[dev] = d.layer_d[orig];
+      mm[dev] = (uint8_t)d.layer_mat[orig];
+      ++dev;
+    }
+    r.n_layers = dev - r.layer_off;
+    mir[k] = r;
+  }
+  return b;
+}
+
+static wg_status upload_design(wg_design* d, cudaStream_t s) {
+  std::vector<uint8_t> b = build_blob(*d);
+  d->blob_bytes = (int)b.size();
+  CU(cudaMalloc(&d->blob, b.size()));
+  CU(cudaMemcpyAsync(d->blob, b.data(), b.size(), cudaMemcpyHostToDevice, s));
+  CU(cudaMalloc(&d->d_mir, sizeof(float) * 3 * d->K));
+  std::vector<float> m(3 * d->K);
+  for (int k = 0; k < d->K; ++k) {
+    m[k] = d->mir_x[k];
+    m[d->K + k] = d->mir_tilt[k];
+    m[2 * d->K + k] = d->omega[k];
+  }
+  CU(cudaMemcpyAsync(d->d_mir, m.data(), sizeof(float) * m.size(), cudaMemcpyHostToDevice, s));
+  CU(cudaMalloc(&d->d_orig_to_dev, sizeof(int) * std::max(1, d->n_orig)));
+  CU(cudaMalloc(&d->d_dev_to_orig, sizeof(int) * std::max(1, d->n_dev)));
+  CU(cudaMalloc(&d->d_stage, sizeof(float) * std::max(1, d->n_orig)));
+  if (d->n_orig)
+    CU(cudaMemcpyAsync(d->d_orig_to_dev, d->orig_to_dev.data(), sizeof(int) * d->n_orig, cudaMemcpyHostToDevice, s));
+  if (d->n_dev)
+    CU(cudaMemcpyAsync(d->d_dev_to_orig, d->dev_to_orig.data(), sizeof(int) * d->n_dev, cudaMemcpyHostToDevice, s));
+  CU(launch_prep_design(d->blob, d->d_mir, d->d_mir + d->K, d->d_mir + 2 * d->K, d->K, d->ic_tilt, d->thick, s));
+  CU(cudaStreamSynchronize(s));
+  return WG_OK;
+}
+
+extern "C" wg_status wg_create_design(wg_ctx* c, const wg_design_desc* s, wg_design** out) {
+  if (!c || !out) return fail(WG_EINVAL, "wg_create_design: NULL ctx/out");
+  *out = nullptr;
+  wg_status st = validate_desc(s);
+  if (st != WG_OK) return st;
+  std::lock_guard<std::mutex> lk(c->mu);
+  CU(cudaSetDevice(c->device));
+  wg_design* d = new wg_design();
+  d->ctx = c;
+  d->dims = s->dims;
+  d->n_mat = s->n_materials;
+  d->K = s->n_mirrors;
+  d->n_slab = s->n_slab;
+  d->thick = s->thickness_mm;
+  d->width = s->width_mm;
+  d->x_end = s->x_end_mm;
+  d->eye_relief = s->eye_relief_mm;
+  d->ic_tilt = s->ic_tilt_deg;
+  d->mat_n.assign(s->material_n, s->material_n + d->n_mat);
+  d->mir_x.assign(s->mirror_x_mm, s->mirror_x_mm + d->K);
+  d->mir_tilt.assign(s->mirror_tilt_deg, s->mirror_tilt_deg + d->K);
+  d->omega.assign(s->mirror_omega, s->mirror_omega + d->K);
+  d->n_layers.assign(s->n_layers, s->n_layers + d->K);
+  int total = 0;
+  for (int k = 0; k < d->K; ++k) total += d->n_layers[k];
+  d->n_orig = total;
+  d->layer_mat.assign(s->layer_material, s->layer_material + total);
+  d->layer_d.assign(s->layer_thickness_nm, s->layer_thickness_nm + total);
+  d->pruned.assign(total, 0);
+  if (s->layer_pruned)
+    for (int i = 0; i < total; ++i) d->pruned[i] = s->layer_pruned[i] ? 1 : 0;
+  d->orig_to_dev.assign(total, -1);
+  for (int i = 0; i < total; ++i) {
+    if (d->pruned[i]) {
+      d->layer_d[i] = 0.0f;
+      continue;
+    }
+    d->orig_to_dev[i] = (int)d->dev_to_orig.size();
+    d->dev_to_orig.push_back(i);
+  }
+  d->n_dev = (int)d->dev_to_orig.size();
+  st = upload_design(d, 0);
+  if (st != WG_OK) {
+    destroy_design_dev(d);
+    delete d;
+    return st;
+  }
+  c->designs.push_back(d);
+  *out = d;
+  return WG_OK;
+}
+
+extern "C" void wg_destroy_design(wg_design* d) {
+  if (!d) return;
+  wg_ctx* c = d->ctx;
+  std::lock_guard<std::mutex> lk(c->mu);
+  cudaSetDevice(c->device);
+  cudaEventSynchronize(c->ws_free);
+  cudaDeviceSynchronize();
+  c->designs.erase(std::remove(c->designs.begin(), c->designs.end(), d), c->designs.end());
+  destroy_design_dev(d);
+  delete d;
+}
+
+extern "C" wg_status wg_set_params(wg_design* d, const float* thickness_nm, int64_t n_thickness,
+                                   const float* tilt_deg, int32_t n_tilt, void* stream) {
+  if (!d) return fail(WG_EINVAL, "wg_set_params: NULL design");
+  wg_ctx* c = d->ctx;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(c->mu);
+  CU(cudaSetDevice(c->device));
+  if (thickness_nm) {
+    if (n_thickness != d->n_orig) return fail(WG_EINVAL, "wg_set_params: %lld thicknesses for %d layers",
+                                              (long long)n_thickness, d->n_orig);
+    if (is_device_ptr(thickness_nm)) {
+      CU(cudaMemcpyAsync(d->d_stage, thickness_nm, sizeof(float) * d->n_orig, cudaMemcpyDeviceToDevice, s));
+    } else {
+      for (int i = 0; i < d->n_orig; ++i)
+        if (!std::isfinite(thickness_nm[i]) || thickness_nm[i] < 0.0f)
+          return fail(WG_EINVAL, "wg_set_params: thickness %d invalid", i);
+      for (int i = 0; i < d->n_orig; ++i) d->layer_d[i] = d->pruned[i] ? 0.0f : thickness_nm[i];
+      CU(cudaMemcpyAsync(d->d_stage, thickness_nm, sizeof(float) * d->n_orig, cudaMemcpyHostToDevice, s));
+    }
+    CU(launch_thickness_update(d->blob, d->d_stage, d->d_orig_to_dev, d->n_orig, s));
+  }
+  if (tilt_deg) {
+    if (n_tilt != d->K) return fail(WG_EINVAL, "wg_set_params: %d tilts for %d mirrors", n_tilt, d->K);
+    for (int k = 0; k < d->K; ++k)
+      if (!std::isfinite(tilt_deg[k]) || !(std::fabs(tilt_deg[k]) < 89.0f))
+        return fail(WG_EINVAL, "wg_set_params: tilt %d invalid", k);
+    d->mir_tilt.assign(tilt_deg, tilt_deg + d->K);
+    CU(cudaMemcpyAsync(d->d_mir + d->K, tilt_deg, sizeof(float) * d->K, cudaMemcpyHostToDevice, s));
+    CU(launch_prep_design(d->blob, d->d_mir, d->d_mir + d->K, d->d_mir + 2 * d->K, d->K, d->ic_tilt, d->thick, s));
+  }
+  return WG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// coating hooks
+// ---------------------------------------------------------------------------
+extern "C" wg_status wg_eval_coating(wg_ctx* c, const wg_design* d, int32_t mirror, int32_t side, int64_t n,
+                                     const float* cos_theta, const float* lambda_nm, float* out_rt, void* stream) {
+  if (!c || !d) return fail(WG_EINVAL, "wg_eval_coating: NULL ctx/design");
+  if (mirror < 0 || mirror >= d->K || (side != 0 && side != 1) || n < 0)
+    return fail(WG_EINVAL, "wg_eval_coating: bad mirror/side/n");
+  if (n == 0) return WG_OK;
+  if (!is_device_ptr(cos_theta) || !is_device_ptr(lambda_nm) || !is_device_ptr(out_rt))
+    return fail(WG_EINVAL, "wg_eval_coating: arrays must be device memory");
+  std::lock_guard<std::mutex> lk(c->mu);
+  CU(cudaSetDevice(c->device));
+  CU(launch_coating_eval(d->blob, mirror, side, n, cos_theta, lambda_nm, out_rt, (cudaStream_t)stream));
+  return WG_OK;
+}
+
+extern "C" wg_status wg_eval_coating_grad(wg_ctx* c, const wg_design* d, int32_t mirror, int32_t side, int64_t n,
+                                          const float* cos_theta, const float* lambda_nm, const float* weights,
+                                          int32_t which, float* grad, void* stream) {
+  if (!c || !d) return fail(WG_EINVAL, "wg_eval_coating_grad: NULL ctx/design");
+  if (mirror < 0 || mirror >= d->K || (side != 0 && side != 1) || n < 0 || (which != 0 && which != 1))
+    return fail(WG_EINVAL, "wg_eval_coating_grad: bad mirror/side/which/n");
+  if (n == 0) return WG_OK;
+  if (!is_device_ptr(cos_theta) || !is_device_ptr(lambda_nm) || !is_device_ptr(weights) || !is_device_ptr(grad))
+    return fail(WG_EINVAL, "wg_eval_coating_grad: arrays must be device memory");
+  std::lock_guard<std::mutex> lk(c->mu);
+  CU(cudaSetDevice(c->device));
+  CU(launch_coating_grad(d->blob, mirror, side, n, cos_theta, lambda_nm, weights, which, grad, (cudaStream_t)stream));
+  return WG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// trace plumbing
+// ---------------------------------------------------------------------------
+struct Plan {
+  long long n_cells, n_cell, total, rb, re, cell_lo, cell_hi, chunk_rays, chunks_per_cell, n_chunks;
+  int n_f, bins, F;
+  long long tally_size;
+};
+
+static wg_status validate_cfg(const wg_design* d, const wg_trace_cfg* cfg) {
+  if (!cfg) return fail(WG_EINVAL, "cfg is NULL");
+  if (cfg->n_lambda < 1 || cfg->n_fx < 1 || cfg->n_fy < 1 || !cfg->lambda_nm || !cfg->field_x_deg || !cfg->field_y_deg)
+    return fail(WG_EINVAL, "cfg: need n_lambda, n_fx, n_fy >= 1 and their arrays");
+  if ((long long)cfg->n_fx * cfg->n_fy > 65536) return fail(WG_EINVAL, "cfg: at most 65536 fields");
+  if (d->dims == 2 && (cfg->n_fy != 1 || cfg->field_y_deg[0] != 0.0f || cfg->eb_ny != 1))
+    return fail(WG_EINVAL, "cfg: 2D designs take one field_y of 0 and eb_ny = 1");
+  if (cfg->pol < 0 || cfg->pol > 3) return fail(WG_EINVAL, "cfg: pol must be 0..3");
+  if (cfg->n_rays < 1) return fail(WG_EINVAL, "cfg: n_rays must be >= 1");
+  if (cfg->max_events < 1 || cfg->max_events > WG_MAX_EVENTS)
+    return fail(WG_EINVAL, "cfg: max_events must be in [1,%d]", WG_MAX_EVENTS);
+  if (cfg->eb_nx < 1 || cfg->eb_ny < 1 || (long long)cfg->eb_nx * cfg->eb_ny > 16384)
+    return fail(WG_EINVAL, "cfg: eyebox bins must be >= 1 and at most 16384 per cell");
+  if (!(cfg->eb_w_mm > 0.0f) || !(cfg->eb_h_mm > 0.0f)) return fail(WG_EINVAL, "cfg: eyebox size must be > 0");
+  for (int i = 0; i < cfg->n_lambda; ++i)
+    if (!(cfg->lambda_nm[i] > 0.0f) || !std::isfinite(cfg->lambda_nm[i]))
+      return fail(WG_EINVAL, "cfg: wavelength %d invalid", i);
+  for (int i = 0; i < cfg->n_fx; ++i)
+    if (!(std::fabs(cfg->field_x_deg[i]) < 80.0f)) return fail(WG_EINVAL, "cfg: field_x %d invalid", i);
+  for (int i = 0; i < cfg->n_fy; ++i)
+    if (!(std::fabs(cfg->field_y_deg[i]) < 80.0f)) return fail(WG_EINVAL, "cfg: field_y %d invalid", i);
+  if (cfg->flags != 0) return fail(WG_EINVAL, "cfg: flags must be 0");
+  return WG_OK;
+}
+
+static wg_status make_plan(const wg_design* d, const wg_trace_cfg* cfg, long long chunk_rays, Plan& p) {
+  wg_status st = validate_cfg(d, cfg);
+  if (st != WG_OK) return st;
+  p.n_f = cfg->n_fx * cfg->n_fy;
+  p.n_cells = (long long)cfg->n_lambda * p.n_f;
+  p.n_cell = (cfg->n_rays + p.n_cells - 1) / p.n_cells;
+  p.total = p.n_cell * p.n_cells;
+  p.rb = std::max<long long>(0, cfg->ray_begin);
+  p.re = cfg->ray_end > 0 ? std::min<long long>(cfg->ray_end, p.total) : p.total;
+  if (p.rb >= p.re) return fail(WG_EINVAL, "cfg: empty ray range [%lld, %lld)", p.rb, p.re);
+  p.cell_lo = p.rb / p.n_cell;
+  p.cell_hi = (p.re - 1) / p.n_cell;
+  p.chunk_rays = std::max<long long>(32, chunk_rays);
+  p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
+  p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
+  p.bins = cfg->eb_nx * cfg->eb_ny;
+  p.F = cfg->pol == WG_POL_PAIR ? 2 : 1;
+  p.tally_size = p.n_cells * p.bins;
+  return WG_OK;
+}
+
+// workspace head: counters[10] u64 | ledger[6] f64 | work u64 | error u32 | pad -> 256 B
+struct WsHead {
+  unsigned long long counters[10];
+  double ledger[6];
+  unsigned long long work;
+  unsigned int error;
+  unsigned int pad[19];
+};
+static_assert(sizeof(WsHead) <= 256, "workspace head");
+
+struct WsLayout {
+  WsHead* head;
+  float* lam;
+  float* fx;
+  float* fy;
+  FieldRec* fields;
+  size_t bytes;
+};
+
+static WsLayout ws_layout(void* base, const wg_trace_cfg* cfg, int n_f) {
+  WsLayout w;
+  uint8_t* b = (uint8_t*)base;
+  size_t off = 0;
+  w.head = (WsHead*)(b + off);
+  off += 256;
+  w.lam = (float*)(b + off);
+  off = align16(off + sizeof(float) * cfg->n_lambda);
+  w.fx = (float*)(b + off);
+  off = align16(off + sizeof(float) * cfg->n_fx);
+  w.fy = (float*)(b + off);
+  off = align16(off + sizeof(float) * cfg->n_fy);
+  w.fields = (FieldRec*)(b + off);
+  off = align16(off + sizeof(FieldRec) * n_f);
+  w.bytes = off;
+  return w;
+}
+
+static wg_status prepare_ws(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, const Plan& p, cudaStream_t s,
+                            WsLayout& w) {
+  w = ws_layout(nullptr, cfg, p.n_f);
+  CU(cudaStreamWaitEvent(s, c->ws_free, 0));
+  if (w.bytes > c->ws.n) {
+    CU(cudaEventSynchronize(c->ws_free));
+    CU(c->ws.ensure(w.bytes + 4096));
+  }
+  w = ws_layout(c->ws.p, cfg, p.n_f);
+  CU(cudaMemsetAsync(w.head, 0, 256, s));
+  CU(cudaMemcpyAsync(w.lam, cfg->lambda_nm, sizeof(float) * cfg->n_lambda, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(w.fx, cfg->field_x_deg, sizeof(float) * cfg->n_fx, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(w.fy, cfg->field_y_deg, sizeof(float) * cfg->n_fy, cudaMemcpyHostToDevice, s));
+  CU(launch_prep_fields(w.fields, w.fx, w.fy, cfg->n_fx, cfg->n_fy, d->n_slab, d->ic_tilt, d->dims, s));
+  return WG_OK;
+}
+
+static TraceArgs base_args(const wg_design* d, const wg_trace_cfg* cfg, const Plan& p, const WsLayout& w) {
+  TraceArgs a;
+  memset(&a, 0, sizeof(a));
+  a.blob = d->blob;
+  a.blob_bytes = d->blob_bytes;
+  a.fields = w.fields;
+  a.lambda = w.lam;
+  a.n_f = p.n_f;
+  a.pol = cfg->pol;
+  a.max_events = cfg->max_events;
+  a.bins = p.bins;
+  a.n_cell = p.n_cell;
+  a.ray_begin = p.rb;
+  a.ray_end = p.re;
+  a.cell_lo = p.cell_lo;
+  a.chunk_rays = p.chunk_rays;
+  a.chunks_per_cell = p.chunks_per_cell;
+  a.n_chunks = p.n_chunks;
+  a.key0 = (uint32_t)cfg->seed;
+  a.key1 = (uint32_t)(cfg->seed >> 32);
+  a.eb_nx = cfg->eb_nx;
+  a.eb_ny = cfg->eb_ny;
+  a.eb_x0 = cfg->eb_cx_mm - 0.5f * cfg->eb_w_mm;
+  a.eb_y0 = cfg->eb_cy_mm - 0.5f * cfg->eb_h_mm;
+  a.eb_sx = (float)cfg->eb_nx / cfg->eb_w_mm;
+  a.eb_sy = (float)cfg->eb_ny / cfg->eb_h_mm;
+  a.pupil_y = cfg->pupil_y_mm;
+  a.ledger = w.head->ledger;
+  a.counters = w.head->counters;
+  a.work = &w.head->work;
+  a.error = &w.head->error;
+  a.records = cfg->ray_records;
+  a.n_layers = d->n_dev;
+  return a;
+}
+
+static wg_status finish_stats(wg_ctx* c, const WsLayout& w, cudaStream_t s, wg_stats* stats, bool timed) {
+  WsHead h;
+  CU(cudaMemcpyAsync(&h, w.head, sizeof(WsHead), cudaMemcpyDeviceToHost, s));
+  CU(cudaStreamSynchronize(s));
+  if (h.error) return fail(WG_ETIMEOUT, "a bounded device wait ran out (error word %u)", h.error);
+  if (stats) {
+    stats->n_rays = (int64_t)h.counters[0];
+    stats->n_hits = (int64_t)h.counters[1];
+    stats->n_events = (int64_t)h.counters[2];
+    stats->n_tir = (int64_t)h.counters[3];
+    stats->n_layer_steps = (int64_t)h.counters[4];
+    stats->overflow = (int32_t)h.counters[5];
+    stats->n_tallied = (int64_t)h.counters[6];
+    stats->n_adjoint_steps = (int64_t)h.counters[7];
+    stats->n_nonfinite = (int64_t)h.counters[8];
+    for (int i = 0; i < 6; ++i) stats->ledger[i] = h.ledger[i];
+    stats->kernel_ms = 0.f;
+    if (timed) cudaEventElapsedTime(&stats->kernel_ms, c->t0, c->t1);
+  }
+  return WG_OK;
+}
+
+static long long default_chunk(const Plan& p) { return std::min<long long>(p.n_cell, 2048); }
+
+extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, double* tally,
+                                      wg_stats* stats) {
+  if (!c || !d || !tally) return fail(WG_EINVAL, "wg_trace_forward: NULL ctx/design/tally");
+  Plan p;
+  wg_status st = make_plan(d, cfg, 2048, p);
+  if (st != WG_OK) return st;
+  p.chunk_rays = default_chunk(p);
+  p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
+  p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
+  const size_t smem = (size_t)d->blob_bytes + sizeof(float) * p.bins;
+  if (smem > 200 * 1024) return fail(WG_EINVAL, "wg_trace_forward: design + eyebox too large for shared memory");
+  cudaStream_t s = (cudaStream_t)cfg->stream;
+  std::lock_guard<std::mutex> lk(c->mu);
+  CU(cudaSetDevice(c->device));
+  WsLayout w;
+  st = prepare_ws(c, d, cfg, p, s, w);
+  if (st != WG_OK) return st;
+  const bool dev_tally = is_device_ptr(tally);
+  double* t = tally;
+  if (!dev_tally) CU(cudaMallocAsync((void**)&t, sizeof(double) * p.tally_size, s));
+  CU(cudaMemsetAsync(t + p.cell_lo * p.bins, 0, sizeof(double) * (p.cell_hi - p.cell_lo + 1) * p.bins, s));
+  TraceArgs a = base_args(d, cfg, p, w);
+  a.tally = t;
+  const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, smem));
+  const int grid = (int)std::min<long long>(p.n_chunks, (long long)c->sm_count * bps);
+  if (stats) CU(cudaEventRecord(c->t0, s));
+  CU(launch_trace_fwd(a, p.F, grid, smem, s));
+  if (stats) CU(cudaEventRecord(c->t1, s));
+  CU(cudaEventRecord(c->ws_free, s));
+  if (!dev_tally) {
+    CU(cudaMemcpyAsync(tally, t, sizeof(double) * p.tally_size, cudaMemcpyDeviceToHost, s));
+    CU(cudaFreeAsync(t, s));
+    CU(cudaStreamSynchronize(s));
+  }
+  if (stats || !dev_tally) return finish_stats(c, w, s, stats, stats != nullptr);
+  return WG_OK;
+}
+
+extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, const double* dL_dtally,
+                                       double* grad_thickness, double* grad_tilt, wg_stats* stats) {
+  if (!c || !d || !dL_dtally || !grad_thickness) return fail(WG_EINVAL, "wg_trace_backward: NULL argument");
+  if (grad_tilt) return fail(WG_EINVAL, "wg_trace_backward: grad_tilt is reserved and must be NULL");
+  Plan p;
+  wg_status st = make_plan(d, cfg, 1024, p);
+  if (st != WG_OK) return st;
+  p.chunk_rays = std::min<long long>(p.n_cell, 1024);
+  p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
+  p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
+  const size_t smem = (size_t)d->blob_bytes + sizeof(float) * std::max(1, d->n_dev);
+  if (smem > 200 * 1024) return fail(WG_EINVAL, "wg_trace_backward: design too large for shared memory");
+  cudaStream_t s = (cudaStream_t)cfg->stream;
+  std::lock_guard<std::mutex> lk(c->mu);
+  CU(cudaSetDevice(c->device));
+  WsLayout w;
+  st = prepare_ws(c, d, cfg, p, s, w);
+  if (st != WG_OK) return st;
+  const int bps = std::max(1, trace_bwd_blocks_per_sm(p.F, smem));
+  const int grid = (int)std::min<long long>(p.n_chunks, (long long)c->sm_count * bps);
+  const int hit_cap = kBlock * TAPE_HITS + 8192;
+  const size_t hit_bytes = (size_t)grid * hit_cap * hit_rec_bytes();
+  const size_t row_bytes = (size_t)grid * std::max(1, d->n_dev) * sizeof(double);
+  if (hit_bytes + row_bytes > c->bwd.n) {
+    CU(cudaEventSynchronize(c->ws_free));
+    CU(c->bwd.ensure(hit_bytes + row_bytes));
+  }
+  uint8_t* bw = (uint8_t*)c->bwd.p;
+  const bool dev_G = is_device_ptr(dL_dtally);
+  const bool dev_g = is_device_ptr(grad_thickness);
+  const double* G = dL_dtally;
+  double* gout = grad_thickness;
+  if (!dev_G) {
+    double* tmp;
+    CU(cudaMallocAsync((void**)&tmp, sizeof(double) * p.tally_size, s));
+    CU(cudaMemcpyAsync(tmp, dL_dtally, sizeof(double) * p.tally_size, cudaMemcpyHostToDevice, s));
+    G = tmp;
+  }
+  if (!dev_g) CU(cudaMallocAsync((void**)&gout, sizeof(double) * std::max(1, d->n_orig), s));
+  CU(cudaMemsetAsync(gout, 0, sizeof(double) * std::max(1, d->n_orig), s));
+  CU(cudaMemsetAsync(bw + hit_bytes, 0, row_bytes, s));
+  TraceArgs a = base_args(d, cfg, p, w);
+  a.G = G;
+  a.hit_buf = (HitRec*)bw;
+  a.hit_cap = hit_cap;
+  a.grad_cta = (double*)(bw + hit_bytes);
+  if (stats) CU(cudaEventRecord(c->t0, s));
+  CU(launch_trace_bwd(a, p.F, grid, smem, s));
+  if (stats) CU(cudaEventRecord(c->t1, s));
+  CU(launch_reduce_grad(a.grad_cta, grid, d->n_dev, d->d_dev_to_orig, gout, s));
+  CU(cudaEventRecord(c->ws_free, s));
+  if (!dev_G) CU(cudaFreeAsync((void*)G, s));
+  if (!dev_g) {
+    CU(cudaMemcpyAsync(grad_thickness, gout, sizeof(double) * d->n_orig, cudaMemcpyDeviceToHost, s));
+    CU(cudaFreeAsync(gout, s));
+    CU(cudaStreamSynchronize(s));
+  }
+  if (stats || !dev_g) return finish_stats(c, w, s, stats, stats != nullptr);
+  return WG_OK;
+}
+
+extern "C" wg_status wg_loss(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, int32_t kind, double w_f,
+                             double w_e, const double* tally, double* out, double* dL_dtally) {
+  if (!c || !d || !tally || !out) return fail(WG_EINVAL, "wg_loss: NULL argument");
+  if (kind != 0 && kind != 1) return fail(WG_EINVAL, "wg_loss: kind must be 0 (CV) or 1 (variance)");
+  Plan p;
+  wg_status st = make_plan(d, cfg, 2048, p);
+  if (st != WG_OK) return st;
+  if (!is_device_ptr(tally) || (dL_dtally && !is_device_ptr(dL_dtally)))
+    return fail(WG_EINVAL, "wg_loss: tally and dL_dtally must be device memory");
+  cudaStream_t s = (cudaStream_t)cfg->stream;
+  std::lock_guard<std::mutex> lk(c->mu);
+  CU(cudaSetDevice(c->device));
+  const size_t need = sizeof(double) * (2 * p.n_cells * 9 + 8);
+  CU(cudaStreamWaitEvent(s, c->ws_free, 0));
+  if (need > c->loss.n) {
+    CU(cudaEventSynchronize(c->ws_free));
+    CU(c->loss.ensure(need));
+  }
+  double* ws = (double*)c->loss.p;
+  double* odev = ws + 2 * p.n_cells * 9;
+  CU(launch_loss_impl(tally, d->dims, cfg->n_lambda, p.n_f, cfg->eb_nx, cfg->eb_ny, cfg->eb_cx_mm, cfg->eb_cy_mm,
+                      cfg->eb_w_mm, cfg->eb_h_mm, 1.0 / (double)p.n_cell, kind, w_f, w_e, ws, odev, dL_dtally, s));
+  CU(cudaMemcpyAsync(out, odev, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
+  CU(cudaEventRecord(c->ws_free, s));
+  CU(cudaStreamSynchronize(s));
+  return WG_OK;
+}

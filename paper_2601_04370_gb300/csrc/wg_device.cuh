@@ -1,0 +1,537 @@
+// Device-side building blocks of the waveguide trace (sm_103a, FP32).
+//
+// Paper: "End-to-end differentiable design of geometric waveguide displays"
+// (arXiv 2601.04370), Methods: Fresnel coefficients (Eq. 2), Airy / transfer
+// matrices (Eq. 3 and Heavens' method), polarization ray tracing (Eq. 4),
+// Monte Carlo reflect/transmit sampling with amplitude rescaling (Eq. 5).
+//
+// GB300 design choices (not the paper's):
+//  * every layer's characteristic matrix is real-structured ([[c, i m12],
+//    [i m21, c]] with real entries, also for evanescent layers); the stack
+//    is applied to the substrate-side vector [1, eta]^T from the substrate
+//    outwards (8 FMA-pipe ops per layer and polarization), which keeps FP32
+//    accurate behind evanescent barriers where a left-to-right matrix
+//    product loses the subdominant part;
+//  * each layer's phase is reduced exactly to [-1/2, 1/2) turn before the
+//    fast sin/cos;
+//  * the field is kept as two complex coefficients in the slab-face s/p basis
+//    of the current direction (s = d x z / |d x z|): a TIR bounce is then a
+//    diagonal multiply; mirror hits rotate into the mirror's s/p basis and
+//    back (same physics as Eq. 4's 3-vector form);
+//  * the product is rescaled by exact powers of two every 8 layers (evanescent
+//    layers grow like cosh), with the exponent tracked separately;
+//  * the adjoint never inverts a layer matrix: it recomputes substrate-side
+//    vectors from checkpoints taken every 8 layers.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wgk {
+
+constexpr int MAX_MAT = 4;
+constexpr int MAX_MIR = 64;
+constexpr int MAX_EVENTS = 128;
+constexpr int TAPE_HITS = 64;
+constexpr int CK = 8;                 // checkpoint stride (layers)
+constexpr int MAX_LAYERS_MIRROR = 512;
+constexpr int MAX_CK = MAX_LAYERS_MIRROR / CK + 1;
+constexpr float TWO_PI = 6.283185307179586f;
+
+enum { S_BOT = 0, S_TOP = 1, S_LEFT = 2, S_RIGHT = 3, S_YNEG = 4, S_YPOS = 5, S_MIR = 8 };
+enum { L_EYEBOX = 0, L_MISSED = 1, L_EXIT_REFL = 2, L_LEAKED = 3, L_ABSORBED = 4, L_TRUNCATED = 5 };
+
+// Philox counter tags ("GEN0", "EVT0")
+constexpr uint32_t TAG_GEN = 0x47454E30u;
+constexpr uint32_t TAG_EVT = 0x45565430u;
+
+// ---------------------------------------------------------------------------
+// Design blob: header | mirrors | layer thickness (FP32) | layer material (u8)
+// Staged into shared memory per CTA with a bulk (TMA) copy.
+// ---------------------------------------------------------------------------
+struct alignas(16) BlobHeader {
+  int dims, n_mat, n_mir, n_layers;      // n_layers: device (non-pruned) layers
+  float n_slab, thick, half_w, x_end;
+  float eye_relief, ic_nx, ic_nz, ic_cot; // input mirror normal (-sin a, cos a), cot a
+  float mat_n[MAX_MAT];
+  int off_mir, off_d, off_m, bytes;       // byte offsets, total size (multiple of 16)
+};
+static_assert(sizeof(BlobHeader) == 80, "header layout");
+
+struct alignas(16) MirrorRec {
+  float nx, nz, c, omega;  // plane: nx x + nz z = c; reflection probability
+  float isw, is1w;         // 1/sqrt(omega), 1/sqrt(1-omega)
+  int layer_off, n_layers; // device layers of this mirror, traversal order = layer 1 first
+};
+static_assert(sizeof(MirrorRec) == 32, "mirror layout");
+
+struct Blob {
+  const BlobHeader* h;
+  const MirrorRec* mir;
+  const float* d;
+  const uint8_t* m;
+  __device__ __forceinline__ void bind(const uint8_t* base) {
+    h = reinterpret_cast<const BlobHeader*>(base);
+    mir = reinterpret_cast<const MirrorRec*>(base + h->off_mir);
+    d = reinterpret_cast<const float*>(base + h->off_d);
+    m = base + h->off_m;
+  }
+};
+
+// per-field launch constants: guided direction after the input mirror and
+// the transverse basis e1 (y projected off d), e2 = d x e1
+struct alignas(16) FieldRec {
+  float dx, dy, dz, pad0;
+  float e1x, e1y, e1z, pad1;
+  float e2x, e2y, e2z, pad2;
+};
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+// 24-bit uniform in [0, 1), exact in FP32
+__device__ __forceinline__ float u24(uint32_t x) { return (float)(x >> 8) * 5.9604644775390625e-08f; }
+
+// ---------------------------------------------------------------------------
+// small complex helpers (float2 = re, im)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // conj(a) * b
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cdiv(float2 a, float2 b) {
+  const float inv = 1.0f / fmaf(b.x, b.x, b.y * b.y);
+  return make_float2(fmaf(a.x, b.x, a.y * b.y) * inv, fmaf(a.y, b.x, -a.x * b.y) * inv);
+}
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+// a / b for |b| anywhere in the FP32 range: both are scaled by 1/max|b_i|
+// first, so |b|^2 cannot overflow (the transfer-matrix vectors reach ~2^70)
+__device__ __forceinline__ float2 cdiv_s(float2 a, float2 b) {
+  const float k = 1.0f / fmaxf(fabsf(b.x), fabsf(b.y));
+  return cdiv(cscale(a, k), cscale(b, k));
+}
+
+// ---------------------------------------------------------------------------
+// Per-hit material constants for the characteristic matrices.
+// Propagating layer (real cos t): x = kappa d, c = cos x, s = sin x,
+//   s-pol m12 = s / eta, m21 = s eta (eta = n cos t); p-pol eta = n / cos t.
+// Evanescent layer (cos t = -i a): x = beta d, c = cosh x, s = sinh x,
+//   s-pol m12 = s/(n a), m21 = -s n a; p-pol m12 = -s a/n, m21 = s n / a.
+// In both cases M = [[c, i m12], [i m21, c]].
+// ---------------------------------------------------------------------------
+// kap: d(phase)/d(thickness) in rad/nm (2 pi n cos / lambda, or beta = 2 pi n a / lambda);
+// kt: the rate the layer loop multiplies by: turns/nm for a propagating layer
+// (the phase is reduced exactly to [-1/2, 1/2) turn before the fast sin/cos),
+// beta for an evanescent one.
+struct MatK {
+  float kap, kt, q12s, q21s, q12p, q21p;
+  int evan;
+};
+
+__device__ __forceinline__ MatK mat_const(float n0, float sin2_0, float n, float inv_lam) {
+  MatK k;
+  const float r = n0 / n;
+  const float rad = fmaf(-(r * r), sin2_0, 1.0f);
+  if (rad >= 0.0f) {
+    const float ct = sqrtf(rad);
+    const float eta = n * ct;
+    k.kt = eta * inv_lam;
+    k.kap = TWO_PI * k.kt;
+    k.q12s = 1.0f / eta;
+    k.q21s = eta;
+    k.q12p = ct / n;
+    k.q21p = n / ct;
+    k.evan = 0;
+  } else {
+    const float a = sqrtf(-rad);
+    const float na = n * a;
+    k.kap = TWO_PI * na * inv_lam;
+    k.kt = k.kap;
+    k.q12s = 1.0f / na;
+    k.q21s = -na;
+    k.q12p = -a / n;
+    k.q21p = n / a;
+    k.evan = 1;
+  }
+  return k;
+}
+
+struct MatTable {
+  MatK k[MAX_MAT];
+  __device__ __forceinline__ void init(const BlobHeader& h, float cos0, float lam) {
+    const float sin2 = fmaf(-cos0, cos0, 1.0f);
+    const float inv_lam = 1.0f / lam;
+#pragma unroll
+    for (int i = 0; i < MAX_MAT; ++i)
+      if (i < h.n_mat) k[i] = mat_const(h.n_slab, sin2, h.mat_n[i], inv_lam);
+  }
+  // register select by material id (no local-memory indexing)
+  __device__ __forceinline__ MatK get(int m) const {
+    MatK r = k[0];
+    if (m == 1) r = k[1];
+    if (m == 2) r = k[2];
+    if (m == 3) r = k[3];
+    return r;
+  }
+};
+
+// c, s of one layer; sigma = d(c)/dx sign (-1 propagating, +1 evanescent)
+__device__ __forceinline__ void layer_cs(const MatK& k, float d, float& c, float& s) {
+  const float x = k.kt * d;
+  if (!k.evan) {
+    const float f = x - rintf(x);  // exact reduction in turns
+    __sincosf(f * TWO_PI, &s, &c);
+  } else {
+    const float e = __expf(x);
+    const float ei = __frcp_rn(e);
+    c = 0.5f * (e + ei);
+    s = 0.5f * (e - ei);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Stack evaluation in vector form. v = [B, C]^T = M_1 ... M_L [1, eta_sub]^T
+// is built from the substrate side, v <- M_j v: the substrate-side solution
+// grows towards the incident side, so each step keeps its FP32 relative
+// error at ~1 ulp (the left-to-right matrix product loses the
+// subdominant part behind evanescent barriers). v = (x, y) complex,
+// M_j = [[c, i m12], [i m21, c]] real-structured:
+//   x' = c x + i m12 y,  y' = i m21 x + c y            (8 FMA-pipe ops)
+// ---------------------------------------------------------------------------
+struct CV {
+  float xr, xi, yr, yi;
+};
+__device__ __forceinline__ void cv_step(CV& v, float c, float m12, float m21) {
+  const float xr = fmaf(c, v.xr, -m12 * v.yi);
+  const float xi = fmaf(c, v.xi, m12 * v.yr);
+  const float yr = fmaf(c, v.yr, -m21 * v.xi);
+  const float yi = fmaf(c, v.yi, m21 * v.xr);
+  v.xr = xr;
+  v.xi = xi;
+  v.yr = yr;
+  v.yi = yi;
+}
+__device__ __forceinline__ float cv_maxabs(const CV& v) {
+  return fmaxf(fmaxf(fabsf(v.xr), fabsf(v.xi)), fmaxf(fabsf(v.yr), fabsf(v.yi)));
+}
+constexpr float TWO_P64 = 1.8446744073709552e19f;   // 2^64
+constexpr float TWO_M64 = 5.421010862427522e-20f;   // 2^-64
+// keep entries below 2^64 by exact power-of-two scaling; e counts the scale
+__device__ __forceinline__ void cv_rescale(CV& v, int& e) {
+  if (cv_maxabs(v) > TWO_P64) {
+    v.xr *= TWO_M64;
+    v.xi *= TWO_M64;
+    v.yr *= TWO_M64;
+    v.yi *= TWO_M64;
+    e += 64;
+  }
+}
+__device__ __forceinline__ float pow2i(int e) {  // 2^e as float, 0 below the range
+  if (e < -149) return 0.0f;
+  if (e > 127) return __int_as_float(0x7f800000);
+  return ldexpf(1.0f, e);
+}
+// x * 2^e without forming 2^e when it is out of range (0 * 2^e = 0)
+__device__ __forceinline__ float scale2(float x, int e) {
+  if (e >= -126 && e <= 127) return x * __int_as_float((e + 127) << 23);
+  return ldexpf(x, e);
+}
+
+struct Coef {
+  float2 rs, rp, ts, tp;
+};
+
+// Stack view of one mirror in shared memory.
+struct StackView {
+  const float* d;
+  const uint8_t* m;
+  int off, L;
+  __device__ __forceinline__ int idx(bool front, int j) const { return front ? off + j : off + L - 1 - j; }
+};
+
+// r = (eta0 B - C)/(eta0 B + C), t = 2 eta0/(eta0 B + C) (Macleod); the
+// scale 2^e of v cancels in r and multiplies t by 2^-e.
+__device__ __forceinline__ void coef_from_v(const CV& v, float eta0, int e, float2& r, float2& t) {
+  const float2 den = make_float2(fmaf(eta0, v.xr, v.yr), fmaf(eta0, v.xi, v.yi));
+  const float2 num = make_float2(fmaf(eta0, v.xr, -v.yr), fmaf(eta0, v.xi, -v.yi));
+  r = cdiv_s(num, den);
+  t = cscale(cdiv_s(make_float2(2.0f * eta0, 0.0f), den), pow2i(-e));
+}
+
+// Effective coefficients in the paper's convention (r_p = -r_p(Abeles)).
+__device__ __forceinline__ Coef tmm_forward(const StackView& st, bool front, const MatTable& mt, float n0,
+                                            float cos0, int& layer_steps) {
+  const float eta_s = n0 * cos0, eta_p = n0 / cos0;
+  CV vs{1.0f, 0.0f, eta_s, 0.0f}, vp{1.0f, 0.0f, eta_p, 0.0f};
+  int es = 0, ep = 0;
+  for (int j = st.L - 1; j >= 0; --j) {
+    const int i = st.idx(front, j);
+    const MatK k = mt.get(st.m[i]);
+    float c, s;
+    layer_cs(k, st.d[i], c, s);
+    cv_step(vs, c, s * k.q12s, s * k.q21s);
+    cv_step(vp, c, s * k.q12p, s * k.q21p);
+    if ((j & (CK - 1)) == 0) {
+      cv_rescale(vs, es);
+      cv_rescale(vp, ep);
+    }
+  }
+  layer_steps += st.L;
+  Coef out;
+  coef_from_v(vs, eta_s, es, out.rs, out.ts);
+  float2 rpm;
+  coef_from_v(vp, eta_p, ep, rpm, out.tp);
+  out.rp = make_float2(-rpm.x, -rpm.y);
+  return out;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint of f = 2 Re(A_s c_s + A_p c_p) (c = r or t) with respect to every
+// layer thickness. With v_j = M_j ... M_{L-1} u and the row
+// a_j = rho M_0 ... M_{j-1}, rho = A (dc/dB, dc/dC):
+//   df/dx_j = 2 Re(a_j G_j v_j) = -2 (q12 Im(a_j0 y_j) + q21 Im(a_j1 x_j)),
+//   G_j = [[0, i q12], [i q21, 0]] (dM_j/dx = M_j G_j), df/dd_j = kappa_j df/dx_j.
+// Sweep 1 runs v from the substrate side and keeps a checkpoint every CK
+// layers; sweep 2 runs a from the incident side, recomputing each segment's
+// v_j from the checkpoint at its far end. No layer matrix is inverted.
+// sink(layer index, df/dd) receives the gradient (per nm).
+// ---------------------------------------------------------------------------
+struct Ckpt {
+  CV s, p;
+  int es, ep;
+};
+
+struct CRow {
+  float2 a0, a1;
+};
+__device__ __forceinline__ void row_step(CRow& a, float c, float m12, float m21) {
+  const float2 a0 = make_float2(fmaf(c, a.a0.x, -m21 * a.a1.y), fmaf(c, a.a0.y, m21 * a.a1.x));
+  const float2 a1 = make_float2(fmaf(c, a.a1.x, -m12 * a.a0.y), fmaf(c, a.a1.y, m12 * a.a0.x));
+  a.a0 = a0;
+  a.a1 = a1;
+}
+// The adjoint keeps both factors of its products a_j . v_j within 2^32 (a:
+// checked every layer; v: checkpoints <= 2^32, and a segment of CK layers
+// grows v by < 2^31), so a . v stays far below the FP32 range whatever the
+// scale factor 2^(e_a + e_v) applied afterwards.
+constexpr float TWO_P32 = 4294967296.0f;
+constexpr float TWO_M32 = 2.3283064365386963e-10f;
+__device__ __forceinline__ float row_maxabs(const CRow& a) {
+  return fmaxf(fmaxf(fabsf(a.a0.x), fabsf(a.a0.y)), fmaxf(fabsf(a.a1.x), fabsf(a.a1.y)));
+}
+__device__ __forceinline__ void row_guard(CRow& a, int& e) {
+  if (row_maxabs(a) > TWO_P32) {
+    a.a0 = cscale(a.a0, TWO_M32);
+    a.a1 = cscale(a.a1, TWO_M32);
+    e += 32;
+  }
+}
+__device__ __forceinline__ void row_renorm(CRow& a, int& e) {
+  const float m = row_maxabs(a);
+  if (m > TWO_P32) {
+    a.a0 = cscale(a.a0, TWO_M32);
+    a.a1 = cscale(a.a1, TWO_M32);
+    e += 32;
+  } else if (m < TWO_M32 && m > 0.0f) {
+    a.a0 = cscale(a.a0, TWO_P32);
+    a.a1 = cscale(a.a1, TWO_P32);
+    e -= 32;
+  }
+}
+__device__ __forceinline__ void cv_rescale32(CV& v, int& e) {
+  if (cv_maxabs(v) > TWO_P32) {
+    v.xr *= TWO_M32;
+    v.xi *= TWO_M32;
+    v.yr *= TWO_M32;
+    v.yi *= TWO_M32;
+    e += 32;
+  }
+}
+
+// rho for one polarization (scaled v, exponent e): returns the row and its exponent
+__device__ __forceinline__ CRow coef_row(const CV& v, float eta0, int e, float2 A, int which, int& ea) {
+  const float2 B = make_float2(v.xr, v.xi), C = make_float2(v.yr, v.yi);
+  const float2 den = make_float2(fmaf(eta0, B.x, C.x), fmaf(eta0, B.y, C.y));
+  CRow a;
+  if (which == 0) {
+    // dr/dB = 2 eta0 C / den^2, dr/dC = -2 eta0 B / den^2
+    const float2 dB = cscale(cdiv_s(cdiv_s(C, den), den), 2.0f * eta0);
+    const float2 dC = cscale(cdiv_s(cdiv_s(B, den), den), -2.0f * eta0);
+    a.a0 = cmul(A, dB);
+    a.a1 = cmul(A, dC);
+    ea = -e;
+  } else {
+    // t = 2 eta0 / den: dt/dB = -eta0 t / den, dt/dC = -t / den
+    const float2 t = cdiv_s(make_float2(2.0f * eta0, 0.0f), den);
+    const float2 td = cdiv_s(t, den);
+    a.a0 = cmul(A, cscale(td, -eta0));
+    a.a1 = cmul(A, cscale(td, -1.0f));
+    ea = -2 * e;
+  }
+  return a;
+}
+
+template <class Sink>
+__device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, const MatTable& mt, float n0,
+                                            float cos0, float2 A_s, float2 A_p, int which, Sink& sink,
+                                            int eA = 0) {
+  // (A_s, A_p) * 2^eA are the weights; eA carries the range of dL/dtally
+  Ckpt ck[MAX_CK];
+  const int L = st.L;
+  const int nseg = (L + CK - 1) / CK;
+  const float eta_s = n0 * cos0, eta_p = n0 / cos0;
+  CV vs{1.0f, 0.0f, eta_s, 0.0f}, vp{1.0f, 0.0f, eta_p, 0.0f};
+  int es = 0, ep = 0;
+  ck[nseg] = Ckpt{vs, vp, 0, 0};
+  for (int j = L - 1; j >= 0; --j) {
+    const int i = st.idx(front, j);
+    const MatK k = mt.get(st.m[i]);
+    float c, s;
+    layer_cs(k, st.d[i], c, s);
+    cv_step(vs, c, s * k.q12s, s * k.q21s);
+    cv_step(vp, c, s * k.q12p, s * k.q21p);
+    cv_rescale32(vs, es);
+    cv_rescale32(vp, ep);
+    if ((j & (CK - 1)) == 0) ck[j / CK] = Ckpt{vs, vp, es, ep};
+  }
+  // paper convention r_p = -r_p(Abeles): flip A_p for reflection
+  const float2 Ap = which == 0 ? make_float2(-A_p.x, -A_p.y) : A_p;
+  int eas, eap;
+  CRow as = coef_row(vs, eta_s, es, A_s, which, eas);
+  CRow ap = coef_row(vp, eta_p, ep, Ap, which, eap);
+  eas += eA;
+  eap += eA;
+  for (int sg = 0; sg < nseg; ++sg) {
+    const int j0 = sg * CK;
+    const Ckpt c1 = ck[sg + 1];
+    CV bs[CK], bp[CK];
+    float bc[CK], bsn[CK];
+    int bm[CK];
+    CV ws = c1.s, wp = c1.p;
+#pragma unroll
+    for (int u = CK - 1; u >= 0; --u) {
+      const int j = j0 + u;
+      if (j < L) {
+        const int i = st.idx(front, j);
+        const int mm = st.m[i];
+        const MatK k = mt.get(mm);
+        float c, s;
+        layer_cs(k, st.d[i], c, s);
+        cv_step(ws, c, s * k.q12s, s * k.q21s);
+        cv_step(wp, c, s * k.q12p, s * k.q21p);
+        bs[u] = ws;
+        bp[u] = wp;
+        bc[u] = c;
+        bsn[u] = s;
+        bm[u] = mm;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < CK; ++u) {
+      const int j = j0 + u;
+      if (j < L) {
+        const MatK k = mt.get(bm[u]);
+        const CV& x = bs[u];
+        const CV& y = bp[u];
+        const float gs = fmaf(k.q12s, fmaf(as.a0.x, x.yi, as.a0.y * x.yr), k.q21s * fmaf(as.a1.x, x.xi, as.a1.y * x.xr));
+        const float gp = fmaf(k.q12p, fmaf(ap.a0.x, y.yi, ap.a0.y * y.yr), k.q21p * fmaf(ap.a1.x, y.xi, ap.a1.y * y.xr));
+        sink(st.idx(front, j), -2.0f * k.kap * (scale2(gs, eas + c1.es) + scale2(gp, eap + c1.ep)));
+        const float c = bc[u], s = bsn[u];
+        row_step(as, c, s * k.q12s, s * k.q21s);
+        row_step(ap, c, s * k.q12p, s * k.q21p);
+        row_guard(as, eas);
+        row_guard(ap, eap);
+      }
+    }
+    row_renorm(as, eas);
+    row_renorm(ap, eap);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Geometry
+// ---------------------------------------------------------------------------
+struct V3 {
+  float x, y, z;
+};
+__device__ __forceinline__ V3 v3(float x, float y, float z) { return V3{x, y, z}; }
+__device__ __forceinline__ float dot3(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ __forceinline__ V3 cross3(V3 a, V3 b) {
+  return V3{fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x)};
+}
+
+// s/p basis of the slab faces for direction d: s = (d_y, -d_x, 0)/|.|, p = s x d
+__device__ __forceinline__ void face_basis(V3 d, V3& s, V3& p) {
+  const float h2 = fmaf(d.x, d.x, d.y * d.y);
+  if (h2 > 1e-30f) {
+    const float r = rsqrtf(h2);
+    s = V3{d.y * r, -d.x * r, 0.0f};
+  } else {
+    s = V3{0.0f, 1.0f, 0.0f};
+  }
+  p = cross3(s, d);
+}
+
+// Nearest surface along (p, d), excluding `last`. Candidate order and ties
+// match the oracle: faces, input mirror, far end, sides, mirrors.
+__device__ __forceinline__ int next_surface(const Blob& B, V3 p, V3 d, int last, float& tmin) {
+  const BlobHeader& h = *B.h;
+  float best = __int_as_float(0x7f800000);
+  int id = -1;
+  auto consider = [&](int sid, float t) {
+    if (sid != last && t > 0.0f && t < best) {
+      best = t;
+      id = sid;
+    }
+  };
+  if (d.z < 0.0f) consider(S_BOT, -p.z / d.z);
+  if (d.z > 0.0f) consider(S_TOP, (h.thick - p.z) / d.z);
+  const float dn = fmaf(d.x, h.ic_nx, d.z * h.ic_nz);
+  if (dn > 0.0f) consider(S_LEFT, -fmaf(p.x, h.ic_nx, p.z * h.ic_nz) / dn);
+  if (d.x > 0.0f) consider(S_RIGHT, (h.x_end - p.x) / d.x);
+  if (h.dims == 3) {
+    if (d.y > 0.0f) consider(S_YPOS, (h.half_w - p.y) / d.y);
+    if (d.y < 0.0f) consider(S_YNEG, (-h.half_w - p.y) / d.y);
+  }
+  for (int k = 0; k < h.n_mir; ++k) {
+    const MirrorRec& m = B.mir[k];
+    const float den = fmaf(d.x, m.nx, d.z * m.nz);
+    if (den == 0.0f) continue;
+    consider(S_MIR + k, (m.c - fmaf(p.x, m.nx, p.z * m.nz)) / den);
+  }
+  tmin = best;
+  return id;
+}
+
+// TIR at a slab face against air: r_s, r_p with u = n cos_i, a = sqrt(n^2 sin^2 - 1)
+//   r_s = (u + i a)/(u - i a), r_p = (c + i n a)/(c - i n a)   (cos_t = -i a)
+__device__ __forceinline__ void tir_coef(float n, float ci, float sin2, float2& rs, float2& rp) {
+  const float a = sqrtf(fmaxf(fmaf(n * n, sin2, -1.0f), 0.0f));
+  const float u = n * ci;
+  const float iu = 1.0f / fmaf(u, u, a * a);
+  rs = make_float2(fmaf(u, u, -a * a) * iu, 2.0f * u * a * iu);
+  const float na = n * a;
+  const float ip = 1.0f / fmaf(ci, ci, na * na);
+  rp = make_float2(fmaf(ci, ci, -na * na) * ip, 2.0f * ci * na * ip);
+}
+
+__device__ __forceinline__ uint32_t fnv(uint32_t h, uint32_t b) { return (h ^ b) * 16777619u; }
+
+}  // namespace wgk

@@ -1,0 +1,75 @@
+// Host-side declarations shared by the CUDA translation units of libwg.so.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wgk {
+
+struct FieldRec;
+struct HitRec;
+
+// Arguments of the trace kernels (passed by value).
+struct TraceArgs {
+  const uint8_t* blob;        // design blob (global), staged into smem
+  int blob_bytes;             // multiple of 16
+  const FieldRec* fields;     // [n_f]
+  const float* lambda;        // [n_lam]
+  int n_f, pol, max_events, bins;  // bins per cell = eb_nx * eb_ny
+  long long n_cell;           // rays per cell
+  long long ray_begin, ray_end;
+  long long cell_lo;          // first cell touched by [ray_begin, ray_end)
+  long long chunk_rays;       // rays per chunk
+  long long chunks_per_cell;
+  long long n_chunks;
+  uint32_t key0, key1;
+  int eb_nx, eb_ny;
+  float eb_x0, eb_y0, eb_sx, eb_sy;  // bin = floor((q - x0) * s)
+  float pupil_y;
+  // outputs
+  double* tally;              // forward: FP64 tally (full layout)
+  const double* G;            // backward: dL/dtally
+  double* ledger;             // [6]
+  unsigned long long* counters;  // [10]: rays, hits, events, tir, layer steps, overflow, tallied,
+                                 // adjoint layer steps, non-finite gradient terms, reserved
+  void* records;              // wg_ray_record* or null
+  unsigned long long* work;   // chunk queue counter (zeroed before launch)
+  unsigned int* error;        // device error word (bounded waits)
+  // backward scratch
+  HitRec* hit_buf;            // [grid][hit_cap]
+  int hit_cap;
+  float* grad_part;           // unused (reserved)
+  double* grad_cta;           // [grid][n_layers] FP64 per-CTA accumulators
+  int n_layers;               // device layers
+};
+
+constexpr int kBlock = 256;
+
+// number of kernels this library has launched (all launchers add to it)
+void note_launches(unsigned long long n);
+unsigned long long launches();
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_prep_design(uint8_t* blob, const float* mir_x, const float* mir_tilt, const float* mir_omega,
+                               int n_mir, float ic_tilt_deg, float thick, cudaStream_t s);
+cudaError_t launch_prep_fields(FieldRec* out, const float* fx, const float* fy, int n_fx, int n_fy,
+                               float n_slab, float ic_tilt_deg, int dims, cudaStream_t s);
+cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_trace_bwd(const TraceArgs& a, int F, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_reduce_grad(const double* grad_cta, int grid, int n_layers, const int* dev_to_orig,
+                               double* grad_out, cudaStream_t s);
+cudaError_t launch_coating_eval(const uint8_t* blob, int mirror, int side, long long n, const float* cos0,
+                                const float* lam, float* out, cudaStream_t s);
+cudaError_t launch_coating_grad(const uint8_t* blob, int mirror, int side, long long n, const float* cos0,
+                                const float* lam, const float* w, int which, float* grad, cudaStream_t s);
+cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const int* orig_to_dev, int n_orig,
+                                    cudaStream_t s);
+int trace_fwd_blocks_per_sm(int F, size_t smem);
+int trace_bwd_blocks_per_sm(int F, size_t smem);
+size_t hit_rec_bytes();
+
+// loss (workspace: 2 * cells * 9 doubles)
+cudaError_t launch_loss_impl(const double* tally, int dims, int n_lam, int n_f, int nx, int ny, double cx, double cy,
+                             double w, double h, double inv_ncell, int kind, double w_f, double w_e, double* ws,
+                             double* out_dev, double* dL, cudaStream_t s);
+
+}  // namespace wgk

@@ -1,0 +1,1049 @@
+// Kernels of the waveguide trace: design/field preparation, the persistent
+// forward Monte Carlo trace (K2), the fused adjoint (K3: replay + per-hit
+// transfer-matrix adjoint), coating test hooks (K1) and gradient reduction.
+//
+// Paper: "End-to-end differentiable design of geometric waveguide displays"
+// (arXiv 2601.04370), Methods: "Multilayer thin-film solver" (Eq. 2, Eq. 3,
+// transfer matrices), "Polarization ray tracing" (Eq. 4), "Differentiable
+// Monte Carlo non-sequential ray tracing" (Eq. 5, I = sum |E|^2); Fig. 3b/c
+// (two-pass intersection, gradient checkpoint between trace and thin film):
+// here the backward pass replays each ray from its Philox key and hands the
+// per-hit coefficient sensitivities to a checkpointed thin-film adjoint.
+#include <cuda_runtime.h>
+
+#include <atomic>
+
+#include "wg_device.cuh"
+#include "wg_internal.h"
+
+namespace wgk {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr float HALF_ULP24 = 2.98023223876953125e-08f;  // 2^-25
+
+struct alignas(16) HitRec {
+  int kfw;     // mirror | front << 8 | which << 9 (0 = r, 1 = t)
+  float cos0;
+  float lam;
+  int eA;      // weights are (As, Ap) * 2^eA (dL/dtally spans the FP64 range)
+  float2 As, Ap;
+};
+static_assert(sizeof(HitRec) == 32, "hit record");
+size_t hit_rec_bytes() { return sizeof(HitRec); }
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launches() { return g_launches.load(std::memory_order_relaxed); }
+
+// per-ray record (layout of wg_ray_record)
+struct RayRec {
+  uint32_t hash;
+  int n_events, n_hits, cat, bin;
+  float I, w;
+  int pad;
+};
+
+// ---------------------------------------------------------------------------
+// Bulk (TMA) staging of the design blob into shared memory, mbarrier
+// completion with a bounded wait. Returns false (uniformly across the CTA)
+// if the wait ran out; the caller then exits after flagging the error.
+// ---------------------------------------------------------------------------
+__device__ bool stage_blob(uint8_t* s_dst, const uint8_t* g_src, int bytes, uint64_t* mbar, unsigned* err) {
+  const uint32_t bar = (uint32_t)__cvta_generic_to_shared(mbar);
+  const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s_dst);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    for (int off = 0; off < bytes; off += 16384) {
+      const int n = min(16384, bytes - off);
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst + off),
+          "l"(g_src + off), "r"(n), "r"(bar)
+          : "memory");
+    }
+  }
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 22) && !done; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(0)
+        : "memory");
+  }
+  const int ok = __syncthreads_and(done != 0);
+  if (!ok && threadIdx.x == 0) atomicOr(err, 1u);
+  return ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Preparation (FP64, tiny): mirror planes from tilts, input-mirror normal,
+// per-field launch directions and transverse bases.
+// ---------------------------------------------------------------------------
+__global__ void k_prep_design(uint8_t* blob, const float* mir_x, const float* mir_tilt, const float* mir_omega,
+                              int n_mir, float ic_tilt_deg, float thick) {
+  BlobHeader* h = reinterpret_cast<BlobHeader*>(blob);
+  MirrorRec* mir = reinterpret_cast<MirrorRec*>(blob + h->off_mir);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const double deg = 3.14159265358979323846 / 180.0;
+  if (k < n_mir) {
+    const double a = (double)mir_tilt[k] * deg;
+    const double nx = -sin(a), nz = cos(a);
+    mir[k].nx = (float)nx;
+    mir[k].nz = (float)nz;
+    mir[k].c = (float)(nx * (double)mir_x[k] + nz * 0.5 * (double)thick);
+    const double w = (double)mir_omega[k];
+    mir[k].omega = mir_omega[k];
+    mir[k].isw = (float)(1.0 / sqrt(w));
+    mir[k].is1w = (float)(1.0 / sqrt(1.0 - w));
+  }
+  if (k == 0) {
+    const double a = (double)ic_tilt_deg * deg;
+    h->ic_nx = (float)(-sin(a));
+    h->ic_nz = (float)cos(a);
+    h->ic_cot = (float)(cos(a) / sin(a));
+  }
+}
+
+__global__ void k_prep_fields(FieldRec* out, const float* fx, const float* fy, int n_fx, int n_fy, float n_slab,
+                              float ic_tilt_deg, int dims) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n_fx * n_fy) return;
+  const double deg = 3.14159265358979323846 / 180.0;
+  const int ix = f % n_fx, iy = f / n_fx;
+  const double tx = tan((double)fx[ix] * deg);
+  const double ty = dims == 3 ? tan((double)fy[iy] * deg) : 0.0;
+  const double an = sqrt(tx * tx + ty * ty + 1.0);
+  const double ax = tx / an, ay = ty / an, n = (double)n_slab;
+  const double gx = ax / n, gy = ay / n, gz = sqrt(1.0 - (ax * ax + ay * ay) / (n * n));
+  const double a = (double)ic_tilt_deg * deg;
+  const double Nx = -sin(a), Nz = cos(a);
+  const double dn = gx * Nx + gz * Nz;
+  const double dx = gx - 2.0 * dn * Nx, dy = gy, dz = gz - 2.0 * dn * Nz;
+  // e1 = normalize(y - (y.d) d), e2 = d x e1
+  double e1x = -dy * dx, e1y = 1.0 - dy * dy, e1z = -dy * dz;
+  const double e1n = sqrt(e1x * e1x + e1y * e1y + e1z * e1z);
+  e1x /= e1n;
+  e1y /= e1n;
+  e1z /= e1n;
+  const double e2x = dy * e1z - dz * e1y, e2y = dz * e1x - dx * e1z, e2z = dx * e1y - dy * e1x;
+  FieldRec r;
+  r.dx = (float)dx;
+  r.dy = (float)dy;
+  r.dz = (float)dz;
+  r.e1x = (float)e1x;
+  r.e1y = (float)e1y;
+  r.e1z = (float)e1z;
+  r.e2x = (float)e2x;
+  r.e2y = (float)e2y;
+  r.e2z = (float)e2z;
+  r.pad0 = r.pad1 = r.pad2 = 0.0f;
+  out[f] = r;
+}
+
+__global__ void k_thickness_update(uint8_t* blob, const float* d_orig, const int* orig_to_dev, int n_orig) {
+  const BlobHeader* h = reinterpret_cast<const BlobHeader*>(blob);
+  float* d = reinterpret_cast<float*>(blob + h->off_d);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n_orig) {
+    const int j = orig_to_dev[i];
+    if (j >= 0) d[j] = d_orig[i];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Ray state and events shared by the forward and backward kernels.
+// ---------------------------------------------------------------------------
+template <int F>
+struct Ray {
+  V3 p, d;
+  float2 a[F], b[F];  // field in the face s/p basis of d
+  long long id;
+  int ev, hits, last;
+  uint32_t hash;
+  uint4 rnd;
+};
+
+struct ChunkConst {
+  V3 fd;                  // guided launch direction
+  float a1, b1, a2, b2;   // e1, e2 in the face basis of fd
+  float lam;
+  long long cell;
+};
+
+template <int F>
+__device__ __forceinline__ void gen_ray(Ray<F>& R, long long id, const ChunkConst& cc, const BlobHeader& H,
+                                        const TraceArgs& A) {
+  const uint4 r0 = philox10(make_uint4((uint32_t)id, (uint32_t)((unsigned long long)id >> 32), 0u, TAG_GEN),
+                            A.key0, A.key1);
+  const float z0 = H.thick * (u24(r0.x) + HALF_ULP24);
+  R.p = v3(z0 * H.ic_cot, H.dims == 3 ? (u24(r0.y) + HALF_ULP24 - 0.5f) * A.pupil_y : 0.0f, z0);
+  R.d = cc.fd;
+  if (F == 2) {
+    R.a[0] = make_float2(cc.a1, 0.f);
+    R.b[0] = make_float2(cc.b1, 0.f);
+    R.a[F - 1] = make_float2(cc.a2, 0.f);
+    R.b[F - 1] = make_float2(cc.b2, 0.f);
+  } else {
+    float c = 1.0f, s = 0.0f;
+    if (A.pol == 1) {
+      sincospif(u24(r0.z), &s, &c);
+    } else if (A.pol == 3) {
+      c = 0.0f;
+      s = 1.0f;
+    }
+    R.a[0] = make_float2(fmaf(c, cc.a1, s * cc.a2), 0.f);
+    R.b[0] = make_float2(fmaf(c, cc.b1, s * cc.b2), 0.f);
+  }
+  R.id = id;
+  R.ev = 0;
+  R.hits = 0;
+  R.last = S_LEFT;
+  R.hash = 2166136261u;
+}
+
+template <int F>
+__device__ __forceinline__ float ray_weight(const Ray<F>& R) {
+  float w = 0.f;
+#pragma unroll
+  for (int f = 0; f < F; ++f) w += cabs2(R.a[f]) + cabs2(R.b[f]);
+  return w * (1.0f / F);
+}
+
+// outcome of a non-mirror event
+struct Outcome {
+  int term;   // 0 alive, 1 terminated
+  int cat;
+  int bin;    // flat tally bin within the cell (eyebox exits), -1 otherwise
+  float I, w;
+  float Ts, Tp;
+};
+
+// Face / end event at surface sid (position already advanced).
+template <int F>
+__device__ __forceinline__ Outcome face_event(Ray<F>& R, int sid, const BlobHeader& H, const TraceArgs& A,
+                                              float2* seg_s, float2* seg_p, int& n_tir) {
+  Outcome o;
+  o.term = 0;
+  o.bin = -1;
+  o.I = 0.f;
+  o.Ts = o.Tp = 0.f;
+  R.hash = fnv(R.hash, (uint32_t)sid);
+  if (sid <= S_TOP) {
+    const float n = H.n_slab;
+    const float cz = R.d.z;
+    const float ci = fabsf(cz);
+    const float sin2 = fmaf(-cz, cz, 1.0f);
+    const float x = n * n * sin2;
+    if (x > 1.0f) {
+      float2 rs, rp;
+      tir_coef(n, ci, sin2, rs, rp);
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        R.a[f] = cmul(rs, R.a[f]);
+        R.b[f] = cmul(rp, R.b[f]);
+      }
+      if (seg_s) {
+        *seg_s = cmul(*seg_s, rs);
+        *seg_p = cmul(*seg_p, rp);
+      }
+      R.d.z = -cz;
+      ++n_tir;
+      return o;
+    }
+    o.term = 1;
+    o.w = ray_weight(R);
+    if (sid == S_BOT) {
+      o.cat = L_LEAKED;
+      return o;
+    }
+    // eye-side exit: Fresnel power transmission glass -> air
+    const float ct = sqrtf(fmaxf(1.0f - x, 0.0f));
+    const float u = n * ci;
+    const float ts = 2.0f * u / (u + ct);
+    const float tp = 2.0f * u / fmaf(n, ct, ci);
+    const float tf = ct / u;
+    o.Ts = tf * ts * ts;
+    o.Tp = tf * tp * tp;
+    float I = 0.f;
+#pragma unroll
+    for (int f = 0; f < F; ++f) I += fmaf(o.Ts, cabs2(R.a[f]), o.Tp * cabs2(R.b[f]));
+    o.I = I * (1.0f / F);
+    const float sfac = H.eye_relief / ct;
+    const float qx = fmaf(sfac * n, R.d.x, R.p.x);
+    const float qy = fmaf(sfac * n, R.d.y, R.p.y);
+    const float fxb = floorf((qx - A.eb_x0) * A.eb_sx);
+    bool inside = fxb >= 0.0f && fxb < (float)A.eb_nx;
+    int ey = 0;
+    if (H.dims == 3) {
+      const float fyb = floorf((qy - A.eb_y0) * A.eb_sy);
+      inside = inside && fyb >= 0.0f && fyb < (float)A.eb_ny;
+      ey = inside ? (int)fyb : 0;
+    }
+    if (inside) {
+      o.cat = L_EYEBOX;
+      o.bin = ey * A.eb_nx + (int)fxb;
+    } else {
+      o.cat = L_MISSED;
+    }
+    return o;
+  }
+  o.term = 1;
+  o.cat = L_ABSORBED;
+  o.w = ray_weight(R);
+  return o;
+}
+
+// Mirror event: coefficients, basis rotation, MC decision and rescaling.
+// Fills the tape entry fields when `te` is non-null.
+struct MirrorStep {
+  float2 cs, cp;   // applied coefficients (incl. 1/sqrt scaling)
+  float cphi, sphi, cpsi, spsi;
+  float cos0;
+  int front, refl;
+};
+
+template <int F>
+__device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob& B, float lam, const TraceArgs& A,
+                                                   int& layer_steps, float2* Es_out, float2* Ep_out) {
+  const BlobHeader& H = *B.h;
+  const MirrorRec& M = B.mir[k];
+  const V3 N = v3(M.nx, 0.0f, M.nz);
+  const float cd = dot3(R.d, N);
+  MirrorStep st;
+  st.front = cd < 0.0f;
+  st.cos0 = fabsf(cd);
+  MatTable mt;
+  mt.init(H, st.cos0, lam);
+  const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+  const Coef cf = tmm_forward(sv, st.front, mt, H.n_slab, st.cos0, layer_steps);
+  V3 sf, pf;
+  face_basis(R.d, sf, pf);
+  V3 sm = cross3(R.d, N);
+  const float sm2 = dot3(sm, sm);
+  if (sm2 > 1e-24f) {
+    const float r = rsqrtf(sm2);
+    sm = v3(sm.x * r, sm.y * r, sm.z * r);
+  } else {
+    sm = sf;
+  }
+  st.cphi = dot3(sf, sm);
+  st.sphi = dot3(pf, sm);
+  const int m = R.hits;
+  if ((m & 3) == 0)
+    R.rnd = philox10(make_uint4((uint32_t)R.id, (uint32_t)((unsigned long long)R.id >> 32), (uint32_t)(m >> 2), TAG_EVT),
+                     A.key0, A.key1);
+  const uint32_t word = (m & 3) == 0 ? R.rnd.x : (m & 3) == 1 ? R.rnd.y : (m & 3) == 2 ? R.rnd.z : R.rnd.w;
+  st.refl = u24(word) < M.omega;
+  V3 d2 = R.d;
+  if (st.refl) {
+    st.cs = cscale(cf.rs, M.isw);
+    st.cp = cscale(cf.rp, M.isw);
+    d2 = v3(fmaf(-2.0f * cd, N.x, R.d.x), R.d.y, fmaf(-2.0f * cd, N.z, R.d.z));
+  } else {
+    st.cs = cscale(cf.ts, M.is1w);
+    st.cp = cscale(cf.tp, M.is1w);
+  }
+  const V3 pm2 = cross3(sm, d2);
+  V3 sf2, pf2;
+  face_basis(d2, sf2, pf2);
+  st.cpsi = dot3(sf2, sm);
+  st.spsi = dot3(sf2, pm2);
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    const float2 Es = make_float2(fmaf(st.cphi, R.a[f].x, st.sphi * R.b[f].x), fmaf(st.cphi, R.a[f].y, st.sphi * R.b[f].y));
+    const float2 Ep = make_float2(fmaf(-st.sphi, R.a[f].x, st.cphi * R.b[f].x), fmaf(-st.sphi, R.a[f].y, st.cphi * R.b[f].y));
+    if (Es_out) {
+      Es_out[f] = Es;
+      Ep_out[f] = Ep;
+    }
+    const float2 Os = cmul(st.cs, Es), Op = cmul(st.cp, Ep);
+    R.a[f] = make_float2(fmaf(st.cpsi, Os.x, st.spsi * Op.x), fmaf(st.cpsi, Os.y, st.spsi * Op.y));
+    R.b[f] = make_float2(fmaf(-st.spsi, Os.x, st.cpsi * Op.x), fmaf(-st.spsi, Os.y, st.cpsi * Op.y));
+  }
+  R.d = d2;
+  R.hash = fnv(R.hash, (uint32_t)(S_MIR + k) | (st.refl ? 0x80u : 0u));
+  R.hits = m + 1;
+  return st;
+}
+
+__device__ __forceinline__ ChunkConst chunk_const(const TraceArgs& A, long long cell) {
+  ChunkConst cc;
+  cc.cell = cell;
+  const int li = (int)(cell / A.n_f), f = (int)(cell % A.n_f);
+  cc.lam = __ldg(A.lambda + li);
+  const FieldRec fr = A.fields[f];
+  cc.fd = v3(fr.dx, fr.dy, fr.dz);
+  V3 sf, pf;
+  face_basis(cc.fd, sf, pf);
+  const V3 e1 = v3(fr.e1x, fr.e1y, fr.e1z), e2 = v3(fr.e2x, fr.e2y, fr.e2z);
+  cc.a1 = dot3(e1, sf);
+  cc.b1 = dot3(e1, pf);
+  cc.a2 = dot3(e2, sf);
+  cc.b2 = dot3(e2, pf);
+  return cc;
+}
+
+// chunk -> cell and ray range; false for an empty chunk
+__device__ __forceinline__ bool chunk_range(const TraceArgs& A, long long chunk, long long& cell, long long& r0,
+                                            long long& r1) {
+  cell = A.cell_lo + chunk / A.chunks_per_cell;
+  const long long j = chunk % A.chunks_per_cell;
+  r0 = cell * A.n_cell + j * A.chunk_rays;
+  r1 = min(r0 + A.chunk_rays, (cell + 1) * A.n_cell);
+  r0 = max(r0, A.ray_begin);
+  r1 = min(r1, A.ray_end);
+  return r0 < r1;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+  return v;
+}
+__device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// K2: forward Monte Carlo trace. Persistent CTAs claim chunks (one cell, a
+// range of rays) from a global queue; lanes pull rays from the chunk with a
+// warp-aggregated shared counter; a warp advances its rays through face
+// events until every live ray sits on a mirror, then runs the per-hit
+// transfer-matrix chain together. Exits are aggregated per warp (lanes with
+// the same bin) into a shared FP32 cell tally that is flushed to the FP64
+// global tally at the end of the chunk.
+// ---------------------------------------------------------------------------
+template <int F>
+__global__ void __launch_bounds__(kBlock) k_trace_fwd(const TraceArgs A) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ unsigned long long s_next;
+  __shared__ long long s_chunk;
+  __shared__ float s_led[6];
+  __shared__ unsigned long long s_cnt[8];
+  float* s_tally = reinterpret_cast<float*>(smem + A.blob_bytes);
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < 6) s_led[tid] = 0.f;
+  if (tid < 8) s_cnt[tid] = 0ull;
+  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;
+  Blob B;
+  B.bind(smem);
+  const BlobHeader& H = *B.h;
+  const unsigned lt_mask = (1u << lane) - 1u;
+
+  float led[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int c_rays = 0, c_hits = 0, c_events = 0, c_tir = 0, c_steps = 0;
+  RayRec* recs = reinterpret_cast<RayRec*>(A.records);
+
+  for (;;) {
+    if (tid == 0) s_chunk = (long long)atomicAdd(A.work, 1ull);
+    for (int i = tid; i < A.bins; i += blockDim.x) s_tally[i] = 0.f;
+    __syncthreads();
+    const long long chunk = s_chunk;
+    if (chunk >= A.n_chunks) break;
+    long long cell, r0, r1;
+    const bool nonempty = chunk_range(A, chunk, cell, r0, r1);
+    if (tid == 0) s_next = (unsigned long long)r0;
+    __syncthreads();
+    if (nonempty) {
+      const ChunkConst cc = chunk_const(A, cell);
+      Ray<F> R;
+      bool has = false, at_mir = false, exhausted = false;
+      int hit_k = 0;
+      for (;;) {
+        // ---- phase A: fetch rays, advance through face events ----
+        for (;;) {
+          const bool need = !has && !exhausted;
+          const unsigned fm = __ballot_sync(FULL, need);
+          if (fm) {
+            const int leader = __ffs(fm) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(&s_next, (unsigned long long)__popc(fm));
+            base = __shfl_sync(FULL, base, leader);
+            if (need) {
+              const long long id = (long long)base + __popc(fm & lt_mask);
+              if (id < r1) {
+                gen_ray(R, id, cc, H, A);
+                has = true;
+                ++c_rays;
+              } else {
+                exhausted = true;
+              }
+            }
+          }
+          const bool adv = has && !at_mir;
+          if (!__any_sync(FULL, adv || (!has && !exhausted))) break;
+          int pend_bin = -1;
+          float pend_I = 0.f;
+          if (adv) {
+            float t;
+            const int sid = next_surface(B, R.p, R.d, R.last, t);
+            ++R.ev;
+            Outcome o;
+            o.term = 0;
+            if (sid < 0) {
+              o.term = 1;
+              o.cat = L_ABSORBED;
+              o.bin = -1;
+              o.I = 0.f;
+              o.w = ray_weight(R);
+            } else {
+              R.p = v3(fmaf(t, R.d.x, R.p.x), fmaf(t, R.d.y, R.p.y), fmaf(t, R.d.z, R.p.z));
+              R.last = sid;
+              if (sid >= S_MIR) {
+                at_mir = true;
+                hit_k = sid - S_MIR;
+              } else {
+                o = face_event<F>(R, sid, H, A, nullptr, nullptr, c_tir);
+              }
+            }
+            if (!o.term && !at_mir && R.ev >= A.max_events) {
+              o.term = 1;
+              o.cat = L_TRUNCATED;
+              o.bin = -1;
+              o.I = 0.f;
+              o.w = ray_weight(R);
+            }
+            if (o.term) {
+              has = false;
+              c_events += R.ev;
+              c_hits += R.hits;
+              if (o.cat == L_EYEBOX) {
+                led[L_EYEBOX] += o.I;
+                led[L_EXIT_REFL] += o.w - o.I;
+                pend_bin = o.bin;
+                pend_I = o.I;
+              } else if (o.cat == L_MISSED) {
+                led[L_MISSED] += o.I;
+                led[L_EXIT_REFL] += o.w - o.I;
+              } else {
+                led[o.cat] += o.w;
+              }
+              if (recs) {
+                RayRec rr;
+                rr.hash = R.hash;
+                rr.n_events = R.ev;
+                rr.n_hits = R.hits;
+                rr.cat = o.cat;
+                rr.bin = o.cat == L_EYEBOX ? (int)(cell * A.bins + o.bin) : -1;
+                rr.I = o.cat == L_EYEBOX ? o.I : 0.f;
+                rr.w = o.w;
+                rr.pad = 0;
+                recs[R.id - A.ray_begin] = rr;
+              }
+            }
+          }
+          // ---- per-warp aggregation of exits, then the block tally ----
+          const unsigned pm = __ballot_sync(FULL, pend_bin >= 0);
+          if (pm) {
+            const int key = pend_bin >= 0 ? pend_bin : -1 - lane;
+            const unsigned peers = __match_any_sync(FULL, key);
+            if (pend_bin >= 0) {
+              float sum = 0.f;
+              for (unsigned mm = peers; mm; mm &= mm - 1) sum += __shfl_sync(peers, pend_I, __ffs(mm) - 1);
+              if (lane == __ffs(peers) - 1) atomicAdd(&s_tally[pend_bin], sum);
+            }
+          }
+        }
+        // ---- phase B: per-hit transfer-matrix chain, all rays on mirrors ----
+        if (!__any_sync(FULL, at_mir)) break;
+        if (at_mir) {
+          mirror_event<F>(R, hit_k, B, cc.lam, A, c_steps, nullptr, nullptr);
+          at_mir = false;
+          if (R.ev >= A.max_events) {
+            has = false;
+            c_events += R.ev;
+            c_hits += R.hits;
+            const float w = ray_weight(R);
+            led[L_TRUNCATED] += w;
+            if (recs) {
+              RayRec rr;
+              rr.hash = R.hash;
+              rr.n_events = R.ev;
+              rr.n_hits = R.hits;
+              rr.cat = L_TRUNCATED;
+              rr.bin = -1;
+              rr.I = 0.f;
+              rr.w = w;
+              rr.pad = 0;
+              recs[R.id - A.ray_begin] = rr;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (nonempty) {
+      double* gt = A.tally + cell * (long long)A.bins;
+      for (int i = tid; i < A.bins; i += blockDim.x) {
+        const float v = s_tally[i];
+        if (v != 0.f) atomicAdd(gt + i, (double)v);
+      }
+    }
+    __syncthreads();
+  }
+  // ---- statistics ----
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    const float v = warp_sum(led[i]);
+    if (lane == 0 && v != 0.f) atomicAdd(&s_led[i], v);
+  }
+  const unsigned long long cv[5] = {(unsigned long long)c_rays, (unsigned long long)c_hits,
+                                    (unsigned long long)c_events, (unsigned long long)c_tir,
+                                    (unsigned long long)c_steps};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const unsigned long long v = warp_sum_u(cv[i]);
+    if (lane == 0 && v) atomicAdd(&s_cnt[i], v);
+  }
+  __syncthreads();
+  if (tid < 6 && s_led[tid] != 0.f) atomicAdd(A.ledger + tid, (double)s_led[tid]);
+  if (tid < 5 && s_cnt[tid]) atomicAdd(A.counters + tid, s_cnt[tid]);
+}
+
+// ---------------------------------------------------------------------------
+// K3: adjoint. Rounds of (replay -> hit records -> thin-film adjoint) per CTA.
+// Replay: the forward trace again from the same keys, with a per-ray tape of
+// mirror hits (incoming field, applied coefficients, basis rotations, TIR
+// products since the previous hit). A ray that ends in the eyebox seeds
+// dL/dE* = G[bin]/F (T_s a, T_p b) and walks its tape backwards, emitting for
+// each hit the weights A of f = 2 Re(A_s c_s + A_p c_p) into the CTA's record
+// buffer. Adjoint: every thread takes records and runs the checkpointed
+// thin-film adjoint, accumulating dL/dd into shared FP32 partials that are
+// added to the CTA's FP64 row after each round.
+// ---------------------------------------------------------------------------
+template <int F>
+struct TapeE {
+  float2 cs, cp;
+  float2 Es[F], Ep[F];
+  float cphi, sphi, cpsi, spsi;
+  float2 seg_s, seg_p;
+  float cos0;
+  int kfw;
+};
+
+struct GradSink {
+  float* s_grad;
+  unsigned long long* nonfinite;
+  __device__ __forceinline__ void operator()(int idx, float g) const {
+    if (isfinite(g)) {
+      atomicAdd(s_grad + idx, g);
+    } else {
+      atomicAdd(nonfinite, 1ull);  // reported in wg_stats; never added
+    }
+  }
+};
+
+template <int F>
+__global__ void __launch_bounds__(kBlock) k_trace_bwd(const TraceArgs A) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ unsigned long long s_next;
+  __shared__ long long s_chunk;
+  __shared__ int s_fill;
+  __shared__ unsigned long long s_cnt[8];
+  float* s_grad = reinterpret_cast<float*>(smem + A.blob_bytes);
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid < 8) s_cnt[tid] = 0ull;
+  if (tid == 0) s_fill = 0;
+  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;
+  Blob B;
+  B.bind(smem);
+  const BlobHeader& H = *B.h;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int i = tid; i < A.n_layers; i += blockDim.x) s_grad[i] = 0.f;
+  HitRec* hb = A.hit_buf + (long long)blockIdx.x * A.hit_cap;
+  double* grow = A.grad_cta + (long long)blockIdx.x * A.n_layers;
+  const int high_water = A.hit_cap - (int)blockDim.x * TAPE_HITS;
+
+  int c_rays = 0, c_hits = 0, c_overflow = 0, c_tallied = 0, c_steps = 0;
+  long long c_asteps = 0;
+  TapeE<F> tape[TAPE_HITS];
+
+  for (;;) {
+    if (tid == 0) s_chunk = (long long)atomicAdd(A.work, 1ull);
+    __syncthreads();
+    const long long chunk = s_chunk;
+    if (chunk >= A.n_chunks) break;
+    long long cell, r0, r1;
+    const bool nonempty = chunk_range(A, chunk, cell, r0, r1);
+    if (tid == 0) s_next = (unsigned long long)r0;
+    __syncthreads();
+    if (!nonempty) {
+      __syncthreads();
+      continue;
+    }
+    const ChunkConst cc = chunk_const(A, cell);
+    const double* Gc = A.G + cell * (long long)A.bins;
+    for (;;) {  // rounds within the chunk
+      Ray<F> R;
+      bool has = false, at_mir = false, exhausted = false;
+      int hit_k = 0;
+      float2 seg_s = make_float2(1.f, 0.f), seg_p = make_float2(1.f, 0.f);
+      for (;;) {
+        for (;;) {
+          const bool paused = *(volatile int*)&s_fill > high_water;
+          const bool need = !has && !exhausted && !paused;
+          const unsigned fm = __ballot_sync(FULL, need);
+          if (fm) {
+            const int leader = __ffs(fm) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(&s_next, (unsigned long long)__popc(fm));
+            base = __shfl_sync(FULL, base, leader);
+            if (need) {
+              const long long id = (long long)base + __popc(fm & lt_mask);
+              if (id < r1) {
+                gen_ray(R, id, cc, H, A);
+                has = true;
+                seg_s = make_float2(1.f, 0.f);
+                seg_p = make_float2(1.f, 0.f);
+                ++c_rays;
+              } else {
+                exhausted = true;
+              }
+            }
+          }
+          const bool adv = has && !at_mir;
+          const bool can_fetch = !has && !exhausted && !(*(volatile int*)&s_fill > high_water);
+          if (!__any_sync(FULL, adv || can_fetch)) break;
+          int emit = 0;  // hits to emit for a ray that ended in the eyebox
+          float g0 = 0.f;  // mantissa of G[bin] in [0.5, 1), exponent eG
+          int eG = 0;
+          Outcome o;
+          o.term = 0;
+          if (adv) {
+            float t;
+            const int sid = next_surface(B, R.p, R.d, R.last, t);
+            ++R.ev;
+            if (sid < 0) {
+              o.term = 1;
+              o.cat = L_ABSORBED;
+            } else {
+              R.p = v3(fmaf(t, R.d.x, R.p.x), fmaf(t, R.d.y, R.p.y), fmaf(t, R.d.z, R.p.z));
+              R.last = sid;
+              if (sid >= S_MIR) {
+                at_mir = true;
+                hit_k = sid - S_MIR;
+              } else {
+                int dummy = 0;
+                o = face_event<F>(R, sid, H, A, &seg_s, &seg_p, dummy);
+              }
+            }
+            if (!o.term && !at_mir && R.ev >= A.max_events) {
+              o.term = 1;
+              o.cat = L_TRUNCATED;
+            }
+            if (o.term) {
+              has = false;
+              c_hits += R.hits;
+              if (o.cat == L_EYEBOX) {
+                const double g = Gc[o.bin];
+                if (g != 0.0) {
+                  if (R.hits <= TAPE_HITS) {
+                    emit = R.hits;
+                    g0 = (float)frexp(g, &eG);
+                  } else {
+                    ++c_overflow;
+                  }
+                }
+                ++c_tallied;
+              }
+            }
+          }
+          // warp-aggregated reservation of record slots
+          int incl = emit;
+#pragma unroll
+          for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(FULL, incl, off);
+            if (lane >= off) incl += v;
+          }
+          const int total = __shfl_sync(FULL, incl, 31);
+          if (total) {
+            int base = 0;
+            if (lane == 31) base = atomicAdd(&s_fill, total);
+            base = __shfl_sync(FULL, base, 31);
+            if (emit) {
+              // reverse Jones sweep over the tape
+              const float sc = g0 * (1.0f / F);
+              float2 ga[F], gb[F];
+#pragma unroll
+              for (int f = 0; f < F; ++f) {
+                ga[f] = cmulc(seg_s, cscale(R.a[f], sc * o.Ts));
+                gb[f] = cmulc(seg_p, cscale(R.b[f], sc * o.Tp));
+              }
+              const int first = base + incl - emit;
+              for (int h = emit - 1; h >= 0; --h) {
+                const TapeE<F>& T = tape[h];
+                float2 gs[F], gp[F];
+                float2 As = make_float2(0.f, 0.f), Ap = make_float2(0.f, 0.f);
+                const int k = T.kfw & 0xff;
+                const bool refl = ((T.kfw >> 9) & 1) == 0;  // bit 9: 0 = reflected (r), 1 = transmitted (t)
+                const float scl = refl ? B.mir[k].isw : B.mir[k].is1w;
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                  gs[f] = make_float2(fmaf(T.cpsi, ga[f].x, -T.spsi * gb[f].x), fmaf(T.cpsi, ga[f].y, -T.spsi * gb[f].y));
+                  gp[f] = make_float2(fmaf(T.spsi, ga[f].x, T.cpsi * gb[f].x), fmaf(T.spsi, ga[f].y, T.cpsi * gb[f].y));
+                  As = cadd(As, cmulc(gs[f], T.Es[f]));
+                  Ap = cadd(Ap, cmulc(gp[f], T.Ep[f]));
+                }
+                HitRec rec;
+                rec.kfw = T.kfw;
+                rec.cos0 = T.cos0;
+                rec.lam = cc.lam;
+                rec.eA = eG;
+                rec.As = cscale(As, scl);
+                rec.Ap = cscale(Ap, scl);
+                hb[first + h] = rec;
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                  const float2 xs = cmulc(T.cs, gs[f]), xp = cmulc(T.cp, gp[f]);
+                  const float2 ya = make_float2(fmaf(T.cphi, xs.x, -T.sphi * xp.x), fmaf(T.cphi, xs.y, -T.sphi * xp.y));
+                  const float2 yb = make_float2(fmaf(T.sphi, xs.x, T.cphi * xp.x), fmaf(T.sphi, xs.y, T.cphi * xp.y));
+                  ga[f] = cmulc(T.seg_s, ya);
+                  gb[f] = cmulc(T.seg_p, yb);
+                }
+              }
+            }
+          }
+        }
+        if (!__any_sync(FULL, at_mir)) break;
+        if (at_mir) {
+          const int h = R.hits;
+          float2 Es[F], Ep[F];
+          const MirrorStep ms = mirror_event<F>(R, hit_k, B, cc.lam, A, c_steps, Es, Ep);
+          if (h < TAPE_HITS) {
+            TapeE<F>& T = tape[h];
+            T.cs = ms.cs;
+            T.cp = ms.cp;
+#pragma unroll
+            for (int f = 0; f < F; ++f) {
+              T.Es[f] = Es[f];
+              T.Ep[f] = Ep[f];
+            }
+            T.cphi = ms.cphi;
+            T.sphi = ms.sphi;
+            T.cpsi = ms.cpsi;
+            T.spsi = ms.spsi;
+            T.seg_s = seg_s;
+            T.seg_p = seg_p;
+            T.cos0 = ms.cos0;
+            T.kfw = hit_k | (ms.front << 8) | ((ms.refl ? 0 : 1) << 9);
+          }
+          seg_s = make_float2(1.f, 0.f);
+          seg_p = make_float2(1.f, 0.f);
+          at_mir = false;
+          if (R.ev >= A.max_events) {
+            has = false;
+            c_hits += R.hits;
+          }
+        }
+      }
+      __syncthreads();
+      // ---- thin-film adjoint over this round's records ----
+      const int fill = s_fill;
+      for (int i = tid; i < fill; i += blockDim.x) {
+        const HitRec rec = hb[i];
+        const int k = rec.kfw & 0xff;
+        const bool front = (rec.kfw >> 8) & 1;
+        const int which = (rec.kfw >> 9) & 1;
+        const MirrorRec& M = B.mir[k];
+        MatTable mt;
+        mt.init(H, rec.cos0, rec.lam);
+        const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+        GradSink sink{s_grad, A.counters + 8};
+        tmm_adjoint(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, rec.eA);
+        c_asteps += M.n_layers;
+      }
+      __syncthreads();
+      for (int i = tid; i < A.n_layers; i += blockDim.x) {
+        const float v = s_grad[i];
+        if (v != 0.f) {
+          grow[i] += (double)v;
+          s_grad[i] = 0.f;
+        }
+      }
+      if (tid == 0) s_fill = 0;
+      const bool done = s_next >= (unsigned long long)r1;
+      __syncthreads();
+      if (done) break;
+    }
+    __syncthreads();
+  }
+  const unsigned long long cv[5] = {(unsigned long long)c_rays, (unsigned long long)c_hits, 0ull, 0ull,
+                                    (unsigned long long)c_steps};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const unsigned long long v = warp_sum_u(cv[i]);
+    if (lane == 0 && v) atomicAdd(&s_cnt[i], v);
+  }
+  const unsigned long long ov = warp_sum_u((unsigned long long)c_overflow);
+  const unsigned long long tl = warp_sum_u((unsigned long long)c_tallied);
+  const unsigned long long as = warp_sum_u((unsigned long long)c_asteps);
+  if (lane == 0) {
+    if (ov) atomicAdd(&s_cnt[5], ov);
+    if (tl) atomicAdd(&s_cnt[6], tl);
+    if (as) atomicAdd(&s_cnt[7], as);
+  }
+  __syncthreads();
+  if (tid < 8 && s_cnt[tid]) atomicAdd(A.counters + tid, s_cnt[tid]);
+}
+
+// sum of the per-CTA FP64 rows, scattered to the design's layer order
+__global__ void k_reduce_grad(const double* grad_cta, int grid, int n_layers, const int* dev_to_orig, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_layers) return;
+  double s = 0.0;
+  for (int b = 0; b < grid; ++b) s += grad_cta[(long long)b * n_layers + i];
+  out[dev_to_orig[i]] = s;
+}
+
+// ---------------------------------------------------------------------------
+// K1: coating evaluation and its adjoint (test hooks, global-memory stack)
+// ---------------------------------------------------------------------------
+__global__ void k_coating_eval(const uint8_t* blob, int mirror, int side, long long n, const float* cos0,
+                               const float* lam, float* out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Blob B;
+  B.bind(blob);
+  const BlobHeader& H = *B.h;
+  const MirrorRec& M = B.mir[mirror];
+  MatTable mt;
+  mt.init(H, cos0[i], lam[i]);
+  const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+  int steps = 0;
+  const Coef c = tmm_forward(sv, side == 0, mt, H.n_slab, cos0[i], steps);
+  float* o = out + i * 8;
+  o[0] = c.rs.x;
+  o[1] = c.rs.y;
+  o[2] = c.rp.x;
+  o[3] = c.rp.y;
+  o[4] = c.ts.x;
+  o[5] = c.ts.y;
+  o[6] = c.tp.x;
+  o[7] = c.tp.y;
+}
+
+struct RowSink {
+  float* row;
+  int off, L;
+  bool front;
+  __device__ __forceinline__ void operator()(int idx, float g) const {
+    const int j = front ? idx - off : off + L - 1 - idx;
+    row[j] = g;
+  }
+};
+
+__global__ void k_coating_grad(const uint8_t* blob, int mirror, int side, long long n, const float* cos0,
+                               const float* lam, const float* w, int which, float* grad) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Blob B;
+  B.bind(blob);
+  const BlobHeader& H = *B.h;
+  const MirrorRec& M = B.mir[mirror];
+  MatTable mt;
+  mt.init(H, cos0[i], lam[i]);
+  const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+  RowSink sink{grad + i * M.n_layers, M.layer_off, M.n_layers, side == 0};
+  tmm_adjoint(sv, side == 0, mt, H.n_slab, cos0[i], make_float2(w[4 * i], w[4 * i + 1]),
+              make_float2(w[4 * i + 2], w[4 * i + 3]), which, sink);
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_prep_design(uint8_t* blob, const float* mir_x, const float* mir_tilt, const float* mir_omega,
+                               int n_mir, float ic_tilt_deg, float thick, cudaStream_t s) {
+  note_launches(1);
+  k_prep_design<<<(n_mir + 63) / 64, 64, 0, s>>>(blob, mir_x, mir_tilt, mir_omega, n_mir, ic_tilt_deg, thick);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prep_fields(FieldRec* out, const float* fx, const float* fy, int n_fx, int n_fy, float n_slab,
+                               float ic_tilt_deg, int dims, cudaStream_t s) {
+  const int n = n_fx * n_fy;
+  note_launches(1);
+  k_prep_fields<<<(n + 127) / 128, 128, 0, s>>>(out, fx, fy, n_fx, n_fy, n_slab, ic_tilt_deg, dims);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const int* orig_to_dev, int n_orig,
+                                    cudaStream_t s) {
+  note_launches(1);
+  k_thickness_update<<<(n_orig + 255) / 256, 256, 0, s>>>(blob, d_orig, orig_to_dev, n_orig);
+  return cudaGetLastError();
+}
+
+template <class K>
+static int occupancy(K kernel, size_t smem) {
+  int n = 0;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kBlock, smem);
+  return n;
+}
+
+int trace_fwd_blocks_per_sm(int F, size_t smem) {
+  return F == 2 ? occupancy(k_trace_fwd<2>, smem) : occupancy(k_trace_fwd<1>, smem);
+}
+int trace_bwd_blocks_per_sm(int F, size_t smem) {
+  return F == 2 ? occupancy(k_trace_bwd<2>, smem) : occupancy(k_trace_bwd<1>, smem);
+}
+
+cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int grid, size_t smem, cudaStream_t s) {
+  if (F == 2) {
+    cudaFuncSetAttribute(k_trace_fwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launches(1);
+    k_trace_fwd<2><<<grid, kBlock, smem, s>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_trace_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launches(1);
+    k_trace_fwd<1><<<grid, kBlock, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_bwd(const TraceArgs& a, int F, int grid, size_t smem, cudaStream_t s) {
+  if (F == 2) {
+    cudaFuncSetAttribute(k_trace_bwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launches(1);
+    k_trace_bwd<2><<<grid, kBlock, smem, s>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_trace_bwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launches(1);
+    k_trace_bwd<1><<<grid, kBlock, smem, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_grad(const double* grad_cta, int grid, int n_layers, const int* dev_to_orig, double* out,
+                               cudaStream_t s) {
+  if (n_layers == 0) return cudaSuccess;
+  note_launches(1);
+  k_reduce_grad<<<(n_layers + 127) / 128, 128, 0, s>>>(grad_cta, grid, n_layers, dev_to_orig, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coating_eval(const uint8_t* blob, int mirror, int side, long long n, const float* cos0,
+                                const float* lam, float* out, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  note_launches(1);
+  k_coating_eval<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(blob, mirror, side, n, cos0, lam, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coating_grad(const uint8_t* blob, int mirror, int side, long long n, const float* cos0,
+                                const float* lam, const float* w, int which, float* grad, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  note_launches(1);
+  k_coating_grad<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(blob, mirror, side, n, cos0, lam, w, which, grad);
+  return cudaGetLastError();
+}
+
+}  // namespace wgk

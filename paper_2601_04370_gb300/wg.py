@@ -1,0 +1,292 @@
+"""Python binding of libwg.so (include/wg.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels. Device buffers are torch
+tensors (device memory and streams come from PyTorch); host buffers are numpy
+arrays. If libwg.so is missing the import fails loudly: there is no CPU
+fallback.
+
+Names follow the C ABI: Context (wg_init / wg_shutdown), Context.create_design
+(wg_create_design), DesignHandle.set_params (wg_set_params), trace_forward,
+trace_backward, loss, eval_coating, eval_coating_grad. WGTrace is a
+torch.autograd.Function over wg_trace_forward / wg_trace_backward.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwg.so")
+
+WG_OK, WG_EINVAL, WG_ENOMEM, WG_EBUSY, WG_ENOTREADY, WG_ETIMEOUT, WG_ECANCELED, WG_EDEVICE, WG_ENOTFOUND = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+STATUS_NAMES = {0: "WG_OK", -1: "WG_EINVAL", -2: "WG_ENOMEM", -3: "WG_EBUSY", -4: "WG_ENOTREADY",
+                -5: "WG_ETIMEOUT", -6: "WG_ECANCELED", -7: "WG_EDEVICE", -8: "WG_ENOTFOUND"}
+
+
+class WGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class InitOpts(C.Structure):
+    _fields_ = [("device", C.c_int32), ("max_slots", C.c_int32), ("hbm_budget_bytes", C.c_size_t),
+                ("autotune_cache", C.c_char_p)]
+
+
+class DesignDesc(C.Structure):
+    _fields_ = [("dims", C.c_int32), ("n_materials", C.c_int32), ("n_mirrors", C.c_int32), ("reserved", C.c_int32),
+                ("n_slab", C.c_float), ("thickness_mm", C.c_float), ("width_mm", C.c_float),
+                ("x_end_mm", C.c_float), ("eye_relief_mm", C.c_float), ("ic_tilt_deg", C.c_float),
+                ("material_n", C.POINTER(C.c_float)), ("mirror_x_mm", C.POINTER(C.c_float)),
+                ("mirror_tilt_deg", C.POINTER(C.c_float)), ("mirror_omega", C.POINTER(C.c_float)),
+                ("n_layers", C.POINTER(C.c_int32)), ("layer_material", C.POINTER(C.c_int32)),
+                ("layer_thickness_nm", C.POINTER(C.c_float)), ("layer_pruned", C.POINTER(C.c_uint8))]
+
+
+class TraceCfg(C.Structure):
+    _fields_ = [("n_lambda", C.c_int32), ("n_fx", C.c_int32), ("n_fy", C.c_int32), ("pol", C.c_int32),
+                ("lambda_nm", C.POINTER(C.c_float)), ("field_x_deg", C.POINTER(C.c_float)),
+                ("field_y_deg", C.POINTER(C.c_float)), ("n_rays", C.c_int64), ("seed", C.c_uint64),
+                ("max_events", C.c_int32), ("eb_nx", C.c_int32), ("eb_ny", C.c_int32), ("flags", C.c_int32),
+                ("pupil_y_mm", C.c_float), ("eb_cx_mm", C.c_float), ("eb_cy_mm", C.c_float),
+                ("eb_w_mm", C.c_float), ("eb_h_mm", C.c_float), ("stream", C.c_void_p),
+                ("ray_begin", C.c_int64), ("ray_end", C.c_int64), ("ray_records", C.c_void_p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_rays", C.c_int64), ("n_hits", C.c_int64), ("n_events", C.c_int64), ("n_tir", C.c_int64),
+                ("n_layer_steps", C.c_int64), ("ledger", C.c_double * 6), ("kernel_ms", C.c_float),
+                ("overflow", C.c_int32), ("n_tallied", C.c_int64), ("n_adjoint_steps", C.c_int64),
+                ("n_nonfinite", C.c_int64)]
+
+    def to_dict(self):
+        return dict(n_rays=self.n_rays, n_hits=self.n_hits, n_events=self.n_events, n_tir=self.n_tir,
+                    n_layer_steps=self.n_layer_steps, ledger=np.array(self.ledger[:]), kernel_ms=self.kernel_ms,
+                    overflow=self.overflow, n_tallied=self.n_tallied, n_adjoint_steps=self.n_adjoint_steps,
+                    n_nonfinite=self.n_nonfinite)
+
+
+RAY_RECORD_DTYPE = np.dtype([("hash", np.uint32), ("n_events", np.int32), ("n_hits", np.int32),
+                             ("cat", np.int32), ("bin", np.int32), ("I", np.float32), ("w", np.float32),
+                             ("pad", np.int32)])
+
+_lib = None
+
+
+def lib():
+    """The loaded libwg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libwg.so not built ({LIB_PATH}); run python -m paper_2601_04370_gb300.build")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, dp, fp = C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double), C.c_void_p
+        L.wg_init.argtypes = [C.POINTER(vp), C.POINTER(InitOpts)]
+        L.wg_shutdown.argtypes = [vp]
+        L.wg_shutdown.restype = None
+        L.wg_last_error.restype = C.c_char_p
+        L.wg_version.restype = C.c_char_p
+        L.wg_kernel_launches.restype = C.c_uint64
+        L.wg_create_design.argtypes = [vp, C.POINTER(DesignDesc), C.POINTER(vp)]
+        L.wg_set_params.argtypes = [vp, fp, i64, fp, i32, vp]
+        L.wg_destroy_design.argtypes = [vp]
+        L.wg_destroy_design.restype = None
+        L.wg_eval_coating.argtypes = [vp, vp, i32, i32, i64, fp, fp, fp, vp]
+        L.wg_eval_coating_grad.argtypes = [vp, vp, i32, i32, i64, fp, fp, fp, i32, fp, vp]
+        L.wg_trace_forward.argtypes = [vp, vp, C.POINTER(TraceCfg), vp, C.POINTER(Stats)]
+        L.wg_trace_backward.argtypes = [vp, vp, C.POINTER(TraceCfg), vp, vp, vp, C.POINTER(Stats)]
+        L.wg_loss.argtypes = [vp, vp, C.POINTER(TraceCfg), i32, C.c_double, C.c_double, vp, dp, vp]
+        for name in ("wg_init", "wg_create_design", "wg_set_params", "wg_eval_coating", "wg_eval_coating_grad",
+                     "wg_trace_forward", "wg_trace_backward", "wg_loss"):
+            getattr(L, name).restype = C.c_int32
+        _lib = L
+    return _lib
+
+
+def _check(st):
+    if st != WG_OK:
+        raise WGError(st, lib().wg_last_error().decode())
+
+
+def _ptr(x) -> Optional[int]:
+    """Address of a torch tensor or numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _current_stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+
+
+class _CfgHolder:
+    """A TraceCfg whose host arrays stay alive as long as the holder."""
+
+    def __init__(self, cfg, stream=None, rays=None, records=None):
+        self.lam = np.ascontiguousarray(cfg.lam_nm, dtype=np.float32)
+        self.fx = np.ascontiguousarray(cfg.fx_deg, dtype=np.float32)
+        self.fy = np.ascontiguousarray(cfg.fy_deg, dtype=np.float32)
+        rb, re = (0, 0) if rays is None else (int(rays[0]), int(rays[1]))
+        self.c = TraceCfg(n_lambda=len(self.lam), n_fx=len(self.fx), n_fy=len(self.fy), pol=int(cfg.pol),
+                          lambda_nm=_fptr(self.lam), field_x_deg=_fptr(self.fx), field_y_deg=_fptr(self.fy),
+                          n_rays=int(cfg.n_rays), seed=int(cfg.seed), max_events=int(cfg.max_events),
+                          eb_nx=int(cfg.eb_nx), eb_ny=int(cfg.eb_ny), flags=0, pupil_y_mm=cfg.pupil_y_mm,
+                          eb_cx_mm=cfg.eb_cx_mm, eb_cy_mm=cfg.eb_cy_mm, eb_w_mm=cfg.eb_w_mm, eb_h_mm=cfg.eb_h_mm,
+                          stream=stream, ray_begin=rb, ray_end=re, ray_records=_ptr(records))
+
+
+class DesignHandle:
+    def __init__(self, ctx, handle, design):
+        self.ctx = ctx
+        self.h = handle
+        self.design = design
+
+    def set_params(self, thickness_nm=None, tilt_deg=None, stream=None):
+        th = tl = None
+        nth = ntl = 0
+        keep = []
+        if thickness_nm is not None:
+            if hasattr(thickness_nm, "data_ptr") and thickness_nm.is_cuda:
+                th = thickness_nm.data_ptr()
+                nth = thickness_nm.numel()
+            else:
+                a = np.ascontiguousarray(np.asarray(thickness_nm, dtype=np.float32))
+                keep.append(a)
+                th, nth = a.ctypes.data, a.size
+        if tilt_deg is not None:
+            a = np.ascontiguousarray(np.asarray(tilt_deg, dtype=np.float32))
+            keep.append(a)
+            tl, ntl = a.ctypes.data, a.size
+        _check(lib().wg_set_params(self.h, th, nth, tl, ntl, stream if stream is not None else _current_stream()))
+
+    def destroy(self):
+        if self.h:
+            lib().wg_destroy_design(self.h)
+            self.h = None
+
+
+class Context:
+    def __init__(self, device: int = 0, max_slots: int = 0, hbm_budget_bytes: int = 0):
+        h = C.c_void_p()
+        opts = InitOpts(device=device, max_slots=max_slots, hbm_budget_bytes=hbm_budget_bytes, autotune_cache=None)
+        _check(lib().wg_init(C.byref(h), C.byref(opts)))
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            lib().wg_shutdown(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def create_design(self, D) -> DesignHandle:
+        keep = [np.ascontiguousarray(D.mat_n, dtype=np.float32), np.ascontiguousarray(D.mirror_x_mm, dtype=np.float32),
+                np.ascontiguousarray(D.mirror_tilt_deg, dtype=np.float32),
+                np.ascontiguousarray(D.mirror_omega, dtype=np.float32),
+                np.ascontiguousarray(D.n_layers, dtype=np.int32), np.ascontiguousarray(D.layer_mat, dtype=np.int32),
+                np.ascontiguousarray(D.layer_d_nm, dtype=np.float32), np.ascontiguousarray(D.pruned, dtype=np.uint8)]
+        desc = DesignDesc(dims=D.dims, n_materials=len(keep[0]), n_mirrors=len(keep[1]), reserved=0,
+                          n_slab=D.n_slab, thickness_mm=D.thickness_mm, width_mm=D.width_mm, x_end_mm=D.x_end_mm,
+                          eye_relief_mm=D.eye_relief_mm, ic_tilt_deg=D.ic_tilt_deg, material_n=_fptr(keep[0]),
+                          mirror_x_mm=_fptr(keep[1]), mirror_tilt_deg=_fptr(keep[2]), mirror_omega=_fptr(keep[3]),
+                          n_layers=keep[4].ctypes.data_as(C.POINTER(C.c_int32)),
+                          layer_material=keep[5].ctypes.data_as(C.POINTER(C.c_int32)),
+                          layer_thickness_nm=_fptr(keep[6]), layer_pruned=keep[7].ctypes.data_as(C.POINTER(C.c_uint8)))
+        h = C.c_void_p()
+        _check(lib().wg_create_design(self.h, C.byref(desc), C.byref(h)))
+        return DesignHandle(self, h, D)
+
+    # ---- coating hooks ----
+    def eval_coating(self, dh, mirror, side, cos_theta, lambda_nm, out, stream=None):
+        _check(lib().wg_eval_coating(self.h, dh.h, mirror, side, cos_theta.numel(), _ptr(cos_theta), _ptr(lambda_nm),
+                                     _ptr(out), stream if stream is not None else _current_stream()))
+
+    def eval_coating_grad(self, dh, mirror, side, cos_theta, lambda_nm, weights, which, grad, stream=None):
+        _check(lib().wg_eval_coating_grad(self.h, dh.h, mirror, side, cos_theta.numel(), _ptr(cos_theta),
+                                          _ptr(lambda_nm), _ptr(weights), which, _ptr(grad),
+                                          stream if stream is not None else _current_stream()))
+
+    # ---- trace ----
+    def trace_forward(self, dh, cfg, tally, stats=True, stream=None, rays=None, records=None):
+        """tally: torch CUDA float64 tensor (device path) or numpy float64 array
+        (host path, copies inside the call). Returns the stats dict or None."""
+        h = _CfgHolder(cfg, stream if stream is not None else _current_stream(), rays, records)
+        st = Stats() if stats else None
+        _check(lib().wg_trace_forward(self.h, dh.h, C.byref(h.c), _ptr(tally), C.byref(st) if stats else None))
+        return st.to_dict() if stats else None
+
+    def trace_backward(self, dh, cfg, dL_dtally, grad_thickness, stats=True, stream=None, rays=None):
+        h = _CfgHolder(cfg, stream if stream is not None else _current_stream(), rays)
+        st = Stats() if stats else None
+        _check(lib().wg_trace_backward(self.h, dh.h, C.byref(h.c), _ptr(dL_dtally), _ptr(grad_thickness), None,
+                                       C.byref(st) if stats else None))
+        return st.to_dict() if stats else None
+
+    def loss(self, dh, cfg, tally, dL_dtally=None, kind=0, w_f=10.0, w_e=3.0, stream=None):
+        """Returns (L, I_mean, U_fov, U_eyebox); fills dL_dtally if given."""
+        h = _CfgHolder(cfg, stream if stream is not None else _current_stream())
+        out = np.zeros(4)
+        _check(lib().wg_loss(self.h, dh.h, C.byref(h.c), kind, w_f, w_e, _ptr(tally),
+                             out.ctypes.data_as(C.POINTER(C.c_double)), _ptr(dL_dtally)))
+        return tuple(float(x) for x in out)
+
+
+def version() -> str:
+    return lib().wg_version().decode()
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libwg.so in this process so far."""
+    return int(lib().wg_kernel_launches())
+
+
+def _torch_autograd():
+    import torch
+
+    class WGTrace(torch.autograd.Function):
+        """tally = WGTrace.apply(thickness_nm, ctx, design_handle, cfg).
+
+        forward: wg_set_params + wg_trace_forward; backward: wg_trace_backward
+        with grad_output as dL/dtally, returning dL/dthickness (FP64 -> FP32)."""
+
+        @staticmethod
+        def forward(actx, thickness, ctx, dh, cfg):
+            dh.set_params(thickness_nm=thickness.detach().float().contiguous())
+            tally = torch.empty(cfg.tally_shape, dtype=torch.float64, device=thickness.device)
+            ctx.trace_forward(dh, cfg, tally, stats=False)
+            actx.wg = (ctx, dh, cfg)
+            actx.n = thickness.numel()
+            actx.dtype = thickness.dtype
+            return tally
+
+        @staticmethod
+        def backward(actx, grad_tally):
+            ctx, dh, cfg = actx.wg
+            g = torch.empty(actx.n, dtype=torch.float64, device=grad_tally.device)
+            ctx.trace_backward(dh, cfg, grad_tally.contiguous().to(torch.float64), g, stats=False)
+            return g.to(actx.dtype), None, None, None
+
+    return WGTrace
+
+
+def __getattr__(name):
+    if name == "WGTrace":
+        return _torch_autograd()
+    raise AttributeError(name)
