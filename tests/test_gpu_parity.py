@@ -53,7 +53,7 @@ def run_gpu(ctx, D, C, records=True, rays=None, dh=None):
     return out
 
 
-def compare(C, g, o, frac_max=1e-4, tol=1e-4):
+def compare(C, g, o, frac_max=1e-4, tol=1e-4, ray_tol=1e-4):
     rg, ro = g["records"], o["records"]
     mism = (rg["hash"] != ro["hash"]) | (rg["bin"] != ro["bin"]) | (rg["n_events"] != ro["n_events"])
     n = len(rg)
@@ -75,7 +75,7 @@ def compare(C, g, o, frac_max=1e-4, tol=1e-4):
     for key in ("I", "w"):
         d = np.abs(rg[key][ok] - ro[key][ok]) / np.maximum(1.0, np.abs(ro[key][ok]))
         if d.size:
-            assert np.quantile(d, 0.999) <= 1e-4, (key, np.quantile(d, 0.999))
+            assert np.quantile(d, 0.999) <= ray_tol, (key, np.quantile(d, 0.999))
             assert d.max() <= 1e-2, (key, d.max())
     assert np.array_equal(rg["n_hits"][ok], ro["n_hits"][ok])
     assert np.array_equal(rg["cat"][ok], ro["cat"][ok])
@@ -185,7 +185,7 @@ def test_trace_200_layer_stacks_match_oracle(ctx, ora):
     D, C = W.differentiation(n_rays=1728 * 40)
     g = run_gpu(ctx, D, C)
     o = ora.trace(D, C, records=True)
-    compare(C, g, o, tol=2.5e-4)
+    compare(C, g, o, tol=2.5e-4, ray_tol=1e-3)
 
 
 def test_trace_ragged_and_tiny_cells(ctx, ora):
