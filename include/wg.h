@@ -265,6 +265,36 @@ wg_status wg_trace_backward(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg*
                             const double* dL_dtally, double* grad_thickness, double* grad_tilt,
                             wg_stats* stats);
 
+/*
+ * Allocation-free forward trace. The paper has no counterpart to this entry
+ * point: it is for callers that cannot allocate device memory while they
+ * trace, for example a host application whose own allocator owns all of the
+ * GPU's memory, or a loop with a fixed memory budget where an allocation
+ * could fail or stall. It computes what wg_trace_forward computes with the
+ * same kernels, but its per-call scratch (counters, energy ledger, chunk
+ * queue, wavelength and field tables) lives in one static device array of
+ * WG_NOALLOC_SCRATCH_BYTES bytes compiled into libwg.so instead of the
+ * context's workspace; every GPU that loads the library holds that array
+ * until the process exits. The call makes no device allocation.
+ *  - tally: device memory only (FP64, tally layout), overwritten for the
+ *    traced cells; a host pointer is rejected with WG_EINVAL (staging it
+ *    would allocate).
+ *  - The scratch needed is 256 B + the wavelength and field-angle arrays +
+ *    48 B per field (up to ~2700 fields); a configuration that needs more
+ *    than WG_NOALLOC_SCRATCH_BYTES is rejected with WG_EINVAL.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the array and clears the parts that must start at
+ *    zero; the array keeps the last call's contents. Calls whose work
+ *    overlaps on the GPU (other streams, other threads) race on the array:
+ *    serialize them.
+ * stats: host, optional (non-NULL synchronizes the stream).
+ */
+#define WG_NOALLOC_SCRATCH_BYTES (128 * 1024)
+wg_status wg_trace_forward_noalloc(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cfg, double* tally,
+                                   wg_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

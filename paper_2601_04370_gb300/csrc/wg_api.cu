@@ -695,3 +695,77 @@ extern "C" wg_status wg_loss(wg_ctx* c, const wg_design* d, const wg_trace_cfg* 
   CU(cudaStreamSynchronize(s));
   return WG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free forward trace (wg_trace_forward_noalloc). For callers that
+// cannot allocate device memory: the per-call scratch lives in this static
+// device array instead of the context's workspace. Host code must not pass
+// the array's name to a kernel (on the host it is only a stand-in); it uses
+// the device address looked up once per device below.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[WG_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[128] = {nullptr};  // device address of the array, per device ordinal
+
+// With the context's device current: the array's device address (looked up
+// on the first call on that device).
+static wg_status noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= 128) return fail(WG_EINVAL, "wg_trace_forward_noalloc: device %d unsupported", device);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(WG_EDEVICE, "wg_trace_forward_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    g_noalloc_addr[device] = p;
+  }
+  *out = g_noalloc_addr[device];
+  return WG_OK;
+}
+
+extern "C" wg_status wg_trace_forward_noalloc(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, double* tally,
+                                              wg_stats* stats) {
+  if (!c || !d || !tally) return fail(WG_EINVAL, "wg_trace_forward_noalloc: NULL ctx/design/tally");
+  Plan p;
+  wg_status st = make_plan(d, cfg, 2048, p);
+  if (st != WG_OK) return st;
+  p.chunk_rays = default_chunk(p);
+  p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
+  p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
+  const size_t smem = (size_t)d->blob_bytes + sizeof(float) * p.bins;
+  if (smem > 200 * 1024) return fail(WG_EINVAL, "wg_trace_forward_noalloc: design + eyebox too large for shared memory");
+  const WsLayout need = ws_layout(nullptr, cfg, p.n_f);
+  if (need.bytes > (size_t)WG_NOALLOC_SCRATCH_BYTES)
+    return fail(WG_EINVAL,
+                "wg_trace_forward_noalloc: this configuration needs %zu bytes of scratch, the static array holds %d "
+                "(%d fields x 48 B + wavelength/angle arrays + 256 B); use fewer fields or wg_trace_forward",
+                need.bytes, WG_NOALLOC_SCRATCH_BYTES, p.n_f);
+  cudaStream_t s = (cudaStream_t)cfg->stream;
+  std::lock_guard<std::mutex> lk(c->mu);
+  CU(cudaSetDevice(c->device));
+  if (!is_device_ptr(tally))
+    return fail(WG_EINVAL, "wg_trace_forward_noalloc: tally must be device memory (host buffers would need staging)");
+  void* base = nullptr;
+  st = noalloc_scratch(c->device, &base);
+  if (st != WG_OK) return st;
+  const WsLayout w = ws_layout(base, cfg, p.n_f);
+  // clear what must start at zero: counters, ledger, chunk queue, error word
+  CU(cudaMemsetAsync(w.head, 0, 256, s));
+  CU(cudaMemcpyAsync(w.lam, cfg->lambda_nm, sizeof(float) * cfg->n_lambda, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(w.fx, cfg->field_x_deg, sizeof(float) * cfg->n_fx, cudaMemcpyHostToDevice, s));
+  CU(cudaMemcpyAsync(w.fy, cfg->field_y_deg, sizeof(float) * cfg->n_fy, cudaMemcpyHostToDevice, s));
+  CU(launch_prep_fields(w.fields, w.fx, w.fy, cfg->n_fx, cfg->n_fy, d->n_slab, d->ic_tilt, d->dims, s));
+  CU(cudaMemsetAsync(tally + p.cell_lo * p.bins, 0, sizeof(double) * (p.cell_hi - p.cell_lo + 1) * p.bins, s));
+  TraceArgs a = base_args(d, cfg, p, w);
+  a.tally = tally;
+  const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, smem));
+  const int grid = (int)std::min<long long>(p.n_chunks, (long long)c->sm_count * bps);
+  if (stats) CU(cudaEventRecord(c->t0, s));
+  CU(launch_trace_fwd(a, p.F, grid, smem, s));
+  if (stats) {
+    CU(cudaEventRecord(c->t1, s));
+    return finish_stats(c, w, s, stats, true);
+  }
+  return WG_OK;
+}

@@ -101,8 +101,9 @@ def lib():
         L.wg_trace_forward.argtypes = [vp, vp, C.POINTER(TraceCfg), vp, C.POINTER(Stats)]
         L.wg_trace_backward.argtypes = [vp, vp, C.POINTER(TraceCfg), vp, vp, vp, C.POINTER(Stats)]
         L.wg_loss.argtypes = [vp, vp, C.POINTER(TraceCfg), i32, C.c_double, C.c_double, vp, dp, vp]
+        L.wg_trace_forward_noalloc.argtypes = [vp, vp, C.POINTER(TraceCfg), vp, C.POINTER(Stats)]
         for name in ("wg_init", "wg_create_design", "wg_set_params", "wg_eval_coating", "wg_eval_coating_grad",
-                     "wg_trace_forward", "wg_trace_backward", "wg_loss"):
+                     "wg_trace_forward", "wg_trace_backward", "wg_loss", "wg_trace_forward_noalloc"):
             getattr(L, name).restype = C.c_int32
         _lib = L
     return _lib
@@ -230,6 +231,15 @@ class Context:
         h = _CfgHolder(cfg, stream if stream is not None else _current_stream(), rays, records)
         st = Stats() if stats else None
         _check(lib().wg_trace_forward(self.h, dh.h, C.byref(h.c), _ptr(tally), C.byref(st) if stats else None))
+        return st.to_dict() if stats else None
+
+    def trace_forward_noalloc(self, dh, cfg, tally, stats=True, stream=None, rays=None):
+        """wg_trace_forward_noalloc: the forward trace for callers that cannot
+        allocate device memory; tally must be a CUDA tensor (float64)."""
+        h = _CfgHolder(cfg, stream if stream is not None else _current_stream(), rays)
+        st = Stats() if stats else None
+        _check(lib().wg_trace_forward_noalloc(self.h, dh.h, C.byref(h.c), _ptr(tally),
+                                              C.byref(st) if stats else None))
         return st.to_dict() if stats else None
 
     def trace_backward(self, dh, cfg, dL_dtally, grad_thickness, stats=True, stream=None, rays=None):

@@ -1,0 +1,73 @@
+"""wg_trace_forward_noalloc: the forward trace for callers that cannot
+allocate device memory (an application whose own allocator owns the GPU's
+memory, a loop with a fixed memory budget). Its scratch is a static device
+array inside libwg.so, so its result must equal wg_trace_forward's on the same
+inputs, call after call (the array keeps the previous call's contents and the
+entry point must reset it).
+
+This file is collected last, so a run that stops at its first failure has run
+every other test before it; it also passes alone in a fresh process.
+"""
+import numpy as np
+import pytest
+
+from paper_2601_04370_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_04370_gb300 import wg
+    c = wg.Context(0)
+    yield c
+    c.close()
+
+
+def _tally(C):
+    return torch.zeros(C.tally_shape, dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("cfg", ["tiny", "representative"])
+def test_noalloc_matches_trace_forward_on_two_calls(ctx, cfg):
+    D, C = W.tiny() if cfg == "tiny" else W.representative(n_rays=1728 * 32)
+    dh = ctx.create_design(D)
+    ref = _tally(C)
+    st_ref = ctx.trace_forward(dh, C, ref)
+    r = ref.cpu().numpy()
+    scale = np.abs(r).max()
+    for call in range(2):
+        out = _tally(C)
+        free0 = torch.cuda.mem_get_info()[0]
+        st = ctx.trace_forward_noalloc(dh, C, out)
+        torch.cuda.synchronize()
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free0   # nothing allocated on the device
+        o = out.cpu().numpy()
+        # same kernels and keys; only the order of FP64 atomic adds may differ
+        assert np.abs(o - r).max() <= 1e-5 * scale, (call, np.abs(o - r).max() / scale)
+        assert st["n_rays"] == st_ref["n_rays"] and st["n_hits"] == st_ref["n_hits"]
+        assert st["n_events"] == st_ref["n_events"]
+        assert np.allclose(st["ledger"], st_ref["ledger"], rtol=1e-5, atol=1e-6)
+    dh.destroy()
+
+
+def test_noalloc_rejects_oversize_and_host_buffers(ctx):
+    from paper_2601_04370_gb300 import wg
+    D, C = W.representative(n_rays=10_000)
+    dh = ctx.create_design(D)
+    big = C.replace(fx_deg=W.cell_centres(30.0, 64), fy_deg=W.cell_centres(17.0, 64))  # 4096 fields
+    with pytest.raises(wg.WGError) as e:
+        ctx.trace_forward_noalloc(dh, big, _tally(big))
+    assert e.value.status == wg.WG_EINVAL and "scratch" in str(e.value)
+    with pytest.raises(wg.WGError) as e:
+        ctx.trace_forward_noalloc(dh, C, np.zeros(C.tally_shape))
+    assert e.value.status == wg.WG_EINVAL
+    # still usable after the rejections
+    out = _tally(C)
+    st = ctx.trace_forward_noalloc(dh, C, out)
+    assert st["n_rays"] == C.total_rays
+    dh.destroy()
