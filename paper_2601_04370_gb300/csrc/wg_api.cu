@@ -93,6 +93,7 @@ struct wg_design {
   int* d_orig_to_dev = nullptr;
   int* d_dev_to_orig = nullptr;
   float* d_stage = nullptr;    // [n_orig] thickness staging for set_params
+  int period = 0;              // material period shared by all stacks (0, 2 or 3)
 };
 
 static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -246,7 +247,26 @@ static std::vector<uint8_t> build_blob(const wg_design& d) {
   return b;
 }
 
+// Smallest P in {2, 3} such that every mirror's (non-pruned) layer i has the
+// material of its layer i mod P; 0 if there is none. The kernels unroll the
+// layer loop by P with the material constants of each slot in registers.
+static int design_period(const wg_design& d) {
+  for (int P : {2, 3}) {
+    bool ok = true;
+    int orig = 0;
+    for (int k = 0; k < d.K && ok; ++k) {
+      std::vector<int> m;
+      for (int l = 0; l < d.n_layers[k]; ++l, ++orig)
+        if (!d.pruned[orig]) m.push_back(d.layer_mat[orig]);
+      for (size_t i = 0; i < m.size() && ok; ++i) ok = m[i] == m[i % P];
+    }
+    if (ok) return P;
+  }
+  return 0;
+}
+
 static wg_status upload_design(wg_design* d, cudaStream_t s) {
+  d->period = design_period(*d);
   std::vector<uint8_t> b = build_blob(*d);
   d->blob_bytes = (int)b.size();
   CU(cudaMalloc(&d->blob, b.size()));
@@ -381,7 +401,7 @@ extern "C" wg_status wg_eval_coating(wg_ctx* c, const wg_design* d, int32_t mirr
     return fail(WG_EINVAL, "wg_eval_coating: arrays must be device memory");
   std::lock_guard<std::mutex> lk(c->mu);
   CU(cudaSetDevice(c->device));
-  CU(launch_coating_eval(d->blob, mirror, side, n, cos_theta, lambda_nm, out_rt, (cudaStream_t)stream));
+  CU(launch_coating_eval(d->blob, d->period, mirror, side, n, cos_theta, lambda_nm, out_rt, (cudaStream_t)stream));
   return WG_OK;
 }
 
@@ -396,7 +416,8 @@ extern "C" wg_status wg_eval_coating_grad(wg_ctx* c, const wg_design* d, int32_t
     return fail(WG_EINVAL, "wg_eval_coating_grad: arrays must be device memory");
   std::lock_guard<std::mutex> lk(c->mu);
   CU(cudaSetDevice(c->device));
-  CU(launch_coating_grad(d->blob, mirror, side, n, cos_theta, lambda_nm, weights, which, grad, (cudaStream_t)stream));
+  CU(launch_coating_grad(d->blob, d->period, mirror, side, n, cos_theta, lambda_nm, weights, which, grad,
+                          (cudaStream_t)stream));
   return WG_OK;
 }
 
@@ -567,7 +588,11 @@ static wg_status finish_stats(wg_ctx* c, const WsLayout& w, cudaStream_t s, wg_s
   return WG_OK;
 }
 
-static long long default_chunk(const Plan& p) { return std::min<long long>(p.n_cell, 2048); }
+// rays per chunk: a cell split into equal chunks of at most 4096 rays
+static long long default_chunk(const Plan& p) {
+  const long long parts = (p.n_cell + 4095) / 4096;
+  return (p.n_cell + parts - 1) / parts;
+}
 
 extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, double* tally,
                                       wg_stats* stats) {
@@ -592,10 +617,10 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
   CU(cudaMemsetAsync(t + p.cell_lo * p.bins, 0, sizeof(double) * (p.cell_hi - p.cell_lo + 1) * p.bins, s));
   TraceArgs a = base_args(d, cfg, p, w);
   a.tally = t;
-  const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, smem));
+  const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, d->period, smem));
   const int grid = (int)std::min<long long>(p.n_chunks, (long long)c->sm_count * bps);
   if (stats) CU(cudaEventRecord(c->t0, s));
-  CU(launch_trace_fwd(a, p.F, grid, smem, s));
+  CU(launch_trace_fwd(a, p.F, d->period, grid, smem, s));
   if (stats) CU(cudaEventRecord(c->t1, s));
   CU(cudaEventRecord(c->ws_free, s));
   if (!dev_tally) {
@@ -607,34 +632,64 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
   return WG_OK;
 }
 
+// chunk layout of the ray range [rb, re) (cells touched, chunks per cell)
+static void plan_range(Plan& p, long long rb, long long re) {
+  p.rb = rb;
+  p.re = re;
+  p.cell_lo = rb / p.n_cell;
+  p.cell_hi = (re - 1) / p.n_cell;
+  p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
+  p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
+}
+
+// Adjoint scratch: hit records of one batch of rays (unsorted and sorted),
+// per-stack counts and offsets, FP64 per-layer sums.
+struct BwdScratch {
+  HitRec* rec;
+  HitRec* sorted;
+  unsigned int* keys;   // [3][128]: counts, offsets, cursors
+  unsigned long long* hit_count;
+  double* grad_acc;
+  long long cap;
+};
+
+static const long long kRecordsPerRay = 16;  // record capacity per ray of a batch (mean ~2)
+
 extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, const double* dL_dtally,
                                        double* grad_thickness, double* grad_tilt, wg_stats* stats) {
   if (!c || !d || !dL_dtally || !grad_thickness) return fail(WG_EINVAL, "wg_trace_backward: NULL argument");
   if (grad_tilt) return fail(WG_EINVAL, "wg_trace_backward: grad_tilt is reserved and must be NULL");
   Plan p;
-  wg_status st = make_plan(d, cfg, 1024, p);
+  wg_status st = make_plan(d, cfg, 2048, p);
   if (st != WG_OK) return st;
-  p.chunk_rays = std::min<long long>(p.n_cell, 1024);
-  p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
-  p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
-  const size_t smem = (size_t)d->blob_bytes + sizeof(float) * std::max(1, d->n_dev);
-  if (smem > 200 * 1024) return fail(WG_EINVAL, "wg_trace_backward: design too large for shared memory");
+  p.chunk_rays = default_chunk(p);
+  const size_t smem_r = (size_t)d->blob_bytes;
+  const size_t smem_a = (size_t)d->blob_bytes + sizeof(float) * std::max(1, d->n_dev);
+  if (smem_a > 200 * 1024) return fail(WG_EINVAL, "wg_trace_backward: design too large for shared memory");
   cudaStream_t s = (cudaStream_t)cfg->stream;
   std::lock_guard<std::mutex> lk(c->mu);
   CU(cudaSetDevice(c->device));
   WsLayout w;
   st = prepare_ws(c, d, cfg, p, s, w);
   if (st != WG_OK) return st;
-  const int bps = std::max(1, trace_bwd_blocks_per_sm(p.F, smem));
-  const int grid = (int)std::min<long long>(p.n_chunks, (long long)c->sm_count * bps);
-  const int hit_cap = kBlock * TAPE_HITS + 8192;
-  const size_t hit_bytes = (size_t)grid * hit_cap * hit_rec_bytes();
-  const size_t row_bytes = (size_t)grid * std::max(1, d->n_dev) * sizeof(double);
-  if (hit_bytes + row_bytes > c->bwd.n) {
+  // batches of whole chunks, large enough to fill the GPU several times
+  const long long total = p.re - p.rb;
+  long long batch = std::min<long long>(total, std::max<long long>(p.chunk_rays * c->sm_count * 4, 1ll << 21));
+  const long long cap = batch * kRecordsPerRay;
+  const size_t rec_bytes = (size_t)cap * hit_rec_bytes();
+  const size_t need = 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + sizeof(double) * std::max(1, d->n_dev);
+  if (need > c->bwd.n) {
     CU(cudaEventSynchronize(c->ws_free));
-    CU(c->bwd.ensure(hit_bytes + row_bytes));
+    CU(c->bwd.ensure(need));
   }
   uint8_t* bw = (uint8_t*)c->bwd.p;
+  BwdScratch sc;
+  sc.rec = (HitRec*)bw;
+  sc.sorted = (HitRec*)(bw + rec_bytes);
+  sc.keys = (unsigned int*)(bw + 2 * rec_bytes);
+  sc.hit_count = (unsigned long long*)(bw + 2 * rec_bytes + 3 * 128 * sizeof(unsigned int));
+  sc.grad_acc = (double*)(bw + 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64);
+  sc.cap = cap;
   const bool dev_G = is_device_ptr(dL_dtally);
   const bool dev_g = is_device_ptr(grad_thickness);
   const double* G = dL_dtally;
@@ -647,16 +702,65 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   }
   if (!dev_g) CU(cudaMallocAsync((void**)&gout, sizeof(double) * std::max(1, d->n_orig), s));
   CU(cudaMemsetAsync(gout, 0, sizeof(double) * std::max(1, d->n_orig), s));
-  CU(cudaMemsetAsync(bw + hit_bytes, 0, row_bytes, s));
-  TraceArgs a = base_args(d, cfg, p, w);
-  a.G = G;
-  a.hit_buf = (HitRec*)bw;
-  a.hit_cap = hit_cap;
-  a.grad_cta = (double*)(bw + hit_bytes);
-  if (stats) CU(cudaEventRecord(c->t0, s));
-  CU(launch_trace_bwd(a, p.F, grid, smem, s));
-  if (stats) CU(cudaEventRecord(c->t1, s));
-  CU(launch_reduce_grad(a.grad_cta, grid, d->n_dev, d->d_dev_to_orig, gout, s));
+  CU(cudaMemsetAsync(sc.grad_acc, 0, sizeof(double) * std::max(1, d->n_dev), s));
+  const int bps_r = std::max(1, bwd_replay_blocks_per_sm(p.F, d->period, smem_r));
+  const int bps_a = std::max(1, bwd_adjoint_blocks_per_sm(d->period, smem_a));
+  float ms_total = 0.f;
+  for (long long b0 = p.rb; b0 < p.re;) {
+    const long long b1 = std::min(p.re, b0 + batch);
+    Plan q = p;
+    plan_range(q, b0, b1);
+    TraceArgs a = base_args(d, cfg, q, w);
+    a.G = G;
+    a.hit_buf = sc.rec;
+    a.hit_cap = cap;
+    a.hit_count = sc.hit_count;
+    a.key_count = sc.keys;
+    CU(cudaMemsetAsync(&w.head->work, 0, sizeof(unsigned long long), s));
+    CU(cudaMemsetAsync(sc.keys, 0, 128 * sizeof(unsigned int), s));
+    CU(cudaMemsetAsync(sc.hit_count, 0, sizeof(unsigned long long), s));
+    const int grid_r = (int)std::min<long long>(q.n_chunks, (long long)c->sm_count * bps_r);
+    if (stats) CU(cudaEventRecord(c->t0, s));
+    CU(launch_bwd_replay(a, p.F, d->period, grid_r, smem_r, s));
+    unsigned long long n_rec = 0;
+    CU(cudaMemcpyAsync(&n_rec, sc.hit_count, sizeof(n_rec), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    if ((long long)n_rec > cap) {
+      // more records than the batch holds (never seen: ~2 records per ray against 16):
+      // redo this batch with half the rays
+      if (b1 - b0 <= 1) return fail(WG_ENOMEM, "wg_trace_backward: one ray needs more than %lld hit records", cap);
+      // (the dropped attempt's replay counters stay in the statistics)
+      batch = std::max<long long>(1, (b1 - b0) / 2);
+      continue;
+    }
+    CU(launch_bwd_sort(sc.rec, (long long)n_rec, sc.keys, sc.keys + 128, sc.keys + 256, sc.sorted, s));
+    AdjArgs aa;
+    aa.blob = d->blob;
+    aa.blob_bytes = d->blob_bytes;
+    aa.recs = sc.sorted;
+    aa.n_rec = (long long)n_rec;
+    aa.rec_chunk = 2048;
+    aa.n_layers = d->n_dev;
+    aa.grad_acc = sc.grad_acc;
+    aa.work = &w.head->work;
+    aa.counters = w.head->counters;
+    aa.error = &w.head->error;
+    CU(cudaMemsetAsync(&w.head->work, 0, sizeof(unsigned long long), s));
+    if (n_rec > 0) {
+      const long long chunks = ((long long)n_rec + aa.rec_chunk - 1) / aa.rec_chunk;
+      const int grid_a = (int)std::min<long long>(chunks, (long long)c->sm_count * bps_a);
+      CU(launch_bwd_adjoint(aa, d->period, grid_a, smem_a, s));
+    }
+    if (stats) {
+      CU(cudaEventRecord(c->t1, s));
+      CU(cudaEventSynchronize(c->t1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, c->t0, c->t1);
+      ms_total += ms;
+    }
+    b0 = b1;
+  }
+  CU(launch_scatter_grad(sc.grad_acc, d->n_dev, d->d_dev_to_orig, gout, s));
   CU(cudaEventRecord(c->ws_free, s));
   if (!dev_G) CU(cudaFreeAsync((void*)G, s));
   if (!dev_g) {
@@ -664,7 +768,11 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     CU(cudaFreeAsync(gout, s));
     CU(cudaStreamSynchronize(s));
   }
-  if (stats || !dev_g) return finish_stats(c, w, s, stats, stats != nullptr);
+  if (stats || !dev_g) {
+    st = finish_stats(c, w, s, stats, false);
+    if (stats) stats->kernel_ms = ms_total;
+    return st;
+  }
   return WG_OK;
 }
 
@@ -680,14 +788,14 @@ extern "C" wg_status wg_loss(wg_ctx* c, const wg_design* d, const wg_trace_cfg* 
   cudaStream_t s = (cudaStream_t)cfg->stream;
   std::lock_guard<std::mutex> lk(c->mu);
   CU(cudaSetDevice(c->device));
-  const size_t need = sizeof(double) * (2 * p.n_cells * 9 + 8);
+  const size_t need = sizeof(double) * (2 * p.n_cells * 9 + 8) + sizeof(unsigned short) * p.bins + 16;
   CU(cudaStreamWaitEvent(s, c->ws_free, 0));
   if (need > c->loss.n) {
     CU(cudaEventSynchronize(c->ws_free));
     CU(c->loss.ensure(need));
   }
   double* ws = (double*)c->loss.p;
-  double* odev = ws + 2 * p.n_cells * 9;
+  double* odev = ws + 2 * p.n_cells * 9;  // 8 doubles; pupil masks follow
   CU(launch_loss_impl(tally, d->dims, cfg->n_lambda, p.n_f, cfg->eb_nx, cfg->eb_ny, cfg->eb_cx_mm, cfg->eb_cy_mm,
                       cfg->eb_w_mm, cfg->eb_h_mm, 1.0 / (double)p.n_cell, kind, w_f, w_e, ws, odev, dL_dtally, s));
   CU(cudaMemcpyAsync(out, odev, sizeof(double) * 4, cudaMemcpyDeviceToHost, s));
@@ -759,10 +867,10 @@ extern "C" wg_status wg_trace_forward_noalloc(wg_ctx* c, const wg_design* d, con
   CU(cudaMemsetAsync(tally + p.cell_lo * p.bins, 0, sizeof(double) * (p.cell_hi - p.cell_lo + 1) * p.bins, s));
   TraceArgs a = base_args(d, cfg, p, w);
   a.tally = tally;
-  const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, smem));
+  const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, d->period, smem));
   const int grid = (int)std::min<long long>(p.n_chunks, (long long)c->sm_count * bps);
   if (stats) CU(cudaEventRecord(c->t0, s));
-  CU(launch_trace_fwd(a, p.F, grid, smem, s));
+  CU(launch_trace_fwd(a, p.F, d->period, grid, smem, s));
   if (stats) {
     CU(cudaEventRecord(c->t1, s));
     return finish_stats(c, w, s, stats, true);

@@ -34,7 +34,7 @@ constexpr int MAX_EVENTS = 128;
 constexpr int TAPE_HITS = 64;
 constexpr int CK = 8;                 // checkpoint stride (layers)
 constexpr int MAX_LAYERS_MIRROR = 512;
-constexpr int MAX_CK = MAX_LAYERS_MIRROR / CK + 1;
+constexpr int MAX_CK = MAX_LAYERS_MIRROR / 6 + 2;  // checkpoints at the shortest segment (6 layers)
 constexpr float TWO_PI = 6.283185307179586f;
 
 enum { S_BOT = 0, S_TOP = 1, S_LEFT = 2, S_RIGHT = 3, S_YNEG = 4, S_YPOS = 5, S_MIR = 8 };
@@ -275,25 +275,60 @@ __device__ __forceinline__ void coef_from_v(const CV& v, float eta0, int e, floa
   t = cscale(cdiv_s(make_float2(2.0f * eta0, 0.0f), den), pow2i(-e));
 }
 
+// Segment length of the layer loops: a multiple of the stack's material
+// period P, so that every step of a segment uses a fixed material slot held
+// in registers (P = 0: any stack; the material is selected per layer).
+template <int P>
+struct Seg {
+  static constexpr int CKP = (P == 3) ? 6 : 8;
+  static constexpr int NSLOT = P > 0 ? P : 1;
+};
+
+// Material constants of the traversal steps j with j % P == v for a stack
+// whose layer i has the material of layer i mod P.
+template <int P>
+__device__ __forceinline__ void stack_slots(const StackView& st, bool front, const MatTable& mt, MatK* kb) {
+#pragma unroll
+  for (int v = 0; v < P; ++v) {
+    int r = front ? v : (((st.L - 1 - v) % P) + P) % P;
+    r = r < st.L ? r : 0;
+    kb[v] = mt.get(st.m[st.off + r]);
+  }
+}
+
 // Effective coefficients in the paper's convention (r_p = -r_p(Abeles)).
+template <int P>
 __device__ __forceinline__ Coef tmm_forward(const StackView& st, bool front, const MatTable& mt, float n0,
                                             float cos0, int& layer_steps) {
+  constexpr int CKP = Seg<P>::CKP;
+  MatK kb[Seg<P>::NSLOT];
+  if constexpr (P > 0) stack_slots<P>(st, front, mt, kb);
   const float eta_s = n0 * cos0, eta_p = n0 / cos0;
   CV vs{1.0f, 0.0f, eta_s, 0.0f}, vp{1.0f, 0.0f, eta_p, 0.0f};
   int es = 0, ep = 0;
-  for (int j = st.L - 1; j >= 0; --j) {
-    const int i = st.idx(front, j);
-    const MatK k = mt.get(st.m[i]);
-    float c, s;
-    layer_cs(k, st.d[i], c, s);
-    cv_step(vs, c, s * k.q12s, s * k.q21s);
-    cv_step(vp, c, s * k.q12p, s * k.q21p);
-    if ((j & (CK - 1)) == 0) {
-      cv_rescale(vs, es);
-      cv_rescale(vp, ep);
+  const int L = st.L;
+  for (int j0 = L > 0 ? ((L - 1) / CKP) * CKP : -1; j0 >= 0; j0 -= CKP) {
+#pragma unroll
+    for (int u = CKP - 1; u >= 0; --u) {
+      const int j = j0 + u;
+      if (j < L) {
+        const int i = st.idx(front, j);
+        MatK k;
+        if constexpr (P > 0) {
+          k = kb[u % P];
+        } else {
+          k = mt.get(st.m[i]);
+        }
+        float c, s;
+        layer_cs(k, st.d[i], c, s);
+        cv_step(vs, c, s * k.q12s, s * k.q21s);
+        cv_step(vp, c, s * k.q12p, s * k.q21p);
+      }
     }
+    cv_rescale(vs, es);
+    cv_rescale(vp, ep);
   }
-  layer_steps += st.L;
+  layer_steps += L;
   Coef out;
   coef_from_v(vs, eta_s, es, out.rs, out.ts);
   float2 rpm;
@@ -388,28 +423,46 @@ __device__ __forceinline__ CRow coef_row(const CV& v, float eta0, int e, float2 
   return a;
 }
 
-template <class Sink>
+template <int P, class Sink>
 __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, const MatTable& mt, float n0,
                                             float cos0, float2 A_s, float2 A_p, int which, Sink& sink,
                                             int eA = 0) {
   // (A_s, A_p) * 2^eA are the weights; eA carries the range of dL/dtally
+  constexpr int CKP = Seg<P>::CKP;
+  MatK kb[Seg<P>::NSLOT];
+  if constexpr (P > 0) stack_slots<P>(st, front, mt, kb);
   Ckpt ck[MAX_CK];
   const int L = st.L;
-  const int nseg = (L + CK - 1) / CK;
+  const int nseg = (L + CKP - 1) / CKP;
   const float eta_s = n0 * cos0, eta_p = n0 / cos0;
   CV vs{1.0f, 0.0f, eta_s, 0.0f}, vp{1.0f, 0.0f, eta_p, 0.0f};
   int es = 0, ep = 0;
   ck[nseg] = Ckpt{vs, vp, 0, 0};
-  for (int j = L - 1; j >= 0; --j) {
-    const int i = st.idx(front, j);
-    const MatK k = mt.get(st.m[i]);
-    float c, s;
-    layer_cs(k, st.d[i], c, s);
-    cv_step(vs, c, s * k.q12s, s * k.q21s);
-    cv_step(vp, c, s * k.q12p, s * k.q21p);
-    cv_rescale32(vs, es);
-    cv_rescale32(vp, ep);
-    if ((j & (CK - 1)) == 0) ck[j / CK] = Ckpt{vs, vp, es, ep};
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int j0 = sg * CKP;
+#pragma unroll
+    for (int u = CKP - 1; u >= 0; --u) {
+      const int j = j0 + u;
+      if (j < L) {
+        const int i = st.idx(front, j);
+        MatK k;
+        if constexpr (P > 0) {
+          k = kb[u % P];
+        } else {
+          k = mt.get(st.m[i]);
+        }
+        float c, s;
+        layer_cs(k, st.d[i], c, s);
+        cv_step(vs, c, s * k.q12s, s * k.q21s);
+        cv_step(vp, c, s * k.q12p, s * k.q21p);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      cv_rescale32(vs, es);
+      cv_rescale32(vp, ep);
+    }
+    ck[sg] = Ckpt{vs, vp, es, ep};
   }
   // paper convention r_p = -r_p(Abeles): flip A_p for reflection
   const float2 Ap = which == 0 ? make_float2(-A_p.x, -A_p.y) : A_p;
@@ -419,19 +472,24 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
   eas += eA;
   eap += eA;
   for (int sg = 0; sg < nseg; ++sg) {
-    const int j0 = sg * CK;
+    const int j0 = sg * CKP;
     const Ckpt c1 = ck[sg + 1];
-    CV bs[CK], bp[CK];
-    float bc[CK], bsn[CK];
-    int bm[CK];
+    CV bs[CKP], bp[CKP];
+    float bc[CKP], bsn[CKP];
+    int bm[CKP];
     CV ws = c1.s, wp = c1.p;
 #pragma unroll
-    for (int u = CK - 1; u >= 0; --u) {
+    for (int u = CKP - 1; u >= 0; --u) {
       const int j = j0 + u;
       if (j < L) {
         const int i = st.idx(front, j);
-        const int mm = st.m[i];
-        const MatK k = mt.get(mm);
+        MatK k;
+        if constexpr (P > 0) {
+          k = kb[u % P];
+        } else {
+          bm[u] = st.m[i];
+          k = mt.get(bm[u]);
+        }
         float c, s;
         layer_cs(k, st.d[i], c, s);
         cv_step(ws, c, s * k.q12s, s * k.q21s);
@@ -440,14 +498,18 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         bp[u] = wp;
         bc[u] = c;
         bsn[u] = s;
-        bm[u] = mm;
       }
     }
 #pragma unroll
-    for (int u = 0; u < CK; ++u) {
+    for (int u = 0; u < CKP; ++u) {
       const int j = j0 + u;
       if (j < L) {
-        const MatK k = mt.get(bm[u]);
+        MatK k;
+        if constexpr (P > 0) {
+          k = kb[u % P];
+        } else {
+          k = mt.get(bm[u]);
+        }
         const CV& x = bs[u];
         const CV& y = bp[u];
         const float gs = fmaf(k.q12s, fmaf(as.a0.x, x.yi, as.a0.y * x.yr), k.q21s * fmaf(as.a1.x, x.xi, as.a1.y * x.xr));

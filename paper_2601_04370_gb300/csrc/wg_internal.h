@@ -34,12 +34,26 @@ struct TraceArgs {
   void* records;              // wg_ray_record* or null
   unsigned long long* work;   // chunk queue counter (zeroed before launch)
   unsigned int* error;        // device error word (bounded waits)
-  // backward scratch
-  HitRec* hit_buf;            // [grid][hit_cap]
-  int hit_cap;
-  float* grad_part;           // unused (reserved)
-  double* grad_cta;           // [grid][n_layers] FP64 per-CTA accumulators
+  // backward replay
+  HitRec* hit_buf;            // [hit_cap] hit records
+  long long hit_cap;
+  unsigned long long* hit_count;  // records reserved (may exceed hit_cap: overflow)
+  unsigned int* key_count;    // [2 * 64] records per stack (mirror, side)
   int n_layers;               // device layers
+};
+
+// Arguments of the thin-film adjoint over sorted hit records.
+struct AdjArgs {
+  const uint8_t* blob;
+  int blob_bytes;
+  const HitRec* recs;         // sorted by stack
+  long long n_rec;
+  int rec_chunk;              // records per CTA work item
+  int n_layers;
+  double* grad_acc;           // [n_layers] FP64 sums (device layer order)
+  unsigned long long* work;
+  unsigned long long* counters;
+  unsigned int* error;
 };
 
 constexpr int kBlock = 256;
@@ -48,26 +62,31 @@ constexpr int kBlock = 256;
 void note_launches(unsigned long long n);
 unsigned long long launches();
 
-// launchers (return cudaError_t of the launch)
+// launchers (return cudaError_t of the launch). P: material period of the
+// design's stacks (0 = any, 2, 3); F: fields per ray (2 = s+p pair).
 cudaError_t launch_prep_design(uint8_t* blob, const float* mir_x, const float* mir_tilt, const float* mir_omega,
                                int n_mir, float ic_tilt_deg, float thick, cudaStream_t s);
 cudaError_t launch_prep_fields(FieldRec* out, const float* fx, const float* fy, int n_fx, int n_fy,
                                float n_slab, float ic_tilt_deg, int dims, cudaStream_t s);
-cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_trace_bwd(const TraceArgs& a, int F, int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_reduce_grad(const double* grad_cta, int grid, int n_layers, const int* dev_to_orig,
-                               double* grad_out, cudaStream_t s);
-cudaError_t launch_coating_eval(const uint8_t* blob, int mirror, int side, long long n, const float* cos0,
+cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_bwd_sort(const HitRec* in, long long n, unsigned int* key_count, unsigned int* key_off,
+                            unsigned int* key_cursor, HitRec* out, cudaStream_t s);
+cudaError_t launch_bwd_adjoint(const AdjArgs& a, int P, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_scatter_grad(const double* acc, int n_layers, const int* dev_to_orig, double* out,
+                                cudaStream_t s);
+cudaError_t launch_coating_eval(const uint8_t* blob, int P, int mirror, int side, long long n, const float* cos0,
                                 const float* lam, float* out, cudaStream_t s);
-cudaError_t launch_coating_grad(const uint8_t* blob, int mirror, int side, long long n, const float* cos0,
+cudaError_t launch_coating_grad(const uint8_t* blob, int P, int mirror, int side, long long n, const float* cos0,
                                 const float* lam, const float* w, int which, float* grad, cudaStream_t s);
 cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const int* orig_to_dev, int n_orig,
                                     cudaStream_t s);
-int trace_fwd_blocks_per_sm(int F, size_t smem);
-int trace_bwd_blocks_per_sm(int F, size_t smem);
+int trace_fwd_blocks_per_sm(int F, int P, size_t smem);
+int bwd_replay_blocks_per_sm(int F, int P, size_t smem);
+int bwd_adjoint_blocks_per_sm(int P, size_t smem);
 size_t hit_rec_bytes();
 
-// loss (workspace: 2 * cells * 9 doubles)
+// loss (workspace: 2 * cells * 9 + 8 doubles, then one u16 pupil mask per eyebox bin)
 cudaError_t launch_loss_impl(const double* tally, int dims, int n_lam, int n_f, int nx, int ny, double cx, double cy,
                              double w, double h, double inv_ncell, int kind, double w_f, double w_e, double* ws,
                              double* out_dev, double* dL, cudaStream_t s);

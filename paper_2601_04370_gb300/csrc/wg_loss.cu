@@ -35,8 +35,20 @@ struct LossGeom {
   double cx, cy, w, h;
 };
 
+// pupil membership bitmask of every eyebox bin (the same for all cells)
+__global__ void k_pupil_masks(LossGeom g, unsigned short* mask) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= g.nx * g.ny) return;
+  const int ex = b % g.nx, ey = b / g.nx;
+  unsigned short m = 0;
+  for (int p = 0; p < g.n_pupil; ++p)
+    if (in_pupil(g.dims, p, ex, ey, g.cx, g.cy, g.w, g.h, g.nx, g.ny)) m |= (unsigned short)(1u << p);
+  mask[b] = m;
+}
+
 // I[cell, p]
-__global__ void k_pupil_sums(const double* tally, LossGeom g, double inv_ncell, double* I) {
+__global__ void k_pupil_sums(const double* tally, LossGeom g, const unsigned short* mask, double inv_ncell,
+                             double* I) {
   const long long cell = blockIdx.x;
   const int bins = g.nx * g.ny;
   __shared__ double s_acc[9][32];
@@ -46,9 +58,10 @@ __global__ void k_pupil_sums(const double* tally, LossGeom g, double inv_ncell, 
   for (int b = threadIdx.x; b < bins; b += blockDim.x) {
     const double v = t[b];
     if (v == 0.0) continue;
-    const int ex = b % g.nx, ey = b / g.nx;
-    for (int p = 0; p < g.n_pupil; ++p)
-      if (in_pupil(g.dims, p, ex, ey, g.cx, g.cy, g.w, g.h, g.nx, g.ny)) acc[p] += v;
+    const unsigned m = mask[b];
+#pragma unroll
+    for (int p = 0; p < 9; ++p)
+      if (m & (1u << p)) acc[p] += v;
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int p = 0; p < g.n_pupil; ++p) {
@@ -142,16 +155,16 @@ __global__ void k_loss_scalar(const double* I, int n_lam, int n_f, int P, int ki
 }
 
 // dL/dtally[cell, bin] = sum_{p containing bin} dL/dI[cell, p] / rays per cell
-__global__ void k_loss_scatter(const double* dI, LossGeom g, double inv_ncell, long long n_cells, double* dL) {
+__global__ void k_loss_scatter(const double* dI, LossGeom g, const unsigned short* mask, double inv_ncell,
+                               long long n_cells, double* dL) {
   const long long bins = (long long)g.nx * g.ny;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n_cells * bins) return;
   const long long cell = i / bins;
-  const int b = (int)(i % bins);
-  const int ex = b % g.nx, ey = b / g.nx;
+  const unsigned m = mask[i % bins];
   double v = 0.0;
   for (int p = 0; p < g.n_pupil; ++p)
-    if (in_pupil(g.dims, p, ex, ey, g.cx, g.cy, g.w, g.h, g.nx, g.ny)) v += dI[cell * g.n_pupil + p];
+    if (m & (1u << p)) v += dI[cell * g.n_pupil + p];
   dL[i] = v * inv_ncell;
 }
 
@@ -162,12 +175,15 @@ cudaError_t launch_loss_impl(const double* tally, int dims, int n_lam, int n_f, 
   const long long n_cells = (long long)n_lam * n_f;
   double* I = ws;
   double* dI = ws + n_cells * g.n_pupil;
-  note_launches(dL ? 3 : 2);
-  k_pupil_sums<<<(unsigned)n_cells, 256, 0, s>>>(tally, g, inv_ncell, I);
+  unsigned short* mask = reinterpret_cast<unsigned short*>(ws + 2 * n_cells * 9 + 8);
+  const int bins = nx * ny;
+  note_launches(dL ? 4 : 3);
+  k_pupil_masks<<<(bins + 255) / 256, 256, 0, s>>>(g, mask);
+  k_pupil_sums<<<(unsigned)n_cells, 256, 0, s>>>(tally, g, mask, inv_ncell, I);
   k_loss_scalar<<<1, 256, 0, s>>>(I, n_lam, n_f, g.n_pupil, kind, w_f, w_e, dI, out_dev);
   if (dL) {
     const long long n = n_cells * nx * ny;
-    k_loss_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dI, g, inv_ncell, n_cells, dL);
+    k_loss_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dI, g, mask, inv_ncell, n_cells, dL);
   }
   return cudaGetLastError();
 }

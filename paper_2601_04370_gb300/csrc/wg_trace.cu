@@ -1,6 +1,7 @@
 // Kernels of the waveguide trace: design/field preparation, the persistent
-// forward Monte Carlo trace (K2), the fused adjoint (K3: replay + per-hit
-// transfer-matrix adjoint), coating test hooks (K1) and gradient reduction.
+// forward Monte Carlo trace (K2), the adjoint (K3: replay -> hit records ->
+// counting sort by stack -> per-hit thin-film adjoint), coating test hooks
+// (K1) and the gradient scatter.
 //
 // Paper: "End-to-end differentiable design of geometric waveguide displays"
 // (arXiv 2601.04370), Methods: "Multilayer thin-film solver" (Eq. 2, Eq. 3,
@@ -22,7 +23,7 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr float HALF_ULP24 = 2.98023223876953125e-08f;  // 2^-25
 
 struct alignas(16) HitRec {
-  int kfw;     // mirror | front << 8 | which << 9 (0 = r, 1 = t)
+  int kfw;     // mirror | front << 8 | which << 9 (0 = r, 1 = t); -1 = slot of a dropped ray
   float cos0;
   float lam;
   int eA;      // weights are (As, Ap) * 2^eA (dL/dtally spans the FP64 range)
@@ -306,7 +307,7 @@ struct MirrorStep {
   int front, refl;
 };
 
-template <int F>
+template <int F, int P>
 __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob& B, float lam, const TraceArgs& A,
                                                    int& layer_steps, float2* Es_out, float2* Ep_out) {
   const BlobHeader& H = *B.h;
@@ -319,7 +320,7 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
   MatTable mt;
   mt.init(H, st.cos0, lam);
   const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
-  const Coef cf = tmm_forward(sv, st.front, mt, H.n_slab, st.cos0, layer_steps);
+  const Coef cf = tmm_forward<P>(sv, st.front, mt, H.n_slab, st.cos0, layer_steps);
   V3 sf, pf;
   face_basis(R.d, sf, pf);
   V3 sm = cross3(R.d, N);
@@ -419,8 +420,8 @@ __device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v) {
 // the same bin) into a shared FP32 cell tally that is flushed to the FP64
 // global tally at the end of the chunk.
 // ---------------------------------------------------------------------------
-template <int F>
-__global__ void __launch_bounds__(kBlock) k_trace_fwd(const TraceArgs A) {
+template <int F, int P>
+__global__ void __launch_bounds__(kBlock, 2) k_trace_fwd(const TraceArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ unsigned long long s_next;
@@ -554,7 +555,7 @@ __global__ void __launch_bounds__(kBlock) k_trace_fwd(const TraceArgs A) {
         // ---- phase B: per-hit transfer-matrix chain, all rays on mirrors ----
         if (!__any_sync(FULL, at_mir)) break;
         if (at_mir) {
-          mirror_event<F>(R, hit_k, B, cc.lam, A, c_steps, nullptr, nullptr);
+          mirror_event<F, P>(R, hit_k, B, cc.lam, A, c_steps, nullptr, nullptr);
           at_mir = false;
           if (R.ev >= A.max_events) {
             has = false;
@@ -608,15 +609,20 @@ __global__ void __launch_bounds__(kBlock) k_trace_fwd(const TraceArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// K3: adjoint. Rounds of (replay -> hit records -> thin-film adjoint) per CTA.
-// Replay: the forward trace again from the same keys, with a per-ray tape of
-// mirror hits (incoming field, applied coefficients, basis rotations, TIR
-// products since the previous hit). A ray that ends in the eyebox seeds
-// dL/dE* = G[bin]/F (T_s a, T_p b) and walks its tape backwards, emitting for
-// each hit the weights A of f = 2 Re(A_s c_s + A_p c_p) into the CTA's record
-// buffer. Adjoint: every thread takes records and runs the checkpointed
-// thin-film adjoint, accumulating dL/dd into shared FP32 partials that are
-// added to the CTA's FP64 row after each round.
+// K3: adjoint, in three kernels with their own register budgets.
+//
+// k_bwd_replay: the forward trace again from the same keys, with a per-ray
+//   tape of mirror hits in local memory (incoming field, applied
+//   coefficients, basis rotations, TIR products since the previous hit). A
+//   ray that ends in the eyebox seeds dL/dE* = G[bin]/F (T_s a, T_p b),
+//   walks its tape backwards and emits one record per hit: the weights A of
+//   f = 2 Re(A_s c_s + A_p c_p) (dL/dc of that hit's raw coefficients).
+// k_bwd_scan + k_bwd_scatter: counting sort of the records by stack
+//   (mirror, side), so a warp's 32 records share one stack.
+// k_bwd_adjoint: one record per lane, checkpointed thin-film adjoint; when
+//   the warp's 32 records share a stack every layer step touches the same
+//   gradient entry in all lanes, which is reduced with shuffles and added
+//   once; partial FP32 sums in shared memory go to FP64 after each chunk.
 // ---------------------------------------------------------------------------
 template <int F>
 struct TapeE {
@@ -628,42 +634,26 @@ struct TapeE {
   int kfw;
 };
 
-struct GradSink {
-  float* s_grad;
-  unsigned long long* nonfinite;
-  __device__ __forceinline__ void operator()(int idx, float g) const {
-    if (isfinite(g)) {
-      atomicAdd(s_grad + idx, g);
-    } else {
-      atomicAdd(nonfinite, 1ull);  // reported in wg_stats; never added
-    }
-  }
-};
-
-template <int F>
-__global__ void __launch_bounds__(kBlock) k_trace_bwd(const TraceArgs A) {
+template <int F, int P>
+__global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ unsigned long long s_next;
   __shared__ long long s_chunk;
-  __shared__ int s_fill;
+  __shared__ unsigned int s_keys[2 * MAX_MIR];
   __shared__ unsigned long long s_cnt[8];
-  float* s_grad = reinterpret_cast<float*>(smem + A.blob_bytes);
   const int tid = threadIdx.x, lane = tid & 31;
+  for (int i = tid; i < 2 * MAX_MIR; i += blockDim.x) s_keys[i] = 0u;
   if (tid < 8) s_cnt[tid] = 0ull;
-  if (tid == 0) s_fill = 0;
   if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;
   Blob B;
   B.bind(smem);
   const BlobHeader& H = *B.h;
   const unsigned lt_mask = (1u << lane) - 1u;
-  for (int i = tid; i < A.n_layers; i += blockDim.x) s_grad[i] = 0.f;
-  HitRec* hb = A.hit_buf + (long long)blockIdx.x * A.hit_cap;
-  double* grow = A.grad_cta + (long long)blockIdx.x * A.n_layers;
-  const int high_water = A.hit_cap - (int)blockDim.x * TAPE_HITS;
+  HitRec* hb = A.hit_buf;
+  const long long cap = A.hit_cap;
 
   int c_rays = 0, c_hits = 0, c_overflow = 0, c_tallied = 0, c_steps = 0;
-  long long c_asteps = 0;
   TapeE<F> tape[TAPE_HITS];
 
   for (;;) {
@@ -675,21 +665,16 @@ __global__ void __launch_bounds__(kBlock) k_trace_bwd(const TraceArgs A) {
     const bool nonempty = chunk_range(A, chunk, cell, r0, r1);
     if (tid == 0) s_next = (unsigned long long)r0;
     __syncthreads();
-    if (!nonempty) {
-      __syncthreads();
-      continue;
-    }
-    const ChunkConst cc = chunk_const(A, cell);
-    const double* Gc = A.G + cell * (long long)A.bins;
-    for (;;) {  // rounds within the chunk
+    if (nonempty) {
+      const ChunkConst cc = chunk_const(A, cell);
+      const double* Gc = A.G + cell * (long long)A.bins;
       Ray<F> R;
       bool has = false, at_mir = false, exhausted = false;
       int hit_k = 0;
       float2 seg_s = make_float2(1.f, 0.f), seg_p = make_float2(1.f, 0.f);
       for (;;) {
         for (;;) {
-          const bool paused = *(volatile int*)&s_fill > high_water;
-          const bool need = !has && !exhausted && !paused;
+          const bool need = !has && !exhausted;
           const unsigned fm = __ballot_sync(FULL, need);
           if (fm) {
             const int leader = __ffs(fm) - 1;
@@ -710,8 +695,7 @@ __global__ void __launch_bounds__(kBlock) k_trace_bwd(const TraceArgs A) {
             }
           }
           const bool adv = has && !at_mir;
-          const bool can_fetch = !has && !exhausted && !(*(volatile int*)&s_fill > high_water);
-          if (!__any_sync(FULL, adv || can_fetch)) break;
+          if (!__any_sync(FULL, adv || (!has && !exhausted))) break;
           int emit = 0;  // hits to emit for a ray that ended in the eyebox
           float g0 = 0.f;  // mantissa of G[bin] in [0.5, 1), exponent eG
           int eG = 0;
@@ -756,7 +740,7 @@ __global__ void __launch_bounds__(kBlock) k_trace_bwd(const TraceArgs A) {
               }
             }
           }
-          // warp-aggregated reservation of record slots
+          // warp-aggregated reservation of record slots in the global buffer
           int incl = emit;
 #pragma unroll
           for (int off = 1; off < 32; off <<= 1) {
@@ -765,48 +749,55 @@ __global__ void __launch_bounds__(kBlock) k_trace_bwd(const TraceArgs A) {
           }
           const int total = __shfl_sync(FULL, incl, 31);
           if (total) {
-            int base = 0;
-            if (lane == 31) base = atomicAdd(&s_fill, total);
+            unsigned long long base = 0;
+            if (lane == 31) base = atomicAdd(A.hit_count, (unsigned long long)total);
             base = __shfl_sync(FULL, base, 31);
             if (emit) {
-              // reverse Jones sweep over the tape
-              const float sc = g0 * (1.0f / F);
-              float2 ga[F], gb[F];
-#pragma unroll
-              for (int f = 0; f < F; ++f) {
-                ga[f] = cmulc(seg_s, cscale(R.a[f], sc * o.Ts));
-                gb[f] = cmulc(seg_p, cscale(R.b[f], sc * o.Tp));
-              }
-              const int first = base + incl - emit;
-              for (int h = emit - 1; h >= 0; --h) {
-                const TapeE<F>& T = tape[h];
-                float2 gs[F], gp[F];
-                float2 As = make_float2(0.f, 0.f), Ap = make_float2(0.f, 0.f);
-                const int k = T.kfw & 0xff;
-                const bool refl = ((T.kfw >> 9) & 1) == 0;  // bit 9: 0 = reflected (r), 1 = transmitted (t)
-                const float scl = refl ? B.mir[k].isw : B.mir[k].is1w;
+              const long long first = (long long)base + incl - emit;
+              if (first + emit > cap) {
+                // no room: drop this ray's gradient and mark its slots inside the buffer
+                for (long long h = first; h < first + emit && h < cap; ++h) hb[h].kfw = -1;
+                ++c_overflow;
+              } else {
+                // reverse Jones sweep over the tape
+                const float sc = g0 * (1.0f / F);
+                float2 ga[F], gb[F];
 #pragma unroll
                 for (int f = 0; f < F; ++f) {
-                  gs[f] = make_float2(fmaf(T.cpsi, ga[f].x, -T.spsi * gb[f].x), fmaf(T.cpsi, ga[f].y, -T.spsi * gb[f].y));
-                  gp[f] = make_float2(fmaf(T.spsi, ga[f].x, T.cpsi * gb[f].x), fmaf(T.spsi, ga[f].y, T.cpsi * gb[f].y));
-                  As = cadd(As, cmulc(gs[f], T.Es[f]));
-                  Ap = cadd(Ap, cmulc(gp[f], T.Ep[f]));
+                  ga[f] = cmulc(seg_s, cscale(R.a[f], sc * o.Ts));
+                  gb[f] = cmulc(seg_p, cscale(R.b[f], sc * o.Tp));
                 }
-                HitRec rec;
-                rec.kfw = T.kfw;
-                rec.cos0 = T.cos0;
-                rec.lam = cc.lam;
-                rec.eA = eG;
-                rec.As = cscale(As, scl);
-                rec.Ap = cscale(Ap, scl);
-                hb[first + h] = rec;
+                for (int h = emit - 1; h >= 0; --h) {
+                  const TapeE<F>& T = tape[h];
+                  float2 gs[F], gp[F];
+                  float2 As = make_float2(0.f, 0.f), Ap = make_float2(0.f, 0.f);
+                  const int k = T.kfw & 0xff;
+                  const bool refl = ((T.kfw >> 9) & 1) == 0;  // bit 9: 0 = reflected (r), 1 = transmitted (t)
+                  const float scl = refl ? B.mir[k].isw : B.mir[k].is1w;
 #pragma unroll
-                for (int f = 0; f < F; ++f) {
-                  const float2 xs = cmulc(T.cs, gs[f]), xp = cmulc(T.cp, gp[f]);
-                  const float2 ya = make_float2(fmaf(T.cphi, xs.x, -T.sphi * xp.x), fmaf(T.cphi, xs.y, -T.sphi * xp.y));
-                  const float2 yb = make_float2(fmaf(T.sphi, xs.x, T.cphi * xp.x), fmaf(T.sphi, xs.y, T.cphi * xp.y));
-                  ga[f] = cmulc(T.seg_s, ya);
-                  gb[f] = cmulc(T.seg_p, yb);
+                  for (int f = 0; f < F; ++f) {
+                    gs[f] = make_float2(fmaf(T.cpsi, ga[f].x, -T.spsi * gb[f].x), fmaf(T.cpsi, ga[f].y, -T.spsi * gb[f].y));
+                    gp[f] = make_float2(fmaf(T.spsi, ga[f].x, T.cpsi * gb[f].x), fmaf(T.spsi, ga[f].y, T.cpsi * gb[f].y));
+                    As = cadd(As, cmulc(gs[f], T.Es[f]));
+                    Ap = cadd(Ap, cmulc(gp[f], T.Ep[f]));
+                  }
+                  HitRec rec;
+                  rec.kfw = T.kfw;
+                  rec.cos0 = T.cos0;
+                  rec.lam = cc.lam;
+                  rec.eA = eG;
+                  rec.As = cscale(As, scl);
+                  rec.Ap = cscale(Ap, scl);
+                  hb[first + h] = rec;
+                  atomicAdd(&s_keys[((T.kfw & 0xff) << 1) | ((T.kfw >> 8) & 1)], 1u);  // stack (mirror, side)
+#pragma unroll
+                  for (int f = 0; f < F; ++f) {
+                    const float2 xs = cmulc(T.cs, gs[f]), xp = cmulc(T.cp, gp[f]);
+                    const float2 ya = make_float2(fmaf(T.cphi, xs.x, -T.sphi * xp.x), fmaf(T.cphi, xs.y, -T.sphi * xp.y));
+                    const float2 yb = make_float2(fmaf(T.sphi, xs.x, T.cphi * xp.x), fmaf(T.sphi, xs.y, T.cphi * xp.y));
+                    ga[f] = cmulc(T.seg_s, ya);
+                    gb[f] = cmulc(T.seg_p, yb);
+                  }
                 }
               }
             }
@@ -816,7 +807,7 @@ __global__ void __launch_bounds__(kBlock) k_trace_bwd(const TraceArgs A) {
         if (at_mir) {
           const int h = R.hits;
           float2 Es[F], Ep[F];
-          const MirrorStep ms = mirror_event<F>(R, hit_k, B, cc.lam, A, c_steps, Es, Ep);
+          const MirrorStep ms = mirror_event<F, P>(R, hit_k, B, cc.lam, A, c_steps, Es, Ep);
           if (h < TAPE_HITS) {
             TapeE<F>& T = tape[h];
             T.cs = ms.cs;
@@ -844,34 +835,6 @@ __global__ void __launch_bounds__(kBlock) k_trace_bwd(const TraceArgs A) {
           }
         }
       }
-      __syncthreads();
-      // ---- thin-film adjoint over this round's records ----
-      const int fill = s_fill;
-      for (int i = tid; i < fill; i += blockDim.x) {
-        const HitRec rec = hb[i];
-        const int k = rec.kfw & 0xff;
-        const bool front = (rec.kfw >> 8) & 1;
-        const int which = (rec.kfw >> 9) & 1;
-        const MirrorRec& M = B.mir[k];
-        MatTable mt;
-        mt.init(H, rec.cos0, rec.lam);
-        const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
-        GradSink sink{s_grad, A.counters + 8};
-        tmm_adjoint(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, rec.eA);
-        c_asteps += M.n_layers;
-      }
-      __syncthreads();
-      for (int i = tid; i < A.n_layers; i += blockDim.x) {
-        const float v = s_grad[i];
-        if (v != 0.f) {
-          grow[i] += (double)v;
-          s_grad[i] = 0.f;
-        }
-      }
-      if (tid == 0) s_fill = 0;
-      const bool done = s_next >= (unsigned long long)r1;
-      __syncthreads();
-      if (done) break;
     }
     __syncthreads();
   }
@@ -884,28 +847,184 @@ __global__ void __launch_bounds__(kBlock) k_trace_bwd(const TraceArgs A) {
   }
   const unsigned long long ov = warp_sum_u((unsigned long long)c_overflow);
   const unsigned long long tl = warp_sum_u((unsigned long long)c_tallied);
-  const unsigned long long as = warp_sum_u((unsigned long long)c_asteps);
   if (lane == 0) {
     if (ov) atomicAdd(&s_cnt[5], ov);
     if (tl) atomicAdd(&s_cnt[6], tl);
-    if (as) atomicAdd(&s_cnt[7], as);
   }
   __syncthreads();
-  if (tid < 8 && s_cnt[tid]) atomicAdd(A.counters + tid, s_cnt[tid]);
+  if (tid < 7 && s_cnt[tid]) atomicAdd(A.counters + tid, s_cnt[tid]);
+  for (int i = tid; i < 2 * MAX_MIR; i += blockDim.x)
+    if (s_keys[i]) atomicAdd(A.key_count + i, s_keys[i]);
 }
 
-// sum of the per-CTA FP64 rows, scattered to the design's layer order
-__global__ void k_reduce_grad(const double* grad_cta, int grid, int n_layers, const int* dev_to_orig, double* out) {
+// exclusive prefix of the per-stack record counts (one block)
+__global__ void k_bwd_scan(const unsigned int* key_count, unsigned int* key_off, unsigned int* key_cursor) {
+  __shared__ unsigned int s[2 * MAX_MIR];
+  const int t = threadIdx.x;
+  if (t < 2 * MAX_MIR) s[t] = key_count[t];
+  __syncthreads();
+  if (t == 0) {
+    unsigned int acc = 0;
+    for (int i = 0; i < 2 * MAX_MIR; ++i) {
+      const unsigned int c = s[i];
+      s[i] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+  if (t < 2 * MAX_MIR) {
+    key_off[t] = s[t];
+    key_cursor[t] = s[t];
+  }
+}
+
+__device__ __forceinline__ int rec_key(int kfw) { return ((kfw & 0xff) << 1) | ((kfw >> 8) & 1); }
+
+// Scatter into stack order. A block takes a tile of kScatterItems records per
+// thread, ranks them per stack in shared memory (warp-aggregated), reserves
+// one range per stack with a single global atomic, then writes.
+constexpr int kScatterItems = 8;
+__global__ void k_bwd_scatter(const HitRec* in, long long n, unsigned int* key_cursor, HitRec* out) {
+  __shared__ unsigned int s_cnt[2 * MAX_MIR], s_base[2 * MAX_MIR];
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int k = tid; k < 2 * MAX_MIR; k += blockDim.x) s_cnt[k] = 0u;
+  __syncthreads();
+  const long long tile = (long long)blockIdx.x * blockDim.x * kScatterItems;
+  HitRec r[kScatterItems];
+  int key[kScatterItems];
+  unsigned int rank[kScatterItems];
+#pragma unroll
+  for (int t = 0; t < kScatterItems; ++t) {
+    const long long i = tile + (long long)t * blockDim.x + tid;
+    key[t] = -1;
+    if (i < n) {
+      r[t] = in[i];
+      if (r[t].kfw >= 0) key[t] = rec_key(r[t].kfw);
+    }
+    const unsigned peers = __match_any_sync(FULL, key[t]);
+    const int leader = __ffs(peers) - 1;
+    unsigned int base = 0;
+    if (key[t] >= 0 && lane == leader) base = atomicAdd(&s_cnt[key[t]], (unsigned)__popc(peers));
+    base = __shfl_sync(FULL, base, leader);
+    rank[t] = base + __popc(peers & ((1u << lane) - 1u));
+  }
+  __syncthreads();
+  for (int k = tid; k < 2 * MAX_MIR; k += blockDim.x)
+    if (s_cnt[k]) s_base[k] = atomicAdd(key_cursor + k, s_cnt[k]);
+  __syncthreads();
+#pragma unroll
+  for (int t = 0; t < kScatterItems; ++t)
+    if (key[t] >= 0) out[s_base[key[t]] + rank[t]] = r[t];
+}
+
+struct LaneSink {
+  float* s_grad;
+  int* bad;
+  __device__ __forceinline__ void operator()(int idx, float g) const {
+    if (isfinite(g)) {
+      atomicAdd(s_grad + idx, g);
+    } else {
+      ++*bad;  // reported in wg_stats; never added
+    }
+  }
+};
+
+// all 32 lanes hold records of the same stack: same gradient entry per step
+struct WarpSink {
+  float* s_grad;
+  int* bad;
+  int lane;
+  __device__ __forceinline__ void operator()(int idx, float g) const {
+    if (!isfinite(g)) {
+      ++*bad;
+      g = 0.f;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) g += __shfl_xor_sync(FULL, g, o);
+    if (lane == 0) atomicAdd(s_grad + idx, g);
+  }
+};
+
+template <int P>
+__global__ void __launch_bounds__(kBlock) k_bwd_adjoint(const AdjArgs A) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ long long s_chunk;
+  __shared__ unsigned long long s_cnt[2];
+  float* s_grad = reinterpret_cast<float*>(smem + A.blob_bytes);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  if (tid < 2) s_cnt[tid] = 0ull;
+  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;
+  Blob B;
+  B.bind(smem);
+  const BlobHeader& H = *B.h;
+  for (int i = tid; i < A.n_layers; i += blockDim.x) s_grad[i] = 0.f;
+  long long c_steps = 0;
+  int bad = 0;
+  for (;;) {
+    if (tid == 0) s_chunk = (long long)atomicAdd(A.work, 1ull);
+    __syncthreads();
+    const long long base = s_chunk * (long long)A.rec_chunk;
+    if (base >= A.n_rec) break;
+    const long long end = min(base + (long long)A.rec_chunk, A.n_rec);
+    for (long long r0 = base + 32ll * warp; r0 < end; r0 += 32ll * nwarp) {
+      const long long i = r0 + lane;
+      const bool valid = i < end;
+      HitRec rec;
+      rec.kfw = -1;
+      if (valid) rec = A.recs[i];
+      const int key = valid ? rec_key(rec.kfw) : -1 - lane;
+      const int key0 = __shfl_sync(FULL, key, 0);
+      const bool uniform = __all_sync(FULL, key == key0);
+      if (valid) {
+        const int k = rec.kfw & 0xff;
+        const bool front = (rec.kfw >> 8) & 1;
+        const int which = (rec.kfw >> 9) & 1;
+        const MirrorRec& M = B.mir[k];
+        MatTable mt;
+        mt.init(H, rec.cos0, rec.lam);
+        const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+        if (uniform) {
+          WarpSink sink{s_grad, &bad, lane};
+          tmm_adjoint<P>(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, rec.eA);
+        } else {
+          LaneSink sink{s_grad, &bad};
+          tmm_adjoint<P>(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, rec.eA);
+        }
+        c_steps += M.n_layers;
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < A.n_layers; i += blockDim.x) {
+      const float v = s_grad[i];
+      if (v != 0.f) {
+        atomicAdd(A.grad_acc + i, (double)v);
+        s_grad[i] = 0.f;
+      }
+    }
+    __syncthreads();
+  }
+  const unsigned long long st = warp_sum_u((unsigned long long)c_steps);
+  const unsigned long long bd = warp_sum_u((unsigned long long)bad);
+  if (lane == 0) {
+    if (st) atomicAdd(&s_cnt[0], st);
+    if (bd) atomicAdd(&s_cnt[1], bd);
+  }
+  __syncthreads();
+  if (tid == 0 && s_cnt[0]) atomicAdd(A.counters + 7, s_cnt[0]);
+  if (tid == 1 && s_cnt[1]) atomicAdd(A.counters + 8, s_cnt[1]);
+}
+
+// FP64 per-layer sums -> the caller's gradient in design order
+__global__ void k_scatter_grad(const double* acc, int n_layers, const int* dev_to_orig, double* out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_layers) return;
-  double s = 0.0;
-  for (int b = 0; b < grid; ++b) s += grad_cta[(long long)b * n_layers + i];
-  out[dev_to_orig[i]] = s;
+  if (i < n_layers) out[dev_to_orig[i]] = acc[i];
 }
 
 // ---------------------------------------------------------------------------
 // K1: coating evaluation and its adjoint (test hooks, global-memory stack)
 // ---------------------------------------------------------------------------
+template <int P>
 __global__ void k_coating_eval(const uint8_t* blob, int mirror, int side, long long n, const float* cos0,
                                const float* lam, float* out) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -918,7 +1037,7 @@ __global__ void k_coating_eval(const uint8_t* blob, int mirror, int side, long l
   mt.init(H, cos0[i], lam[i]);
   const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
   int steps = 0;
-  const Coef c = tmm_forward(sv, side == 0, mt, H.n_slab, cos0[i], steps);
+  const Coef c = tmm_forward<P>(sv, side == 0, mt, H.n_slab, cos0[i], steps);
   float* o = out + i * 8;
   o[0] = c.rs.x;
   o[1] = c.rs.y;
@@ -940,6 +1059,7 @@ struct RowSink {
   }
 };
 
+template <int P>
 __global__ void k_coating_grad(const uint8_t* blob, int mirror, int side, long long n, const float* cos0,
                                const float* lam, const float* w, int which, float* grad) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -952,8 +1072,8 @@ __global__ void k_coating_grad(const uint8_t* blob, int mirror, int side, long l
   mt.init(H, cos0[i], lam[i]);
   const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
   RowSink sink{grad + i * M.n_layers, M.layer_off, M.n_layers, side == 0};
-  tmm_adjoint(sv, side == 0, mt, H.n_slab, cos0[i], make_float2(w[4 * i], w[4 * i + 1]),
-              make_float2(w[4 * i + 2], w[4 * i + 3]), which, sink);
+  tmm_adjoint<P>(sv, side == 0, mt, H.n_slab, cos0[i], make_float2(w[4 * i], w[4 * i + 1]),
+                 make_float2(w[4 * i + 2], w[4 * i + 3]), which, sink);
 }
 
 // ---------------------------------------------------------------------------
@@ -989,60 +1109,73 @@ static int occupancy(K kernel, size_t smem) {
   return n;
 }
 
-int trace_fwd_blocks_per_sm(int F, size_t smem) {
-  return F == 2 ? occupancy(k_trace_fwd<2>, smem) : occupancy(k_trace_fwd<1>, smem);
-}
-int trace_bwd_blocks_per_sm(int F, size_t smem) {
-  return F == 2 ? occupancy(k_trace_bwd<2>, smem) : occupancy(k_trace_bwd<1>, smem);
+// kernel instance for (fields F, material period P)
+#define WG_PICK_FP(K, F, P) \
+  ((F) == 2 ? ((P) == 3 ? K<2, 3> : (P) == 2 ? K<2, 2> : K<2, 0>) : ((P) == 3 ? K<1, 3> : (P) == 2 ? K<1, 2> : K<1, 0>))
+#define WG_PICK_P(K, P) ((P) == 3 ? K<3> : (P) == 2 ? K<2> : K<0>)
+
+int trace_fwd_blocks_per_sm(int F, int P, size_t smem) { return occupancy(WG_PICK_FP(k_trace_fwd, F, P), smem); }
+int bwd_replay_blocks_per_sm(int F, int P, size_t smem) { return occupancy(WG_PICK_FP(k_bwd_replay, F, P), smem); }
+int bwd_adjoint_blocks_per_sm(int P, size_t smem) { return occupancy(WG_PICK_P(k_bwd_adjoint, P), smem); }
+
+cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s) {
+  auto k = WG_PICK_FP(k_trace_fwd, F, P);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  note_launches(1);
+  k<<<grid, kBlock, smem, s>>>(a);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int grid, size_t smem, cudaStream_t s) {
-  if (F == 2) {
-    cudaFuncSetAttribute(k_trace_fwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s) {
+  auto k = WG_PICK_FP(k_bwd_replay, F, P);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  note_launches(1);
+  k<<<grid, kBlock, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_sort(const HitRec* in, long long n, unsigned int* key_count, unsigned int* key_off,
+                            unsigned int* key_cursor, HitRec* out, cudaStream_t s) {
+  note_launches(1);
+  k_bwd_scan<<<1, 2 * MAX_MIR, 0, s>>>(key_count, key_off, key_cursor);
+  if (n > 0) {
     note_launches(1);
-    k_trace_fwd<2><<<grid, kBlock, smem, s>>>(a);
-  } else {
-    cudaFuncSetAttribute(k_trace_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    note_launches(1);
-    k_trace_fwd<1><<<grid, kBlock, smem, s>>>(a);
+    const long long per_block = 256ll * kScatterItems;
+    k_bwd_scatter<<<(unsigned)((n + per_block - 1) / per_block), 256, 0, s>>>(in, n, key_cursor, out);
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_trace_bwd(const TraceArgs& a, int F, int grid, size_t smem, cudaStream_t s) {
-  if (F == 2) {
-    cudaFuncSetAttribute(k_trace_bwd<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    note_launches(1);
-    k_trace_bwd<2><<<grid, kBlock, smem, s>>>(a);
-  } else {
-    cudaFuncSetAttribute(k_trace_bwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    note_launches(1);
-    k_trace_bwd<1><<<grid, kBlock, smem, s>>>(a);
-  }
+cudaError_t launch_bwd_adjoint(const AdjArgs& a, int P, int grid, size_t smem, cudaStream_t s) {
+  auto k = WG_PICK_P(k_bwd_adjoint, P);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  note_launches(1);
+  k<<<grid, kBlock, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_grad(const double* grad_cta, int grid, int n_layers, const int* dev_to_orig, double* out,
-                               cudaStream_t s) {
+cudaError_t launch_scatter_grad(const double* acc, int n_layers, const int* dev_to_orig, double* out,
+                                cudaStream_t s) {
   if (n_layers == 0) return cudaSuccess;
   note_launches(1);
-  k_reduce_grad<<<(n_layers + 127) / 128, 128, 0, s>>>(grad_cta, grid, n_layers, dev_to_orig, out);
+  k_scatter_grad<<<(n_layers + 127) / 128, 128, 0, s>>>(acc, n_layers, dev_to_orig, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_coating_eval(const uint8_t* blob, int mirror, int side, long long n, const float* cos0,
+cudaError_t launch_coating_eval(const uint8_t* blob, int P, int mirror, int side, long long n, const float* cos0,
                                 const float* lam, float* out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   note_launches(1);
-  k_coating_eval<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(blob, mirror, side, n, cos0, lam, out);
+  WG_PICK_P(k_coating_eval, P)<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(blob, mirror, side, n, cos0, lam, out);
   return cudaGetLastError();
 }
 
-cudaError_t launch_coating_grad(const uint8_t* blob, int mirror, int side, long long n, const float* cos0,
+cudaError_t launch_coating_grad(const uint8_t* blob, int P, int mirror, int side, long long n, const float* cos0,
                                 const float* lam, const float* w, int which, float* grad, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   note_launches(1);
-  k_coating_grad<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(blob, mirror, side, n, cos0, lam, w, which, grad);
+  WG_PICK_P(k_coating_grad, P)<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(blob, mirror, side, n, cos0, lam, w,
+                                                                            which, grad);
   return cudaGetLastError();
 }
 
