@@ -221,7 +221,12 @@ static std::vector<uint8_t> build_blob(const wg_design& d) {
   h.half_w = 0.5f * d.width;
   h.x_end = d.x_end;
   h.eye_relief = d.eye_relief;
-  for (int i = 0; i < d.n_mat; ++i) h.mat_n[i] = d.mat_n[i];
+  for (int i = 0; i < d.n_mat; ++i) {
+    h.mat_n[i] = d.mat_n[i];
+    h.mat_inv_n[i] = (float)(1.0 / (double)d.mat_n[i]);
+    const double r = (double)d.n_slab / (double)d.mat_n[i];
+    h.mat_r2[i] = (float)(r * r);
+  }
   h.off_mir = (int)off_mir;
   h.off_d = (int)off_d;
   h.off_m = (int)off_m;
@@ -603,7 +608,7 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
   p.chunk_rays = default_chunk(p);
   p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
   p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
-  const size_t smem = (size_t)d->blob_bytes + sizeof(float) * p.bins;
+  const size_t smem = fwd_smem_bytes(d->blob_bytes, p.bins);
   if (smem > 200 * 1024) return fail(WG_EINVAL, "wg_trace_forward: design + eyebox too large for shared memory");
   cudaStream_t s = (cudaStream_t)cfg->stream;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -654,6 +659,7 @@ struct BwdScratch {
 };
 
 static const long long kRecordsPerRay = 16;  // record capacity per ray of a batch (mean ~2)
+static const long long kReplayUnit = 64;     // rays per work unit of the replay kernel
 
 extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, const double* dL_dtally,
                                        double* grad_thickness, double* grad_tilt, wg_stats* stats) {
@@ -662,7 +668,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   Plan p;
   wg_status st = make_plan(d, cfg, 2048, p);
   if (st != WG_OK) return st;
-  p.chunk_rays = default_chunk(p);
+  p.chunk_rays = kReplayUnit;  // the replay's warps claim ranges of this many rays
   const size_t smem_r = (size_t)d->blob_bytes;
   const size_t smem_a = (size_t)d->blob_bytes + sizeof(float) * std::max(1, d->n_dev);
   if (smem_a > 200 * 1024) return fail(WG_EINVAL, "wg_trace_backward: design too large for shared memory");
@@ -672,9 +678,9 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   WsLayout w;
   st = prepare_ws(c, d, cfg, p, s, w);
   if (st != WG_OK) return st;
-  // batches of whole chunks, large enough to fill the GPU several times
+  // batches of rays large enough to fill the GPU many times over
   const long long total = p.re - p.rb;
-  long long batch = std::min<long long>(total, std::max<long long>(p.chunk_rays * c->sm_count * 4, 1ll << 21));
+  long long batch = std::min<long long>(total, std::max<long long>(4096ll * c->sm_count * 4, 1ll << 21));
   const long long cap = batch * kRecordsPerRay;
   const size_t rec_bytes = (size_t)cap * hit_rec_bytes();
   const size_t need = 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + sizeof(double) * std::max(1, d->n_dev);
@@ -841,7 +847,7 @@ extern "C" wg_status wg_trace_forward_noalloc(wg_ctx* c, const wg_design* d, con
   p.chunk_rays = default_chunk(p);
   p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
   p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
-  const size_t smem = (size_t)d->blob_bytes + sizeof(float) * p.bins;
+  const size_t smem = fwd_smem_bytes(d->blob_bytes, p.bins);
   if (smem > 200 * 1024) return fail(WG_EINVAL, "wg_trace_forward_noalloc: design + eyebox too large for shared memory");
   const WsLayout need = ws_layout(nullptr, cfg, p.n_f);
   if (need.bytes > (size_t)WG_NOALLOC_SCRATCH_BYTES)

@@ -54,8 +54,14 @@ struct alignas(16) BlobHeader {
   float eye_relief, ic_nx, ic_nz, ic_cot; // input mirror normal (-sin a, cos a), cot a
   float mat_n[MAX_MAT];
   int off_mir, off_d, off_m, bytes;       // byte offsets, total size (multiple of 16)
+  // 1: inside the slab the input mirror, the mirror planes in index order and
+  // the end face are disjoint and ordered along x, so a ray between plane k-1
+  // and plane k can only meet one of those two next (set by k_prep_design)
+  int ordered, pad_[3];
+  float mat_inv_n[MAX_MAT];               // 1 / n
+  float mat_r2[MAX_MAT];                  // (n_slab / n)^2
 };
-static_assert(sizeof(BlobHeader) == 80, "header layout");
+static_assert(sizeof(BlobHeader) == 128, "header layout");
 
 struct alignas(16) MirrorRec {
   float nx, nz, c, omega;  // plane: nx x + nz z = c; reflection probability
@@ -145,10 +151,13 @@ struct MatK {
   int evan;
 };
 
-__device__ __forceinline__ MatK mat_const(float n0, float sin2_0, float n, float inv_lam) {
+// rad = 1 - (n0/n)^2 sin^2 t0 = cos^2 t with (n0/n)^2 rounded once from FP64.
+// cos t (which sets every layer's phase rate, and a long stack multiplies
+// the phase error by its length) is a correctly rounded square root, and the
+// quotients are IEEE except cos t / n = cos t * (1/n).
+__device__ __forceinline__ MatK mat_const(float sin2_0, float n, float inv_n, float r2, float inv_lam) {
   MatK k;
-  const float r = n0 / n;
-  const float rad = fmaf(-(r * r), sin2_0, 1.0f);
+  const float rad = fmaf(-r2, sin2_0, 1.0f);
   if (rad >= 0.0f) {
     const float ct = sqrtf(rad);
     const float eta = n * ct;
@@ -156,7 +165,7 @@ __device__ __forceinline__ MatK mat_const(float n0, float sin2_0, float n, float
     k.kap = TWO_PI * k.kt;
     k.q12s = 1.0f / eta;
     k.q21s = eta;
-    k.q12p = ct / n;
+    k.q12p = ct * inv_n;
     k.q21p = n / ct;
     k.evan = 0;
   } else {
@@ -166,7 +175,7 @@ __device__ __forceinline__ MatK mat_const(float n0, float sin2_0, float n, float
     k.kt = k.kap;
     k.q12s = 1.0f / na;
     k.q21s = -na;
-    k.q12p = -a / n;
+    k.q12p = -a * inv_n;
     k.q21p = n / a;
     k.evan = 1;
   }
@@ -180,7 +189,7 @@ struct MatTable {
     const float inv_lam = 1.0f / lam;
 #pragma unroll
     for (int i = 0; i < MAX_MAT; ++i)
-      if (i < h.n_mat) k[i] = mat_const(h.n_slab, sin2, h.mat_n[i], inv_lam);
+      if (i < h.n_mat) k[i] = mat_const(sin2, h.mat_n[i], h.mat_inv_n[i], h.mat_r2[i], inv_lam);
   }
   // register select by material id (no local-memory indexing)
   __device__ __forceinline__ MatK get(int m) const {
@@ -266,13 +275,24 @@ struct StackView {
   __device__ __forceinline__ int idx(bool front, int j) const { return front ? off + j : off + L - 1 - j; }
 };
 
+// 1 / b for |b| anywhere in the FP32 range: b is scaled by 1/max|b_i| first,
+// so |b|^2 cannot overflow (the transfer-matrix vectors reach ~2^70); the
+// reciprocals are the fast ones (operands far inside the normal range)
+__device__ __forceinline__ float2 crcp_s(float2 b) {
+  const float k = __fdividef(1.0f, fmaxf(fabsf(b.x), fabsf(b.y)));
+  const float2 s = make_float2(b.x * k, b.y * k);
+  const float inv = __fdividef(1.0f, fmaf(s.x, s.x, s.y * s.y)) * k;
+  return make_float2(s.x * inv, -s.y * inv);
+}
+
 // r = (eta0 B - C)/(eta0 B + C), t = 2 eta0/(eta0 B + C) (Macleod); the
 // scale 2^e of v cancels in r and multiplies t by 2^-e.
 __device__ __forceinline__ void coef_from_v(const CV& v, float eta0, int e, float2& r, float2& t) {
   const float2 den = make_float2(fmaf(eta0, v.xr, v.yr), fmaf(eta0, v.xi, v.yi));
   const float2 num = make_float2(fmaf(eta0, v.xr, -v.yr), fmaf(eta0, v.xi, -v.yi));
-  r = cdiv_s(num, den);
-  t = cscale(cdiv_s(make_float2(2.0f * eta0, 0.0f), den), pow2i(-e));
+  const float2 q = crcp_s(den);
+  r = cmul(num, q);
+  t = cscale(cscale(q, 2.0f * eta0), pow2i(-e));
 }
 
 // Segment length of the layer loops: a multiple of the stack's material
@@ -553,7 +573,13 @@ __device__ __forceinline__ void face_basis(V3 d, V3& s, V3& p) {
 
 // Nearest surface along (p, d), excluding `last`. Candidate order and ties
 // match the oracle: faces, input mirror, far end, sides, mirrors.
-__device__ __forceinline__ int next_surface(const Blob& B, V3 p, V3 d, int last, float& tmin) {
+// Nearest surface ahead of the ray (the surface it sits on excluded). With
+// reg >= 0 (an ordered design) the ray lies in region reg, between mirror
+// plane reg-1 (the input mirror for reg = 0) and mirror plane reg (the end
+// face for reg = K); every other plane is behind one of those two inside the
+// slab, so only they are tested. reg < 0 tests every plane. Distances use
+// the fast quotient (denominators are direction cosines, |x| <= 1).
+__device__ __forceinline__ int next_surface(const Blob& B, V3 p, V3 d, int last, int reg, float& tmin) {
   const BlobHeader& h = *B.h;
   float best = __int_as_float(0x7f800000);
   int id = -1;
@@ -563,23 +589,42 @@ __device__ __forceinline__ int next_surface(const Blob& B, V3 p, V3 d, int last,
       id = sid;
     }
   };
-  if (d.z < 0.0f) consider(S_BOT, -p.z / d.z);
-  if (d.z > 0.0f) consider(S_TOP, (h.thick - p.z) / d.z);
-  const float dn = fmaf(d.x, h.ic_nx, d.z * h.ic_nz);
-  if (dn > 0.0f) consider(S_LEFT, -fmaf(p.x, h.ic_nx, p.z * h.ic_nz) / dn);
-  if (d.x > 0.0f) consider(S_RIGHT, (h.x_end - p.x) / d.x);
+  if (d.z < 0.0f) consider(S_BOT, __fdividef(-p.z, d.z));
+  if (d.z > 0.0f) consider(S_TOP, __fdividef(h.thick - p.z, d.z));
   if (h.dims == 3) {
-    if (d.y > 0.0f) consider(S_YPOS, (h.half_w - p.y) / d.y);
-    if (d.y < 0.0f) consider(S_YNEG, (-h.half_w - p.y) / d.y);
+    if (d.y > 0.0f) consider(S_YPOS, __fdividef(h.half_w - p.y, d.y));
+    if (d.y < 0.0f) consider(S_YNEG, __fdividef(-h.half_w - p.y, d.y));
   }
-  for (int k = 0; k < h.n_mir; ++k) {
+  const int K = h.n_mir;
+  int k0 = 0, k1 = K;
+  bool left = true, right = true;
+  if (reg >= 0) {
+    k0 = max(reg - 1, 0);
+    k1 = min(reg + 1, K);
+    left = reg == 0;
+    right = reg == K;
+  }
+  if (left) {
+    const float dn = fmaf(d.x, h.ic_nx, d.z * h.ic_nz);
+    if (dn > 0.0f) consider(S_LEFT, __fdividef(-fmaf(p.x, h.ic_nx, p.z * h.ic_nz), dn));
+  }
+  if (right && d.x > 0.0f) consider(S_RIGHT, __fdividef(h.x_end - p.x, d.x));
+  for (int k = k0; k < k1; ++k) {
     const MirrorRec& m = B.mir[k];
     const float den = fmaf(d.x, m.nx, d.z * m.nz);
     if (den == 0.0f) continue;
-    consider(S_MIR + k, (m.c - fmaf(p.x, m.nx, p.z * m.nz)) / den);
+    consider(S_MIR + k, __fdividef(m.c - fmaf(p.x, m.nx, p.z * m.nz), den));
   }
   tmin = best;
   return id;
+}
+
+// region after leaving mirror plane k with direction d: the side of the
+// plane that d points to (k + 1 = larger x); -1 stays -1 (unordered design)
+__device__ __forceinline__ int region_after(const Blob& B, int reg, int k, V3 d) {
+  if (reg < 0) return reg;
+  const MirrorRec& m = B.mir[k];
+  return fmaf(d.x, m.nx, d.z * m.nz) * m.nx > 0.0f ? k + 1 : k;
 }
 
 // TIR at a slab face against air: r_s, r_p with u = n cos_i, a = sqrt(n^2 sin^2 - 1)
@@ -587,10 +632,10 @@ __device__ __forceinline__ int next_surface(const Blob& B, V3 p, V3 d, int last,
 __device__ __forceinline__ void tir_coef(float n, float ci, float sin2, float2& rs, float2& rp) {
   const float a = sqrtf(fmaxf(fmaf(n * n, sin2, -1.0f), 0.0f));
   const float u = n * ci;
-  const float iu = 1.0f / fmaf(u, u, a * a);
+  const float iu = __fdividef(1.0f, fmaf(u, u, a * a));
   rs = make_float2(fmaf(u, u, -a * a) * iu, 2.0f * u * a * iu);
   const float na = n * a;
-  const float ip = 1.0f / fmaf(ci, ci, na * na);
+  const float ip = __fdividef(1.0f, fmaf(ci, ci, na * na));
   rp = make_float2(fmaf(ci, ci, -na * na) * ip, 2.0f * ci * na * ip);
 }
 

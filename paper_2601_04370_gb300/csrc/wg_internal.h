@@ -57,6 +57,12 @@ struct AdjArgs {
 };
 
 constexpr int kBlock = 256;
+// the forward kernel keeps this many chunks (cells) in flight per CTA, each
+// with its own FP32 shared tally
+constexpr int kFwdSlots = 3;
+inline size_t fwd_smem_bytes(int blob_bytes, long long bins) {
+  return (size_t)blob_bytes + sizeof(float) * (size_t)kFwdSlots * (size_t)bins;
+}
 
 // number of kernels this library has launched (all launchers add to it)
 void note_launches(unsigned long long n);

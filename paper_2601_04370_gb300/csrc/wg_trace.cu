@@ -44,6 +44,14 @@ struct RayRec {
   int pad;
 };
 
+// device clock in ns (%globaltimer) and the limit of every bounded wait
+__device__ __forceinline__ unsigned long long gtimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+constexpr unsigned long long kWaitLimitNs = 500ull * 1000ull * 1000ull;  // 0.5 s
+
 // ---------------------------------------------------------------------------
 // Bulk (TMA) staging of the design blob into shared memory, mbarrier
 // completion with a bounded wait. Returns false (uniformly across the CTA)
@@ -68,12 +76,14 @@ __device__ bool stage_blob(uint8_t* s_dst, const uint8_t* g_src, int bytes, uint
     }
   }
   uint32_t done = 0;
+  const unsigned long long t_start = gtimer_ns();
   for (int it = 0; it < (1 << 22) && !done; ++it) {
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
         : "r"(bar), "r"(0)
         : "memory");
+    if (!done && gtimer_ns() - t_start > kWaitLimitNs) break;
   }
   const int ok = __syncthreads_and(done != 0);
   if (!ok && threadIdx.x == 0) atomicOr(err, 1u);
@@ -88,9 +98,8 @@ __global__ void k_prep_design(uint8_t* blob, const float* mir_x, const float* mi
                               int n_mir, float ic_tilt_deg, float thick) {
   BlobHeader* h = reinterpret_cast<BlobHeader*>(blob);
   MirrorRec* mir = reinterpret_cast<MirrorRec*>(blob + h->off_mir);
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const double deg = 3.14159265358979323846 / 180.0;
-  if (k < n_mir) {
+  for (int k = threadIdx.x; k < n_mir; k += blockDim.x) {
     const double a = (double)mir_tilt[k] * deg;
     const double nx = -sin(a), nz = cos(a);
     mir[k].nx = (float)nx;
@@ -101,11 +110,32 @@ __global__ void k_prep_design(uint8_t* blob, const float* mir_x, const float* mi
     mir[k].isw = (float)(1.0 / sqrt(w));
     mir[k].is1w = (float)(1.0 / sqrt(1.0 - w));
   }
-  if (k == 0) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
     const double a = (double)ic_tilt_deg * deg;
     h->ic_nx = (float)(-sin(a));
     h->ic_nz = (float)cos(a);
     h->ic_cot = (float)(cos(a) / sin(a));
+    // ordering of the planes along x on both faces (planes that are ordered
+    // on both faces do not cross inside the slab), with a 0.1 um margin
+    const double margin = 1e-4;
+    int ok = fabs((double)h->ic_nx) > 1e-3;
+    for (int f = 0; f < 2 && ok; ++f) {
+      const double z = f ? (double)thick : 0.0;
+      double prev = ok ? -(double)h->ic_nz * z / (double)h->ic_nx : 0.0;
+      for (int k = 0; k < n_mir && ok; ++k) {
+        const double nx = mir[k].nx, nz = mir[k].nz, c = mir[k].c;
+        if (fabs(nx) < 1e-3) {
+          ok = 0;
+          break;
+        }
+        const double x = (c - nz * z) / nx;
+        ok = x > prev + margin;
+        prev = x;
+      }
+      ok = ok && (double)h->x_end > prev + margin;
+    }
+    h->ordered = ok;
   }
 }
 
@@ -164,6 +194,7 @@ struct Ray {
   float2 a[F], b[F];  // field in the face s/p basis of d
   long long id;
   int ev, hits, last;
+  int reg;            // region between mirror planes (ordered designs), else -1
   uint32_t hash;
   uint4 rnd;
 };
@@ -203,6 +234,7 @@ __device__ __forceinline__ void gen_ray(Ray<F>& R, long long id, const ChunkCons
   R.ev = 0;
   R.hits = 0;
   R.last = S_LEFT;
+  R.reg = H.ordered ? 0 : -1;  // rays start on the input mirror, left of mirror 0
   R.hash = 2166136261u;
 }
 
@@ -366,6 +398,7 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
     R.b[f] = make_float2(fmaf(-st.spsi, Os.x, st.cpsi * Op.x), fmaf(-st.spsi, Os.y, st.cpsi * Op.y));
   }
   R.d = d2;
+  R.reg = region_after(B, R.reg, k, d2);
   R.hash = fnv(R.hash, (uint32_t)(S_MIR + k) | (st.refl ? 0x80u : 0u));
   R.hits = m + 1;
   return st;
@@ -412,27 +445,199 @@ __device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v) {
 }
 
 // ---------------------------------------------------------------------------
-// K2: forward Monte Carlo trace. Persistent CTAs claim chunks (one cell, a
-// range of rays) from a global queue; lanes pull rays from the chunk with a
-// warp-aggregated shared counter; a warp advances its rays through face
-// events until every live ray sits on a mirror, then runs the per-hit
-// transfer-matrix chain together. Exits are aggregated per warp (lanes with
-// the same bin) into a shared FP32 cell tally that is flushed to the FP64
-// global tally at the end of the chunk.
+// K2: forward Monte Carlo trace. Persistent CTAs; lanes pull rays from a
+// CTA-wide sequence that runs over the chunks (one cell, a range of rays)
+// the CTA has bound to its kSlots tally slots. A warp advances its rays
+// through face events until every live ray sits on a mirror, then runs the
+// per-hit transfer-matrix chain together. Exits are aggregated per warp
+// (lanes with the same slot and bin) into the slot's FP32 shared tally; the
+// warp that finishes a chunk's last ray flushes the slot to the FP64 global
+// tally and frees it for the CTA's next chunk. No CTA barrier separates
+// chunks, so lanes never idle at a chunk's tail while rays remain.
 // ---------------------------------------------------------------------------
+constexpr int kSlots = kFwdSlots;
+constexpr int kSizeBits = 20;  // chunk size field of SlotState::range
+
+struct SlotState {
+  unsigned long long range;  // (first virtual ray << kSizeBits) | rays: one word, read whole
+  long long cell, r0;
+  int j;                     // CTA-local chunk number bound to the slot
+  unsigned int done;         // rays of the chunk finished
+  ChunkConst cc;
+};
+
+struct FwdRing {
+  SlotState slot[kSlots];
+  unsigned long long vnext;  // next virtual ray handed out
+  unsigned long long ready;  // virtual rays of the chunks bound so far
+  int free_for[kSlots];      // the chunk number slot s takes next (set when its previous chunk is flushed)
+  int jready;                // chunks bound so far (under lock)
+  int lock, no_more;
+};
+
+template <class T>
+__device__ __forceinline__ T vload(const T& x) {
+  return *const_cast<const volatile T*>(&x);
+}
+template <class T>
+__device__ __forceinline__ void vstore(T& x, T v) {
+  *const_cast<volatile T*>(&x) = v;
+}
+
+// Bind the global queue's next chunks to free slots (one thread; returns
+// false at once if another thread holds the lock).
+__device__ bool ring_bind(FwdRing& S, const TraceArgs& A) {
+  if (atomicCAS(&S.lock, 0, 1) != 0) return false;
+  __threadfence_block();
+  bool made = false;
+  for (int it = 0; it < 2 * kSlots; ++it) {
+    const int j = S.jready;
+    const int s = j % kSlots;
+    // slot s takes chunk j only after chunk j - kSlots was flushed from it
+    if (vload(S.no_more) || vload(S.free_for[s]) != j) break;
+    const long long c = (long long)atomicAdd(A.work, 1ull);
+    if (c >= A.n_chunks) {
+      __threadfence_block();  // every bound chunk's `ready` before `no_more`
+      vstore(S.no_more, 1);
+      break;
+    }
+    long long cell, r0, r1;
+    const bool ne = chunk_range(A, c, cell, r0, r1);
+    S.jready = j + 1;
+    if (!ne) {  // nothing to trace: the slot stays free for the next chunk
+      vstore(S.free_for[s], j + kSlots);
+      continue;
+    }
+    SlotState& st = S.slot[s];
+    st.cell = cell;
+    st.r0 = r0;
+    st.j = j;
+    st.done = 0u;
+    st.cc = chunk_const(A, cell);
+    const unsigned long long v0 = S.ready;
+    __threadfence_block();
+    vstore(st.range, (v0 << kSizeBits) | (unsigned long long)(r1 - r0));
+    __threadfence_block();
+    vstore(S.ready, v0 + (unsigned long long)(r1 - r0));
+    made = true;
+  }
+  __threadfence_block();
+  atomicExch(&S.lock, 0);
+  return made;
+}
+
+// per-ray record of ray index i of the launch range (bounds-checked)
+__device__ __forceinline__ void put_rec(RayRec* recs, long long i, const TraceArgs& A, const RayRec& rr) {
+  if (i >= 0 && i < A.ray_end - A.ray_begin) {
+    recs[i] = rr;
+  } else {
+    atomicOr(A.error, 8u);
+  }
+}
+
+// true once the global queue is exhausted and every bound ray handed out.
+// Evaluated by lane 0 and broadcast: the shared words can change between two
+// lanes' reads, and a loop exit taken by only part of a warp would leave the
+// rest at a different full-warp intrinsic.
+__device__ __forceinline__ bool ring_drained(const FwdRing& S, int lane) {
+  int d = 0;
+  if (lane == 0 && vload(S.no_more)) {
+    __threadfence_block();
+    d = vload(S.vnext) >= vload(S.ready);
+  }
+  return __shfl_sync(FULL, d, 0) != 0;
+}
+// device clock read by lane 0, the same value in every lane
+__device__ __forceinline__ unsigned long long warp_time_ns() { return __shfl_sync(FULL, gtimer_ns(), 0); }
+
+// Up to n consecutive virtual rays for one warp (called by its leader).
+__device__ unsigned long long ring_fetch(FwdRing& S, const TraceArgs& A, int n, int& got) {
+  got = 0;
+  for (int tries = 0; tries < 8; ++tries) {
+    const unsigned long long old = vload(S.vnext);
+    const unsigned long long re = vload(S.ready);
+    if (re - old < 2ull * kBlock) ring_bind(S, A);  // keep a chunk bound ahead
+    if (old >= re) {
+      if (vload(S.ready) == re) return 0;
+      continue;
+    }
+    const int take = (int)min((unsigned long long)n, re - old);
+    if (atomicCAS(&S.vnext, old, old + (unsigned long long)take) == old) {
+      got = take;
+      return old;
+    }
+  }
+  return 0;
+}
+
+// Flush slot s (whole warp) and free it.
+__device__ void ring_flush(FwdRing& S, int s, float* s_tally, const TraceArgs& A, int lane) {
+  const SlotState& st = S.slot[s];
+  float* tl = s_tally + (long long)s * A.bins;
+  double* gt = A.tally + st.cell * (long long)A.bins;
+  for (int i = lane; i < A.bins; i += 32) {
+    const float v = tl[i];
+    if (v != 0.f) {
+      atomicAdd(gt + i, (double)v);
+      tl[i] = 0.f;
+    }
+  }
+  __syncwarp();
+  __threadfence_block();
+  if (lane == 0) vstore(S.free_for[s], st.j + kSlots);
+}
+
+// Count the warp's finished rays into their chunks; the warp that finishes
+// a chunk's last ray flushes its slot. The fence orders each warp's tally
+// adds before its counts, so a slot is flushed only after every add to it.
+__device__ __forceinline__ void ring_finish(FwdRing& S, bool fin, int slot, float* s_tally, const TraceArgs& A,
+                                            int lane) {
+  if (!__any_sync(FULL, fin)) return;
+  __threadfence_block();
+  __syncwarp();  // every lane's tally adds ordered before the counts below
+  const int key = fin ? slot : -1 - lane;
+  const unsigned peers = __match_any_sync(FULL, key);
+  bool complete = false;
+  if (fin && lane == __ffs(peers) - 1) {
+    const unsigned c = __popc(peers);
+    const unsigned old = atomicAdd(&S.slot[slot].done, c);
+    complete = old + c == (unsigned)(vload(S.slot[slot].range) & ((1ull << kSizeBits) - 1ull));
+  }
+  unsigned cm = __ballot_sync(FULL, complete);
+  while (cm) {
+    const int src = __ffs(cm) - 1;
+    cm &= cm - 1;
+    const int s = __shfl_sync(FULL, slot, src);
+    __syncwarp();
+    __threadfence_block();
+    ring_flush(S, s, s_tally, A, lane);
+  }
+}
+
 template <int F, int P>
 __global__ void __launch_bounds__(kBlock, 2) k_trace_fwd(const TraceArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_mbar;
-  __shared__ unsigned long long s_next;
-  __shared__ long long s_chunk;
+  __shared__ FwdRing S;
   __shared__ float s_led[6];
   __shared__ unsigned long long s_cnt[8];
   float* s_tally = reinterpret_cast<float*>(smem + A.blob_bytes);
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid < 6) s_led[tid] = 0.f;
   if (tid < 8) s_cnt[tid] = 0ull;
-  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;
+  if (tid < kSlots) {
+    S.free_for[tid] = tid;
+    S.slot[tid].range = 0ull;
+  }
+  if (tid == 0) {
+    S.vnext = 0ull;
+    S.ready = 0ull;
+    S.jready = 0;
+    S.lock = 0;
+    S.no_more = 0;
+  }
+  for (int i = tid; i < kSlots * A.bins; i += blockDim.x) s_tally[i] = 0.f;
+  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;  // includes a CTA barrier
   Blob B;
   B.bind(smem);
   const BlobHeader& H = *B.h;
@@ -442,154 +647,188 @@ __global__ void __launch_bounds__(kBlock, 2) k_trace_fwd(const TraceArgs A) {
   int c_rays = 0, c_hits = 0, c_events = 0, c_tir = 0, c_steps = 0;
   RayRec* recs = reinterpret_cast<RayRec*>(A.records);
 
+  Ray<F> R;
+  bool has = false, at_mir = false;
+  int hit_k = 0, slot = 0;
+  float lam = 0.f;
+  unsigned idle = 0;  // consecutive passes without work (0xffffffff: stop)
+  unsigned long long idle_t0 = 0;
+  // safety net: a warp needs at most ~2 loop passes per event of each ray it
+  // traces (plus bounded idle waits); past this cap it flags and stops
+  const unsigned long long it_cap =
+      4ull * (unsigned long long)A.max_events *
+          (unsigned long long)((A.ray_end - A.ray_begin) / ((long long)gridDim.x * (kBlock / 32)) + 256) +
+      (1ull << 24);
+  unsigned long long iters = 0;
   for (;;) {
-    if (tid == 0) s_chunk = (long long)atomicAdd(A.work, 1ull);
-    for (int i = tid; i < A.bins; i += blockDim.x) s_tally[i] = 0.f;
-    __syncthreads();
-    const long long chunk = s_chunk;
-    if (chunk >= A.n_chunks) break;
-    long long cell, r0, r1;
-    const bool nonempty = chunk_range(A, chunk, cell, r0, r1);
-    if (tid == 0) s_next = (unsigned long long)r0;
-    __syncthreads();
-    if (nonempty) {
-      const ChunkConst cc = chunk_const(A, cell);
-      Ray<F> R;
-      bool has = false, at_mir = false, exhausted = false;
-      int hit_k = 0;
-      for (;;) {
-        // ---- phase A: fetch rays, advance through face events ----
-        for (;;) {
-          const bool need = !has && !exhausted;
-          const unsigned fm = __ballot_sync(FULL, need);
-          if (fm) {
-            const int leader = __ffs(fm) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(&s_next, (unsigned long long)__popc(fm));
-            base = __shfl_sync(FULL, base, leader);
-            if (need) {
-              const long long id = (long long)base + __popc(fm & lt_mask);
-              if (id < r1) {
-                gen_ray(R, id, cc, H, A);
-                has = true;
-                ++c_rays;
-              } else {
-                exhausted = true;
-              }
-            }
+    // ---- phase A: fetch rays, advance through face events ----
+    for (;;) {
+      if (++iters > it_cap) {
+        if (lane == 0) atomicOr(A.error, 16u);
+        idle = 0xffffffffu;
+        break;
+      }
+      const unsigned fm = __ballot_sync(FULL, !has);
+      bool fetched = false;
+      if (fm) {
+        const int leader = __ffs(fm) - 1;
+        unsigned long long base = 0;
+        int got = 0;
+        if (lane == leader) base = ring_fetch(S, A, __popc(fm), got);
+        base = __shfl_sync(FULL, base, leader);
+        got = __shfl_sync(FULL, got, leader);
+        __threadfence_block();
+        const int rank = __popc(fm & lt_mask);
+        if (!has && rank < got) {
+          const unsigned long long v = base + (unsigned long long)rank;
+          int sl = -1;
+#pragma unroll
+          for (int s = 0; s < kSlots; ++s) {
+            const unsigned long long r = vload(S.slot[s].range);
+            const unsigned long long v0 = r >> kSizeBits;
+            if (v >= v0 && v < v0 + (r & ((1ull << kSizeBits) - 1ull))) sl = s;
           }
-          const bool adv = has && !at_mir;
-          if (!__any_sync(FULL, adv || (!has && !exhausted))) break;
-          int pend_bin = -1;
-          float pend_I = 0.f;
-          if (adv) {
-            float t;
-            const int sid = next_surface(B, R.p, R.d, R.last, t);
-            ++R.ev;
-            Outcome o;
-            o.term = 0;
-            if (sid < 0) {
-              o.term = 1;
-              o.cat = L_ABSORBED;
-              o.bin = -1;
-              o.I = 0.f;
-              o.w = ray_weight(R);
-            } else {
-              R.p = v3(fmaf(t, R.d.x, R.p.x), fmaf(t, R.d.y, R.p.y), fmaf(t, R.d.z, R.p.z));
-              R.last = sid;
-              if (sid >= S_MIR) {
-                at_mir = true;
-                hit_k = sid - S_MIR;
-              } else {
-                o = face_event<F>(R, sid, H, A, nullptr, nullptr, c_tir);
-              }
-            }
-            if (!o.term && !at_mir && R.ev >= A.max_events) {
-              o.term = 1;
-              o.cat = L_TRUNCATED;
-              o.bin = -1;
-              o.I = 0.f;
-              o.w = ray_weight(R);
-            }
-            if (o.term) {
-              has = false;
-              c_events += R.ev;
-              c_hits += R.hits;
-              if (o.cat == L_EYEBOX) {
-                led[L_EYEBOX] += o.I;
-                led[L_EXIT_REFL] += o.w - o.I;
-                pend_bin = o.bin;
-                pend_I = o.I;
-              } else if (o.cat == L_MISSED) {
-                led[L_MISSED] += o.I;
-                led[L_EXIT_REFL] += o.w - o.I;
-              } else {
-                led[o.cat] += o.w;
-              }
-              if (recs) {
-                RayRec rr;
-                rr.hash = R.hash;
-                rr.n_events = R.ev;
-                rr.n_hits = R.hits;
-                rr.cat = o.cat;
-                rr.bin = o.cat == L_EYEBOX ? (int)(cell * A.bins + o.bin) : -1;
-                rr.I = o.cat == L_EYEBOX ? o.I : 0.f;
-                rr.w = o.w;
-                rr.pad = 0;
-                recs[R.id - A.ray_begin] = rr;
-              }
-            }
-          }
-          // ---- per-warp aggregation of exits, then the block tally ----
-          const unsigned pm = __ballot_sync(FULL, pend_bin >= 0);
-          if (pm) {
-            const int key = pend_bin >= 0 ? pend_bin : -1 - lane;
-            const unsigned peers = __match_any_sync(FULL, key);
-            if (pend_bin >= 0) {
-              float sum = 0.f;
-              for (unsigned mm = peers; mm; mm &= mm - 1) sum += __shfl_sync(peers, pend_I, __ffs(mm) - 1);
-              if (lane == __ffs(peers) - 1) atomicAdd(&s_tally[pend_bin], sum);
-            }
+          if (sl < 0) {
+            atomicOr(A.error, 4u);  // a handed-out ray outside every bound chunk: never traced
+          } else {
+            slot = sl;
+            const SlotState& st = S.slot[slot];
+            const ChunkConst cc = st.cc;
+            lam = cc.lam;
+            gen_ray(R, st.r0 + (long long)(v - (st.range >> kSizeBits)), cc, H, A);
+            has = true;
+            ++c_rays;
           }
         }
-        // ---- phase B: per-hit transfer-matrix chain, all rays on mirrors ----
-        if (!__any_sync(FULL, at_mir)) break;
-        if (at_mir) {
-          mirror_event<F, P>(R, hit_k, B, cc.lam, A, c_steps, nullptr, nullptr);
-          at_mir = false;
-          if (R.ev >= A.max_events) {
-            has = false;
-            c_events += R.ev;
-            c_hits += R.hits;
-            const float w = ray_weight(R);
-            led[L_TRUNCATED] += w;
-            if (recs) {
-              RayRec rr;
-              rr.hash = R.hash;
-              rr.n_events = R.ev;
-              rr.n_hits = R.hits;
-              rr.cat = L_TRUNCATED;
-              rr.bin = -1;
-              rr.I = 0.f;
-              rr.w = w;
-              rr.pad = 0;
-              recs[R.id - A.ray_begin] = rr;
-            }
+        fetched = got > 0;
+      }
+      const bool adv = has && !at_mir;
+      if (!__any_sync(FULL, adv)) {
+        if (__any_sync(FULL, has) || fetched) break;
+        // nothing in this warp: done when every chunk is bound and handed out
+        if (ring_drained(S, lane)) break;
+        __nanosleep(256);
+        const unsigned long long now = warp_time_ns();
+        if (idle == 0) idle_t0 = now;
+        ++idle;
+        if (now - idle_t0 > kWaitLimitNs) {  // no work for 0.5 s: give up and flag
+          if (lane == 0) atomicOr(A.error, 2u);
+          idle = 0xffffffffu;
+          break;
+        }
+        continue;
+      }
+      idle = 0;
+      int pend_bin = -1;
+      float pend_I = 0.f;
+      bool fin = false;
+      if (adv) {
+        float t;
+        const int sid = next_surface(B, R.p, R.d, R.last, R.reg, t);
+        ++R.ev;
+        Outcome o;
+        o.term = 0;
+        if (sid < 0) {
+          o.term = 1;
+          o.cat = L_ABSORBED;
+          o.bin = -1;
+          o.I = 0.f;
+          o.w = ray_weight(R);
+        } else {
+          R.p = v3(fmaf(t, R.d.x, R.p.x), fmaf(t, R.d.y, R.p.y), fmaf(t, R.d.z, R.p.z));
+          R.last = sid;
+          if (sid >= S_MIR) {
+            at_mir = true;
+            hit_k = sid - S_MIR;
+          } else {
+            o = face_event<F>(R, sid, H, A, nullptr, nullptr, c_tir);
+          }
+        }
+        if (!o.term && !at_mir && R.ev >= A.max_events) {
+          o.term = 1;
+          o.cat = L_TRUNCATED;
+          o.bin = -1;
+          o.I = 0.f;
+          o.w = ray_weight(R);
+        }
+        if (o.term) {
+          has = false;
+          fin = true;
+          c_events += R.ev;
+          c_hits += R.hits;
+          if (o.cat == L_EYEBOX) {
+            led[L_EYEBOX] += o.I;
+            led[L_EXIT_REFL] += o.w - o.I;
+            pend_bin = o.bin;
+            pend_I = o.I;
+          } else if (o.cat == L_MISSED) {
+            led[L_MISSED] += o.I;
+            led[L_EXIT_REFL] += o.w - o.I;
+          } else {
+            led[o.cat] += o.w;
+          }
+          if (recs) {
+            RayRec rr;
+            rr.hash = R.hash;
+            rr.n_events = R.ev;
+            rr.n_hits = R.hits;
+            rr.cat = o.cat;
+            rr.bin = o.cat == L_EYEBOX ? (int)(S.slot[slot].cell * A.bins + o.bin) : -1;
+            rr.I = o.cat == L_EYEBOX ? o.I : 0.f;
+            rr.w = o.w;
+            rr.pad = 0;
+            put_rec(recs, R.id - A.ray_begin, A, rr);
           }
         }
       }
+      // ---- per-warp aggregation of exits into the slot tallies ----
+      const unsigned pm = __ballot_sync(FULL, pend_bin >= 0);
+      if (pm) {
+        const int key = pend_bin >= 0 ? slot * A.bins + pend_bin : -1 - lane;
+        const unsigned peers = __match_any_sync(FULL, key);
+        if (pend_bin >= 0) {
+          float sum = 0.f;
+          for (unsigned mm = peers; mm; mm &= mm - 1) sum += __shfl_sync(peers, pend_I, __ffs(mm) - 1);
+          if (lane == __ffs(peers) - 1) atomicAdd(&s_tally[key], sum);
+        }
+      }
+      ring_finish(S, fin, slot, s_tally, A, lane);
     }
-    __syncthreads();
-    if (nonempty) {
-      double* gt = A.tally + cell * (long long)A.bins;
-      for (int i = tid; i < A.bins; i += blockDim.x) {
-        const float v = s_tally[i];
-        if (v != 0.f) atomicAdd(gt + i, (double)v);
+    // ---- phase B: per-hit transfer-matrix chain, all rays on mirrors ----
+    if (!__any_sync(FULL, at_mir)) {
+      if (!__any_sync(FULL, has) && ring_drained(S, lane)) break;
+      if (idle == 0xffffffffu) break;
+      continue;
+    }
+    bool fin = false;
+    if (at_mir) {
+      mirror_event<F, P>(R, hit_k, B, lam, A, c_steps, nullptr, nullptr);
+      at_mir = false;
+      if (R.ev >= A.max_events) {
+        has = false;
+        fin = true;
+        c_events += R.ev;
+        c_hits += R.hits;
+        const float w = ray_weight(R);
+        led[L_TRUNCATED] += w;
+        if (recs) {
+          RayRec rr;
+          rr.hash = R.hash;
+          rr.n_events = R.ev;
+          rr.n_hits = R.hits;
+          rr.cat = L_TRUNCATED;
+          rr.bin = -1;
+          rr.I = 0.f;
+          rr.w = w;
+          rr.pad = 0;
+          put_rec(recs, R.id - A.ray_begin, A, rr);
+        }
       }
     }
-    __syncthreads();
+    ring_finish(S, fin, slot, s_tally, A, lane);
   }
   // ---- statistics ----
+  __syncthreads();
 #pragma unroll
   for (int i = 0; i < 6; ++i) {
     const float v = warp_sum(led[i]);
@@ -617,6 +856,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_trace_fwd(const TraceArgs A) {
 //   ray that ends in the eyebox seeds dL/dE* = G[bin]/F (T_s a, T_p b),
 //   walks its tape backwards and emits one record per hit: the weights A of
 //   f = 2 Re(A_s c_s + A_p c_p) (dL/dc of that hit's raw coefficients).
+//   Each warp claims short ray ranges of one cell from the global queue and
+//   its lanes keep their own cell, so no CTA barrier separates ranges.
 // k_bwd_scan + k_bwd_scatter: counting sort of the records by stack
 //   (mirror, side), so a warp's 32 records share one stack.
 // k_bwd_adjoint: one record per lane, checkpointed thin-film adjoint; when
@@ -638,8 +879,6 @@ template <int F, int P>
 __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_mbar;
-  __shared__ unsigned long long s_next;
-  __shared__ long long s_chunk;
   __shared__ unsigned int s_keys[2 * MAX_MIR];
   __shared__ unsigned long long s_cnt[8];
   const int tid = threadIdx.x, lane = tid & 31;
@@ -656,46 +895,54 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
   int c_rays = 0, c_hits = 0, c_overflow = 0, c_tallied = 0, c_steps = 0;
   TapeE<F> tape[TAPE_HITS];
 
+  // warp-private work unit (a short ray range of one cell, warp-uniform)
+  long long u_cell = 0, u_next = 0, u_end = 0;
+  bool u_more = true;
+  ChunkConst ucc;
+  ucc.lam = 0.f;
+  Ray<F> R;
+  bool has = false, at_mir = false;
+  int hit_k = 0;
+  long long cell_l = 0;  // cell and wavelength of this lane's ray
+  float lam_l = 0.f;
+  float2 seg_s = make_float2(1.f, 0.f), seg_p = make_float2(1.f, 0.f);
   for (;;) {
-    if (tid == 0) s_chunk = (long long)atomicAdd(A.work, 1ull);
-    __syncthreads();
-    const long long chunk = s_chunk;
-    if (chunk >= A.n_chunks) break;
-    long long cell, r0, r1;
-    const bool nonempty = chunk_range(A, chunk, cell, r0, r1);
-    if (tid == 0) s_next = (unsigned long long)r0;
-    __syncthreads();
-    if (nonempty) {
-      const ChunkConst cc = chunk_const(A, cell);
-      const double* Gc = A.G + cell * (long long)A.bins;
-      Ray<F> R;
-      bool has = false, at_mir = false, exhausted = false;
-      int hit_k = 0;
-      float2 seg_s = make_float2(1.f, 0.f), seg_p = make_float2(1.f, 0.f);
-      for (;;) {
         for (;;) {
-          const bool need = !has && !exhausted;
-          const unsigned fm = __ballot_sync(FULL, need);
-          if (fm) {
-            const int leader = __ffs(fm) - 1;
-            unsigned long long base = 0;
-            if (lane == leader) base = atomicAdd(&s_next, (unsigned long long)__popc(fm));
-            base = __shfl_sync(FULL, base, leader);
-            if (need) {
-              const long long id = (long long)base + __popc(fm & lt_mask);
-              if (id < r1) {
-                gen_ray(R, id, cc, H, A);
-                has = true;
-                seg_s = make_float2(1.f, 0.f);
-                seg_p = make_float2(1.f, 0.f);
-                ++c_rays;
-              } else {
-                exhausted = true;
+          // lanes without a ray take the next rays of the warp's unit; the
+          // warp claims units from the global queue as they run out
+          unsigned fm = __ballot_sync(FULL, !has);
+          while (fm && u_more) {
+            if (u_next >= u_end) {
+              long long c = 0;
+              if (lane == 0) c = (long long)atomicAdd(A.work, 1ull);
+              c = __shfl_sync(FULL, c, 0);
+              if (c >= A.n_chunks) {
+                u_more = false;
+                break;
               }
+              long long cell, r0, r1;
+              if (!chunk_range(A, c, cell, r0, r1)) continue;
+              u_cell = cell;
+              u_next = r0;
+              u_end = r1;
+              ucc = chunk_const(A, cell);
             }
+            const int take = (int)min((long long)__popc(fm), u_end - u_next);
+            const int rank = __popc(fm & lt_mask);
+            if (!has && rank < take) {
+              gen_ray(R, u_next + rank, ucc, H, A);
+              has = true;
+              cell_l = u_cell;
+              lam_l = ucc.lam;
+              seg_s = make_float2(1.f, 0.f);
+              seg_p = make_float2(1.f, 0.f);
+              ++c_rays;
+            }
+            u_next += take;
+            fm = __ballot_sync(FULL, !has);
           }
           const bool adv = has && !at_mir;
-          if (!__any_sync(FULL, adv || (!has && !exhausted))) break;
+          if (!__any_sync(FULL, adv)) break;
           int emit = 0;  // hits to emit for a ray that ended in the eyebox
           float g0 = 0.f;  // mantissa of G[bin] in [0.5, 1), exponent eG
           int eG = 0;
@@ -703,7 +950,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
           o.term = 0;
           if (adv) {
             float t;
-            const int sid = next_surface(B, R.p, R.d, R.last, t);
+            const int sid = next_surface(B, R.p, R.d, R.last, R.reg, t);
             ++R.ev;
             if (sid < 0) {
               o.term = 1;
@@ -727,7 +974,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
               has = false;
               c_hits += R.hits;
               if (o.cat == L_EYEBOX) {
-                const double g = Gc[o.bin];
+                const double g = A.G[cell_l * A.bins + o.bin];
                 if (g != 0.0) {
                   if (R.hits <= TAPE_HITS) {
                     emit = R.hits;
@@ -784,7 +1031,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                   HitRec rec;
                   rec.kfw = T.kfw;
                   rec.cos0 = T.cos0;
-                  rec.lam = cc.lam;
+                  rec.lam = lam_l;
                   rec.eA = eG;
                   rec.As = cscale(As, scl);
                   rec.Ap = cscale(Ap, scl);
@@ -803,11 +1050,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
             }
           }
         }
-        if (!__any_sync(FULL, at_mir)) break;
+        if (!__any_sync(FULL, at_mir)) break;  // no ray left in this warp and no unit to claim
         if (at_mir) {
           const int h = R.hits;
           float2 Es[F], Ep[F];
-          const MirrorStep ms = mirror_event<F, P>(R, hit_k, B, cc.lam, A, c_steps, Es, Ep);
+          const MirrorStep ms = mirror_event<F, P>(R, hit_k, B, lam_l, A, c_steps, Es, Ep);
           if (h < TAPE_HITS) {
             TapeE<F>& T = tape[h];
             T.cs = ms.cs;
@@ -834,10 +1081,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
             c_hits += R.hits;
           }
         }
-      }
-    }
-    __syncthreads();
   }
+  __syncthreads();
   const unsigned long long cv[5] = {(unsigned long long)c_rays, (unsigned long long)c_hits, 0ull, 0ull,
                                     (unsigned long long)c_steps};
 #pragma unroll
@@ -1082,7 +1327,7 @@ __global__ void k_coating_grad(const uint8_t* blob, int mirror, int side, long l
 cudaError_t launch_prep_design(uint8_t* blob, const float* mir_x, const float* mir_tilt, const float* mir_omega,
                                int n_mir, float ic_tilt_deg, float thick, cudaStream_t s) {
   note_launches(1);
-  k_prep_design<<<(n_mir + 63) / 64, 64, 0, s>>>(blob, mir_x, mir_tilt, mir_omega, n_mir, ic_tilt_deg, thick);
+  k_prep_design<<<1, 64, 0, s>>>(blob, mir_x, mir_tilt, mir_omega, n_mir, ic_tilt_deg, thick);
   return cudaGetLastError();
 }
 
