@@ -57,6 +57,17 @@ typedef int32_t wg_status;
 #define WG_POL_S 2
 #define WG_POL_P 3
 
+/* wg_trace_cfg.flags. By default wg_trace_forward also lists, in device
+ * memory owned by the design (16 bytes per traced ray), the rays that ended
+ * in the eyebox with their tally bin, tagged with the configuration and the
+ * mirror geometry it traced. Ray paths do not depend on layer thicknesses
+ * (Methods, Monte Carlo sampling: decisions depend only on the keys and the
+ * geometry), so a later wg_trace_backward with the same configuration and
+ * geometry, whatever the thicknesses, replays only the listed rays whose bin
+ * has a non-zero dL/dtally; every other ray contributes no gradient. Any
+ * other backward call replays every ray. */
+#define WG_TRACE_NO_EXIT_LIST 1  /* forward: do not record the list */
+
 /* energy ledger slots (wg_stats.ledger) */
 #define WG_LEDGER_EYEBOX 0     /* tallied intensity */
 #define WG_LEDGER_MISSED 1     /* left through the eye-side face outside the eyebox */
@@ -122,7 +133,7 @@ typedef struct wg_trace_cfg {
   uint64_t seed;
   int32_t max_events;         /* surface events per ray, <= WG_MAX_EVENTS */
   int32_t eb_nx, eb_ny;       /* eyebox bins (2D: eb_ny = 1) */
-  int32_t flags;              /* reserved, 0 */
+  int32_t flags;              /* WG_TRACE_* bits, 0 = defaults */
   float pupil_y_mm;           /* 3D: lateral extent of the launch region */
   float eb_cx_mm, eb_cy_mm, eb_w_mm, eb_h_mm;  /* eyebox centre and size */
   void* stream;               /* cudaStream_t or NULL */

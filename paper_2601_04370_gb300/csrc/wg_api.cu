@@ -94,6 +94,11 @@ struct wg_design {
   int* d_dev_to_orig = nullptr;
   float* d_stage = nullptr;    // [n_orig] thickness staging for set_params
   int period = 0;              // material period shared by all stacks (0, 2 or 3)
+  int geom_version = 0;        // bumped whenever the mirror geometry (tilts) changes
+  // eyebox rays of the last listing forward trace: count (u64) | ExitRec[],
+  // valid for the configuration and geometry with fingerprint exit_fp (0: none)
+  DevBuf exits;
+  uint64_t exit_fp = 0;
 };
 
 static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -144,6 +149,8 @@ static void destroy_design_dev(wg_design* d) {
   if (d->d_orig_to_dev) cudaFree(d->d_orig_to_dev);
   if (d->d_dev_to_orig) cudaFree(d->d_dev_to_orig);
   if (d->d_stage) cudaFree(d->d_stage);
+  d->exits.release();
+  d->exit_fp = 0;
   d->blob = nullptr;
 }
 
@@ -387,6 +394,8 @@ extern "C" wg_status wg_set_params(wg_design* d, const float* thickness_nm, int6
       if (!std::isfinite(tilt_deg[k]) || !(std::fabs(tilt_deg[k]) < 89.0f))
         return fail(WG_EINVAL, "wg_set_params: tilt %d invalid", k);
     d->mir_tilt.assign(tilt_deg, tilt_deg + d->K);
+    ++d->geom_version;  // ray paths change with the geometry: the eyebox-ray list is stale
+    d->exit_fp = 0;
     CU(cudaMemcpyAsync(d->d_mir + d->K, tilt_deg, sizeof(float) * d->K, cudaMemcpyHostToDevice, s));
     CU(launch_prep_design(d->blob, d->d_mir, d->d_mir + d->K, d->d_mir + 2 * d->K, d->K, d->ic_tilt, d->thick, s));
   }
@@ -456,7 +465,7 @@ static wg_status validate_cfg(const wg_design* d, const wg_trace_cfg* cfg) {
     if (!(std::fabs(cfg->field_x_deg[i]) < 80.0f)) return fail(WG_EINVAL, "cfg: field_x %d invalid", i);
   for (int i = 0; i < cfg->n_fy; ++i)
     if (!(std::fabs(cfg->field_y_deg[i]) < 80.0f)) return fail(WG_EINVAL, "cfg: field_y %d invalid", i);
-  if (cfg->flags != 0) return fail(WG_EINVAL, "cfg: flags must be 0");
+  if (cfg->flags & ~WG_TRACE_NO_EXIT_LIST) return fail(WG_EINVAL, "cfg: unknown flags 0x%x", cfg->flags);
   return WG_OK;
 }
 
@@ -470,6 +479,9 @@ static wg_status make_plan(const wg_design* d, const wg_trace_cfg* cfg, long lon
   p.rb = std::max<long long>(0, cfg->ray_begin);
   p.re = cfg->ray_end > 0 ? std::min<long long>(cfg->ray_end, p.total) : p.total;
   if (p.rb >= p.re) return fail(WG_EINVAL, "cfg: empty ray range [%lld, %lld)", p.rb, p.re);
+  if (p.re - p.rb >= (1ll << 32))
+    return fail(WG_EINVAL, "cfg: %lld rays in one call; at most 2^32 - 1 (split the range with ray_begin/ray_end)",
+                p.re - p.rb);
   p.cell_lo = p.rb / p.n_cell;
   p.cell_hi = (p.re - 1) / p.n_cell;
   p.chunk_rays = std::max<long long>(32, chunk_rays);
@@ -571,6 +583,49 @@ static TraceArgs base_args(const wg_design* d, const wg_trace_cfg* cfg, const Pl
   return a;
 }
 
+// Fingerprint of everything a ray's path and tally bin depend on: the
+// configuration's rays, keys, fields, wavelengths, eyebox and event cap, and
+// the design's geometry version (not its layer thicknesses). Never 0.
+static uint64_t path_fingerprint(const wg_design* d, const wg_trace_cfg* cfg, const Plan& p) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void* x, size_t n) {
+    const uint8_t* b = static_cast<const uint8_t*>(x);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  };
+  mix(&d->geom_version, sizeof(d->geom_version));
+  mix(&cfg->n_lambda, 4 * sizeof(int32_t));  // n_lambda, n_fx, n_fy, pol
+  mix(cfg->lambda_nm, sizeof(float) * cfg->n_lambda);
+  mix(cfg->field_x_deg, sizeof(float) * cfg->n_fx);
+  mix(cfg->field_y_deg, sizeof(float) * cfg->n_fy);
+  mix(&p.n_cell, sizeof(p.n_cell));
+  mix(&p.rb, sizeof(p.rb));
+  mix(&p.re, sizeof(p.re));
+  mix(&cfg->seed, sizeof(cfg->seed));
+  mix(&cfg->max_events, 3 * sizeof(int32_t));  // max_events, eb_nx, eb_ny
+  mix(&cfg->pupil_y_mm, 5 * sizeof(float));    // pupil_y, eyebox centre and size
+  return h | 1ull;
+}
+
+// Device list of eyebox rays for a forward trace of p (null when not recorded).
+static const size_t kExitHead = 64;  // count word, padded
+static wg_status prepare_exit_list(wg_design* d, const wg_trace_cfg* cfg, const Plan& p, cudaStream_t s,
+                                   TraceArgs& a) {
+  d->exit_fp = 0;
+  if (cfg->flags & WG_TRACE_NO_EXIT_LIST) return WG_OK;
+  const long long n = p.re - p.rb;
+  const size_t bytes = kExitHead + sizeof(ExitRec) * (size_t)n;
+  if (bytes > ((size_t)8 << 30)) return WG_OK;  // not worth 8 GB: the backward replays every ray
+  if (bytes > d->exits.n) CU(d->exits.ensure(bytes));
+  CU(cudaMemsetAsync(d->exits.p, 0, sizeof(unsigned long long), s));
+  a.exit_count = static_cast<unsigned long long*>(d->exits.p);
+  a.exit_list = reinterpret_cast<ExitRec*>(static_cast<uint8_t*>(d->exits.p) + kExitHead);
+  a.exit_cap = n;
+  return WG_OK;
+}
+
 static wg_status finish_stats(wg_ctx* c, const WsLayout& w, cudaStream_t s, wg_stats* stats, bool timed) {
   WsHead h;
   CU(cudaMemcpyAsync(&h, w.head, sizeof(WsHead), cudaMemcpyDeviceToHost, s));
@@ -608,7 +663,7 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
   p.chunk_rays = default_chunk(p);
   p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
   p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
-  const size_t smem = fwd_smem_bytes(d->blob_bytes, p.bins);
+  const size_t smem = fwd_smem_bytes(d->blob_bytes, p.bins, p.F);
   if (smem > 200 * 1024) return fail(WG_EINVAL, "wg_trace_forward: design + eyebox too large for shared memory");
   cudaStream_t s = (cudaStream_t)cfg->stream;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -622,10 +677,14 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
   CU(cudaMemsetAsync(t + p.cell_lo * p.bins, 0, sizeof(double) * (p.cell_hi - p.cell_lo + 1) * p.bins, s));
   TraceArgs a = base_args(d, cfg, p, w);
   a.tally = t;
+  wg_design* dm = const_cast<wg_design*>(d);  // the eyebox-ray list is a cache owned by the design
+  st = prepare_exit_list(dm, cfg, p, s, a);
+  if (st != WG_OK) return st;
   const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, d->period, smem));
   const int grid = (int)std::min<long long>(p.n_chunks, (long long)c->sm_count * bps);
   if (stats) CU(cudaEventRecord(c->t0, s));
   CU(launch_trace_fwd(a, p.F, d->period, grid, smem, s));
+  if (a.exit_list) dm->exit_fp = path_fingerprint(d, cfg, p);
   if (stats) CU(cudaEventRecord(c->t1, s));
   CU(cudaEventRecord(c->ws_free, s));
   if (!dev_tally) {
@@ -711,12 +770,32 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   CU(cudaMemsetAsync(sc.grad_acc, 0, sizeof(double) * std::max(1, d->n_dev), s));
   const int bps_r = std::max(1, bwd_replay_blocks_per_sm(p.F, d->period, smem_r));
   const int bps_a = std::max(1, bwd_adjoint_blocks_per_sm(d->period, smem_a));
+  // rays to replay: the eyebox rays listed by the forward trace of this
+  // configuration and geometry if there is such a list, else the ray range
+  bool use_list = d->exit_fp != 0 && d->exit_fp == path_fingerprint(d, cfg, p);
+  long long n_list = 0;
+  if (use_list) {
+    unsigned long long cnt = 0;
+    CU(cudaMemcpyAsync(&cnt, d->exits.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    use_list = (long long)cnt <= p.re - p.rb;  // more would mean the list overflowed
+    n_list = (long long)cnt;
+  }
+  const ExitRec* list =
+      use_list ? reinterpret_cast<const ExitRec*>(static_cast<const uint8_t*>(d->exits.p) + kExitHead) : nullptr;
+  const long long w_begin = use_list ? 0 : p.rb, w_end = use_list ? n_list : p.re;
   float ms_total = 0.f;
-  for (long long b0 = p.rb; b0 < p.re;) {
-    const long long b1 = std::min(p.re, b0 + batch);
+  for (long long b0 = w_begin; b0 < w_end;) {
+    const long long b1 = std::min(w_end, b0 + batch);
     Plan q = p;
-    plan_range(q, b0, b1);
+    if (!use_list) plan_range(q, b0, b1);
     TraceArgs a = base_args(d, cfg, q, w);
+    if (use_list) {
+      a.replay_list = list;
+      a.list_begin = b0;
+      a.list_end = b1;
+      a.n_chunks = (b1 - b0 + kReplayUnit - 1) / kReplayUnit;
+    }
     a.G = G;
     a.hit_buf = sc.rec;
     a.hit_cap = cap;
@@ -725,7 +804,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     CU(cudaMemsetAsync(&w.head->work, 0, sizeof(unsigned long long), s));
     CU(cudaMemsetAsync(sc.keys, 0, 128 * sizeof(unsigned int), s));
     CU(cudaMemsetAsync(sc.hit_count, 0, sizeof(unsigned long long), s));
-    const int grid_r = (int)std::min<long long>(q.n_chunks, (long long)c->sm_count * bps_r);
+    const int grid_r = (int)std::max<long long>(1, std::min<long long>(a.n_chunks, (long long)c->sm_count * bps_r));
     if (stats) CU(cudaEventRecord(c->t0, s));
     CU(launch_bwd_replay(a, p.F, d->period, grid_r, smem_r, s));
     unsigned long long n_rec = 0;
@@ -847,7 +926,7 @@ extern "C" wg_status wg_trace_forward_noalloc(wg_ctx* c, const wg_design* d, con
   p.chunk_rays = default_chunk(p);
   p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
   p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
-  const size_t smem = fwd_smem_bytes(d->blob_bytes, p.bins);
+  const size_t smem = fwd_smem_bytes(d->blob_bytes, p.bins, p.F);
   if (smem > 200 * 1024) return fail(WG_EINVAL, "wg_trace_forward_noalloc: design + eyebox too large for shared memory");
   const WsLayout need = ws_layout(nullptr, cfg, p.n_f);
   if (need.bytes > (size_t)WG_NOALLOC_SCRATCH_BYTES)

@@ -8,6 +8,15 @@ namespace wgk {
 struct FieldRec;
 struct HitRec;
 
+// A ray that ended in the eyebox: its id and flat tally index. The forward
+// trace lists them; the adjoint replays only listed rays whose bin has a
+// non-zero dL/dtally (every other ray contributes no gradient).
+struct ExitRec {
+  long long id;
+  int flat;
+  int pad;
+};
+
 // Arguments of the trace kernels (passed by value).
 struct TraceArgs {
   const uint8_t* blob;        // design blob (global), staged into smem
@@ -40,6 +49,13 @@ struct TraceArgs {
   unsigned long long* hit_count;  // records reserved (may exceed hit_cap: overflow)
   unsigned int* key_count;    // [2 * 64] records per stack (mirror, side)
   int n_layers;               // device layers
+  // forward: list of eyebox rays (null: not recorded)
+  ExitRec* exit_list;
+  long long exit_cap;
+  unsigned long long* exit_count;
+  // backward: replay the list entries [list_begin, list_end) instead of a ray range (null: ray range)
+  const ExitRec* replay_list;
+  long long list_begin, list_end;
 };
 
 // Arguments of the thin-film adjoint over sorted hit records.
@@ -60,8 +76,12 @@ constexpr int kBlock = 256;
 // the forward kernel keeps this many chunks (cells) in flight per CTA, each
 // with its own FP32 shared tally
 constexpr int kFwdSlots = 3;
-inline size_t fwd_smem_bytes(int blob_bytes, long long bins) {
-  return (size_t)blob_bytes + sizeof(float) * (size_t)kFwdSlots * (size_t)bins;
+// rays a warp of the forward kernel owns at a time (its lanes plus its two
+// shared-memory queues); a queued ray takes 9 + 4 F words
+constexpr int kFwdQCap = 48;
+inline size_t fwd_smem_bytes(int blob_bytes, long long bins, int F) {
+  return (size_t)blob_bytes + sizeof(float) * (size_t)kFwdSlots * (size_t)bins +
+         sizeof(uint32_t) * (size_t)(kBlock / 32) * 2 * (size_t)kFwdQCap * (size_t)(9 + 4 * F);
 }
 
 // number of kernels this library has launched (all launchers add to it)

@@ -196,7 +196,6 @@ struct Ray {
   int ev, hits, last;
   int reg;            // region between mirror planes (ordered designs), else -1
   uint32_t hash;
-  uint4 rnd;
 };
 
 struct ChunkConst {
@@ -365,11 +364,13 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
   }
   st.cphi = dot3(sf, sm);
   st.sphi = dot3(pf, sm);
+  // hit m draws word m & 3 of the block for counter (ray, m >> 2); the block
+  // is recomputed per hit so the ray state needs no RNG words
   const int m = R.hits;
-  if ((m & 3) == 0)
-    R.rnd = philox10(make_uint4((uint32_t)R.id, (uint32_t)((unsigned long long)R.id >> 32), (uint32_t)(m >> 2), TAG_EVT),
-                     A.key0, A.key1);
-  const uint32_t word = (m & 3) == 0 ? R.rnd.x : (m & 3) == 1 ? R.rnd.y : (m & 3) == 2 ? R.rnd.z : R.rnd.w;
+  const uint4 rnd = philox10(
+      make_uint4((uint32_t)R.id, (uint32_t)((unsigned long long)R.id >> 32), (uint32_t)(m >> 2), TAG_EVT), A.key0,
+      A.key1);
+  const uint32_t word = (m & 3) == 0 ? rnd.x : (m & 3) == 1 ? rnd.y : (m & 3) == 2 ? rnd.z : rnd.w;
   st.refl = u24(word) < M.omega;
   V3 d2 = R.d;
   if (st.refl) {
@@ -614,6 +615,58 @@ __device__ __forceinline__ void ring_finish(FwdRing& S, bool fin, int slot, floa
   }
 }
 
+// Per-warp ray queues of the forward kernel, in shared memory (structure of
+// arrays, one 32-bit word per field and slot): rays waiting at a mirror for
+// the warp's next transfer-matrix round, and rays waiting for a geometry
+// lane. A warp owns at most kFwdQCap rays (lanes + both queues), so neither
+// queue can overflow.
+constexpr int kQCap = kFwdQCap;
+
+template <int F>
+__device__ __forceinline__ void q_put(uint32_t* q, unsigned i, const Ray<F>& R, long long ray_begin, int slot) {
+  uint32_t* w = q + i;
+  constexpr int C = kQCap;
+  w[0 * C] = __float_as_uint(R.p.x);
+  w[1 * C] = __float_as_uint(R.p.y);
+  w[2 * C] = __float_as_uint(R.p.z);
+  w[3 * C] = __float_as_uint(R.d.x);
+  w[4 * C] = __float_as_uint(R.d.y);
+  w[5 * C] = __float_as_uint(R.d.z);
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    w[(6 + 4 * f) * C] = __float_as_uint(R.a[f].x);
+    w[(7 + 4 * f) * C] = __float_as_uint(R.a[f].y);
+    w[(8 + 4 * f) * C] = __float_as_uint(R.b[f].x);
+    w[(9 + 4 * f) * C] = __float_as_uint(R.b[f].y);
+  }
+  // counters: events (8 bits), hits (8), last surface (7), region + 1 (7), tally slot (2)
+  w[(6 + 4 * F) * C] = (uint32_t)(R.id - ray_begin);
+  w[(7 + 4 * F) * C] = (uint32_t)R.ev | ((uint32_t)R.hits << 8) | ((uint32_t)R.last << 16) |
+                       ((uint32_t)(R.reg + 1) << 23) | ((uint32_t)slot << 30);
+  w[(8 + 4 * F) * C] = R.hash;
+}
+
+template <int F>
+__device__ __forceinline__ int q_get(const uint32_t* q, unsigned i, Ray<F>& R, long long ray_begin) {
+  const uint32_t* w = q + i;
+  constexpr int C = kQCap;
+  R.p = v3(__uint_as_float(w[0 * C]), __uint_as_float(w[1 * C]), __uint_as_float(w[2 * C]));
+  R.d = v3(__uint_as_float(w[3 * C]), __uint_as_float(w[4 * C]), __uint_as_float(w[5 * C]));
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    R.a[f] = make_float2(__uint_as_float(w[(6 + 4 * f) * C]), __uint_as_float(w[(7 + 4 * f) * C]));
+    R.b[f] = make_float2(__uint_as_float(w[(8 + 4 * f) * C]), __uint_as_float(w[(9 + 4 * f) * C]));
+  }
+  R.id = ray_begin + (long long)w[(6 + 4 * F) * C];
+  const uint32_t c = w[(7 + 4 * F) * C];
+  R.ev = (int)(c & 0xffu);
+  R.hits = (int)((c >> 8) & 0xffu);
+  R.last = (int)((c >> 16) & 0x7fu);
+  R.reg = (int)((c >> 23) & 0x7fu) - 1;
+  R.hash = w[(8 + 4 * F) * C];
+  return (int)(c >> 30);
+}
+
 template <int F, int P>
 __global__ void __launch_bounds__(kBlock, 2) k_trace_fwd(const TraceArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -621,8 +674,12 @@ __global__ void __launch_bounds__(kBlock, 2) k_trace_fwd(const TraceArgs A) {
   __shared__ FwdRing S;
   __shared__ float s_led[6];
   __shared__ unsigned long long s_cnt[8];
+  constexpr int NW = 9 + 4 * F;
   float* s_tally = reinterpret_cast<float*>(smem + A.blob_bytes);
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  uint32_t* mq = reinterpret_cast<uint32_t*>(smem + A.blob_bytes + sizeof(float) * kSlots * A.bins) +
+                 wid * 2 * NW * kQCap;
+  uint32_t* gq = mq + NW * kQCap;
   if (tid < 6) s_led[tid] = 0.f;
   if (tid < 8) s_cnt[tid] = 0ull;
   if (tid < kSlots) {
@@ -648,11 +705,12 @@ __global__ void __launch_bounds__(kBlock, 2) k_trace_fwd(const TraceArgs A) {
   RayRec* recs = reinterpret_cast<RayRec*>(A.records);
 
   Ray<F> R;
-  bool has = false, at_mir = false;
-  int hit_k = 0, slot = 0;
-  float lam = 0.f;
-  unsigned idle = 0;  // consecutive passes without work (0xffffffff: stop)
+  bool has = false;
+  int slot = 0;
+  unsigned mh = 0, mt = 0, gh = 0, gt = 0;  // queue heads / tails (warp-uniform)
+  int n_fly = 0;                            // rays this warp owns (warp-uniform)
   unsigned long long idle_t0 = 0;
+  bool idling = false;
   // safety net: a warp needs at most ~2 loop passes per event of each ray it
   // traces (plus bounded idle waits); past this cap it flags and stops
   const unsigned long long it_cap =
@@ -661,68 +719,60 @@ __global__ void __launch_bounds__(kBlock, 2) k_trace_fwd(const TraceArgs A) {
       (1ull << 24);
   unsigned long long iters = 0;
   for (;;) {
-    // ---- phase A: fetch rays, advance through face events ----
-    for (;;) {
-      if (++iters > it_cap) {
-        if (lane == 0) atomicOr(A.error, 16u);
-        idle = 0xffffffffu;
-        break;
+    if (++iters > it_cap) {
+      if (lane == 0) atomicOr(A.error, 16u);
+      break;
+    }
+    // ---- free lanes take rays waiting for geometry, then new rays ----
+    unsigned need = __ballot_sync(FULL, !has);
+    if (need && gt != gh) {
+      const unsigned avail = gt - gh;
+      const unsigned rank = __popc(need & lt_mask);
+      if (!has && rank < avail) {
+        slot = q_get<F>(gq, (gh + rank) % kQCap, R, A.ray_begin);
+        has = true;
       }
-      const unsigned fm = __ballot_sync(FULL, !has);
-      bool fetched = false;
-      if (fm) {
-        const int leader = __ffs(fm) - 1;
-        unsigned long long base = 0;
-        int got = 0;
-        if (lane == leader) base = ring_fetch(S, A, __popc(fm), got);
-        base = __shfl_sync(FULL, base, leader);
-        got = __shfl_sync(FULL, got, leader);
-        __threadfence_block();
-        const int rank = __popc(fm & lt_mask);
-        if (!has && rank < got) {
-          const unsigned long long v = base + (unsigned long long)rank;
-          int sl = -1;
+      gh += min((unsigned)__popc(need), avail);
+      need = __ballot_sync(FULL, !has);
+    }
+    if (need && n_fly < kQCap) {
+      const int leader = __ffs(need) - 1;
+      unsigned long long base = 0;
+      int got = 0;
+      if (lane == leader) base = ring_fetch(S, A, min(__popc(need), kQCap - n_fly), got);
+      base = __shfl_sync(FULL, base, leader);
+      got = __shfl_sync(FULL, got, leader);
+      __threadfence_block();
+      const int rank = __popc(need & lt_mask);
+      bool mapped = false;
+      if (!has && rank < got) {
+        const unsigned long long v = base + (unsigned long long)rank;
+        int sl = -1;
 #pragma unroll
-          for (int s = 0; s < kSlots; ++s) {
-            const unsigned long long r = vload(S.slot[s].range);
-            const unsigned long long v0 = r >> kSizeBits;
-            if (v >= v0 && v < v0 + (r & ((1ull << kSizeBits) - 1ull))) sl = s;
-          }
-          if (sl < 0) {
-            atomicOr(A.error, 4u);  // a handed-out ray outside every bound chunk: never traced
-          } else {
-            slot = sl;
-            const SlotState& st = S.slot[slot];
-            const ChunkConst cc = st.cc;
-            lam = cc.lam;
-            gen_ray(R, st.r0 + (long long)(v - (st.range >> kSizeBits)), cc, H, A);
-            has = true;
-            ++c_rays;
-          }
+        for (int s = 0; s < kSlots; ++s) {
+          const unsigned long long r = vload(S.slot[s].range);
+          const unsigned long long v0 = r >> kSizeBits;
+          if (v >= v0 && v < v0 + (r & ((1ull << kSizeBits) - 1ull))) sl = s;
         }
-        fetched = got > 0;
-      }
-      const bool adv = has && !at_mir;
-      if (!__any_sync(FULL, adv)) {
-        if (__any_sync(FULL, has) || fetched) break;
-        // nothing in this warp: done when every chunk is bound and handed out
-        if (ring_drained(S, lane)) break;
-        __nanosleep(256);
-        const unsigned long long now = warp_time_ns();
-        if (idle == 0) idle_t0 = now;
-        ++idle;
-        if (now - idle_t0 > kWaitLimitNs) {  // no work for 0.5 s: give up and flag
-          if (lane == 0) atomicOr(A.error, 2u);
-          idle = 0xffffffffu;
-          break;
+        if (sl < 0) {
+          atomicOr(A.error, 4u);  // a handed-out ray outside every bound chunk: never traced
+        } else {
+          slot = sl;
+          const SlotState& st = S.slot[slot];
+          gen_ray(R, st.r0 + (long long)(v - (st.range >> kSizeBits)), st.cc, H, A);
+          has = true;
+          mapped = true;
+          ++c_rays;
         }
-        continue;
       }
-      idle = 0;
+      n_fly += __popc(__ballot_sync(FULL, mapped));
+    }
+    // ---- one event per lane ----
+    if (__any_sync(FULL, has)) {
       int pend_bin = -1;
       float pend_I = 0.f;
-      bool fin = false;
-      if (adv) {
+      bool fin = false, to_mir = false;
+      if (has) {
         float t;
         const int sid = next_surface(B, R.p, R.d, R.last, R.reg, t);
         ++R.ev;
@@ -738,13 +788,12 @@ __global__ void __launch_bounds__(kBlock, 2) k_trace_fwd(const TraceArgs A) {
           R.p = v3(fmaf(t, R.d.x, R.p.x), fmaf(t, R.d.y, R.p.y), fmaf(t, R.d.z, R.p.z));
           R.last = sid;
           if (sid >= S_MIR) {
-            at_mir = true;
-            hit_k = sid - S_MIR;
+            to_mir = true;
           } else {
             o = face_event<F>(R, sid, H, A, nullptr, nullptr, c_tir);
           }
         }
-        if (!o.term && !at_mir && R.ev >= A.max_events) {
+        if (!o.term && !to_mir && R.ev >= A.max_events) {
           o.term = 1;
           o.cat = L_TRUNCATED;
           o.bin = -1;
@@ -752,7 +801,6 @@ __global__ void __launch_bounds__(kBlock, 2) k_trace_fwd(const TraceArgs A) {
           o.w = ray_weight(R);
         }
         if (o.term) {
-          has = false;
           fin = true;
           c_events += R.ev;
           c_hits += R.hits;
@@ -780,8 +828,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_trace_fwd(const TraceArgs A) {
             put_rec(recs, R.id - A.ray_begin, A, rr);
           }
         }
+        if (fin || to_mir) has = false;
       }
-      // ---- per-warp aggregation of exits into the slot tallies ----
+      // rays that reached a mirror wait in the mirror queue
+      const unsigned pmask = __ballot_sync(FULL, to_mir);
+      if (to_mir) q_put<F>(mq, (mt + __popc(pmask & lt_mask)) % kQCap, R, A.ray_begin, slot);
+      mt += __popc(pmask);
+      // per-warp aggregation of exits into the slot tallies
       const unsigned pm = __ballot_sync(FULL, pend_bin >= 0);
       if (pm) {
         const int key = pend_bin >= 0 ? slot * A.bins + pend_bin : -1 - lane;
@@ -791,41 +844,84 @@ __global__ void __launch_bounds__(kBlock, 2) k_trace_fwd(const TraceArgs A) {
           for (unsigned mm = peers; mm; mm &= mm - 1) sum += __shfl_sync(peers, pend_I, __ffs(mm) - 1);
           if (lane == __ffs(peers) - 1) atomicAdd(&s_tally[key], sum);
         }
-      }
-      ring_finish(S, fin, slot, s_tally, A, lane);
-    }
-    // ---- phase B: per-hit transfer-matrix chain, all rays on mirrors ----
-    if (!__any_sync(FULL, at_mir)) {
-      if (!__any_sync(FULL, has) && ring_drained(S, lane)) break;
-      if (idle == 0xffffffffu) break;
-      continue;
-    }
-    bool fin = false;
-    if (at_mir) {
-      mirror_event<F, P>(R, hit_k, B, lam, A, c_steps, nullptr, nullptr);
-      at_mir = false;
-      if (R.ev >= A.max_events) {
-        has = false;
-        fin = true;
-        c_events += R.ev;
-        c_hits += R.hits;
-        const float w = ray_weight(R);
-        led[L_TRUNCATED] += w;
-        if (recs) {
-          RayRec rr;
-          rr.hash = R.hash;
-          rr.n_events = R.ev;
-          rr.n_hits = R.hits;
-          rr.cat = L_TRUNCATED;
-          rr.bin = -1;
-          rr.I = 0.f;
-          rr.w = w;
-          rr.pad = 0;
-          put_rec(recs, R.id - A.ray_begin, A, rr);
+        // list of eyebox rays for the adjoint (one reservation per warp)
+        if (A.exit_list) {
+          const int leader = __ffs(pm) - 1;
+          unsigned long long base = 0;
+          if (lane == leader) base = atomicAdd(A.exit_count, (unsigned long long)__popc(pm));
+          base = __shfl_sync(FULL, base, leader);
+          if (pend_bin >= 0) {
+            const unsigned long long i = base + __popc(pm & lt_mask);
+            if (i < (unsigned long long)A.exit_cap) {
+              ExitRec e;
+              e.id = R.id;
+              e.flat = (int)(S.slot[slot].cell * A.bins + pend_bin);
+              e.pad = 0;
+              A.exit_list[i] = e;
+            }
+          }
         }
       }
+      ring_finish(S, fin, slot, s_tally, A, lane);
+      n_fly -= __popc(__ballot_sync(FULL, fin));
     }
-    ring_finish(S, fin, slot, s_tally, A, lane);
+    // ---- transfer-matrix round: 32 queued hits (fewer when nothing else can run) ----
+    const unsigned nm = mt - mh;
+    if (nm >= 32u || (nm > 0u && !__any_sync(FULL, has) && gt == gh)) {
+      // the geometry rays wait in the geometry queue meanwhile
+      const unsigned hm = __ballot_sync(FULL, has);
+      if (has) q_put<F>(gq, (gt + __popc(hm & lt_mask)) % kQCap, R, A.ray_begin, slot);
+      gt += __popc(hm);
+      has = false;
+      const unsigned n = min(nm, 32u);
+      bool fin = false, keep = false;
+      if ((unsigned)lane < n) {
+        slot = q_get<F>(mq, (mh + lane) % kQCap, R, A.ray_begin);
+        mirror_event<F, P>(R, R.last - S_MIR, B, S.slot[slot].cc.lam, A, c_steps, nullptr, nullptr);
+        if (R.ev >= A.max_events) {
+          fin = true;
+          c_events += R.ev;
+          c_hits += R.hits;
+          const float w = ray_weight(R);
+          led[L_TRUNCATED] += w;
+          if (recs) {
+            RayRec rr;
+            rr.hash = R.hash;
+            rr.n_events = R.ev;
+            rr.n_hits = R.hits;
+            rr.cat = L_TRUNCATED;
+            rr.bin = -1;
+            rr.I = 0.f;
+            rr.w = w;
+            rr.pad = 0;
+            put_rec(recs, R.id - A.ray_begin, A, rr);
+          }
+        } else {
+          keep = true;
+        }
+      }
+      mh += n;
+      const unsigned km = __ballot_sync(FULL, keep);
+      if (keep) q_put<F>(gq, (gt + __popc(km & lt_mask)) % kQCap, R, A.ray_begin, slot);
+      gt += __popc(km);
+      ring_finish(S, fin, slot, s_tally, A, lane);
+      n_fly -= __popc(__ballot_sync(FULL, fin));
+      continue;
+    }
+    // ---- no ray in this warp: finished, or wait for the CTA's next chunk ----
+    if (n_fly == 0) {
+      if (ring_drained(S, lane)) break;
+      __nanosleep(256);
+      const unsigned long long now = warp_time_ns();
+      if (!idling) idle_t0 = now;
+      idling = true;
+      if (now - idle_t0 > kWaitLimitNs) {  // no work for 0.5 s: give up and flag
+        if (lane == 0) atomicOr(A.error, 2u);
+        break;
+      }
+    } else {
+      idling = false;
+    }
   }
   // ---- statistics ----
   __syncthreads();
@@ -920,23 +1016,42 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                 u_more = false;
                 break;
               }
-              long long cell, r0, r1;
-              if (!chunk_range(A, c, cell, r0, r1)) continue;
-              u_cell = cell;
-              u_next = r0;
-              u_end = r1;
-              ucc = chunk_const(A, cell);
+              if (A.replay_list) {  // a range of the forward's eyebox-ray list
+                u_next = A.list_begin + c * A.chunk_rays;
+                u_end = min(u_next + A.chunk_rays, A.list_end);
+              } else {
+                long long cell, r0, r1;
+                if (!chunk_range(A, c, cell, r0, r1)) continue;
+                u_cell = cell;
+                u_next = r0;
+                u_end = r1;
+                ucc = chunk_const(A, cell);
+              }
             }
             const int take = (int)min((long long)__popc(fm), u_end - u_next);
             const int rank = __popc(fm & lt_mask);
             if (!has && rank < take) {
-              gen_ray(R, u_next + rank, ucc, H, A);
-              has = true;
-              cell_l = u_cell;
-              lam_l = ucc.lam;
-              seg_s = make_float2(1.f, 0.f);
-              seg_p = make_float2(1.f, 0.f);
-              ++c_rays;
+              if (A.replay_list) {
+                // listed ray: replayed only if its bin carries gradient
+                const ExitRec e = A.replay_list[u_next + rank];
+                if (A.G[e.flat] != 0.0) {
+                  cell_l = e.flat / A.bins;
+                  const ChunkConst cc = chunk_const(A, cell_l);
+                  gen_ray(R, e.id, cc, H, A);
+                  lam_l = cc.lam;
+                  has = true;
+                }
+              } else {
+                gen_ray(R, u_next + rank, ucc, H, A);
+                cell_l = u_cell;
+                lam_l = ucc.lam;
+                has = true;
+              }
+              if (has) {
+                seg_s = make_float2(1.f, 0.f);
+                seg_p = make_float2(1.f, 0.f);
+                ++c_rays;
+              }
             }
             u_next += take;
             fm = __ballot_sync(FULL, !has);

@@ -71,6 +71,9 @@ class Stats(C.Structure):
                     n_nonfinite=self.n_nonfinite)
 
 
+# wg_trace_cfg.flags bits (include/wg.h)
+TRACE_NO_EXIT_LIST = 1  # forward: do not list the eyebox rays for the adjoint
+
 RAY_RECORD_DTYPE = np.dtype([("hash", np.uint32), ("n_events", np.int32), ("n_hits", np.int32),
                              ("cat", np.int32), ("bin", np.int32), ("I", np.float32), ("w", np.float32),
                              ("pad", np.int32)])
@@ -135,7 +138,7 @@ def _current_stream():
 class _CfgHolder:
     """A TraceCfg whose host arrays stay alive as long as the holder."""
 
-    def __init__(self, cfg, stream=None, rays=None, records=None):
+    def __init__(self, cfg, stream=None, rays=None, records=None, flags=0):
         self.lam = np.ascontiguousarray(cfg.lam_nm, dtype=np.float32)
         self.fx = np.ascontiguousarray(cfg.fx_deg, dtype=np.float32)
         self.fy = np.ascontiguousarray(cfg.fy_deg, dtype=np.float32)
@@ -143,7 +146,7 @@ class _CfgHolder:
         self.c = TraceCfg(n_lambda=len(self.lam), n_fx=len(self.fx), n_fy=len(self.fy), pol=int(cfg.pol),
                           lambda_nm=_fptr(self.lam), field_x_deg=_fptr(self.fx), field_y_deg=_fptr(self.fy),
                           n_rays=int(cfg.n_rays), seed=int(cfg.seed), max_events=int(cfg.max_events),
-                          eb_nx=int(cfg.eb_nx), eb_ny=int(cfg.eb_ny), flags=0, pupil_y_mm=cfg.pupil_y_mm,
+                          eb_nx=int(cfg.eb_nx), eb_ny=int(cfg.eb_ny), flags=int(flags), pupil_y_mm=cfg.pupil_y_mm,
                           eb_cx_mm=cfg.eb_cx_mm, eb_cy_mm=cfg.eb_cy_mm, eb_w_mm=cfg.eb_w_mm, eb_h_mm=cfg.eb_h_mm,
                           stream=stream, ray_begin=rb, ray_end=re, ray_records=_ptr(records))
 
@@ -225,10 +228,11 @@ class Context:
                                           stream if stream is not None else _current_stream()))
 
     # ---- trace ----
-    def trace_forward(self, dh, cfg, tally, stats=True, stream=None, rays=None, records=None):
+    def trace_forward(self, dh, cfg, tally, stats=True, stream=None, rays=None, records=None, flags=0):
         """tally: torch CUDA float64 tensor (device path) or numpy float64 array
-        (host path, copies inside the call). Returns the stats dict or None."""
-        h = _CfgHolder(cfg, stream if stream is not None else _current_stream(), rays, records)
+        (host path, copies inside the call). flags: TRACE_* bits. Returns the
+        stats dict or None."""
+        h = _CfgHolder(cfg, stream if stream is not None else _current_stream(), rays, records, flags)
         st = Stats() if stats else None
         _check(lib().wg_trace_forward(self.h, dh.h, C.byref(h.c), _ptr(tally), C.byref(st) if stats else None))
         return st.to_dict() if stats else None

@@ -331,6 +331,35 @@ def test_backward_3d_matches_oracle_adjoint(ctx, ora, L):
     dh.destroy()
 
 
+def test_backward_eyebox_list_matches_full_replay(ctx):
+    """The adjoint that replays only the forward's eyebox rays (whose bins
+    carry gradient) equals the one that replays every ray; a tilt update
+    (even to the same values) or a forward without the list makes the next
+    backward replay every ray."""
+    from paper_2601_04370_gb300 import wg
+    D, C = W.representative(n_rays=1728 * 16)
+    dh = ctx.create_design(D)
+    tally = torch.zeros(C.tally_shape, dtype=torch.float64, device="cuda")
+    ctx.trace_forward(dh, C, tally)
+    G = torch.zeros_like(tally)
+    ctx.loss(dh, C, tally, G)
+    g_list = torch.zeros(D.total_layers, dtype=torch.float64, device="cuda")
+    s_list = ctx.trace_backward(dh, C, G, g_list)
+    dh.set_params(tilt_deg=D.mirror_tilt_deg)
+    g_full = torch.zeros_like(g_list)
+    s_full = ctx.trace_backward(dh, C, G, g_full)
+    assert s_full["n_rays"] == C.total_rays
+    assert 0 < s_list["n_rays"] < s_full["n_rays"]
+    # the same per-hit terms summed in another order: partial sums per chunk
+    # of records are FP32 before the FP64 accumulation (2^-24 per term)
+    a, b = g_list.cpu().numpy(), g_full.cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()
+    ctx.trace_forward(dh, C, tally, flags=wg.TRACE_NO_EXIT_LIST)
+    g_again = torch.zeros_like(g_list)
+    assert ctx.trace_backward(dh, C, G, g_again)["n_rays"] == C.total_rays
+    dh.destroy()
+
+
 def test_backward_pruned_layers_zero(ctx, ora):
     D, C = W.batching(n_designs=2, seed=4)[0]
     C = C.replace(n_rays=1728 * 4)
