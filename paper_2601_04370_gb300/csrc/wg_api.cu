@@ -729,7 +729,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   if (st != WG_OK) return st;
   p.chunk_rays = kReplayUnit;  // the replay's warps claim ranges of this many rays
   const size_t smem_r = (size_t)d->blob_bytes;
-  const size_t smem_a = (size_t)d->blob_bytes + sizeof(float) * std::max(1, d->n_dev);
+  const size_t smem_a = adj_smem_bytes(d->blob_bytes, d->n_dev, d->period);
   if (smem_a > 200 * 1024) return fail(WG_EINVAL, "wg_trace_backward: design too large for shared memory");
   cudaStream_t s = (cudaStream_t)cfg->stream;
   std::lock_guard<std::mutex> lk(c->mu);

@@ -443,10 +443,20 @@ __device__ __forceinline__ CRow coef_row(const CV& v, float eta0, int e, float2 
   return a;
 }
 
+// Words per layer of the segment buffer (s and p substrate-side vectors, c, s).
+constexpr int kSegWords = 10;
+// Shared-memory floats of one warp's segment buffers for material period P.
+template <int P>
+__host__ __device__ constexpr int seg_floats_per_warp() {
+  return Seg<P>::CKP * kSegWords * 32;
+}
+
+// seg: this lane's column of its warp's segment buffer (element (u, w) at
+// seg[(u * kSegWords + w) * 32]; the 32 lanes' columns interleave).
 template <int P, class Sink>
 __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, const MatTable& mt, float n0,
                                             float cos0, float2 A_s, float2 A_p, int which, Sink& sink,
-                                            int eA = 0) {
+                                            float* seg, int eA = 0) {
   // (A_s, A_p) * 2^eA are the weights; eA carries the range of dL/dtally
   constexpr int CKP = Seg<P>::CKP;
   MatK kb[Seg<P>::NSLOT];
@@ -494,10 +504,9 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
   for (int sg = 0; sg < nseg; ++sg) {
     const int j0 = sg * CKP;
     const Ckpt c1 = ck[sg + 1];
-    CV bs[CKP], bp[CKP];
-    float bc[CKP], bsn[CKP];
-    int bm[CKP];
     CV ws = c1.s, wp = c1.p;
+    // the segment's substrate-side vectors and (c, s), recomputed from the
+    // checkpoint at its far end and kept in this lane's shared-memory column
 #pragma unroll
     for (int u = CKP - 1; u >= 0; --u) {
       const int j = j0 + u;
@@ -507,17 +516,23 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         if constexpr (P > 0) {
           k = kb[u % P];
         } else {
-          bm[u] = st.m[i];
-          k = mt.get(bm[u]);
+          k = mt.get(st.m[i]);
         }
         float c, s;
         layer_cs(k, st.d[i], c, s);
         cv_step(ws, c, s * k.q12s, s * k.q21s);
         cv_step(wp, c, s * k.q12p, s * k.q21p);
-        bs[u] = ws;
-        bp[u] = wp;
-        bc[u] = c;
-        bsn[u] = s;
+        float* b = seg + u * kSegWords * 32;
+        b[0 * 32] = ws.xr;
+        b[1 * 32] = ws.xi;
+        b[2 * 32] = ws.yr;
+        b[3 * 32] = ws.yi;
+        b[4 * 32] = wp.xr;
+        b[5 * 32] = wp.xi;
+        b[6 * 32] = wp.yr;
+        b[7 * 32] = wp.yi;
+        b[8 * 32] = c;
+        b[9 * 32] = s;
       }
     }
 #pragma unroll
@@ -528,14 +543,16 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         if constexpr (P > 0) {
           k = kb[u % P];
         } else {
-          k = mt.get(bm[u]);
+          k = mt.get(st.m[st.idx(front, j)]);
         }
-        const CV& x = bs[u];
-        const CV& y = bp[u];
+        const float* b = seg + u * kSegWords * 32;
+        const CV x{b[0 * 32], b[1 * 32], b[2 * 32], b[3 * 32]};
+        const CV y{b[4 * 32], b[5 * 32], b[6 * 32], b[7 * 32]};
+        const float bc_u = b[8 * 32], bs_u = b[9 * 32];
         const float gs = fmaf(k.q12s, fmaf(as.a0.x, x.yi, as.a0.y * x.yr), k.q21s * fmaf(as.a1.x, x.xi, as.a1.y * x.xr));
         const float gp = fmaf(k.q12p, fmaf(ap.a0.x, y.yi, ap.a0.y * y.yr), k.q21p * fmaf(ap.a1.x, y.xi, ap.a1.y * y.xr));
         sink(st.idx(front, j), -2.0f * k.kap * (scale2(gs, eas + c1.es) + scale2(gp, eap + c1.ep)));
-        const float c = bc[u], s = bsn[u];
+        const float c = bc_u, s = bs_u;
         row_step(as, c, s * k.q12s, s * k.q21s);
         row_step(ap, c, s * k.q12p, s * k.q21p);
         row_guard(as, eas);

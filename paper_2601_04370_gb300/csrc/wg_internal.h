@@ -110,6 +110,8 @@ cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const in
 int trace_fwd_blocks_per_sm(int F, int P, size_t smem);
 int bwd_replay_blocks_per_sm(int F, int P, size_t smem);
 int bwd_adjoint_blocks_per_sm(int P, size_t smem);
+// dynamic shared memory of the adjoint kernel (blob, per-layer sums, segment buffers)
+size_t adj_smem_bytes(int blob_bytes, int n_layers, int P);
 size_t hit_rec_bytes();
 
 // loss (workspace: 2 * cells * 9 + 8 doubles, then one u16 pupil mask per eyebox bin)

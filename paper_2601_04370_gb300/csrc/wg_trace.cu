@@ -12,6 +12,7 @@
 // per-hit coefficient sensitivities to a checkpointed thin-film adjoint.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "wg_device.cuh"
@@ -1277,42 +1278,52 @@ __global__ void k_bwd_scatter(const HitRec* in, long long n, unsigned int* key_c
     if (key[t] >= 0) out[s_base[key[t]] + rank[t]] = r[t];
 }
 
-struct LaneSink {
-  float* s_grad;
-  int* bad;
-  __device__ __forceinline__ void operator()(int idx, float g) const {
-    if (isfinite(g)) {
-      atomicAdd(s_grad + idx, g);
-    } else {
-      ++*bad;  // reported in wg_stats; never added
-    }
-  }
-};
-
-// all 32 lanes hold records of the same stack: same gradient entry per step
-struct WarpSink {
+// Per-layer gradient terms of one record per lane. When all 32 lanes hold
+// records of the same stack (uniform, warp-uniform flag) every step touches
+// the same entry in all lanes: reduced with shuffles and added once; else
+// added per lane. Non-finite terms are counted (wg_stats) and never added.
+struct GradSink {
   float* s_grad;
   int* bad;
   int lane;
+  bool uniform;
   __device__ __forceinline__ void operator()(int idx, float g) const {
     if (!isfinite(g)) {
       ++*bad;
       g = 0.f;
     }
+    if (uniform) {
 #pragma unroll
-    for (int o = 16; o; o >>= 1) g += __shfl_xor_sync(FULL, g, o);
-    if (lane == 0) atomicAdd(s_grad + idx, g);
+      for (int o = 16; o; o >>= 1) g += __shfl_xor_sync(FULL, g, o);
+      if (lane == 0) atomicAdd(s_grad + idx, g);
+    } else if (g != 0.f) {
+      atomicAdd(s_grad + idx, g);
+    }
   }
 };
 
+// shared memory of the adjoint kernel: blob | per-layer FP32 sums (padded
+// to 32 floats) | per-warp segment buffers
 template <int P>
-__global__ void __launch_bounds__(kBlock) k_bwd_adjoint(const AdjArgs A) {
+static size_t adj_smem_bytes_p(int blob_bytes, int n_layers) {
+  return (size_t)blob_bytes + sizeof(float) * (size_t)((std::max(1, n_layers) + 31) & ~31) +
+         sizeof(float) * (size_t)(kBlock / 32) * (size_t)seg_floats_per_warp<P>();
+}
+size_t adj_smem_bytes(int blob_bytes, int n_layers, int P) {
+  if (P == 3) return adj_smem_bytes_p<3>(blob_bytes, n_layers);
+  if (P == 2) return adj_smem_bytes_p<2>(blob_bytes, n_layers);
+  return adj_smem_bytes_p<0>(blob_bytes, n_layers);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kBlock, 2) k_bwd_adjoint(const AdjArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ long long s_chunk;
   __shared__ unsigned long long s_cnt[2];
   float* s_grad = reinterpret_cast<float*>(smem + A.blob_bytes);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  float* seg = s_grad + ((max(1, A.n_layers) + 31) & ~31) + warp * seg_floats_per_warp<P>() + lane;
   if (tid < 2) s_cnt[tid] = 0ull;
   if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;
   Blob B;
@@ -1344,13 +1355,8 @@ __global__ void __launch_bounds__(kBlock) k_bwd_adjoint(const AdjArgs A) {
         MatTable mt;
         mt.init(H, rec.cos0, rec.lam);
         const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
-        if (uniform) {
-          WarpSink sink{s_grad, &bad, lane};
-          tmm_adjoint<P>(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, rec.eA);
-        } else {
-          LaneSink sink{s_grad, &bad};
-          tmm_adjoint<P>(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, rec.eA);
-        }
+        GradSink sink{s_grad, &bad, lane, uniform};
+        tmm_adjoint<P>(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, seg, rec.eA);
         c_steps += M.n_layers;
       }
     }
@@ -1420,8 +1426,11 @@ struct RowSink {
 };
 
 template <int P>
-__global__ void k_coating_grad(const uint8_t* blob, int mirror, int side, long long n, const float* cos0,
-                               const float* lam, const float* w, int which, float* grad) {
+__global__ void __launch_bounds__(128) k_coating_grad(const uint8_t* blob, int mirror, int side, long long n,
+                                                       const float* cos0, const float* lam, const float* w, int which,
+                                                       float* grad) {
+  __shared__ float s_seg[4 * seg_floats_per_warp<P>()];
+  float* seg = s_seg + (threadIdx.x >> 5) * seg_floats_per_warp<P>() + (threadIdx.x & 31);
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   Blob B;
@@ -1433,7 +1442,7 @@ __global__ void k_coating_grad(const uint8_t* blob, int mirror, int side, long l
   const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
   RowSink sink{grad + i * M.n_layers, M.layer_off, M.n_layers, side == 0};
   tmm_adjoint<P>(sv, side == 0, mt, H.n_slab, cos0[i], make_float2(w[4 * i], w[4 * i + 1]),
-                 make_float2(w[4 * i + 2], w[4 * i + 3]), which, sink);
+                 make_float2(w[4 * i + 2], w[4 * i + 3]), which, sink, seg);
 }
 
 // ---------------------------------------------------------------------------
