@@ -27,14 +27,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ray-mirror interactions/s fwd & fwd+bwd at <=1e-4 rel err; p50/p99 eval latency"
 UNIT = "interactions/s"
-# algorithmic FP32 flops per transfer-matrix layer step (counting an FMA as 2):
-#   forward: phase 1 mul + per polarization (2 mul for the layer matrix,
-#   4 mul + 4 fma for the 2x2 product) = 29;
-#   adjoint: reverse sweep per polarization (2 mul + 4 mul + 4 fma) and the
-#   layer gradient (q21 (p2 z1 + p4 z3) - q12 (p1 z2 + p3 z4): 2 fma + 2 mul
-#   + 2 mul + 1 fma = 9) = 2*(14+9) + 3 to combine = 49.
-FLOPS_FWD_LAYER = 29
-FLOPS_ADJ_LAYER = 49
+# Algorithmic FP32 work per ray-mirror interaction (an FMA counts 2 flops):
+# 33 flops per non-pruned layer of the hit's stack (phase, range reduction and
+# the s and p 2x2 chain) plus 250 per hit for the coefficients, bases, Jones
+# update and geometry. The thin-film adjoint costs about three forward layer
+# chains per layer of each record (forward sweep, recomputation, reverse
+# sweep with the layer gradients).
+FLOPS_PER_LAYER = 33
+FLOPS_PER_HIT = 250
+FLOPS_ADJ_LAYER = 3 * FLOPS_PER_LAYER
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -268,8 +269,9 @@ def run_ours(args):
     loss = ctx.loss(dh, C, tally, G)
     st_b = ctx.trace_backward(dh, C, G, grad)
     hits = st_f["n_hits"]
-    flops_fwd = FLOPS_FWD_LAYER * st_f["n_layer_steps"]
-    flops_bwd = FLOPS_FWD_LAYER * st_b["n_layer_steps"] + FLOPS_ADJ_LAYER * st_b["n_adjoint_steps"]
+    flops_fwd = FLOPS_PER_LAYER * st_f["n_layer_steps"] + FLOPS_PER_HIT * hits
+    flops_bwd = (FLOPS_PER_LAYER * st_b["n_layer_steps"] + FLOPS_PER_HIT * st_b["n_hits"] +
+                 FLOPS_ADJ_LAYER * st_b["n_adjoint_steps"])
 
     def step(evs):
         flush.zero_()
@@ -338,12 +340,19 @@ def run_ours(args):
         fwd_s = statistics.mean(fwd_ms) / 1e3
         ach_b = flops_bwd / bwd_s / 1e12
         ach_f = flops_fwd / fwd_s / 1e12
-        roof = {"bound": "alu", "kernel": "k_trace_bwd", "achieved": ach_b, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach_b / peak, "traffic": profile_traffic("k_trace_bwd"),
+        # the dominant kernel of the step (largest share of the launch list) is
+        # the forward trace; its duration is the event pair around the
+        # forward call on the launching stream (the kernel plus two tiny
+        # preparation launches)
+        roof = {"bound": "alu", "kernel": "k_trace_fwd", "achieved": ach_f, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach_f / peak, "traffic": profile_traffic("k_trace_fwd"),
+                "flops_per_launch": flops_fwd,
+                "units": f"{hits} interactions x ({FLOPS_PER_LAYER} x {st_f['n_layer_steps'] / hits:.1f} layers "
+                         f"+ {FLOPS_PER_HIT}) flops",
                 "peak_source": f"derived: {sm} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz "
                                f"(sm_max_mhz of {pk_kind} peaks)"}
-        roof_f = {"bound": "alu", "kernel": "k_trace_fwd", "achieved": ach_f, "peak": peak, "unit": "TFLOP/s",
-                  "frac": ach_f / peak, "traffic": profile_traffic("k_trace_fwd")}
+        roof_b = {"bound": "alu", "kernels": "k_bwd_replay + sort + k_bwd_adjoint", "achieved": ach_b,
+                  "peak": peak, "unit": "TFLOP/s", "frac": ach_b / peak, "flops_per_call": flops_bwd}
         cpu = None
         if ws == 1 and not args.no_cpu_baseline:
             cpu, _, _ = cpu_oracle_rate(D, C, G.cpu().numpy(), budget_s=args.cpu_budget)
@@ -355,7 +364,7 @@ def run_ours(args):
                           "parallelism": f"replicas x{ws} (rays sharded by seed, no collective)"},
                "fwd_interactions_per_s": fwd_rate, "fwd_ms": statistics.mean(fwd_ms),
                "bwd_ms": statistics.mean(bwd_ms), "loss": loss[0], "wall_s": t_wall,
-               "roofline": roof, "roofline_fwd": roof_f, "cpu_baseline": cpu,
+               "roofline": roof, "roofline_bwd": roof_b, "cpu_baseline": cpu,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": launches, "clocks": ck}
         print(json.dumps(out))

@@ -108,11 +108,51 @@ __device__ void spread_grad(const double* x, int n, long long stride, int kind, 
   }
 }
 
-// One block: scalars and dL/dI. I is [n_lam][n_f][P]; dI same layout.
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// spread_grad for one group with a whole warp (n values, stride): the sums
+// are warp reductions; val is returned in every lane
+__device__ void spread_grad_warp(const double* x, int n, long long stride, int kind, double scale, double* dx,
+                                 double& val, int lane) {
+  double mu = 0.0;
+  for (int i = lane; i < n; i += 32) mu += x[i * stride];
+  mu = warp_sum_d(mu) / n;
+  double var = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const double d = x[i * stride] - mu;
+    var += d * d;
+  }
+  var = warp_sum_d(var) / n;
+  if (kind == 1) {
+    val = var;
+    for (int i = lane; i < n; i += 32) dx[i * stride] += scale * 2.0 * (x[i * stride] - mu) / n;
+    return;
+  }
+  const double sd = sqrt(var);
+  if (mu == 0.0) {
+    val = 0.0;
+    return;
+  }
+  val = sd / mu;
+  if (sd <= 0.0) return;
+  for (int i = lane; i < n; i += 32) {
+    const double dsd = (x[i * stride] - mu) / (n * sd);
+    dx[i * stride] += scale * (dsd / mu - (val / mu) / n);
+  }
+}
+
+// One block: scalars and dL/dI. I is [n_lam][n_f][P]; dI same layout. The
+// field-uniformity groups (long: n_f values) take a warp each; the
+// eyebox-uniformity groups (P values) a thread each.
 __global__ void k_loss_scalar(const double* I, int n_lam, int n_f, int P, int kind, double w_f, double w_e, double* dI,
                               double* out) {
   const long long N = (long long)n_lam * n_f * P;
   __shared__ double s_red[3][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double sum = 0.0, uf = 0.0, ue = 0.0;
   for (long long i = threadIdx.x; i < N; i += blockDim.x) {
     sum += I[i];
@@ -121,11 +161,12 @@ __global__ void k_loss_scalar(const double* I, int n_lam, int n_f, int P, int ki
   __syncthreads();
   // U_FoV: over fields for each (lambda, p); gradients touch disjoint entries
   const int nfov = n_lam * P;
-  for (int q = threadIdx.x; q < nfov; q += blockDim.x) {
+  for (int q = wid; q < nfov; q += nw) {
     const int l = q / P, p = q % P;
     double v;
-    spread_grad(I + (long long)l * n_f * P + p, n_f, P, kind, w_f / nfov, dI + (long long)l * n_f * P + p, v);
-    uf += v;
+    spread_grad_warp(I + (long long)l * n_f * P + p, n_f, P, kind, w_f / nfov, dI + (long long)l * n_f * P + p, v,
+                     lane);
+    if (lane == 0) uf += v;
   }
   __syncthreads();
   const int neb = n_lam * n_f;
@@ -134,7 +175,6 @@ __global__ void k_loss_scalar(const double* I, int n_lam, int n_f, int P, int ki
     spread_grad(I + (long long)q * P, P, 1, kind, w_e / neb, dI + (long long)q * P, v);
     ue += v;
   }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double vals[3] = {sum, uf, ue};
   for (int k = 0; k < 3; ++k) {
     double v = vals[k];
@@ -180,7 +220,7 @@ cudaError_t launch_loss_impl(const double* tally, int dims, int n_lam, int n_f, 
   note_launches(dL ? 4 : 3);
   k_pupil_masks<<<(bins + 255) / 256, 256, 0, s>>>(g, mask);
   k_pupil_sums<<<(unsigned)n_cells, 256, 0, s>>>(tally, g, mask, inv_ncell, I);
-  k_loss_scalar<<<1, 256, 0, s>>>(I, n_lam, n_f, g.n_pupil, kind, w_f, w_e, dI, out_dev);
+  k_loss_scalar<<<1, 512, 0, s>>>(I, n_lam, n_f, g.n_pupil, kind, w_f, w_e, dI, out_dev);
   if (dL) {
     const long long n = n_cells * nx * ny;
     k_loss_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dI, g, mask, inv_ncell, n_cells, dL);
