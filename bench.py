@@ -215,6 +215,54 @@ def cpu_oracle_rate(D, C, G, budget_s=12.0, max_rays=None):
                        f"FP64 forward + adjoint, {t:.1f} s wall on {nthreads} host threads"), h, t
 
 
+def run_serving(dev, n_requests, max_slots, cache_path):
+    """The serving trace (Poisson arrivals at 200 req/s, designs drawn from the
+    64-design batching pool and kept resident, 5% loss+gradient requests at
+    1e6..1e8 rays) submitted at its arrival times through wg_submit; latency
+    of a request = submit -> completion as the runtime measures it."""
+    import numpy as np
+    from paper_2601_04370_gb300 import wg
+    from paper_2601_04370_gb300 import workloads as W
+    reqs = W.serving_trace(n_requests=n_requests)
+    ctx = wg.Context(dev, max_slots=max_slots, autotune_cache=cache_path)
+    handles = {}
+    for r in reqs:
+        if id(r["design"]) not in handles:
+            handles[id(r["design"])] = ctx.create_design(r["design"])
+
+    def run(subset):
+        keep, tickets = [], []
+        t0 = time.perf_counter()
+        for r in subset:
+            dt = r["arrival_s"] - subset[0]["arrival_s"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            dh = handles[id(r["design"])]
+            if r["kind"] == "fwd_bwd":
+                g, lo = np.zeros(r["design"].total_layers), np.zeros(4)
+                keep.append((g, lo))
+                tickets.append(ctx.submit(dh, r["cfg"], kind=wg.REQ_LOSS_GRAD, grad=g, loss=lo))
+            else:
+                tickets.append(ctx.submit(dh, r["cfg"]))
+        res = [ctx.poll(t) for t in tickets]
+        wall = time.perf_counter() - t0
+        return res, wall
+
+    run(reqs[:min(64, len(reqs))])  # warm-up: autotuning of the classes, first captures
+    res, wall = run(reqs)
+    ok = [r for r in res if r["status"] == wg.WG_OK]
+    lat = np.array([r["queue_ms"] + r["run_ms"] for r in ok])
+    hits = sum(r["stats"]["n_hits"] for r in ok)
+    out = {"requests": len(reqs), "completed": len(ok), "p50_ms": float(np.percentile(lat, 50)),
+           "p99_ms": float(np.percentile(lat, 99)), "interactions_per_s": hits / wall, "wall_s": wall,
+           "mean_batch": float(np.mean([r["batch_size"] for r in ok])),
+           "graph_replays": int(sum(r["graph_replayed"] for r in ok))}
+    for dh in handles.values():
+        dh.destroy()
+    ctx.close()
+    return out
+
+
 def run_reference(args):
     ws, rank, local, pg = dist_setup(args)
     if rank != 0:
@@ -331,6 +379,29 @@ def run_ours(args):
     e2e_max = allmax(pg, sum(e2e_t), dev)
     e2e_value = hits_all / e2e_max
 
+    # serving: the same request trace batched by the runtime and one design per launch
+    serving = None
+    if args.serve_requests > 0:
+        import tempfile
+        cache = os.path.join(tempfile.mkdtemp(prefix="wg_tune_"), "autotune.txt")
+        barrier(pg, dev)
+
+        def serve_child(slots):
+            # each mode in its own process (its own contexts; a failure there is reported, not fatal)
+            cmd = [sys.executable, "-X", "faulthandler", os.path.abspath(__file__), "--serve-child",
+                   f"{dev},{args.serve_requests},{slots},{cache}"]
+            r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
+            lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+            if r.returncode == 0 and lines:
+                return json.loads(lines[-1])
+            return {"error": f"exit {r.returncode}", "stderr_tail": r.stderr[-1500:]}
+
+        b = serve_child(64)
+        o = serve_child(1)
+        serving = {"trace": f"{args.serve_requests} requests, Poisson 200 req/s (seed 5), designs from the 64-design "
+                            f"batching pool (K 3..8, L 10..200, 30% pruned), fwd at 1e5..1e7 rays, 5% loss+grad at "
+                            f"1e6..1e8 rays", "batched": b, "one_design_per_launch": o}
+
     out = None
     if rank == 0:
         sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -366,7 +437,7 @@ def run_ours(args):
                "bwd_ms": statistics.mean(bwd_ms), "loss": loss[0], "wall_s": t_wall,
                "roofline": roof, "roofline_bwd": roof_b, "cpu_baseline": cpu,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-               "gpu_launches": launches, "clocks": ck}
+               "gpu_launches": launches, "clocks": ck, "serving": serving}
         print(json.dumps(out))
     dh.destroy()
     ctx.close()
@@ -383,7 +454,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--serve-requests", type=int, default=400,
+                    help="requests of the serving trace (0: skip the serving measurement)")
+    ap.add_argument("--serve-child", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.serve_child:
+        dev, n, slots, cache = args.serve_child.split(",", 3)
+        import torch
+        torch.cuda.set_device(int(dev))
+        print(json.dumps(run_serving(int(dev), int(n), int(slots), cache)))
+        return 0
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

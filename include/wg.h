@@ -306,6 +306,66 @@ wg_status wg_trace_backward(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg*
 wg_status wg_trace_forward_noalloc(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cfg, double* tally,
                                    wg_stats* stats);
 
+/* ------------------------------------------------------------------------
+ * Serving: design evaluations (the inner step of the paper's design
+ * optimisation, Methods) submitted as they arrive.
+ *
+ * wg_submit copies the request and returns at once. A scheduler thread of
+ * the context (started by the first submit, stopped by wg_shutdown) forms a
+ * batch from whatever is queued whenever the GPU is free: FIFO, at most
+ * wg_init_opts.max_slots requests, admitted while the batch's device memory
+ * fits the HBM budget (wg_init_opts.hbm_budget_bytes, 0 = 80% of free HBM).
+ * It traces the batch's forward passes in fused persistent launches (one per
+ * kernel variant, each design on its own range of CTAs, chunk sizes and CTAs
+ * per SM from the autotuned table); a batch whose launches were captured
+ * before replays the captured CUDA graph. Then it runs the loss and adjoint
+ * of loss+gradient requests and completes the tickets. Designs stay resident
+ * on the device; the caller must not change or destroy a design while a
+ * request that uses it is pending.
+ * ------------------------------------------------------------------------ */
+typedef uint64_t wg_ticket;
+#define WG_REQ_FORWARD 0    /* forward trace: tally and statistics */
+#define WG_REQ_LOSS_GRAD 1  /* forward + loss (Eq. 1) + adjoint: loss terms and thickness gradient */
+
+typedef struct wg_request {
+  int32_t kind;             /* WG_REQ_* */
+  int32_t loss_kind;        /* LOSS_GRAD: 0 = coefficient of variation (the paper's), 1 = variance */
+  double w_f, w_e;          /* LOSS_GRAD: weights of U_FoV and U_eyebox */
+  const wg_design* design;
+  wg_trace_cfg cfg;         /* copied with its arrays; stream, ray_records are ignored */
+  double* tally;            /* NULL or host/device [tally size]: the forward tally */
+  double* grad_thickness;   /* LOSS_GRAD: NULL or host/device [sum of layers] */
+  double* loss;             /* LOSS_GRAD: NULL or host [4]: L, I_mean, U_FoV, U_eyebox */
+} wg_request;
+
+typedef struct wg_result {
+  wg_status status;         /* of the evaluation: WG_OK, WG_ECANCELED or its error */
+  int32_t batch_size;       /* requests in the batch that served it */
+  int32_t graph_replayed;   /* 1 if the batch's forward replayed a captured CUDA graph */
+  int32_t pad;
+  double queue_ms;          /* submit -> start of its batch (host clock) */
+  double run_ms;            /* start of its batch -> completion */
+  wg_stats stats;           /* forward statistics of this request (kernel_ms: its fused launches) */
+} wg_result;
+
+/* WG_EINVAL (bad request), WG_ENOMEM (needs more device memory than the
+ * budget: can never be admitted), WG_EBUSY (queue full: 4096 pending). The
+ * output buffers must stay valid until the ticket is done. */
+wg_status wg_submit(wg_ctx* ctx, const wg_request* req, wg_ticket* ticket);
+/* Waits up to timeout_us (0: no wait, < 0: forever) for the ticket. WG_OK:
+ * done, *out filled and the ticket released; WG_ENOTREADY: still pending;
+ * WG_ENOTFOUND: unknown or already released ticket. */
+wg_status wg_poll(wg_ctx* ctx, wg_ticket ticket, int64_t timeout_us, wg_result* out);
+/* A queued request is dropped; a running one completes with its outputs
+ * unspecified. Its wg_poll then reports status WG_ECANCELED. */
+wg_status wg_cancel(wg_ctx* ctx, wg_ticket ticket);
+/* Times the forward kernel's chunk size and CTAs per SM on (a bounded sample
+ * of) this evaluation and stores the fastest for its class (fields per ray,
+ * material period, layers per mirror, rays per cell) in the context's table,
+ * and in wg_init_opts.autotune_cache when given. The scheduler tunes classes
+ * it has not seen on their first batch. */
+wg_status wg_autotune(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cfg);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,6 +15,7 @@
 
 #include "wg.h"
 #include "wg_device.cuh"
+#include "wg_host.h"
 #include "wg_internal.h"
 
 using namespace wgk;
@@ -77,7 +78,10 @@ struct wg_ctx {
   cudaEvent_t t0 = nullptr, t1 = nullptr;
   int max_slots = 64;
   size_t hbm_budget = 0;
+  std::string autotune_cache;
   std::vector<wg_design*> designs;
+  DevBuf fws;     // fused-forward workspace (per-job heads, configuration arrays, job table)
+  void* serve = nullptr;  // serving runtime state (wg_serve.cu)
 };
 
 struct wg_design {
@@ -134,6 +138,7 @@ extern "C" wg_status wg_init(wg_ctx** out, const wg_init_opts* opts) {
   c->sm_count = prop.multiProcessorCount;
   if (opts && opts->max_slots > 0) c->max_slots = opts->max_slots;
   if (opts) c->hbm_budget = opts->hbm_budget_bytes;
+  if (opts && opts->autotune_cache) c->autotune_cache = opts->autotune_cache;
   if (cudaEventCreateWithFlags(&c->ws_free, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreate(&c->t0) != cudaSuccess || cudaEventCreate(&c->t1) != cudaSuccess) {
     delete c;
@@ -156,6 +161,7 @@ static void destroy_design_dev(wg_design* d) {
 
 extern "C" void wg_shutdown(wg_ctx* c) {
   if (!c) return;
+  wgh::serve_shutdown(c);  // stops the scheduler thread first: it uses the context
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
   for (wg_design* d : c->designs) {
@@ -165,6 +171,7 @@ extern "C" void wg_shutdown(wg_ctx* c) {
   c->ws.release();
   c->bwd.release();
   c->loss.release();
+  c->fws.release();
   if (c->ws_free) cudaEventDestroy(c->ws_free);
   if (c->t0) cudaEventDestroy(c->t0);
   if (c->t1) cudaEventDestroy(c->t1);
@@ -695,6 +702,346 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
   if (stats || !dev_tally) return finish_stats(c, w, s, stats, stats != nullptr);
   return WG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// fused multi-design forward (serving runtime)
+// ---------------------------------------------------------------------------
+namespace wgh {
+
+wg_status set_error(wg_status st, const char* msg) { return fail(st, "%s", msg); }
+int ctx_device(const wg_ctx* c) { return c->device; }
+int ctx_sm_count(const wg_ctx* c) { return c->sm_count; }
+int ctx_max_slots(const wg_ctx* c) { return c->max_slots; }
+size_t ctx_hbm_budget(const wg_ctx* c) { return c->hbm_budget; }
+const char* ctx_autotune_cache(const wg_ctx* c) { return c->autotune_cache.empty() ? nullptr : c->autotune_cache.c_str(); }
+void** ctx_serve_slot(wg_ctx* c) { return &c->serve; }
+const void* fused_dev_base(const wg_ctx* c) { return c->fws.p; }
+long long design_params(const wg_design* d) { return d->n_orig; }
+void design_shape(const wg_design* d, int* K, int* n_dev, int* period) {
+  *K = d->K;
+  *n_dev = d->n_dev;
+  *period = d->period;
+}
+
+long long tally_doubles(const wg_design* d, const wg_trace_cfg* cfg) {
+  Plan p;
+  if (make_plan(d, cfg, 2048, p) != WG_OK) return -1;
+  return p.tally_size;
+}
+
+size_t eval_device_bytes(const wg_design* d, const wg_trace_cfg* cfg, bool backward) {
+  Plan p;
+  if (make_plan(d, cfg, 2048, p) != WG_OK) return 0;
+  const long long rays = p.re - p.rb;
+  size_t b = sizeof(double) * (size_t)p.tally_size;      // tally
+  b += 64 + sizeof(ExitRec) * (size_t)rays;              // eyebox-ray list
+  if (backward) {
+    b += sizeof(double) * (size_t)p.tally_size;          // dL/dtally
+    const long long batch = std::min<long long>(rays, 1ll << 22);
+    b += 2 * (size_t)batch * 16 * hit_rec_bytes();       // hit records of one replay batch (and sorted copy)
+  }
+  return b;
+}
+
+// Pinned host staging of a fused launch: per-job configuration arrays, the
+// job table and the CTA-to-job map (copied to the device by stream-ordered
+// copies that a CUDA graph can capture), and the per-job heads read back.
+struct FusedPinned {
+  void* p = nullptr;
+  size_t n = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= n) return cudaSuccess;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    n = 0;
+    cudaError_t e = cudaMallocHost(&p, bytes);
+    if (e == cudaSuccess) n = bytes;
+    return e;
+  }
+  ~FusedPinned() {
+    if (p) cudaFreeHost(p);
+  }
+};
+
+// per-job workspace heads of a fused launch, contiguous at this stride
+static const size_t kHeadStride = 256;
+// a fused launch has this many times the CTAs the GPU holds at once
+static const int kOversub = 4;
+
+struct FusedBatch::Impl {
+  FusedPinned pin;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;  // around the fused launches (recorded by graph replays too)
+  size_t dev_bytes = 0;
+  struct Copy {
+    size_t src, dst, bytes;  // pinned offset -> device offset
+  };
+  std::vector<Copy> copies;
+  struct Group {
+    int F, P, grid, first, cta0;
+    size_t smem;
+  };
+  std::vector<Group> groups;
+  std::vector<Plan> plans;
+  std::vector<WsLayout> lay;
+  std::vector<TraceArgs> args;
+  size_t heads_pin = 0;  // pinned offset of the heads read back
+  size_t tab_dev = 0, cta_dev = 0;
+  int n = 0;
+};
+
+FusedBatch::FusedBatch() : impl(new Impl) {}
+FusedBatch::~FusedBatch() {
+  if (impl->e0) cudaEventDestroy(impl->e0);
+  if (impl->e1) cudaEventDestroy(impl->e1);
+  delete impl;
+}
+
+wg_status fused_prepare(wg_ctx* c, FusedJob* jobs, int n, int blocks_per_sm, FusedBatch& fb) {
+  if (!c || !jobs || n < 1) return fail(WG_EINVAL, "fused forward: no jobs");
+  FusedBatch::Impl& B = *fb.impl;
+  B.n = n;
+  B.plans.assign(n, Plan());
+  B.lay.assign(n, WsLayout());
+  B.args.assign(n, TraceArgs());
+  B.copies.clear();
+  B.groups.clear();
+  std::vector<size_t> smem(n);
+  for (int j = 0; j < n; ++j) {
+    FusedJob& J = jobs[j];
+    J.status = WG_OK;
+    memset(&J.stats, 0, sizeof(J.stats));
+    if (!J.design || !J.cfg || !J.tally) return fail(WG_EINVAL, "fused forward: job %d incomplete", j);
+    Plan& p = B.plans[j];
+    wg_status st = make_plan(J.design, J.cfg, 2048, p);
+    if (st != WG_OK) return st;
+    p.chunk_rays = J.chunk_rays > 0 ? std::min<long long>(J.chunk_rays, p.n_cell) : default_chunk(p);
+    p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
+    p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
+    smem[j] = fwd_smem_bytes(J.design->blob_bytes, p.bins, p.F);
+    if (smem[j] > 200 * 1024) return fail(WG_EINVAL, "fused forward: job %d design + eyebox too large", j);
+  }
+  // device arena: heads (contiguous) | per-job arrays | job table | CTA map;
+  // the pinned buffer mirrors the same offsets for what is copied in
+  const int max_grid = c->sm_count * 2;
+  // <= 6 groups, each <= kOversub * G + 1.5 n_g CTAs
+  const size_t max_ctas = 6 * (size_t)kOversub * (size_t)max_grid + 2 * (size_t)n;
+  size_t off = align16((size_t)n * kHeadStride);
+  std::vector<size_t> job_off(n);
+  for (int j = 0; j < n; ++j) {
+    job_off[j] = off;
+    off += align16(ws_layout(nullptr, jobs[j].cfg, B.plans[j].n_f).bytes - 256);
+  }
+  B.tab_dev = off;
+  off += align16(sizeof(TraceArgs) * (size_t)n);
+  B.cta_dev = off;
+  off += align16(sizeof(int) * max_ctas);
+  B.dev_bytes = off;
+  B.heads_pin = off;  // pinned: same layout plus the heads read back at the end
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    CU(cudaSetDevice(c->device));
+    if (off > c->fws.n) {
+      CU(cudaEventSynchronize(c->ws_free));
+      CU(c->fws.ensure(off + 4096));
+    }
+  }
+  CU(B.pin.ensure(off + (size_t)kHeadStride * (size_t)n));
+  if (!B.e0) CU(cudaEventCreate(&B.e0));
+  if (!B.e1) CU(cudaEventCreate(&B.e1));
+  uint8_t* dev = static_cast<uint8_t*>(c->fws.p);
+  uint8_t* pin = static_cast<uint8_t*>(B.pin.p);
+  // a design evaluated twice in one batch keeps no eyebox-ray list (one list per design)
+  std::vector<int> dup(n, 0);
+  for (int j = 0; j < n; ++j)
+    for (int k = 0; k < n; ++k)
+      if (k != j && jobs[k].design == jobs[j].design) dup[j] = 1;
+  for (int j = 0; j < n; ++j) {
+    FusedJob& J = jobs[j];
+    const Plan& p = B.plans[j];
+    WsLayout w = ws_layout(dev + job_off[j] - 256, J.cfg, p.n_f);
+    w.head = reinterpret_cast<WsHead*>(dev + kHeadStride * (size_t)j);
+    B.lay[j] = w;
+    const size_t o_lam = (size_t)((uint8_t*)w.lam - dev), o_fx = (size_t)((uint8_t*)w.fx - dev),
+                 o_fy = (size_t)((uint8_t*)w.fy - dev);
+    memcpy(pin + o_lam, J.cfg->lambda_nm, sizeof(float) * J.cfg->n_lambda);
+    memcpy(pin + o_fx, J.cfg->field_x_deg, sizeof(float) * J.cfg->n_fx);
+    memcpy(pin + o_fy, J.cfg->field_y_deg, sizeof(float) * J.cfg->n_fy);
+    B.copies.push_back({o_lam, o_lam, (size_t)((uint8_t*)w.fields - (uint8_t*)w.lam)});  // lam, fx, fy together
+    TraceArgs a = base_args(J.design, J.cfg, p, w);
+    a.tally = J.tally;
+    a.records = nullptr;
+    if (dup[j]) {
+      const_cast<wg_design*>(J.design)->exit_fp = 0;
+    } else if (!(J.cfg->flags & WG_TRACE_NO_EXIT_LIST)) {
+      wg_design* dm = const_cast<wg_design*>(J.design);
+      dm->exit_fp = 0;
+      const long long nr = p.re - p.rb;
+      const size_t bytes = kExitHead + sizeof(ExitRec) * (size_t)nr;
+      if (bytes <= ((size_t)8 << 30)) {
+        std::lock_guard<std::mutex> lk(c->mu);
+        if (bytes > dm->exits.n) CU(dm->exits.ensure(bytes));
+        a.exit_count = static_cast<unsigned long long*>(dm->exits.p);
+        a.exit_list = reinterpret_cast<ExitRec*>(static_cast<uint8_t*>(dm->exits.p) + kExitHead);
+        a.exit_cap = nr;
+      }
+    }
+    B.args[j] = a;
+  }
+  // groups of jobs sharing the kernel variant (fields per ray, material period)
+  std::vector<int> order(n);
+  for (int j = 0; j < n; ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+    return B.plans[x].F * 4 + jobs[x].design->period < B.plans[y].F * 4 + jobs[y].design->period;
+  });
+  TraceArgs* tab_h = reinterpret_cast<TraceArgs*>(pin + B.tab_dev);
+  int* cta_h = reinterpret_cast<int*>(pin + B.cta_dev);
+  size_t n_cta = 0;
+  for (size_t g0 = 0; g0 < order.size();) {
+    size_t g1 = g0;
+    const int F = B.plans[order[g0]].F, P = jobs[order[g0]].design->period;
+    size_t sm_max = 0;
+    double cost = 0.0;
+    auto job_cost = [&](int j) {
+      const double layers = (double)jobs[j].design->n_dev / std::max(1, jobs[j].design->K);
+      return (double)(B.plans[j].re - B.plans[j].rb) * (10.0 + layers);
+    };
+    while (g1 < order.size() && B.plans[order[g1]].F == F && jobs[order[g1]].design->period == P) {
+      sm_max = std::max(sm_max, smem[order[g1]]);
+      cost += job_cost(order[g1]);
+      ++g1;
+    }
+    int bps = std::max(1, trace_fwd_blocks_per_sm(F, P, sm_max));
+    if (blocks_per_sm > 0) bps = std::min(bps, blocks_per_sm);
+    const int G = c->sm_count * bps;
+    FusedBatch::Impl::Group gr{F, P, 0, (int)g0, (int)n_cta, sm_max};
+    // CTAs per job in proportion to its estimated work (at least one, at most
+    // its chunks), kOversub times what the GPU holds at once, in an order
+    // that interleaves the jobs: a job's CTAs exit when its chunks are gone
+    // and the hardware then starts pending CTAs, which belong to every job,
+    // so the jobs that are still running get the freed SMs
+    std::vector<std::pair<double, int>> seq;
+    for (size_t q = g0; q < g1; ++q) {
+      const int j = order[q];
+      long long k = (long long)std::llround((double)kOversub * G * job_cost(j) / std::max(cost, 1.0));
+      k = std::max<long long>(1, std::min<long long>(k, B.plans[j].n_chunks));
+      B.args[j].n_cta = (int)k;
+      tab_h[q] = B.args[j];
+      for (long long b = 0; b < k; ++b) seq.push_back({((double)b + 0.5) / (double)k, (int)q});
+    }
+    std::stable_sort(seq.begin(), seq.end());
+    for (const auto& e : seq)
+      if (n_cta < max_ctas) cta_h[n_cta++] = e.second;
+    gr.grid = (int)(n_cta - (size_t)gr.cta0);
+    B.groups.push_back(gr);
+    g0 = g1;
+  }
+  B.copies.push_back({B.tab_dev, B.tab_dev, sizeof(TraceArgs) * (size_t)n});
+  B.copies.push_back({B.cta_dev, B.cta_dev, sizeof(int) * n_cta});
+  return WG_OK;
+}
+
+wg_status fused_enqueue(wg_ctx* c, FusedJob* jobs, FusedBatch& fb, cudaStream_t s) {
+  FusedBatch::Impl& B = *fb.impl;
+  uint8_t* dev = static_cast<uint8_t*>(c->fws.p);
+  const uint8_t* pin = static_cast<const uint8_t*>(B.pin.p);
+  std::lock_guard<std::mutex> lk(c->mu);
+  CU(cudaSetDevice(c->device));
+  CU(cudaMemsetAsync(dev, 0, (size_t)B.n * kHeadStride, s));
+  for (const auto& cp : B.copies) CU(cudaMemcpyAsync(dev + cp.dst, pin + cp.src, cp.bytes, cudaMemcpyHostToDevice, s));
+  for (int j = 0; j < B.n; ++j) {
+    const FusedJob& J = jobs[j];
+    const Plan& p = B.plans[j];
+    const WsLayout& w = B.lay[j];
+    CU(launch_prep_fields(w.fields, w.fx, w.fy, J.cfg->n_fx, J.cfg->n_fy, J.design->n_slab, J.design->ic_tilt,
+                          J.design->dims, s));
+    CU(cudaMemsetAsync(J.tally + p.cell_lo * p.bins, 0, sizeof(double) * (p.cell_hi - p.cell_lo + 1) * p.bins, s));
+    if (B.args[j].exit_count) CU(cudaMemsetAsync(B.args[j].exit_count, 0, sizeof(unsigned long long), s));
+  }
+  const TraceArgs* tab = reinterpret_cast<const TraceArgs*>(dev + B.tab_dev);
+  const int* cta = reinterpret_cast<const int*>(dev + B.cta_dev);
+  CU(cudaEventRecord(B.e0, s));
+  for (const auto& g : B.groups) CU(launch_trace_fwd_fused(tab, cta + g.cta0, g.F, g.P, g.grid, g.smem, s));
+  CU(cudaEventRecord(B.e1, s));
+  CU(cudaMemcpyAsync(static_cast<uint8_t*>(B.pin.p) + B.heads_pin, dev, (size_t)kHeadStride * (size_t)B.n,
+                     cudaMemcpyDeviceToHost, s));
+  return WG_OK;
+}
+
+wg_status fused_finish(wg_ctx* c, FusedJob* jobs, FusedBatch& fb) {
+  FusedBatch::Impl& B = *fb.impl;
+  const uint8_t* heads = static_cast<const uint8_t*>(B.pin.p) + B.heads_pin;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, B.e0, B.e1) != cudaSuccess) cudaGetLastError();
+  for (int j = 0; j < B.n; ++j) {
+    const WsHead& h = *reinterpret_cast<const WsHead*>(heads + (size_t)kHeadStride * (size_t)j);
+    wg_stats& st = jobs[j].stats;
+    jobs[j].status = h.error ? WG_ETIMEOUT : WG_OK;
+    jobs[j].error_word = h.error;
+    jobs[j].n_cta = B.args[j].n_cta;
+    jobs[j].n_chunks = B.plans[j].n_chunks;
+    st.n_rays = (int64_t)h.counters[0];
+    st.n_hits = (int64_t)h.counters[1];
+    st.n_events = (int64_t)h.counters[2];
+    st.n_tir = (int64_t)h.counters[3];
+    st.n_layer_steps = (int64_t)h.counters[4];
+    for (int i = 0; i < 6; ++i) st.ledger[i] = h.ledger[i];
+    st.kernel_ms = ms;
+    if (B.args[j].exit_list)
+      const_cast<wg_design*>(jobs[j].design)->exit_fp = path_fingerprint(jobs[j].design, jobs[j].cfg, B.plans[j]);
+  }
+  return WG_OK;
+}
+
+// Everything fused_enqueue bakes into a captured graph besides what it copies
+// from the pinned buffer: device and pinned addresses, copy and memset
+// extents, kernel launch shapes and the per-job preparation arguments.
+uint64_t fused_signature(const wg_ctx* c, const FusedJob* jobs, const FusedBatch& fb) {
+  const FusedBatch::Impl& B = *fb.impl;
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void* x, size_t n) {
+    const uint8_t* b = static_cast<const uint8_t*>(x);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  };
+  auto mixv = [&](auto v) { mix(&v, sizeof(v)); };
+  mixv(c->fws.p);
+  mixv(B.pin.p);
+  mixv(B.n);
+  for (const auto& cp : B.copies) mix(&cp, sizeof(cp));
+  for (const auto& g : B.groups) {
+    mixv(g.F), mixv(g.P), mixv(g.grid), mixv(g.first), mixv(g.cta0), mixv(g.smem);
+  }
+  for (int j = 0; j < B.n; ++j) {
+    const Plan& p = B.plans[j];
+    mixv(jobs[j].tally), mixv(p.cell_lo), mixv(p.cell_hi), mixv(p.bins);
+    mixv(B.args[j].exit_count);
+    mixv(B.lay[j].fields), mixv(jobs[j].cfg->n_fx), mixv(jobs[j].cfg->n_fy);
+    mixv(jobs[j].design->n_slab), mixv(jobs[j].design->ic_tilt), mixv(jobs[j].design->dims);
+  }
+  return h;
+}
+
+wg_status fused_forward(wg_ctx* c, FusedJob* jobs, int n, int blocks_per_sm, cudaStream_t s) {
+  FusedBatch fb;
+  wg_status st = fused_prepare(c, jobs, n, blocks_per_sm, fb);
+  if (st != WG_OK) return st;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    CU(cudaStreamWaitEvent(s, c->ws_free, 0));
+  }
+  st = fused_enqueue(c, jobs, fb, s);
+  if (st != WG_OK) return st;
+  {
+    std::lock_guard<std::mutex> lk(c->mu);
+    CU(cudaEventRecord(c->ws_free, s));
+  }
+  CU(cudaStreamSynchronize(s));
+  return fused_finish(c, jobs, fb);
+}
+
+}  // namespace wgh
 
 // chunk layout of the ray range [rb, re) (cells touched, chunks per cell)
 static void plan_range(Plan& p, long long rb, long long re) {

@@ -56,6 +56,7 @@ struct TraceArgs {
   // backward: replay the list entries [list_begin, list_end) instead of a ray range (null: ray range)
   const ExitRec* replay_list;
   long long list_begin, list_end;
+  int n_cta;                  // CTAs of the launch working on this job
 };
 
 // Arguments of the thin-film adjoint over sorted hit records.
@@ -95,6 +96,10 @@ cudaError_t launch_prep_design(uint8_t* blob, const float* mir_x, const float* m
 cudaError_t launch_prep_fields(FieldRec* out, const float* fx, const float* fy, int n_fx, int n_fy,
                                float n_slab, float ic_tilt_deg, int dims, cudaStream_t s);
 cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s);
+// several jobs (designs / configurations with the same F and P) in one
+// launch: CTA b works on job cta_job[b] (device arrays; each job's n_cta set)
+cudaError_t launch_trace_fwd_fused(const TraceArgs* jobs_dev, const int* cta_job_dev, int F, int P, int grid,
+                                   size_t smem, cudaStream_t s);
 cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_bwd_sort(const HitRec* in, long long n, unsigned int* key_count, unsigned int* key_off,
                             unsigned int* key_cursor, HitRec* out, cudaStream_t s);

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstring>
 
 #include "wg_device.cuh"
 #include "wg_internal.h"
@@ -669,12 +670,18 @@ __device__ __forceinline__ int q_get(const uint32_t* q, unsigned i, Ray<F>& R, l
 }
 
 template <int F, int P>
-__global__ void __launch_bounds__(kBlock, 2) k_trace_fwd(const TraceArgs A) {
+__global__ void __launch_bounds__(kBlock, 2)
+    k_trace_fwd(const TraceArgs A0, const TraceArgs* __restrict__ jobs, const int* __restrict__ cta_job) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_mbar;
   __shared__ FwdRing S;
   __shared__ float s_led[6];
   __shared__ unsigned long long s_cnt[8];
+  // this CTA's job: one design + configuration for the whole launch (a fused
+  // launch gives each job its own range of CTAs; jobs == null: the one job A0)
+  __shared__ TraceArgs A;
+  if (threadIdx.x == 0) A = jobs ? jobs[cta_job[blockIdx.x]] : A0;
+  __syncthreads();
   constexpr int NW = 9 + 4 * F;
   float* s_tally = reinterpret_cast<float*>(smem + A.blob_bytes);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -716,7 +723,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_trace_fwd(const TraceArgs A) {
   // traces (plus bounded idle waits); past this cap it flags and stops
   const unsigned long long it_cap =
       4ull * (unsigned long long)A.max_events *
-          (unsigned long long)((A.ray_end - A.ray_begin) / ((long long)gridDim.x * (kBlock / 32)) + 256) +
+          (unsigned long long)((A.ray_end - A.ray_begin) / ((long long)max(1, A.n_cta) * (kBlock / 32)) + 256) +
       (1ull << 24);
   unsigned long long iters = 0;
   for (;;) {
@@ -1491,7 +1498,20 @@ cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int grid, size_t 
   auto k = WG_PICK_FP(k_trace_fwd, F, P);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   note_launches(1);
-  k<<<grid, kBlock, smem, s>>>(a);
+  TraceArgs a1 = a;
+  a1.n_cta = grid;
+  k<<<grid, kBlock, smem, s>>>(a1, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_fwd_fused(const TraceArgs* jobs_dev, const int* cta_job_dev, int F, int P, int grid,
+                                   size_t smem, cudaStream_t s) {
+  auto k = WG_PICK_FP(k_trace_fwd, F, P);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  note_launches(1);
+  TraceArgs unused;
+  memset(&unused, 0, sizeof(unused));
+  k<<<grid, kBlock, smem, s>>>(unused, jobs_dev, cta_job_dev);
   return cudaGetLastError();
 }
 

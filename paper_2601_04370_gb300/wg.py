@@ -71,6 +71,25 @@ class Stats(C.Structure):
                     n_nonfinite=self.n_nonfinite)
 
 
+# serving (include/wg.h)
+REQ_FORWARD, REQ_LOSS_GRAD = 0, 1
+
+
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("loss_kind", C.c_int32), ("w_f", C.c_double), ("w_e", C.c_double),
+                ("design", C.c_void_p), ("cfg", TraceCfg), ("tally", C.c_void_p), ("grad_thickness", C.c_void_p),
+                ("loss", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("batch_size", C.c_int32), ("graph_replayed", C.c_int32),
+                ("pad", C.c_int32), ("queue_ms", C.c_double), ("run_ms", C.c_double), ("stats", Stats)]
+
+    def to_dict(self):
+        return dict(status=self.status, batch_size=self.batch_size, graph_replayed=bool(self.graph_replayed),
+                    queue_ms=self.queue_ms, run_ms=self.run_ms, stats=self.stats.to_dict())
+
+
 # wg_trace_cfg.flags bits (include/wg.h)
 TRACE_NO_EXIT_LIST = 1  # forward: do not list the eyebox rays for the adjoint
 
@@ -105,8 +124,13 @@ def lib():
         L.wg_trace_backward.argtypes = [vp, vp, C.POINTER(TraceCfg), vp, vp, vp, C.POINTER(Stats)]
         L.wg_loss.argtypes = [vp, vp, C.POINTER(TraceCfg), i32, C.c_double, C.c_double, vp, dp, vp]
         L.wg_trace_forward_noalloc.argtypes = [vp, vp, C.POINTER(TraceCfg), vp, C.POINTER(Stats)]
+        L.wg_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]
+        L.wg_poll.argtypes = [vp, C.c_uint64, i64, C.POINTER(Result)]
+        L.wg_cancel.argtypes = [vp, C.c_uint64]
+        L.wg_autotune.argtypes = [vp, vp, C.POINTER(TraceCfg)]
         for name in ("wg_init", "wg_create_design", "wg_set_params", "wg_eval_coating", "wg_eval_coating_grad",
-                     "wg_trace_forward", "wg_trace_backward", "wg_loss", "wg_trace_forward_noalloc"):
+                     "wg_trace_forward", "wg_trace_backward", "wg_loss", "wg_trace_forward_noalloc",
+                     "wg_submit", "wg_poll", "wg_cancel", "wg_autotune"):
             getattr(L, name).restype = C.c_int32
         _lib = L
     return _lib
@@ -182,9 +206,12 @@ class DesignHandle:
 
 
 class Context:
-    def __init__(self, device: int = 0, max_slots: int = 0, hbm_budget_bytes: int = 0):
+    def __init__(self, device: int = 0, max_slots: int = 0, hbm_budget_bytes: int = 0,
+                 autotune_cache: Optional[str] = None):
         h = C.c_void_p()
-        opts = InitOpts(device=device, max_slots=max_slots, hbm_budget_bytes=hbm_budget_bytes, autotune_cache=None)
+        self._cache = autotune_cache.encode() if autotune_cache else None
+        opts = InitOpts(device=device, max_slots=max_slots, hbm_budget_bytes=hbm_budget_bytes,
+                        autotune_cache=self._cache)
         _check(lib().wg_init(C.byref(h), C.byref(opts)))
         self.h = h
         self.device = device
@@ -193,6 +220,34 @@ class Context:
         if self.h:
             lib().wg_shutdown(self.h)
             self.h = None
+
+    # ---- serving ----
+    def submit(self, dh, cfg, kind=REQ_FORWARD, tally=None, grad=None, loss=None, loss_kind=0, w_f=10.0, w_e=3.0):
+        """wg_submit: returns a ticket. tally / grad: host (numpy float64) or
+        device (torch float64) buffers, loss: numpy float64[4]; they must stay
+        alive until the ticket is polled done."""
+        h = _CfgHolder(cfg, None)
+        r = Request(kind=kind, loss_kind=loss_kind, w_f=w_f, w_e=w_e, design=dh.h, cfg=h.c, tally=_ptr(tally),
+                    grad_thickness=_ptr(grad), loss=_ptr(loss))
+        t = C.c_uint64()
+        _check(lib().wg_submit(self.h, C.byref(r), C.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket, timeout_us=-1):
+        """wg_poll: the result dict when done, None while pending (timeout)."""
+        res = Result()
+        st = lib().wg_poll(self.h, ticket, int(timeout_us), C.byref(res))
+        if st == WG_ENOTREADY:
+            return None
+        _check(st)
+        return res.to_dict()
+
+    def cancel(self, ticket):
+        _check(lib().wg_cancel(self.h, ticket))
+
+    def autotune(self, dh, cfg):
+        h = _CfgHolder(cfg, None)
+        _check(lib().wg_autotune(self.h, dh.h, C.byref(h.c)))
 
     def __enter__(self):
         return self

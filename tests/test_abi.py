@@ -28,7 +28,8 @@ def libwg():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for n in ("wg_init", "wg_shutdown", "wg_create_design", "wg_set_params", "wg_destroy_design",
-              "wg_eval_coating", "wg_trace_forward", "wg_trace_backward", "wg_loss", "wg_last_error"):
+              "wg_eval_coating", "wg_trace_forward", "wg_trace_backward", "wg_loss", "wg_last_error",
+              "wg_submit", "wg_poll", "wg_cancel", "wg_autotune"):
         assert n in names
 
 
@@ -63,6 +64,8 @@ int main(void) {
          sizeof(wg_stats), sizeof(wg_ray_record));
   printf("%zu %zu %zu\n", offsetof(wg_trace_cfg, stream), offsetof(wg_trace_cfg, ray_records),
          offsetof(wg_stats, kernel_ms));
+  printf("%zu %zu %zu %zu\n", sizeof(wg_request), sizeof(wg_result), offsetof(wg_request, cfg),
+         offsetof(wg_result, stats));
   return 0;
 }
 '''
@@ -72,9 +75,11 @@ int main(void) {
     exe = os.path.join(tmp, "abi_sizes")
     open(c, "w").write(code)
     subprocess.check_call(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
-    a, b = subprocess.check_output([exe], text=True).strip().splitlines()
+    a, b, c2 = subprocess.check_output([exe], text=True).strip().splitlines()
     sizes = [int(x) for x in a.split()]
     offs = [int(x) for x in b.split()]
     assert sizes == [ctypes.sizeof(wg.InitOpts), ctypes.sizeof(wg.DesignDesc), ctypes.sizeof(wg.TraceCfg),
                      ctypes.sizeof(wg.Stats), wg.RAY_RECORD_DTYPE.itemsize]
     assert offs == [wg.TraceCfg.stream.offset, wg.TraceCfg.ray_records.offset, wg.Stats.kernel_ms.offset]
+    assert [int(x) for x in c2.split()] == [ctypes.sizeof(wg.Request), ctypes.sizeof(wg.Result),
+                                             wg.Request.cfg.offset, wg.Result.stats.offset]
