@@ -262,15 +262,22 @@ wg_status wg_loss(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cfg, int3
                   double w_e, const double* tally, double* out, double* dL_dtally);
 
 /*
- * Adjoint of the trace with respect to layer thicknesses: replays every ray
- * from its Philox key (nothing is stored by the forward pass), propagates
- * G[bin] dI/dE backwards through the ray's Jones maps, and back-propagates
- * each hit's coefficient sensitivity through the characteristic-matrix chain
- * (checkpointed forward products, no matrix inversion). The sampled path is
- * held fixed (the sampling does not depend on the thicknesses).
- * dL_dtally: host or device FP64 in tally layout. grad_thickness: host or
- * device FP64 [sum n_layers] (pruned layers get 0), overwritten. grad_tilt:
- * reserved, must be NULL. Errors: WG_EINVAL, WG_ENOMEM, WG_EDEVICE.
+ * Adjoint of the trace with respect to layer thicknesses and mirror tilts
+ * (Fig. 3b/c): replays the rays from their Philox keys (only the forward's
+ * listed eyebox rays whose bins carry gradient when the list matches, see
+ * WG_TRACE_NO_EXIT_LIST; every ray otherwise), propagates G[bin] dI/dE
+ * backwards through each ray's Jones maps and back-propagates each hit's
+ * coefficient sensitivity through the characteristic-matrix chain
+ * (checkpointed forward products, no matrix inversion). The sampled path
+ * (keys, surfaces, decisions, TIR counts, bin) is held fixed: exact for the
+ * thicknesses, which the sampling does not depend on; for the tilts it is
+ * the derivative along the fixed path (a ray whose path or bin would change
+ * contributes only that). dL_dtally: host or device FP64 in tally layout.
+ * grad_thickness: host or device FP64 [sum n_layers] (pruned layers get 0),
+ * overwritten. grad_tilt: NULL, or host or device FP64 [n_mirrors],
+ * overwritten with dL/d(tilt) per degree (forward-mode tangents of every
+ * ray's directions and fields, 8 mirrors per replay pass).
+ * Errors: WG_EINVAL, WG_ENOMEM, WG_EDEVICE, WG_ETIMEOUT.
  */
 wg_status wg_trace_backward(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cfg,
                             const double* dL_dtally, double* grad_thickness, double* grad_tilt,

@@ -1070,7 +1070,6 @@ static const long long kReplayUnit = 64;     // rays per work unit of the replay
 extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, const double* dL_dtally,
                                        double* grad_thickness, double* grad_tilt, wg_stats* stats) {
   if (!c || !d || !dL_dtally || !grad_thickness) return fail(WG_EINVAL, "wg_trace_backward: NULL argument");
-  if (grad_tilt) return fail(WG_EINVAL, "wg_trace_backward: grad_tilt is reserved and must be NULL");
   Plan p;
   wg_status st = make_plan(d, cfg, 2048, p);
   if (st != WG_OK) return st;
@@ -1193,6 +1192,36 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     b0 = b1;
   }
   CU(launch_scatter_grad(sc.grad_acc, d->n_dev, d->d_dev_to_orig, gout, s));
+  if (grad_tilt) {
+    // mirror tilts: forward-mode tangents over the same rays, 8 mirrors per pass
+    const bool dev_t = is_device_ptr(grad_tilt);
+    double* gt = grad_tilt;
+    if (!dev_t) CU(cudaMallocAsync((void**)&gt, sizeof(double) * d->K, s));
+    CU(cudaMemsetAsync(gt, 0, sizeof(double) * d->K, s));
+    const size_t smem_t = tilt_smem_bytes(d->blob_bytes, p.F);
+    const int bps_t = std::max(1, tilt_blocks_per_sm(p.F, d->period, smem_t));
+    const long long items = use_list ? n_list : p.re - p.rb;
+    for (int k0 = 0; k0 < d->K && items > 0; k0 += 8) {
+      Plan q = p;
+      if (!use_list) plan_range(q, p.rb, p.re);
+      TraceArgs a = base_args(d, cfg, q, w);
+      a.G = G;
+      a.grad_tilt = gt;
+      a.tilt_k0 = k0;
+      if (use_list) {
+        a.replay_list = list;
+        a.list_begin = 0;
+        a.list_end = n_list;
+      }
+      const int grid = (int)std::max<long long>(1, std::min<long long>((items + 127) / 128, (long long)c->sm_count * bps_t));
+      CU(launch_tilt_grad(a, p.F, d->period, grid, smem_t, s));
+    }
+    if (!dev_t) {
+      CU(cudaMemcpyAsync(grad_tilt, gt, sizeof(double) * d->K, cudaMemcpyDeviceToHost, s));
+      CU(cudaFreeAsync(gt, s));
+      CU(cudaStreamSynchronize(s));
+    }
+  }
   CU(cudaEventRecord(c->ws_free, s));
   if (!dev_G) CU(cudaFreeAsync((void*)G, s));
   if (!dev_g) {

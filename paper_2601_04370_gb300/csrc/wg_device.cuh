@@ -658,4 +658,191 @@ __device__ __forceinline__ void tir_coef(float n, float ci, float sin2, float2& 
 
 __device__ __forceinline__ uint32_t fnv(uint32_t h, uint32_t b) { return (h ^ b) * 16777619u; }
 
+// ---------------------------------------------------------------------------
+// Forward-mode derivatives for the mirror-tilt gradient. The sampled path is
+// held fixed (keys, surfaces, decisions, TIR counts, tally bin), so a tilt
+// acts through the incidence angles (the coefficients of every layer stack),
+// the local s/p bases, the reflected directions and the angle-dependent TIR
+// and exit Fresnel factors; positions do not reach the intensity.
+// ---------------------------------------------------------------------------
+// d/d(cos t0) of a material's constants (value k, the same branch)
+struct MatKD {
+  float dkt, dq12s, dq21s, dq12p, dq21p;
+};
+__device__ __forceinline__ MatKD mat_const_d(const MatK& k, float cos0, float n, float inv_n, float r2,
+                                             float inv_lam) {
+  const float drad = 2.0f * r2 * cos0;  // rad = 1 - r2 (1 - cos0^2)
+  MatKD D;
+  if (!k.evan) {
+    const float eta = k.q21s, ct = fmaxf(eta * inv_n, 1e-20f);
+    const float dct = 0.5f * drad / ct, deta = n * dct;
+    D.dkt = deta * inv_lam;  // turns per nm
+    D.dq12s = -deta * k.q12s * k.q12s;
+    D.dq21s = deta;
+    D.dq12p = dct * inv_n;
+    D.dq21p = -dct * k.q21p / ct;
+  } else {
+    const float na = -k.q21s, a = fmaxf(na * inv_n, 1e-20f);
+    const float da = -0.5f * drad / a, dna = n * da;
+    D.dkt = TWO_PI * dna * inv_lam;  // rad per nm, as kt
+    D.dq12s = -dna * k.q12s * k.q12s;
+    D.dq21s = -dna;
+    D.dq12p = -da * inv_n;
+    D.dq21p = -da * k.q21p / a;
+  }
+  return D;
+}
+
+struct MatTableD {
+  MatKD k[MAX_MAT];
+  __device__ __forceinline__ void init(const BlobHeader& h, float cos0, float lam, const MatTable& mt) {
+    const float inv_lam = 1.0f / lam;
+#pragma unroll
+    for (int i = 0; i < MAX_MAT; ++i)
+      if (i < h.n_mat) k[i] = mat_const_d(mt.k[i], cos0, h.mat_n[i], h.mat_inv_n[i], h.mat_r2[i], inv_lam);
+  }
+  __device__ __forceinline__ MatKD get(int m) const {
+    MatKD r = k[0];
+    if (m == 1) r = k[1];
+    if (m == 2) r = k[2];
+    if (m == 3) r = k[3];
+    return r;
+  }
+};
+
+// v' = M v and its derivative dv' = dM v + M dv (M = [[c, i m12], [i m21, c]])
+__device__ __forceinline__ void cv_step_d(CV& v, CV& dv, float c, float m12, float m21, float dc, float dm12,
+                                          float dm21) {
+  const CV o = v;
+  cv_step(v, c, m12, m21);
+  const float xr = fmaf(dc, o.xr, fmaf(c, dv.xr, -fmaf(dm12, o.yi, m12 * dv.yi)));
+  const float xi = fmaf(dc, o.xi, fmaf(c, dv.xi, fmaf(dm12, o.yr, m12 * dv.yr)));
+  const float yr = fmaf(dc, o.yr, fmaf(c, dv.yr, -fmaf(dm21, o.xi, m21 * dv.xi)));
+  const float yi = fmaf(dc, o.yi, fmaf(c, dv.yi, fmaf(dm21, o.xr, m21 * dv.xr)));
+  dv.xr = xr;
+  dv.xi = xi;
+  dv.yr = yr;
+  dv.yi = yi;
+}
+
+// r, t and their derivatives from the (scaled) vector and its derivative
+__device__ __forceinline__ void coef_from_v_d(const CV& v, const CV& dv, float eta0, float deta0, int e, float2& r,
+                                              float2& t, float2& dr, float2& dt) {
+  const float2 B = make_float2(v.xr, v.xi), C = make_float2(v.yr, v.yi);
+  const float2 dB = make_float2(dv.xr, dv.xi), dC = make_float2(dv.yr, dv.yi);
+  const float2 den = make_float2(fmaf(eta0, B.x, C.x), fmaf(eta0, B.y, C.y));
+  const float2 num = make_float2(fmaf(eta0, B.x, -C.x), fmaf(eta0, B.y, -C.y));
+  const float2 dden = make_float2(fmaf(deta0, B.x, fmaf(eta0, dB.x, dC.x)), fmaf(deta0, B.y, fmaf(eta0, dB.y, dC.y)));
+  const float2 dnum = make_float2(fmaf(deta0, B.x, fmaf(eta0, dB.x, -dC.x)), fmaf(deta0, B.y, fmaf(eta0, dB.y, -dC.y)));
+  const float2 q = crcp_s(den);
+  const float sc = pow2i(-e);
+  r = cmul(num, q);
+  t = cscale(q, 2.0f * eta0 * sc);
+  dr = cmul(csub(dnum, cmul(r, dden)), q);
+  dt = cmul(csub(make_float2(2.0f * deta0 * sc, 0.0f), cmul(t, dden)), q);
+}
+
+// Coefficients in the paper's convention and their derivatives d/d(cos t0).
+template <int P>
+__device__ __forceinline__ void tmm_forward_dual(const StackView& st, bool front, const MatTable& mt,
+                                                 const MatTableD& mtd, float n0, float cos0, Coef& cf, Coef& dcf) {
+  const float eta_s = n0 * cos0, eta_p = n0 / cos0;
+  const float deta_s = n0, deta_p = -eta_p / cos0;
+  CV vs{1.0f, 0.0f, eta_s, 0.0f}, vp{1.0f, 0.0f, eta_p, 0.0f};
+  CV dvs{0.0f, 0.0f, deta_s, 0.0f}, dvp{0.0f, 0.0f, deta_p, 0.0f};
+  int es = 0, ep = 0;
+  for (int j = st.L - 1; j >= 0; --j) {
+    const int i = st.idx(front, j);
+    const int m = st.m[i];
+    const MatK k = mt.get(m);
+    const MatKD kd = mtd.get(m);
+    const float dthk = st.d[i];
+    float c, s, dc, ds;
+    layer_cs(k, dthk, c, s);
+    if (!k.evan) {
+      const float dth = TWO_PI * dthk * kd.dkt;  // d(phase)
+      dc = -s * dth;
+      ds = c * dth;
+    } else {
+      const float dx = dthk * kd.dkt;
+      dc = s * dx;
+      ds = c * dx;
+    }
+    cv_step_d(vs, dvs, c, s * k.q12s, s * k.q21s, dc, fmaf(ds, k.q12s, s * kd.dq12s), fmaf(ds, k.q21s, s * kd.dq21s));
+    cv_step_d(vp, dvp, c, s * k.q12p, s * k.q21p, dc, fmaf(ds, k.q12p, s * kd.dq12p), fmaf(ds, k.q21p, s * kd.dq21p));
+    if ((j & 7) == 0) {  // the same exact power-of-two scale on the vector and its derivative
+      if (fmaxf(cv_maxabs(vs), cv_maxabs(dvs)) > TWO_P64) {
+        vs = CV{vs.xr * TWO_M64, vs.xi * TWO_M64, vs.yr * TWO_M64, vs.yi * TWO_M64};
+        dvs = CV{dvs.xr * TWO_M64, dvs.xi * TWO_M64, dvs.yr * TWO_M64, dvs.yi * TWO_M64};
+        es += 64;
+      }
+      if (fmaxf(cv_maxabs(vp), cv_maxabs(dvp)) > TWO_P64) {
+        vp = CV{vp.xr * TWO_M64, vp.xi * TWO_M64, vp.yr * TWO_M64, vp.yi * TWO_M64};
+        dvp = CV{dvp.xr * TWO_M64, dvp.xi * TWO_M64, dvp.yr * TWO_M64, dvp.yi * TWO_M64};
+        ep += 64;
+      }
+    }
+  }
+  float2 rpm, drpm;
+  coef_from_v_d(vs, dvs, eta_s, deta_s, es, cf.rs, cf.ts, dcf.rs, dcf.ts);
+  coef_from_v_d(vp, dvp, eta_p, deta_p, ep, rpm, cf.tp, drpm, dcf.tp);
+  cf.rp = make_float2(-rpm.x, -rpm.y);
+  dcf.rp = make_float2(-drpm.x, -drpm.y);
+}
+
+// d/d(cos i) of the TIR coefficients at a slab face (|r| = 1: r = e^{2i phi},
+// dr = 2i r dphi) for cos i = ci
+__device__ __forceinline__ void tir_coef_d(float n, float ci, float2 rs, float2 rp, float2& drs, float2& drp) {
+  const float a2 = fmaf(n * n, fmaf(-ci, ci, 1.0f), -1.0f);
+  const float a = sqrtf(fmaxf(a2, 1e-30f));
+  const float da = -n * n * ci / a;
+  const float u = n * ci;
+  const float dphi = (u * da - a * n) / fmaf(u, u, a * a);
+  const float na = n * a;
+  const float dpsi = (ci * n * da - na) / fmaf(ci, ci, na * na);
+  drs = make_float2(-2.0f * dphi * rs.y, 2.0f * dphi * rs.x);
+  drp = make_float2(-2.0f * dpsi * rp.y, 2.0f * dpsi * rp.x);
+}
+
+// d/d(cos i) of the exit power transmittances T_s, T_p (glass -> air)
+__device__ __forceinline__ void exit_T_d(float n, float ci, float& dTs, float& dTp) {
+  const float x = n * n * fmaf(-ci, ci, 1.0f);
+  const float ct = sqrtf(fmaxf(1.0f - x, 1e-30f));
+  const float dct = n * n * ci / ct;
+  const float u = n * ci, du = n;
+  const float ts = 2.0f * u / (u + ct), tp = 2.0f * u / fmaf(n, ct, ci);
+  const float dts = 2.0f * (du * ct - u * dct) / ((u + ct) * (u + ct));
+  const float dtpd = fmaf(n, ct, ci);
+  const float dtp = 2.0f * (du * dtpd - u * fmaf(n, dct, 1.0f)) / (dtpd * dtpd);
+  const float tf = ct / u, dtf = (dct * u - ct * du) / (u * u);
+  dTs = fmaf(dtf, ts * ts, 2.0f * tf * ts * dts);
+  dTp = fmaf(dtf, tp * tp, 2.0f * tf * tp * dtp);
+}
+
+// tangents of the face basis s = (d_y, -d_x, 0)/h, p = s x d. With
+// (d_x, d_y) = h (cos psi, sin psi), s only turns with the azimuth psi:
+// ds = (d_x, d_y, 0)/h dpsi, dpsi = (d_x dd_y - d_y dd_x)/h^2. Written this way
+// ds stays orthogonal to s for any h (differentiating s/h term by term leaves
+// a rounding residue times 1/h along s, which near a vertical direction is
+// a spurious scaling of the field), and it is exactly zero in a 2D slab.
+__device__ __forceinline__ void face_basis_d(V3 d, V3 dd, V3 s, V3& ds, V3& dp) {
+  const float h2 = fmaf(d.x, d.x, d.y * d.y);
+  if (h2 > 1e-30f) {
+    const float r = rsqrtf(h2);
+    const float dpsi = fmaf(d.x, dd.y, -d.y * dd.x) * (r * r);
+    ds = V3{d.x * r * dpsi, d.y * r * dpsi, 0.0f};
+  } else {
+    ds = V3{0.0f, 0.0f, 0.0f};
+  }
+  const V3 a = cross3(ds, d), b = cross3(s, dd);
+  dp = V3{a.x + b.x, a.y + b.y, a.z + b.z};
+}
+
+// tangent of w / |w|
+__device__ __forceinline__ V3 normalize_d(V3 w, V3 dw) {
+  const float r = rsqrtf(dot3(w, w));
+  const float k = dot3(w, dw) * r * r;
+  return V3{(dw.x - w.x * k) * r, (dw.y - w.y * k) * r, (dw.z - w.z * k) * r};
+}
+
 }  // namespace wgk

@@ -57,6 +57,9 @@ struct TraceArgs {
   const ExitRec* replay_list;
   long long list_begin, list_end;
   int n_cta;                  // CTAs of the launch working on this job
+  // tilt gradient: FP64 per-degree sums for mirrors [tilt_k0, tilt_k0 + 8)
+  double* grad_tilt;
+  int tilt_k0;
 };
 
 // Arguments of the thin-film adjoint over sorted hit records.
@@ -112,6 +115,11 @@ cudaError_t launch_coating_grad(const uint8_t* blob, int P, int mirror, int side
                                 const float* lam, const float* w, int which, float* grad, cudaStream_t s);
 cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const int* orig_to_dev, int n_orig,
                                     cudaStream_t s);
+// mirror-tilt gradient of the rays of a (listed or ranged) backward launch,
+// one pass per group of 8 mirrors starting at a.tilt_k0
+cudaError_t launch_tilt_grad(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s);
+size_t tilt_smem_bytes(int blob_bytes, int F);
+int tilt_blocks_per_sm(int F, int P, size_t smem);
 int trace_fwd_blocks_per_sm(int F, int P, size_t smem);
 int bwd_replay_blocks_per_sm(int F, int P, size_t smem);
 int bwd_adjoint_blocks_per_sm(int P, size_t smem);

@@ -1225,6 +1225,246 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
     if (s_keys[i]) atomicAdd(A.key_count + i, s_keys[i]);
 }
 
+// ---------------------------------------------------------------------------
+// K3b: mirror-tilt gradient (forward mode). Each listed eyebox ray (or each
+// ray of the range) is traced again with the forward pass's arithmetic, so
+// its path and bin are the forward's, carrying tangents of its direction and
+// field with respect to the tilts of up to kTiltPass mirrors (per lane in
+// shared memory, word w of tangent t at col[(t * W + w) * 32]); at the
+// eyebox exit G[bin] dI/d(tilt) accumulates per mirror (FP64, per degree).
+// ---------------------------------------------------------------------------
+constexpr int kTiltPass = 8;
+constexpr int kTiltBlock = 128;
+
+template <int F>
+__device__ __forceinline__ float& tan_w(float* col, int t, int w) {
+  return col[(t * (3 + 4 * F) + w) * 32];
+}
+
+// mirror_event with tangents: values by the same expressions (so the
+// direction and decision are the forward's), coefficients and their
+// derivative with respect to cos(theta_0) from the dual layer chain
+template <int F>
+__device__ void mirror_event_tilt(Ray<F>& R, int k, const Blob& B, float lam, const TraceArgs& A, int k0, int nk,
+                                  float* col) {
+  const BlobHeader& H = *B.h;
+  const MirrorRec& M = B.mir[k];
+  const V3 N = v3(M.nx, 0.0f, M.nz);
+  const V3 dN = v3(-M.nz, 0.0f, M.nx);  // dN/d(tilt) per radian
+  const float cd = dot3(R.d, N);
+  const bool front = cd < 0.0f;
+  const float cos0 = fabsf(cd);
+  MatTable mt;
+  mt.init(H, cos0, lam);
+  MatTableD mtd;
+  mtd.init(H, cos0, lam, mt);
+  const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+  Coef cf, dcf;
+  tmm_forward_dual<0>(sv, front, mt, mtd, H.n_slab, cos0, cf, dcf);
+  V3 sf, pf;
+  face_basis(R.d, sf, pf);
+  const V3 w = cross3(R.d, N);
+  const float sm2 = dot3(w, w);
+  const bool degen = !(sm2 > 1e-24f);
+  V3 sm = sf;
+  if (!degen) {
+    const float r = rsqrtf(sm2);
+    sm = v3(w.x * r, w.y * r, w.z * r);
+  }
+  const float cphi = dot3(sf, sm), sphi = dot3(pf, sm);
+  const int m = R.hits;
+  const uint4 rnd = philox10(
+      make_uint4((uint32_t)R.id, (uint32_t)((unsigned long long)R.id >> 32), (uint32_t)(m >> 2), TAG_EVT), A.key0,
+      A.key1);
+  const uint32_t word = (m & 3) == 0 ? rnd.x : (m & 3) == 1 ? rnd.y : (m & 3) == 2 ? rnd.z : rnd.w;
+  const bool refl = u24(word) < M.omega;
+  float2 cs, cp, dcs, dcp;
+  V3 d2 = R.d;
+  if (refl) {
+    cs = cscale(cf.rs, M.isw), cp = cscale(cf.rp, M.isw);
+    dcs = cscale(dcf.rs, M.isw), dcp = cscale(dcf.rp, M.isw);
+    d2 = v3(fmaf(-2.0f * cd, N.x, R.d.x), R.d.y, fmaf(-2.0f * cd, N.z, R.d.z));
+  } else {
+    cs = cscale(cf.ts, M.is1w), cp = cscale(cf.tp, M.is1w);
+    dcs = cscale(dcf.ts, M.is1w), dcp = cscale(dcf.tp, M.is1w);
+  }
+  const V3 pm2 = cross3(sm, d2);
+  V3 sf2, pf2;
+  face_basis(d2, sf2, pf2);
+  const float cpsi = dot3(sf2, sm), spsi = dot3(sf2, pm2);
+  // tangents (the field before the hit is still in R)
+  for (int t = 0; t < nk; ++t) {
+    const bool own = k0 + t == k;
+    const V3 dd = v3(tan_w<F>(col, t, 0), tan_w<F>(col, t, 1), tan_w<F>(col, t, 2));
+    const V3 dNt = own ? dN : v3(0.0f, 0.0f, 0.0f);
+    const float dcd = dot3(dd, N) + dot3(R.d, dNt);
+    const float dcos0 = front ? -dcd : dcd;
+    const float2 dcs_t = cscale(dcs, dcos0), dcp_t = cscale(dcp, dcos0);
+    V3 dsf, dpf;
+    face_basis_d(R.d, dd, sf, dsf, dpf);
+    V3 dsm = dsf;
+    if (!degen) {
+      const V3 a = cross3(dd, N), b = cross3(R.d, dNt);
+      dsm = normalize_d(w, v3(a.x + b.x, a.y + b.y, a.z + b.z));
+    }
+    const float dcphi = dot3(dsf, sm) + dot3(sf, dsm), dsphi = dot3(dpf, sm) + dot3(pf, dsm);
+    V3 dd2 = dd;
+    if (refl) dd2 = v3(dd.x - 2.0f * fmaf(dcd, N.x, cd * dNt.x), dd.y, dd.z - 2.0f * fmaf(dcd, N.z, cd * dNt.z));
+    const V3 e1 = cross3(dsm, d2), e2 = cross3(sm, dd2);
+    const V3 dpm2 = v3(e1.x + e2.x, e1.y + e2.y, e1.z + e2.z);
+    V3 dsf2, dpf2;
+    face_basis_d(d2, dd2, sf2, dsf2, dpf2);
+    const float dcpsi = dot3(dsf2, sm) + dot3(sf2, dsm), dspsi = dot3(dsf2, pm2) + dot3(sf2, dpm2);
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+      const float2 a = R.a[f], b = R.b[f];
+      const float2 da = make_float2(tan_w<F>(col, t, 3 + 4 * f), tan_w<F>(col, t, 4 + 4 * f));
+      const float2 db = make_float2(tan_w<F>(col, t, 5 + 4 * f), tan_w<F>(col, t, 6 + 4 * f));
+      const float2 Es = make_float2(fmaf(cphi, a.x, sphi * b.x), fmaf(cphi, a.y, sphi * b.y));
+      const float2 Ep = make_float2(fmaf(-sphi, a.x, cphi * b.x), fmaf(-sphi, a.y, cphi * b.y));
+      const float2 dEs = make_float2(dcphi * a.x + cphi * da.x + dsphi * b.x + sphi * db.x,
+                                     dcphi * a.y + cphi * da.y + dsphi * b.y + sphi * db.y);
+      const float2 dEp = make_float2(-dsphi * a.x - sphi * da.x + dcphi * b.x + cphi * db.x,
+                                     -dsphi * a.y - sphi * da.y + dcphi * b.y + cphi * db.y);
+      const float2 Os = cmul(cs, Es), Op = cmul(cp, Ep);
+      const float2 dOs = cadd(cmul(dcs_t, Es), cmul(cs, dEs)), dOp = cadd(cmul(dcp_t, Ep), cmul(cp, dEp));
+      tan_w<F>(col, t, 3 + 4 * f) = dcpsi * Os.x + cpsi * dOs.x + dspsi * Op.x + spsi * dOp.x;
+      tan_w<F>(col, t, 4 + 4 * f) = dcpsi * Os.y + cpsi * dOs.y + dspsi * Op.y + spsi * dOp.y;
+      tan_w<F>(col, t, 5 + 4 * f) = -dspsi * Os.x - spsi * dOs.x + dcpsi * Op.x + cpsi * dOp.x;
+      tan_w<F>(col, t, 6 + 4 * f) = -dspsi * Os.y - spsi * dOs.y + dcpsi * Op.y + cpsi * dOp.y;
+    }
+    tan_w<F>(col, t, 0) = dd2.x;
+    tan_w<F>(col, t, 1) = dd2.y;
+    tan_w<F>(col, t, 2) = dd2.z;
+  }
+  // values (as mirror_event)
+#pragma unroll
+  for (int f = 0; f < F; ++f) {
+    const float2 Es = make_float2(fmaf(cphi, R.a[f].x, sphi * R.b[f].x), fmaf(cphi, R.a[f].y, sphi * R.b[f].y));
+    const float2 Ep = make_float2(fmaf(-sphi, R.a[f].x, cphi * R.b[f].x), fmaf(-sphi, R.a[f].y, cphi * R.b[f].y));
+    const float2 Os = cmul(cs, Es), Op = cmul(cp, Ep);
+    R.a[f] = make_float2(fmaf(cpsi, Os.x, spsi * Op.x), fmaf(cpsi, Os.y, spsi * Op.y));
+    R.b[f] = make_float2(fmaf(-spsi, Os.x, cpsi * Op.x), fmaf(-spsi, Os.y, cpsi * Op.y));
+  }
+  R.d = d2;
+  R.reg = region_after(B, R.reg, k, d2);
+  R.hash = fnv(R.hash, (uint32_t)(S_MIR + k) | (refl ? 0x80u : 0u));
+  R.hits = m + 1;
+}
+
+template <int F>
+__global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ __align__(8) uint64_t s_mbar;
+  constexpr int W = 3 + 4 * F;
+  const int lane = threadIdx.x & 31;
+  float* col = reinterpret_cast<float*>(smem + A.blob_bytes) + (threadIdx.x >> 5) * (kTiltPass * W * 32) + lane;
+  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;
+  Blob B;
+  B.bind(smem);
+  const BlobHeader& H = *B.h;
+  const int k0 = A.tilt_k0, nk = min(kTiltPass, H.n_mir - k0);
+  double acc[kTiltPass];
+#pragma unroll
+  for (int t = 0; t < kTiltPass; ++t) acc[t] = 0.0;
+  const bool listed = A.replay_list != nullptr;
+  const long long n_items = listed ? A.list_end - A.list_begin : A.ray_end - A.ray_begin;
+  const float n = H.n_slab;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_items;
+       i += (long long)gridDim.x * blockDim.x) {
+    long long id, cell;
+    if (listed) {
+      const ExitRec e = A.replay_list[A.list_begin + i];
+      if (A.G[e.flat] == 0.0) continue;
+      id = e.id;
+      cell = e.flat / A.bins;
+    } else {
+      id = A.ray_begin + i;
+      cell = id / A.n_cell;
+    }
+    const ChunkConst cc = chunk_const(A, cell);
+    Ray<F> R;
+    gen_ray(R, id, cc, H, A);
+    for (int t = 0; t < nk; ++t)
+      for (int w = 0; w < W; ++w) tan_w<F>(col, t, w) = 0.0f;
+    for (;;) {
+      float tt;
+      const int sid = next_surface(B, R.p, R.d, R.last, R.reg, tt);
+      ++R.ev;
+      if (sid < 0) break;
+      R.p = v3(fmaf(tt, R.d.x, R.p.x), fmaf(tt, R.d.y, R.p.y), fmaf(tt, R.d.z, R.p.z));
+      R.last = sid;
+      if (sid >= S_MIR) {
+        mirror_event_tilt<F>(R, sid - S_MIR, B, cc.lam, A, k0, nk, col);
+        if (R.ev >= A.max_events) break;
+        continue;
+      }
+      const float dz0 = R.d.z;
+      float2 a0[F], b0[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        a0[f] = R.a[f];
+        b0[f] = R.b[f];
+      }
+      int dummy = 0;
+      const Outcome o = face_event<F>(R, sid, H, A, nullptr, nullptr, dummy);
+      const float ci = fabsf(dz0), sg = dz0 < 0.0f ? -1.0f : 1.0f;
+      if (!o.term) {  // TIR: d_z flipped, field times (r_s, r_p)(cos i)
+        float2 rs, rp, drs, drp;
+        tir_coef(n, ci, fmaf(-ci, ci, 1.0f), rs, rp);
+        tir_coef_d(n, ci, rs, rp, drs, drp);
+        for (int t = 0; t < nk; ++t) {
+          const float ddz = tan_w<F>(col, t, 2);
+          const float dci = sg * ddz;
+          tan_w<F>(col, t, 2) = -ddz;
+#pragma unroll
+          for (int f = 0; f < F; ++f) {
+            const float2 da = make_float2(tan_w<F>(col, t, 3 + 4 * f), tan_w<F>(col, t, 4 + 4 * f));
+            const float2 db = make_float2(tan_w<F>(col, t, 5 + 4 * f), tan_w<F>(col, t, 6 + 4 * f));
+            const float2 na = cadd(cmul(rs, da), cscale(cmul(drs, a0[f]), dci));
+            const float2 nb = cadd(cmul(rp, db), cscale(cmul(drp, b0[f]), dci));
+            tan_w<F>(col, t, 3 + 4 * f) = na.x;
+            tan_w<F>(col, t, 4 + 4 * f) = na.y;
+            tan_w<F>(col, t, 5 + 4 * f) = nb.x;
+            tan_w<F>(col, t, 6 + 4 * f) = nb.y;
+          }
+        }
+        if (R.ev >= A.max_events) break;
+        continue;
+      }
+      if (o.cat == L_EYEBOX) {  // dI = (dT_s |a|^2 + 2 T_s Re(a* da) + ...) / F
+        const double g = A.G[cell * A.bins + o.bin];
+        float dTs, dTp;
+        exit_T_d(n, ci, dTs, dTp);
+        for (int t = 0; t < nk; ++t) {
+          const float dci = sg * tan_w<F>(col, t, 2);
+          float dI = 0.0f;
+#pragma unroll
+          for (int f = 0; f < F; ++f) {
+            const float2 da = make_float2(tan_w<F>(col, t, 3 + 4 * f), tan_w<F>(col, t, 4 + 4 * f));
+            const float2 db = make_float2(tan_w<F>(col, t, 5 + 4 * f), tan_w<F>(col, t, 6 + 4 * f));
+            dI += dTs * dci * cabs2(R.a[f]) + 2.0f * o.Ts * fmaf(R.a[f].x, da.x, R.a[f].y * da.y);
+            dI += dTp * dci * cabs2(R.b[f]) + 2.0f * o.Tp * fmaf(R.b[f].x, db.x, R.b[f].y * db.y);
+          }
+          acc[t] += g * (double)(dI * (1.0f / F));
+        }
+      }
+      break;
+    }
+  }
+  const double per_degree = 3.14159265358979323846 / 180.0;
+  for (int t = 0; t < nk; ++t) {
+    double v = acc[t];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if (lane == 0 && v != 0.0) atomicAdd(A.grad_tilt + k0 + t, v * per_degree);
+  }
+}
+
+size_t tilt_smem_bytes(int blob_bytes, int F) {
+  return (size_t)blob_bytes + sizeof(float) * (size_t)(kTiltBlock / 32) * kTiltPass * (3 + 4 * F) * 32;
+}
+
 // exclusive prefix of the per-stack record counts (one block)
 __global__ void k_bwd_scan(const unsigned int* key_count, unsigned int* key_off, unsigned int* key_cursor) {
   __shared__ unsigned int s[2 * MAX_MIR];
@@ -1493,6 +1733,23 @@ static int occupancy(K kernel, size_t smem) {
 int trace_fwd_blocks_per_sm(int F, int P, size_t smem) { return occupancy(WG_PICK_FP(k_trace_fwd, F, P), smem); }
 int bwd_replay_blocks_per_sm(int F, int P, size_t smem) { return occupancy(WG_PICK_FP(k_bwd_replay, F, P), smem); }
 int bwd_adjoint_blocks_per_sm(int P, size_t smem) { return occupancy(WG_PICK_P(k_bwd_adjoint, P), smem); }
+int tilt_blocks_per_sm(int F, int P, size_t smem) {
+  (void)P;
+  auto k = F == 2 ? k_tilt_grad<2> : k_tilt_grad<1>;
+  int n = 0;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kTiltBlock, smem);
+  return n;
+}
+
+cudaError_t launch_tilt_grad(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s) {
+  (void)P;
+  auto k = F == 2 ? k_tilt_grad<2> : k_tilt_grad<1>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  note_launches(1);
+  k<<<grid, kTiltBlock, smem, s>>>(a);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s) {
   auto k = WG_PICK_FP(k_trace_fwd, F, P);

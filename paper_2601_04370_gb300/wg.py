@@ -301,11 +301,14 @@ class Context:
                                               C.byref(st) if stats else None))
         return st.to_dict() if stats else None
 
-    def trace_backward(self, dh, cfg, dL_dtally, grad_thickness, stats=True, stream=None, rays=None):
+    def trace_backward(self, dh, cfg, dL_dtally, grad_thickness, stats=True, stream=None, rays=None,
+                       grad_tilt=None):
+        """grad_thickness (and grad_tilt, [n_mirrors] per degree, optional):
+        torch CUDA float64 tensors or numpy float64 arrays, overwritten."""
         h = _CfgHolder(cfg, stream if stream is not None else _current_stream(), rays)
         st = Stats() if stats else None
-        _check(lib().wg_trace_backward(self.h, dh.h, C.byref(h.c), _ptr(dL_dtally), _ptr(grad_thickness), None,
-                                       C.byref(st) if stats else None))
+        _check(lib().wg_trace_backward(self.h, dh.h, C.byref(h.c), _ptr(dL_dtally), _ptr(grad_thickness),
+                                       _ptr(grad_tilt), C.byref(st) if stats else None))
         return st.to_dict() if stats else None
 
     def loss(self, dh, cfg, tally, dL_dtally=None, kind=0, w_f=10.0, w_e=3.0, stream=None):

@@ -331,6 +331,30 @@ def test_backward_3d_matches_oracle_adjoint(ctx, ora, L):
     dh.destroy()
 
 
+@pytest.mark.parametrize("cfg", ["rep", "tiny"])
+def test_tilt_gradient_matches_oracle_adjoint(ctx, ora, cfg):
+    """dL/d(tilt) per degree along the fixed sampled paths (forward-mode
+    tangents on the GPU, reverse-mode AD in the FP64 oracle)."""
+    if cfg == "rep":
+        D, C = W.representative(n_rays=1728 * 8)
+    else:
+        D, C = W.tiny()
+    dh = ctx.create_design(D)
+    tally = torch.zeros(C.tally_shape, dtype=torch.float64, device="cuda")
+    ctx.trace_forward(dh, C, tally)
+    G = torch.zeros_like(tally)
+    ctx.loss(dh, C, tally, G)
+    g = torch.zeros(D.total_layers, dtype=torch.float64, device="cuda")
+    gt = np.zeros(len(D.mirror_x_mm))
+    st = ctx.trace_backward(dh, C, G, g, grad_tilt=gt)
+    assert st["overflow"] == 0 and st["n_nonfinite"] == 0
+    ref_d, ref_t = ora.trace_grad(D, C, G.cpu().numpy())
+    _grad_compare(g.cpu().numpy(), ref_d)
+    assert np.all(np.isfinite(gt))
+    assert np.linalg.norm(gt - ref_t) <= 1e-3 * np.linalg.norm(ref_t), (gt, ref_t)
+    dh.destroy()
+
+
 def test_backward_eyebox_list_matches_full_replay(ctx):
     """The adjoint that replays only the forward's eyebox rays (whose bins
     carry gradient) equals the one that replays every ray; a tilt update
