@@ -309,13 +309,14 @@ def run_ours(args):
     tally = torch.zeros(C.tally_shape, dtype=torch.float64, device="cuda")
     G = torch.zeros_like(tally)
     grad = torch.zeros(D.total_layers, dtype=torch.float64, device="cuda")
+    grad_t = torch.zeros(len(D.mirror_x_mm), dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
     # work counts of one step (the same keys every step)
     st_f = ctx.trace_forward(dh, C, tally)
     loss = ctx.loss(dh, C, tally, G)
-    st_b = ctx.trace_backward(dh, C, G, grad)
+    st_b = ctx.trace_backward(dh, C, G, grad, grad_tilt=grad_t)
     hits = st_f["n_hits"]
     flops_fwd = FLOPS_PER_LAYER * st_f["n_layer_steps"] + FLOPS_PER_HIT * hits
     flops_bwd = (FLOPS_PER_LAYER * st_b["n_layer_steps"] + FLOPS_PER_HIT * st_b["n_hits"] +
@@ -328,12 +329,26 @@ def run_ours(args):
         evs[1].record(stream)
         ctx.loss(dh, C, tally, G)
         evs[2].record(stream)
-        ctx.trace_backward(dh, C, G, grad, stats=False)
+        ctx.trace_backward(dh, C, G, grad, stats=False, grad_tilt=grad_t)
         evs[3].record(stream)
 
     for _ in range(args.warmup):
         step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
     torch.cuda.synchronize()
+
+    def bwd_ms_of(**kw):
+        # outside the timed region: the backward with and without the tilt pass
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t = []
+        for _ in range(3):
+            flush.zero_()
+            e0.record(stream)
+            ctx.trace_backward(dh, C, G, grad, stats=False, **kw)
+            e1.record(stream)
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1))
+        return statistics.median(t)
+    tilt_ms = bwd_ms_of(grad_tilt=grad_t) - bwd_ms_of()
     barrier(pg, dev)
     torch.cuda.synchronize()
     clocks = Clocks(dev)
@@ -361,20 +376,22 @@ def run_ours(args):
     # end to end through the C ABI with host buffers: thickness from pinned
     # host memory in, loss and gradient out, every step
     th_host = torch.tensor(D.layer_d_nm, dtype=torch.float32).pin_memory().numpy()
+    tl_host = torch.tensor(D.mirror_tilt_deg, dtype=torch.float32).pin_memory().numpy()
     g_host = np.zeros(D.total_layers)
+    gt_host = np.zeros(len(D.mirror_x_mm))
     cfg_bytes = 4 * (len(C.lam_nm) + len(C.fx_deg) + len(C.fy_deg))
-    h2d = th_host.nbytes + 2 * cfg_bytes
-    d2h = 4 * 8 + g_host.nbytes
+    h2d = th_host.nbytes + tl_host.nbytes + 2 * cfg_bytes
+    d2h = 4 * 8 + g_host.nbytes + gt_host.nbytes
     e2e_t = []
     barrier(pg, dev)
     for i in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        dh.set_params(thickness_nm=th_host)
+        dh.set_params(thickness_nm=th_host, tilt_deg=tl_host)
         ctx.trace_forward(dh, C, tally, stats=False)
         ctx.loss(dh, C, tally, G)
-        ctx.trace_backward(dh, C, G, g_host, stats=False)
+        ctx.trace_backward(dh, C, G, g_host, stats=False, grad_tilt=gt_host)
         e2e_t.append(time.perf_counter() - t0)
     e2e_max = allmax(pg, sum(e2e_t), dev)
     e2e_value = hits_all / e2e_max
@@ -407,7 +424,7 @@ def run_ours(args):
         sm = torch.cuda.get_device_properties(dev).multi_processor_count
         smax = float(pk.get("sm_max_mhz", 2070.0))
         peak = fp32_peak_tflops(sm, smax)
-        bwd_s = statistics.mean(bwd_ms) / 1e3
+        bwd_s = statistics.mean(bwd_ms) / 1e3 - max(tilt_ms, 0.0) / 1e3  # thickness adjoint only
         fwd_s = statistics.mean(fwd_ms) / 1e3
         ach_b = flops_bwd / bwd_s / 1e12
         ach_f = flops_fwd / fwd_s / 1e12
@@ -422,7 +439,7 @@ def run_ours(args):
                          f"+ {FLOPS_PER_HIT}) flops",
                 "peak_source": f"derived: {sm} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz "
                                f"(sm_max_mhz of {pk_kind} peaks)"}
-        roof_b = {"bound": "alu", "kernels": "k_bwd_replay + sort + k_bwd_adjoint", "achieved": ach_b,
+        roof_b = {"bound": "alu", "kernels": "k_bwd_replay + sort + k_bwd_adjoint (tilt pass excluded)", "achieved": ach_b,
                   "peak": peak, "unit": "TFLOP/s", "frac": ach_b / peak, "flops_per_call": flops_bwd}
         cpu = None
         if ws == 1 and not args.no_cpu_baseline:
@@ -434,7 +451,7 @@ def run_ours(args):
                           "interactions_per_step_per_gpu": hits, "l2": "flushed between steps (256 MiB write)",
                           "parallelism": f"replicas x{ws} (rays sharded by seed, no collective)"},
                "fwd_interactions_per_s": fwd_rate, "fwd_ms": statistics.mean(fwd_ms),
-               "bwd_ms": statistics.mean(bwd_ms), "loss": loss[0], "wall_s": t_wall,
+               "bwd_ms": statistics.mean(bwd_ms), "tilt_pass_ms": tilt_ms, "loss": loss[0], "wall_s": t_wall,
                "roofline": roof, "roofline_bwd": roof_b, "cpu_baseline": cpu,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": launches, "clocks": ck, "serving": serving}

@@ -1088,7 +1088,10 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   long long batch = std::min<long long>(total, std::max<long long>(4096ll * c->sm_count * 4, 1ll << 21));
   const long long cap = batch * kRecordsPerRay;
   const size_t rec_bytes = (size_t)cap * hit_rec_bytes();
-  const size_t need = 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + sizeof(double) * std::max(1, d->n_dev);
+  const bool tilt = grad_tilt != nullptr;
+  const size_t acc_bytes = (sizeof(double) * std::max(1, d->n_dev) + 15) & ~(size_t)15;
+  const size_t aux_bytes = tilt ? (size_t)cap * sizeof(TiltAux) + (size_t)batch * sizeof(RayHead) : 0;
+  const size_t need = 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + acc_bytes + aux_bytes;
   if (need > c->bwd.n) {
     CU(cudaEventSynchronize(c->ws_free));
     CU(c->bwd.ensure(need));
@@ -1101,6 +1104,12 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   sc.hit_count = (unsigned long long*)(bw + 2 * rec_bytes + 3 * 128 * sizeof(unsigned int));
   sc.grad_acc = (double*)(bw + 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64);
   sc.cap = cap;
+  TiltAux* tilt_aux = nullptr;
+  RayHead* heads = nullptr;
+  if (tilt) {
+    tilt_aux = (TiltAux*)(bw + 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + acc_bytes);
+    heads = (RayHead*)((uint8_t*)tilt_aux + (size_t)cap * sizeof(TiltAux));
+  }
   const bool dev_G = is_device_ptr(dL_dtally);
   const bool dev_g = is_device_ptr(grad_thickness);
   const double* G = dL_dtally;
@@ -1114,7 +1123,17 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   if (!dev_g) CU(cudaMallocAsync((void**)&gout, sizeof(double) * std::max(1, d->n_orig), s));
   CU(cudaMemsetAsync(gout, 0, sizeof(double) * std::max(1, d->n_orig), s));
   CU(cudaMemsetAsync(sc.grad_acc, 0, sizeof(double) * std::max(1, d->n_dev), s));
-  const int bps_r = std::max(1, bwd_replay_blocks_per_sm(p.F, d->period, smem_r));
+  const int bps_r = std::max(1, bwd_replay_blocks_per_sm(p.F, d->period, tilt, smem_r));
+  // mirror tilts: the replay records each hit's coefficients and dL/d(cos t0);
+  // after each batch a tangent pass per 8 mirrors re-traces its rays
+  double* gt = grad_tilt;
+  const bool dev_t = tilt && is_device_ptr(grad_tilt);
+  const size_t smem_t = tilt_smem_bytes(d->blob_bytes, p.F);
+  const int bps_t = tilt ? std::max(1, tilt_blocks_per_sm(p.F, d->period, smem_t)) : 0;
+  if (tilt) {
+    if (!dev_t) CU(cudaMallocAsync((void**)&gt, sizeof(double) * d->K, s));
+    CU(cudaMemsetAsync(gt, 0, sizeof(double) * d->K, s));
+  }
   const int bps_a = std::max(1, bwd_adjoint_blocks_per_sm(d->period, smem_a));
   // rays to replay: the eyebox rays listed by the forward trace of this
   // configuration and geometry if there is such a list, else the ray range
@@ -1147,15 +1166,20 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     a.hit_cap = cap;
     a.hit_count = sc.hit_count;
     a.key_count = sc.keys;
+    a.tilt_aux = tilt_aux;
+    a.ray_heads = heads;
+    a.head_cap = b1 - b0;
+    a.head_count = sc.hit_count + 1;
     CU(cudaMemsetAsync(&w.head->work, 0, sizeof(unsigned long long), s));
     CU(cudaMemsetAsync(sc.keys, 0, 128 * sizeof(unsigned int), s));
-    CU(cudaMemsetAsync(sc.hit_count, 0, sizeof(unsigned long long), s));
+    CU(cudaMemsetAsync(sc.hit_count, 0, 2 * sizeof(unsigned long long), s));
     const int grid_r = (int)std::max<long long>(1, std::min<long long>(a.n_chunks, (long long)c->sm_count * bps_r));
     if (stats) CU(cudaEventRecord(c->t0, s));
-    CU(launch_bwd_replay(a, p.F, d->period, grid_r, smem_r, s));
-    unsigned long long n_rec = 0;
-    CU(cudaMemcpyAsync(&n_rec, sc.hit_count, sizeof(n_rec), cudaMemcpyDeviceToHost, s));
+    CU(launch_bwd_replay(a, p.F, d->period, tilt, grid_r, smem_r, s));
+    unsigned long long counts[2] = {0, 0};  // records, ray heads
+    CU(cudaMemcpyAsync(counts, sc.hit_count, sizeof(counts), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
+    const unsigned long long n_rec = counts[0];
     if ((long long)n_rec > cap) {
       // more records than the batch holds (never seen: ~2 records per ray against 16):
       // redo this batch with half the rays
@@ -1182,6 +1206,16 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
       const int grid_a = (int)std::min<long long>(chunks, (long long)c->sm_count * bps_a);
       CU(launch_bwd_adjoint(aa, d->period, grid_a, smem_a, s));
     }
+    const long long n_heads = std::min<long long>((long long)counts[1], b1 - b0);
+    for (int k0 = 0; tilt && n_heads > 0 && k0 < d->K; k0 += 8) {
+      TraceArgs at = a;
+      at.n_heads = n_heads;
+      at.grad_tilt = gt;
+      at.tilt_k0 = k0;
+      const int grid_t =
+          (int)std::max<long long>(1, std::min<long long>((n_heads + 127) / 128, (long long)c->sm_count * bps_t));
+      CU(launch_tilt_grad(at, p.F, d->period, grid_t, smem_t, s));
+    }
     if (stats) {
       CU(cudaEventRecord(c->t1, s));
       CU(cudaEventSynchronize(c->t1));
@@ -1192,35 +1226,10 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     b0 = b1;
   }
   CU(launch_scatter_grad(sc.grad_acc, d->n_dev, d->d_dev_to_orig, gout, s));
-  if (grad_tilt) {
-    // mirror tilts: forward-mode tangents over the same rays, 8 mirrors per pass
-    const bool dev_t = is_device_ptr(grad_tilt);
-    double* gt = grad_tilt;
-    if (!dev_t) CU(cudaMallocAsync((void**)&gt, sizeof(double) * d->K, s));
-    CU(cudaMemsetAsync(gt, 0, sizeof(double) * d->K, s));
-    const size_t smem_t = tilt_smem_bytes(d->blob_bytes, p.F);
-    const int bps_t = std::max(1, tilt_blocks_per_sm(p.F, d->period, smem_t));
-    const long long items = use_list ? n_list : p.re - p.rb;
-    for (int k0 = 0; k0 < d->K && items > 0; k0 += 8) {
-      Plan q = p;
-      if (!use_list) plan_range(q, p.rb, p.re);
-      TraceArgs a = base_args(d, cfg, q, w);
-      a.G = G;
-      a.grad_tilt = gt;
-      a.tilt_k0 = k0;
-      if (use_list) {
-        a.replay_list = list;
-        a.list_begin = 0;
-        a.list_end = n_list;
-      }
-      const int grid = (int)std::max<long long>(1, std::min<long long>((items + 127) / 128, (long long)c->sm_count * bps_t));
-      CU(launch_tilt_grad(a, p.F, d->period, grid, smem_t, s));
-    }
-    if (!dev_t) {
-      CU(cudaMemcpyAsync(grad_tilt, gt, sizeof(double) * d->K, cudaMemcpyDeviceToHost, s));
-      CU(cudaFreeAsync(gt, s));
-      CU(cudaStreamSynchronize(s));
-    }
+  if (tilt && !dev_t) {
+    CU(cudaMemcpyAsync(grad_tilt, gt, sizeof(double) * d->K, cudaMemcpyDeviceToHost, s));
+    CU(cudaFreeAsync(gt, s));
+    CU(cudaStreamSynchronize(s));
   }
   CU(cudaEventRecord(c->ws_free, s));
   if (!dev_G) CU(cudaFreeAsync((void*)G, s));

@@ -17,6 +17,23 @@ struct ExitRec {
   int pad;
 };
 
+// Per hit record of a replay that also serves the tilt gradient: the applied
+// coefficients of the hit (incl. the 1/sqrt(omega) rescale) and dL/d(cos t0)
+// of the hit through its coating, 2 Re(A_s dc_s + A_p dc_p) with G folded in.
+struct TiltAux {
+  float2 cs, cp;
+  double g_cos;
+};
+// A replayed ray with records: the tilt pass re-traces it and reads its hits'
+// TiltAux entries [first, first + emit).
+struct RayHead {
+  long long id;
+  int cell;
+  int first;
+  int emit;
+  int pad;
+};
+
 // Arguments of the trace kernels (passed by value).
 struct TraceArgs {
   const uint8_t* blob;        // design blob (global), staged into smem
@@ -60,6 +77,13 @@ struct TraceArgs {
   // tilt gradient: FP64 per-degree sums for mirrors [tilt_k0, tilt_k0 + 8)
   double* grad_tilt;
   int tilt_k0;
+  // replay with the tilt gradient: per-record TiltAux [hit_cap], one RayHead
+  // per ray with records (head_count counts them); the tilt pass reads n_heads
+  TiltAux* tilt_aux;
+  RayHead* ray_heads;
+  long long head_cap;
+  unsigned long long* head_count;
+  long long n_heads;
 };
 
 // Arguments of the thin-film adjoint over sorted hit records.
@@ -103,7 +127,8 @@ cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int grid, size_t 
 // launch: CTA b works on job cta_job[b] (device arrays; each job's n_cta set)
 cudaError_t launch_trace_fwd_fused(const TraceArgs* jobs_dev, const int* cta_job_dev, int F, int P, int grid,
                                    size_t smem, cudaStream_t s);
-cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s);
+// tilt: also record TiltAux per hit and a RayHead per ray (a.tilt_aux, a.ray_heads)
+cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, bool tilt, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_bwd_sort(const HitRec* in, long long n, unsigned int* key_count, unsigned int* key_off,
                             unsigned int* key_cursor, HitRec* out, cudaStream_t s);
 cudaError_t launch_bwd_adjoint(const AdjArgs& a, int P, int grid, size_t smem, cudaStream_t s);
@@ -115,13 +140,13 @@ cudaError_t launch_coating_grad(const uint8_t* blob, int P, int mirror, int side
                                 const float* lam, const float* w, int which, float* grad, cudaStream_t s);
 cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const int* orig_to_dev, int n_orig,
                                     cudaStream_t s);
-// mirror-tilt gradient of the rays of a (listed or ranged) backward launch,
-// one pass per group of 8 mirrors starting at a.tilt_k0
+// mirror-tilt gradient of the a.n_heads rays a tilt replay recorded, one
+// pass per group of 8 mirrors starting at a.tilt_k0
 cudaError_t launch_tilt_grad(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s);
 size_t tilt_smem_bytes(int blob_bytes, int F);
 int tilt_blocks_per_sm(int F, int P, size_t smem);
 int trace_fwd_blocks_per_sm(int F, int P, size_t smem);
-int bwd_replay_blocks_per_sm(int F, int P, size_t smem);
+int bwd_replay_blocks_per_sm(int F, int P, bool tilt, size_t smem);
 int bwd_adjoint_blocks_per_sm(int P, size_t smem);
 // dynamic shared memory of the adjoint kernel (blob, per-layer sums, segment buffers)
 size_t adj_smem_bytes(int blob_bytes, int n_layers, int P);

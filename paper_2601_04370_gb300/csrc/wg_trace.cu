@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 #include <cstring>
 
 #include "wg_device.cuh"
@@ -335,12 +336,15 @@ __device__ __forceinline__ Outcome face_event(Ray<F>& R, int sid, const BlobHead
 // Fills the tape entry fields when `te` is non-null.
 struct MirrorStep {
   float2 cs, cp;   // applied coefficients (incl. 1/sqrt scaling)
+  float2 dcs, dcp;  // their derivatives d/d(cos t0) (DUAL only)
   float cphi, sphi, cpsi, spsi;
   float cos0;
   int front, refl;
 };
 
-template <int F, int P>
+// DUAL: the coefficients come with their derivatives with respect to
+// cos(theta_0) from the dual layer chain (the replay for the tilt gradient)
+template <int F, int P, bool DUAL = false>
 __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob& B, float lam, const TraceArgs& A,
                                                    int& layer_steps, float2* Es_out, float2* Ep_out) {
   const BlobHeader& H = *B.h;
@@ -353,7 +357,15 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
   MatTable mt;
   mt.init(H, st.cos0, lam);
   const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
-  const Coef cf = tmm_forward<P>(sv, st.front, mt, H.n_slab, st.cos0, layer_steps);
+  Coef cf, dcf;
+  if constexpr (DUAL) {
+    MatTableD mtd;
+    mtd.init(H, st.cos0, lam, mt);
+    tmm_forward_dual<P>(sv, st.front, mt, mtd, H.n_slab, st.cos0, cf, dcf);
+    layer_steps += M.n_layers;
+  } else {
+    cf = tmm_forward<P>(sv, st.front, mt, H.n_slab, st.cos0, layer_steps);
+  }
   V3 sf, pf;
   face_basis(R.d, sf, pf);
   V3 sm = cross3(R.d, N);
@@ -378,10 +390,18 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
   if (st.refl) {
     st.cs = cscale(cf.rs, M.isw);
     st.cp = cscale(cf.rp, M.isw);
+    if constexpr (DUAL) {
+      st.dcs = cscale(dcf.rs, M.isw);
+      st.dcp = cscale(dcf.rp, M.isw);
+    }
     d2 = v3(fmaf(-2.0f * cd, N.x, R.d.x), R.d.y, fmaf(-2.0f * cd, N.z, R.d.z));
   } else {
     st.cs = cscale(cf.ts, M.is1w);
     st.cp = cscale(cf.tp, M.is1w);
+    if constexpr (DUAL) {
+      st.dcs = cscale(dcf.ts, M.is1w);
+      st.dcp = cscale(dcf.tp, M.is1w);
+    }
   }
   const V3 pm2 = cross3(sm, d2);
   V3 sf2, pf2;
@@ -969,8 +989,12 @@ __global__ void __launch_bounds__(kBlock, 2)
 //   gradient entry in all lanes, which is reduced with shuffles and added
 //   once; partial FP32 sums in shared memory go to FP64 after each chunk.
 // ---------------------------------------------------------------------------
-template <int F>
-struct TapeE {
+struct TapeNoDual {};
+struct TapeDual {
+  float2 dcs, dcp;  // d/d(cos t0) of the applied coefficients
+};
+template <int F, bool T>
+struct TapeE : std::conditional_t<T, TapeDual, TapeNoDual> {
   float2 cs, cp;
   float2 Es[F], Ep[F];
   float cphi, sphi, cpsi, spsi;
@@ -979,7 +1003,10 @@ struct TapeE {
   int kfw;
 };
 
-template <int F, int P>
+// T: the replay also serves the tilt gradient. Coefficients come from the
+// dual layer chain, and each emitted record gets its TiltAux (applied
+// coefficients, dL/d(cos t0) through the coating) and its ray a RayHead.
+template <int F, int P, bool T>
 __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_mbar;
@@ -997,7 +1024,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
   const long long cap = A.hit_cap;
 
   int c_rays = 0, c_hits = 0, c_overflow = 0, c_tallied = 0, c_steps = 0;
-  TapeE<F> tape[TAPE_HITS];
+  TapeE<F, T> tape[TAPE_HITS];
 
   // warp-private work unit (a short ray range of one cell, warp-uniform)
   long long u_cell = 0, u_next = 0, u_end = 0;
@@ -1122,6 +1149,27 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
             unsigned long long base = 0;
             if (lane == 31) base = atomicAdd(A.hit_count, (unsigned long long)total);
             base = __shfl_sync(FULL, base, 31);
+            if constexpr (T) {
+              // one head per ray whose records fit (warp-aggregated slot)
+              const long long f0 = (long long)base + incl - emit;
+              const bool ok = emit > 0 && f0 + emit <= cap;
+              const unsigned hm = __ballot_sync(FULL, ok);
+              unsigned long long hb0 = 0;
+              if (lane == 0) hb0 = atomicAdd(A.head_count, (unsigned long long)__popc(hm));
+              hb0 = __shfl_sync(FULL, hb0, 0);
+              if (ok) {
+                const long long hi = (long long)hb0 + __popc(hm & lt_mask);
+                if (hi < A.head_cap) {
+                  RayHead rh;
+                  rh.id = R.id;
+                  rh.cell = (int)cell_l;
+                  rh.first = (int)f0;
+                  rh.emit = emit;
+                  rh.pad = 0;
+                  A.ray_heads[hi] = rh;
+                }
+              }
+            }
             if (emit) {
               const long long first = (long long)base + incl - emit;
               if (first + emit > cap) {
@@ -1138,35 +1186,44 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                   gb[f] = cmulc(seg_p, cscale(R.b[f], sc * o.Tp));
                 }
                 for (int h = emit - 1; h >= 0; --h) {
-                  const TapeE<F>& T = tape[h];
+                  const TapeE<F, T>& E = tape[h];
                   float2 gs[F], gp[F];
                   float2 As = make_float2(0.f, 0.f), Ap = make_float2(0.f, 0.f);
-                  const int k = T.kfw & 0xff;
-                  const bool refl = ((T.kfw >> 9) & 1) == 0;  // bit 9: 0 = reflected (r), 1 = transmitted (t)
+                  const int k = E.kfw & 0xff;
+                  const bool refl = ((E.kfw >> 9) & 1) == 0;  // bit 9: 0 = reflected (r), 1 = transmitted (t)
                   const float scl = refl ? B.mir[k].isw : B.mir[k].is1w;
 #pragma unroll
                   for (int f = 0; f < F; ++f) {
-                    gs[f] = make_float2(fmaf(T.cpsi, ga[f].x, -T.spsi * gb[f].x), fmaf(T.cpsi, ga[f].y, -T.spsi * gb[f].y));
-                    gp[f] = make_float2(fmaf(T.spsi, ga[f].x, T.cpsi * gb[f].x), fmaf(T.spsi, ga[f].y, T.cpsi * gb[f].y));
-                    As = cadd(As, cmulc(gs[f], T.Es[f]));
-                    Ap = cadd(Ap, cmulc(gp[f], T.Ep[f]));
+                    gs[f] = make_float2(fmaf(E.cpsi, ga[f].x, -E.spsi * gb[f].x), fmaf(E.cpsi, ga[f].y, -E.spsi * gb[f].y));
+                    gp[f] = make_float2(fmaf(E.spsi, ga[f].x, E.cpsi * gb[f].x), fmaf(E.spsi, ga[f].y, E.cpsi * gb[f].y));
+                    As = cadd(As, cmulc(gs[f], E.Es[f]));
+                    Ap = cadd(Ap, cmulc(gp[f], E.Ep[f]));
                   }
                   HitRec rec;
-                  rec.kfw = T.kfw;
-                  rec.cos0 = T.cos0;
+                  rec.kfw = E.kfw;
+                  rec.cos0 = E.cos0;
                   rec.lam = lam_l;
                   rec.eA = eG;
                   rec.As = cscale(As, scl);
                   rec.Ap = cscale(Ap, scl);
                   hb[first + h] = rec;
-                  atomicAdd(&s_keys[((T.kfw & 0xff) << 1) | ((T.kfw >> 8) & 1)], 1u);  // stack (mirror, side)
+                  if constexpr (T) {
+                    // dL/d(cos t0) of this hit through its coating (G's exponent restored)
+                    const float gc = 2.0f * (fmaf(As.x, E.dcs.x, -As.y * E.dcs.y) + fmaf(Ap.x, E.dcp.x, -Ap.y * E.dcp.y));
+                    TiltAux ta;
+                    ta.cs = E.cs;
+                    ta.cp = E.cp;
+                    ta.g_cos = ldexp((double)gc, eG);
+                    A.tilt_aux[first + h] = ta;
+                  }
+                  atomicAdd(&s_keys[((E.kfw & 0xff) << 1) | ((E.kfw >> 8) & 1)], 1u);  // stack (mirror, side)
 #pragma unroll
                   for (int f = 0; f < F; ++f) {
-                    const float2 xs = cmulc(T.cs, gs[f]), xp = cmulc(T.cp, gp[f]);
-                    const float2 ya = make_float2(fmaf(T.cphi, xs.x, -T.sphi * xp.x), fmaf(T.cphi, xs.y, -T.sphi * xp.y));
-                    const float2 yb = make_float2(fmaf(T.sphi, xs.x, T.cphi * xp.x), fmaf(T.sphi, xs.y, T.cphi * xp.y));
-                    ga[f] = cmulc(T.seg_s, ya);
-                    gb[f] = cmulc(T.seg_p, yb);
+                    const float2 xs = cmulc(E.cs, gs[f]), xp = cmulc(E.cp, gp[f]);
+                    const float2 ya = make_float2(fmaf(E.cphi, xs.x, -E.sphi * xp.x), fmaf(E.cphi, xs.y, -E.sphi * xp.y));
+                    const float2 yb = make_float2(fmaf(E.sphi, xs.x, E.cphi * xp.x), fmaf(E.sphi, xs.y, E.cphi * xp.y));
+                    ga[f] = cmulc(E.seg_s, ya);
+                    gb[f] = cmulc(E.seg_p, yb);
                   }
                 }
               }
@@ -1177,24 +1234,28 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
         if (at_mir) {
           const int h = R.hits;
           float2 Es[F], Ep[F];
-          const MirrorStep ms = mirror_event<F, P>(R, hit_k, B, lam_l, A, c_steps, Es, Ep);
+          const MirrorStep ms = mirror_event<F, P, T>(R, hit_k, B, lam_l, A, c_steps, Es, Ep);
           if (h < TAPE_HITS) {
-            TapeE<F>& T = tape[h];
-            T.cs = ms.cs;
-            T.cp = ms.cp;
+            TapeE<F, T>& E = tape[h];
+            E.cs = ms.cs;
+            E.cp = ms.cp;
+            if constexpr (T) {
+              E.dcs = ms.dcs;
+              E.dcp = ms.dcp;
+            }
 #pragma unroll
             for (int f = 0; f < F; ++f) {
-              T.Es[f] = Es[f];
-              T.Ep[f] = Ep[f];
+              E.Es[f] = Es[f];
+              E.Ep[f] = Ep[f];
             }
-            T.cphi = ms.cphi;
-            T.sphi = ms.sphi;
-            T.cpsi = ms.cpsi;
-            T.spsi = ms.spsi;
-            T.seg_s = seg_s;
-            T.seg_p = seg_p;
-            T.cos0 = ms.cos0;
-            T.kfw = hit_k | (ms.front << 8) | ((ms.refl ? 0 : 1) << 9);
+            E.cphi = ms.cphi;
+            E.sphi = ms.sphi;
+            E.cpsi = ms.cpsi;
+            E.spsi = ms.spsi;
+            E.seg_s = seg_s;
+            E.seg_p = seg_p;
+            E.cos0 = ms.cos0;
+            E.kfw = hit_k | (ms.front << 8) | ((ms.refl ? 0 : 1) << 9);
           }
           seg_s = make_float2(1.f, 0.f);
           seg_p = make_float2(1.f, 0.f);
@@ -1226,12 +1287,20 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// K3b: mirror-tilt gradient (forward mode). Each listed eyebox ray (or each
-// ray of the range) is traced again with the forward pass's arithmetic, so
-// its path and bin are the forward's, carrying tangents of its direction and
-// field with respect to the tilts of up to kTiltPass mirrors (per lane in
-// shared memory, word w of tangent t at col[(t * W + w) * 32]); at the
-// eyebox exit G[bin] dI/d(tilt) accumulates per mirror (FP64, per degree).
+// K3b: mirror-tilt gradient, split in two parts along the sampled path.
+// (1) Through the coatings: the replay differentiates each hit's coefficients
+//     with respect to cos(theta_0) (dual layer chain) and its reverse sweep
+//     forms g = dL/d(cos theta_0) of the hit (TiltAux); here g times the
+//     tangent of cos(theta_0) of that hit.
+// (2) Everything else with the coefficients held at their values: the
+//     reflected directions, the mirror and face s/p bases, the TIR phases and
+//     the exit transmittances. k_tilt_grad re-traces each ray that produced
+//     records (RayHead) with the forward's geometry, reads the applied
+//     coefficients of its hits from TiltAux (no layer chain), and carries
+//     tangents of its direction and field with respect to the tilts of up to
+//     kTiltPass mirrors (per lane in shared memory, word w of tangent t at
+//     col[(t * W + w) * 32]). At the eyebox exit G[bin] dI/d(tilt) is added.
+// Sums are FP64 per lane in shared memory, reported per degree.
 // ---------------------------------------------------------------------------
 constexpr int kTiltPass = 8;
 constexpr int kTiltBlock = 128;
@@ -1241,26 +1310,17 @@ __device__ __forceinline__ float& tan_w(float* col, int t, int w) {
   return col[(t * (3 + 4 * F) + w) * 32];
 }
 
-// mirror_event with tangents: values by the same expressions (so the
-// direction and decision are the forward's), coefficients and their
-// derivative with respect to cos(theta_0) from the dual layer chain
+// mirror_event with tangents: the same geometry and decision as the
+// forward, the coefficients as the replay applied them
 template <int F>
-__device__ void mirror_event_tilt(Ray<F>& R, int k, const Blob& B, float lam, const TraceArgs& A, int k0, int nk,
-                                  float* col) {
-  const BlobHeader& H = *B.h;
+__device__ void mirror_event_tilt(Ray<F>& R, int k, const Blob& B, const TraceArgs& A, int k0, int nk, float* col,
+                                  double* acc, const TiltAux& X) {
   const MirrorRec& M = B.mir[k];
   const V3 N = v3(M.nx, 0.0f, M.nz);
   const V3 dN = v3(-M.nz, 0.0f, M.nx);  // dN/d(tilt) per radian
   const float cd = dot3(R.d, N);
   const bool front = cd < 0.0f;
-  const float cos0 = fabsf(cd);
-  MatTable mt;
-  mt.init(H, cos0, lam);
-  MatTableD mtd;
-  mtd.init(H, cos0, lam, mt);
-  const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
-  Coef cf, dcf;
-  tmm_forward_dual<0>(sv, front, mt, mtd, H.n_slab, cos0, cf, dcf);
+  const float2 cs = X.cs, cp = X.cp;
   V3 sf, pf;
   face_basis(R.d, sf, pf);
   const V3 w = cross3(R.d, N);
@@ -1278,16 +1338,8 @@ __device__ void mirror_event_tilt(Ray<F>& R, int k, const Blob& B, float lam, co
       A.key1);
   const uint32_t word = (m & 3) == 0 ? rnd.x : (m & 3) == 1 ? rnd.y : (m & 3) == 2 ? rnd.z : rnd.w;
   const bool refl = u24(word) < M.omega;
-  float2 cs, cp, dcs, dcp;
   V3 d2 = R.d;
-  if (refl) {
-    cs = cscale(cf.rs, M.isw), cp = cscale(cf.rp, M.isw);
-    dcs = cscale(dcf.rs, M.isw), dcp = cscale(dcf.rp, M.isw);
-    d2 = v3(fmaf(-2.0f * cd, N.x, R.d.x), R.d.y, fmaf(-2.0f * cd, N.z, R.d.z));
-  } else {
-    cs = cscale(cf.ts, M.is1w), cp = cscale(cf.tp, M.is1w);
-    dcs = cscale(dcf.ts, M.is1w), dcp = cscale(dcf.tp, M.is1w);
-  }
+  if (refl) d2 = v3(fmaf(-2.0f * cd, N.x, R.d.x), R.d.y, fmaf(-2.0f * cd, N.z, R.d.z));
   const V3 pm2 = cross3(sm, d2);
   V3 sf2, pf2;
   face_basis(d2, sf2, pf2);
@@ -1298,8 +1350,7 @@ __device__ void mirror_event_tilt(Ray<F>& R, int k, const Blob& B, float lam, co
     const V3 dd = v3(tan_w<F>(col, t, 0), tan_w<F>(col, t, 1), tan_w<F>(col, t, 2));
     const V3 dNt = own ? dN : v3(0.0f, 0.0f, 0.0f);
     const float dcd = dot3(dd, N) + dot3(R.d, dNt);
-    const float dcos0 = front ? -dcd : dcd;
-    const float2 dcs_t = cscale(dcs, dcos0), dcp_t = cscale(dcp, dcos0);
+    acc[t * 32] += X.g_cos * (double)(front ? -dcd : dcd);  // part (1)
     V3 dsf, dpf;
     face_basis_d(R.d, dd, sf, dsf, dpf);
     V3 dsm = dsf;
@@ -1327,7 +1378,7 @@ __device__ void mirror_event_tilt(Ray<F>& R, int k, const Blob& B, float lam, co
       const float2 dEp = make_float2(-dsphi * a.x - sphi * da.x + dcphi * b.x + cphi * db.x,
                                      -dsphi * a.y - sphi * da.y + dcphi * b.y + cphi * db.y);
       const float2 Os = cmul(cs, Es), Op = cmul(cp, Ep);
-      const float2 dOs = cadd(cmul(dcs_t, Es), cmul(cs, dEs)), dOp = cadd(cmul(dcp_t, Ep), cmul(cp, dEp));
+      const float2 dOs = cmul(cs, dEs), dOp = cmul(cp, dEp);  // part (2): coefficients held
       tan_w<F>(col, t, 3 + 4 * f) = dcpsi * Os.x + cpsi * dOs.x + dspsi * Op.x + spsi * dOp.x;
       tan_w<F>(col, t, 4 + 4 * f) = dcpsi * Os.y + cpsi * dOs.y + dspsi * Op.y + spsi * dOp.y;
       tan_w<F>(col, t, 5 + 4 * f) = -dspsi * Os.x - spsi * dOs.x + dcpsi * Op.x + cpsi * dOp.x;
@@ -1357,34 +1408,24 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_mbar;
   constexpr int W = 3 + 4 * F;
-  const int lane = threadIdx.x & 31;
-  float* col = reinterpret_cast<float*>(smem + A.blob_bytes) + (threadIdx.x >> 5) * (kTiltPass * W * 32) + lane;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* acc = reinterpret_cast<double*>(smem + A.blob_bytes) + warp * (kTiltPass * 32) + lane;
+  float* col = reinterpret_cast<float*>(smem + A.blob_bytes + sizeof(double) * (kTiltBlock / 32) * kTiltPass * 32) +
+               warp * (kTiltPass * W * 32) + lane;
   if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;
   Blob B;
   B.bind(smem);
   const BlobHeader& H = *B.h;
   const int k0 = A.tilt_k0, nk = min(kTiltPass, H.n_mir - k0);
-  double acc[kTiltPass];
-#pragma unroll
-  for (int t = 0; t < kTiltPass; ++t) acc[t] = 0.0;
-  const bool listed = A.replay_list != nullptr;
-  const long long n_items = listed ? A.list_end - A.list_begin : A.ray_end - A.ray_begin;
+  for (int t = 0; t < kTiltPass; ++t) acc[t * 32] = 0.0;
   const float n = H.n_slab;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_items;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < A.n_heads;
        i += (long long)gridDim.x * blockDim.x) {
-    long long id, cell;
-    if (listed) {
-      const ExitRec e = A.replay_list[A.list_begin + i];
-      if (A.G[e.flat] == 0.0) continue;
-      id = e.id;
-      cell = e.flat / A.bins;
-    } else {
-      id = A.ray_begin + i;
-      cell = id / A.n_cell;
-    }
+    const RayHead rh = A.ray_heads[i];
+    const long long cell = rh.cell;
     const ChunkConst cc = chunk_const(A, cell);
     Ray<F> R;
-    gen_ray(R, id, cc, H, A);
+    gen_ray(R, rh.id, cc, H, A);
     for (int t = 0; t < nk; ++t)
       for (int w = 0; w < W; ++w) tan_w<F>(col, t, w) = 0.0f;
     for (;;) {
@@ -1395,7 +1436,12 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
       R.p = v3(fmaf(tt, R.d.x, R.p.x), fmaf(tt, R.d.y, R.p.y), fmaf(tt, R.d.z, R.p.z));
       R.last = sid;
       if (sid >= S_MIR) {
-        mirror_event_tilt<F>(R, sid - S_MIR, B, cc.lam, A, k0, nk, col);
+        if (R.hits >= rh.emit) {  // more hits than the replay recorded: not the replayed path
+          atomicOr(A.error, 8u);
+          break;
+        }
+        const TiltAux X = A.tilt_aux[rh.first + R.hits];
+        mirror_event_tilt<F>(R, sid - S_MIR, B, A, k0, nk, col, acc, X);
         if (R.ev >= A.max_events) break;
         continue;
       }
@@ -1433,6 +1479,10 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
         continue;
       }
       if (o.cat == L_EYEBOX) {  // dI = (dT_s |a|^2 + 2 T_s Re(a* da) + ...) / F
+        if (R.hits != rh.emit) {
+          atomicOr(A.error, 8u);
+          break;
+        }
         const double g = A.G[cell * A.bins + o.bin];
         float dTs, dTp;
         exit_T_d(n, ci, dTs, dTp);
@@ -1446,7 +1496,7 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
             dI += dTs * dci * cabs2(R.a[f]) + 2.0f * o.Ts * fmaf(R.a[f].x, da.x, R.a[f].y * da.y);
             dI += dTp * dci * cabs2(R.b[f]) + 2.0f * o.Tp * fmaf(R.b[f].x, db.x, R.b[f].y * db.y);
           }
-          acc[t] += g * (double)(dI * (1.0f / F));
+          acc[t * 32] += g * (double)(dI * (1.0f / F));
         }
       }
       break;
@@ -1454,7 +1504,7 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
   }
   const double per_degree = 3.14159265358979323846 / 180.0;
   for (int t = 0; t < nk; ++t) {
-    double v = acc[t];
+    double v = acc[t * 32];
 #pragma unroll
     for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     if (lane == 0 && v != 0.0) atomicAdd(A.grad_tilt + k0 + t, v * per_degree);
@@ -1462,7 +1512,8 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
 }
 
 size_t tilt_smem_bytes(int blob_bytes, int F) {
-  return (size_t)blob_bytes + sizeof(float) * (size_t)(kTiltBlock / 32) * kTiltPass * (3 + 4 * F) * 32;
+  return (size_t)blob_bytes + sizeof(double) * (size_t)(kTiltBlock / 32) * kTiltPass * 32 +
+         sizeof(float) * (size_t)(kTiltBlock / 32) * kTiltPass * (3 + 4 * F) * 32;
 }
 
 // exclusive prefix of the per-stack record counts (one block)
@@ -1731,7 +1782,14 @@ static int occupancy(K kernel, size_t smem) {
 #define WG_PICK_P(K, P) ((P) == 3 ? K<3> : (P) == 2 ? K<2> : K<0>)
 
 int trace_fwd_blocks_per_sm(int F, int P, size_t smem) { return occupancy(WG_PICK_FP(k_trace_fwd, F, P), smem); }
-int bwd_replay_blocks_per_sm(int F, int P, size_t smem) { return occupancy(WG_PICK_FP(k_bwd_replay, F, P), smem); }
+template <bool T>
+static void (*pick_replay(int F, int P))(const TraceArgs) {
+  return F == 2 ? (P == 3 ? k_bwd_replay<2, 3, T> : P == 2 ? k_bwd_replay<2, 2, T> : k_bwd_replay<2, 0, T>)
+                : (P == 3 ? k_bwd_replay<1, 3, T> : P == 2 ? k_bwd_replay<1, 2, T> : k_bwd_replay<1, 0, T>);
+}
+int bwd_replay_blocks_per_sm(int F, int P, bool tilt, size_t smem) {
+  return occupancy(tilt ? pick_replay<true>(F, P) : pick_replay<false>(F, P), smem);
+}
 int bwd_adjoint_blocks_per_sm(int P, size_t smem) { return occupancy(WG_PICK_P(k_bwd_adjoint, P), smem); }
 int tilt_blocks_per_sm(int F, int P, size_t smem) {
   (void)P;
@@ -1772,8 +1830,8 @@ cudaError_t launch_trace_fwd_fused(const TraceArgs* jobs_dev, const int* cta_job
   return cudaGetLastError();
 }
 
-cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s) {
-  auto k = WG_PICK_FP(k_bwd_replay, F, P);
+cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, bool tilt, int grid, size_t smem, cudaStream_t s) {
+  auto k = tilt ? pick_replay<true>(F, P) : pick_replay<false>(F, P);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   note_launches(1);
   k<<<grid, kBlock, smem, s>>>(a);
