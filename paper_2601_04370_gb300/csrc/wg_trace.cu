@@ -1312,9 +1312,11 @@ __device__ __forceinline__ float& tan_w(float* col, int t, int w) {
 
 // mirror_event with tangents: the same geometry and decision as the
 // forward, the coefficients as the replay applied them
+// live: bit t set once the ray has hit mirror k0 + t (every other tangent is
+// still zero, and its column is not touched)
 template <int F>
 __device__ void mirror_event_tilt(Ray<F>& R, int k, const Blob& B, const TraceArgs& A, int k0, int nk, float* col,
-                                  double* acc, const TiltAux& X) {
+                                  double* acc, const TiltAux& X, unsigned& live) {
   const MirrorRec& M = B.mir[k];
   const V3 N = v3(M.nx, 0.0f, M.nz);
   const V3 dN = v3(-M.nz, 0.0f, M.nx);  // dN/d(tilt) per radian
@@ -1344,9 +1346,15 @@ __device__ void mirror_event_tilt(Ray<F>& R, int k, const Blob& B, const TraceAr
   V3 sf2, pf2;
   face_basis(d2, sf2, pf2);
   const float cpsi = dot3(sf2, sm), spsi = dot3(sf2, pm2);
+  const int to = k - k0;
+  if (to >= 0 && to < nk && !((live >> to) & 1u)) {
+    for (int w = 0; w < 3 + 4 * F; ++w) tan_w<F>(col, to, w) = 0.0f;
+    live |= 1u << to;
+  }
   // tangents (the field before the hit is still in R)
-  for (int t = 0; t < nk; ++t) {
-    const bool own = k0 + t == k;
+  for (unsigned lm = live; lm; lm &= lm - 1) {
+    const int t = __ffs(lm) - 1;
+    const bool own = t == to;
     const V3 dd = v3(tan_w<F>(col, t, 0), tan_w<F>(col, t, 1), tan_w<F>(col, t, 2));
     const V3 dNt = own ? dN : v3(0.0f, 0.0f, 0.0f);
     const float dcd = dot3(dd, N) + dot3(R.d, dNt);
@@ -1426,8 +1434,7 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
     const ChunkConst cc = chunk_const(A, cell);
     Ray<F> R;
     gen_ray(R, rh.id, cc, H, A);
-    for (int t = 0; t < nk; ++t)
-      for (int w = 0; w < W; ++w) tan_w<F>(col, t, w) = 0.0f;
+    unsigned live = 0u;
     for (;;) {
       float tt;
       const int sid = next_surface(B, R.p, R.d, R.last, R.reg, tt);
@@ -1441,7 +1448,7 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
           break;
         }
         const TiltAux X = A.tilt_aux[rh.first + R.hits];
-        mirror_event_tilt<F>(R, sid - S_MIR, B, A, k0, nk, col, acc, X);
+        mirror_event_tilt<F>(R, sid - S_MIR, B, A, k0, nk, col, acc, X, live);
         if (R.ev >= A.max_events) break;
         continue;
       }
@@ -1456,10 +1463,15 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
       const Outcome o = face_event<F>(R, sid, H, A, nullptr, nullptr, dummy);
       const float ci = fabsf(dz0), sg = dz0 < 0.0f ? -1.0f : 1.0f;
       if (!o.term) {  // TIR: d_z flipped, field times (r_s, r_p)(cos i)
+        if (!live) {
+          if (R.ev >= A.max_events) break;
+          continue;
+        }
         float2 rs, rp, drs, drp;
         tir_coef(n, ci, fmaf(-ci, ci, 1.0f), rs, rp);
         tir_coef_d(n, ci, rs, rp, drs, drp);
-        for (int t = 0; t < nk; ++t) {
+        for (unsigned lm = live; lm; lm &= lm - 1) {
+          const int t = __ffs(lm) - 1;
           const float ddz = tan_w<F>(col, t, 2);
           const float dci = sg * ddz;
           tan_w<F>(col, t, 2) = -ddz;
@@ -1486,7 +1498,8 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
         const double g = A.G[cell * A.bins + o.bin];
         float dTs, dTp;
         exit_T_d(n, ci, dTs, dTp);
-        for (int t = 0; t < nk; ++t) {
+        for (unsigned lm = live; lm; lm &= lm - 1) {
+          const int t = __ffs(lm) - 1;
           const float dci = sg * tan_w<F>(col, t, 2);
           float dI = 0.0f;
 #pragma unroll
