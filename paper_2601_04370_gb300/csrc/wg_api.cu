@@ -103,6 +103,7 @@ struct wg_design {
   // valid for the configuration and geometry with fingerprint exit_fp (0: none)
   DevBuf exits;
   uint64_t exit_fp = 0;
+  long long exit_cap = 0;  // entries of the list (rays + hole allowance)
 };
 
 static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -618,11 +619,11 @@ static uint64_t path_fingerprint(const wg_design* d, const wg_trace_cfg* cfg, co
 
 // Device list of eyebox rays for a forward trace of p (null when not recorded).
 static const size_t kExitHead = 64;  // count word, padded
-static wg_status prepare_exit_list(wg_design* d, const wg_trace_cfg* cfg, const Plan& p, cudaStream_t s,
-                                   TraceArgs& a) {
+static wg_status prepare_exit_list(wg_design* d, const wg_trace_cfg* cfg, const Plan& p, int sm_count,
+                                   cudaStream_t s, TraceArgs& a) {
   d->exit_fp = 0;
   if (cfg->flags & WG_TRACE_NO_EXIT_LIST) return WG_OK;
-  const long long n = p.re - p.rb;
+  const long long n = exit_list_cap(p.re - p.rb, sm_count);
   const size_t bytes = kExitHead + sizeof(ExitRec) * (size_t)n;
   if (bytes > ((size_t)8 << 30)) return WG_OK;  // not worth 8 GB: the backward replays every ray
   if (bytes > d->exits.n) CU(d->exits.ensure(bytes));
@@ -630,6 +631,7 @@ static wg_status prepare_exit_list(wg_design* d, const wg_trace_cfg* cfg, const 
   a.exit_count = static_cast<unsigned long long*>(d->exits.p);
   a.exit_list = reinterpret_cast<ExitRec*>(static_cast<uint8_t*>(d->exits.p) + kExitHead);
   a.exit_cap = n;
+  d->exit_cap = n;
   return WG_OK;
 }
 
@@ -685,7 +687,7 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
   TraceArgs a = base_args(d, cfg, p, w);
   a.tally = t;
   wg_design* dm = const_cast<wg_design*>(d);  // the eyebox-ray list is a cache owned by the design
-  st = prepare_exit_list(dm, cfg, p, s, a);
+  st = prepare_exit_list(dm, cfg, p, c->sm_count, s, a);
   if (st != WG_OK) return st;
   const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, d->period, smem));
   const int grid = (int)std::min<long long>(p.n_chunks, (long long)c->sm_count * bps);
@@ -734,7 +736,7 @@ size_t eval_device_bytes(const wg_design* d, const wg_trace_cfg* cfg, bool backw
   if (make_plan(d, cfg, 2048, p) != WG_OK) return 0;
   const long long rays = p.re - p.rb;
   size_t b = sizeof(double) * (size_t)p.tally_size;      // tally
-  b += 64 + sizeof(ExitRec) * (size_t)rays;              // eyebox-ray list
+  b += 64 + sizeof(ExitRec) * (size_t)exit_list_cap(rays, d->ctx->sm_count);  // eyebox-ray list (with holes)
   if (backward) {
     b += sizeof(double) * (size_t)p.tally_size;          // dL/dtally
     const long long batch = std::min<long long>(rays, 1ll << 22);
@@ -875,7 +877,7 @@ wg_status fused_prepare(wg_ctx* c, FusedJob* jobs, int n, int blocks_per_sm, Fus
     } else if (!(J.cfg->flags & WG_TRACE_NO_EXIT_LIST)) {
       wg_design* dm = const_cast<wg_design*>(J.design);
       dm->exit_fp = 0;
-      const long long nr = p.re - p.rb;
+      const long long nr = exit_list_cap(p.re - p.rb, c->sm_count);
       const size_t bytes = kExitHead + sizeof(ExitRec) * (size_t)nr;
       if (bytes <= ((size_t)8 << 30)) {
         std::lock_guard<std::mutex> lk(c->mu);
@@ -883,6 +885,7 @@ wg_status fused_prepare(wg_ctx* c, FusedJob* jobs, int n, int blocks_per_sm, Fus
         a.exit_count = static_cast<unsigned long long*>(dm->exits.p);
         a.exit_list = reinterpret_cast<ExitRec*>(static_cast<uint8_t*>(dm->exits.p) + kExitHead);
         a.exit_cap = nr;
+        dm->exit_cap = nr;
       }
     }
     B.args[j] = a;
@@ -1143,7 +1146,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     unsigned long long cnt = 0;
     CU(cudaMemcpyAsync(&cnt, d->exits.p, sizeof(cnt), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
-    use_list = (long long)cnt <= p.re - p.rb;  // more would mean the list overflowed
+    use_list = (long long)cnt <= d->exit_cap;  // more would mean the list overflowed
     n_list = (long long)cnt;
   }
   const ExitRec* list =

@@ -151,34 +151,38 @@ struct MatK {
   int evan;
 };
 
-// rad = 1 - (n0/n)^2 sin^2 t0 = cos^2 t with (n0/n)^2 rounded once from FP64.
-// cos t (which sets every layer's phase rate, and a long stack multiplies
-// the phase error by its length) is a correctly rounded square root, and the
-// quotients are IEEE except cos t / n = cos t * (1/n).
+// rad = 1 - (n0/n)^2 sin^2 t0 = cos^2 t with (n0/n)^2 rounded once from FP64;
+// c = sqrt|rad| is cos t (propagating) or a (evanescent, cos t = -i a).
+// c sets every layer's phase rate, and a long stack multiplies the phase
+// error by its length, so it is taken to within about half an ulp: the
+// hardware reciprocal square root r, one Newton step on r (Newton-Raphson for
+// 1/sqrt), then c = rad r with one Newton correction of the square. The
+// quotients 1/(n c) and n/c start from r / n and n r and take one Newton
+// correction each (residual of the product, times the reciprocal), which
+// brings them to about half an ulp as well.
+// No divide and no branch: each hit evaluates this for every material.
 __device__ __forceinline__ MatK mat_const(float sin2_0, float n, float inv_n, float r2, float inv_lam) {
   MatK k;
   const float rad = fmaf(-r2, sin2_0, 1.0f);
-  if (rad >= 0.0f) {
-    const float ct = sqrtf(rad);
-    const float eta = n * ct;
-    k.kt = eta * inv_lam;
-    k.kap = TWO_PI * k.kt;
-    k.q12s = 1.0f / eta;
-    k.q21s = eta;
-    k.q12p = ct * inv_n;
-    k.q21p = n / ct;
-    k.evan = 0;
-  } else {
-    const float a = sqrtf(-rad);
-    const float na = n * a;
-    k.kap = TWO_PI * na * inv_lam;
-    k.kt = k.kap;
-    k.q12s = 1.0f / na;
-    k.q21s = -na;
-    k.q12p = -a * inv_n;
-    k.q21p = n / a;
-    k.evan = 1;
-  }
+  const bool ev = !(rad >= 0.0f);
+  const float x = fmaxf(fabsf(rad), 1e-30f);
+  float r = rsqrtf(x);
+  r = fmaf(0.5f * r, fmaf(-x * r, r, 1.0f), r);
+  float c = x * r;
+  c = fmaf(0.5f * r, fmaf(-c, c, x), c);
+  const float nc = n * c;
+  const float kt = nc * inv_lam;
+  float q12 = r * inv_n;
+  q12 = fmaf(q12, fmaf(-nc, q12, 1.0f), q12);  // 1 / (n c)
+  float q21p = n * r;
+  q21p = fmaf(fmaf(-c, q21p, n), r, q21p);     // n / c
+  k.kap = TWO_PI * kt;
+  k.kt = ev ? k.kap : kt;
+  k.q12s = q12;
+  k.q21s = ev ? -nc : nc;
+  k.q12p = (ev ? -c : c) * inv_n;
+  k.q21p = q21p;
+  k.evan = ev;
   return k;
 }
 

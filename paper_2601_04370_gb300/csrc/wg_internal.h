@@ -107,6 +107,13 @@ constexpr int kFwdSlots = 3;
 // rays a warp of the forward kernel owns at a time (its lanes plus its two
 // shared-memory queues); a queued ray takes 9 + 4 F words
 constexpr int kFwdQCap = 48;
+// a warp of the forward kernel reserves eyebox-ray list slots this many at a
+// time (one global atomic per chunk); slots it leaves unused are holes
+// (flat = -1). The list holds at most rays + 64 warps per SM x one chunk.
+constexpr int kExitChunk = 64;
+inline long long exit_list_cap(long long rays, int sm_count) {
+  return rays + (long long)sm_count * 64 * kExitChunk;
+}
 inline size_t fwd_smem_bytes(int blob_bytes, long long bins, int F) {
   return (size_t)blob_bytes + sizeof(float) * (size_t)kFwdSlots * (size_t)bins +
          sizeof(uint32_t) * (size_t)(kBlock / 32) * 2 * (size_t)kFwdQCap * (size_t)(9 + 4 * F);

@@ -746,6 +746,7 @@ __global__ void __launch_bounds__(kBlock, 2)
           (unsigned long long)((A.ray_end - A.ray_begin) / ((long long)max(1, A.n_cta) * (kBlock / 32)) + 256) +
       (1ull << 24);
   unsigned long long iters = 0;
+  unsigned long long x_next = 0, x_end = 0;  // this warp's unused eyebox-list slots (warp-uniform)
   for (;;) {
     if (++iters > it_cap) {
       if (lane == 0) atomicOr(A.error, 16u);
@@ -872,14 +873,18 @@ __global__ void __launch_bounds__(kBlock, 2)
           for (unsigned mm = peers; mm; mm &= mm - 1) sum += __shfl_sync(peers, pend_I, __ffs(mm) - 1);
           if (lane == __ffs(peers) - 1) atomicAdd(&s_tally[key], sum);
         }
-        // list of eyebox rays for the adjoint (one reservation per warp)
+        // list of eyebox rays for the adjoint: slots from the warp's reserved
+        // chunk, a new chunk of kExitChunk when it runs out
         if (A.exit_list) {
-          const int leader = __ffs(pm) - 1;
-          unsigned long long base = 0;
-          if (lane == leader) base = atomicAdd(A.exit_count, (unsigned long long)__popc(pm));
-          base = __shfl_sync(FULL, base, leader);
+          const unsigned cnt = __popc(pm), rank = __popc(pm & lt_mask);
+          const unsigned left = (unsigned)(x_end - x_next);
+          unsigned long long nb = 0;
+          if (cnt > left) {
+            if (lane == 0) nb = atomicAdd(A.exit_count, (unsigned long long)kExitChunk);
+            nb = __shfl_sync(FULL, nb, 0);
+          }
           if (pend_bin >= 0) {
-            const unsigned long long i = base + __popc(pm & lt_mask);
+            const unsigned long long i = rank < left ? x_next + rank : nb + (rank - left);
             if (i < (unsigned long long)A.exit_cap) {
               ExitRec e;
               e.id = R.id;
@@ -887,6 +892,12 @@ __global__ void __launch_bounds__(kBlock, 2)
               e.pad = 0;
               A.exit_list[i] = e;
             }
+          }
+          if (cnt > left) {
+            x_next = nb + (cnt - left);
+            x_end = nb + kExitChunk;
+          } else {
+            x_next += cnt;
           }
         }
       }
@@ -949,6 +960,16 @@ __global__ void __launch_bounds__(kBlock, 2)
       }
     } else {
       idling = false;
+    }
+  }
+  // the rest of the warp's last chunk: holes
+  for (unsigned long long i = x_next + lane; i < x_end; i += 32) {
+    if (i < (unsigned long long)A.exit_cap) {
+      ExitRec e;
+      e.id = -1;
+      e.flat = -1;
+      e.pad = 0;
+      A.exit_list[i] = e;
     }
   }
   // ---- statistics ----
@@ -1069,7 +1090,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
               if (A.replay_list) {
                 // listed ray: replayed only if its bin carries gradient
                 const ExitRec e = A.replay_list[u_next + rank];
-                if (A.G[e.flat] != 0.0) {
+                if (e.flat >= 0 && A.G[e.flat] != 0.0) {  // flat < 0: a hole of the list
                   cell_l = e.flat / A.bins;
                   const ChunkConst cc = chunk_const(A, cell_l);
                   gen_ray(R, e.id, cc, H, A);
