@@ -65,7 +65,9 @@ typedef int32_t wg_status;
  * geometry), so a later wg_trace_backward with the same configuration and
  * geometry, whatever the thicknesses, replays only the listed rays whose bin
  * has a non-zero dL/dtally; every other ray contributes no gradient. Any
- * other backward call replays every ray. */
+ * other backward call replays every ray. The list holds up to 16 bytes x
+ * (rays + 4096 x the GPU's SM count); unused slots are marked with bin -1.
+ * A forward with WG_TRACE_NO_EXIT_LIST leaves an earlier list as it was. */
 #define WG_TRACE_NO_EXIT_LIST 1  /* forward: do not record the list */
 
 /* energy ledger slots (wg_stats.ledger) */
@@ -326,7 +328,12 @@ wg_status wg_trace_forward_noalloc(wg_ctx* ctx, const wg_design* d, const wg_tra
  * kernel variant, each design on its own range of CTAs, chunk sizes and CTAs
  * per SM from the autotuned table); a batch whose launches were captured
  * before replays the captured CUDA graph. Then it runs the loss and adjoint
- * of loss+gradient requests and completes the tickets. Designs stay resident
+ * of loss+gradient requests and completes the tickets. With max_slots > 1
+ * loss+gradient requests run instead on a second lane (its own thread,
+ * internal context and lower-priority stream, FIFO, one at a time) that
+ * overlaps the forward lane on the GPU, so forward requests do not wait for
+ * adjoints; forward requests then record no eyebox-ray list. max_slots = 1
+ * serves every request FIFO, one design per launch. Designs stay resident
  * on the device; the caller must not change or destroy a design while a
  * request that uses it is pending.
  * ------------------------------------------------------------------------ */

@@ -621,8 +621,10 @@ static uint64_t path_fingerprint(const wg_design* d, const wg_trace_cfg* cfg, co
 static const size_t kExitHead = 64;  // count word, padded
 static wg_status prepare_exit_list(wg_design* d, const wg_trace_cfg* cfg, const Plan& p, int sm_count,
                                    cudaStream_t s, TraceArgs& a) {
-  d->exit_fp = 0;
+  // a forward without the list leaves the design's list (and the
+  // configuration and geometry it is valid for) as it is
   if (cfg->flags & WG_TRACE_NO_EXIT_LIST) return WG_OK;
+  d->exit_fp = 0;
   const long long n = exit_list_cap(p.re - p.rb, sm_count);
   const size_t bytes = kExitHead + sizeof(ExitRec) * (size_t)n;
   if (bytes > ((size_t)8 << 30)) return WG_OK;  // not worth 8 GB: the backward replays every ray
@@ -767,8 +769,6 @@ struct FusedPinned {
 
 // per-job workspace heads of a fused launch, contiguous at this stride
 static const size_t kHeadStride = 256;
-// a fused launch has this many times the CTAs the GPU holds at once
-static const int kOversub = 4;
 
 struct FusedBatch::Impl {
   FusedPinned pin;
@@ -825,8 +825,8 @@ wg_status fused_prepare(wg_ctx* c, FusedJob* jobs, int n, int blocks_per_sm, Fus
   // device arena: heads (contiguous) | per-job arrays | job table | CTA map;
   // the pinned buffer mirrors the same offsets for what is copied in
   const int max_grid = c->sm_count * 2;
-  // <= 6 groups, each <= kOversub * G + 1.5 n_g CTAs
-  const size_t max_ctas = 6 * (size_t)kOversub * (size_t)max_grid + 2 * (size_t)n;
+  // every job <= G CTAs (G <= max_grid)
+  const size_t max_ctas = (size_t)n * (size_t)max_grid;
   size_t off = align16((size_t)n * kHeadStride);
   std::vector<size_t> job_off(n);
   for (int j = 0; j < n; ++j) {
@@ -872,9 +872,11 @@ wg_status fused_prepare(wg_ctx* c, FusedJob* jobs, int n, int blocks_per_sm, Fus
     TraceArgs a = base_args(J.design, J.cfg, p, w);
     a.tally = J.tally;
     a.records = nullptr;
-    if (dup[j]) {
+    if (J.cfg->flags & WG_TRACE_NO_EXIT_LIST) {
+      // no list: the design's list stays valid for what it was made for
+    } else if (dup[j]) {
       const_cast<wg_design*>(J.design)->exit_fp = 0;
-    } else if (!(J.cfg->flags & WG_TRACE_NO_EXIT_LIST)) {
+    } else {
       wg_design* dm = const_cast<wg_design*>(J.design);
       dm->exit_fp = 0;
       const long long nr = exit_list_cap(p.re - p.rb, c->sm_count);
@@ -917,19 +919,24 @@ wg_status fused_prepare(wg_ctx* c, FusedJob* jobs, int n, int blocks_per_sm, Fus
     if (blocks_per_sm > 0) bps = std::min(bps, blocks_per_sm);
     const int G = c->sm_count * bps;
     FusedBatch::Impl::Group gr{F, P, 0, (int)g0, (int)n_cta, sm_max};
-    // CTAs per job in proportion to its estimated work (at least one, at most
-    // its chunks), kOversub times what the GPU holds at once, in an order
-    // that interleaves the jobs: a job's CTAs exit when its chunks are gone
-    // and the hardware then starts pending CTAs, which belong to every job,
-    // so the jobs that are still running get the freed SMs
+    // CTAs per job: as many as the GPU holds at once (at most its chunks),
+    // in an order that interleaves the jobs in proportion to their estimated
+    // work. The first G CTAs to start share the GPU between the jobs; a CTA
+    // exits when its job's chunks are gone, and the hardware then starts
+    // pending CTAs, whichever job they belong to (one with no chunks left
+    // exits at once). So a job that runs longer than estimated still gets
+    // every freed SM for its tail, where a proportional split of CTAs would
+    // leave it with its own share only.
     std::vector<std::pair<double, int>> seq;
     for (size_t q = g0; q < g1; ++q) {
       const int j = order[q];
-      long long k = (long long)std::llround((double)kOversub * G * job_cost(j) / std::max(cost, 1.0));
-      k = std::max<long long>(1, std::min<long long>(k, B.plans[j].n_chunks));
+      const double share = job_cost(j) / std::max(cost, 1.0);
+      const long long k = std::max<long long>(1, std::min<long long>(G, B.plans[j].n_chunks));
       B.args[j].n_cta = (int)k;
       tab_h[q] = B.args[j];
-      for (long long b = 0; b < k; ++b) seq.push_back({((double)b + 0.5) / (double)k, (int)q});
+      // start times ~ b / (share * G): a job's first CTAs come early in
+      // proportion to its work, the rest of its G behind everyone's share
+      for (long long b = 0; b < k; ++b) seq.push_back({((double)b + 0.5) / (std::max(share, 1e-6) * G), (int)q});
     }
     std::stable_sort(seq.begin(), seq.end());
     for (const auto& e : seq)

@@ -7,6 +7,17 @@
 // its own CTAs; a batch whose device work was captured before replays the
 // CUDA graph), then runs the loss and adjoint of loss+gradient requests on
 // the same stream, copies the outputs and completes the tickets.
+//
+// With max_slots > 1 loss+gradient requests go to a second lane instead: a
+// thread with its own internal context (scratch, workspaces) and a stream of
+// lower priority runs them FIFO (forward with the eyebox-ray list, loss,
+// adjoint), while the first lane keeps fusing forward requests on a stream of
+// higher priority. The two overlap on the GPU (the forward lane's CTAs are
+// scheduled first whenever the adjoint's kernels leave SMs free), so a short
+// forward request never waits for a long adjoint to finish. Forward-only
+// requests of this mode skip the eyebox-ray list (no adjoint follows them),
+// which also leaves each design's list to the gradient lane alone.
+// max_slots = 1 keeps one lane: every request FIFO, one design per launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -82,6 +93,19 @@ struct Serve {
   std::mutex tune_mu;
   std::map<uint64_t, Tuned> tune;
   std::list<std::pair<uint64_t, Graph>> graphs;
+  // compositions seen once (captured when they come again), and the staging
+  // reused by batches that run without a graph
+  std::list<uint64_t> seen;
+  std::unique_ptr<wgh::FusedBatch> direct_fb;
+  // gradient lane (max_slots > 1)
+  bool two_lanes = false;
+  std::deque<Ticket*> gqueue;
+  std::condition_variable cv_gwork;
+  std::thread gth;
+  wg_ctx* gctx = nullptr;
+  cudaStream_t gstream = nullptr;
+  void* garena = nullptr;
+  size_t garena_n = 0;
 };
 
 constexpr size_t kMaxQueue = 4096;
@@ -89,6 +113,7 @@ constexpr size_t kMaxQueue = 4096;
 // completes when the batch does, so a bounded batch keeps latency short
 constexpr long long kBatchRays = 1ll << 25;
 constexpr size_t kMaxGraphs = 16;
+constexpr size_t kMaxSeen = 256;
 
 // class of an evaluation for the autotuned table
 uint64_t tune_key(const wg_design* d, const wg_trace_cfg* cfg) {
@@ -122,18 +147,19 @@ void save_tune_cache(Serve& S) {
   fclose(f);
 }
 
-wg_status ensure_arena(Serve& S, size_t bytes) {
-  if (bytes <= S.arena_n) return WG_OK;
-  if (S.arena) cudaFree(S.arena);
-  S.arena = nullptr;
-  S.arena_n = 0;
-  if (cudaMalloc(&S.arena, bytes) != cudaSuccess) {
+wg_status ensure_buf(void*& p, size_t& n, size_t bytes) {
+  if (bytes <= n) return WG_OK;
+  if (p) cudaFree(p);
+  p = nullptr;
+  n = 0;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
     cudaGetLastError();
     return wgh::set_error(WG_ENOMEM, "serving: device arena allocation failed");
   }
-  S.arena_n = bytes;
+  n = bytes;
   return WG_OK;
 }
+wg_status ensure_arena(Serve& S, size_t bytes) { return ensure_buf(S.arena, S.arena_n, bytes); }
 
 // Times candidate launch shapes on a bounded sample of (d, cfg) and stores
 // the fastest for its class.
@@ -244,6 +270,30 @@ wg_status run_forward(Serve& S, std::vector<wgh::FusedJob>& jobs, int bps, bool*
     cudaGraphExecDestroy(g->exec);
     S.graphs.pop_front();
     g = nullptr;
+  } else {
+    // a composition met for the first time runs directly on the reused
+    // staging; capturing pays off only for one that comes back
+    bool again = false;
+    for (auto it = S.seen.begin(); it != S.seen.end(); ++it)
+      if (*it == key) {
+        again = true;
+        S.seen.erase(it);
+        break;
+      }
+    if (!again) {
+      S.seen.push_front(key);
+      while (S.seen.size() > kMaxSeen) S.seen.pop_back();
+      if (!S.direct_fb) S.direct_fb = std::make_unique<wgh::FusedBatch>();
+      wg_status st = wgh::fused_prepare(S.ctx, jobs.data(), n, bps, *S.direct_fb);
+      if (st != WG_OK) return st;
+      st = wgh::fused_enqueue(S.ctx, jobs.data(), *S.direct_fb, S.stream);
+      if (st != WG_OK) return st;
+      if (cudaStreamSynchronize(S.stream) != cudaSuccess) {
+        cudaGetLastError();
+        return wgh::set_error(WG_EDEVICE, "serving: forward batch failed");
+      }
+      return wgh::fused_finish(S.ctx, jobs.data(), *S.direct_fb);
+    }
   }
   auto fb = std::make_unique<wgh::FusedBatch>();
   wg_status st = wgh::fused_prepare(S.ctx, jobs.data(), n, bps, *fb);
@@ -402,6 +452,80 @@ void run_batch(Serve& S, std::vector<Ticket*>& batch) {
   }
 }
 
+// One loss+gradient request on the gradient lane: forward (with the
+// eyebox-ray list), loss, adjoint, outputs; all on the lane's own context.
+void run_grad(Serve& S, Ticket& t) {
+  const size_t a_tally = ((sizeof(double) * (size_t)t.tally_n) + 255) & ~(size_t)255;
+  const size_t a_grad = ((sizeof(double) * (size_t)std::max(1ll, t.grad_n)) + 255) & ~(size_t)255;
+  wg_status e = ensure_buf(S.garena, S.garena_n, 2 * a_tally + a_grad);
+  if (e != WG_OK) {
+    t.result.status = e;
+    t.err = "serving: device arena allocation failed";
+    return;
+  }
+  uint8_t* A = static_cast<uint8_t*>(S.garena);
+  double* tally = reinterpret_cast<double*>(A);
+  double* G = reinterpret_cast<double*>(A + a_tally);
+  double* grad = reinterpret_cast<double*>(A + 2 * a_tally);
+  wg_trace_cfg cfg = t.req.cfg;
+  cfg.stream = S.gstream;
+  wg_stats st;
+  memset(&st, 0, sizeof(st));
+  double loss[4] = {0, 0, 0, 0};
+  e = wg_trace_forward(S.gctx, t.req.design, &cfg, tally, &st);
+  t.result.stats = st;
+  if (e == WG_OK && !t.cancel) e = wg_loss(S.gctx, t.req.design, &cfg, t.req.loss_kind, t.req.w_f, t.req.w_e, tally, loss, G);
+  if (e == WG_OK && !t.cancel) e = wg_trace_backward(S.gctx, t.req.design, &cfg, G, grad, nullptr, nullptr);
+  if (e == WG_OK && t.req.grad_thickness &&
+      cudaMemcpyAsync(t.req.grad_thickness, grad, sizeof(double) * (size_t)t.grad_n, cudaMemcpyDefault, S.gstream) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    e = WG_EDEVICE;
+  }
+  if (e == WG_OK && t.req.tally &&
+      cudaMemcpyAsync(t.req.tally, tally, sizeof(double) * (size_t)t.tally_n, cudaMemcpyDefault, S.gstream) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    e = WG_EDEVICE;
+  }
+  if (cudaStreamSynchronize(S.gstream) != cudaSuccess) {
+    cudaGetLastError();
+    if (e == WG_OK) e = WG_EDEVICE;
+  }
+  if (e == WG_OK && t.req.loss) memcpy(t.req.loss, loss, sizeof(loss));
+  if (e != WG_OK) {
+    t.result.status = e;
+    t.err = wg_last_error();
+  }
+}
+
+void gscheduler(Serve* Sp) {
+  Serve& S = *Sp;
+  cudaSetDevice(wgh::ctx_device(S.ctx));
+  for (;;) {
+    Ticket* t = nullptr;
+    {
+      std::unique_lock<std::mutex> lk(S.mu);
+      S.cv_gwork.wait(lk, [&] { return S.stop || !S.gqueue.empty(); });
+      if (S.stop) break;
+      t = S.gqueue.front();
+      S.gqueue.pop_front();
+      t->state = RUNNING;
+      t->t_start = Clock::now();
+      t->result.status = WG_OK;
+      t->result.batch_size = 1;
+    }
+    run_grad(S, *t);
+    {
+      std::lock_guard<std::mutex> lk(S.mu);
+      t->t_done = Clock::now();
+      if (t->cancel) t->result.status = WG_ECANCELED;
+      t->state = DONE;
+    }
+    S.cv_done.notify_all();
+  }
+}
+
 void scheduler(Serve* Sp) {
   Serve& S = *Sp;
   cudaSetDevice(wgh::ctx_device(S.ctx));
@@ -465,13 +589,34 @@ Serve* serve_of(wg_ctx* c, bool create) {
     Serve* S = new Serve();
     S->ctx = c;
     cudaSetDevice(wgh::ctx_device(c));
-    if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    S->two_lanes = wgh::ctx_max_slots(c) > 1;
+    int lo = 0, hi = 0;  // numerically lower = higher priority
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess) {
+      cudaGetLastError();
+      lo = hi = 0;
+    }
+    if (cudaStreamCreateWithPriority(&S->stream, cudaStreamNonBlocking, S->two_lanes ? hi : lo) != cudaSuccess) {
       cudaGetLastError();
       delete S;
       return nullptr;
     }
+    if (S->two_lanes) {
+      wg_init_opts o;
+      memset(&o, 0, sizeof(o));
+      o.device = wgh::ctx_device(c);
+      o.max_slots = 1;
+      if (wg_init(&S->gctx, &o) != WG_OK ||
+          cudaStreamCreateWithPriority(&S->gstream, cudaStreamNonBlocking, lo) != cudaSuccess) {
+        cudaGetLastError();
+        if (S->gctx) wg_shutdown(S->gctx);
+        cudaStreamDestroy(S->stream);
+        delete S;
+        return nullptr;
+      }
+    }
     load_tune_cache(*S);
     S->th = std::thread(scheduler, S);
+    if (S->two_lanes) S->gth = std::thread(gscheduler, S);
     *slot = S;
   }
   return static_cast<Serve*>(*slot);
@@ -493,12 +638,25 @@ void serve_shutdown(wg_ctx* c) {
       t->result.status = WG_ECANCELED;
     }
     S->queue.clear();
+    for (Ticket* t : S->gqueue) {
+      t->state = DONE;
+      t->result.status = WG_ECANCELED;
+    }
+    S->gqueue.clear();
   }
   S->cv_work.notify_all();
+  S->cv_gwork.notify_all();
   if (S->th.joinable()) S->th.join();
+  if (S->gth.joinable()) S->gth.join();
   S->cv_done.notify_all();
   cudaSetDevice(ctx_device(c));
   if (S->stream) cudaStreamSynchronize(S->stream);
+  if (S->gstream) {
+    cudaStreamSynchronize(S->gstream);
+    cudaStreamDestroy(S->gstream);
+  }
+  if (S->garena) cudaFree(S->garena);
+  if (S->gctx) wg_shutdown(S->gctx);
   for (auto& g : S->graphs) cudaGraphExecDestroy(g.second.exec);
   S->graphs.clear();
   if (S->arena) cudaFree(S->arena);
@@ -558,10 +716,19 @@ extern "C" wg_status wg_submit(wg_ctx* c, const wg_request* req, wg_ticket* tick
     t->id = S->next_id++;
     t->t_submit = Clock::now();
     *ticket = t->id;
-    S->queue.push_back(t.get());
+    if (S->two_lanes && bwd) {
+      S->gqueue.push_back(t.get());
+    } else {
+      if (S->two_lanes) t->req.cfg.flags |= WG_TRACE_NO_EXIT_LIST;  // no adjoint follows
+      S->queue.push_back(t.get());
+    }
     S->all.emplace(t->id, std::move(t));
   }
-  S->cv_work.notify_one();
+  if (S->two_lanes && bwd) {
+    S->cv_gwork.notify_one();
+  } else {
+    S->cv_work.notify_one();
+  }
   return WG_OK;
 }
 
@@ -600,6 +767,7 @@ extern "C" wg_status wg_cancel(wg_ctx* c, wg_ticket ticket) {
   Ticket* t = it->second.get();
   if (t->state == QUEUED) {
     S->queue.erase(std::remove(S->queue.begin(), S->queue.end(), t), S->queue.end());
+    S->gqueue.erase(std::remove(S->gqueue.begin(), S->gqueue.end(), t), S->gqueue.end());
     t->state = DONE;
     t->result.status = WG_ECANCELED;
     t->t_start = t->t_done = Clock::now();

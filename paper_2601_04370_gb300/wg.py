@@ -333,27 +333,35 @@ def _torch_autograd():
     import torch
 
     class WGTrace(torch.autograd.Function):
-        """tally = WGTrace.apply(thickness_nm, ctx, design_handle, cfg).
+        """tally = WGTrace.apply(thickness_nm, ctx, design_handle, cfg[, tilt_deg]).
 
-        forward: wg_set_params + wg_trace_forward; backward: wg_trace_backward
-        with grad_output as dL/dtally, returning dL/dthickness (FP64 -> FP32)."""
+        forward: wg_set_params (thicknesses, and the mirror tilts in degrees
+        when given) + wg_trace_forward; backward: wg_trace_backward with
+        grad_output as dL/dtally, returning dL/dthickness and, for a tilt
+        tensor, dL/dtilt per degree (FP64 -> the inputs' dtypes)."""
 
         @staticmethod
-        def forward(actx, thickness, ctx, dh, cfg):
-            dh.set_params(thickness_nm=thickness.detach().float().contiguous())
+        def forward(actx, thickness, ctx, dh, cfg, tilt_deg=None):
+            tl = None if tilt_deg is None else tilt_deg.detach().float().cpu().numpy()
+            dh.set_params(thickness_nm=thickness.detach().float().contiguous(), tilt_deg=tl)
             tally = torch.empty(cfg.tally_shape, dtype=torch.float64, device=thickness.device)
             ctx.trace_forward(dh, cfg, tally, stats=False)
             actx.wg = (ctx, dh, cfg)
             actx.n = thickness.numel()
             actx.dtype = thickness.dtype
+            actx.tilt = None if tilt_deg is None else (tilt_deg.numel(), tilt_deg.dtype, tilt_deg.device)
             return tally
 
         @staticmethod
         def backward(actx, grad_tally):
             ctx, dh, cfg = actx.wg
             g = torch.empty(actx.n, dtype=torch.float64, device=grad_tally.device)
-            ctx.trace_backward(dh, cfg, grad_tally.contiguous().to(torch.float64), g, stats=False)
-            return g.to(actx.dtype), None, None, None
+            gt = None
+            if actx.tilt is not None and actx.needs_input_grad[4]:
+                gt = torch.empty(actx.tilt[0], dtype=torch.float64, device=grad_tally.device)
+            ctx.trace_backward(dh, cfg, grad_tally.contiguous().to(torch.float64), g, stats=False, grad_tilt=gt)
+            g_tilt = None if gt is None else gt.to(device=actx.tilt[2], dtype=actx.tilt[1])
+            return g.to(actx.dtype), None, None, None, g_tilt
 
     return WGTrace
 

@@ -411,6 +411,25 @@ def test_autograd_function(ctx, ora):
     dh.destroy()
 
 
+def test_autograd_function_with_tilts(ctx, ora):
+    """WGTrace with a tilt tensor: the tilt gradient (per degree) and the
+    thickness gradient both match the oracle's adjoint."""
+    from paper_2601_04370_gb300 import wg
+    D, C = W.tiny()
+    dh = ctx.create_design(D)
+    th = torch.tensor(D.layer_d_nm, dtype=torch.float32, device="cuda", requires_grad=True)
+    tl = torch.tensor(D.mirror_tilt_deg, dtype=torch.float32, device="cuda", requires_grad=True)
+    tally = wg.WGTrace.apply(th, ctx, dh, C, tl)
+    G = torch.zeros_like(tally)
+    ctx.loss(dh, C, tally.detach(), G)
+    (tally * G).sum().backward()
+    ref_d, ref_t = ora.trace_grad(D, C, G.cpu().numpy())
+    _grad_compare(th.grad.double().cpu().numpy(), ref_d)
+    gt = tl.grad.double().cpu().numpy()
+    assert np.linalg.norm(gt - ref_t) <= 1e-3 * np.linalg.norm(ref_t), (gt, ref_t)
+    dh.destroy()
+
+
 def test_set_params_updates_thickness(ctx, ora):
     D, C = W.tiny()
     dh = ctx.create_design(D)
