@@ -1100,7 +1100,8 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   const size_t rec_bytes = (size_t)cap * hit_rec_bytes();
   const bool tilt = grad_tilt != nullptr;
   const size_t acc_bytes = (sizeof(double) * std::max(1, d->n_dev) + 15) & ~(size_t)15;
-  const size_t aux_bytes = tilt ? (size_t)cap * sizeof(TiltAux) + (size_t)batch * sizeof(RayHead) : 0;
+  const size_t aux_bytes =
+      tilt ? (size_t)cap * (sizeof(TiltAux) + sizeof(unsigned int)) + (size_t)batch * sizeof(RayHead) : 0;
   const size_t need = 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + acc_bytes + aux_bytes;
   if (need > c->bwd.n) {
     CU(cudaEventSynchronize(c->ws_free));
@@ -1116,9 +1117,11 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   sc.cap = cap;
   TiltAux* tilt_aux = nullptr;
   RayHead* heads = nullptr;
+  unsigned int* perm = nullptr;  // sorted record -> its slot in tilt_aux
   if (tilt) {
     tilt_aux = (TiltAux*)(bw + 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + acc_bytes);
     heads = (RayHead*)((uint8_t*)tilt_aux + (size_t)cap * sizeof(TiltAux));
+    perm = (unsigned int*)((uint8_t*)heads + (size_t)batch * sizeof(RayHead));
   }
   const bool dev_G = is_device_ptr(dL_dtally);
   const bool dev_g = is_device_ptr(grad_thickness);
@@ -1134,7 +1137,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   CU(cudaMemsetAsync(gout, 0, sizeof(double) * std::max(1, d->n_orig), s));
   CU(cudaMemsetAsync(sc.grad_acc, 0, sizeof(double) * std::max(1, d->n_dev), s));
   const int bps_r = std::max(1, bwd_replay_blocks_per_sm(p.F, d->period, tilt, smem_r));
-  // mirror tilts: the replay records each hit's coefficients and dL/d(cos t0);
+  // mirror tilts: the replay records each hit's coefficients, the adjoint kernel its dL/d(cos t0);
   // after each batch a tangent pass per 8 mirrors re-traces its rays
   double* gt = grad_tilt;
   const bool dev_t = tilt && is_device_ptr(grad_tilt);
@@ -1198,8 +1201,10 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
       batch = std::max<long long>(1, (b1 - b0) / 2);
       continue;
     }
-    CU(launch_bwd_sort(sc.rec, (long long)n_rec, sc.keys, sc.keys + 128, sc.keys + 256, sc.sorted, s));
+    CU(launch_bwd_sort(sc.rec, (long long)n_rec, sc.keys, sc.keys + 128, sc.keys + 256, sc.sorted, perm, s));
     AdjArgs aa;
+    aa.tilt_aux = tilt_aux;
+    aa.perm = perm;
     aa.blob = d->blob;
     aa.blob_bytes = d->blob_bytes;
     aa.recs = sc.sorted;

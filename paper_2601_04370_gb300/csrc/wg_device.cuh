@@ -362,6 +362,87 @@ __device__ __forceinline__ Coef tmm_forward(const StackView& st, bool front, con
 }
 
 // ---------------------------------------------------------------------------
+// Derivatives with respect to cos(theta_0) of the layer constants and of the
+// layer chain (dual numbers), for the mirror-tilt gradient.
+// ---------------------------------------------------------------------------
+// d/d(cos t0) of a material's constants (value k, the same branch)
+struct MatKD {
+  float dkt, dq12s, dq21s, dq12p, dq21p;
+};
+__device__ __forceinline__ MatKD mat_const_d(const MatK& k, float cos0, float n, float inv_n, float r2,
+                                             float inv_lam) {
+  const float drad = 2.0f * r2 * cos0;  // rad = 1 - r2 (1 - cos0^2)
+  MatKD D;
+  if (!k.evan) {
+    const float eta = k.q21s, ct = fmaxf(eta * inv_n, 1e-20f);
+    const float dct = 0.5f * drad / ct, deta = n * dct;
+    D.dkt = deta * inv_lam;  // turns per nm
+    D.dq12s = -deta * k.q12s * k.q12s;
+    D.dq21s = deta;
+    D.dq12p = dct * inv_n;
+    D.dq21p = -dct * k.q21p / ct;
+  } else {
+    const float na = -k.q21s, a = fmaxf(na * inv_n, 1e-20f);
+    const float da = -0.5f * drad / a, dna = n * da;
+    D.dkt = TWO_PI * dna * inv_lam;  // rad per nm, as kt
+    D.dq12s = -dna * k.q12s * k.q12s;
+    D.dq21s = -dna;
+    D.dq12p = -da * inv_n;
+    D.dq21p = -da * k.q21p / a;
+  }
+  return D;
+}
+
+struct MatTableD {
+  MatKD k[MAX_MAT];
+  __device__ __forceinline__ void init(const BlobHeader& h, float cos0, float lam, const MatTable& mt) {
+    const float inv_lam = 1.0f / lam;
+#pragma unroll
+    for (int i = 0; i < MAX_MAT; ++i)
+      if (i < h.n_mat) k[i] = mat_const_d(mt.k[i], cos0, h.mat_n[i], h.mat_inv_n[i], h.mat_r2[i], inv_lam);
+  }
+  __device__ __forceinline__ MatKD get(int m) const {
+    MatKD r = k[0];
+    if (m == 1) r = k[1];
+    if (m == 2) r = k[2];
+    if (m == 3) r = k[3];
+    return r;
+  }
+};
+
+// v' = M v and its derivative dv' = dM v + M dv (M = [[c, i m12], [i m21, c]])
+__device__ __forceinline__ void cv_step_d(CV& v, CV& dv, float c, float m12, float m21, float dc, float dm12,
+                                          float dm21) {
+  const CV o = v;
+  cv_step(v, c, m12, m21);
+  const float xr = fmaf(dc, o.xr, fmaf(c, dv.xr, -fmaf(dm12, o.yi, m12 * dv.yi)));
+  const float xi = fmaf(dc, o.xi, fmaf(c, dv.xi, fmaf(dm12, o.yr, m12 * dv.yr)));
+  const float yr = fmaf(dc, o.yr, fmaf(c, dv.yr, -fmaf(dm21, o.xi, m21 * dv.xi)));
+  const float yi = fmaf(dc, o.yi, fmaf(c, dv.yi, fmaf(dm21, o.xr, m21 * dv.xr)));
+  dv.xr = xr;
+  dv.xi = xi;
+  dv.yr = yr;
+  dv.yi = yi;
+}
+
+// r, t and their derivatives from the (scaled) vector and its derivative
+__device__ __forceinline__ void coef_from_v_d(const CV& v, const CV& dv, float eta0, float deta0, int e, float2& r,
+                                              float2& t, float2& dr, float2& dt) {
+  const float2 B = make_float2(v.xr, v.xi), C = make_float2(v.yr, v.yi);
+  const float2 dB = make_float2(dv.xr, dv.xi), dC = make_float2(dv.yr, dv.yi);
+  const float2 den = make_float2(fmaf(eta0, B.x, C.x), fmaf(eta0, B.y, C.y));
+  const float2 num = make_float2(fmaf(eta0, B.x, -C.x), fmaf(eta0, B.y, -C.y));
+  const float2 dden = make_float2(fmaf(deta0, B.x, fmaf(eta0, dB.x, dC.x)), fmaf(deta0, B.y, fmaf(eta0, dB.y, dC.y)));
+  const float2 dnum = make_float2(fmaf(deta0, B.x, fmaf(eta0, dB.x, -dC.x)), fmaf(deta0, B.y, fmaf(eta0, dB.y, -dC.y)));
+  const float2 q = crcp_s(den);
+  const float sc = pow2i(-e);
+  r = cmul(num, q);
+  t = cscale(q, 2.0f * eta0 * sc);
+  dr = cmul(csub(dnum, cmul(r, dden)), q);
+  dt = cmul(csub(make_float2(2.0f * deta0 * sc, 0.0f), cmul(t, dden)), q);
+}
+
+// ---------------------------------------------------------------------------
 // Adjoint of f = 2 Re(A_s c_s + A_p c_p) (c = r or t) with respect to every
 // layer thickness. With v_j = M_j ... M_{L-1} u and the row
 // a_j = rho M_0 ... M_{j-1}, rho = A (dc/dB, dc/dC):
@@ -455,12 +536,25 @@ __host__ __device__ constexpr int seg_floats_per_warp() {
   return Seg<P>::CKP * kSegWords * 32;
 }
 
+// v and its derivative kept below 2^32 by the same exact power of two
+__device__ __forceinline__ void cv_rescale32_d(CV& v, CV& dv, int& e) {
+  if (fmaxf(cv_maxabs(v), cv_maxabs(dv)) > TWO_P32) {
+    v = CV{v.xr * TWO_M32, v.xi * TWO_M32, v.yr * TWO_M32, v.yi * TWO_M32};
+    dv = CV{dv.xr * TWO_M32, dv.xi * TWO_M32, dv.yr * TWO_M32, dv.yi * TWO_M32};
+    e += 32;
+  }
+}
+
 // seg: this lane's column of its warp's segment buffer (element (u, w) at
 // seg[(u * kSegWords + w) * 32]; the 32 lanes' columns interleave).
-template <int P, class Sink>
+// DUAL: sweep 1 also carries d/d(cos t0) of the substrate-side vectors (the
+// constants' derivatives from mtd) and *g_cos receives df/d(cos t0) of the
+// record through its coating, 2 Re(A_s dc_s + A_p dc_p), without 2^eA.
+template <int P, class Sink, bool DUAL = false>
 __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, const MatTable& mt, float n0,
                                             float cos0, float2 A_s, float2 A_p, int which, Sink& sink,
-                                            float* seg, int eA = 0) {
+                                            float* seg, int eA = 0, const MatTableD* mtd = nullptr,
+                                            float* g_cos = nullptr) {
   // (A_s, A_p) * 2^eA are the weights; eA carries the range of dL/dtally
   constexpr int CKP = Seg<P>::CKP;
   MatK kb[Seg<P>::NSLOT];
@@ -472,31 +566,94 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
   CV vs{1.0f, 0.0f, eta_s, 0.0f}, vp{1.0f, 0.0f, eta_p, 0.0f};
   int es = 0, ep = 0;
   ck[nseg] = Ckpt{vs, vp, 0, 0};
-  for (int sg = nseg - 1; sg >= 0; --sg) {
-    const int j0 = sg * CKP;
+  if constexpr (DUAL) {
+    const float deta_s = n0, deta_p = -eta_p / cos0;
+    CV dvs{0.0f, 0.0f, deta_s, 0.0f}, dvp{0.0f, 0.0f, deta_p, 0.0f};
+    MatKD kbd[Seg<P>::NSLOT];
+    if constexpr (P > 0) {
 #pragma unroll
-    for (int u = CKP - 1; u >= 0; --u) {
-      const int j = j0 + u;
-      if (j < L) {
-        const int i = st.idx(front, j);
-        MatK k;
-        if constexpr (P > 0) {
-          k = kb[u % P];
-        } else {
-          k = mt.get(st.m[i]);
-        }
-        float c, s;
-        layer_cs(k, st.d[i], c, s);
-        cv_step(vs, c, s * k.q12s, s * k.q21s);
-        cv_step(vp, c, s * k.q12p, s * k.q21p);
+      for (int v = 0; v < P; ++v) {
+        int r = front ? v : (((st.L - 1 - v) % P) + P) % P;
+        r = r < st.L ? r : 0;
+        kbd[v] = mtd->get(st.m[st.off + r]);
       }
     }
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+      const int j0 = sg * CKP;
 #pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      cv_rescale32(vs, es);
-      cv_rescale32(vp, ep);
+      for (int u = CKP - 1; u >= 0; --u) {
+        const int j = j0 + u;
+        if (j < L) {
+          const int i = st.idx(front, j);
+          MatK k;
+          MatKD kd;
+          if constexpr (P > 0) {
+            k = kb[u % P];
+            kd = kbd[u % P];
+          } else {
+            const int m = st.m[i];
+            k = mt.get(m);
+            kd = mtd->get(m);
+          }
+          const float dthk = st.d[i];
+          float c, s, dc, ds;
+          layer_cs(k, dthk, c, s);
+          if (!k.evan) {
+            const float dth = TWO_PI * dthk * kd.dkt;  // d(phase)
+            dc = -s * dth;
+            ds = c * dth;
+          } else {
+            const float dx = dthk * kd.dkt;
+            dc = s * dx;
+            ds = c * dx;
+          }
+          cv_step_d(vs, dvs, c, s * k.q12s, s * k.q21s, dc, fmaf(ds, k.q12s, s * kd.dq12s),
+                    fmaf(ds, k.q21s, s * kd.dq21s));
+          cv_step_d(vp, dvp, c, s * k.q12p, s * k.q21p, dc, fmaf(ds, k.q12p, s * kd.dq12p),
+                    fmaf(ds, k.q21p, s * kd.dq21p));
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        cv_rescale32_d(vs, dvs, es);
+        cv_rescale32_d(vp, dvp, ep);
+      }
+      ck[sg] = Ckpt{vs, vp, es, ep};
     }
-    ck[sg] = Ckpt{vs, vp, es, ep};
+    float2 rs, ts, drs, dts, rpm, tp, drpm, dtp;
+    coef_from_v_d(vs, dvs, eta_s, deta_s, es, rs, ts, drs, dts);
+    coef_from_v_d(vp, dvp, eta_p, deta_p, ep, rpm, tp, drpm, dtp);
+    // paper convention r_p = -r_p(Abeles)
+    const float2 dcs = which == 0 ? drs : dts;
+    const float2 dcp = which == 0 ? make_float2(-drpm.x, -drpm.y) : dtp;
+    *g_cos = 2.0f * (fmaf(A_s.x, dcs.x, -A_s.y * dcs.y) + fmaf(A_p.x, dcp.x, -A_p.y * dcp.y));
+  } else {
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+      const int j0 = sg * CKP;
+#pragma unroll
+      for (int u = CKP - 1; u >= 0; --u) {
+        const int j = j0 + u;
+        if (j < L) {
+          const int i = st.idx(front, j);
+          MatK k;
+          if constexpr (P > 0) {
+            k = kb[u % P];
+          } else {
+            k = mt.get(st.m[i]);
+          }
+          float c, s;
+          layer_cs(k, st.d[i], c, s);
+          cv_step(vs, c, s * k.q12s, s * k.q21s);
+          cv_step(vp, c, s * k.q12p, s * k.q21p);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        cv_rescale32(vs, es);
+        cv_rescale32(vp, ep);
+      }
+      ck[sg] = Ckpt{vs, vp, es, ep};
+    }
   }
   // paper convention r_p = -r_p(Abeles): flip A_p for reflection
   const float2 Ap = which == 0 ? make_float2(-A_p.x, -A_p.y) : A_p;
@@ -669,161 +826,6 @@ __device__ __forceinline__ uint32_t fnv(uint32_t h, uint32_t b) { return (h ^ b)
 // the local s/p bases, the reflected directions and the angle-dependent TIR
 // and exit Fresnel factors; positions do not reach the intensity.
 // ---------------------------------------------------------------------------
-// d/d(cos t0) of a material's constants (value k, the same branch)
-struct MatKD {
-  float dkt, dq12s, dq21s, dq12p, dq21p;
-};
-__device__ __forceinline__ MatKD mat_const_d(const MatK& k, float cos0, float n, float inv_n, float r2,
-                                             float inv_lam) {
-  const float drad = 2.0f * r2 * cos0;  // rad = 1 - r2 (1 - cos0^2)
-  MatKD D;
-  if (!k.evan) {
-    const float eta = k.q21s, ct = fmaxf(eta * inv_n, 1e-20f);
-    const float dct = 0.5f * drad / ct, deta = n * dct;
-    D.dkt = deta * inv_lam;  // turns per nm
-    D.dq12s = -deta * k.q12s * k.q12s;
-    D.dq21s = deta;
-    D.dq12p = dct * inv_n;
-    D.dq21p = -dct * k.q21p / ct;
-  } else {
-    const float na = -k.q21s, a = fmaxf(na * inv_n, 1e-20f);
-    const float da = -0.5f * drad / a, dna = n * da;
-    D.dkt = TWO_PI * dna * inv_lam;  // rad per nm, as kt
-    D.dq12s = -dna * k.q12s * k.q12s;
-    D.dq21s = -dna;
-    D.dq12p = -da * inv_n;
-    D.dq21p = -da * k.q21p / a;
-  }
-  return D;
-}
-
-struct MatTableD {
-  MatKD k[MAX_MAT];
-  __device__ __forceinline__ void init(const BlobHeader& h, float cos0, float lam, const MatTable& mt) {
-    const float inv_lam = 1.0f / lam;
-#pragma unroll
-    for (int i = 0; i < MAX_MAT; ++i)
-      if (i < h.n_mat) k[i] = mat_const_d(mt.k[i], cos0, h.mat_n[i], h.mat_inv_n[i], h.mat_r2[i], inv_lam);
-  }
-  __device__ __forceinline__ MatKD get(int m) const {
-    MatKD r = k[0];
-    if (m == 1) r = k[1];
-    if (m == 2) r = k[2];
-    if (m == 3) r = k[3];
-    return r;
-  }
-};
-
-// v' = M v and its derivative dv' = dM v + M dv (M = [[c, i m12], [i m21, c]])
-__device__ __forceinline__ void cv_step_d(CV& v, CV& dv, float c, float m12, float m21, float dc, float dm12,
-                                          float dm21) {
-  const CV o = v;
-  cv_step(v, c, m12, m21);
-  const float xr = fmaf(dc, o.xr, fmaf(c, dv.xr, -fmaf(dm12, o.yi, m12 * dv.yi)));
-  const float xi = fmaf(dc, o.xi, fmaf(c, dv.xi, fmaf(dm12, o.yr, m12 * dv.yr)));
-  const float yr = fmaf(dc, o.yr, fmaf(c, dv.yr, -fmaf(dm21, o.xi, m21 * dv.xi)));
-  const float yi = fmaf(dc, o.yi, fmaf(c, dv.yi, fmaf(dm21, o.xr, m21 * dv.xr)));
-  dv.xr = xr;
-  dv.xi = xi;
-  dv.yr = yr;
-  dv.yi = yi;
-}
-
-// r, t and their derivatives from the (scaled) vector and its derivative
-__device__ __forceinline__ void coef_from_v_d(const CV& v, const CV& dv, float eta0, float deta0, int e, float2& r,
-                                              float2& t, float2& dr, float2& dt) {
-  const float2 B = make_float2(v.xr, v.xi), C = make_float2(v.yr, v.yi);
-  const float2 dB = make_float2(dv.xr, dv.xi), dC = make_float2(dv.yr, dv.yi);
-  const float2 den = make_float2(fmaf(eta0, B.x, C.x), fmaf(eta0, B.y, C.y));
-  const float2 num = make_float2(fmaf(eta0, B.x, -C.x), fmaf(eta0, B.y, -C.y));
-  const float2 dden = make_float2(fmaf(deta0, B.x, fmaf(eta0, dB.x, dC.x)), fmaf(deta0, B.y, fmaf(eta0, dB.y, dC.y)));
-  const float2 dnum = make_float2(fmaf(deta0, B.x, fmaf(eta0, dB.x, -dC.x)), fmaf(deta0, B.y, fmaf(eta0, dB.y, -dC.y)));
-  const float2 q = crcp_s(den);
-  const float sc = pow2i(-e);
-  r = cmul(num, q);
-  t = cscale(q, 2.0f * eta0 * sc);
-  dr = cmul(csub(dnum, cmul(r, dden)), q);
-  dt = cmul(csub(make_float2(2.0f * deta0 * sc, 0.0f), cmul(t, dden)), q);
-}
-
-// v and its derivative scaled by the same exact power of two
-__device__ __forceinline__ void cv_rescale_d(CV& v, CV& dv, int& e) {
-  if (fmaxf(cv_maxabs(v), cv_maxabs(dv)) > TWO_P64) {
-    v = CV{v.xr * TWO_M64, v.xi * TWO_M64, v.yr * TWO_M64, v.yi * TWO_M64};
-    dv = CV{dv.xr * TWO_M64, dv.xi * TWO_M64, dv.yr * TWO_M64, dv.yi * TWO_M64};
-    e += 64;
-  }
-}
-
-// Coefficients in the paper's convention and their derivatives d/d(cos t0):
-// the layer loop of tmm_forward (segments of the material period, material
-// constants and their derivatives in registers) carrying the dual vector.
-template <int P>
-__device__ __forceinline__ void tmm_forward_dual(const StackView& st, bool front, const MatTable& mt,
-                                                 const MatTableD& mtd, float n0, float cos0, Coef& cf, Coef& dcf) {
-  constexpr int CKP = Seg<P>::CKP;
-  MatK kb[Seg<P>::NSLOT];
-  MatKD kbd[Seg<P>::NSLOT];
-  if constexpr (P > 0) {
-#pragma unroll
-    for (int v = 0; v < P; ++v) {
-      int r = front ? v : (((st.L - 1 - v) % P) + P) % P;
-      r = r < st.L ? r : 0;
-      const int m = st.m[st.off + r];
-      kb[v] = mt.get(m);
-      kbd[v] = mtd.get(m);
-    }
-  }
-  const float eta_s = n0 * cos0, eta_p = n0 / cos0;
-  const float deta_s = n0, deta_p = -eta_p / cos0;
-  CV vs{1.0f, 0.0f, eta_s, 0.0f}, vp{1.0f, 0.0f, eta_p, 0.0f};
-  CV dvs{0.0f, 0.0f, deta_s, 0.0f}, dvp{0.0f, 0.0f, deta_p, 0.0f};
-  int es = 0, ep = 0;
-  const int L = st.L;
-  for (int j0 = L > 0 ? ((L - 1) / CKP) * CKP : -1; j0 >= 0; j0 -= CKP) {
-#pragma unroll
-    for (int u = CKP - 1; u >= 0; --u) {
-      const int j = j0 + u;
-      if (j < L) {
-        const int i = st.idx(front, j);
-        MatK k;
-        MatKD kd;
-        if constexpr (P > 0) {
-          k = kb[u % P];
-          kd = kbd[u % P];
-        } else {
-          const int m = st.m[i];
-          k = mt.get(m);
-          kd = mtd.get(m);
-        }
-        const float dthk = st.d[i];
-        float c, s, dc, ds;
-        layer_cs(k, dthk, c, s);
-        if (!k.evan) {
-          const float dth = TWO_PI * dthk * kd.dkt;  // d(phase)
-          dc = -s * dth;
-          ds = c * dth;
-        } else {
-          const float dx = dthk * kd.dkt;
-          dc = s * dx;
-          ds = c * dx;
-        }
-        cv_step_d(vs, dvs, c, s * k.q12s, s * k.q21s, dc, fmaf(ds, k.q12s, s * kd.dq12s),
-                  fmaf(ds, k.q21s, s * kd.dq21s));
-        cv_step_d(vp, dvp, c, s * k.q12p, s * k.q21p, dc, fmaf(ds, k.q12p, s * kd.dq12p),
-                  fmaf(ds, k.q21p, s * kd.dq21p));
-      }
-    }
-    cv_rescale_d(vs, dvs, es);
-    cv_rescale_d(vp, dvp, ep);
-  }
-  float2 rpm, drpm;
-  coef_from_v_d(vs, dvs, eta_s, deta_s, es, cf.rs, cf.ts, dcf.rs, dcf.ts);
-  coef_from_v_d(vp, dvp, eta_p, deta_p, ep, rpm, cf.tp, drpm, dcf.tp);
-  cf.rp = make_float2(-rpm.x, -rpm.y);
-  dcf.rp = make_float2(-drpm.x, -drpm.y);
-}
-
 // d/d(cos i) of the TIR coefficients at a slab face (|r| = 1: r = e^{2i phi},
 // dr = 2i r dphi) for cos i = ci
 __device__ __forceinline__ void tir_coef_d(float n, float ci, float2 rs, float2 rp, float2& drs, float2& drp) {

@@ -98,6 +98,10 @@ struct AdjArgs {
   unsigned long long* work;
   unsigned long long* counters;
   unsigned int* error;
+  // tilt gradient (null: none): dL/d(cos t0) of each record, written to
+  // tilt_aux[perm[i]].g_cos (the record's slot before the sort)
+  TiltAux* tilt_aux;
+  const unsigned int* perm;
 };
 
 constexpr int kBlock = 256;
@@ -136,9 +140,10 @@ cudaError_t launch_trace_fwd_fused(const TraceArgs* jobs_dev, const int* cta_job
                                    size_t smem, cudaStream_t s);
 // tilt: also record TiltAux per hit and a RayHead per ray (a.tilt_aux, a.ray_heads)
 cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, bool tilt, int grid, size_t smem, cudaStream_t s);
+// perm (may be null): perm[sorted position] = index of the record in `in`
 cudaError_t launch_bwd_sort(const HitRec* in, long long n, unsigned int* key_count, unsigned int* key_off,
-                            unsigned int* key_cursor, HitRec* out, cudaStream_t s);
-cudaError_t launch_bwd_adjoint(const AdjArgs& a, int P, int grid, size_t smem, cudaStream_t s);
+                            unsigned int* key_cursor, HitRec* out, unsigned int* perm, cudaStream_t s);
+cudaError_t launch_bwd_adjoint(const AdjArgs& a, int P, int grid, size_t smem, cudaStream_t s);  // a.tilt_aux picks the variant
 cudaError_t launch_scatter_grad(const double* acc, int n_layers, const int* dev_to_orig, double* out,
                                 cudaStream_t s);
 cudaError_t launch_coating_eval(const uint8_t* blob, int P, int mirror, int side, long long n, const float* cos0,

@@ -14,7 +14,6 @@
 
 #include <algorithm>
 #include <atomic>
-#include <type_traits>
 #include <cstring>
 
 #include "wg_device.cuh"
@@ -336,15 +335,12 @@ __device__ __forceinline__ Outcome face_event(Ray<F>& R, int sid, const BlobHead
 // Fills the tape entry fields when `te` is non-null.
 struct MirrorStep {
   float2 cs, cp;   // applied coefficients (incl. 1/sqrt scaling)
-  float2 dcs, dcp;  // their derivatives d/d(cos t0) (DUAL only)
   float cphi, sphi, cpsi, spsi;
   float cos0;
   int front, refl;
 };
 
-// DUAL: the coefficients come with their derivatives with respect to
-// cos(theta_0) from the dual layer chain (the replay for the tilt gradient)
-template <int F, int P, bool DUAL = false>
+template <int F, int P>
 __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob& B, float lam, const TraceArgs& A,
                                                    int& layer_steps, float2* Es_out, float2* Ep_out) {
   const BlobHeader& H = *B.h;
@@ -357,15 +353,7 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
   MatTable mt;
   mt.init(H, st.cos0, lam);
   const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
-  Coef cf, dcf;
-  if constexpr (DUAL) {
-    MatTableD mtd;
-    mtd.init(H, st.cos0, lam, mt);
-    tmm_forward_dual<P>(sv, st.front, mt, mtd, H.n_slab, st.cos0, cf, dcf);
-    layer_steps += M.n_layers;
-  } else {
-    cf = tmm_forward<P>(sv, st.front, mt, H.n_slab, st.cos0, layer_steps);
-  }
+  const Coef cf = tmm_forward<P>(sv, st.front, mt, H.n_slab, st.cos0, layer_steps);
   V3 sf, pf;
   face_basis(R.d, sf, pf);
   V3 sm = cross3(R.d, N);
@@ -390,18 +378,10 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
   if (st.refl) {
     st.cs = cscale(cf.rs, M.isw);
     st.cp = cscale(cf.rp, M.isw);
-    if constexpr (DUAL) {
-      st.dcs = cscale(dcf.rs, M.isw);
-      st.dcp = cscale(dcf.rp, M.isw);
-    }
     d2 = v3(fmaf(-2.0f * cd, N.x, R.d.x), R.d.y, fmaf(-2.0f * cd, N.z, R.d.z));
   } else {
     st.cs = cscale(cf.ts, M.is1w);
     st.cp = cscale(cf.tp, M.is1w);
-    if constexpr (DUAL) {
-      st.dcs = cscale(dcf.ts, M.is1w);
-      st.dcp = cscale(dcf.tp, M.is1w);
-    }
   }
   const V3 pm2 = cross3(sm, d2);
   V3 sf2, pf2;
@@ -1010,12 +990,8 @@ __global__ void __launch_bounds__(kBlock, 2)
 //   gradient entry in all lanes, which is reduced with shuffles and added
 //   once; partial FP32 sums in shared memory go to FP64 after each chunk.
 // ---------------------------------------------------------------------------
-struct TapeNoDual {};
-struct TapeDual {
-  float2 dcs, dcp;  // d/d(cos t0) of the applied coefficients
-};
-template <int F, bool T>
-struct TapeE : std::conditional_t<T, TapeDual, TapeNoDual> {
+template <int F>
+struct TapeE {
   float2 cs, cp;
   float2 Es[F], Ep[F];
   float cphi, sphi, cpsi, spsi;
@@ -1024,9 +1000,9 @@ struct TapeE : std::conditional_t<T, TapeDual, TapeNoDual> {
   int kfw;
 };
 
-// T: the replay also serves the tilt gradient. Coefficients come from the
-// dual layer chain, and each emitted record gets its TiltAux (applied
-// coefficients, dL/d(cos t0) through the coating) and its ray a RayHead.
+// T: the replay also serves the tilt gradient: each emitted record gets its
+// TiltAux (the applied coefficients; the adjoint kernel adds dL/d(cos t0))
+// and its ray a RayHead.
 template <int F, int P, bool T>
 __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -1045,7 +1021,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
   const long long cap = A.hit_cap;
 
   int c_rays = 0, c_hits = 0, c_overflow = 0, c_tallied = 0, c_steps = 0;
-  TapeE<F, T> tape[TAPE_HITS];
+  TapeE<F> tape[TAPE_HITS];
 
   // warp-private work unit (a short ray range of one cell, warp-uniform)
   long long u_cell = 0, u_next = 0, u_end = 0;
@@ -1207,7 +1183,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                   gb[f] = cmulc(seg_p, cscale(R.b[f], sc * o.Tp));
                 }
                 for (int h = emit - 1; h >= 0; --h) {
-                  const TapeE<F, T>& E = tape[h];
+                  const TapeE<F>& E = tape[h];
                   float2 gs[F], gp[F];
                   float2 As = make_float2(0.f, 0.f), Ap = make_float2(0.f, 0.f);
                   const int k = E.kfw & 0xff;
@@ -1229,12 +1205,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                   rec.Ap = cscale(Ap, scl);
                   hb[first + h] = rec;
                   if constexpr (T) {
-                    // dL/d(cos t0) of this hit through its coating (G's exponent restored)
-                    const float gc = 2.0f * (fmaf(As.x, E.dcs.x, -As.y * E.dcs.y) + fmaf(Ap.x, E.dcp.x, -Ap.y * E.dcp.y));
                     TiltAux ta;
                     ta.cs = E.cs;
                     ta.cp = E.cp;
-                    ta.g_cos = ldexp((double)gc, eG);
+                    ta.g_cos = 0.0;  // set by the adjoint kernel
                     A.tilt_aux[first + h] = ta;
                   }
                   atomicAdd(&s_keys[((E.kfw & 0xff) << 1) | ((E.kfw >> 8) & 1)], 1u);  // stack (mirror, side)
@@ -1255,15 +1229,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
         if (at_mir) {
           const int h = R.hits;
           float2 Es[F], Ep[F];
-          const MirrorStep ms = mirror_event<F, P, T>(R, hit_k, B, lam_l, A, c_steps, Es, Ep);
+          const MirrorStep ms = mirror_event<F, P>(R, hit_k, B, lam_l, A, c_steps, Es, Ep);
           if (h < TAPE_HITS) {
-            TapeE<F, T>& E = tape[h];
+            TapeE<F>& E = tape[h];
             E.cs = ms.cs;
             E.cp = ms.cp;
-            if constexpr (T) {
-              E.dcs = ms.dcs;
-              E.dcp = ms.dcp;
-            }
 #pragma unroll
             for (int f = 0; f < F; ++f) {
               E.Es[f] = Es[f];
@@ -1309,10 +1279,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
 
 // ---------------------------------------------------------------------------
 // K3b: mirror-tilt gradient, split in two parts along the sampled path.
-// (1) Through the coatings: the replay differentiates each hit's coefficients
-//     with respect to cos(theta_0) (dual layer chain) and its reverse sweep
-//     forms g = dL/d(cos theta_0) of the hit (TiltAux); here g times the
-//     tangent of cos(theta_0) of that hit.
+// (1) Through the coatings: the thin-film adjoint kernel, whose first sweep
+//     also runs the dual layer chain, forms g = dL/d(cos theta_0) of every
+//     hit record from its weights A (TiltAux); here g times the tangent of
+//     cos(theta_0) of that hit.
 // (2) Everything else with the coefficients held at their values: the
 //     reflected directions, the mirror and face s/p bases, the TIR phases and
 //     the exit transmittances. k_tilt_grad re-traces each ray that produced
@@ -1577,7 +1547,9 @@ __device__ __forceinline__ int rec_key(int kfw) { return ((kfw & 0xff) << 1) | (
 // thread, ranks them per stack in shared memory (warp-aggregated), reserves
 // one range per stack with a single global atomic, then writes.
 constexpr int kScatterItems = 8;
-__global__ void k_bwd_scatter(const HitRec* in, long long n, unsigned int* key_cursor, HitRec* out) {
+// perm (optional): perm[sorted position] = record index before the sort
+__global__ void k_bwd_scatter(const HitRec* in, long long n, unsigned int* key_cursor, HitRec* out,
+                              unsigned int* perm) {
   __shared__ unsigned int s_cnt[2 * MAX_MIR], s_base[2 * MAX_MIR];
   const int tid = threadIdx.x, lane = tid & 31;
   for (int k = tid; k < 2 * MAX_MIR; k += blockDim.x) s_cnt[k] = 0u;
@@ -1607,7 +1579,11 @@ __global__ void k_bwd_scatter(const HitRec* in, long long n, unsigned int* key_c
   __syncthreads();
 #pragma unroll
   for (int t = 0; t < kScatterItems; ++t)
-    if (key[t] >= 0) out[s_base[key[t]] + rank[t]] = r[t];
+    if (key[t] >= 0) {
+      const unsigned int pos = s_base[key[t]] + rank[t];
+      out[pos] = r[t];
+      if (perm) perm[pos] = (unsigned int)(tile + (long long)t * blockDim.x + tid);
+    }
 }
 
 // Per-layer gradient terms of one record per lane. When all 32 lanes hold
@@ -1647,7 +1623,9 @@ size_t adj_smem_bytes(int blob_bytes, int n_layers, int P) {
   return adj_smem_bytes_p<0>(blob_bytes, n_layers);
 }
 
-template <int P>
+// T: also dL/d(cos t0) of every record through its coating (the tilt
+// gradient's coating term), written to A.tilt_aux[A.perm[i]].g_cos
+template <int P, bool T>
 __global__ void __launch_bounds__(kBlock, 2) k_bwd_adjoint(const AdjArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_mbar;
@@ -1688,7 +1666,16 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_adjoint(const AdjArgs A) {
         mt.init(H, rec.cos0, rec.lam);
         const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
         GradSink sink{s_grad, &bad, lane, uniform};
-        tmm_adjoint<P>(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, seg, rec.eA);
+        if constexpr (T) {
+          MatTableD mtd;
+          mtd.init(H, rec.cos0, rec.lam, mt);
+          float g = 0.f;
+          tmm_adjoint<P, GradSink, true>(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, seg, rec.eA,
+                                         &mtd, &g);
+          A.tilt_aux[A.perm[i]].g_cos = ldexp((double)g, rec.eA);
+        } else {
+          tmm_adjoint<P>(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, seg, rec.eA);
+        }
         c_steps += M.n_layers;
       }
     }
@@ -1824,7 +1811,11 @@ static void (*pick_replay(int F, int P))(const TraceArgs) {
 int bwd_replay_blocks_per_sm(int F, int P, bool tilt, size_t smem) {
   return occupancy(tilt ? pick_replay<true>(F, P) : pick_replay<false>(F, P), smem);
 }
-int bwd_adjoint_blocks_per_sm(int P, size_t smem) { return occupancy(WG_PICK_P(k_bwd_adjoint, P), smem); }
+template <bool T>
+static void (*pick_adjoint(int P))(const AdjArgs) {
+  return P == 3 ? k_bwd_adjoint<3, T> : P == 2 ? k_bwd_adjoint<2, T> : k_bwd_adjoint<0, T>;
+}
+int bwd_adjoint_blocks_per_sm(int P, size_t smem) { return occupancy(pick_adjoint<false>(P), smem); }
 int tilt_blocks_per_sm(int F, int P, size_t smem) {
   (void)P;
   auto k = F == 2 ? k_tilt_grad<2> : k_tilt_grad<1>;
@@ -1873,19 +1864,19 @@ cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, bool tilt, int g
 }
 
 cudaError_t launch_bwd_sort(const HitRec* in, long long n, unsigned int* key_count, unsigned int* key_off,
-                            unsigned int* key_cursor, HitRec* out, cudaStream_t s) {
+                            unsigned int* key_cursor, HitRec* out, unsigned int* perm, cudaStream_t s) {
   note_launches(1);
   k_bwd_scan<<<1, 2 * MAX_MIR, 0, s>>>(key_count, key_off, key_cursor);
   if (n > 0) {
     note_launches(1);
     const long long per_block = 256ll * kScatterItems;
-    k_bwd_scatter<<<(unsigned)((n + per_block - 1) / per_block), 256, 0, s>>>(in, n, key_cursor, out);
+    k_bwd_scatter<<<(unsigned)((n + per_block - 1) / per_block), 256, 0, s>>>(in, n, key_cursor, out, perm);
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_bwd_adjoint(const AdjArgs& a, int P, int grid, size_t smem, cudaStream_t s) {
-  auto k = WG_PICK_P(k_bwd_adjoint, P);
+  auto k = a.tilt_aux ? pick_adjoint<true>(P) : pick_adjoint<false>(P);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   note_launches(1);
   k<<<grid, kBlock, smem, s>>>(a);
