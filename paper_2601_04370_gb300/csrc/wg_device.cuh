@@ -212,8 +212,10 @@ __device__ __forceinline__ void layer_cs(const MatK& k, float d, float& c, float
     const float f = x - rintf(x);  // exact reduction in turns
     __sincosf(f * TWO_PI, &s, &c);
   } else {
+    // e^x and e^-x from two independent hardware exponentials (no
+    // dependent reciprocal; both with the same relative accuracy)
     const float e = __expf(x);
-    const float ei = __frcp_rn(e);
+    const float ei = __expf(-x);
     c = 0.5f * (e + ei);
     s = 0.5f * (e - ei);
   }
