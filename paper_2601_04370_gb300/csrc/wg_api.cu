@@ -571,6 +571,7 @@ static TraceArgs base_args(const wg_design* d, const wg_trace_cfg* cfg, const Pl
   a.ray_end = p.re;
   a.cell_lo = p.cell_lo;
   a.chunk_rays = p.chunk_rays;
+  a.n_slots = fwd_slots(p.chunk_rays);
   a.chunks_per_cell = p.chunks_per_cell;
   a.n_chunks = p.n_chunks;
   a.key0 = (uint32_t)cfg->seed;
@@ -674,7 +675,7 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
   p.chunk_rays = default_chunk(p);
   p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
   p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
-  const size_t smem = fwd_smem_bytes(d->blob_bytes, p.bins, p.F);
+  const size_t smem = fwd_smem_bytes(d->blob_bytes, p.bins, p.F, fwd_slots(p.chunk_rays));
   if (smem > 200 * 1024) return fail(WG_EINVAL, "wg_trace_forward: design + eyebox too large for shared memory");
   cudaStream_t s = (cudaStream_t)cfg->stream;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -819,7 +820,7 @@ wg_status fused_prepare(wg_ctx* c, FusedJob* jobs, int n, int blocks_per_sm, Fus
     p.chunk_rays = J.chunk_rays > 0 ? std::min<long long>(J.chunk_rays, p.n_cell) : default_chunk(p);
     p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
     p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
-    smem[j] = fwd_smem_bytes(J.design->blob_bytes, p.bins, p.F);
+    smem[j] = fwd_smem_bytes(J.design->blob_bytes, p.bins, p.F, fwd_slots(p.chunk_rays));
     if (smem[j] > 200 * 1024) return fail(WG_EINVAL, "fused forward: job %d design + eyebox too large", j);
   }
   // device arena: heads (contiguous) | per-job arrays | job table | CTA map;
@@ -1326,7 +1327,7 @@ extern "C" wg_status wg_trace_forward_noalloc(wg_ctx* c, const wg_design* d, con
   p.chunk_rays = default_chunk(p);
   p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
   p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
-  const size_t smem = fwd_smem_bytes(d->blob_bytes, p.bins, p.F);
+  const size_t smem = fwd_smem_bytes(d->blob_bytes, p.bins, p.F, fwd_slots(p.chunk_rays));
   if (smem > 200 * 1024) return fail(WG_EINVAL, "wg_trace_forward_noalloc: design + eyebox too large for shared memory");
   const WsLayout need = ws_layout(nullptr, cfg, p.n_f);
   if (need.bytes > (size_t)WG_NOALLOC_SCRATCH_BYTES)

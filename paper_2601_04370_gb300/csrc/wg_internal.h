@@ -74,6 +74,7 @@ struct TraceArgs {
   const ExitRec* replay_list;
   long long list_begin, list_end;
   int n_cta;                  // CTAs of the launch working on this job
+  int n_slots;                // forward: tally slots per CTA (1..kFwdSlots)
   // tilt gradient: FP64 per-degree sums for mirrors [tilt_k0, tilt_k0 + 8)
   double* grad_tilt;
   int tilt_k0;
@@ -105,9 +106,13 @@ struct AdjArgs {
 };
 
 constexpr int kBlock = 256;
-// the forward kernel keeps this many chunks (cells) in flight per CTA, each
-// with its own FP32 shared tally
+// the forward kernel keeps up to this many chunks (cells) in flight per CTA,
+// each with its own FP32 shared tally. Large chunks take two: a CTA then
+// draws its rays from fewer cells at a time (same wavelength and field, so
+// its warps diverge less); small chunks take three, so a CTA does not wait
+// for a slot while a chunk's last slow rays finish.
 constexpr int kFwdSlots = 3;
+inline int fwd_slots(long long chunk_rays) { return chunk_rays >= 1536 ? 2 : 3; }
 // rays a warp of the forward kernel owns at a time (its lanes plus its two
 // shared-memory queues); a queued ray takes 9 + 4 F words
 constexpr int kFwdQCap = 48;
@@ -118,8 +123,8 @@ constexpr int kExitChunk = 64;
 inline long long exit_list_cap(long long rays, int sm_count) {
   return rays + (long long)sm_count * 64 * kExitChunk;
 }
-inline size_t fwd_smem_bytes(int blob_bytes, long long bins, int F) {
-  return (size_t)blob_bytes + sizeof(float) * (size_t)kFwdSlots * (size_t)bins +
+inline size_t fwd_smem_bytes(int blob_bytes, long long bins, int F, int n_slots) {
+  return (size_t)blob_bytes + sizeof(float) * (size_t)n_slots * (size_t)bins +
          sizeof(uint32_t) * (size_t)(kBlock / 32) * 2 * (size_t)kFwdQCap * (size_t)(9 + 4 * F);
 }
 

@@ -450,7 +450,7 @@ __device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v) {
 // ---------------------------------------------------------------------------
 // K2: forward Monte Carlo trace. Persistent CTAs; lanes pull rays from a
 // CTA-wide sequence that runs over the chunks (one cell, a range of rays)
-// the CTA has bound to its kSlots tally slots. A warp advances its rays
+// the CTA has bound to its tally slots (A.n_slots <= kSlots). A warp advances its rays
 // through face events until every live ray sits on a mirror, then runs the
 // per-hit transfer-matrix chain together. Exits are aggregated per warp
 // (lanes with the same slot and bin) into the slot's FP32 shared tally; the
@@ -471,6 +471,7 @@ struct SlotState {
 
 struct FwdRing {
   SlotState slot[kSlots];
+  int ns;                    // slots in use (the launch's n_slots)
   unsigned long long vnext;  // next virtual ray handed out
   unsigned long long ready;  // virtual rays of the chunks bound so far
   int free_for[kSlots];      // the chunk number slot s takes next (set when its previous chunk is flushed)
@@ -493,10 +494,11 @@ __device__ bool ring_bind(FwdRing& S, const TraceArgs& A) {
   if (atomicCAS(&S.lock, 0, 1) != 0) return false;
   __threadfence_block();
   bool made = false;
-  for (int it = 0; it < 2 * kSlots; ++it) {
+  const int ns = S.ns;
+  for (int it = 0; it < 2 * ns; ++it) {
     const int j = S.jready;
-    const int s = j % kSlots;
-    // slot s takes chunk j only after chunk j - kSlots was flushed from it
+    const int s = j % ns;
+    // slot s takes chunk j only after chunk j - ns was flushed from it
     if (vload(S.no_more) || vload(S.free_for[s]) != j) break;
     const long long c = (long long)atomicAdd(A.work, 1ull);
     if (c >= A.n_chunks) {
@@ -508,7 +510,7 @@ __device__ bool ring_bind(FwdRing& S, const TraceArgs& A) {
     const bool ne = chunk_range(A, c, cell, r0, r1);
     S.jready = j + 1;
     if (!ne) {  // nothing to trace: the slot stays free for the next chunk
-      vstore(S.free_for[s], j + kSlots);
+      vstore(S.free_for[s], j + ns);
       continue;
     }
     SlotState& st = S.slot[s];
@@ -587,7 +589,7 @@ __device__ void ring_flush(FwdRing& S, int s, float* s_tally, const TraceArgs& A
   }
   __syncwarp();
   __threadfence_block();
-  if (lane == 0) vstore(S.free_for[s], st.j + kSlots);
+  if (lane == 0) vstore(S.free_for[s], st.j + S.ns);
 }
 
 // Count the warp's finished rays into their chunks; the warp that finishes
@@ -685,7 +687,8 @@ __global__ void __launch_bounds__(kBlock, 2)
   constexpr int NW = 9 + 4 * F;
   float* s_tally = reinterpret_cast<float*>(smem + A.blob_bytes);
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  uint32_t* mq = reinterpret_cast<uint32_t*>(smem + A.blob_bytes + sizeof(float) * kSlots * A.bins) +
+  const int n_slots = min(max(A.n_slots, 1), kSlots);
+  uint32_t* mq = reinterpret_cast<uint32_t*>(smem + A.blob_bytes + sizeof(float) * n_slots * A.bins) +
                  wid * 2 * NW * kQCap;
   uint32_t* gq = mq + NW * kQCap;
   if (tid < 6) s_led[tid] = 0.f;
@@ -695,13 +698,14 @@ __global__ void __launch_bounds__(kBlock, 2)
     S.slot[tid].range = 0ull;
   }
   if (tid == 0) {
+    S.ns = n_slots;
     S.vnext = 0ull;
     S.ready = 0ull;
     S.jready = 0;
     S.lock = 0;
     S.no_more = 0;
   }
-  for (int i = tid; i < kSlots * A.bins; i += blockDim.x) s_tally[i] = 0.f;
+  for (int i = tid; i < n_slots * A.bins; i += blockDim.x) s_tally[i] = 0.f;
   if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;  // includes a CTA barrier
   Blob B;
   B.bind(smem);
