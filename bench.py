@@ -32,10 +32,12 @@ UNIT = "interactions/s"
 # the s and p 2x2 chain) plus 250 per hit for the coefficients, bases, Jones
 # update and geometry. The thin-film adjoint costs about three forward layer
 # chains per layer of each record (forward sweep, recomputation, reverse
-# sweep with the layer gradients).
+# sweep with the layer gradients); with the mirror-tilt gradient its first
+# sweep also carries the derivative chain (one more chain per layer).
 FLOPS_PER_LAYER = 33
 FLOPS_PER_HIT = 250
 FLOPS_ADJ_LAYER = 3 * FLOPS_PER_LAYER
+FLOPS_ADJ_LAYER_TILT = 4 * FLOPS_PER_LAYER
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -324,15 +326,19 @@ def run_ours(args):
     flops_bwd = (FLOPS_PER_LAYER * st_b["n_layer_steps"] + FLOPS_PER_HIT * st_b["n_hits"] +
                  FLOPS_ADJ_LAYER * st_b["n_adjoint_steps"])
 
-    def step(evs):
+    adj = []  # per timed step: the library's event times of its adjoint launches
+
+    def step(evs, keep=False):
         flush.zero_()
         evs[0].record(stream)
         ctx.trace_forward(dh, C, tally, stats=False)
         evs[1].record(stream)
         ctx.loss(dh, C, tally, G)
         evs[2].record(stream)
-        ctx.trace_backward(dh, C, G, grad, stats=False, grad_tilt=grad_t)
+        sb = ctx.trace_backward(dh, C, G, grad, stats=True, grad_tilt=grad_t)
         evs[3].record(stream)
+        if keep:
+            adj.append(sb)
 
     for _ in range(args.warmup):
         step([torch.cuda.Event(enable_timing=True) for _ in range(4)])
@@ -359,7 +365,7 @@ def run_ours(args):
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     t_wall0 = time.perf_counter()
     for i in range(args.steps):
-        step(evs[i])
+        step(evs[i], keep=True)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     barrier(pg, dev)
@@ -430,17 +436,31 @@ def run_ours(args):
         fwd_s = statistics.mean(fwd_ms) / 1e3
         ach_b = flops_bwd / bwd_s / 1e12
         ach_f = flops_fwd / fwd_s / 1e12
+        peak_source = (f"derived: {sm} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz "
+                       f"(sm_max_mhz of {pk_kind} peaks)")
         # the dominant kernel of the step (largest share of the launch list) is
-        # the forward trace; its duration is the event pair around the
-        # forward call on the launching stream (the kernel plus two tiny
-        # preparation launches)
-        roof = {"bound": "alu", "kernel": "k_trace_fwd", "achieved": ach_f, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach_f / peak, "traffic": profile_traffic("k_trace_fwd"),
-                "flops_per_launch": flops_fwd,
-                "units": f"{hits} interactions x ({FLOPS_PER_LAYER} x {st_f['n_layer_steps'] / hits:.1f} layers "
-                         f"+ {FLOPS_PER_HIT}) flops",
-                "peak_source": f"derived: {sm} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz "
-                               f"(sm_max_mhz of {pk_kind} peaks)"}
+        # the thin-film adjoint (tilt variant); its launches are timed by the
+        # library with CUDA events on the launching stream during the timed
+        # steps (wg_stats adjoint_ms / n_adjoint_launches)
+        n_adj = sum(s["n_adjoint_launches"] for s in adj)
+        adj_ms = sum(s["adjoint_ms"] for s in adj)
+        adj_steps = sum(s["n_adjoint_steps"] for s in adj)
+        flops_adj = FLOPS_ADJ_LAYER_TILT * adj_steps / max(1, n_adj)
+        ach_a = flops_adj / (adj_ms / max(1, n_adj) / 1e3) / 1e12 if adj_ms > 0 else 0.0
+        roof = {"bound": "alu", "kernel": "k_bwd_adjoint (tilt variant)", "achieved": ach_a, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach_a / peak, "traffic": profile_traffic("k_bwd_adjoint"),
+                "flops_per_launch": flops_adj, "launch_ms": adj_ms / max(1, n_adj), "launches": n_adj,
+                "units": f"{adj_steps / max(1, n_adj):.4g} record layer steps per launch x "
+                         f"{FLOPS_ADJ_LAYER_TILT} flops",
+                "peak_source": peak_source}
+        # the forward trace: the event pair around the forward call on the
+        # launching stream (the kernel plus two tiny preparation launches)
+        roof_f = {"bound": "alu", "kernel": "k_trace_fwd", "achieved": ach_f, "peak": peak, "unit": "TFLOP/s",
+                  "frac": ach_f / peak, "traffic": profile_traffic("k_trace_fwd"),
+                  "flops_per_launch": flops_fwd,
+                  "units": f"{hits} interactions x ({FLOPS_PER_LAYER} x {st_f['n_layer_steps'] / hits:.1f} layers "
+                           f"+ {FLOPS_PER_HIT}) flops",
+                  "peak_source": peak_source}
         roof_b = {"bound": "alu", "kernels": "k_bwd_replay + sort + k_bwd_adjoint (tilt pass excluded)", "achieved": ach_b,
                   "peak": peak, "unit": "TFLOP/s", "frac": ach_b / peak, "flops_per_call": flops_bwd}
         cpu = None
@@ -454,7 +474,7 @@ def run_ours(args):
                           "parallelism": f"replicas x{ws} (rays sharded by seed, no collective)"},
                "fwd_interactions_per_s": fwd_rate, "fwd_ms": statistics.mean(fwd_ms),
                "bwd_ms": statistics.mean(bwd_ms), "tilt_pass_ms": tilt_ms, "loss": loss[0], "wall_s": t_wall,
-               "roofline": roof, "roofline_bwd": roof_b, "cpu_baseline": cpu,
+               "roofline": roof, "roofline_fwd": roof_f, "roofline_bwd": roof_b, "cpu_baseline": cpu,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": launches, "clocks": ck, "serving": serving}
         print(json.dumps(out))

@@ -167,6 +167,10 @@ typedef struct wg_stats {
   int64_t n_tallied;      /* backward: rays that ended in the eyebox */
   int64_t n_adjoint_steps;/* backward: layer steps of the thin-film adjoint */
   int64_t n_nonfinite;    /* backward: non-finite per-layer terms dropped (expected 0) */
+  float replay_ms;        /* backward: device time of the replay launches (CUDA events) */
+  float adjoint_ms;       /* backward: device time of the thin-film adjoint launches */
+  float tilt_ms;          /* backward: device time of the tilt tangent passes (0 without grad_tilt) */
+  int32_t n_adjoint_launches; /* backward: thin-film adjoint launches (one per replay batch with records) */
 } wg_stats;
 
 /* ---- context ---------------------------------------------------------- */

@@ -76,6 +76,7 @@ struct wg_ctx {
   DevBuf loss;    // loss workspace
   cudaEvent_t ws_free = nullptr;  // last use of the workspaces
   cudaEvent_t t0 = nullptr, t1 = nullptr;
+  cudaEvent_t kev[6] = {};  // backward with stats: around the replay, adjoint and tilt launches
   int max_slots = 64;
   size_t hbm_budget = 0;
   std::string autotune_cache;
@@ -141,7 +142,10 @@ extern "C" wg_status wg_init(wg_ctx** out, const wg_init_opts* opts) {
   if (opts) c->hbm_budget = opts->hbm_budget_bytes;
   if (opts && opts->autotune_cache) c->autotune_cache = opts->autotune_cache;
   if (cudaEventCreateWithFlags(&c->ws_free, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreate(&c->t0) != cudaSuccess || cudaEventCreate(&c->t1) != cudaSuccess) {
+      cudaEventCreate(&c->t0) != cudaSuccess || cudaEventCreate(&c->t1) != cudaSuccess ||
+      cudaEventCreate(&c->kev[0]) != cudaSuccess || cudaEventCreate(&c->kev[1]) != cudaSuccess ||
+      cudaEventCreate(&c->kev[2]) != cudaSuccess || cudaEventCreate(&c->kev[3]) != cudaSuccess ||
+      cudaEventCreate(&c->kev[4]) != cudaSuccess || cudaEventCreate(&c->kev[5]) != cudaSuccess) {
     delete c;
     return fail(WG_EDEVICE, "wg_init: event creation failed");
   }
@@ -176,6 +180,8 @@ extern "C" void wg_shutdown(wg_ctx* c) {
   if (c->ws_free) cudaEventDestroy(c->ws_free);
   if (c->t0) cudaEventDestroy(c->t0);
   if (c->t1) cudaEventDestroy(c->t1);
+  for (cudaEvent_t e : c->kev)
+    if (e) cudaEventDestroy(e);
   delete c;
 }
 
@@ -653,6 +659,8 @@ static wg_status finish_stats(wg_ctx* c, const WsLayout& w, cudaStream_t s, wg_s
     stats->n_tallied = (int64_t)h.counters[6];
     stats->n_adjoint_steps = (int64_t)h.counters[7];
     stats->n_nonfinite = (int64_t)h.counters[8];
+    stats->replay_ms = stats->adjoint_ms = stats->tilt_ms = 0.f;
+    stats->n_adjoint_launches = 0;
     for (int i = 0; i < 6; ++i) stats->ledger[i] = h.ledger[i];
     stats->kernel_ms = 0.f;
     if (timed) cudaEventElapsedTime(&stats->kernel_ms, c->t0, c->t1);
@@ -1163,7 +1171,8 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   const ExitRec* list =
       use_list ? reinterpret_cast<const ExitRec*>(static_cast<const uint8_t*>(d->exits.p) + kExitHead) : nullptr;
   const long long w_begin = use_list ? 0 : p.rb, w_end = use_list ? n_list : p.re;
-  float ms_total = 0.f;
+  float ms_total = 0.f, ms_replay = 0.f, ms_adjoint = 0.f, ms_tilt = 0.f;
+  int n_adj_launches = 0;
   for (long long b0 = w_begin; b0 < w_end;) {
     const long long b1 = std::min(w_end, b0 + batch);
     Plan q = p;
@@ -1190,6 +1199,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     const int grid_r = (int)std::max<long long>(1, std::min<long long>(a.n_chunks, (long long)c->sm_count * bps_r));
     if (stats) CU(cudaEventRecord(c->t0, s));
     CU(launch_bwd_replay(a, p.F, d->period, tilt, grid_r, smem_r, s));
+    if (stats) CU(cudaEventRecord(c->kev[1], s));
     unsigned long long counts[2] = {0, 0};  // records, ray heads
     CU(cudaMemcpyAsync(counts, sc.hit_count, sizeof(counts), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
@@ -1217,11 +1227,14 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     aa.counters = w.head->counters;
     aa.error = &w.head->error;
     CU(cudaMemsetAsync(&w.head->work, 0, sizeof(unsigned long long), s));
+    if (stats) CU(cudaEventRecord(c->kev[2], s));
     if (n_rec > 0) {
       const long long chunks = ((long long)n_rec + aa.rec_chunk - 1) / aa.rec_chunk;
       const int grid_a = (int)std::min<long long>(chunks, (long long)c->sm_count * bps_a);
       CU(launch_bwd_adjoint(aa, d->period, grid_a, smem_a, s));
+      ++n_adj_launches;
     }
+    if (stats) CU(cudaEventRecord(c->kev[3], s));
     const long long n_heads = std::min<long long>((long long)counts[1], b1 - b0);
     for (int k0 = 0; tilt && n_heads > 0 && k0 < d->K; k0 += 8) {
       TraceArgs at = a;
@@ -1235,9 +1248,15 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     if (stats) {
       CU(cudaEventRecord(c->t1, s));
       CU(cudaEventSynchronize(c->t1));
-      float ms = 0.f;
+      float ms = 0.f, mr = 0.f, ma = 0.f, mt = 0.f;
       cudaEventElapsedTime(&ms, c->t0, c->t1);
+      cudaEventElapsedTime(&mr, c->t0, c->kev[1]);
+      cudaEventElapsedTime(&ma, c->kev[2], c->kev[3]);
+      cudaEventElapsedTime(&mt, c->kev[3], c->t1);
       ms_total += ms;
+      ms_replay += mr;
+      ms_adjoint += ma;
+      ms_tilt += mt;
     }
     b0 = b1;
   }
@@ -1256,7 +1275,13 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   }
   if (stats || !dev_g) {
     st = finish_stats(c, w, s, stats, false);
-    if (stats) stats->kernel_ms = ms_total;
+    if (stats) {
+      stats->kernel_ms = ms_total;
+      stats->replay_ms = ms_replay;
+      stats->adjoint_ms = ms_adjoint;
+      stats->tilt_ms = ms_tilt;
+      stats->n_adjoint_launches = n_adj_launches;
+    }
     return st;
   }
   return WG_OK;

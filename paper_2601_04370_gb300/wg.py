@@ -62,13 +62,15 @@ class Stats(C.Structure):
     _fields_ = [("n_rays", C.c_int64), ("n_hits", C.c_int64), ("n_events", C.c_int64), ("n_tir", C.c_int64),
                 ("n_layer_steps", C.c_int64), ("ledger", C.c_double * 6), ("kernel_ms", C.c_float),
                 ("overflow", C.c_int32), ("n_tallied", C.c_int64), ("n_adjoint_steps", C.c_int64),
-                ("n_nonfinite", C.c_int64)]
+                ("n_nonfinite", C.c_int64), ("replay_ms", C.c_float), ("adjoint_ms", C.c_float),
+                ("tilt_ms", C.c_float), ("n_adjoint_launches", C.c_int32)]
 
     def to_dict(self):
         return dict(n_rays=self.n_rays, n_hits=self.n_hits, n_events=self.n_events, n_tir=self.n_tir,
                     n_layer_steps=self.n_layer_steps, ledger=np.array(self.ledger[:]), kernel_ms=self.kernel_ms,
                     overflow=self.overflow, n_tallied=self.n_tallied, n_adjoint_steps=self.n_adjoint_steps,
-                    n_nonfinite=self.n_nonfinite)
+                    n_nonfinite=self.n_nonfinite, replay_ms=self.replay_ms, adjoint_ms=self.adjoint_ms,
+                    tilt_ms=self.tilt_ms, n_adjoint_launches=self.n_adjoint_launches)
 
 
 # serving (include/wg.h)
