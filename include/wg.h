@@ -384,6 +384,41 @@ wg_status wg_cancel(wg_ctx* ctx, wg_ticket ticket);
  * it has not seen on their first batch. */
 wg_status wg_autotune(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cfg);
 
+/* ------------------------------------------------------------------------
+ * Optimizer of the layer thicknesses (Results, "Evaluation": all PRMA
+ * thicknesses optimized jointly within 20-200 nm; a soft gap between 0 and
+ * 20 nm lets layers be eliminated, which prunes an over-parameterized stack).
+ * The paper does not name its optimizer: this is Adam on the thicknesses in
+ * nm, followed by a projection: clamp to [0, d_max]; a value inside the gap
+ * (0, d_min) goes to 0 below d_min / 2, else to d_min. A layer at zero
+ * thickness stays in its stack as an identity layer (its gradient keeps
+ * flowing); layers the design prunes are never updated. One optimization
+ * step is wg_trace_forward, wg_loss, wg_trace_backward, wg_adam_step.
+ * ------------------------------------------------------------------------ */
+typedef struct wg_adam_opts {
+  float lr_nm;     /* step size in nm (0 = 2) */
+  float beta1;     /* first-moment decay (0 = 0.9) */
+  float beta2;     /* second-moment decay (0 = 0.999) */
+  float eps;       /* (0 = 1e-8) */
+  float d_min_nm;  /* smallest manufacturable thickness, upper end of the gap (0 = 20) */
+  float d_max_nm;  /* upper bound (0 = 200) */
+} wg_adam_opts;
+typedef struct wg_adam wg_adam;
+
+/* Optimizer state (FP32 thicknesses, FP64 moments, on the design's device)
+ * for design d. thickness_nm: the starting thicknesses ([sum n_layers],
+ * host or device; NULL: the design's as last set from the host). NULL opts:
+ * the defaults. Does not change the design. Errors: WG_EINVAL, WG_ENOMEM. */
+wg_status wg_adam_create(wg_design* d, const wg_adam_opts* opts, const float* thickness_nm, wg_adam** out);
+/* One step with dL/dthickness ([sum n_layers] FP64, host or device, as
+ * wg_trace_backward writes it); the projected thicknesses go to the design
+ * (wg_set_params, stream-ordered on `stream`). Non-finite gradient entries
+ * leave their layer unchanged. Errors: WG_EINVAL, WG_EDEVICE. */
+wg_status wg_adam_step(wg_adam* a, const double* grad_thickness, void* stream);
+/* Copies the current thicknesses ([sum n_layers] FP32, host or device). */
+wg_status wg_adam_params(wg_adam* a, float* thickness_nm, void* stream);
+void wg_adam_destroy(wg_adam* a);
+
 #ifdef __cplusplus
 }
 #endif

@@ -355,3 +355,36 @@ def loss_and_grad(tally, dims, Cfg, kind="cv", w_f=10.0, w_e=3.0):
     M = pupil_masks(dims, Cfg).reshape(-1, ny * nx).astype(np.float64)
     G = (dI @ M) / Cfg.n_cell                      # [lam, f, bins]
     return L, dict(I_mean=mean, u_fov=u_f, u_eyebox=u_e), G.reshape(Cfg.tally_shape)
+
+
+def adam_projected_step(theta, m, v, g, t, lr=2.0, beta1=0.9, beta2=0.999, eps=1e-8, d_min=20.0, d_max=200.0,
+                        fixed=None):
+    """One optimizer step on the layer thicknesses (Results, "Evaluation":
+    thicknesses within 20-200 nm, a soft gap between 0 and 20 nm through
+    which layers can be eliminated). The paper does not name the optimizer;
+    this is Adam (Kingma and Ba, 2015, Algorithm 1) written out in FP64 on
+    the thicknesses in nm:
+        m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+        theta <- theta - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),
+    then the projection: clamp to [0, d_max]; a value in the gap (0, d_min)
+    goes to 0 below d_min / 2, else to d_min. Thicknesses are kept in FP32
+    (as the design stores them). Layers with fixed[i] set, and layers whose
+    gradient is not finite, are left as they are. Returns new (theta, m, v)."""
+    theta = np.asarray(theta, dtype=np.float32).astype(np.float64)
+    m = np.array(m, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    upd = np.isfinite(g)
+    if fixed is not None:
+        upd &= ~np.asarray(fixed, dtype=bool)
+    gg = np.where(upd, g, 0.0)
+    m_new = beta1 * m + (1.0 - beta1) * gg
+    v_new = beta2 * v + (1.0 - beta2) * gg * gg
+    mhat = m_new / (1.0 - beta1 ** t)
+    vhat = v_new / (1.0 - beta2 ** t)
+    x = theta - lr * mhat / (np.sqrt(vhat) + eps)
+    x = np.clip(x, 0.0, d_max)
+    gap = (x > 0.0) & (x < d_min)
+    x = np.where(gap, np.where(x < 0.5 * d_min, 0.0, d_min), x)
+    theta_new = np.where(upd, x, theta).astype(np.float32)
+    return theta_new, np.where(upd, m_new, m), np.where(upd, v_new, v)

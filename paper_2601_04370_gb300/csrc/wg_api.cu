@@ -730,6 +730,9 @@ const char* ctx_autotune_cache(const wg_ctx* c) { return c->autotune_cache.empty
 void** ctx_serve_slot(wg_ctx* c) { return &c->serve; }
 const void* fused_dev_base(const wg_ctx* c) { return c->fws.p; }
 long long design_params(const wg_design* d) { return d->n_orig; }
+wg_ctx* design_ctx(const wg_design* d) { return d->ctx; }
+const float* design_thickness(const wg_design* d) { return d->layer_d.data(); }
+const uint8_t* design_pruned(const wg_design* d) { return d->pruned.data(); }
 void design_shape(const wg_design* d, int* K, int* n_dev, int* period) {
   *K = d->K;
   *n_dev = d->n_dev;

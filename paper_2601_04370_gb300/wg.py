@@ -130,6 +130,11 @@ def lib():
         L.wg_poll.argtypes = [vp, C.c_uint64, i64, C.POINTER(Result)]
         L.wg_cancel.argtypes = [vp, C.c_uint64]
         L.wg_autotune.argtypes = [vp, vp, C.POINTER(TraceCfg)]
+        L.wg_adam_create.argtypes = [vp, C.POINTER(AdamOpts), vp, C.POINTER(vp)]
+        L.wg_adam_step.argtypes = [vp, vp, vp]
+        L.wg_adam_params.argtypes = [vp, vp, vp]
+        L.wg_adam_destroy.argtypes = [vp]
+        L.wg_adam_destroy.restype = None
         for name in ("wg_init", "wg_create_design", "wg_set_params", "wg_eval_coating", "wg_eval_coating_grad",
                      "wg_trace_forward", "wg_trace_backward", "wg_loss", "wg_trace_forward_noalloc",
                      "wg_submit", "wg_poll", "wg_cancel", "wg_autotune"):
@@ -177,11 +182,86 @@ class _CfgHolder:
                           stream=stream, ray_begin=rb, ray_end=re, ray_records=_ptr(records))
 
 
+class AdamOpts(C.Structure):
+    _fields_ = [("lr_nm", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("d_min_nm", C.c_float), ("d_max_nm", C.c_float)]
+
+
+class Adam:
+    """Thickness optimizer of a design (wg_adam_*): Adam in nm, then the
+    projection onto [0, d_max] with the soft gap (0, d_min) (0 below
+    d_min / 2, else d_min). Each step writes the thicknesses to the design."""
+
+    def __init__(self, dh, lr_nm=2.0, beta1=0.9, beta2=0.999, eps=1e-8, d_min_nm=20.0, d_max_nm=200.0,
+                 thickness_nm=None):
+        self.dh = dh
+        self.n = dh.n_params
+        o = AdamOpts(lr_nm, beta1, beta2, eps, d_min_nm, d_max_nm)
+        h = C.c_void_p()
+        keep = None
+        ptr = None
+        if thickness_nm is not None:
+            if hasattr(thickness_nm, "data_ptr") and thickness_nm.is_cuda:
+                ptr = thickness_nm.data_ptr()
+            else:
+                keep = np.ascontiguousarray(np.asarray(thickness_nm, dtype=np.float32))
+                ptr = keep.ctypes.data
+        _check(lib().wg_adam_create(dh.h, C.byref(o), ptr, C.byref(h)))
+        self.h = h
+
+    def step(self, grad_thickness, stream=None):
+        """grad_thickness: FP64 [n] (torch CUDA tensor or numpy array)."""
+        _check(lib().wg_adam_step(self.h, _ptr(grad_thickness), stream if stream is not None else _current_stream()))
+
+    def params(self):
+        out = np.zeros(self.n, dtype=np.float32)
+        _check(lib().wg_adam_params(self.h, out.ctypes.data, None))
+        return out
+
+    def close(self):
+        if self.h:
+            lib().wg_adam_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def optimize(ctx, dh, cfg, n_iter, adam=None, loss_kind=0, w_f=10.0, w_e=3.0, callback=None):
+    """Thickness optimization of a design (the paper's loop, Results: the
+    loss of Eq. 1 on the traced tally, its adjoint, one optimizer step per
+    iteration). The Philox keys stay the same every iteration, so the
+    objective is a deterministic function of the thicknesses. Returns the
+    per-iteration (L, I_mean, U_fov, U_eyebox) and the optimizer."""
+    import torch
+    adam = adam if adam is not None else Adam(dh)
+    tally = torch.zeros(cfg.tally_shape, dtype=torch.float64, device="cuda")
+    G = torch.zeros_like(tally)
+    g = torch.zeros(dh.n_params, dtype=torch.float64, device="cuda")
+    hist = []
+    for it in range(n_iter):
+        ctx.trace_forward(dh, cfg, tally, stats=False)
+        hist.append(ctx.loss(dh, cfg, tally, G, kind=loss_kind, w_f=w_f, w_e=w_e))
+        ctx.trace_backward(dh, cfg, G, g, stats=False)
+        adam.step(g)
+        if callback is not None:
+            callback(it, hist[-1], adam)
+    return np.array(hist), adam
+
+
 class DesignHandle:
     def __init__(self, ctx, handle, design):
         self.ctx = ctx
         self.h = handle
         self.design = design
+
+    @property
+    def n_params(self):
+        """Layer thicknesses of the design (its gradient's length)."""
+        return int(self.design.total_layers)
 
     def set_params(self, thickness_nm=None, tilt_deg=None, stream=None):
         th = tl = None

@@ -255,6 +255,15 @@ def with_tilts(D: Design, tilt_deg) -> Design:
     return D.replace(mirror_tilt_deg=_f32(tilt_deg))
 
 
+def gaussian_thickness(D: Design, seed=0, sigma_nm=30.0, lo_nm=20.0, hi_nm=200.0):
+    """Starting thicknesses of an optimization (Results: a Gaussian centred at
+    the midpoint of the thickness bounds; the spread is not given, 30 nm here),
+    clipped to the bounds; layers the design prunes stay at 0."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d = np.clip(rng.normal(0.5 * (lo_nm + hi_nm), sigma_nm, size=D.total_layers), lo_nm, hi_nm)
+    return _f32(np.where(np.asarray(D.pruned, dtype=bool), 0.0, d))
+
+
 def seeded_params(n_total, n_pick, seed=3):
     rng = np.random.Generator(np.random.PCG64(seed))
     return np.sort(rng.choice(n_total, size=n_pick, replace=False))
