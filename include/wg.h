@@ -138,6 +138,15 @@ typedef struct wg_trace_cfg {
   int32_t flags;              /* WG_TRACE_* bits, 0 = defaults */
   float pupil_y_mm;           /* 3D: lateral extent of the launch region */
   float eb_cx_mm, eb_cy_mm, eb_w_mm, eb_h_mm;  /* eyebox centre and size */
+  int32_t lut_bins;           /* 0: each hit runs its stack's transfer-matrix chain. N in
+                                 [16, 65536]: the coating look-up table of the paper's
+                                 memory-saving variant (Fig. 3c, Results): per mirror,
+                                 side and wavelength the coefficients at cos(theta_0) =
+                                 (j + 1/2) / N are computed once per call, every hit
+                                 interpolates linearly in cos(theta_0), and the adjoint
+                                 scatters dL/dc into the table's entries and runs the
+                                 thin-film adjoint once per entry. wg_trace_forward and
+                                 wg_trace_backward only (not served, not no-alloc). */
   void* stream;               /* cudaStream_t or NULL */
   int64_t ray_begin, ray_end; /* traced ray ids [begin, end); end <= 0: all */
   void* ray_records;          /* NULL or device wg_ray_record[end - begin] */

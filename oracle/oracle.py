@@ -52,7 +52,7 @@ class OraDesign(C.Structure):
 class OraCfg(C.Structure):
     _fields_ = [("n_lam", C.c_int32), ("n_fx", C.c_int32), ("n_fy", C.c_int32), ("pol", C.c_int32),
                 ("n_rays", C.c_int64), ("seed", C.c_uint64), ("max_events", C.c_int32),
-                ("eb_nx", C.c_int32), ("eb_ny", C.c_int32), ("pad0", C.c_int32),
+                ("eb_nx", C.c_int32), ("eb_ny", C.c_int32), ("lut_bins", C.c_int32),
                 ("pupil_y_mm", C.c_double), ("eb_cx_mm", C.c_double), ("eb_cy_mm", C.c_double),
                 ("eb_w_mm", C.c_double), ("eb_h_mm", C.c_double),
                 ("lam_nm", C.POINTER(C.c_double)), ("fx_deg", C.POINTER(C.c_double)),
@@ -206,7 +206,8 @@ class _Marshalled:
                            layer_d_nm=d64(D.layer_d_nm), pruned=typed(D.pruned, np.uint8, C.c_uint8))
         self.c = OraCfg(n_lam=len(Cfg.lam_nm), n_fx=len(Cfg.fx_deg), n_fy=len(Cfg.fy_deg), pol=Cfg.pol,
                         n_rays=Cfg.n_rays, seed=Cfg.seed, max_events=Cfg.max_events, eb_nx=Cfg.eb_nx,
-                        eb_ny=Cfg.eb_ny, pad0=0, pupil_y_mm=Cfg.pupil_y_mm, eb_cx_mm=Cfg.eb_cx_mm,
+                        eb_ny=Cfg.eb_ny, lut_bins=int(getattr(Cfg, "lut_bins", 0)), pupil_y_mm=Cfg.pupil_y_mm,
+                        eb_cx_mm=Cfg.eb_cx_mm,
                         eb_cy_mm=Cfg.eb_cy_mm, eb_w_mm=Cfg.eb_w_mm, eb_h_mm=Cfg.eb_h_mm,
                         lam_nm=d64(Cfg.lam_nm), fx_deg=d64(Cfg.fx_deg), fy_deg=d64(Cfg.fy_deg))
 

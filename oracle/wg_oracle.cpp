@@ -42,6 +42,7 @@
 #include <cstdint>
 #include <cstring>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 namespace ora {
@@ -429,7 +430,7 @@ struct OraCfg {
   uint64_t seed;
   int32_t max_events;
   int32_t eb_nx, eb_ny;
-  int32_t pad0;
+  int32_t lut_bins;  // 0: exact coefficients per hit; N: the coating table (see mirror_coef)
   double pupil_y_mm;
   double eb_cx_mm, eb_cy_mm, eb_w_mm, eb_h_mm;
   const double* lam_nm;   // [n_lam]
@@ -638,7 +639,7 @@ static V3<double> vval(const V3<T>& v) {
 
 // Effective coefficients of mirror k seen from side `front`.
 template <class T>
-static Coef<T> mirror_coef(const TraceCtx<T>& X, int k, bool front, const T& cos_i, double lambda) {
+static Coef<T> mirror_coef_at(const TraceCtx<T>& X, int k, bool front, const T& cos_i, double lambda) {
   const OraDesign& D = *X.D;
   int off = X.layer_off[k], L = D.n_layers[k];
   std::vector<double> n;
@@ -652,6 +653,91 @@ static Coef<T> mirror_coef(const TraceCtx<T>& X, int k, bool front, const T& cos
     d.push_back(X.P->d[off + l]);
   }
   return tmm(D.n_slab, D.n_slab, cos_i, (int)n.size(), n.data(), d.data(), lambda);
+}
+
+// Exact coefficients of mirror k's stack in FP64 at cos(theta_0) = c (the
+// thicknesses' values), for the look-up table's grid derivatives.
+template <class T>
+static Coef<double> mirror_coef_value(const TraceCtx<T>& X, int k, bool front, double c, double lambda) {
+  const OraDesign& D = *X.D;
+  int off = X.layer_off[k], L = D.n_layers[k];
+  std::vector<double> n, d;
+  for (int j = 0; j < L; ++j) {
+    int l = front ? j : L - 1 - j;
+    if (D.pruned[off + l]) continue;
+    n.push_back(D.mat_n[D.layer_mat[off + l]]);
+    d.push_back(val(X.P->d[off + l]));
+  }
+  return tmm(D.n_slab, D.n_slab, c, (int)n.size(), n.data(), d.data(), lambda);
+}
+
+// d/d(cos t0) of the exact coefficients at c: central differences at h and
+// h/2 combined by Richardson extrapolation (error O(h^4) ~ 1e-20 relative
+// to the fringe scale, rounding ~1e-11), in FP64.
+template <class T>
+static Coef<double> mirror_coef_dcos(const TraceCtx<T>& X, int k, bool front, double c, double lambda) {
+  auto cd = [&](double h) {
+    const Coef<double> p = mirror_coef_value(X, k, front, c + h, lambda);
+    const Coef<double> m = mirror_coef_value(X, k, front, c - h, lambda);
+    const double s = 1.0 / (2.0 * h);
+    Coef<double> r;
+    r.rs = scale(p.rs - m.rs, s);
+    r.rp = scale(p.rp - m.rp, s);
+    r.ts = scale(p.ts - m.ts, s);
+    r.tp = scale(p.tp - m.tp, s);
+    return r;
+  };
+  const double h = 1e-5;
+  const Coef<double> a = cd(h), b = cd(0.5 * h);
+  Coef<double> r;
+  r.rs = scale(b.rs, 4.0 / 3.0) - scale(a.rs, 1.0 / 3.0);
+  r.rp = scale(b.rp, 4.0 / 3.0) - scale(a.rp, 1.0 / 3.0);
+  r.ts = scale(b.ts, 4.0 / 3.0) - scale(a.ts, 1.0 / 3.0);
+  r.tp = scale(b.tp, 4.0 / 3.0) - scale(a.tp, 1.0 / 3.0);
+  return r;
+}
+
+// Coefficients of a hit. With C.lut_bins = N > 0, the coating look-up table
+// of the paper's memory-saving variant (Fig. 3c, Results): the stack's
+// coefficients and their derivatives with respect to cos(theta_0) are known
+// at the N bin centres cos_j = (j + 1/2) / N, and a hit interpolates both
+// linearly between the two centres that bracket its cos(theta_0) (weights
+// clamped to the end points). The value is that interpolation of the exact
+// coefficients (a function of the thicknesses through both entries); its
+// derivative with respect to cos(theta_0) (through which the mirror tilts act)
+// is the interpolated exact derivative. Written out as that definition.
+template <class T>
+static Coef<T> mirror_coef(const TraceCtx<T>& X, int k, bool front, const T& cos_i, double lambda) {
+  const int N = X.C->lut_bins;
+  if (N <= 0) return mirror_coef_at(X, k, front, cos_i, lambda);
+  const double ci = val(cos_i);
+  const double x = ci * N - 0.5;  // position in bins: cos_j = (j + 1/2) / N
+  int j = (int)std::floor(x);
+  j = std::min(std::max(j, 0), N - 2);
+  const double cj = (j + 0.5) / N, cj1 = (j + 1.5) / N;
+  const double f = std::min(std::max((ci - cj) * N, 0.0), 1.0);
+  const Coef<T> a = mirror_coef_at(X, k, front, T(cj), lambda);
+  const Coef<T> b = mirror_coef_at(X, k, front, T(cj1), lambda);
+  Coef<T> c;
+  c.rs = a.rs + scale(b.rs - a.rs, T(f));
+  c.rp = a.rp + scale(b.rp - a.rp, T(f));
+  c.ts = a.ts + scale(b.ts - a.ts, T(f));
+  c.tp = a.tp + scale(b.tp - a.tp, T(f));
+  if constexpr (!std::is_same<T, double>::value) {
+    // the cos(theta_0) dependence: (cos_i - its value) times the interpolated derivative
+    const Coef<double> da = mirror_coef_dcos(X, k, front, cj, lambda);
+    const Coef<double> db = mirror_coef_dcos(X, k, front, cj1, lambda);
+    const T dx = cos_i - T(ci);
+    auto term = [&](const Cx<double>& p, const Cx<double>& q) {
+      const Cx<double> dd = p + scale(q - p, f);
+      return scale(Cx<T>(T(dd.re), T(dd.im)), dx);
+    };
+    c.rs = c.rs + term(da.rs, db.rs);
+    c.rp = c.rp + term(da.rp, db.rp);
+    c.ts = c.ts + term(da.ts, db.ts);
+    c.tp = c.tp + term(da.tp, db.tp);
+  }
+  return c;
 }
 
 // One Monte Carlo ray (Methods: polarization ray tracing + MC sampling).

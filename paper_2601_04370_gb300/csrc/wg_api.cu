@@ -82,6 +82,7 @@ struct wg_ctx {
   std::string autotune_cache;
   std::vector<wg_design*> designs;
   DevBuf fws;     // fused-forward workspace (per-job heads, configuration arrays, job table)
+  DevBuf lut;     // coating look-up table of the last call that asked for one
   void* serve = nullptr;  // serving runtime state (wg_serve.cu)
 };
 
@@ -480,6 +481,8 @@ static wg_status validate_cfg(const wg_design* d, const wg_trace_cfg* cfg) {
   for (int i = 0; i < cfg->n_fy; ++i)
     if (!(std::fabs(cfg->field_y_deg[i]) < 80.0f)) return fail(WG_EINVAL, "cfg: field_y %d invalid", i);
   if (cfg->flags & ~WG_TRACE_NO_EXIT_LIST) return fail(WG_EINVAL, "cfg: unknown flags 0x%x", cfg->flags);
+  if (cfg->lut_bins != 0 && (cfg->lut_bins < 16 || cfg->lut_bins > 65536))
+    return fail(WG_EINVAL, "cfg: lut_bins must be 0 or in [16, 65536]");
   return WG_OK;
 }
 
@@ -644,6 +647,31 @@ static wg_status prepare_exit_list(wg_design* d, const wg_trace_cfg* cfg, const 
   return WG_OK;
 }
 
+// Coating look-up table (cfg->lut_bins > 0): built on s for the design's
+// current thicknesses and the call's wavelengths; bin centres cos_j = (j + 1/2) / N.
+static long long lut_entries(const wg_design* d, const wg_trace_cfg* cfg) {
+  return (long long)d->K * 2 * cfg->n_lambda * cfg->lut_bins;
+}
+static wg_status prepare_lut(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, const WsLayout& w, cudaStream_t s,
+                             TraceArgs& a) {
+  if (cfg->lut_bins <= 0) return WG_OK;
+  const int N = cfg->lut_bins;
+  const long long ne = lut_entries(d, cfg);
+  const size_t bytes = sizeof(float4) * 4 * (size_t)ne;
+  if (bytes > c->lut.n) {
+    CU(cudaEventSynchronize(c->ws_free));
+    CU(c->lut.ensure(bytes));
+  }
+  const float c0 = 0.5f / (float)N, dc = 1.0f / (float)N;
+  CU(launch_lut_build(d->blob, d->period, d->K, cfg->n_lambda, w.lam, N, c0, dc, static_cast<float4*>(c->lut.p), s));
+  a.lut = static_cast<const float4*>(c->lut.p);
+  a.lut_n = N;
+  a.n_lam = cfg->n_lambda;
+  a.lut_c0 = c0;
+  a.lut_inv_dc = (float)N;
+  return WG_OK;
+}
+
 static wg_status finish_stats(wg_ctx* c, const WsLayout& w, cudaStream_t s, wg_stats* stats, bool timed) {
   WsHead h;
   CU(cudaMemcpyAsync(&h, w.head, sizeof(WsHead), cudaMemcpyDeviceToHost, s));
@@ -699,6 +727,8 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
   a.tally = t;
   wg_design* dm = const_cast<wg_design*>(d);  // the eyebox-ray list is a cache owned by the design
   st = prepare_exit_list(dm, cfg, p, c->sm_count, s, a);
+  if (st != WG_OK) return st;
+  st = prepare_lut(c, d, cfg, w, s, a);
   if (st != WG_OK) return st;
   const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, d->period, smem));
   const int grid = (int)std::min<long long>(p.n_chunks, (long long)c->sm_count * bps);
@@ -825,6 +855,7 @@ wg_status fused_prepare(wg_ctx* c, FusedJob* jobs, int n, int blocks_per_sm, Fus
     J.status = WG_OK;
     memset(&J.stats, 0, sizeof(J.stats));
     if (!J.design || !J.cfg || !J.tally) return fail(WG_EINVAL, "fused forward: job %d incomplete", j);
+    if (J.cfg->lut_bins) return fail(WG_EINVAL, "fused forward: job %d asks for the coating table (not fused)", j);
     Plan& p = B.plans[j];
     wg_status st = make_plan(J.design, J.cfg, 2048, p);
     if (st != WG_OK) return st;
@@ -1114,7 +1145,11 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   const size_t acc_bytes = (sizeof(double) * std::max(1, d->n_dev) + 15) & ~(size_t)15;
   const size_t aux_bytes =
       tilt ? (size_t)cap * (sizeof(TiltAux) + sizeof(unsigned int)) + (size_t)batch * sizeof(RayHead) : 0;
-  const size_t need = 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + acc_bytes + aux_bytes;
+  // coating table: FP64 dL/dc per entry and the second stage's records
+  const bool use_lut = cfg->lut_bins > 0;
+  const long long n_lut = use_lut ? lut_entries(d, cfg) : 0;
+  const size_t lut_bytes = use_lut ? (size_t)n_lut * (8 * sizeof(double) + 2 * hit_rec_bytes()) : 0;
+  const size_t need = 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + acc_bytes + aux_bytes + lut_bytes;
   if (need > c->bwd.n) {
     CU(cudaEventSynchronize(c->ws_free));
     CU(c->bwd.ensure(need));
@@ -1134,6 +1169,12 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     tilt_aux = (TiltAux*)(bw + 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + acc_bytes);
     heads = (RayHead*)((uint8_t*)tilt_aux + (size_t)cap * sizeof(TiltAux));
     perm = (unsigned int*)((uint8_t*)heads + (size_t)batch * sizeof(RayHead));
+  }
+  double* lut_grad = nullptr;
+  HitRec* lut_recs = nullptr;
+  if (use_lut) {
+    lut_grad = (double*)(bw + 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + acc_bytes + aux_bytes);
+    lut_recs = (HitRec*)((uint8_t*)lut_grad + (size_t)n_lut * 8 * sizeof(double));
   }
   const bool dev_G = is_device_ptr(dL_dtally);
   const bool dev_g = is_device_ptr(grad_thickness);
@@ -1160,6 +1201,16 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     CU(cudaMemsetAsync(gt, 0, sizeof(double) * d->K, s));
   }
   const int bps_a = std::max(1, bwd_adjoint_blocks_per_sm(d->period, smem_a));
+  // coating table: the same table as the forward's (same thicknesses), and
+  // the FP64 sums of dL/dc per entry that the replay scatters into
+  TraceArgs lut_a;
+  memset(&lut_a, 0, sizeof(lut_a));
+  if (use_lut) {
+    st = prepare_lut(c, d, cfg, w, s, lut_a);
+    if (st != WG_OK) return st;
+    CU(cudaMemsetAsync(lut_grad, 0, (size_t)n_lut * 8 * sizeof(double), s));
+    lut_a.lut_grad = lut_grad;
+  }
   // rays to replay: the eyebox rays listed by the forward trace of this
   // configuration and geometry if there is such a list, else the ray range
   bool use_list = d->exit_fp != 0 && d->exit_fp == path_fingerprint(d, cfg, p);
@@ -1196,6 +1247,12 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     a.ray_heads = heads;
     a.head_cap = b1 - b0;
     a.head_count = sc.hit_count + 1;
+    a.lut = lut_a.lut;
+    a.lut_n = lut_a.lut_n;
+    a.n_lam = lut_a.n_lam;
+    a.lut_c0 = lut_a.lut_c0;
+    a.lut_inv_dc = lut_a.lut_inv_dc;
+    a.lut_grad = lut_a.lut_grad;
     CU(cudaMemsetAsync(&w.head->work, 0, sizeof(unsigned long long), s));
     CU(cudaMemsetAsync(sc.keys, 0, 128 * sizeof(unsigned int), s));
     CU(cudaMemsetAsync(sc.hit_count, 0, 2 * sizeof(unsigned long long), s));
@@ -1215,7 +1272,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
       batch = std::max<long long>(1, (b1 - b0) / 2);
       continue;
     }
-    CU(launch_bwd_sort(sc.rec, (long long)n_rec, sc.keys, sc.keys + 128, sc.keys + 256, sc.sorted, perm, s));
+    if (!use_lut) CU(launch_bwd_sort(sc.rec, (long long)n_rec, sc.keys, sc.keys + 128, sc.keys + 256, sc.sorted, perm, s));
     AdjArgs aa;
     aa.tilt_aux = tilt_aux;
     aa.perm = perm;
@@ -1231,7 +1288,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     aa.error = &w.head->error;
     CU(cudaMemsetAsync(&w.head->work, 0, sizeof(unsigned long long), s));
     if (stats) CU(cudaEventRecord(c->kev[2], s));
-    if (n_rec > 0) {
+    if (n_rec > 0 && !use_lut) {  // (table mode: one adjoint over the table's entries after the last batch)
       const long long chunks = ((long long)n_rec + aa.rec_chunk - 1) / aa.rec_chunk;
       const int grid_a = (int)std::min<long long>(chunks, (long long)c->sm_count * bps_a);
       CU(launch_bwd_adjoint(aa, d->period, grid_a, smem_a, s));
@@ -1262,6 +1319,38 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
       ms_tilt += mt;
     }
     b0 = b1;
+  }
+  if (use_lut) {
+    // second stage: the thin-film adjoint once per (table entry, r or t) with
+    // the entry's accumulated dL/dc as its weights
+    CU(launch_lut_records(lut_grad, d->K, cfg->n_lambda, w.lam, lut_a.lut_n, lut_a.lut_c0, 1.0f / lut_a.lut_inv_dc,
+                          lut_recs, s));
+    AdjArgs aa;
+    memset(&aa, 0, sizeof(aa));
+    aa.blob = d->blob;
+    aa.blob_bytes = d->blob_bytes;
+    aa.recs = lut_recs;
+    aa.n_rec = 2 * n_lut;
+    aa.rec_chunk = 2048;
+    aa.n_layers = d->n_dev;
+    aa.grad_acc = sc.grad_acc;
+    aa.work = &w.head->work;
+    aa.counters = w.head->counters;
+    aa.error = &w.head->error;
+    CU(cudaMemsetAsync(&w.head->work, 0, sizeof(unsigned long long), s));
+    if (stats) CU(cudaEventRecord(c->kev[2], s));
+    const long long chunks = (aa.n_rec + aa.rec_chunk - 1) / aa.rec_chunk;
+    const int grid_a = (int)std::min<long long>(chunks, (long long)c->sm_count * bps_a);
+    CU(launch_bwd_adjoint(aa, d->period, grid_a, smem_a, s));
+    ++n_adj_launches;
+    if (stats) {
+      CU(cudaEventRecord(c->kev[3], s));
+      CU(cudaEventSynchronize(c->kev[3]));
+      float ma = 0.f;
+      cudaEventElapsedTime(&ma, c->kev[2], c->kev[3]);
+      ms_adjoint += ma;
+      ms_total += ma;
+    }
   }
   CU(launch_scatter_grad(sc.grad_acc, d->n_dev, d->d_dev_to_orig, gout, s));
   if (tilt && !dev_t) {
@@ -1349,6 +1438,7 @@ static wg_status noalloc_scratch(int device, void** out) {
 extern "C" wg_status wg_trace_forward_noalloc(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, double* tally,
                                               wg_stats* stats) {
   if (!c || !d || !tally) return fail(WG_EINVAL, "wg_trace_forward_noalloc: NULL ctx/design/tally");
+  if (cfg && cfg->lut_bins) return fail(WG_EINVAL, "wg_trace_forward_noalloc: the coating table needs allocations");
   Plan p;
   wg_status st = make_plan(d, cfg, 2048, p);
   if (st != WG_OK) return st;

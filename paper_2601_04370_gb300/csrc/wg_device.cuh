@@ -258,6 +258,11 @@ __device__ __forceinline__ void cv_rescale(CV& v, int& e) {
     e += 64;
   }
 }
+// 2^e as a double from its exponent bits (0 below the normal range): exact,
+// without the FP64 arithmetic of ldexp (few FP64 units per SM)
+__device__ __forceinline__ double pow2d(int e) {
+  return e < -1022 ? 0.0 : __longlong_as_double((long long)(1023 + min(e, 1023)) << 52);
+}
 __device__ __forceinline__ float pow2i(int e) {  // 2^e as float, 0 below the range
   if (e < -149) return 0.0f;
   if (e > 127) return __int_as_float(0x7f800000);
@@ -442,6 +447,85 @@ __device__ __forceinline__ void coef_from_v_d(const CV& v, const CV& dv, float e
   t = cscale(q, 2.0f * eta0 * sc);
   dr = cmul(csub(dnum, cmul(r, dden)), q);
   dt = cmul(csub(make_float2(2.0f * deta0 * sc, 0.0f), cmul(t, dden)), q);
+}
+
+// v and its derivative scaled by the same exact power of two
+__device__ __forceinline__ void cv_rescale_d(CV& v, CV& dv, int& e) {
+  if (fmaxf(cv_maxabs(v), cv_maxabs(dv)) > TWO_P64) {
+    v = CV{v.xr * TWO_M64, v.xi * TWO_M64, v.yr * TWO_M64, v.yi * TWO_M64};
+    dv = CV{dv.xr * TWO_M64, dv.xi * TWO_M64, dv.yr * TWO_M64, dv.yi * TWO_M64};
+    e += 64;
+  }
+}
+
+// Coefficients in the paper's convention and their derivatives d/d(cos t0):
+// the layer loop of tmm_forward (segments of the material period, material
+// constants and their derivatives in registers) carrying the dual vector
+// (the coating look-up table's entries).
+template <int P>
+__device__ __forceinline__ void tmm_forward_dual(const StackView& st, bool front, const MatTable& mt,
+                                                 const MatTableD& mtd, float n0, float cos0, Coef& cf, Coef& dcf) {
+  constexpr int CKP = Seg<P>::CKP;
+  MatK kb[Seg<P>::NSLOT];
+  MatKD kbd[Seg<P>::NSLOT];
+  if constexpr (P > 0) {
+#pragma unroll
+    for (int v = 0; v < P; ++v) {
+      int r = front ? v : (((st.L - 1 - v) % P) + P) % P;
+      r = r < st.L ? r : 0;
+      const int m = st.m[st.off + r];
+      kb[v] = mt.get(m);
+      kbd[v] = mtd.get(m);
+    }
+  }
+  const float eta_s = n0 * cos0, eta_p = n0 / cos0;
+  const float deta_s = n0, deta_p = -eta_p / cos0;
+  CV vs{1.0f, 0.0f, eta_s, 0.0f}, vp{1.0f, 0.0f, eta_p, 0.0f};
+  CV dvs{0.0f, 0.0f, deta_s, 0.0f}, dvp{0.0f, 0.0f, deta_p, 0.0f};
+  int es = 0, ep = 0;
+  const int L = st.L;
+  for (int j0 = L > 0 ? ((L - 1) / CKP) * CKP : -1; j0 >= 0; j0 -= CKP) {
+#pragma unroll
+    for (int u = CKP - 1; u >= 0; --u) {
+      const int j = j0 + u;
+      if (j < L) {
+        const int i = st.idx(front, j);
+        MatK k;
+        MatKD kd;
+        if constexpr (P > 0) {
+          k = kb[u % P];
+          kd = kbd[u % P];
+        } else {
+          const int m = st.m[i];
+          k = mt.get(m);
+          kd = mtd.get(m);
+        }
+        const float dthk = st.d[i];
+        float c, s, dc, ds;
+        layer_cs(k, dthk, c, s);
+        if (!k.evan) {
+          const float dth = TWO_PI * dthk * kd.dkt;  // d(phase)
+          dc = -s * dth;
+          ds = c * dth;
+        } else {
+          const float dx = dthk * kd.dkt;
+          dc = s * dx;
+          ds = c * dx;
+        }
+        cv_step_d(vs, dvs, c, s * k.q12s, s * k.q21s, dc, fmaf(ds, k.q12s, s * kd.dq12s),
+                  fmaf(ds, k.q21s, s * kd.dq21s));
+        cv_step_d(vp, dvp, c, s * k.q12p, s * k.q21p, dc, fmaf(ds, k.q12p, s * kd.dq12p),
+                  fmaf(ds, k.q21p, s * kd.dq21p));
+      }
+    }
+    cv_rescale_d(vs, dvs, es);
+    cv_rescale_d(vp, dvp, ep);
+  }
+  float2 rpm, drpm;
+  coef_from_v_d(vs, dvs, eta_s, deta_s, es, cf.rs, cf.ts, dcf.rs, dcf.ts);
+  coef_from_v_d(vp, dvp, eta_p, deta_p, ep, rpm, cf.tp, drpm, dcf.tp);
+  cf.rp = make_float2(-rpm.x, -rpm.y);
+  dcf.rp = make_float2(-drpm.x, -drpm.y);
 }
 
 // ---------------------------------------------------------------------------

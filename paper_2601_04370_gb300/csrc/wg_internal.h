@@ -85,6 +85,16 @@ struct TraceArgs {
   long long head_cap;
   unsigned long long* head_count;
   long long n_heads;
+  // coating look-up table (null: exact transfer-matrix chain per hit):
+  // per (mirror, side (0: ray on the +normal side), wavelength, cos bin j)
+  // the raw coefficients at cos_j = lut_c0 + j / lut_inv_dc and their
+  // derivatives d/d(cos t0), as float4 {r_s, r_p}, {t_s, t_p}, {dr_s, dr_p},
+  // {dt_s, dt_p}; hits interpolate both linearly in cos(theta_0)
+  const float4* lut;
+  int lut_n, n_lam;
+  float lut_c0, lut_inv_dc;
+  // backward with the table: FP64 dL/d(coefficient) per entry, {r_s, r_p, t_s, t_p} x {re, im}
+  double* lut_grad;
 };
 
 // Arguments of the thin-film adjoint over sorted hit records.
@@ -157,6 +167,13 @@ cudaError_t launch_coating_grad(const uint8_t* blob, int P, int mirror, int side
                                 const float* lam, const float* w, int which, float* grad, cudaStream_t s);
 cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const int* orig_to_dev, int n_orig,
                                     cudaStream_t s);
+// coating look-up table: entries for every (mirror, side, wavelength, bin)
+// of the design (lam: device [n_lam]); records: one hit record per (entry,
+// r or t) carrying the entry's accumulated FP64 weights, in stack order
+cudaError_t launch_lut_build(const uint8_t* blob, int P, int n_mir, int n_lam, const float* lam, int n, float c0,
+                             float dc, float4* out, cudaStream_t s);
+cudaError_t launch_lut_records(const double* grad, int n_mir, int n_lam, const float* lam, int n, float c0, float dc,
+                               HitRec* out, cudaStream_t s);
 // mirror-tilt gradient of the a.n_heads rays a tilt replay recorded, one
 // pass per group of 8 mirrors starting at a.tilt_k0
 cudaError_t launch_tilt_grad(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s);

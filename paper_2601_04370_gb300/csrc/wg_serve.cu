@@ -675,6 +675,7 @@ extern "C" wg_status wg_submit(wg_ctx* c, const wg_request* req, wg_ticket* tick
   if (req->kind == WG_REQ_LOSS_GRAD && req->loss_kind != 0 && req->loss_kind != 1)
     return wgh::set_error(WG_EINVAL, "wg_submit: loss_kind must be 0 (CV) or 1 (variance)");
   if (req->cfg.ray_records) return wgh::set_error(WG_EINVAL, "wg_submit: per-ray records are not served");
+  if (req->cfg.lut_bins) return wgh::set_error(WG_EINVAL, "wg_submit: the coating table is not served");
   auto t = std::make_unique<Ticket>();
   t->req = *req;
   const wg_trace_cfg& src = req->cfg;

@@ -340,9 +340,26 @@ struct MirrorStep {
   int front, refl;
 };
 
+// Entry and weight of the coating table for cos(theta_0) = c: the hit's
+// coefficients are (1 - f) entry(j) + f entry(j + 1); f is clamped to [0, 1]
+// (constant beyond the grid's end points).
+__device__ __forceinline__ void lut_locate(const TraceArgs& A, float c, int& j, float& f) {
+  const float x = (c - A.lut_c0) * A.lut_inv_dc;
+  j = min(max((int)floorf(x), 0), A.lut_n - 2);
+  f = fminf(fmaxf(x - (float)j, 0.0f), 1.0f);
+}
+__device__ __forceinline__ long long lut_entry(const TraceArgs& A, int k, bool front, int li, int j) {
+  return (((long long)k * 2 + (front ? 0 : 1)) * A.n_lam + li) * A.lut_n + j;
+}
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float f) {
+  return make_float2(fmaf(f, b.x - a.x, a.x), fmaf(f, b.y - a.y, a.y));
+}
+
+// li: wavelength index of the hit (the coating table's, when A.lut is set)
 template <int F, int P>
-__device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob& B, float lam, const TraceArgs& A,
-                                                   int& layer_steps, float2* Es_out, float2* Ep_out) {
+__device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob& B, float lam, int li,
+                                                   const TraceArgs& A, int& layer_steps, float2* Es_out,
+                                                   float2* Ep_out) {
   const BlobHeader& H = *B.h;
   const MirrorRec& M = B.mir[k];
   const V3 N = v3(M.nx, 0.0f, M.nz);
@@ -350,10 +367,23 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
   MirrorStep st;
   st.front = cd < 0.0f;
   st.cos0 = fabsf(cd);
-  MatTable mt;
-  mt.init(H, st.cos0, lam);
-  const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
-  const Coef cf = tmm_forward<P>(sv, st.front, mt, H.n_slab, st.cos0, layer_steps);
+  Coef cf;
+  if (A.lut) {
+    int j;
+    float f;
+    lut_locate(A, st.cos0, j, f);
+    const float4* e = A.lut + 4 * lut_entry(A, k, st.front, li, j);
+    const float4 a0 = __ldg(e), a1 = __ldg(e + 1), b0 = __ldg(e + 4), b1 = __ldg(e + 5);
+    cf.rs = lerp2(make_float2(a0.x, a0.y), make_float2(b0.x, b0.y), f);
+    cf.rp = lerp2(make_float2(a0.z, a0.w), make_float2(b0.z, b0.w), f);
+    cf.ts = lerp2(make_float2(a1.x, a1.y), make_float2(b1.x, b1.y), f);
+    cf.tp = lerp2(make_float2(a1.z, a1.w), make_float2(b1.z, b1.w), f);
+  } else {
+    MatTable mt;
+    mt.init(H, st.cos0, lam);
+    const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+    cf = tmm_forward<P>(sv, st.front, mt, H.n_slab, st.cos0, layer_steps);
+  }
   V3 sf, pf;
   face_basis(R.d, sf, pf);
   V3 sm = cross3(R.d, N);
@@ -900,7 +930,8 @@ __global__ void __launch_bounds__(kBlock, 2)
       bool fin = false, keep = false;
       if ((unsigned)lane < n) {
         slot = q_get<F>(mq, (mh + lane) % kQCap, R, A.ray_begin);
-        mirror_event<F, P>(R, R.last - S_MIR, B, S.slot[slot].cc.lam, A, c_steps, nullptr, nullptr);
+        mirror_event<F, P>(R, R.last - S_MIR, B, S.slot[slot].cc.lam, (int)(S.slot[slot].cc.cell / A.n_f), A, c_steps,
+                           nullptr, nullptr);
         if (R.ev >= A.max_events) {
           fin = true;
           c_events += R.ev;
@@ -1200,22 +1231,56 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                     As = cadd(As, cmulc(gs[f], E.Es[f]));
                     Ap = cadd(Ap, cmulc(gp[f], E.Ep[f]));
                   }
-                  HitRec rec;
-                  rec.kfw = E.kfw;
-                  rec.cos0 = E.cos0;
-                  rec.lam = lam_l;
-                  rec.eA = eG;
-                  rec.As = cscale(As, scl);
-                  rec.Ap = cscale(Ap, scl);
-                  hb[first + h] = rec;
+                  double g_cos = 0.0;  // dL/d(cos t0) of the hit through its coating (table mode)
+                  if (A.lut) {
+                    // two-stage adjoint: dL/dc of the hit goes to the two table
+                    // entries it interpolated, with the interpolation weights
+                    int j;
+                    float f;
+                    lut_locate(A, E.cos0, j, f);
+                    const bool front = (E.kfw >> 8) & 1;
+                    const long long e = lut_entry(A, k, front, (int)(cell_l / A.n_f), j);
+                    // FP32 relative to the ray's exponent of dL/dtally; one exact
+                    // power of two turns each value into FP64 for the sums
+                    const double p2 = pow2d(eG);
+                    const float2 gs_ = cscale(As, scl), gp_ = cscale(Ap, scl);
+                    const float gq[4] = {gs_.x, gs_.y, gp_.x, gp_.y};
+                    double* g0 = A.lut_grad + 8 * e + (refl ? 0 : 4);
+                    const float w0 = 1.0f - f, w1 = f;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                      if (gq[q] != 0.0f) {
+                        if (w0 != 0.0f) atomicAdd(g0 + q, (double)(w0 * gq[q]) * p2);
+                        if (w1 != 0.0f) atomicAdd(g0 + 8 + q, (double)(w1 * gq[q]) * p2);
+                      }
+                    }
+                    if constexpr (T) {
+                      // d/d(cos t0) of the coefficients: the tabulated exact
+                      // derivatives, interpolated like the values
+                      const float4* t4 = A.lut + 4 * e + 2 + (refl ? 0 : 1);
+                      const float4 a = __ldg(t4), b = __ldg(t4 + 4);
+                      const float2 ds = make_float2(fmaf(f, b.x - a.x, a.x), fmaf(f, b.y - a.y, a.y));
+                      const float2 dp = make_float2(fmaf(f, b.z - a.z, a.z), fmaf(f, b.w - a.w, a.w));
+                      g_cos = (double)(2.0f * (cmul(gs_, ds).x + cmul(gp_, dp).x)) * p2;
+                    }
+                  } else {
+                    HitRec rec;
+                    rec.kfw = E.kfw;
+                    rec.cos0 = E.cos0;
+                    rec.lam = lam_l;
+                    rec.eA = eG;
+                    rec.As = cscale(As, scl);
+                    rec.Ap = cscale(Ap, scl);
+                    hb[first + h] = rec;
+                    atomicAdd(&s_keys[((E.kfw & 0xff) << 1) | ((E.kfw >> 8) & 1)], 1u);  // stack (mirror, side)
+                  }
                   if constexpr (T) {
                     TiltAux ta;
                     ta.cs = E.cs;
                     ta.cp = E.cp;
-                    ta.g_cos = 0.0;  // set by the adjoint kernel
+                    ta.g_cos = g_cos;  // exact mode: set by the adjoint kernel
                     A.tilt_aux[first + h] = ta;
                   }
-                  atomicAdd(&s_keys[((E.kfw & 0xff) << 1) | ((E.kfw >> 8) & 1)], 1u);  // stack (mirror, side)
 #pragma unroll
                   for (int f = 0; f < F; ++f) {
                     const float2 xs = cmulc(E.cs, gs[f]), xp = cmulc(E.cp, gp[f]);
@@ -1233,7 +1298,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
         if (at_mir) {
           const int h = R.hits;
           float2 Es[F], Ep[F];
-          const MirrorStep ms = mirror_event<F, P>(R, hit_k, B, lam_l, A, c_steps, Es, Ep);
+          const MirrorStep ms = mirror_event<F, P>(R, hit_k, B, lam_l, (int)(cell_l / A.n_f), A, c_steps, Es, Ep);
           if (h < TAPE_HITS) {
             TapeE<F>& E = tape[h];
             E.cs = ms.cs;
@@ -1676,7 +1741,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_adjoint(const AdjArgs A) {
           float g = 0.f;
           tmm_adjoint<P, GradSink, true>(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, seg, rec.eA,
                                          &mtd, &g);
-          A.tilt_aux[A.perm[i]].g_cos = ldexp((double)g, rec.eA);
+          A.tilt_aux[A.perm[i]].g_cos = (double)g * pow2d(rec.eA);
         } else {
           tmm_adjoint<P>(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, seg, rec.eA);
         }
@@ -1713,6 +1778,69 @@ __global__ void k_scatter_grad(const double* acc, int n_layers, const int* dev_t
 // ---------------------------------------------------------------------------
 // K1: coating evaluation and its adjoint (test hooks, global-memory stack)
 // ---------------------------------------------------------------------------
+// Coating look-up table: one thread per (mirror, side, wavelength, bin j),
+// the raw coefficients at cos_j = c0 + j dc and their derivatives d/d(cos t0)
+// from the dual layer chain (entry layout as TraceArgs::lut)
+template <int P>
+__global__ void k_lut_build(const uint8_t* blob, int n_mir, int n_lam, const float* lam, int n, float c0, float dc,
+                            float4* out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)n_mir * 2 * n_lam * n;
+  if (i >= total) return;
+  const int j = (int)(i % n);
+  const long long q = i / n;
+  const int li = (int)(q % n_lam);
+  const int side = (int)((q / n_lam) % 2);
+  const int k = (int)(q / (2ll * n_lam));
+  Blob B;
+  B.bind(blob);
+  const BlobHeader& H = *B.h;
+  const MirrorRec& M = B.mir[k];
+  const float c = fmaf((float)j, dc, c0);
+  MatTable mt;
+  mt.init(H, c, lam[li]);
+  MatTableD mtd;
+  mtd.init(H, c, lam[li], mt);
+  const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+  Coef cf, dcf;
+  tmm_forward_dual<P>(sv, side == 0, mt, mtd, H.n_slab, c, cf, dcf);
+  out[4 * i] = make_float4(cf.rs.x, cf.rs.y, cf.rp.x, cf.rp.y);
+  out[4 * i + 1] = make_float4(cf.ts.x, cf.ts.y, cf.tp.x, cf.tp.y);
+  out[4 * i + 2] = make_float4(dcf.rs.x, dcf.rs.y, dcf.rp.x, dcf.rp.y);
+  out[4 * i + 3] = make_float4(dcf.ts.x, dcf.ts.y, dcf.tp.x, dcf.tp.y);
+}
+
+// Hit records of the table's second stage: one per (entry, r or t), in
+// stack order, with the entry's accumulated dL/dc as weights (a common
+// power of two split off into eA, as for the per-hit records)
+__global__ void k_lut_records(const double* grad, int n_mir, int n_lam, const float* lam, int n, float c0, float dc,
+                              HitRec* out) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)n_mir * 2 * n_lam * 2 * n;
+  if (i >= total) return;
+  const int j = (int)(i % n);
+  long long q = i / n;
+  const int which = (int)(q % 2);
+  q /= 2;
+  const int li = (int)(q % n_lam);
+  q /= n_lam;
+  const int side = (int)(q % 2);
+  const int k = (int)(q / 2);
+  const long long e = (((long long)k * 2 + side) * n_lam + li) * n + j;
+  const double* g = grad + 8 * e + 4 * which;
+  const double m = fmax(fmax(fabs(g[0]), fabs(g[1])), fmax(fabs(g[2]), fabs(g[3])));
+  int eA = 0;
+  if (m > 0.0) frexp(m, &eA);
+  HitRec r;
+  r.kfw = k | ((side == 0 ? 1 : 0) << 8) | (which << 9);
+  r.cos0 = fmaf((float)j, dc, c0);
+  r.lam = lam[li];
+  r.eA = eA;
+  r.As = make_float2((float)ldexp(g[0], -eA), (float)ldexp(g[1], -eA));
+  r.Ap = make_float2((float)ldexp(g[2], -eA), (float)ldexp(g[3], -eA));
+  out[i] = r;
+}
+
 template <int P>
 __global__ void k_coating_eval(const uint8_t* blob, int mirror, int side, long long n, const float* cos0,
                                const float* lam, float* out) {
@@ -1900,6 +2028,24 @@ cudaError_t launch_coating_eval(const uint8_t* blob, int P, int mirror, int side
   if (n <= 0) return cudaSuccess;
   note_launches(1);
   WG_PICK_P(k_coating_eval, P)<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(blob, mirror, side, n, cos0, lam, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lut_build(const uint8_t* blob, int P, int n_mir, int n_lam, const float* lam, int n, float c0,
+                             float dc, float4* out, cudaStream_t s) {
+  const long long total = (long long)n_mir * 2 * n_lam * n;
+  if (total <= 0) return cudaSuccess;
+  note_launches(1);
+  WG_PICK_P(k_lut_build, P)<<<(unsigned)((total + 127) / 128), 128, 0, s>>>(blob, n_mir, n_lam, lam, n, c0, dc, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lut_records(const double* grad, int n_mir, int n_lam, const float* lam, int n, float c0, float dc,
+                               HitRec* out, cudaStream_t s) {
+  const long long total = (long long)n_mir * 2 * n_lam * 2 * n;
+  if (total <= 0) return cudaSuccess;
+  note_launches(1);
+  k_lut_records<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(grad, n_mir, n_lam, lam, n, c0, dc, out);
   return cudaGetLastError();
 }
 

@@ -54,7 +54,7 @@ class TraceCfg(C.Structure):
                 ("field_y_deg", C.POINTER(C.c_float)), ("n_rays", C.c_int64), ("seed", C.c_uint64),
                 ("max_events", C.c_int32), ("eb_nx", C.c_int32), ("eb_ny", C.c_int32), ("flags", C.c_int32),
                 ("pupil_y_mm", C.c_float), ("eb_cx_mm", C.c_float), ("eb_cy_mm", C.c_float),
-                ("eb_w_mm", C.c_float), ("eb_h_mm", C.c_float), ("stream", C.c_void_p),
+                ("eb_w_mm", C.c_float), ("eb_h_mm", C.c_float), ("lut_bins", C.c_int32), ("stream", C.c_void_p),
                 ("ray_begin", C.c_int64), ("ray_end", C.c_int64), ("ray_records", C.c_void_p)]
 
 
@@ -179,6 +179,7 @@ class _CfgHolder:
                           n_rays=int(cfg.n_rays), seed=int(cfg.seed), max_events=int(cfg.max_events),
                           eb_nx=int(cfg.eb_nx), eb_ny=int(cfg.eb_ny), flags=int(flags), pupil_y_mm=cfg.pupil_y_mm,
                           eb_cx_mm=cfg.eb_cx_mm, eb_cy_mm=cfg.eb_cy_mm, eb_w_mm=cfg.eb_w_mm, eb_h_mm=cfg.eb_h_mm,
+                          lut_bins=int(getattr(cfg, "lut_bins", 0)),
                           stream=stream, ray_begin=rb, ray_end=re, ray_records=_ptr(records))
 
 

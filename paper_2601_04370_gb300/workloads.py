@@ -98,6 +98,7 @@ class TraceConfig:
     eb_h_mm: float = 8.0
     eb_nx: int = 64
     eb_ny: int = 1
+    lut_bins: int = 0         # 0: each hit's exact layer chain; N: the coating table with N bins of cos(theta_0)
 
     def __post_init__(self):
         self.lam_nm = _f32(self.lam_nm)
