@@ -394,6 +394,27 @@ wg_status wg_cancel(wg_ctx* ctx, wg_ticket ticket);
 wg_status wg_autotune(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cfg);
 
 /* ------------------------------------------------------------------------
+ * Reflection-probability pre-optimization (Methods, "Learned reflection
+ * probabilities"): before the thicknesses are optimized, each mirror's
+ * omega is chosen to bring throughput to the pupils, with each coating
+ * idealized as a scalar reflectance (here equal to its omega, so every
+ * sampled path has weight one) and geometric tracing without polarization.
+ * ------------------------------------------------------------------------ */
+/* The model's trace of cfg's rays: tally (host or device FP64, tally layout,
+ * overwritten) gets each eyebox ray's unpolarized exit transmittance
+ * (T_s + T_p) / 2; with dL_dtally (host or device, may be NULL)
+ * grad_omega (host or device FP64 [n_mirrors], may be NULL, overwritten)
+ * gets dL/d omega, the score-function estimator: the sum over tallied rays of
+ * dL/dtally[bin] I (n_r,k / omega_k - n_t,k / (1 - omega_k)). Same Philox
+ * decisions as wg_trace_forward. Errors: WG_EINVAL, WG_ENOMEM, WG_EDEVICE. */
+wg_status wg_omega_trace(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cfg, const double* dL_dtally,
+                         double* tally, double* grad_omega);
+/* Replaces the mirrors' reflection probabilities ([n_mirrors], host, each in
+ * (0, 1)); the sampled paths change, so an earlier eyebox-ray list no longer
+ * applies. Returns once the device copy is done. Errors: WG_EINVAL. */
+wg_status wg_set_omega(wg_design* d, const float* omega, int32_t n, void* stream);
+
+/* ------------------------------------------------------------------------
  * Optimizer of the layer thicknesses (Results, "Evaluation": all PRMA
  * thicknesses optimized jointly within 20-200 nm; a soft gap between 0 and
  * 20 nm lets layers be eliminated, which prunes an over-parameterized stack).

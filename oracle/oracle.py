@@ -91,6 +91,10 @@ def lib():
                                     C.c_int, dp, dp, C.POINTER(OraStats), C.c_void_p]
             L.ora_split.argtypes = [C.POINTER(OraDesign), C.POINTER(OraCfg), C.c_int64, C.c_int64,
                                     C.c_int, C.c_double, dp, dp, C.POINTER(C.c_int64)]
+            L.ora_geo_trace.argtypes = [C.POINTER(OraDesign), C.POINTER(OraCfg), C.c_int64, C.c_int64, C.c_int,
+                                        C.c_void_p, dp, C.c_void_p]
+            L.ora_geo_split.argtypes = [C.POINTER(OraDesign), C.POINTER(OraCfg), C.c_int64, C.c_int64, C.c_int,
+                                        C.c_double, dp]
             L.ora_trace_grad.argtypes = [C.POINTER(OraDesign), C.POINTER(OraCfg), C.c_int64,
                                          C.c_int64, C.c_int, dp, C.c_void_p, dp, dp, C.c_void_p]
             L.ora_trace_path.argtypes = [C.POINTER(OraDesign), C.POINTER(OraCfg), C.c_int64,
@@ -255,6 +259,33 @@ def split(D, Cfg, rays=None, nthreads=0, prune=0.0):
     lib().ora_split(C.byref(m.d), C.byref(m.c), r0, r1, int(nthreads), float(prune), _dptr(tally),
                     _dptr(ledger), C.byref(nb))
     return dict(tally=tally.reshape(Cfg.tally_shape), ledger=ledger, n_branches=int(nb.value))
+
+
+def geo_trace(D, Cfg, G=None, rays=None, nthreads=0):
+    """Reflection-probability pre-optimization model (Methods, "Learned
+    reflection probabilities"): geometric Monte Carlo trace with each coating
+    a scalar reflectance equal to its mirror's omega, no polarization, the
+    unpolarized Fresnel transmittance at the eye-side face. Returns (tally,
+    dL/d omega [K] for G = dL/dtally, or None): the score-function estimator
+    sum over tallied rays of G[bin] I (n_r/omega - n_t/(1 - omega))."""
+    m = _Marshalled(D, Cfg)
+    r0, r1 = _range(Cfg, rays)
+    tally = np.zeros(Cfg.tally_size)
+    grad = np.zeros(D.n_mirrors) if G is not None else None
+    g = None if G is None else np.ascontiguousarray(np.asarray(G, dtype=np.float64).reshape(-1))
+    lib().ora_geo_trace(C.byref(m.d), C.byref(m.c), r0, r1, int(nthreads),
+                        None if g is None else g.ctypes.data, _dptr(tally), None if grad is None else grad.ctypes.data)
+    return tally.reshape(Cfg.tally_shape), grad
+
+
+def geo_split(D, Cfg, rays=None, nthreads=0, prune=1e-12):
+    """Expected tally of the geometric model for the same launch points, by
+    deterministic splitting (reflect with probability omega, transmit 1 - omega)."""
+    m = _Marshalled(D, Cfg)
+    r0, r1 = _range(Cfg, rays)
+    tally = np.zeros(Cfg.tally_size)
+    lib().ora_geo_split(C.byref(m.d), C.byref(m.c), r0, r1, int(nthreads), float(prune), _dptr(tally))
+    return tally.reshape(Cfg.tally_shape)
 
 
 def trace_grad(D, Cfg, G, rays=None, nthreads=0, mask=None, ray_intensity=False):

@@ -1385,4 +1385,189 @@ int ora_hardware_threads(void) {
   return hw > 0 ? hw : 1;
 }
 
+// ---------------------------------------------------------------------------
+// Reflection-probability pre-optimization (Methods, "Learned reflection
+// probabilities"): each coating idealized as a scalar reflectance, here equal
+// to its mirror's omega, and geometric ray tracing without polarization. At a
+// slab face a ray beyond the critical angle reflects completely (TIR);
+// otherwise the eye-side face transmits the unpolarized Fresnel power
+// (T_s + T_p) / 2 and the ray is tallied at the eye plane, and the back face
+// leaks. With the sampling probability equal to the reflectance every path
+// has weight one, and the derivative of the expected tally with respect to
+// omega_k is the score-function estimator
+//   d E[I] / d omega_k = E[ I (n_r,k / omega_k - n_t,k / (1 - omega_k)) ]
+// (n_r,k / n_t,k: the path's reflections / transmissions at mirror k).
+// ---------------------------------------------------------------------------
+// the eye-side exit: unpolarized transmittance and flat tally index (-1 outside the eyebox)
+static double geo_exit(const OraDesign& D, const OraCfg& C, const V3<double>& p, const V3<double>& d, int64_t cell,
+                       int64_t& flat) {
+  const double n = D.n_slab, cos_i = std::fabs(d.z), sin2 = 1.0 - d.z * d.z;
+  const double ct = std::sqrt(1.0 - n * n * sin2);
+  Fresnel<double> fr = fresnel(n, 1.0, Cx<double>(cos_i), Cx<double>(ct));
+  const double tf = ct / (cos_i * n);
+  const double T = 0.5 * (abs2(fr.ts) + abs2(fr.tp)) * tf;
+  const double ax = n * d.x, ay = n * d.y, az = ct;
+  const double sfac = D.eye_relief_mm / az;
+  const double qx = p.x + sfac * ax, qy = p.y + sfac * ay;
+  int ex = (int)std::floor((qx - (C.eb_cx_mm - 0.5 * C.eb_w_mm)) / C.eb_w_mm * C.eb_nx);
+  int ey = 0;
+  bool inside = ex >= 0 && ex < C.eb_nx;
+  if (D.dims == 3) {
+    ey = (int)std::floor((qy - (C.eb_cy_mm - 0.5 * C.eb_h_mm)) / C.eb_h_mm * C.eb_ny);
+    inside = inside && ey >= 0 && ey < C.eb_ny;
+  }
+  flat = inside ? cell * bins_per_cell(C) + (int64_t)ey * C.eb_nx + ex : -1;
+  return T;
+}
+
+// one Monte Carlo ray of the geometric trace: adds its tallied power to
+// tally (local, cells from cell0) and, with G, G[bin] I times its score to grad
+static void geo_ray(const TraceCtx<double>& X, uint64_t ray, double* tally, int64_t cell0, const double* G,
+                    double* grad) {
+  const OraDesign& D = *X.D;
+  const OraCfg& C = *X.C;
+  Launch<double> L = launch<double>(D, C, ray);
+  const int64_t cell = (int64_t)L.lam_i * C.n_fx * C.n_fy + L.f;
+  V3<double> p = L.p, d = L.d;
+  const double n = D.n_slab;
+  std::vector<std::pair<int, bool>> hits;
+  int last = S_LEFT, m = 0;
+  for (int ev = 0; ev < C.max_events; ++ev) {
+    double tmin = 0.0;
+    const int sid = next_surface(D, *X.P, p, d, last, tmin);
+    if (sid < 0) return;
+    p = p + d * tmin;
+    last = sid;
+    if (sid >= S_MIR) {
+      const int k = sid - S_MIR;
+      const V3<double> N = mirror_normal(X.P->tilt[k]);
+      const double cd = dot(d, N);
+      U4 ctr = {{(uint32_t)ray, (uint32_t)(ray >> 32), (uint32_t)(m >> 2), TAG_EVT}};
+      U4 rr = philox4x32_10(ctr, (uint32_t)C.seed, (uint32_t)(C.seed >> 32));
+      const bool refl = u24(rr.v[m & 3]) < (double)D.mir_omega[k];
+      ++m;
+      hits.push_back({k, refl});
+      if (refl) d = d - N * (2.0 * cd);
+      continue;
+    }
+    if (sid == S_BOT || sid == S_TOP) {
+      if (n * n * (1.0 - d.z * d.z) > 1.0) {
+        d = V3<double>(d.x, d.y, -d.z);
+        continue;
+      }
+      if (sid == S_BOT) return;
+      int64_t flat;
+      const double T = geo_exit(D, C, p, d, cell, flat);
+      if (flat < 0) return;
+      tally[flat - cell0 * bins_per_cell(C)] += T;
+      if (G && grad)
+        for (const auto& h : hits) {
+          const double w = (double)D.mir_omega[h.first];
+          grad[h.first] += G[flat] * T * (h.second ? 1.0 / w : -1.0 / (1.0 - w));
+        }
+      return;
+    }
+    return;  // far end, input mirror or a side: absorbed
+  }
+}
+
+// deterministic splitting of the same model: every branch with its
+// probability weight (reflect omega, transmit 1 - omega), pruned below prune
+static void geo_split_rec(const TraceCtx<double>& X, double* tally, int64_t cell0, int64_t cell, V3<double> p,
+                          V3<double> d, double w, int last, int ev, double prune) {
+  const OraDesign& D = *X.D;
+  const OraCfg& C = *X.C;
+  const double n = D.n_slab;
+  for (; ev < C.max_events; ++ev) {
+    double tmin = 0.0;
+    const int sid = next_surface(D, *X.P, p, d, last, tmin);
+    if (sid < 0) return;
+    p = p + d * tmin;
+    last = sid;
+    if (sid >= S_MIR) {
+      const int k = sid - S_MIR;
+      const V3<double> N = mirror_normal(X.P->tilt[k]);
+      const double om = (double)D.mir_omega[k];
+      if (w * om > prune) geo_split_rec(X, tally, cell0, cell, p, d - N * (2.0 * dot(d, N)), w * om, sid, ev + 1, prune);
+      if (w * (1.0 - om) > prune) geo_split_rec(X, tally, cell0, cell, p, d, w * (1.0 - om), sid, ev + 1, prune);
+      return;
+    }
+    if (sid == S_BOT || sid == S_TOP) {
+      if (n * n * (1.0 - d.z * d.z) > 1.0) {
+        d = V3<double>(d.x, d.y, -d.z);
+        continue;
+      }
+      if (sid == S_BOT) return;
+      int64_t flat;
+      const double T = geo_exit(D, C, p, d, cell, flat);
+      if (flat >= 0) tally[flat - cell0 * bins_per_cell(C)] += w * T;
+      return;
+    }
+    return;
+  }
+}
+
+extern "C" {
+// Geometric Monte Carlo trace of rays [r0, r1): tally (full layout, zeroed
+// here) and, with G (dL/dtally, full layout), grad_omega[K] = dL/d omega_k.
+int ora_geo_trace(const OraDesign* D, const OraCfg* C, int64_t r0, int64_t r1, int nthreads, const double* G,
+                  double* tally, double* grad_omega) {
+  Params<double> P = params_of(*D);
+  TraceCtx<double> X = make_ctx(*D, *C, P);
+  const int64_t bpc = bins_per_cell(*C), ncell = n_cell_of(*C);
+  std::memset(tally, 0, sizeof(double) * cells_of(*C) * bpc);
+  if (grad_omega) std::memset(grad_omega, 0, sizeof(double) * D->n_mir);
+  const int nt = pick_threads(nthreads, r1 - r0);
+  struct Part {
+    std::vector<double> tally, grad;
+    int64_t cell0 = 0;
+  };
+  std::vector<Part> parts(nt);
+  parallel_rays(nt, r0, r1, [&](int ti, int64_t a, int64_t b) {
+    Part& pt = parts[ti];
+    if (a >= b) return;
+    pt.cell0 = a / ncell;
+    pt.tally.assign(((b - 1) / ncell - pt.cell0 + 1) * bpc, 0.0);
+    pt.grad.assign(D->n_mir, 0.0);
+    for (int64_t r = a; r < b; ++r) geo_ray(X, (uint64_t)r, pt.tally.data(), pt.cell0, G, pt.grad.data());
+  });
+  for (auto& pt : parts) {
+    for (size_t i = 0; i < pt.tally.size(); ++i) tally[pt.cell0 * bpc + (int64_t)i] += pt.tally[i];
+    if (grad_omega)
+      for (size_t k = 0; k < pt.grad.size(); ++k) grad_omega[k] += pt.grad[k];
+  }
+  return 0;
+}
+
+// Expected tally of the geometric model for the launches of rays [r0, r1)
+// by deterministic splitting (every reflect/transmit branch, weight-pruned).
+int ora_geo_split(const OraDesign* D, const OraCfg* C, int64_t r0, int64_t r1, int nthreads, double prune,
+                  double* tally) {
+  Params<double> P = params_of(*D);
+  TraceCtx<double> X = make_ctx(*D, *C, P);
+  const int64_t bpc = bins_per_cell(*C), ncell = n_cell_of(*C);
+  std::memset(tally, 0, sizeof(double) * cells_of(*C) * bpc);
+  const int nt = pick_threads(nthreads, r1 - r0);
+  struct Part {
+    std::vector<double> tally;
+    int64_t cell0 = 0;
+  };
+  std::vector<Part> parts(nt);
+  parallel_rays(nt, r0, r1, [&](int ti, int64_t a, int64_t b) {
+    Part& pt = parts[ti];
+    if (a >= b) return;
+    pt.cell0 = a / ncell;
+    pt.tally.assign(((b - 1) / ncell - pt.cell0 + 1) * bpc, 0.0);
+    for (int64_t r = a; r < b; ++r) {
+      Launch<double> L = launch<double>(*D, *C, (uint64_t)r);
+      const int64_t cell = (int64_t)L.lam_i * C->n_fx * C->n_fy + L.f;
+      geo_split_rec(X, pt.tally.data(), pt.cell0, cell, L.p, L.d, 1.0, S_LEFT, 0, prune);
+    }
+  });
+  for (auto& pt : parts)
+    for (size_t i = 0; i < pt.tally.size(); ++i) tally[pt.cell0 * bpc + (int64_t)i] += pt.tally[i];
+  return 0;
+}
+}  // extern "C"
+
 }  // extern "C"

@@ -417,6 +417,24 @@ extern "C" wg_status wg_set_params(wg_design* d, const float* thickness_nm, int6
   return WG_OK;
 }
 
+extern "C" wg_status wg_set_omega(wg_design* d, const float* omega, int32_t n, void* stream) {
+  if (!d || !omega) return fail(WG_EINVAL, "wg_set_omega: NULL design/omega");
+  if (n != d->K) return fail(WG_EINVAL, "wg_set_omega: %d values for %d mirrors", n, d->K);
+  for (int k = 0; k < n; ++k)
+    if (!(omega[k] > 0.0f && omega[k] < 1.0f)) return fail(WG_EINVAL, "wg_set_omega: omega %d outside (0, 1)", k);
+  wg_ctx* c = d->ctx;
+  cudaStream_t s = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(c->mu);
+  CU(cudaSetDevice(c->device));
+  d->omega.assign(omega, omega + n);
+  ++d->geom_version;  // the sampled paths change with omega: the eyebox-ray list is stale
+  d->exit_fp = 0;
+  CU(cudaMemcpyAsync(d->d_mir + 2 * d->K, omega, sizeof(float) * d->K, cudaMemcpyHostToDevice, s));
+  CU(launch_prep_design(d->blob, d->d_mir, d->d_mir + d->K, d->d_mir + 2 * d->K, d->K, d->ic_tilt, d->thick, s));
+  CU(cudaStreamSynchronize(s));  // the caller's omega array may go once this returns
+  return WG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // coating hooks
 // ---------------------------------------------------------------------------
@@ -700,6 +718,51 @@ static wg_status finish_stats(wg_ctx* c, const WsLayout& w, cudaStream_t s, wg_s
 static long long default_chunk(const Plan& p) {
   const long long parts = (p.n_cell + 4095) / 4096;
   return (p.n_cell + parts - 1) / parts;
+}
+
+extern "C" wg_status wg_omega_trace(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, const double* dL_dtally,
+                                    double* tally, double* grad_omega) {
+  if (!c || !d || !tally) return fail(WG_EINVAL, "wg_omega_trace: NULL ctx/design/tally");
+  if (cfg && (cfg->lut_bins || cfg->ray_records)) return fail(WG_EINVAL, "wg_omega_trace: no coating table or records");
+  Plan p;
+  wg_status st = make_plan(d, cfg, 2048, p);
+  if (st != WG_OK) return st;
+  cudaStream_t s = (cudaStream_t)cfg->stream;
+  std::lock_guard<std::mutex> lk(c->mu);
+  CU(cudaSetDevice(c->device));
+  WsLayout w;
+  st = prepare_ws(c, d, cfg, p, s, w);
+  if (st != WG_OK) return st;
+  double* t = tally;
+  const bool dev_t = is_device_ptr(tally);
+  if (!dev_t) CU(cudaMallocAsync((void**)&t, sizeof(double) * p.tally_size, s));
+  CU(cudaMemsetAsync(t, 0, sizeof(double) * p.tally_size, s));
+  const double* G = dL_dtally;
+  if (G && !is_device_ptr(G)) {
+    double* tmp;
+    CU(cudaMallocAsync((void**)&tmp, sizeof(double) * p.tally_size, s));
+    CU(cudaMemcpyAsync(tmp, dL_dtally, sizeof(double) * p.tally_size, cudaMemcpyHostToDevice, s));
+    G = tmp;
+  }
+  double* g = grad_omega;
+  const bool dev_g = grad_omega && is_device_ptr(grad_omega);
+  if (grad_omega && !dev_g) CU(cudaMallocAsync((void**)&g, sizeof(double) * d->K, s));
+  if (g) CU(cudaMemsetAsync(g, 0, sizeof(double) * d->K, s));
+  TraceArgs a = base_args(d, cfg, p, w);
+  a.tally = t;
+  a.G = G;
+  CU(launch_omega_trace(a, G ? g : nullptr, c->sm_count, s));
+  CU(cudaEventRecord(c->ws_free, s));
+  if (!dev_t) {
+    CU(cudaMemcpyAsync(tally, t, sizeof(double) * p.tally_size, cudaMemcpyDeviceToHost, s));
+    CU(cudaFreeAsync(t, s));
+  }
+  if (G && G != dL_dtally) CU(cudaFreeAsync((void*)G, s));
+  if (grad_omega && !dev_g) {
+    CU(cudaMemcpyAsync(grad_omega, g, sizeof(double) * d->K, cudaMemcpyDeviceToHost, s));
+    CU(cudaFreeAsync(g, s));
+  }
+  return finish_stats(c, w, s, nullptr, false);
 }
 
 extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, double* tally,

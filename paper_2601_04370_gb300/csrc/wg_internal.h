@@ -174,6 +174,9 @@ cudaError_t launch_lut_build(const uint8_t* blob, int P, int n_mir, int n_lam, c
                              float dc, float4* out, cudaStream_t s);
 cudaError_t launch_lut_records(const double* grad, int n_mir, int n_lam, const float* lam, int n, float c0, float dc,
                                HitRec* out, cudaStream_t s);
+// reflection-probability pre-optimization: geometric trace of the rays of a
+// (a.tally, a.G; grad_omega [n_mir] FP64 sums, may be null)
+cudaError_t launch_omega_trace(const TraceArgs& a, double* grad_omega, int sm_count, cudaStream_t s);
 // mirror-tilt gradient of the a.n_heads rays a tilt replay recorded, one
 // pass per group of 8 mirrors starting at a.tilt_k0
 cudaError_t launch_tilt_grad(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s);

@@ -1584,6 +1584,119 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Reflection-probability pre-optimization (Methods, "Learned reflection
+// probabilities"): each coating a scalar reflectance equal to its mirror's
+// omega, geometric tracing without polarization. With the sampling
+// probability equal to the reflectance every path has weight one: a ray that
+// reaches the eyebox adds the unpolarized exit transmittance (T_s + T_p) / 2
+// to the tally (a two-field ray with unit s and p amplitudes through
+// face_event), and with G = dL/dtally its score to dL/d omega:
+//   G[bin] I sum over its hits (reflected ? 1/omega_k : -1/(1 - omega_k)).
+// One ray per thread; the gradient is summed per CTA in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kOmegaBlock = 256;
+__global__ void __launch_bounds__(kOmegaBlock) k_omega_trace(const TraceArgs A, double* grad_omega) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ __align__(8) uint64_t s_mbar;
+  __shared__ double s_grad[MAX_MIR];
+  __shared__ unsigned long long s_cnt[3];
+  for (int k = threadIdx.x; k < MAX_MIR; k += blockDim.x) s_grad[k] = 0.0;
+  if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0ull;
+  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;
+  Blob B;
+  B.bind(smem);
+  const BlobHeader& H = *B.h;
+  unsigned long long c_rays = 0, c_hits = 0, c_over = 0;
+  for (long long id = A.ray_begin + blockIdx.x * (long long)blockDim.x + threadIdx.x; id < A.ray_end;
+       id += (long long)gridDim.x * blockDim.x) {
+    const long long cell = id / A.n_cell;
+    const ChunkConst cc = chunk_const(A, cell);
+    Ray<2> R;
+    gen_ray(R, id, cc, H, A);
+    R.a[0] = make_float2(1.f, 0.f);
+    R.b[0] = make_float2(0.f, 0.f);
+    R.a[1] = make_float2(0.f, 0.f);
+    R.b[1] = make_float2(1.f, 0.f);
+    uint8_t hk[TAPE_HITS];  // mirror | 0x80 if reflected, per hit
+    int nh = 0;
+    ++c_rays;
+    for (;;) {
+      float t;
+      const int sid = next_surface(B, R.p, R.d, R.last, R.reg, t);
+      ++R.ev;
+      if (sid < 0) break;
+      R.p = v3(fmaf(t, R.d.x, R.p.x), fmaf(t, R.d.y, R.p.y), fmaf(t, R.d.z, R.p.z));
+      R.last = sid;
+      if (sid >= S_MIR) {
+        const int k = sid - S_MIR;
+        const MirrorRec& M = B.mir[k];
+        const float cd = fmaf(R.d.x, M.nx, R.d.z * M.nz);
+        const int m = R.hits;
+        const uint4 rnd = philox10(
+            make_uint4((uint32_t)R.id, (uint32_t)((unsigned long long)R.id >> 32), (uint32_t)(m >> 2), TAG_EVT),
+            A.key0, A.key1);
+        const uint32_t word = (m & 3) == 0 ? rnd.x : (m & 3) == 1 ? rnd.y : (m & 3) == 2 ? rnd.z : rnd.w;
+        const bool refl = u24(word) < M.omega;
+        if (refl) R.d = v3(fmaf(-2.0f * cd, M.nx, R.d.x), R.d.y, fmaf(-2.0f * cd, M.nz, R.d.z));
+        R.reg = region_after(B, R.reg, k, R.d);
+        R.hits = m + 1;
+        if (nh < TAPE_HITS) hk[nh] = (uint8_t)(k | (refl ? 0x80 : 0));
+        ++nh;
+        if (R.ev >= A.max_events) break;
+        continue;
+      }
+      int dummy = 0;
+      const Outcome o = face_event<2>(R, sid, H, A, nullptr, nullptr, dummy);
+      if (!o.term) {
+        if (R.ev >= A.max_events) break;
+        continue;
+      }
+      if (o.cat == L_EYEBOX) {
+        const long long flat = cell * A.bins + o.bin;
+        atomicAdd(A.tally + flat, (double)o.I);
+        if (grad_omega && A.G) {
+          const double g = A.G[flat] * (double)o.I;
+          if (nh > TAPE_HITS) {
+            ++c_over;  // more hits than the list holds: no gradient from this ray
+          } else if (g != 0.0) {
+            for (int h = 0; h < nh; ++h) {
+              const int k = hk[h] & 0x7f;
+              const double w = (double)B.mir[k].omega;
+              atomicAdd(&s_grad[k], (hk[h] & 0x80) ? g / w : -g / (1.0 - w));
+            }
+          }
+        }
+      }
+      break;
+    }
+    c_hits += R.hits;
+  }
+  const unsigned long long cv[3] = {c_rays, c_hits, c_over};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const unsigned long long v = warp_sum_u(cv[i]);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(&s_cnt[i], v);
+  }
+  __syncthreads();
+  if (grad_omega)
+    for (int k = threadIdx.x; k < H.n_mir; k += blockDim.x)
+      if (s_grad[k] != 0.0) atomicAdd(grad_omega + k, s_grad[k]);
+  if (threadIdx.x == 0 && s_cnt[0]) atomicAdd(A.counters + 0, s_cnt[0]);
+  if (threadIdx.x == 1 && s_cnt[1]) atomicAdd(A.counters + 1, s_cnt[1]);
+  if (threadIdx.x == 2 && s_cnt[2]) atomicAdd(A.counters + 5, s_cnt[2]);
+}
+
+cudaError_t launch_omega_trace(const TraceArgs& a, double* grad_omega, int sm_count, cudaStream_t s) {
+  const long long n = a.ray_end - a.ray_begin;
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::max<long long>(1, std::min<long long>((n + kOmegaBlock - 1) / kOmegaBlock, 8ll * sm_count));
+  cudaFuncSetAttribute(k_omega_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, a.blob_bytes);
+  note_launches(1);
+  k_omega_trace<<<grid, kOmegaBlock, a.blob_bytes, s>>>(a, grad_omega);
+  return cudaGetLastError();
+}
+
 size_t tilt_smem_bytes(int blob_bytes, int F) {
   return (size_t)blob_bytes + sizeof(double) * (size_t)(kTiltBlock / 32) * kTiltPass * 32 +
          sizeof(float) * (size_t)(kTiltBlock / 32) * kTiltPass * (3 + 4 * F) * 32;

@@ -1,9 +1,12 @@
 """Thickness optimization of a synthetic design (Results, "Evaluation"):
 
-  python -m paper_2601_04370_gb300.optimize --design representative --rays 1000000 --iters 300
+  python -m paper_2601_04370_gb300.optimize --design representative --rays 1000000 --iters 300 [--omega-iters 60]
 
-Starts from thicknesses drawn from a Gaussian at the midpoint of the 20-200 nm
-bounds, then iterates forward trace, loss (Eq. 1), adjoint and the projected
+With --omega-iters, the reflection probabilities are pre-optimized first
+(Methods, "Learned reflection probabilities": scalar-reflectance geometric
+model, throughput to the pupils). Starts from thicknesses drawn from a
+Gaussian at the midpoint of the 20-200 nm bounds, then iterates forward
+trace, loss (Eq. 1), adjoint and the projected
 Adam step (layers can be eliminated through the soft gap 0-20 nm). Prints the
 loss terms every `--every` iterations and, at the end, the eyebox throughput,
 the CVs and how many layers were driven to zero thickness. The Philox keys
@@ -25,6 +28,8 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=2.0)
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--every", type=int, default=50)
+    ap.add_argument("--omega-iters", type=int, default=0)
+    ap.add_argument("--omega-lr", type=float, default=0.03)
     args = ap.parse_args(argv)
     import numpy as np
 
@@ -38,6 +43,11 @@ def main(argv=None):
     D = W.with_thickness(D, W.gaussian_thickness(D, seed=args.seed))
     ctx = wg.Context(0)
     dh = ctx.create_design(D)
+    omega = None
+    if args.omega_iters > 0:
+        oh, om = wg.optimize_omega(ctx, dh, C, args.omega_iters, lr=args.omega_lr)
+        omega = {"I_mean_start": float(oh[0]), "I_mean_end": float(oh[-1]), "omega": [float(x) for x in om]}
+        print(json.dumps({"omega_preopt": omega}), flush=True)
     adam = wg.Adam(dh, lr_nm=args.lr)
 
     def report(it, h, a):
@@ -49,7 +59,7 @@ def main(argv=None):
     wall = time.perf_counter() - t0
     th = adam.params()
     live = np.asarray(D.pruned) == 0
-    out = {"design": args.design, "rays": args.rays, "iters": args.iters, "wall_s": wall,
+    out = {"design": args.design, "rays": args.rays, "iters": args.iters, "wall_s": wall, "omega_preopt": omega,
            "start": dict(zip(("loss", "I_mean", "cv_fov", "cv_eyebox"), map(float, hist[0]))),
            "end": dict(zip(("loss", "I_mean", "cv_fov", "cv_eyebox"), map(float, hist[-1]))),
            "layers": int(live.sum()), "driven_to_zero": int(((th == 0.0) & live).sum()),

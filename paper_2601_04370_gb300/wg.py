@@ -130,6 +130,8 @@ def lib():
         L.wg_poll.argtypes = [vp, C.c_uint64, i64, C.POINTER(Result)]
         L.wg_cancel.argtypes = [vp, C.c_uint64]
         L.wg_autotune.argtypes = [vp, vp, C.POINTER(TraceCfg)]
+        L.wg_omega_trace.argtypes = [vp, vp, C.POINTER(TraceCfg), vp, vp, vp]
+        L.wg_set_omega.argtypes = [vp, vp, i32, vp]
         L.wg_adam_create.argtypes = [vp, C.POINTER(AdamOpts), vp, C.POINTER(vp)]
         L.wg_adam_step.argtypes = [vp, vp, vp]
         L.wg_adam_params.argtypes = [vp, vp, vp]
@@ -253,11 +255,45 @@ def optimize(ctx, dh, cfg, n_iter, adam=None, loss_kind=0, w_f=10.0, w_e=3.0, ca
     return np.array(hist), adam
 
 
+def optimize_omega(ctx, dh, cfg, n_iter, lr=0.02, lo=0.02, hi=0.98, beta1=0.9, beta2=0.999, eps=1e-8):
+    """Reflection-probability pre-optimization (Methods, "Learned reflection
+    probabilities"): maximizes the mean pupil throughput I_mean (the
+    brightness term of Eq. 1) of the scalar-reflectance geometric model over
+    the mirrors' omega. Each iteration traces cfg's rays (wg_omega_trace,
+    fixed Philox keys), takes the score-function gradient and one Adam step
+    on the K values (here on the host), clipped to [lo, hi], and sets omega.
+    Returns the per-iteration I_mean and the final omega."""
+    import torch
+    tally = torch.zeros(cfg.tally_shape, dtype=torch.float64, device="cuda")
+    G = torch.zeros_like(tally)
+    ctx.loss(dh, cfg, tally, G, w_f=0.0, w_e=0.0)  # dL/dtally of L = -I_mean: the pupil masks, any tally
+    om = np.asarray(dh.design.mirror_omega, dtype=np.float64).copy()
+    m = np.zeros_like(om)
+    v = np.zeros_like(om)
+    g = np.zeros_like(om)
+    hist = []
+    for t in range(1, n_iter + 1):
+        ctx.omega_trace(dh, cfg, tally, G, g)
+        hist.append(ctx.loss(dh, cfg, tally, w_f=0.0, w_e=0.0)[1])
+        m = beta1 * m + (1.0 - beta1) * g
+        v = beta2 * v + (1.0 - beta2) * g * g
+        om = np.clip(om - lr * (m / (1.0 - beta1 ** t)) / (np.sqrt(v / (1.0 - beta2 ** t)) + eps), lo, hi)
+        dh.set_omega(om)
+    ctx.omega_trace(dh, cfg, tally)
+    hist.append(ctx.loss(dh, cfg, tally, w_f=0.0, w_e=0.0)[1])
+    return np.array(hist), om.astype(np.float32)
+
+
 class DesignHandle:
     def __init__(self, ctx, handle, design):
         self.ctx = ctx
         self.h = handle
         self.design = design
+
+    def set_omega(self, omega, stream=None):
+        """wg_set_omega: the mirrors' reflection probabilities ([K], each in (0, 1))."""
+        a = np.ascontiguousarray(np.asarray(omega, dtype=np.float32))
+        _check(lib().wg_set_omega(self.h, a.ctypes.data, int(a.size), stream if stream is not None else _current_stream()))
 
     @property
     def n_params(self):
@@ -393,6 +429,13 @@ class Context:
         _check(lib().wg_trace_backward(self.h, dh.h, C.byref(h.c), _ptr(dL_dtally), _ptr(grad_thickness),
                                        _ptr(grad_tilt), C.byref(st) if stats else None))
         return st.to_dict() if stats else None
+
+    def omega_trace(self, dh, cfg, tally, dL_dtally=None, grad_omega=None, stream=None):
+        """wg_omega_trace: the reflection-probability model's geometric trace
+        (scalar reflectance = omega, no polarization): tally, and with
+        dL_dtally the score-function dL/d omega into grad_omega ([K] FP64)."""
+        h = _CfgHolder(cfg, stream if stream is not None else _current_stream())
+        _check(lib().wg_omega_trace(self.h, dh.h, C.byref(h.c), _ptr(dL_dtally), _ptr(tally), _ptr(grad_omega)))
 
     def loss(self, dh, cfg, tally, dL_dtally=None, kind=0, w_f=10.0, w_e=3.0, stream=None):
         """Returns (L, I_mean, U_fov, U_eyebox); fills dL_dtally if given."""
