@@ -1207,7 +1207,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   const bool tilt = grad_tilt != nullptr;
   const size_t acc_bytes = (sizeof(double) * std::max(1, d->n_dev) + 15) & ~(size_t)15;
   const size_t aux_bytes =
-      tilt ? (size_t)cap * (sizeof(TiltAux) + sizeof(unsigned int)) + (size_t)batch * sizeof(RayHead) : 0;
+      tilt ? (size_t)cap * (sizeof(TiltAux) + sizeof(unsigned int)) + 2 * (size_t)batch * sizeof(RayHead) + 512 : 0;
   // coating table: FP64 dL/dc per entry and the second stage's records
   const bool use_lut = cfg->lut_bins > 0;
   const long long n_lut = use_lut ? lut_entries(d, cfg) : 0;
@@ -1232,6 +1232,13 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     tilt_aux = (TiltAux*)(bw + 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + acc_bytes);
     heads = (RayHead*)((uint8_t*)tilt_aux + (size_t)cap * sizeof(TiltAux));
     perm = (unsigned int*)((uint8_t*)heads + (size_t)batch * sizeof(RayHead));
+  }
+  // the heads sorted by hit count for the tangent pass, and the sort's counters
+  RayHead* heads_sorted = nullptr;
+  unsigned int* head_keys = nullptr;
+  if (tilt) {
+    heads_sorted = (RayHead*)((uint8_t*)perm + (size_t)cap * sizeof(unsigned int));
+    head_keys = (unsigned int*)((uint8_t*)heads_sorted + (size_t)batch * sizeof(RayHead));
   }
   double* lut_grad = nullptr;
   HitRec* lut_recs = nullptr;
@@ -1359,8 +1366,10 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     }
     if (stats) CU(cudaEventRecord(c->kev[3], s));
     const long long n_heads = std::min<long long>((long long)counts[1], b1 - b0);
+    if (tilt && n_heads > 0) CU(launch_heads_sort(heads, n_heads, head_keys, heads_sorted, s));
     for (int k0 = 0; tilt && n_heads > 0 && k0 < d->K; k0 += 8) {
       TraceArgs at = a;
+      at.ray_heads = heads_sorted;
       at.n_heads = n_heads;
       at.grad_tilt = gt;
       at.tilt_k0 = k0;

@@ -174,6 +174,8 @@ cudaError_t launch_lut_build(const uint8_t* blob, int P, int n_mir, int n_lam, c
                              float dc, float4* out, cudaStream_t s);
 cudaError_t launch_lut_records(const double* grad, int n_mir, int n_lam, const float* lam, int n, float c0, float dc,
                                HitRec* out, cudaStream_t s);
+// ray heads grouped by their mirror-hit count (cnt: device [65] scratch)
+cudaError_t launch_heads_sort(const RayHead* in, long long n, unsigned int* cnt, RayHead* out, cudaStream_t s);
 // reflection-probability pre-optimization: geometric trace of the rays of a
 // (a.tally, a.G; grad_omega [n_mir] FP64 sums, may be null)
 cudaError_t launch_omega_trace(const TraceArgs& a, double* grad_omega, int sm_count, cudaStream_t s);
