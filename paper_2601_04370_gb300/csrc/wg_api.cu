@@ -83,6 +83,7 @@ struct wg_ctx {
   std::vector<wg_design*> designs;
   DevBuf fws;     // fused-forward workspace (per-job heads, configuration arrays, job table)
   DevBuf lut;     // coating look-up table of the last call that asked for one
+  DevBuf lsort;   // the eyebox-ray list grouped by hit count, for the replay
   void* serve = nullptr;  // serving runtime state (wg_serve.cu)
 };
 
@@ -1294,6 +1295,17 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   }
   const ExitRec* list =
       use_list ? reinterpret_cast<const ExitRec*>(static_cast<const uint8_t*>(d->exits.p) + kExitHead) : nullptr;
+  if (use_list && n_list > 0) {
+    // rays grouped by their hit count: a replay warp then gets rays of equal length
+    const size_t lb = 512 + sizeof(ExitRec) * (size_t)n_list;
+    if (lb > c->lsort.n) {
+      CU(cudaEventSynchronize(c->ws_free));
+      CU(c->lsort.ensure(lb));
+    }
+    ExitRec* sorted = reinterpret_cast<ExitRec*>(static_cast<uint8_t*>(c->lsort.p) + 512);
+    CU(launch_exits_sort(list, n_list, static_cast<unsigned int*>(c->lsort.p), sorted, s));
+    list = sorted;
+  }
   const long long w_begin = use_list ? 0 : p.rb, w_end = use_list ? n_list : p.re;
   float ms_total = 0.f, ms_replay = 0.f, ms_adjoint = 0.f, ms_tilt = 0.f;
   int n_adj_launches = 0;

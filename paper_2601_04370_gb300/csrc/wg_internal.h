@@ -13,8 +13,8 @@ struct HitRec;
 // non-zero dL/dtally (every other ray contributes no gradient).
 struct ExitRec {
   long long id;
-  int flat;
-  int pad;
+  int flat;  // flat tally index; -1: an unused slot (hole)
+  int pad;   // the ray's mirror hits (the backward groups rays by it)
 };
 
 // Per hit record of a replay that also serves the tilt gradient: the applied
@@ -174,8 +174,9 @@ cudaError_t launch_lut_build(const uint8_t* blob, int P, int n_mir, int n_lam, c
                              float dc, float4* out, cudaStream_t s);
 cudaError_t launch_lut_records(const double* grad, int n_mir, int n_lam, const float* lam, int n, float c0, float dc,
                                HitRec* out, cudaStream_t s);
-// ray heads grouped by their mirror-hit count (cnt: device [65] scratch)
+// ray heads / listed eyebox rays grouped by their mirror-hit count (cnt: device [65] scratch)
 cudaError_t launch_heads_sort(const RayHead* in, long long n, unsigned int* cnt, RayHead* out, cudaStream_t s);
+cudaError_t launch_exits_sort(const ExitRec* in, long long n, unsigned int* cnt, ExitRec* out, cudaStream_t s);
 // reflection-probability pre-optimization: geometric trace of the rays of a
 // (a.tally, a.G; grad_omega [n_mir] FP64 sums, may be null)
 cudaError_t launch_omega_trace(const TraceArgs& a, double* grad_omega, int sm_count, cudaStream_t s);

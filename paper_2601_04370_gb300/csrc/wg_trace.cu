@@ -903,7 +903,7 @@ __global__ void __launch_bounds__(kBlock, 2)
               ExitRec e;
               e.id = R.id;
               e.flat = (int)(S.slot[slot].cell * A.bins + pend_bin);
-              e.pad = 0;
+              e.pad = R.hits;  // the backward sorts the list by it
               A.exit_list[i] = e;
             }
           }
@@ -1697,60 +1697,73 @@ cudaError_t launch_omega_trace(const TraceArgs& a, double* grad_omega, int sm_co
   return cudaGetLastError();
 }
 
-// Ray heads grouped by their number of mirror hits (a counting sort over
-// 1..TAPE_HITS): a warp of the tangent pass then re-traces rays of equal
-// length instead of waiting for its longest one.
-constexpr int kHeadKeys = TAPE_HITS + 1;
-__global__ void k_heads_count(const RayHead* h, long long n, unsigned int* cnt) {
-  __shared__ unsigned int s[kHeadKeys];
-  for (int i = threadIdx.x; i < kHeadKeys; i += blockDim.x) s[i] = 0u;
+// Records grouped by the number of mirror hits of their ray (a counting sort
+// over 0..TAPE_HITS): the replay and the tangent pass then give each warp rays
+// of equal length instead of waiting for its longest one. Keys: a ray head's
+// emit, a listed eyebox ray's hit count (ExitRec::pad; holes go first).
+constexpr int kHitKeys = TAPE_HITS + 1;
+__device__ __forceinline__ int hit_key(const RayHead& r) { return min(max(r.emit, 0), TAPE_HITS); }
+__device__ __forceinline__ int hit_key(const ExitRec& r) { return r.flat < 0 ? 0 : min(max(r.pad, 0), TAPE_HITS); }
+
+template <class R>
+__global__ void k_hits_count(const R* in, long long n, unsigned int* cnt) {
+  __shared__ unsigned int s[kHitKeys];
+  for (int i = threadIdx.x; i < kHitKeys; i += blockDim.x) s[i] = 0u;
   __syncthreads();
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    atomicAdd(&s[min(max(h[i].emit, 0), TAPE_HITS)], 1u);
+    atomicAdd(&s[hit_key(in[i])], 1u);
   __syncthreads();
-  for (int i = threadIdx.x; i < kHeadKeys; i += blockDim.x)
+  for (int i = threadIdx.x; i < kHitKeys; i += blockDim.x)
     if (s[i]) atomicAdd(cnt + i, s[i]);
 }
 // counts -> exclusive offsets, in place (one thread)
-__global__ void k_heads_offsets(unsigned int* cnt) {
+__global__ void k_hits_offsets(unsigned int* cnt) {
   unsigned int run = 0;
-  for (int i = 0; i < kHeadKeys; ++i) {
+  for (int i = 0; i < kHitKeys; ++i) {
     const unsigned int c = cnt[i];
     cnt[i] = run;
     run += c;
   }
 }
-// each block ranks its heads per key in shared memory and reserves one
+// each block ranks its records per key in shared memory and reserves one
 // range per key from the global cursors
-__global__ void k_heads_scatter(const RayHead* in, long long n, unsigned int* cursor, RayHead* out) {
-  __shared__ unsigned int s_cnt[kHeadKeys], s_base[kHeadKeys];
-  for (int i = threadIdx.x; i < kHeadKeys; i += blockDim.x) s_cnt[i] = 0u;
+template <class R>
+__global__ void k_hits_scatter(const R* in, long long n, unsigned int* cursor, R* out) {
+  __shared__ unsigned int s_cnt[kHitKeys], s_base[kHitKeys];
+  for (int i = threadIdx.x; i < kHitKeys; i += blockDim.x) s_cnt[i] = 0u;
   __syncthreads();
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  RayHead r;
+  R r;
   int key = -1;
   unsigned int rank = 0;
   if (i < n) {
     r = in[i];
-    key = min(max(r.emit, 0), TAPE_HITS);
+    key = hit_key(r);
     rank = atomicAdd(&s_cnt[key], 1u);
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < kHeadKeys; k += blockDim.x)
+  for (int k = threadIdx.x; k < kHitKeys; k += blockDim.x)
     if (s_cnt[k]) s_base[k] = atomicAdd(cursor + k, s_cnt[k]);
   __syncthreads();
   if (key >= 0) out[s_base[key] + rank] = r;
 }
 
-cudaError_t launch_heads_sort(const RayHead* in, long long n, unsigned int* cnt, RayHead* out, cudaStream_t s) {
+template <class R>
+static cudaError_t hits_sort(const R* in, long long n, unsigned int* cnt, R* out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * kHeadKeys, s);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(unsigned int) * kHitKeys, s);
   if (e != cudaSuccess) return e;
   note_launches(3);
-  k_heads_count<<<(unsigned)std::min<long long>((n + 255) / 256, 1024), 256, 0, s>>>(in, n, cnt);
-  k_heads_offsets<<<1, 1, 0, s>>>(cnt);
-  k_heads_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, n, cnt, out);
+  k_hits_count<R><<<(unsigned)std::min<long long>((n + 255) / 256, 1024), 256, 0, s>>>(in, n, cnt);
+  k_hits_offsets<<<1, 1, 0, s>>>(cnt);
+  k_hits_scatter<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, n, cnt, out);
   return cudaGetLastError();
+}
+cudaError_t launch_heads_sort(const RayHead* in, long long n, unsigned int* cnt, RayHead* out, cudaStream_t s) {
+  return hits_sort(in, n, cnt, out, s);
+}
+cudaError_t launch_exits_sort(const ExitRec* in, long long n, unsigned int* cnt, ExitRec* out, cudaStream_t s) {
+  return hits_sort(in, n, cnt, out, s);
 }
 
 size_t tilt_smem_bytes(int blob_bytes, int F) {
