@@ -32,12 +32,14 @@ UNIT = "interactions/s"
 # the s and p 2x2 chain) plus 250 per hit for the coefficients, bases, Jones
 # update and geometry. The thin-film adjoint costs about three forward layer
 # chains per layer of each record (forward sweep, recomputation, reverse
-# sweep with the layer gradients); with the mirror-tilt gradient its first
-# sweep also carries the derivative chain (one more chain per layer).
+# sweep with the layer gradients); with the mirror-tilt gradient the reverse
+# sweep also forms d/d(cos theta_0) of each record: per layer the row's two
+# products with the next substrate-side vector for each polarization and the
+# rho-weighted sums, 29 flops.
 FLOPS_PER_LAYER = 33
 FLOPS_PER_HIT = 250
 FLOPS_ADJ_LAYER = 3 * FLOPS_PER_LAYER
-FLOPS_ADJ_LAYER_TILT = 4 * FLOPS_PER_LAYER
+FLOPS_ADJ_LAYER_TILT = 3 * FLOPS_PER_LAYER + 29
 L2_FLUSH_BYTES = 256 << 20
 
 

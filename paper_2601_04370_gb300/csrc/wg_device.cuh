@@ -622,24 +622,67 @@ __host__ __device__ constexpr int seg_floats_per_warp() {
   return Seg<P>::CKP * kSegWords * 32;
 }
 
-// v and its derivative kept below 2^32 by the same exact power of two
-__device__ __forceinline__ void cv_rescale32_d(CV& v, CV& dv, int& e) {
-  if (fmaxf(cv_maxabs(v), cv_maxabs(dv)) > TWO_P32) {
-    v = CV{v.xr * TWO_M32, v.xi * TWO_M32, v.yr * TWO_M32, v.yi * TWO_M32};
-    dv = CV{dv.xr * TWO_M32, dv.xi * TWO_M32, dv.yr * TWO_M32, dv.yi * TWO_M32};
+// rho = d ln(cos t)/d(cos t0) of each material for the reverse sweep's
+// tilt terms (cos t = sqrt(rad), or a for cos t = -i a; both give
+// r2 cos0 / rad). A layer's phase rate and its four quotients all scale
+// with it: d(kap)/dcos = rho kap, dq21s = rho q21s, dq12s = -rho q12s,
+// dq12p = rho q12p, dq21p = -rho q21p.
+struct TiltTable {
+  float rho[MAX_MAT];
+  __device__ __forceinline__ void init(const BlobHeader& h, float cos0) {
+    const float sin2 = fmaf(-cos0, cos0, 1.0f);
+#pragma unroll
+    for (int i = 0; i < MAX_MAT; ++i) {
+      const float rad = fmaf(-h.mat_r2[i], sin2, 1.0f);
+      const float q = copysignf(fmaxf(fabsf(rad), 1e-30f), rad);
+      rho[i] = i < h.n_mat ? h.mat_r2[i] * cos0 / q : 0.0f;
+    }
+  }
+  __device__ __forceinline__ float get(int m) const {
+    float r = rho[0];
+    if (m == 1) r = rho[1];
+    if (m == 2) r = rho[2];
+    if (m == 3) r = rho[3];
+    return r;
+  }
+};
+
+// 2 Re(A dc/d(eta0)) at fixed (B, C) for one polarization: r = (eta0 B - C)/den
+// gives 2 B C / den^2, t = 2 eta0 2^-e / den gives 2 C 2^-e / den^2
+// (den = eta0 B + C on the scaled vector; A already carries the r_p sign).
+__device__ __forceinline__ float coef_deta(const CV& v, float eta0, int e, float2 A, int which) {
+  const float2 B = make_float2(v.xr, v.xi), C = make_float2(v.yr, v.yi);
+  const float2 den = make_float2(fmaf(eta0, B.x, C.x), fmaf(eta0, B.y, C.y));
+  const float2 cd = cdiv_s(C, den);
+  const float2 x = which == 0 ? cmul(cdiv_s(B, den), cd) : cscale(cdiv_s(cd, den), pow2i(-e));
+  return 4.0f * fmaf(A.x, x.x, -A.y * x.y);
+}
+
+// the row's guard, first folding the tilt partial sum kept at its exponent
+__device__ __forceinline__ void row_guard_fold(CRow& a, int& e, float& acc, float& g, int e_off) {
+  if (row_maxabs(a) > TWO_P32) {
+    g = fmaf(-2.0f, scale2(acc, e + e_off), g);
+    acc = 0.0f;
+    a.a0 = cscale(a.a0, TWO_M32);
+    a.a1 = cscale(a.a1, TWO_M32);
     e += 32;
   }
 }
 
 // seg: this lane's column of its warp's segment buffer (element (u, w) at
 // seg[(u * kSegWords + w) * 32]; the 32 lanes' columns interleave).
-// DUAL: sweep 1 also carries d/d(cos t0) of the substrate-side vectors (the
-// constants' derivatives from mtd) and *g_cos receives df/d(cos t0) of the
-// record through its coating, 2 Re(A_s dc_s + A_p dc_p), without 2^eA.
+// DUAL: *g_cos also receives df/d(cos t0) of the record through its coating,
+// without 2^eA, from the same reverse sweep (reverse-mode, no derivative
+// chain): with v_j = M_j v_{j+1} (substrate side) and the row a_j,
+//   df/dcos = 2 Re[ A dc/d(eta0) deta0 + sum_j a_j dM_j/dcos v_{j+1} + a_L (0, deta0)^T ],
+// where M = c I + s K(q) gives a dM/dcos v_{j+1} = dphi a K v_j (the
+// thickness term's product, times dphi/dcos) + s a dK(dq) v_{j+1} (the same
+// two products on v_{j+1} with the quotients' derivatives); both scale with
+// the material's rho (tt).
 template <int P, class Sink, bool DUAL = false>
 __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, const MatTable& mt, float n0,
                                             float cos0, float2 A_s, float2 A_p, int which, Sink& sink,
-                                            float* seg, int eA = 0, const MatTableD* mtd = nullptr,
+                                            float* seg, int eA = 0, const TiltTable* tt = nullptr,
                                             float* g_cos = nullptr) {
   // (A_s, A_p) * 2^eA are the weights; eA carries the range of dL/dtally
   constexpr int CKP = Seg<P>::CKP;
@@ -652,108 +695,8 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
   CV vs{1.0f, 0.0f, eta_s, 0.0f}, vp{1.0f, 0.0f, eta_p, 0.0f};
   int es = 0, ep = 0;
   ck[nseg] = Ckpt{vs, vp, 0, 0};
-  if constexpr (DUAL) {
-    const float deta_s = n0, deta_p = -eta_p / cos0;
-    CV dvs{0.0f, 0.0f, deta_s, 0.0f}, dvp{0.0f, 0.0f, deta_p, 0.0f};
-    MatKD kbd[Seg<P>::NSLOT];
-    if constexpr (P > 0) {
-#pragma unroll
-      for (int v = 0; v < P; ++v) {
-        int r = front ? v : (((st.L - 1 - v) % P) + P) % P;
-        r = r < st.L ? r : 0;
-        kbd[v] = mtd->get(st.m[st.off + r]);
-      }
-    }
-    for (int sg = nseg - 1; sg >= 0; --sg) {
-      const int j0 = sg * CKP;
-#pragma unroll
-      for (int u = CKP - 1; u >= 0; --u) {
-        const int j = j0 + u;
-        if (j < L) {
-          const int i = st.idx(front, j);
-          MatK k;
-          MatKD kd;
-          if constexpr (P > 0) {
-            k = kb[u % P];
-            kd = kbd[u % P];
-          } else {
-            const int m = st.m[i];
-            k = mt.get(m);
-            kd = mtd->get(m);
-          }
-          const float dthk = st.d[i];
-          float c, s, dc, ds;
-          layer_cs(k, dthk, c, s);
-          if (!k.evan) {
-            const float dth = TWO_PI * dthk * kd.dkt;  // d(phase)
-            dc = -s * dth;
-            ds = c * dth;
-          } else {
-            const float dx = dthk * kd.dkt;
-            dc = s * dx;
-            ds = c * dx;
-          }
-          cv_step_d(vs, dvs, c, s * k.q12s, s * k.q21s, dc, fmaf(ds, k.q12s, s * kd.dq12s),
-                    fmaf(ds, k.q21s, s * kd.dq21s));
-          cv_step_d(vp, dvp, c, s * k.q12p, s * k.q21p, dc, fmaf(ds, k.q12p, s * kd.dq12p),
-                    fmaf(ds, k.q21p, s * kd.dq21p));
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        cv_rescale32_d(vs, dvs, es);
-        cv_rescale32_d(vp, dvp, ep);
-      }
-      ck[sg] = Ckpt{vs, vp, es, ep};
-    }
-    float2 rs, ts, drs, dts, rpm, tp, drpm, dtp;
-    coef_from_v_d(vs, dvs, eta_s, deta_s, es, rs, ts, drs, dts);
-    coef_from_v_d(vp, dvp, eta_p, deta_p, ep, rpm, tp, drpm, dtp);
-    // paper convention r_p = -r_p(Abeles)
-    const float2 dcs = which == 0 ? drs : dts;
-    const float2 dcp = which == 0 ? make_float2(-drpm.x, -drpm.y) : dtp;
-    *g_cos = 2.0f * (fmaf(A_s.x, dcs.x, -A_s.y * dcs.y) + fmaf(A_p.x, dcp.x, -A_p.y * dcp.y));
-  } else {
-    for (int sg = nseg - 1; sg >= 0; --sg) {
-      const int j0 = sg * CKP;
-#pragma unroll
-      for (int u = CKP - 1; u >= 0; --u) {
-        const int j = j0 + u;
-        if (j < L) {
-          const int i = st.idx(front, j);
-          MatK k;
-          if constexpr (P > 0) {
-            k = kb[u % P];
-          } else {
-            k = mt.get(st.m[i]);
-          }
-          float c, s;
-          layer_cs(k, st.d[i], c, s);
-          cv_step(vs, c, s * k.q12s, s * k.q21s);
-          cv_step(vp, c, s * k.q12p, s * k.q21p);
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        cv_rescale32(vs, es);
-        cv_rescale32(vp, ep);
-      }
-      ck[sg] = Ckpt{vs, vp, es, ep};
-    }
-  }
-  // paper convention r_p = -r_p(Abeles): flip A_p for reflection
-  const float2 Ap = which == 0 ? make_float2(-A_p.x, -A_p.y) : A_p;
-  int eas, eap;
-  CRow as = coef_row(vs, eta_s, es, A_s, which, eas);
-  CRow ap = coef_row(vp, eta_p, ep, Ap, which, eap);
-  eas += eA;
-  eap += eA;
-  for (int sg = 0; sg < nseg; ++sg) {
+  for (int sg = nseg - 1; sg >= 0; --sg) {
     const int j0 = sg * CKP;
-    const Ckpt c1 = ck[sg + 1];
-    CV ws = c1.s, wp = c1.p;
-    // the segment's substrate-side vectors and (c, s), recomputed from the
-    // checkpoint at its far end and kept in this lane's shared-memory column
 #pragma unroll
     for (int u = CKP - 1; u >= 0; --u) {
       const int j = j0 + u;
@@ -767,47 +710,141 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         }
         float c, s;
         layer_cs(k, st.d[i], c, s);
-        cv_step(ws, c, s * k.q12s, s * k.q21s);
-        cv_step(wp, c, s * k.q12p, s * k.q21p);
-        float* b = seg + u * kSegWords * 32;
-        b[0 * 32] = ws.xr;
-        b[1 * 32] = ws.xi;
-        b[2 * 32] = ws.yr;
-        b[3 * 32] = ws.yi;
-        b[4 * 32] = wp.xr;
-        b[5 * 32] = wp.xi;
-        b[6 * 32] = wp.yr;
-        b[7 * 32] = wp.yi;
-        b[8 * 32] = c;
-        b[9 * 32] = s;
+        cv_step(vs, c, s * k.q12s, s * k.q21s);
+        cv_step(vp, c, s * k.q12p, s * k.q21p);
       }
     }
 #pragma unroll
-    for (int u = 0; u < CKP; ++u) {
+    for (int t = 0; t < 3; ++t) {
+      cv_rescale32(vs, es);
+      cv_rescale32(vp, ep);
+    }
+    ck[sg] = Ckpt{vs, vp, es, ep};
+  }
+  // paper convention r_p = -r_p(Abeles): flip A_p for reflection
+  const float2 Ap = which == 0 ? make_float2(-A_p.x, -A_p.y) : A_p;
+  int eas, eap;
+  CRow as = coef_row(vs, eta_s, es, A_s, which, eas);
+  CRow ap = coef_row(vp, eta_p, ep, Ap, which, eap);
+  const float deta_s = n0, deta_p = -eta_p / cos0;
+  float gc = 0.0f, acc_s = 0.0f, acc_p = 0.0f;
+  float rb[Seg<P>::NSLOT];
+  if constexpr (DUAL) {
+    gc = fmaf(deta_s, coef_deta(vs, eta_s, es, A_s, which), deta_p * coef_deta(vp, eta_p, ep, Ap, which));
+    if constexpr (P > 0) {
+#pragma unroll
+      for (int v = 0; v < P; ++v) {
+        int r = front ? v : (((st.L - 1 - v) % P) + P) % P;
+        r = r < st.L ? r : 0;
+        rb[v] = tt->get(st.m[st.off + r]);
+      }
+    }
+  }
+  eas += eA;
+  eap += eA;
+  for (int sg = 0; sg < nseg; ++sg) {
+    const int j0 = sg * CKP;
+    const Ckpt c1 = ck[sg + 1];
+    CV ws = c1.s, wp = c1.p;
+    // the segment's substrate-side vectors and (c, s), recomputed from the
+    // checkpoint at its far end and kept in this lane's shared-memory column
+    // (slots past the stack's end hold the checkpoint itself, v_L)
+#pragma unroll
+    for (int u = CKP - 1; u >= 0; --u) {
       const int j = j0 + u;
+      float c = 1.0f, s = 0.0f;
       if (j < L) {
+        const int i = st.idx(front, j);
         MatK k;
         if constexpr (P > 0) {
           k = kb[u % P];
         } else {
-          k = mt.get(st.m[st.idx(front, j)]);
+          k = mt.get(st.m[i]);
+        }
+        layer_cs(k, st.d[i], c, s);
+        cv_step(ws, c, s * k.q12s, s * k.q21s);
+        cv_step(wp, c, s * k.q12p, s * k.q21p);
+      }
+      float* b = seg + u * kSegWords * 32;
+      b[0 * 32] = ws.xr;
+      b[1 * 32] = ws.xi;
+      b[2 * 32] = ws.yr;
+      b[3 * 32] = ws.yi;
+      b[4 * 32] = wp.xr;
+      b[5 * 32] = wp.xi;
+      b[6 * 32] = wp.yr;
+      b[7 * 32] = wp.yi;
+      b[8 * 32] = c;
+      b[9 * 32] = s;
+    }
+    // v_j of step u (the row's products with v_{j+1} read the next slot,
+    // or the checkpoint for the segment's last step)
+    CV x{seg[0], seg[32], seg[2 * 32], seg[3 * 32]};
+    CV y{seg[4 * 32], seg[5 * 32], seg[6 * 32], seg[7 * 32]};
+#pragma unroll
+    for (int u = 0; u < CKP; ++u) {
+      const int j = j0 + u;
+      CV xn = c1.s, yn = c1.p;
+      if (u + 1 < CKP) {
+        const float* bn = seg + (u + 1) * kSegWords * 32;
+        xn = CV{bn[0 * 32], bn[1 * 32], bn[2 * 32], bn[3 * 32]};
+        yn = CV{bn[4 * 32], bn[5 * 32], bn[6 * 32], bn[7 * 32]};
+      }
+      if (j < L) {
+        MatK k;
+        float rho = 0.0f;
+        if constexpr (P > 0) {
+          k = kb[u % P];
+          if constexpr (DUAL) rho = rb[u % P];
+        } else {
+          const int m = st.m[st.idx(front, j)];
+          k = mt.get(m);
+          if constexpr (DUAL) rho = tt->get(m);
         }
         const float* b = seg + u * kSegWords * 32;
-        const CV x{b[0 * 32], b[1 * 32], b[2 * 32], b[3 * 32]};
-        const CV y{b[4 * 32], b[5 * 32], b[6 * 32], b[7 * 32]};
-        const float bc_u = b[8 * 32], bs_u = b[9 * 32];
+        const float c = b[8 * 32], s = b[9 * 32];
         const float gs = fmaf(k.q12s, fmaf(as.a0.x, x.yi, as.a0.y * x.yr), k.q21s * fmaf(as.a1.x, x.xi, as.a1.y * x.xr));
         const float gp = fmaf(k.q12p, fmaf(ap.a0.x, y.yi, ap.a0.y * y.yr), k.q21p * fmaf(ap.a1.x, y.xi, ap.a1.y * y.xr));
-        sink(st.idx(front, j), -2.0f * k.kap * (scale2(gs, eas + c1.es) + scale2(gp, eap + c1.ep)));
-        const float c = bc_u, s = bs_u;
+        const int i = st.idx(front, j);
+        sink(i, -2.0f * k.kap * (scale2(gs, eas + c1.es) + scale2(gp, eap + c1.ep)));
+        if constexpr (DUAL) {
+          // rho (phase term kap d g + quotient term on v_{j+1}), at this
+          // step's exponents
+          const float kd = k.kap * st.d[i];
+          const float qs = fmaf(k.q21s, fmaf(as.a1.x, xn.xi, as.a1.y * xn.xr),
+                                -k.q12s * fmaf(as.a0.x, xn.yi, as.a0.y * xn.yr));
+          const float qp = fmaf(k.q12p, fmaf(ap.a0.x, yn.yi, ap.a0.y * yn.yr),
+                                -k.q21p * fmaf(ap.a1.x, yn.xi, ap.a1.y * yn.xr));
+          acc_s = fmaf(rho, fmaf(kd, gs, s * qs), acc_s);
+          acc_p = fmaf(rho, fmaf(kd, gp, s * qp), acc_p);
+        }
         row_step(as, c, s * k.q12s, s * k.q21s);
         row_step(ap, c, s * k.q12p, s * k.q21p);
-        row_guard(as, eas);
-        row_guard(ap, eap);
+        if constexpr (DUAL) {
+          row_guard_fold(as, eas, acc_s, gc, c1.es - eA);
+          row_guard_fold(ap, eap, acc_p, gc, c1.ep - eA);
+        } else {
+          row_guard(as, eas);
+          row_guard(ap, eap);
+        }
       }
+      x = xn;
+      y = yn;
+    }
+    if constexpr (DUAL) {
+      gc = fmaf(-2.0f, scale2(acc_s, eas + c1.es - eA), gc);
+      gc = fmaf(-2.0f, scale2(acc_p, eap + c1.ep - eA), gc);
+      acc_s = 0.0f;
+      acc_p = 0.0f;
     }
     row_renorm(as, eas);
     row_renorm(ap, eap);
+  }
+  if constexpr (DUAL) {
+    // a_L (0, deta0)^T: v_L = (1, eta0) at exponent 0
+    gc = fmaf(2.0f * deta_s, scale2(as.a1.x, eas - eA), gc);
+    gc = fmaf(2.0f * deta_p, scale2(ap.a1.x, eap - eA), gc);
+    *g_cos = gc;
   }
 }
 

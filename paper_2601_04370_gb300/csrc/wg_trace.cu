@@ -1918,11 +1918,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_adjoint(const AdjArgs A) {
         const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
         GradSink sink{s_grad, &bad, lane, uniform};
         if constexpr (T) {
-          MatTableD mtd;
-          mtd.init(H, rec.cos0, rec.lam, mt);
+          TiltTable tt;
+          tt.init(H, rec.cos0);
           float g = 0.f;
           tmm_adjoint<P, GradSink, true>(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, seg, rec.eA,
-                                         &mtd, &g);
+                                         &tt, &g);
           A.tilt_aux[A.perm[i]].g_cos = (double)g * pow2d(rec.eA);
         } else {
           tmm_adjoint<P>(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, seg, rec.eA);
