@@ -46,7 +46,8 @@ class OraDesign(C.Structure):
                 ("mat_n", C.POINTER(C.c_double)), ("mir_x_mm", C.POINTER(C.c_double)),
                 ("mir_tilt_deg", C.POINTER(C.c_double)), ("mir_omega", C.POINTER(C.c_float)),
                 ("n_layers", C.POINTER(C.c_int32)), ("layer_mat", C.POINTER(C.c_int32)),
-                ("layer_d_nm", C.POINTER(C.c_double)), ("pruned", C.POINTER(C.c_uint8))]
+                ("layer_d_nm", C.POINTER(C.c_double)), ("pruned", C.POINTER(C.c_uint8)),
+                ("mir_geo", C.POINTER(C.c_double))]
 
 
 class OraCfg(C.Structure):
@@ -207,7 +208,9 @@ class _Marshalled:
                            mir_omega=typed(D.mirror_omega, np.float32, C.c_float),
                            n_layers=typed(D.n_layers, np.int32, C.c_int32),
                            layer_mat=typed(D.layer_mat, np.int32, C.c_int32),
-                           layer_d_nm=d64(D.layer_d_nm), pruned=typed(D.pruned, np.uint8, C.c_uint8))
+                           layer_d_nm=d64(D.layer_d_nm), pruned=typed(D.pruned, np.uint8, C.c_uint8),
+                           mir_geo=(d64(D.mirror_geo) if getattr(D, "mirror_geo", None) is not None
+                                    else C.POINTER(C.c_double)()))
         self.c = OraCfg(n_lam=len(Cfg.lam_nm), n_fx=len(Cfg.fx_deg), n_fy=len(Cfg.fy_deg), pol=Cfg.pol,
                         n_rays=Cfg.n_rays, seed=Cfg.seed, max_events=Cfg.max_events, eb_nx=Cfg.eb_nx,
                         eb_ny=Cfg.eb_ny, lut_bins=int(getattr(Cfg, "lut_bins", 0)), pupil_y_mm=Cfg.pupil_y_mm,

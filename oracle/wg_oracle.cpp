@@ -423,6 +423,11 @@ struct OraDesign {
   const int32_t* layer_mat;    // [sum n_layers]
   const double* layer_d_nm;    // [sum n_layers]
   const uint8_t* pruned;       // [sum n_layers]
+  // NULL: every mirror is a PRMA plane (above). Else row k (14 values) makes
+  // mirror k a general plane: normal N0 at the tilt t0, pivot point, tilt
+  // axis a (unit, perpendicular to N0), the rectangle [x0, x1] x [y0, y1] of
+  // the slab's (x, y) where it acts, and t0 (deg).
+  const double* mir_geo;
 };
 struct OraCfg {
   int32_t n_lam, n_fx, n_fy, pol;  // pol: 0 s+p pair, 1 random linear, 2 s, 3 p
@@ -556,10 +561,27 @@ static Launch<T> launch(const OraDesign& D, const OraCfg& C, uint64_t ray) {
   return L;
 }
 
-// Mirror geometry: plane through (x_k, 0, t/2) with normal (-sin a, 0, cos a).
+// Mirror geometry. PRMA mirror: plane through (x_k, 0, t/2) with normal
+// (-sin a, 0, cos a) at tilt a. General mirror (row k of mir_geo): normal
+// N(a) = cos(a - a0) N0 + sin(a - a0) (axis x N0), the rotation of N0 about
+// the axis by a - a0 (a0 = the row's tilt of N0), normalized, plane through
+// the pivot, acting only where the crossing lies in its (x, y) rectangle.
 template <class T>
-static inline V3<T> mirror_normal(const T& tilt) {
-  return V3<T>(-sin(tilt), T(0.0), cos(tilt));
+static inline V3<T> mirror_normal(const OraDesign& D, int k, const T& tilt) {
+  if (!D.mir_geo) return V3<T>(-sin(tilt), T(0.0), cos(tilt));
+  const double* g = D.mir_geo + 14 * k;
+  const T del = tilt - T(g[13] * DEG);
+  const T c = cos(del), s = sin(del);
+  const V3<double> aN = cross(V3<double>(g[6], g[7], g[8]), V3<double>(g[0], g[1], g[2]));
+  const V3<T> N(c * T(g[0]) + s * T(aN.x), c * T(g[1]) + s * T(aN.y), c * T(g[2]) + s * T(aN.z));
+  // unit to FP64 rounding (the stored values are float32)
+  const T inv = T(1.0) / sqrt(N.x * N.x + N.y * N.y + N.z * N.z);
+  return V3<T>(N.x * inv, N.y * inv, N.z * inv);
+}
+static inline V3<double> mirror_pivot(const OraDesign& D, int k) {
+  if (!D.mir_geo) return V3<double>(D.mir_x_mm[k], 0.0, 0.5 * D.thickness_mm);
+  const double* g = D.mir_geo + 14 * k;
+  return V3<double>(g[3], g[4], g[5]);
 }
 
 // Nearest surface along the ray; excludes the surface the ray sits on.
@@ -591,11 +613,19 @@ static int next_surface(const OraDesign& D, const Params<T>& P, const V3<T>& p, 
     if (val(d.y) < 0.0) consider(S_YNEG, (T(-hw) - p.y) / d.y);
   }
   for (int k = 0; k < D.n_mir; ++k) {
-    V3<T> N = mirror_normal(P.tilt[k]);
+    V3<T> N = mirror_normal(D, k, P.tilt[k]);
     T den = dot(d, N);
     if (val(den) == 0.0) continue;
-    V3<T> c(T(D.mir_x_mm[k]), T(0.0), T(0.5 * tz));
-    consider(S_MIR + k, dot(c - p, N) / den);
+    const V3<double> pv = mirror_pivot(D, k);
+    V3<T> c(T(pv.x), T(pv.y), T(pv.z));
+    const T t = dot(c - p, N) / den;
+    if (D.mir_geo) {
+      // a general mirror acts only inside its rectangle
+      const double* g = D.mir_geo + 14 * k;
+      const double qx = val(p.x) + val(t) * val(d.x), qy = val(p.y) + val(t) * val(d.y);
+      if (!(qx >= g[9] && qx <= g[10] && qy >= g[11] && qy <= g[12])) continue;
+    }
+    consider(S_MIR + k, t);
   }
   return id;
 }
@@ -773,7 +803,7 @@ static RayOut<T> trace_ray(const TraceCtx<T>& X, uint64_t ray) {
     last = sid;
     if (sid >= S_MIR) {
       int k = sid - S_MIR;
-      V3<T> N = mirror_normal(X.P->tilt[k]);
+      V3<T> N = mirror_normal(*X.D, k, X.P->tilt[k]);
       T cd = dot(d, N);
       bool front = val(cd) < 0.0;
       T cos_i = front ? -cd : cd;
@@ -979,7 +1009,7 @@ static void split_rec(const TraceCtx<double>& X, SplitAcc& A, int cell, double l
     last = sid;
     if (sid >= S_MIR) {
       int k = sid - S_MIR;
-      V3<double> N = mirror_normal(X.P->tilt[k]);
+      V3<double> N = mirror_normal(*X.D, k, X.P->tilt[k]);
       double cd = dot(d, N);
       bool front = cd < 0.0;
       Coef<double> cf = mirror_coef(X, k, front, front ? -cd : cd, lambda);
@@ -1440,7 +1470,7 @@ static void geo_ray(const TraceCtx<double>& X, uint64_t ray, double* tally, int6
     last = sid;
     if (sid >= S_MIR) {
       const int k = sid - S_MIR;
-      const V3<double> N = mirror_normal(X.P->tilt[k]);
+      const V3<double> N = mirror_normal(*X.D, k, X.P->tilt[k]);
       const double cd = dot(d, N);
       U4 ctr = {{(uint32_t)ray, (uint32_t)(ray >> 32), (uint32_t)(m >> 2), TAG_EVT}};
       U4 rr = philox4x32_10(ctr, (uint32_t)C.seed, (uint32_t)(C.seed >> 32));
@@ -1486,7 +1516,7 @@ static void geo_split_rec(const TraceCtx<double>& X, double* tally, int64_t cell
     last = sid;
     if (sid >= S_MIR) {
       const int k = sid - S_MIR;
-      const V3<double> N = mirror_normal(X.P->tilt[k]);
+      const V3<double> N = mirror_normal(*X.D, k, X.P->tilt[k]);
       const double om = (double)D.mir_omega[k];
       if (w * om > prune) geo_split_rec(X, tally, cell0, cell, p, d - N * (2.0 * dot(d, N)), w * om, sid, ev + 1, prune);
       if (w * (1.0 - om) > prune) geo_split_rec(X, tally, cell0, cell, p, d, w * (1.0 - om), sid, ev + 1, prune);

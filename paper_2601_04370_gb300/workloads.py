@@ -52,6 +52,12 @@ class Design:
     layer_mat: np.ndarray      # int32 [sum L] material id, layer 1 first
     layer_d_nm: np.ndarray     # float32 [sum L]
     pruned: np.ndarray         # uint8 [sum L]
+    # None: every mirror is a PRMA plane through (x_k, 0, t/2) tilted about y.
+    # Else float32 [K, 14], mirror k a general plane: unit normal N0 (3) at
+    # the tilt t0, pivot (3), tilt axis (3; unit, perpendicular to N0; the
+    # tilt mirror_tilt_deg[k] rotates N0 about it by tilt - t0), the (x, y)
+    # rectangle x0, x1, y0, y1 where the mirror acts (+-inf: unbounded), t0.
+    mirror_geo: np.ndarray | None = None
 
     def __post_init__(self):
         for name in ("n_slab", "thickness_mm", "width_mm", "x_end_mm", "eye_relief_mm", "ic_tilt_deg"):
@@ -64,6 +70,8 @@ class Design:
         self.layer_mat = np.asarray(self.layer_mat, dtype=np.int32)
         self.layer_d_nm = _f32(self.layer_d_nm)
         self.pruned = np.asarray(self.pruned, dtype=np.uint8)
+        if self.mirror_geo is not None:
+            self.mirror_geo = _f32(self.mirror_geo).reshape(-1, 14)
 
     @property
     def n_mirrors(self) -> int:
@@ -206,6 +214,85 @@ def differentiation(n_rays=100_000_000, seed=11):
     """As representative but 200 layers per mirror (1200 thickness parameters)
     plus 6 tilts, 1e8 rays."""
     return representative(n_rays=n_rays, seed=seed, n_layers=200, design_seed=2)
+
+
+def _general_row(n0, pivot, axis, rect, t0):
+    return list(n0) + list(pivot) + list(axis) + list(rect) + [t0]
+
+
+def pupil_expander_design(n_fold=30, n_out=16, n_layers=23, seed=3, n_slab=1.9, t_mm=1.7, tilt=26.0,
+                          fold_x0=5.0, fold_dx=0.5, band_mm=6.0, out_y0=8.0, out_dy=1.0,
+                          mat_n=(N_TA2O5_PAPER, N_SIO2)):
+    """Two-dimensional pupil expansion (Results, "System Architecture": a
+    1.7 mm slab of index 1.9, an input mirror, 30 folding and 16 output
+    mirrors, 23-layer Ta2O5/SiO2 stacks, thicknesses 20-200 nm). The paper
+    gives no placement, so it is synthesized: guided light leaves the input
+    mirror along +x; fold mirror k is the vertical plane x - y = fold_x0 +
+    k fold_dx at 45 deg (a reflection swaps d_x and d_y, so TIR is kept),
+    acting in the band |y| <= band_mm; the folded light travels along +y to
+    output mirror j, the plane through (0, out_y0 + j out_dy, t/2) tilted
+    about x by the input mirror's tilt, acting over the fold region's x
+    range. Reflection probabilities follow the equal-extraction rule within
+    each array. Tilt axes: z for the fold mirrors, x for the output mirrors."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    K = n_fold + n_out
+    nl, mats, ds, pr = cycling_stack(rng, K, n_layers, len(mat_n), d_lo=20.0, d_hi=200.0)
+    inf = np.inf
+    s2 = np.sqrt(0.5)
+    rows, xs, tilts = [], [], []
+    for k in range(n_fold):
+        xk = fold_x0 + fold_dx * k
+        rows.append(_general_row((-s2, s2, 0.0), (xk, 0.0, 0.5 * t_mm), (0.0, 0.0, 1.0), (-inf, inf, -band_mm, band_mm),
+                                 45.0))
+        xs.append(xk)
+        tilts.append(45.0)
+    a = np.deg2rad(tilt)
+    x_lo, x_hi = fold_x0 - band_mm - 2.0, fold_x0 + fold_dx * (n_fold - 1) + band_mm + 2.0
+    for j in range(n_out):
+        yj = out_y0 + out_dy * j
+        rows.append(_general_row((0.0, -np.sin(a), np.cos(a)), (0.0, yj, 0.5 * t_mm), (1.0, 0.0, 0.0),
+                                 (x_lo, x_hi, -inf, inf), tilt))
+        xs.append(0.5 * (x_lo + x_hi))
+        tilts.append(tilt)
+    omega = np.concatenate([default_omega(n_fold), default_omega(n_out)])
+    y_hi = out_y0 + out_dy * (n_out - 1) + t_mm / np.tan(a) + 1.0
+    return Design(dims=3, n_slab=n_slab, thickness_mm=t_mm, width_mm=2.0 * y_hi, x_end_mm=x_hi + 1.0,
+                  eye_relief_mm=15.0, ic_tilt_deg=tilt, mat_n=list(mat_n), mirror_x_mm=xs,
+                  mirror_tilt_deg=tilts, mirror_omega=omega, n_layers=nl, layer_mat=mats, layer_d_nm=ds,
+                  pruned=pr, mirror_geo=np.array(rows))
+
+
+def pupil_expander(n_rays=10_000_000, seed=13, n_fields=16, eb_bins=64):
+    """The two-dimensional pupil-expansion design (pupil_expander_design):
+    9 wavelengths (450/470/490, 500/530/560, 620/660/700 nm), a 16x16 field
+    grid over 38x38 deg (cell centres), random linear polarization, a
+    1.6 mm panel, 16x16 mm eyebox at 15 mm eye relief centred over the output
+    region, 64x64 bins."""
+    D = pupil_expander_design()
+    g = D.mirror_geo
+    fold = g[:, 2] == 0.0
+    xc = float(0.5 * (D.mirror_x_mm[fold].min() + D.mirror_x_mm[fold].max()))
+    yc = float(0.5 * (g[~fold, 4].min() + g[~fold, 4].max()))
+    C = TraceConfig(lam_nm=[450.0, 470.0, 490.0, 500.0, 530.0, 560.0, 620.0, 660.0, 700.0],
+                    fx_deg=cell_centres(38.0, n_fields), fy_deg=cell_centres(38.0, n_fields),
+                    pol=POL_RANDOM_LINEAR, n_rays=n_rays, seed=seed, pupil_y_mm=1.6, eb_cx_mm=xc, eb_cy_mm=yc,
+                    eb_w_mm=16.0, eb_h_mm=16.0, eb_nx=eb_bins, eb_ny=eb_bins)
+    return D, C
+
+
+def pupil_expander_small(n_rays=20_000, seed=13):
+    """A small two-dimensional expander for parity tests: 4 fold and 3 output
+    mirrors with 6-layer stacks, 1 wavelength, 3x3 fields, 16x16 bins."""
+    D = pupil_expander_design(n_fold=4, n_out=3, n_layers=6, fold_dx=1.5, band_mm=3.0, out_y0=5.0,
+                              out_dy=1.5)
+    g = D.mirror_geo
+    fold = g[:, 2] == 0.0
+    xc = float(0.5 * (D.mirror_x_mm[fold].min() + D.mirror_x_mm[fold].max()))
+    yc = float(0.5 * (g[~fold, 4].min() + g[~fold, 4].max()))
+    C = TraceConfig(lam_nm=[530.0], fx_deg=cell_centres(20.0, 3), fy_deg=cell_centres(20.0, 3),
+                    pol=POL_RANDOM_LINEAR, n_rays=n_rays, seed=seed, pupil_y_mm=1.6, eb_cx_mm=xc, eb_cy_mm=yc,
+                    eb_w_mm=12.0, eb_h_mm=12.0, eb_nx=16, eb_ny=16)
+    return D, C
 
 
 def batching(n_designs=64, seed=4):
