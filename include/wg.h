@@ -98,6 +98,18 @@ typedef struct wg_init_opts {
  * layer 1 faces the +normal side. A pruned layer has zero thickness and is
  * skipped. mirror_omega[k] is the Monte Carlo reflection probability
  * (Methods, "Differentiable Monte Carlo ...", Eq. 5), 0 < omega < 1.
+ * mirror_geometry (NULL: the planes above) makes every mirror a general
+ * plane, for fold-and-output layouts such as the paper's two-dimensional
+ * pupil expansion (30 folding and 16 output mirrors, Results, "System
+ * Architecture"). Row k holds 14 floats: a unit normal N0, a pivot point on
+ * the plane (mm), a unit tilt axis perpendicular to N0, the rectangle x0, x1,
+ * y0, y1 (mm, +-inf allowed) of the slab's (x, y) where the mirror acts (a ray
+ * that crosses the plane outside it passes unchanged), and t0 (deg), the
+ * tilt at which the normal is N0. At the tilt t = mirror_tilt_deg[k] (or
+ * wg_set_params) the normal is cos(t - t0) N0 + sin(t - t0) axis x N0, the
+ * plane through the pivot; the tilt gradient is per degree of that rotation.
+ * mirror_x_mm is then only a label. WG_EINVAL for a non-unit normal or axis, an axis not
+ * perpendicular to the normal, or an empty rectangle.
  * All arrays are host memory owned by the caller; wg_create_design copies
  * them.
  */
@@ -115,6 +127,7 @@ typedef struct wg_design_desc {
   const int32_t* layer_material;    /* [sum n_layers] material index */
   const float* layer_thickness_nm;  /* [sum n_layers] */
   const uint8_t* layer_pruned;      /* [sum n_layers] 1 = pruned, or NULL */
+  const float* mirror_geometry;     /* [n_mirrors][14] general mirrors (above), or NULL */
 } wg_design_desc;
 
 /*

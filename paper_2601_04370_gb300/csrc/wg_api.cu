@@ -97,6 +97,8 @@ struct wg_design {
   uint8_t* blob = nullptr;
   int blob_bytes = 0;
   float* d_mir = nullptr;      // [3][K]: x, tilt, omega
+  std::vector<float> geo;      // general mirrors: [K][14] as in the descriptor; empty: PRMA
+  float* d_geo = nullptr;      // device copy of geo, or NULL
   int* d_orig_to_dev = nullptr;
   int* d_dev_to_orig = nullptr;
   float* d_stage = nullptr;    // [n_orig] thickness staging for set_params
@@ -158,6 +160,7 @@ extern "C" wg_status wg_init(wg_ctx** out, const wg_init_opts* opts) {
 static void destroy_design_dev(wg_design* d) {
   if (d->blob) cudaFree(d->blob);
   if (d->d_mir) cudaFree(d->d_mir);
+  if (d->d_geo) cudaFree(d->d_geo);
   if (d->d_orig_to_dev) cudaFree(d->d_orig_to_dev);
   if (d->d_dev_to_orig) cudaFree(d->d_dev_to_orig);
   if (d->d_stage) cudaFree(d->d_stage);
@@ -215,6 +218,19 @@ static wg_status validate_desc(const wg_design_desc* s) {
     if (!std::isfinite(s->mirror_x_mm[k]) || !std::isfinite(s->mirror_tilt_deg[k]) ||
         !(std::fabs(s->mirror_tilt_deg[k]) < 89.0f))
       return fail(WG_EINVAL, "design: mirror %d position/tilt invalid", k);
+    if (s->mirror_geometry) {
+      const float* g = s->mirror_geometry + 14 * k;
+      for (int i = 0; i < 14; ++i)
+        if (!std::isfinite(g[i]) && (i < 9 || i == 13))
+          return fail(WG_EINVAL, "design: mirror %d geometry value %d not finite", k, i);
+      const double nn = (double)g[0] * g[0] + (double)g[1] * g[1] + (double)g[2] * g[2];
+      const double aa = (double)g[6] * g[6] + (double)g[7] * g[7] + (double)g[8] * g[8];
+      const double an = (double)g[0] * g[6] + (double)g[1] * g[7] + (double)g[2] * g[8];
+      if (std::fabs(nn - 1.0) > 1e-4 || std::fabs(aa - 1.0) > 1e-4 || std::fabs(an) > 1e-4)
+        return fail(WG_EINVAL, "design: mirror %d normal and tilt axis must be unit and perpendicular", k);
+      if (!(g[9] <= g[10]) || !(g[11] <= g[12]))
+        return fail(WG_EINVAL, "design: mirror %d rectangle must have x0 <= x1 and y0 <= y1", k);
+    }
     total += s->n_layers[k];
   }
   for (long long i = 0; i < total; ++i) {
@@ -307,6 +323,10 @@ static wg_status upload_design(wg_design* d, cudaStream_t s) {
     m[2 * d->K + k] = d->omega[k];
   }
   CU(cudaMemcpyAsync(d->d_mir, m.data(), sizeof(float) * m.size(), cudaMemcpyHostToDevice, s));
+  if (!d->geo.empty()) {
+    CU(cudaMalloc(&d->d_geo, sizeof(float) * d->geo.size()));
+    CU(cudaMemcpyAsync(d->d_geo, d->geo.data(), sizeof(float) * d->geo.size(), cudaMemcpyHostToDevice, s));
+  }
   CU(cudaMalloc(&d->d_orig_to_dev, sizeof(int) * std::max(1, d->n_orig)));
   CU(cudaMalloc(&d->d_dev_to_orig, sizeof(int) * std::max(1, d->n_dev)));
   CU(cudaMalloc(&d->d_stage, sizeof(float) * std::max(1, d->n_orig)));
@@ -314,7 +334,7 @@ static wg_status upload_design(wg_design* d, cudaStream_t s) {
     CU(cudaMemcpyAsync(d->d_orig_to_dev, d->orig_to_dev.data(), sizeof(int) * d->n_orig, cudaMemcpyHostToDevice, s));
   if (d->n_dev)
     CU(cudaMemcpyAsync(d->d_dev_to_orig, d->dev_to_orig.data(), sizeof(int) * d->n_dev, cudaMemcpyHostToDevice, s));
-  CU(launch_prep_design(d->blob, d->d_mir, d->d_mir + d->K, d->d_mir + 2 * d->K, d->K, d->ic_tilt, d->thick, s));
+  CU(launch_prep_design(d->blob, d->d_mir, d->d_mir + d->K, d->d_mir + 2 * d->K, d->d_geo, d->K, d->ic_tilt, d->thick, s));
   CU(cudaStreamSynchronize(s));
   return WG_OK;
 }
@@ -341,6 +361,7 @@ extern "C" wg_status wg_create_design(wg_ctx* c, const wg_design_desc* s, wg_des
   d->mir_x.assign(s->mirror_x_mm, s->mirror_x_mm + d->K);
   d->mir_tilt.assign(s->mirror_tilt_deg, s->mirror_tilt_deg + d->K);
   d->omega.assign(s->mirror_omega, s->mirror_omega + d->K);
+  if (s->mirror_geometry) d->geo.assign(s->mirror_geometry, s->mirror_geometry + 14 * (size_t)d->K);
   d->n_layers.assign(s->n_layers, s->n_layers + d->K);
   int total = 0;
   for (int k = 0; k < d->K; ++k) total += d->n_layers[k];
@@ -413,7 +434,7 @@ extern "C" wg_status wg_set_params(wg_design* d, const float* thickness_nm, int6
     ++d->geom_version;  // ray paths change with the geometry: the eyebox-ray list is stale
     d->exit_fp = 0;
     CU(cudaMemcpyAsync(d->d_mir + d->K, tilt_deg, sizeof(float) * d->K, cudaMemcpyHostToDevice, s));
-    CU(launch_prep_design(d->blob, d->d_mir, d->d_mir + d->K, d->d_mir + 2 * d->K, d->K, d->ic_tilt, d->thick, s));
+    CU(launch_prep_design(d->blob, d->d_mir, d->d_mir + d->K, d->d_mir + 2 * d->K, d->d_geo, d->K, d->ic_tilt, d->thick, s));
   }
   return WG_OK;
 }
@@ -431,7 +452,7 @@ extern "C" wg_status wg_set_omega(wg_design* d, const float* omega, int32_t n, v
   ++d->geom_version;  // the sampled paths change with omega: the eyebox-ray list is stale
   d->exit_fp = 0;
   CU(cudaMemcpyAsync(d->d_mir + 2 * d->K, omega, sizeof(float) * d->K, cudaMemcpyHostToDevice, s));
-  CU(launch_prep_design(d->blob, d->d_mir, d->d_mir + d->K, d->d_mir + 2 * d->K, d->K, d->ic_tilt, d->thick, s));
+  CU(launch_prep_design(d->blob, d->d_mir, d->d_mir + d->K, d->d_mir + 2 * d->K, d->d_geo, d->K, d->ic_tilt, d->thick, s));
   CU(cudaStreamSynchronize(s));  // the caller's omega array may go once this returns
   return WG_OK;
 }
@@ -1208,7 +1229,8 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   const bool tilt = grad_tilt != nullptr;
   const size_t acc_bytes = (sizeof(double) * std::max(1, d->n_dev) + 15) & ~(size_t)15;
   const size_t aux_bytes =
-      tilt ? (size_t)cap * (sizeof(TiltAux) + sizeof(unsigned int)) + 2 * (size_t)batch * sizeof(RayHead) + 512 : 0;
+      tilt ? (size_t)cap * (sizeof(TiltAux) + sizeof(unsigned int)) + 2 * (size_t)batch * sizeof(RayHead) + kHitSortScratch
+           : 0;
   // coating table: FP64 dL/dc per entry and the second stage's records
   const bool use_lut = cfg->lut_bins > 0;
   const long long n_lut = use_lut ? lut_entries(d, cfg) : 0;
@@ -1297,12 +1319,12 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
       use_list ? reinterpret_cast<const ExitRec*>(static_cast<const uint8_t*>(d->exits.p) + kExitHead) : nullptr;
   if (use_list && n_list > 0) {
     // rays grouped by their hit count: a replay warp then gets rays of equal length
-    const size_t lb = 512 + sizeof(ExitRec) * (size_t)n_list;
+    const size_t lb = kHitSortScratch + sizeof(ExitRec) * (size_t)n_list;
     if (lb > c->lsort.n) {
       CU(cudaEventSynchronize(c->ws_free));
       CU(c->lsort.ensure(lb));
     }
-    ExitRec* sorted = reinterpret_cast<ExitRec*>(static_cast<uint8_t*>(c->lsort.p) + 512);
+    ExitRec* sorted = reinterpret_cast<ExitRec*>(static_cast<uint8_t*>(c->lsort.p) + kHitSortScratch);
     CU(launch_exits_sort(list, n_list, static_cast<unsigned int*>(c->lsort.p), sorted, s));
     list = sorted;
   }

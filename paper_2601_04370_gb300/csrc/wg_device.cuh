@@ -31,7 +31,7 @@ namespace wgk {
 constexpr int MAX_MAT = 4;
 constexpr int MAX_MIR = 64;
 constexpr int MAX_EVENTS = 128;
-constexpr int TAPE_HITS = 64;
+constexpr int TAPE_HITS = 128;  // = WG_MAX_EVENTS: a ray's mirror hits always fit
 constexpr int CK = 8;                 // checkpoint stride (layers)
 constexpr int MAX_LAYERS_MIRROR = 512;
 constexpr int MAX_CK = MAX_LAYERS_MIRROR / 6 + 2;  // checkpoints at the shortest segment (6 layers)
@@ -57,18 +57,24 @@ struct alignas(16) BlobHeader {
   // 1: inside the slab the input mirror, the mirror planes in index order and
   // the end face are disjoint and ordered along x, so a ray between plane k-1
   // and plane k can only meet one of those two next (set by k_prep_design)
-  int ordered, pad_[3];
+  int ordered;
+  // 1: general mirrors (any normal, a tilt axis, an (x, y) rectangle where
+  // the plane acts); 0: PRMA planes nx x + nz z = c across the whole slab
+  int general, pad_[2];
   float mat_inv_n[MAX_MAT];               // 1 / n
   float mat_r2[MAX_MAT];                  // (n_slab / n)^2
 };
 static_assert(sizeof(BlobHeader) == 128, "header layout");
 
 struct alignas(16) MirrorRec {
-  float nx, nz, c, omega;  // plane: nx x + nz z = c; reflection probability
-  float isw, is1w;         // 1/sqrt(omega), 1/sqrt(1-omega)
-  int layer_off, n_layers; // device layers of this mirror, traversal order = layer 1 first
+  float nx, ny, nz, c;       // plane n . p = c (PRMA: ny = 0)
+  float omega, isw, is1w;    // reflection probability, 1/sqrt(omega), 1/sqrt(1-omega)
+  int layer_off;             // first device layer; traversal order = layer 1 first
+  int n_layers;              // device layers of this mirror
+  float ax, ay, az;          // tilt axis: dn/d(tilt) = a x n per radian (PRMA: a = -y)
+  float x0, x1, y0, y1;      // (x, y) rectangle where a general mirror acts
 };
-static_assert(sizeof(MirrorRec) == 32, "mirror layout");
+static_assert(sizeof(MirrorRec) == 64, "mirror layout");
 
 struct Blob {
   const BlobHeader* h;
@@ -912,9 +918,15 @@ __device__ __forceinline__ int next_surface(const Blob& B, V3 p, V3 d, int last,
   if (right && d.x > 0.0f) consider(S_RIGHT, __fdividef(h.x_end - p.x, d.x));
   for (int k = k0; k < k1; ++k) {
     const MirrorRec& m = B.mir[k];
-    const float den = fmaf(d.x, m.nx, d.z * m.nz);
+    const float den = fmaf(d.x, m.nx, fmaf(d.y, m.ny, d.z * m.nz));
     if (den == 0.0f) continue;
-    consider(S_MIR + k, __fdividef(m.c - fmaf(p.x, m.nx, p.z * m.nz), den));
+    const float t = __fdividef(m.c - fmaf(p.x, m.nx, fmaf(p.y, m.ny, p.z * m.nz)), den);
+    if (h.general) {
+      // a general mirror acts only inside its rectangle
+      const float qx = fmaf(t, d.x, p.x), qy = fmaf(t, d.y, p.y);
+      if (!(qx >= m.x0 && qx <= m.x1 && qy >= m.y0 && qy <= m.y1)) continue;
+    }
+    consider(S_MIR + k, t);
   }
   tmin = best;
   return id;
@@ -925,7 +937,7 @@ __device__ __forceinline__ int next_surface(const Blob& B, V3 p, V3 d, int last,
 __device__ __forceinline__ int region_after(const Blob& B, int reg, int k, V3 d) {
   if (reg < 0) return reg;
   const MirrorRec& m = B.mir[k];
-  return fmaf(d.x, m.nx, d.z * m.nz) * m.nx > 0.0f ? k + 1 : k;
+  return fmaf(d.x, m.nx, fmaf(d.y, m.ny, d.z * m.nz)) * m.nx > 0.0f ? k + 1 : k;
 }
 
 // TIR at a slab face against air: r_s, r_p with u = n cos_i, a = sqrt(n^2 sin^2 - 1)

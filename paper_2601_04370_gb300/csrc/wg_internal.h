@@ -145,7 +145,7 @@ unsigned long long launches();
 // launchers (return cudaError_t of the launch). P: material period of the
 // design's stacks (0 = any, 2, 3); F: fields per ray (2 = s+p pair).
 cudaError_t launch_prep_design(uint8_t* blob, const float* mir_x, const float* mir_tilt, const float* mir_omega,
-                               int n_mir, float ic_tilt_deg, float thick, cudaStream_t s);
+                               const float* geo, int n_mir, float ic_tilt_deg, float thick, cudaStream_t s);
 cudaError_t launch_prep_fields(FieldRec* out, const float* fx, const float* fy, int n_fx, int n_fy,
                                float n_slab, float ic_tilt_deg, int dims, cudaStream_t s);
 cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s);
@@ -174,7 +174,10 @@ cudaError_t launch_lut_build(const uint8_t* blob, int P, int n_mir, int n_lam, c
                              float dc, float4* out, cudaStream_t s);
 cudaError_t launch_lut_records(const double* grad, int n_mir, int n_lam, const float* lam, int n, float c0, float dc,
                                HitRec* out, cudaStream_t s);
-// ray heads / listed eyebox rays grouped by their mirror-hit count (cnt: device [65] scratch)
+// ray heads / listed eyebox rays grouped by their mirror-hit count (cnt: device
+// scratch of kHitSortScratch bytes)
+// bytes of the hit-count sort's counters (one per hit count 0..TAPE_HITS)
+constexpr size_t kHitSortScratch = 1024;
 cudaError_t launch_heads_sort(const RayHead* in, long long n, unsigned int* cnt, RayHead* out, cudaStream_t s);
 cudaError_t launch_exits_sort(const ExitRec* in, long long n, unsigned int* cnt, ExitRec* out, cudaStream_t s);
 // reflection-probability pre-optimization: geometric trace of the rays of a

@@ -96,17 +96,52 @@ __device__ bool stage_blob(uint8_t* s_dst, const uint8_t* g_src, int bytes, uint
 // Preparation (FP64, tiny): mirror planes from tilts, input-mirror normal,
 // per-field launch directions and transverse bases.
 // ---------------------------------------------------------------------------
+// geo (general designs, else NULL): per mirror 14 floats, the normal N0 at
+// the nominal tilt, the pivot, the tilt axis a, the rectangle x0 x1 y0 y1 and
+// the nominal tilt (deg); the normal at tilt t is N0 rotated about a by
+// t - t0, cos(t - t0) N0 + sin(t - t0) a x N0, through the pivot.
 __global__ void k_prep_design(uint8_t* blob, const float* mir_x, const float* mir_tilt, const float* mir_omega,
-                              int n_mir, float ic_tilt_deg, float thick) {
+                              const float* geo, int n_mir, float ic_tilt_deg, float thick) {
   BlobHeader* h = reinterpret_cast<BlobHeader*>(blob);
   MirrorRec* mir = reinterpret_cast<MirrorRec*>(blob + h->off_mir);
   const double deg = 3.14159265358979323846 / 180.0;
   for (int k = threadIdx.x; k < n_mir; k += blockDim.x) {
     const double a = (double)mir_tilt[k] * deg;
-    const double nx = -sin(a), nz = cos(a);
-    mir[k].nx = (float)nx;
-    mir[k].nz = (float)nz;
-    mir[k].c = (float)(nx * (double)mir_x[k] + nz * 0.5 * (double)thick);
+    if (!geo) {
+      const double nx = -sin(a), nz = cos(a);
+      mir[k].nx = (float)nx;
+      mir[k].ny = 0.0f;
+      mir[k].nz = (float)nz;
+      mir[k].c = (float)(nx * (double)mir_x[k] + nz * 0.5 * (double)thick);
+      mir[k].ax = 0.0f;
+      mir[k].ay = -1.0f;
+      mir[k].az = 0.0f;
+      mir[k].x0 = mir[k].y0 = -__int_as_float(0x7f800000);
+      mir[k].x1 = mir[k].y1 = __int_as_float(0x7f800000);
+    } else {
+      const float* g = geo + 14 * k;
+      const double del = a - (double)g[13] * deg;
+      const double c = cos(del), sn = sin(del);
+      const double n0x = g[0], n0y = g[1], n0z = g[2], ax = g[6], ay = g[7], az = g[8];
+      double nx = c * n0x + sn * (ay * n0z - az * n0y);
+      double ny = c * n0y + sn * (az * n0x - ax * n0z);
+      double nz = c * n0z + sn * (ax * n0y - ay * n0x);
+      const double inv = 1.0 / sqrt(nx * nx + ny * ny + nz * nz);  // unit in FP64 (float32 inputs)
+      nx *= inv;
+      ny *= inv;
+      nz *= inv;
+      mir[k].nx = (float)nx;
+      mir[k].ny = (float)ny;
+      mir[k].nz = (float)nz;
+      mir[k].c = (float)(nx * (double)g[3] + ny * (double)g[4] + nz * (double)g[5]);
+      mir[k].ax = g[6];
+      mir[k].ay = g[7];
+      mir[k].az = g[8];
+      mir[k].x0 = g[9];
+      mir[k].x1 = g[10];
+      mir[k].y0 = g[11];
+      mir[k].y1 = g[12];
+    }
     const double w = (double)mir_omega[k];
     mir[k].omega = mir_omega[k];
     mir[k].isw = (float)(1.0 / sqrt(w));
@@ -118,10 +153,12 @@ __global__ void k_prep_design(uint8_t* blob, const float* mir_x, const float* mi
     h->ic_nx = (float)(-sin(a));
     h->ic_nz = (float)cos(a);
     h->ic_cot = (float)(cos(a) / sin(a));
+    h->general = geo != nullptr;
     // ordering of the planes along x on both faces (planes that are ordered
-    // on both faces do not cross inside the slab), with a 0.1 um margin
+    // on both faces do not cross inside the slab), with a 0.1 um margin;
+    // general designs test every plane
     const double margin = 1e-4;
-    int ok = fabs((double)h->ic_nx) > 1e-3;
+    int ok = fabs((double)h->ic_nx) > 1e-3 && geo == nullptr;
     for (int f = 0; f < 2 && ok; ++f) {
       const double z = f ? (double)thick : 0.0;
       double prev = ok ? -(double)h->ic_nz * z / (double)h->ic_nx : 0.0;
@@ -362,7 +399,7 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
                                                    float2* Ep_out) {
   const BlobHeader& H = *B.h;
   const MirrorRec& M = B.mir[k];
-  const V3 N = v3(M.nx, 0.0f, M.nz);
+  const V3 N = v3(M.nx, M.ny, M.nz);
   const float cd = dot3(R.d, N);
   MirrorStep st;
   st.front = cd < 0.0f;
@@ -408,7 +445,7 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
   if (st.refl) {
     st.cs = cscale(cf.rs, M.isw);
     st.cp = cscale(cf.rp, M.isw);
-    d2 = v3(fmaf(-2.0f * cd, N.x, R.d.x), R.d.y, fmaf(-2.0f * cd, N.z, R.d.z));
+    d2 = v3(fmaf(-2.0f * cd, N.x, R.d.x), fmaf(-2.0f * cd, N.y, R.d.y), fmaf(-2.0f * cd, N.z, R.d.z));
   } else {
     st.cs = cscale(cf.ts, M.is1w);
     st.cp = cscale(cf.tp, M.is1w);
@@ -1378,8 +1415,8 @@ template <int F>
 __device__ void mirror_event_tilt(Ray<F>& R, int k, const Blob& B, const TraceArgs& A, int k0, int nk, float* col,
                                   double* acc, const TiltAux& X, unsigned& live) {
   const MirrorRec& M = B.mir[k];
-  const V3 N = v3(M.nx, 0.0f, M.nz);
-  const V3 dN = v3(-M.nz, 0.0f, M.nx);  // dN/d(tilt) per radian
+  const V3 N = v3(M.nx, M.ny, M.nz);
+  const V3 dN = cross3(v3(M.ax, M.ay, M.az), N);  // dN/d(tilt) per radian
   const float cd = dot3(R.d, N);
   const bool front = cd < 0.0f;
   const float2 cs = X.cs, cp = X.cp;
@@ -1401,7 +1438,7 @@ __device__ void mirror_event_tilt(Ray<F>& R, int k, const Blob& B, const TraceAr
   const uint32_t word = (m & 3) == 0 ? rnd.x : (m & 3) == 1 ? rnd.y : (m & 3) == 2 ? rnd.z : rnd.w;
   const bool refl = u24(word) < M.omega;
   V3 d2 = R.d;
-  if (refl) d2 = v3(fmaf(-2.0f * cd, N.x, R.d.x), R.d.y, fmaf(-2.0f * cd, N.z, R.d.z));
+  if (refl) d2 = v3(fmaf(-2.0f * cd, N.x, R.d.x), fmaf(-2.0f * cd, N.y, R.d.y), fmaf(-2.0f * cd, N.z, R.d.z));
   const V3 pm2 = cross3(sm, d2);
   V3 sf2, pf2;
   face_basis(d2, sf2, pf2);
@@ -1411,7 +1448,11 @@ __device__ void mirror_event_tilt(Ray<F>& R, int k, const Blob& B, const TraceAr
     for (int w = 0; w < 3 + 4 * F; ++w) tan_w<F>(col, to, w) = 0.0f;
     live |= 1u << to;
   }
-  // tangents (the field before the hit is still in R)
+  // tangents (the field before the hit is still in R). The field tangent is
+  // carried as the projections of dE on the current face basis,
+  // (dE.s, dE.p): then only the mirror basis is differentiated here, never
+  // the face basis, whose azimuth turns at a rate ~1/h for a direction near
+  // the face normal (the out-coupled ray of the 0 deg field).
   for (unsigned lm = live; lm; lm &= lm - 1) {
     const int t = __ffs(lm) - 1;
     const bool own = t == to;
@@ -1419,38 +1460,43 @@ __device__ void mirror_event_tilt(Ray<F>& R, int k, const Blob& B, const TraceAr
     const V3 dNt = own ? dN : v3(0.0f, 0.0f, 0.0f);
     const float dcd = dot3(dd, N) + dot3(R.d, dNt);
     acc[t * 32] += X.g_cos * (double)(front ? -dcd : dcd);  // part (1)
-    V3 dsf, dpf;
-    face_basis_d(R.d, dd, sf, dsf, dpf);
-    V3 dsm = dsf;
+    V3 dsm;
     if (!degen) {
       const V3 a = cross3(dd, N), b = cross3(R.d, dNt);
       dsm = normalize_d(w, v3(a.x + b.x, a.y + b.y, a.z + b.z));
+    } else {
+      V3 dpf;
+      face_basis_d(R.d, dd, sf, dsm, dpf);  // normal incidence: the mirror basis is the face basis
     }
-    const float dcphi = dot3(dsf, sm) + dot3(sf, dsm), dsphi = dot3(dpf, sm) + dot3(pf, dsm);
+    const V3 u1 = cross3(dsm, R.d), u2 = cross3(sm, dd);
+    const V3 dpm = v3(u1.x + u2.x, u1.y + u2.y, u1.z + u2.z);
     V3 dd2 = dd;
-    if (refl) dd2 = v3(dd.x - 2.0f * fmaf(dcd, N.x, cd * dNt.x), dd.y, dd.z - 2.0f * fmaf(dcd, N.z, cd * dNt.z));
+    if (refl)
+      dd2 = v3(dd.x - 2.0f * fmaf(dcd, N.x, cd * dNt.x), dd.y - 2.0f * fmaf(dcd, N.y, cd * dNt.y),
+               dd.z - 2.0f * fmaf(dcd, N.z, cd * dNt.z));
     const V3 e1 = cross3(dsm, d2), e2 = cross3(sm, dd2);
     const V3 dpm2 = v3(e1.x + e2.x, e1.y + e2.y, e1.z + e2.z);
-    V3 dsf2, dpf2;
-    face_basis_d(d2, dd2, sf2, dsf2, dpf2);
-    const float dcpsi = dot3(dsf2, sm) + dot3(sf2, dsm), dspsi = dot3(dsf2, pm2) + dot3(sf2, dpm2);
+    const float qs = dot3(sf, dsm), qp = dot3(pf, dsm), rs_ = dot3(sf, dpm), rp_ = dot3(pf, dpm);
+    const float us = dot3(dsm, sf2), up = dot3(dsm, pf2), vs = dot3(dpm2, sf2), vp = dot3(dpm2, pf2);
 #pragma unroll
     for (int f = 0; f < F; ++f) {
       const float2 a = R.a[f], b = R.b[f];
-      const float2 da = make_float2(tan_w<F>(col, t, 3 + 4 * f), tan_w<F>(col, t, 4 + 4 * f));
-      const float2 db = make_float2(tan_w<F>(col, t, 5 + 4 * f), tan_w<F>(col, t, 6 + 4 * f));
+      const float2 xa = make_float2(tan_w<F>(col, t, 3 + 4 * f), tan_w<F>(col, t, 4 + 4 * f));
+      const float2 xb = make_float2(tan_w<F>(col, t, 5 + 4 * f), tan_w<F>(col, t, 6 + 4 * f));
       const float2 Es = make_float2(fmaf(cphi, a.x, sphi * b.x), fmaf(cphi, a.y, sphi * b.y));
       const float2 Ep = make_float2(fmaf(-sphi, a.x, cphi * b.x), fmaf(-sphi, a.y, cphi * b.y));
-      const float2 dEs = make_float2(dcphi * a.x + cphi * da.x + dsphi * b.x + sphi * db.x,
-                                     dcphi * a.y + cphi * da.y + dsphi * b.y + sphi * db.y);
-      const float2 dEp = make_float2(-dsphi * a.x - sphi * da.x + dcphi * b.x + cphi * db.x,
-                                     -dsphi * a.y - sphi * da.y + dcphi * b.y + cphi * db.y);
+      // d(E.sm) and d(E.pm) of the incoming field
+      const float2 dEs = make_float2(cphi * xa.x + sphi * xb.x + qs * a.x + qp * b.x,
+                                     cphi * xa.y + sphi * xb.y + qs * a.y + qp * b.y);
+      const float2 dEp = make_float2(-sphi * xa.x + cphi * xb.x + rs_ * a.x + rp_ * b.x,
+                                     -sphi * xa.y + cphi * xb.y + rs_ * a.y + rp_ * b.y);
       const float2 Os = cmul(cs, Es), Op = cmul(cp, Ep);
       const float2 dOs = cmul(cs, dEs), dOp = cmul(cp, dEp);  // part (2): coefficients held
-      tan_w<F>(col, t, 3 + 4 * f) = dcpsi * Os.x + cpsi * dOs.x + dspsi * Op.x + spsi * dOp.x;
-      tan_w<F>(col, t, 4 + 4 * f) = dcpsi * Os.y + cpsi * dOs.y + dspsi * Op.y + spsi * dOp.y;
-      tan_w<F>(col, t, 5 + 4 * f) = -dspsi * Os.x - spsi * dOs.x + dcpsi * Op.x + cpsi * dOp.x;
-      tan_w<F>(col, t, 6 + 4 * f) = -dspsi * Os.y - spsi * dOs.y + dcpsi * Op.y + cpsi * dOp.y;
+      // dE' = dOs sm + dOp pm2 + Os dsm + Op dpm2, projected on (sf2, pf2)
+      tan_w<F>(col, t, 3 + 4 * f) = cpsi * dOs.x + spsi * dOp.x + us * Os.x + vs * Op.x;
+      tan_w<F>(col, t, 4 + 4 * f) = cpsi * dOs.y + spsi * dOp.y + us * Os.y + vs * Op.y;
+      tan_w<F>(col, t, 5 + 4 * f) = -spsi * dOs.x + cpsi * dOp.x + up * Os.x + vp * Op.x;
+      tan_w<F>(col, t, 6 + 4 * f) = -spsi * dOs.y + cpsi * dOp.y + up * Os.y + vp * Op.y;
     }
     tan_w<F>(col, t, 0) = dd2.x;
     tan_w<F>(col, t, 1) = dd2.y;
@@ -1513,6 +1559,7 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
         continue;
       }
       const float dz0 = R.d.z;
+      const V3 d0 = R.d;
       float2 a0[F], b0[F];
 #pragma unroll
       for (int f = 0; f < F; ++f) {
@@ -1530,17 +1577,25 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
         float2 rs, rp, drs, drp;
         tir_coef(n, ci, fmaf(-ci, ci, 1.0f), rs, rp);
         tir_coef_d(n, ci, rs, rp, drs, drp);
+        const float2 rsp = cadd(rs, rp);
+        // TIR needs sin(i) > 1/n: the face basis is well conditioned here
+        const float ih2 = 1.0f / fmaf(d0.x, d0.x, d0.y * d0.y);
         for (unsigned lm = live; lm; lm &= lm - 1) {
           const int t = __ffs(lm) - 1;
-          const float ddz = tan_w<F>(col, t, 2);
+          const float ddx = tan_w<F>(col, t, 0), ddy = tan_w<F>(col, t, 1), ddz = tan_w<F>(col, t, 2);
           const float dci = sg * ddz;
+          // the face basis turns about d at om = p . ds = -d_z dpsi; in
+          // projections the TIR map gains (r_s + r_p) om terms
+          const float om = -dz0 * fmaf(d0.x, ddy, -d0.y * ddx) * ih2;
           tan_w<F>(col, t, 2) = -ddz;
 #pragma unroll
           for (int f = 0; f < F; ++f) {
             const float2 da = make_float2(tan_w<F>(col, t, 3 + 4 * f), tan_w<F>(col, t, 4 + 4 * f));
             const float2 db = make_float2(tan_w<F>(col, t, 5 + 4 * f), tan_w<F>(col, t, 6 + 4 * f));
-            const float2 na = cadd(cmul(rs, da), cscale(cmul(drs, a0[f]), dci));
-            const float2 nb = cadd(cmul(rp, db), cscale(cmul(drp, b0[f]), dci));
+            const float2 na =
+                cadd(cadd(cmul(rs, da), cscale(cmul(drs, a0[f]), dci)), cscale(cmul(rsp, b0[f]), om));
+            const float2 nb =
+                csub(cadd(cmul(rp, db), cscale(cmul(drp, b0[f]), dci)), cscale(cmul(rsp, a0[f]), om));
             tan_w<F>(col, t, 3 + 4 * f) = na.x;
             tan_w<F>(col, t, 4 + 4 * f) = na.y;
             tan_w<F>(col, t, 5 + 4 * f) = nb.x;
@@ -1558,9 +1613,18 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
         const double g = A.G[cell * A.bins + o.bin];
         float dTs, dTp;
         exit_T_d(n, ci, dTs, dTp);
+        // om (T_s - T_p), the turn of the face basis times the s/p contrast:
+        // T_s - T_p = -4 n c_i c_t (n^2 - 1)^2 h^2 / ((n c_i + c_t)^2 (c_i + n c_t)^2)
+        // and om = -d_z (d_x dd_y - d_y dd_x) / h^2, so h^2 cancels and the
+        // term stays exact for a ray leaving along the normal
+        const float ct = sqrtf(fmaxf(1.0f - n * n * fmaf(-ci, ci, 1.0f), 0.0f));
+        const float q1 = fmaf(n, ci, ct), q2 = fmaf(n, ct, ci), nn1 = fmaf(n, n, -1.0f);
+        const float kx = 4.0f * n * ci * ct * nn1 * nn1 / (q1 * q1 * q2 * q2);
         for (unsigned lm = live; lm; lm &= lm - 1) {
           const int t = __ffs(lm) - 1;
+          const float ddx = tan_w<F>(col, t, 0), ddy = tan_w<F>(col, t, 1);
           const float dci = sg * tan_w<F>(col, t, 2);
+          const float wdt = dz0 * fmaf(d0.x, ddy, -d0.y * ddx) * kx;
           float dI = 0.0f;
 #pragma unroll
           for (int f = 0; f < F; ++f) {
@@ -1568,6 +1632,7 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
             const float2 db = make_float2(tan_w<F>(col, t, 5 + 4 * f), tan_w<F>(col, t, 6 + 4 * f));
             dI += dTs * dci * cabs2(R.a[f]) + 2.0f * o.Ts * fmaf(R.a[f].x, da.x, R.a[f].y * da.y);
             dI += dTp * dci * cabs2(R.b[f]) + 2.0f * o.Tp * fmaf(R.b[f].x, db.x, R.b[f].y * db.y);
+            dI += 2.0f * wdt * fmaf(R.a[f].x, R.b[f].x, R.a[f].y * R.b[f].y);
           }
           acc[t * 32] += g * (double)(dI * (1.0f / F));
         }
@@ -1631,14 +1696,14 @@ __global__ void __launch_bounds__(kOmegaBlock) k_omega_trace(const TraceArgs A, 
       if (sid >= S_MIR) {
         const int k = sid - S_MIR;
         const MirrorRec& M = B.mir[k];
-        const float cd = fmaf(R.d.x, M.nx, R.d.z * M.nz);
+        const float cd = fmaf(R.d.x, M.nx, fmaf(R.d.y, M.ny, R.d.z * M.nz));
         const int m = R.hits;
         const uint4 rnd = philox10(
             make_uint4((uint32_t)R.id, (uint32_t)((unsigned long long)R.id >> 32), (uint32_t)(m >> 2), TAG_EVT),
             A.key0, A.key1);
         const uint32_t word = (m & 3) == 0 ? rnd.x : (m & 3) == 1 ? rnd.y : (m & 3) == 2 ? rnd.z : rnd.w;
         const bool refl = u24(word) < M.omega;
-        if (refl) R.d = v3(fmaf(-2.0f * cd, M.nx, R.d.x), R.d.y, fmaf(-2.0f * cd, M.nz, R.d.z));
+        if (refl) R.d = v3(fmaf(-2.0f * cd, M.nx, R.d.x), fmaf(-2.0f * cd, M.ny, R.d.y), fmaf(-2.0f * cd, M.nz, R.d.z));
         R.reg = region_after(B, R.reg, k, R.d);
         R.hits = m + 1;
         if (nh < TAPE_HITS) hk[nh] = (uint8_t)(k | (refl ? 0x80 : 0));
@@ -1702,6 +1767,7 @@ cudaError_t launch_omega_trace(const TraceArgs& a, double* grad_omega, int sm_co
 // of equal length instead of waiting for its longest one. Keys: a ray head's
 // emit, a listed eyebox ray's hit count (ExitRec::pad; holes go first).
 constexpr int kHitKeys = TAPE_HITS + 1;
+static_assert(sizeof(unsigned int) * kHitKeys <= kHitSortScratch, "hit-count sort scratch");
 __device__ __forceinline__ int hit_key(const RayHead& r) { return min(max(r.emit, 0), TAPE_HITS); }
 __device__ __forceinline__ int hit_key(const ExitRec& r) { return r.flat < 0 ? 0 : min(max(r.pad, 0), TAPE_HITS); }
 
@@ -2082,9 +2148,9 @@ __global__ void __launch_bounds__(128) k_coating_grad(const uint8_t* blob, int m
 // launchers
 // ---------------------------------------------------------------------------
 cudaError_t launch_prep_design(uint8_t* blob, const float* mir_x, const float* mir_tilt, const float* mir_omega,
-                               int n_mir, float ic_tilt_deg, float thick, cudaStream_t s) {
+                               const float* geo, int n_mir, float ic_tilt_deg, float thick, cudaStream_t s) {
   note_launches(1);
-  k_prep_design<<<1, 64, 0, s>>>(blob, mir_x, mir_tilt, mir_omega, n_mir, ic_tilt_deg, thick);
+  k_prep_design<<<1, 64, 0, s>>>(blob, mir_x, mir_tilt, mir_omega, geo, n_mir, ic_tilt_deg, thick);
   return cudaGetLastError();
 }
 

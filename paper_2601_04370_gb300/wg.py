@@ -45,7 +45,8 @@ class DesignDesc(C.Structure):
                 ("material_n", C.POINTER(C.c_float)), ("mirror_x_mm", C.POINTER(C.c_float)),
                 ("mirror_tilt_deg", C.POINTER(C.c_float)), ("mirror_omega", C.POINTER(C.c_float)),
                 ("n_layers", C.POINTER(C.c_int32)), ("layer_material", C.POINTER(C.c_int32)),
-                ("layer_thickness_nm", C.POINTER(C.c_float)), ("layer_pruned", C.POINTER(C.c_uint8))]
+                ("layer_thickness_nm", C.POINTER(C.c_float)), ("layer_pruned", C.POINTER(C.c_uint8)),
+                ("mirror_geometry", C.POINTER(C.c_float))]
 
 
 class TraceCfg(C.Structure):
@@ -387,6 +388,10 @@ class Context:
                           n_layers=keep[4].ctypes.data_as(C.POINTER(C.c_int32)),
                           layer_material=keep[5].ctypes.data_as(C.POINTER(C.c_int32)),
                           layer_thickness_nm=_fptr(keep[6]), layer_pruned=keep[7].ctypes.data_as(C.POINTER(C.c_uint8)))
+        geo = getattr(D, "mirror_geo", None)
+        if geo is not None:
+            keep.append(np.ascontiguousarray(geo, dtype=np.float32).reshape(-1))
+            desc.mirror_geometry = _fptr(keep[-1])
         h = C.c_void_p()
         _check(lib().wg_create_design(self.h, C.byref(desc), C.byref(h)))
         return DesignHandle(self, h, D)
