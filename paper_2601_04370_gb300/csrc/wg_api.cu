@@ -245,7 +245,9 @@ static wg_status validate_desc(const wg_design_desc* s) {
 // host layout of the blob; geometry-derived fields are filled by k_prep_design
 static std::vector<uint8_t> build_blob(const wg_design& d) {
   const size_t off_mir = sizeof(BlobHeader);
-  const size_t off_d = align16(off_mir + sizeof(MirrorRec) * d.K);
+  // general designs: the plane-family table follows the mirror records
+  const size_t fam_bytes = d.geo.empty() ? 0 : sizeof(FamRec) * d.K;
+  const size_t off_d = align16(off_mir + sizeof(MirrorRec) * d.K + fam_bytes);
   const size_t off_m = align16(off_d + sizeof(float) * d.n_dev);
   const size_t bytes = align16(off_m + (size_t)d.n_dev + 1);
   std::vector<uint8_t> b(bytes, 0);

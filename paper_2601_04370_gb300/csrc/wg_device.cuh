@@ -60,7 +60,9 @@ struct alignas(16) BlobHeader {
   int ordered;
   // 1: general mirrors (any normal, a tilt axis, an (x, y) rectangle where
   // the plane acts); 0: PRMA planes nx x + nz z = c across the whole slab
-  int general, pad_[2];
+  int general;
+  int n_fam;  // general designs: plane families (FamRec table after the mirror records)
+  int pad_;
   float mat_inv_n[MAX_MAT];               // 1 / n
   float mat_r2[MAX_MAT];                  // (n_slab / n)^2
 };
@@ -76,14 +78,24 @@ struct alignas(16) MirrorRec {
 };
 static_assert(sizeof(MirrorRec) == 64, "mirror layout");
 
+// A family of a general design: mirrors k0 .. k0 + n - 1 with the same normal
+// (bitwise) and offsets c monotone in the index (dir = +1 increasing, -1
+// decreasing), searched by offset instead of plane by plane. Every mirror is
+// in exactly one family (a single mirror is a family of one).
+struct alignas(16) FamRec {
+  int k0, n, dir, pad;
+};
+
 struct Blob {
   const BlobHeader* h;
   const MirrorRec* mir;
+  const FamRec* fam;  // general designs: right after the mirror records
   const float* d;
   const uint8_t* m;
   __device__ __forceinline__ void bind(const uint8_t* base) {
     h = reinterpret_cast<const BlobHeader*>(base);
     mir = reinterpret_cast<const MirrorRec*>(base + h->off_mir);
+    fam = reinterpret_cast<const FamRec*>(base + h->off_mir + sizeof(MirrorRec) * h->n_mir);
     d = reinterpret_cast<const float*>(base + h->off_d);
     m = base + h->off_m;
   }
@@ -878,6 +890,48 @@ __device__ __forceinline__ void face_basis(V3 d, V3& s, V3& p) {
   p = cross3(s, d);
 }
 
+// General mirrors, family by family. Within a family the distance
+// t_i = (c_i - p.N)/(d.N) is monotone in the index, so the members are
+// visited in order of distance from the first one ahead (binary search on c)
+// until one acts (the crossing inside its rectangle) or lies beyond the
+// nearest surface so far: the same choice as testing every plane, from the
+// same t values (one normal per family). Kept out of line, so the PRMA path
+// of the trace kernels keeps its code size.
+static __device__ __noinline__ void next_mirror_general(const Blob B, V3 p, V3 d, int last, float& best, int& id) {
+  const BlobHeader& h = *B.h;
+  for (int f = 0; f < h.n_fam; ++f) {
+    const FamRec fr = B.fam[f];
+    const MirrorRec& m0 = B.mir[fr.k0];
+    const float den = fmaf(d.x, m0.nx, fmaf(d.y, m0.ny, d.z * m0.nz));
+    if (den == 0.0f) continue;
+    const float pn = fmaf(p.x, m0.nx, fmaf(p.y, m0.ny, p.z * m0.nz));
+    const bool up = den > 0.0f;  // ahead: c > p.N (den > 0) or c < p.N (den < 0)
+    const int step = (up == (fr.dir > 0)) ? 1 : -1;
+    // ahead(i) is false then true along the index for step = +1, true then
+    // false for step = -1; lo = the index where it switches
+    int lo = 0, hi = fr.n;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      const float c = B.mir[fr.k0 + mid].c;
+      const bool ahead = up ? (c > pn) : (c < pn);
+      if (ahead == (step < 0)) lo = mid + 1;
+      else hi = mid;
+    }
+    for (int i = step > 0 ? lo : lo - 1; i >= 0 && i < fr.n; i += step) {
+      const int k = fr.k0 + i;
+      const MirrorRec& m = B.mir[k];
+      const float t = __fdividef(m.c - pn, den);
+      if (!(t < best)) break;
+      if (!(t > 0.0f) || S_MIR + k == last) continue;
+      const float qx = fmaf(t, d.x, p.x), qy = fmaf(t, d.y, p.y);
+      if (!(qx >= m.x0 && qx <= m.x1 && qy >= m.y0 && qy <= m.y1)) continue;
+      best = t;
+      id = S_MIR + k;
+      break;
+    }
+  }
+}
+
 // Nearest surface along (p, d), excluding `last`. Candidate order and ties
 // match the oracle: faces, input mirror, far end, sides, mirrors.
 // Nearest surface ahead of the ray (the surface it sits on excluded). With
@@ -916,17 +970,15 @@ __device__ __forceinline__ int next_surface(const Blob& B, V3 p, V3 d, int last,
     if (dn > 0.0f) consider(S_LEFT, __fdividef(-fmaf(p.x, h.ic_nx, p.z * h.ic_nz), dn));
   }
   if (right && d.x > 0.0f) consider(S_RIGHT, __fdividef(h.x_end - p.x, d.x));
-  for (int k = k0; k < k1; ++k) {
-    const MirrorRec& m = B.mir[k];
-    const float den = fmaf(d.x, m.nx, fmaf(d.y, m.ny, d.z * m.nz));
-    if (den == 0.0f) continue;
-    const float t = __fdividef(m.c - fmaf(p.x, m.nx, fmaf(p.y, m.ny, p.z * m.nz)), den);
-    if (h.general) {
-      // a general mirror acts only inside its rectangle
-      const float qx = fmaf(t, d.x, p.x), qy = fmaf(t, d.y, p.y);
-      if (!(qx >= m.x0 && qx <= m.x1 && qy >= m.y0 && qy <= m.y1)) continue;
+  if (!h.general) {
+    for (int k = k0; k < k1; ++k) {
+      const MirrorRec& m = B.mir[k];
+      const float den = fmaf(d.x, m.nx, fmaf(d.y, m.ny, d.z * m.nz));
+      if (den == 0.0f) continue;
+      consider(S_MIR + k, __fdividef(m.c - fmaf(p.x, m.nx, fmaf(p.y, m.ny, p.z * m.nz)), den));
     }
-    consider(S_MIR + k, t);
+  } else {
+    next_mirror_general(B, p, d, last, best, id);
   }
   tmin = best;
   return id;

@@ -154,6 +154,29 @@ __global__ void k_prep_design(uint8_t* blob, const float* mir_x, const float* mi
     h->ic_nz = (float)cos(a);
     h->ic_cot = (float)(cos(a) / sin(a));
     h->general = geo != nullptr;
+    h->n_fam = 0;
+    if (geo) {
+      // families: runs of consecutive mirrors with the same normal (bitwise)
+      // and strictly monotone offsets
+      FamRec* fam = reinterpret_cast<FamRec*>(blob + h->off_mir + sizeof(MirrorRec) * n_mir);
+      int nf = 0;
+      for (int k = 0; k < n_mir;) {
+        int j = k + 1, dir = 0;
+        while (j < n_mir && mir[j].nx == mir[k].nx && mir[j].ny == mir[k].ny && mir[j].nz == mir[k].nz) {
+          const int sd = mir[j].c > mir[j - 1].c ? 1 : (mir[j].c < mir[j - 1].c ? -1 : 0);
+          if (sd == 0 || (dir != 0 && sd != dir)) break;
+          dir = sd;
+          ++j;
+        }
+        fam[nf].k0 = k;
+        fam[nf].n = j - k;
+        fam[nf].dir = dir == 0 ? 1 : dir;
+        fam[nf].pad = 0;
+        ++nf;
+        k = j;
+      }
+      h->n_fam = nf;
+    }
     // ordering of the planes along x on both faces (planes that are ordered
     // on both faces do not cross inside the slab), with a 0.1 um margin;
     // general designs test every plane
