@@ -2,6 +2,10 @@
 
   python -m paper_2601_04370_gb300.optimize --design representative --rays 1000000 --iters 300 [--omega-iters 60]
 
+--design expander optimizes the two-dimensional pupil expander (30 fold + 16
+output mirrors with 23-layer stacks: 1058 thicknesses, the scale of the
+paper's design) instead of the six-mirror array (--layers does not apply).
+
 With --omega-iters, the reflection probabilities are pre-optimized first
 (Methods, "Learned reflection probabilities": scalar-reflectance geometric
 model, throughput to the pupils). Starts from thicknesses drawn from a
@@ -21,7 +25,7 @@ import time
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("--design", choices=("tiny", "representative"), default="representative")
+    ap.add_argument("--design", choices=("tiny", "representative", "expander"), default="representative")
     ap.add_argument("--rays", type=int, default=1_000_000)
     ap.add_argument("--layers", type=int, default=40)
     ap.add_argument("--iters", type=int, default=300)
@@ -38,6 +42,8 @@ def main(argv=None):
 
     if args.design == "tiny":
         D, C = W.tiny(n_rays=args.rays)
+    elif args.design == "expander":
+        D, C = W.pupil_expander(n_rays=args.rays)
     else:
         D, C = W.representative(n_rays=args.rays, n_layers=args.layers)
     D = W.with_thickness(D, W.gaussian_thickness(D, seed=args.seed))

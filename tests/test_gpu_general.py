@@ -111,6 +111,23 @@ def test_full_size_expander_sampled(ctx, ora):
     assert abs(g["stats"]["ledger"].sum() - N) <= 6 * np.sqrt((w ** 2).sum())
 
 
+def test_general_geometry_is_validated(ctx):
+    """The descriptor's general rows are checked before anything is uploaded:
+    unit normal and axis, axis perpendicular to the normal, a non-empty
+    rectangle, finite values."""
+    from paper_2601_04370_gb300 import wg
+    D, _ = W.pupil_expander_small()
+    bad = []
+    g = D.mirror_geo.copy(); g[0, 0:3] *= 1.1; bad.append(g)            # normal not unit
+    g = D.mirror_geo.copy(); g[1, 6:9] = [1.0, 0.0, 0.0]; bad.append(g)  # axis not perpendicular (fold normal has x)
+    g = D.mirror_geo.copy(); g[2, 9:11] = [3.0, 2.0]; bad.append(g)      # x0 > x1
+    g = D.mirror_geo.copy(); g[3, 4] = np.nan; bad.append(g)             # pivot not finite
+    for gb in bad:
+        with pytest.raises(wg.WGError) as e:
+            ctx.create_design(D.replace(mirror_geo=gb))
+        assert e.value.status == wg.WG_EINVAL
+
+
 def test_served_general_and_prma_designs_match_direct_calls(ctx):
     Dg, Cg = W.pupil_expander_small()
     Dp, Cp = W.representative(n_rays=1728 * 4, n_layers=8)
