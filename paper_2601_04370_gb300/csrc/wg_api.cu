@@ -109,7 +109,19 @@ struct wg_design {
   DevBuf exits;
   uint64_t exit_fp = 0;
   long long exit_cap = 0;  // entries of the list (rays + hole allowance)
+  // applied coefficients of the first kCoefSlots hits of every ray of the
+  // last listing forward (TraceArgs::coef), valid for the paths with
+  // fingerprint coef_fp, the thicknesses of version coef_thick and the
+  // coating table size coef_lut
+  DevBuf coefs;
+  uint64_t coef_fp = 0;
+  int coef_thick = -1, coef_lut = 0;
+  long long coef_base = 0, coef_rays = 0;
+  int thick_version = 0;  // bumped whenever the thicknesses change
 };
+
+// hits per ray whose coefficients the listing forward keeps for the replay
+constexpr int kCoefSlots = 8;
 
 static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -166,6 +178,8 @@ static void destroy_design_dev(wg_design* d) {
   if (d->d_stage) cudaFree(d->d_stage);
   d->exits.release();
   d->exit_fp = 0;
+  d->coefs.release();
+  d->coef_fp = 0;
   d->blob = nullptr;
 }
 
@@ -426,6 +440,7 @@ extern "C" wg_status wg_set_params(wg_design* d, const float* thickness_nm, int6
       CU(cudaMemcpyAsync(d->d_stage, thickness_nm, sizeof(float) * d->n_orig, cudaMemcpyHostToDevice, s));
     }
     CU(launch_thickness_update(d->blob, d->d_stage, d->d_orig_to_dev, d->n_orig, s));
+    ++d->thick_version;  // the coefficients kept by the last listing forward are stale
   }
   if (tilt_deg) {
     if (n_tilt != d->K) return fail(WG_EINVAL, "wg_set_params: %d tilts for %d mirrors", n_tilt, d->K);
@@ -817,11 +832,32 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
   if (st != WG_OK) return st;
   st = prepare_lut(c, d, cfg, w, s, a);
   if (st != WG_OK) return st;
+  // a listing forward keeps each hit's applied coefficients for the replay
+  // (a forward without the list leaves the kept ones as they are)
+  if (!(cfg->flags & WG_TRACE_NO_EXIT_LIST)) dm->coef_fp = 0;
+  if (a.exit_list) {
+    const size_t cb = sizeof(float4) * kCoefSlots * (size_t)(p.re - p.rb);
+    if (cb <= ((size_t)8 << 30)) {
+      if (cb > dm->coefs.n) CU(dm->coefs.ensure(cb));
+      a.coef = static_cast<float4*>(dm->coefs.p);
+      a.coef_base = p.rb;
+      a.coef_rays = p.re - p.rb;
+      a.coef_slots = kCoefSlots;
+      a.coef_mode = 1;
+    }
+  }
   const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, d->period, smem));
   const int grid = (int)std::min<long long>(p.n_chunks, (long long)c->sm_count * bps);
   if (stats) CU(cudaEventRecord(c->t0, s));
   CU(launch_trace_fwd(a, p.F, d->period, grid, smem, s));
   if (a.exit_list) dm->exit_fp = path_fingerprint(d, cfg, p);
+  if (a.coef_mode == 1) {
+    dm->coef_fp = dm->exit_fp;
+    dm->coef_thick = d->thick_version;
+    dm->coef_lut = cfg->lut_bins;
+    dm->coef_base = p.rb;
+    dm->coef_rays = p.re - p.rb;
+  }
   if (stats) CU(cudaEventRecord(c->t1, s));
   CU(cudaEventRecord(c->ws_free, s));
   if (!dev_tally) {
@@ -1331,6 +1367,10 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     list = sorted;
   }
   const long long w_begin = use_list ? 0 : p.rb, w_end = use_list ? n_list : p.re;
+  // the listing forward's coefficients, if they are those of these paths,
+  // thicknesses and coating table
+  const bool use_coef = d->coef_fp != 0 && d->coef_fp == path_fingerprint(d, cfg, p) &&
+                        d->coef_thick == d->thick_version && d->coef_lut == cfg->lut_bins;
   float ms_total = 0.f, ms_replay = 0.f, ms_adjoint = 0.f, ms_tilt = 0.f;
   int n_adj_launches = 0;
   for (long long b0 = w_begin; b0 < w_end;) {
@@ -1338,6 +1378,13 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     Plan q = p;
     if (!use_list) plan_range(q, b0, b1);
     TraceArgs a = base_args(d, cfg, q, w);
+    if (use_coef) {
+      a.coef = static_cast<float4*>(d->coefs.p);
+      a.coef_base = d->coef_base;
+      a.coef_rays = d->coef_rays;
+      a.coef_slots = kCoefSlots;
+      a.coef_mode = 2;
+    }
     if (use_list) {
       a.replay_list = list;
       a.list_begin = b0;

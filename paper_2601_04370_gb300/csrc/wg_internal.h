@@ -95,6 +95,15 @@ struct TraceArgs {
   float lut_c0, lut_inv_dc;
   // backward with the table: FP64 dL/d(coefficient) per entry, {r_s, r_p, t_s, t_p} x {re, im}
   double* lut_grad;
+  // Applied coefficients (c_s, c_p as a float4) of the first coef_slots
+  // mirror hits of every ray of a listing forward, at
+  // (ray - coef_base) * coef_slots + hit (a ray's hits share a line for the
+  // replay, which reads them in order): written by the forward (coef_mode 1)
+  // and read back by the replay (coef_mode 2), which then skips those hits'
+  // layer chains; 0: not used.
+  float4* coef;
+  long long coef_base, coef_rays;
+  int coef_slots, coef_mode;
 };
 
 // Arguments of the thin-film adjoint over sorted hit records.

@@ -416,7 +416,9 @@ __device__ __forceinline__ float2 lerp2(float2 a, float2 b, float f) {
 }
 
 // li: wavelength index of the hit (the coating table's, when A.lut is set)
-template <int F, int P>
+// CM: 1 in the forward (may keep the applied coefficients, TraceArgs::coef),
+// 2 in the replay (may read them back); the other direction is compiled out.
+template <int F, int P, int CM>
 __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob& B, float lam, int li,
                                                    const TraceArgs& A, int& layer_steps, float2* Es_out,
                                                    float2* Ep_out) {
@@ -427,8 +429,14 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
   MirrorStep st;
   st.front = cd < 0.0f;
   st.cos0 = fabsf(cd);
+  // the listing forward's applied coefficients of this hit, when kept
+  const int m = R.hits;
+  const bool kept = CM == 2 && A.coef_mode == 2 && m < A.coef_slots;
   Coef cf;
-  if (A.lut) {
+  float4 kv;
+  if (kept) {
+    kv = A.coef[(R.id - A.coef_base) * A.coef_slots + m];
+  } else if (A.lut) {
     int j;
     float f;
     lut_locate(A, st.cos0, j, f);
@@ -444,6 +452,27 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
     const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
     cf = tmm_forward<P>(sv, st.front, mt, H.n_slab, st.cos0, layer_steps);
   }
+  // hit m draws word m & 3 of the block for counter (ray, m >> 2); the block
+  // is recomputed per hit so the ray state needs no RNG words
+  const uint4 rnd = philox10(
+      make_uint4((uint32_t)R.id, (uint32_t)((unsigned long long)R.id >> 32), (uint32_t)(m >> 2), TAG_EVT), A.key0,
+      A.key1);
+  const uint32_t word = (m & 3) == 0 ? rnd.x : (m & 3) == 1 ? rnd.y : (m & 3) == 2 ? rnd.z : rnd.w;
+  st.refl = u24(word) < M.omega;
+  if (kept) {
+    st.cs = make_float2(kv.x, kv.y);
+    st.cp = make_float2(kv.z, kv.w);
+  } else {
+    if (st.refl) {
+      st.cs = cscale(cf.rs, M.isw);
+      st.cp = cscale(cf.rp, M.isw);
+    } else {
+      st.cs = cscale(cf.ts, M.is1w);
+      st.cp = cscale(cf.tp, M.is1w);
+    }
+    if (CM == 1 && A.coef_mode == 1 && m < A.coef_slots)
+      A.coef[(R.id - A.coef_base) * A.coef_slots + m] = make_float4(st.cs.x, st.cs.y, st.cp.x, st.cp.y);
+  }
   V3 sf, pf;
   face_basis(R.d, sf, pf);
   V3 sm = cross3(R.d, N);
@@ -456,23 +485,8 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
   }
   st.cphi = dot3(sf, sm);
   st.sphi = dot3(pf, sm);
-  // hit m draws word m & 3 of the block for counter (ray, m >> 2); the block
-  // is recomputed per hit so the ray state needs no RNG words
-  const int m = R.hits;
-  const uint4 rnd = philox10(
-      make_uint4((uint32_t)R.id, (uint32_t)((unsigned long long)R.id >> 32), (uint32_t)(m >> 2), TAG_EVT), A.key0,
-      A.key1);
-  const uint32_t word = (m & 3) == 0 ? rnd.x : (m & 3) == 1 ? rnd.y : (m & 3) == 2 ? rnd.z : rnd.w;
-  st.refl = u24(word) < M.omega;
   V3 d2 = R.d;
-  if (st.refl) {
-    st.cs = cscale(cf.rs, M.isw);
-    st.cp = cscale(cf.rp, M.isw);
-    d2 = v3(fmaf(-2.0f * cd, N.x, R.d.x), fmaf(-2.0f * cd, N.y, R.d.y), fmaf(-2.0f * cd, N.z, R.d.z));
-  } else {
-    st.cs = cscale(cf.ts, M.is1w);
-    st.cp = cscale(cf.tp, M.is1w);
-  }
+  if (st.refl) d2 = v3(fmaf(-2.0f * cd, N.x, R.d.x), fmaf(-2.0f * cd, N.y, R.d.y), fmaf(-2.0f * cd, N.z, R.d.z));
   const V3 pm2 = cross3(sm, d2);
   V3 sf2, pf2;
   face_basis(d2, sf2, pf2);
@@ -990,7 +1004,7 @@ __global__ void __launch_bounds__(kBlock, 2)
       bool fin = false, keep = false;
       if ((unsigned)lane < n) {
         slot = q_get<F>(mq, (mh + lane) % kQCap, R, A.ray_begin);
-        mirror_event<F, P>(R, R.last - S_MIR, B, S.slot[slot].cc.lam, (int)(S.slot[slot].cc.cell / A.n_f), A, c_steps,
+        mirror_event<F, P, 1>(R, R.last - S_MIR, B, S.slot[slot].cc.lam, (int)(S.slot[slot].cc.cell / A.n_f), A, c_steps,
                            nullptr, nullptr);
         if (R.ev >= A.max_events) {
           fin = true;
@@ -1358,7 +1372,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
         if (at_mir) {
           const int h = R.hits;
           float2 Es[F], Ep[F];
-          const MirrorStep ms = mirror_event<F, P>(R, hit_k, B, lam_l, (int)(cell_l / A.n_f), A, c_steps, Es, Ep);
+          const MirrorStep ms = mirror_event<F, P, 2>(R, hit_k, B, lam_l, (int)(cell_l / A.n_f), A, c_steps, Es, Ep);
           if (h < TAPE_HITS) {
             TapeE<F>& E = tape[h];
             E.cs = ms.cs;
