@@ -833,9 +833,10 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
   st = prepare_lut(c, d, cfg, w, s, a);
   if (st != WG_OK) return st;
   // a listing forward keeps each hit's applied coefficients for the replay
-  // (a forward without the list leaves the kept ones as they are)
+  // (a forward without the list leaves the kept ones as they are); not with
+  // the coating table, whose coefficients cost the replay two loads per hit
   if (!(cfg->flags & WG_TRACE_NO_EXIT_LIST)) dm->coef_fp = 0;
-  if (a.exit_list) {
+  if (a.exit_list && cfg->lut_bins <= 0) {
     const size_t cb = sizeof(float4) * kCoefSlots * (size_t)(p.re - p.rb);
     if (cb <= ((size_t)8 << 30)) {
       if (cb > dm->coefs.n) CU(dm->coefs.ensure(cb));

@@ -67,8 +67,9 @@ def test_thickness_update_between_forward_and_backward(ctx, ora):
 
 
 def test_coating_method_change_between_forward_and_backward(ctx, ora):
-    """A table forward's coefficients are not the exact ones: an exact
-    backward after it re-runs the chains."""
+    """A table forward keeps no coefficients (and a kept exact set from an
+    earlier forward is not the table's): an exact backward after it re-runs
+    the chains."""
     D, C = W.representative(n_rays=1728 * 8, n_layers=40)
     dh = ctx.create_design(D)
     G = _fwd_loss(ctx, dh, C.replace(lut_bins=4096))
