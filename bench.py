@@ -85,9 +85,11 @@ def profile_traffic(kernel):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 50 ms, timestamped) around the timed region;
+    start() returns once samples are being written, and the summary counts
+    the samples that fall inside the window given to stop()."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -101,41 +103,56 @@ class Clocks:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.device), "-lms", "200"], stdout=self.fh,
+                                          "-i", str(self.device), "-lms", "50"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
+            t0 = time.time()
+            while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
 
-    def stop(self):
+    def stop(self, window=None):
+        """window: (t0, t1) host times (time.time()) of the timed region."""
         if not self.proc:
             return None
+        time.sleep(0.1)  # a sample after the window
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.fh.close()
+        import datetime
         rows = []
         for line in open(self.path):
             v = [x.strip() for x in line.split(",")]
-            if len(v) < 9:
+            if len(v) < 10:
                 continue
             try:
-                rows.append(dict(sm=float(v[1]), smax=float(v[2]), power=float(v[3]), hw=v[5], hwt=v[6], swt=v[7],
-                                 swp=v[8]))
+                ts = datetime.datetime.strptime(v[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = None
+            try:
+                rows.append(dict(ts=ts, sm=float(v[2]), smax=float(v[3]), power=float(v[4]), hw=v[6], hwt=v[7],
+                                 swt=v[8], swp=v[9]))
             except ValueError:
                 continue
         if not rows:
             return None
+        inside = rows
+        if window is not None:
+            w = [r for r in rows if r["ts"] is not None and window[0] - 0.06 <= r["ts"] <= window[1] + 0.06]
+            inside = w or rows
         smax = max(r["smax"] for r in rows)
-        load = [r for r in rows if r["power"] > 200.0] or rows
+        load = [r for r in inside if r["power"] > 200.0] or inside
         reasons = []
         for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"), ("swt", "sw_thermal_slowdown"),
                           ("swp", "sw_power_cap")):
-            if any(r[key].lower().startswith("active") for r in rows):
+            if any(r[key].lower().startswith("active") for r in inside):
                 reasons.append(name)
         return {"sm_mhz": statistics.median(r["sm"] for r in load), "sm_max_mhz": smax, "reasons": reasons,
-                "samples": len(rows), "samples_under_load": len(load)}
+                "samples": len(rows), "samples_in_timed_region": len(inside), "samples_under_load": len(load),
+                "interval_ms": 50}
 
 
 def dist_setup(args):
@@ -373,15 +390,17 @@ def run_ours(args):
     clocks.start()
     n0 = wg.kernel_launches()
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    t_win0 = time.time()
     t_wall0 = time.perf_counter()
     for i in range(args.steps):
         step(evs[i], keep=True)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
+    t_win1 = time.time()
     barrier(pg, dev)
     torch.cuda.synchronize()
     launches = wg.kernel_launches() - n0
-    ck = clocks.stop()
+    ck = clocks.stop(window=(t_win0, t_win1))
     step_ms = [e[0].elapsed_time(e[3]) for e in evs]
     fwd_ms = [e[0].elapsed_time(e[1]) for e in evs]
     bwd_ms = [e[2].elapsed_time(e[3]) for e in evs]
