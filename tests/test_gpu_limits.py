@@ -1,0 +1,80 @@
+"""Parity at the limits the boundary accepts and at degenerate coatings:
+64 mirrors (the most a design may have; up to ~32 mirror hits per ray),
+512 layers per mirror (the most a mirror may carry), a mirror with no layers
+and a mirror whose layers are all pruned (a bare glass-glass plane: r = 0,
+t = 1)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2601_04370_gb300 import workloads as W
+
+from test_gpu_parity import _grad_compare, compare, ctx, run_gpu  # noqa: F401 (fixture)
+
+pytestmark = pytest.mark.gpu
+
+
+def _fwd_bwd(ctx, D, C):
+    dh = ctx.create_design(D)
+    g = run_gpu(ctx, D, C, dh=dh)
+    tally = torch.as_tensor(g["tally"], device="cuda")
+    G = torch.zeros_like(tally)
+    ctx.loss(dh, C, tally, G)
+    grad = torch.zeros(D.total_layers, dtype=torch.float64, device="cuda")
+    gt = np.zeros(D.n_mirrors)
+    st = ctx.trace_backward(dh, C, G, grad, grad_tilt=gt)
+    dh.destroy()
+    return g, G.cpu().numpy(), grad.cpu().numpy(), gt, st
+
+
+def test_64_mirrors(ctx, ora):
+    D = W._prma_design(2, 1.71, 1.0, 64, 4, [W.N_SIO2, W.N_TIO2], seed=6, spacing=1.0)
+    _, C = W.tiny(n_rays=4000)
+    C = C.replace(max_events=128, eb_cx_mm=float(D.mirror_x_mm[:8].mean()))
+    g, G, gd, gt, st = _fwd_bwd(ctx, D, C)
+    assert g["stats"]["n_hits"] > 20 * C.total_rays   # long paths through the array
+    compare(C, g, ora.trace(D, C, records=True))
+    assert st["overflow"] == 0 and st["n_nonfinite"] == 0
+    ref_d, ref_t = ora.trace_grad(D, C, G)
+    _grad_compare(gd, ref_d)
+    assert np.linalg.norm(gt - ref_t) <= 1e-3 * np.linalg.norm(ref_t)
+
+
+def test_512_layers_per_mirror(ctx, ora):
+    """Tallies hold 1e-4. Gradients: the 1e-3 bound holds to 200 layers (the
+    largest configuration, tests in test_gpu_parity.py); at 512 layers the FP32
+    conditioning of single coatings widens (per-hit relative error p99 3e-3 to
+    7e-3 against 1e-3 to 3e-3 at 200 layers, measured against the oracle), and
+    the traced gradient sits near 1e-2, so the bound here is 3e-2."""
+    D = W._prma_design(3, 1.71, 1.5, 2, 512, [W.N_SIO2, W.N_TIO2, W.N_TA2O5], seed=5)
+    _, C = W.representative(n_rays=3000, n_layers=8)
+    C = C.replace(fx_deg=[-12.0, 0.5, 9.0], fy_deg=[-6.0, 4.0], eb_nx=16, eb_ny=12, n_rays=3000,
+                  eb_cx_mm=float(D.mirror_x_mm.mean()))
+    g, G, gd, gt, st = _fwd_bwd(ctx, D, C)
+    compare(C, g, ora.trace(D, C, records=True), ray_tol=1e-3)
+    assert st["overflow"] == 0 and st["n_nonfinite"] == 0
+    ref_d, ref_t = ora.trace_grad(D, C, G)
+    assert np.all(np.isfinite(gd))
+    assert np.linalg.norm(gd - ref_d) <= 3e-2 * np.linalg.norm(ref_d)
+    assert np.linalg.norm(gt - ref_t) <= 3e-2 * np.linalg.norm(ref_t)
+
+
+@pytest.mark.parametrize("kind", ["no_layers", "all_pruned"])
+def test_bare_mirror(ctx, ora, kind):
+    D, C = W.tiny(n_rays=4000)
+    if kind == "no_layers":
+        D = D.replace(n_layers=np.array([0, 8], np.int32), layer_mat=D.layer_mat[8:], layer_d_nm=D.layer_d_nm[8:],
+                      pruned=np.zeros(8, np.uint8))
+    else:
+        pr = D.pruned.copy()
+        pr[:8] = 1
+        d = D.layer_d_nm.copy()
+        d[:8] = 0.0
+        D = D.replace(pruned=pr, layer_d_nm=d)
+    g, G, gd, gt, st = _fwd_bwd(ctx, D, C)
+    compare(C, g, ora.trace(D, C, records=True))
+    ref_d, ref_t = ora.trace_grad(D, C, G)
+    _grad_compare(gd, ref_d)
+    assert np.linalg.norm(gt - ref_t) <= 1e-3 * np.linalg.norm(ref_t)
+    if kind == "all_pruned":
+        assert np.all(gd[:8] == 0.0)
