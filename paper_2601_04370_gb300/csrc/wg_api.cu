@@ -109,19 +109,25 @@ struct wg_design {
   DevBuf exits;
   uint64_t exit_fp = 0;
   long long exit_cap = 0;  // entries of the list (rays + hole allowance)
-  // applied coefficients of the first kCoefSlots hits of every ray of the
+  // applied coefficients of the first coef_slots hits of every ray of the
   // last listing forward (TraceArgs::coef), valid for the paths with
   // fingerprint coef_fp, the thicknesses of version coef_thick and the
   // coating table size coef_lut
   DevBuf coefs;
   uint64_t coef_fp = 0;
-  int coef_thick = -1, coef_lut = 0;
+  int coef_thick = -1, coef_lut = 0, coef_slots = 0;
   long long coef_base = 0, coef_rays = 0;
   int thick_version = 0;  // bumped whenever the thicknesses change
 };
 
-// hits per ray whose coefficients the listing forward keeps for the replay
-constexpr int kCoefSlots = 8;
+// hits per ray whose coefficients the listing forward keeps for the replay:
+// 8 (a PRMA ray meets ~4 mirrors), 32 for designs of more than 8 mirrors,
+// fewer when the store would pass 8 GB
+static int coef_slots_for(int n_mirrors, long long rays) {
+  const int want = n_mirrors > 8 ? 32 : 8;
+  const long long fit = (8ll << 30) / (16ll * std::max(1ll, rays));
+  return (int)std::min<long long>(want, fit);
+}
 
 static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -837,13 +843,14 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
   // the coating table, whose coefficients cost the replay two loads per hit
   if (!(cfg->flags & WG_TRACE_NO_EXIT_LIST)) dm->coef_fp = 0;
   if (a.exit_list && cfg->lut_bins <= 0) {
-    const size_t cb = sizeof(float4) * kCoefSlots * (size_t)(p.re - p.rb);
-    if (cb <= ((size_t)8 << 30)) {
+    const int slots = coef_slots_for(d->K, p.re - p.rb);
+    if (slots > 0) {
+      const size_t cb = sizeof(float4) * (size_t)slots * (size_t)(p.re - p.rb);
       if (cb > dm->coefs.n) CU(dm->coefs.ensure(cb));
       a.coef = static_cast<float4*>(dm->coefs.p);
       a.coef_base = p.rb;
       a.coef_rays = p.re - p.rb;
-      a.coef_slots = kCoefSlots;
+      a.coef_slots = slots;
       a.coef_mode = 1;
     }
   }
@@ -858,6 +865,7 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
     dm->coef_lut = cfg->lut_bins;
     dm->coef_base = p.rb;
     dm->coef_rays = p.re - p.rb;
+    dm->coef_slots = a.coef_slots;
   }
   if (stats) CU(cudaEventRecord(c->t1, s));
   CU(cudaEventRecord(c->ws_free, s));
@@ -1410,7 +1418,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
       a.coef = static_cast<float4*>(d->coefs.p);
       a.coef_base = d->coef_base;
       a.coef_rays = d->coef_rays;
-      a.coef_slots = kCoefSlots;
+      a.coef_slots = d->coef_slots;
       a.coef_mode = 2;
     }
     if (use_list) {
