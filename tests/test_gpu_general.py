@@ -163,3 +163,35 @@ def test_tilt_gradient_with_rays_leaving_along_the_normal(ctx, ora):
     _, ref_t = ora.trace_grad(D, C, G.cpu().numpy())
     assert np.linalg.norm(gt - ref_t) <= 1e-3 * np.linalg.norm(ref_t), (gt, ref_t)
     dh.destroy()
+
+
+def test_expander_omega_trace_matches_oracle(ctx, ora):
+    """The geometric trace of the omega pre-optimization with general mirrors
+    (fold and output reflections in 3D) against the oracle's."""
+    D, C = W.pupil_expander_small(n_rays=40_000)
+    om = np.linspace(0.2, 0.8, D.n_mirrors).astype(np.float32)
+    dh = ctx.create_design(D)
+    dh.set_omega(om)
+    Do = D.replace(mirror_omega=om)
+    tally = torch.zeros(C.tally_shape, dtype=torch.float64, device="cuda")
+    G = torch.zeros_like(tally)
+    ctx.loss(dh, C, tally, G, w_f=0.0, w_e=0.0)
+    g = np.zeros(D.n_mirrors)
+    ctx.omega_trace(dh, C, tally, G, g)
+    ref_t, ref_g = ora.geo_trace(Do, C, G=G.cpu().numpy())
+    t = tally.cpu().numpy()
+    assert np.abs(t - ref_t).max() <= 1e-4 * np.abs(ref_t).max()
+    assert np.linalg.norm(g - ref_g) <= 1e-3 * np.linalg.norm(ref_g), (g, ref_g)
+    dh.destroy()
+
+
+def test_expander_noalloc_forward_matches_trace_forward(ctx):
+    D, C = W.pupil_expander_small()
+    dh = ctx.create_design(D)
+    a = torch.zeros(C.tally_shape, dtype=torch.float64, device="cuda")
+    b = torch.zeros_like(a)
+    ctx.trace_forward(dh, C, a)
+    ctx.trace_forward_noalloc(dh, C, b)
+    a, b = a.cpu().numpy(), b.cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max()
+    dh.destroy()
