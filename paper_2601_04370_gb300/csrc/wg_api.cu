@@ -1249,7 +1249,7 @@ struct BwdScratch {
   long long cap;
 };
 
-static const long long kRecordsPerRay = 16;  // record capacity per ray of a batch (mean ~2)
+static const long long kRecordsPerRay = 16;  // record capacity per ray of a batch without the list (the list gives exact counts)
 static const long long kReplayUnit = 64;     // rays per work unit of the replay kernel
 
 extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, const double* dL_dtally,

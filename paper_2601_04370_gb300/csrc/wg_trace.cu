@@ -1084,7 +1084,9 @@ __global__ void __launch_bounds__(kBlock, 2)
 // ---------------------------------------------------------------------------
 // K3: adjoint, in three kernels with their own register budgets.
 //
-// k_bwd_replay: the forward trace again from the same keys, with a per-ray
+// k_bwd_replay: the forward trace again from the same keys (the applied
+//   coefficients of a ray's first hits read back from the listing forward,
+//   TraceArgs::coef, instead of re-running their layer chains), with a per-ray
 //   tape of mirror hits in local memory (incoming field, applied
 //   coefficients, basis rotations, TIR products since the previous hit). A
 //   ray that ends in the eyebox seeds dL/dE* = G[bin]/F (T_s a, T_p b),
@@ -1098,6 +1100,8 @@ __global__ void __launch_bounds__(kBlock, 2)
 //   the warp's 32 records share a stack every layer step touches the same
 //   gradient entry in all lanes, which is reduced with shuffles and added
 //   once; partial FP32 sums in shared memory go to FP64 after each chunk.
+//   With the tilt gradient the reverse sweep also forms each record's
+//   dL/d(cos theta_0) (tmm_adjoint<..., DUAL>).
 // ---------------------------------------------------------------------------
 template <int F>
 struct TapeE {
