@@ -210,14 +210,16 @@ WORKLOAD_NAME = ("representative fwd+loss+adjoint: 3D slab n=1.71 t=1.5mm, 6 PRM
 
 def cpu_oracle_rate(D, C, G, budget_s=12.0, max_rays=None):
     """Oracle (FP64 CPU) forward + adjoint on a bounded sample of the same
-    workload: rays spread over all cells (blocks of 16 rays per cell stride)."""
+    workload: the first k rays of each of m cells spread evenly over the
+    grid, k grown to a whole cell and then m, until the sample takes about
+    the budget (small samples are dominated by per-call thread start-up)."""
     from oracle import oracle as O
     nthreads = O.hardware_threads()
 
-    cells = list(range(0, C.n_cells, max(1, C.n_cells // 64)))
+    def cells_of(m):
+        return list(range(0, C.n_cells, max(1, C.n_cells // m)))[:m]
 
-    def run(k):
-        # sample: the first k rays of each of 64 cells spread over the grid
+    def run(k, cells):
         hits = 0
         t0 = time.perf_counter()
         for cell in cells:
@@ -227,20 +229,22 @@ def cpu_oracle_rate(D, C, G, budget_s=12.0, max_rays=None):
             O.trace_grad(D, C, G, rays=(r0, r0 + k), nthreads=nthreads)
         return hits, time.perf_counter() - t0
 
-    run(2)  # one-time costs (library load, host threads) stay out of the calibration
-    # grow the sample until it takes about the budget (small samples are
-    # dominated by per-call thread start-up, so one extrapolation falls short)
+    m = min(64, C.n_cells)
+    run(2, cells_of(m))  # one-time costs (library load, host threads) stay out of the calibration
     k = 8
-    h, t = run(k)
-    while t < 0.5 * budget_s and k < C.n_cell:
-        k = int(min(C.n_cell, max(2 * k, k * budget_s / max(t, 1e-3))))
-        if max_rays:
-            k = min(k, max(1, max_rays // len(cells)))
-        h, t = run(k)
-        if max_rays and k >= max_rays // len(cells):
+    h, t = run(k, cells_of(m))
+    limit = max_rays if max_rays else 1 << 62
+    while t < 0.5 * budget_s and k * m < limit:
+        grow = max(2.0, budget_s / max(t, 1e-3))
+        if k < C.n_cell:
+            k = int(min(C.n_cell, k * grow, max(1, limit // m)))
+        elif m < C.n_cells:
+            m = int(min(C.n_cells, m * grow, max(1, limit // k)))
+        else:
             break
+        h, t = run(k, cells_of(m))
     return dict(value=h / t, unit=UNIT, cores=nthreads, kind="oracle",
-                sample=f"{k * len(cells)} rays ({k} per cell from {len(cells)} of {C.n_cells} cells), "
+                sample=f"{k * m} rays ({k} per cell from {m} of {C.n_cells} cells), "
                        f"FP64 forward + adjoint, {t:.1f} s wall on {nthreads} host threads"), h, t
 
 
