@@ -208,11 +208,13 @@ WORKLOAD_NAME = ("representative fwd+loss+adjoint: 3D slab n=1.71 t=1.5mm, 6 PRM
                  "random linear pol, 1e7 rays per GPU, 64x48 eyebox bins, max 100 events")
 
 
-def cpu_oracle_rate(D, C, G, budget_s=12.0, max_rays=None):
+def cpu_oracle_rate(D, C, G, budget_s=12.0, max_rays=None, sample=None):
     """Oracle (FP64 CPU) forward + adjoint on a bounded sample of the same
     workload: the first k rays of each of m cells spread evenly over the
     grid, k grown to a whole cell and then m, until the sample takes about
-    the budget (small samples are dominated by per-call thread start-up)."""
+    the budget (small samples are dominated by per-call thread start-up).
+    sample=(k, m) reuses a calibrated sample size. Returns (record, hits,
+    seconds, (k, m))."""
     from oracle import oracle as O
     nthreads = O.hardware_threads()
 
@@ -229,6 +231,12 @@ def cpu_oracle_rate(D, C, G, budget_s=12.0, max_rays=None):
             O.trace_grad(D, C, G, rays=(r0, r0 + k), nthreads=nthreads)
         return hits, time.perf_counter() - t0
 
+    if sample is not None:
+        k, m = sample
+        h, t = run(k, cells_of(m))
+        return dict(value=h / t, unit=UNIT, cores=nthreads, kind="oracle",
+                    sample=f"{k * m} rays ({k} per cell from {m} of {C.n_cells} cells), "
+                           f"FP64 forward + adjoint, {t:.1f} s wall on {nthreads} host threads"), h, t, (k, m)
     m = min(64, C.n_cells)
     run(2, cells_of(m))  # one-time costs (library load, host threads) stay out of the calibration
     k = 8
@@ -245,7 +253,7 @@ def cpu_oracle_rate(D, C, G, budget_s=12.0, max_rays=None):
         h, t = run(k, cells_of(m))
     return dict(value=h / t, unit=UNIT, cores=nthreads, kind="oracle",
                 sample=f"{k * m} rays ({k} per cell from {m} of {C.n_cells} cells), "
-                       f"FP64 forward + adjoint, {t:.1f} s wall on {nthreads} host threads"), h, t
+                       f"FP64 forward + adjoint, {t:.1f} s wall on {nthreads} host threads"), h, t, (k, m)
 
 
 def run_serving(dev, n_requests, max_slots, cache_path):
@@ -308,10 +316,10 @@ def run_reference(args):
     rng = np.random.default_rng(0)
     G = rng.normal(size=C.tally_shape) / C.n_cell
     per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
-    base, h, t = cpu_oracle_rate(D, C, G, budget_s=per_step)
+    base, h, t, smp = cpu_oracle_rate(D, C, G, budget_s=per_step)
     rates = []
     for i in range(args.warmup + args.steps):
-        b, h, t = cpu_oracle_rate(D, C, G, budget_s=per_step)
+        b, h, t, _ = cpu_oracle_rate(D, C, G, sample=smp)
         if i >= args.warmup:
             rates.append((h, t))
     H = sum(h for h, _ in rates)
@@ -508,7 +516,7 @@ def run_ours(args):
                     "interactions_per_step": e_hits, "hits_per_ray": e_hits / CE.total_rays,
                     "overflow": sbe["overflow"], "nonfinite": sbe["n_nonfinite"]}
         if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-            expander["cpu_baseline"], _, _ = cpu_oracle_rate(DE, CE, Ge.cpu().numpy(),
+            expander["cpu_baseline"], _, _, _ = cpu_oracle_rate(DE, CE, Ge.cpu().numpy(),
                                                              budget_s=max(2.0, args.cpu_budget / 3))
         dhe.destroy()
 
@@ -573,7 +581,7 @@ def run_ours(args):
                   "peak": peak, "unit": "TFLOP/s", "frac": ach_b / peak, "flops_per_call": flops_bwd}
         cpu = None
         if ws == 1 and not args.no_cpu_baseline:
-            cpu, _, _ = cpu_oracle_rate(D, C, G.cpu().numpy(), budget_s=args.cpu_budget)
+            cpu, _, _, _ = cpu_oracle_rate(D, C, G.cpu().numpy(), budget_s=args.cpu_budget)
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
