@@ -1250,7 +1250,7 @@ struct BwdScratch {
 };
 
 static const long long kRecordsPerRay = 16;  // record capacity per ray of a batch without the list (the list gives exact counts)
-static const long long kReplayUnit = 64;     // rays per work unit of the replay kernel
+static const long long kReplayUnit = 32;     // rays per work unit of the replay kernel (32: shorter tails than 64)
 
 extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, const double* dL_dtally,
                                        double* grad_thickness, double* grad_tilt, wg_stats* stats) {
@@ -1469,7 +1469,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     aa.blob_bytes = d->blob_bytes;
     aa.recs = sc.sorted;
     aa.n_rec = (long long)n_rec;
-    aa.rec_chunk = 2048;
+    aa.rec_chunk = 1024;
     aa.n_layers = d->n_dev;
     aa.grad_acc = sc.grad_acc;
     aa.work = &w.head->work;
@@ -1522,7 +1522,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     aa.blob_bytes = d->blob_bytes;
     aa.recs = lut_recs;
     aa.n_rec = 2 * n_lut;
-    aa.rec_chunk = 2048;
+    aa.rec_chunk = 1024;
     aa.n_layers = d->n_dev;
     aa.grad_acc = sc.grad_acc;
     aa.work = &w.head->work;
