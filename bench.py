@@ -513,8 +513,18 @@ def run_ours(args):
                     "ms_per_step": 1e3 * e_t / len(e_ms), "fwd_ms": statistics.mean(e_f),
                     "bwd_ms": statistics.mean(e_b), "tilt_pass_ms": statistics.mean(e_tilt),
                     "fwd_interactions_per_s": e_hits / (statistics.mean(e_f) / 1e3),
+                    "roofline_fwd": None,
                     "interactions_per_step": e_hits, "hits_per_ray": e_hits / CE.total_rays,
                     "overflow": sbe["overflow"], "nonfinite": sbe["n_nonfinite"]}
+        # the forward's FP32 roofline on this design (33 flops per layer of the
+        # hit's stack + 250 per hit, as for the representative workload)
+        lay = sfe["n_layer_steps"] / max(1, e_hits)
+        sm_e = torch.cuda.get_device_properties(dev).multi_processor_count
+        pk_e = fp32_peak_tflops(sm_e, float(pk.get("sm_max_mhz", 2070.0)))
+        ach_e = e_hits * (FLOPS_PER_LAYER * lay + FLOPS_PER_HIT) / (statistics.mean(e_f) / 1e3) / 1e12
+        expander["roofline_fwd"] = {"bound": "alu", "kernel": "k_trace_fwd", "achieved": ach_e, "peak": pk_e,
+                                    "unit": "TFLOP/s", "frac": ach_e / pk_e,
+                                    "units": f"{FLOPS_PER_LAYER} x {lay:.1f} layers + {FLOPS_PER_HIT} flops per interaction"}
         if rank == 0 and ws == 1 and not args.no_cpu_baseline:
             expander["cpu_baseline"], _, _, _ = cpu_oracle_rate(DE, CE, Ge.cpu().numpy(),
                                                              budget_s=max(2.0, args.cpu_budget / 3))
