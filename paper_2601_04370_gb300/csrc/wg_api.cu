@@ -129,6 +129,10 @@ static int coef_slots_for(int n_mirrors, long long rays) {
   return (int)std::min<long long>(want, fit);
 }
 
+// instantiation of the trace kernels: 0 for the PRMA's slab planes, 1 for
+// general mirrors (the plane-family search compiled inline)
+static int geo_mode(const wg_design* d) { return d->geo.empty() ? 0 : 1; }
+
 static size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 static bool is_device_ptr(const void* p) {
@@ -796,7 +800,7 @@ extern "C" wg_status wg_omega_trace(wg_ctx* c, const wg_design* d, const wg_trac
   TraceArgs a = base_args(d, cfg, p, w);
   a.tally = t;
   a.G = G;
-  CU(launch_omega_trace(a, G ? g : nullptr, c->sm_count, s));
+  CU(launch_omega_trace(a, G ? g : nullptr, geo_mode(d), c->sm_count, s));
   CU(cudaEventRecord(c->ws_free, s));
   if (!dev_t) {
     CU(cudaMemcpyAsync(tally, t, sizeof(double) * p.tally_size, cudaMemcpyDeviceToHost, s));
@@ -854,10 +858,10 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
       a.coef_mode = 1;
     }
   }
-  const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, d->period, smem));
+  const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, d->period, geo_mode(d), smem));
   const int grid = (int)std::min<long long>(p.n_chunks, (long long)c->sm_count * bps);
   if (stats) CU(cudaEventRecord(c->t0, s));
-  CU(launch_trace_fwd(a, p.F, d->period, grid, smem, s));
+  CU(launch_trace_fwd(a, p.F, d->period, geo_mode(d), grid, smem, s));
   if (a.exit_list) dm->exit_fp = path_fingerprint(d, cfg, p);
   if (a.coef_mode == 1) {
     dm->coef_fp = dm->exit_fp;
@@ -1090,7 +1094,7 @@ wg_status fused_prepare(wg_ctx* c, FusedJob* jobs, int n, int blocks_per_sm, Fus
       cost += job_cost(order[g1]);
       ++g1;
     }
-    int bps = std::max(1, trace_fwd_blocks_per_sm(F, P, sm_max));
+    int bps = std::max(1, trace_fwd_blocks_per_sm(F, P, 2, sm_max));
     if (blocks_per_sm > 0) bps = std::min(bps, blocks_per_sm);
     const int G = c->sm_count * bps;
     FusedBatch::Impl::Group gr{F, P, 0, (int)g0, (int)n_cta, sm_max};
@@ -1380,13 +1384,13 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   if (!dev_g) CU(cudaMallocAsync((void**)&gout, sizeof(double) * std::max(1, d->n_orig), s));
   CU(cudaMemsetAsync(gout, 0, sizeof(double) * std::max(1, d->n_orig), s));
   CU(cudaMemsetAsync(sc.grad_acc, 0, sizeof(double) * std::max(1, d->n_dev), s));
-  const int bps_r = std::max(1, bwd_replay_blocks_per_sm(p.F, d->period, tilt, smem_r));
+  const int bps_r = std::max(1, bwd_replay_blocks_per_sm(p.F, d->period, tilt, geo_mode(d), smem_r));
   // mirror tilts: the replay records each hit's coefficients, the adjoint kernel its dL/d(cos t0);
   // after each batch a tangent pass per 8 mirrors re-traces its rays
   double* gt = grad_tilt;
   const bool dev_t = tilt && is_device_ptr(grad_tilt);
   const size_t smem_t = tilt_smem_bytes(d->blob_bytes, p.F);
-  const int bps_t = tilt ? std::max(1, tilt_blocks_per_sm(p.F, d->period, smem_t)) : 0;
+  const int bps_t = tilt ? std::max(1, tilt_blocks_per_sm(p.F, d->period, geo_mode(d), smem_t)) : 0;
   if (tilt) {
     if (!dev_t) CU(cudaMallocAsync((void**)&gt, sizeof(double) * d->K, s));
     CU(cudaMemsetAsync(gt, 0, sizeof(double) * d->K, s));
@@ -1447,7 +1451,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     CU(cudaMemsetAsync(sc.hit_count, 0, 2 * sizeof(unsigned long long), s));
     const int grid_r = (int)std::max<long long>(1, std::min<long long>(a.n_chunks, (long long)c->sm_count * bps_r));
     if (stats) CU(cudaEventRecord(c->t0, s));
-    CU(launch_bwd_replay(a, p.F, d->period, tilt, grid_r, smem_r, s));
+    CU(launch_bwd_replay(a, p.F, d->period, tilt, geo_mode(d), grid_r, smem_r, s));
     if (stats) CU(cudaEventRecord(c->kev[1], s));
     unsigned long long counts[2] = {0, 0};  // records, ray heads
     CU(cudaMemcpyAsync(counts, sc.hit_count, sizeof(counts), cudaMemcpyDeviceToHost, s));
@@ -1494,7 +1498,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
       at.tilt_k0 = k0;
       const int grid_t =
           (int)std::max<long long>(1, std::min<long long>((n_heads + 127) / 128, (long long)c->sm_count * bps_t));
-      CU(launch_tilt_grad(at, p.F, d->period, grid_t, smem_t, s));
+      CU(launch_tilt_grad(at, p.F, d->period, geo_mode(d), grid_t, smem_t, s));
     }
     if (stats) {
       CU(cudaEventRecord(c->t1, s));
@@ -1662,10 +1666,10 @@ extern "C" wg_status wg_trace_forward_noalloc(wg_ctx* c, const wg_design* d, con
   CU(cudaMemsetAsync(tally + p.cell_lo * p.bins, 0, sizeof(double) * (p.cell_hi - p.cell_lo + 1) * p.bins, s));
   TraceArgs a = base_args(d, cfg, p, w);
   a.tally = tally;
-  const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, d->period, smem));
+  const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, d->period, geo_mode(d), smem));
   const int grid = (int)std::min<long long>(p.n_chunks, (long long)c->sm_count * bps);
   if (stats) CU(cudaEventRecord(c->t0, s));
-  CU(launch_trace_fwd(a, p.F, d->period, grid, smem, s));
+  CU(launch_trace_fwd(a, p.F, d->period, geo_mode(d), grid, smem, s));
   if (stats) {
     CU(cudaEventRecord(c->t1, s));
     return finish_stats(c, w, s, stats, true);

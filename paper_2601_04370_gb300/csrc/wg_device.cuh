@@ -895,9 +895,10 @@ __device__ __forceinline__ void face_basis(V3 d, V3& s, V3& p) {
 // visited in order of distance from the first one ahead (binary search on c)
 // until one acts (the crossing inside its rectangle) or lies beyond the
 // nearest surface so far: the same choice as testing every plane, from the
-// same t values (one normal per family). Kept out of line, so the PRMA path
-// of the trace kernels keeps its code size.
-static __device__ __noinline__ void next_mirror_general(const Blob B, V3 p, V3 d, int last, float& best, int& id) {
+// same t values (one normal per family). Inlined into the kernels
+// instantiated for general designs; next_mirror_general is its out-of-line
+// form for launches that mix both kinds of design.
+__device__ __forceinline__ void next_mirror_families(const Blob& B, V3 p, V3 d, int last, float& best, int& id) {
   const BlobHeader& h = *B.h;
   for (int f = 0; f < h.n_fam; ++f) {
     const FamRec fr = B.fam[f];
@@ -931,6 +932,9 @@ static __device__ __noinline__ void next_mirror_general(const Blob B, V3 p, V3 d
     }
   }
 }
+static __device__ __noinline__ void next_mirror_general(const Blob B, V3 p, V3 d, int last, float& best, int& id) {
+  next_mirror_families(B, p, d, last, best, id);
+}
 
 // Nearest surface along (p, d), excluding `last`. Candidate order and ties
 // match the oracle: faces, input mirror, far end, sides, mirrors.
@@ -940,6 +944,9 @@ static __device__ __noinline__ void next_mirror_general(const Blob B, V3 p, V3 d
 // face for reg = K); every other plane is behind one of those two inside the
 // slab, so only they are tested. reg < 0 tests every plane. Distances use
 // the fast quotient (denominators are direction cosines, |x| <= 1).
+// GM: 0 PRMA designs only, 1 general designs only (the family search
+// inline), 2 either (decided per design; the family search out of line).
+template <int GM>
 __device__ __forceinline__ int next_surface(const Blob& B, V3 p, V3 d, int last, int reg, float& tmin) {
   const BlobHeader& h = *B.h;
   float best = __int_as_float(0x7f800000);
@@ -970,15 +977,21 @@ __device__ __forceinline__ int next_surface(const Blob& B, V3 p, V3 d, int last,
     if (dn > 0.0f) consider(S_LEFT, __fdividef(-fmaf(p.x, h.ic_nx, p.z * h.ic_nz), dn));
   }
   if (right && d.x > 0.0f) consider(S_RIGHT, __fdividef(h.x_end - p.x, d.x));
-  if (!h.general) {
+  auto prma_planes = [&]() {
     for (int k = k0; k < k1; ++k) {
       const MirrorRec& m = B.mir[k];
       const float den = fmaf(d.x, m.nx, fmaf(d.y, m.ny, d.z * m.nz));
       if (den == 0.0f) continue;
       consider(S_MIR + k, __fdividef(m.c - fmaf(p.x, m.nx, fmaf(p.y, m.ny, p.z * m.nz)), den));
     }
+  };
+  if constexpr (GM == 0) {
+    prma_planes();
+  } else if constexpr (GM == 1) {
+    next_mirror_families(B, p, d, last, best, id);
   } else {
-    next_mirror_general(B, p, d, last, best, id);
+    if (!h.general) prma_planes();
+    else next_mirror_general(B, p, d, last, best, id);
   }
   tmin = best;
   return id;

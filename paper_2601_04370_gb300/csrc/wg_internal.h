@@ -157,13 +157,13 @@ cudaError_t launch_prep_design(uint8_t* blob, const float* mir_x, const float* m
                                const float* geo, int n_mir, float ic_tilt_deg, float thick, cudaStream_t s);
 cudaError_t launch_prep_fields(FieldRec* out, const float* fx, const float* fy, int n_fx, int n_fy,
                                float n_slab, float ic_tilt_deg, int dims, cudaStream_t s);
-cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int gm, int grid, size_t smem, cudaStream_t s);
 // several jobs (designs / configurations with the same F and P) in one
 // launch: CTA b works on job cta_job[b] (device arrays; each job's n_cta set)
 cudaError_t launch_trace_fwd_fused(const TraceArgs* jobs_dev, const int* cta_job_dev, int F, int P, int grid,
                                    size_t smem, cudaStream_t s);
 // tilt: also record TiltAux per hit and a RayHead per ray (a.tilt_aux, a.ray_heads)
-cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, bool tilt, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, bool tilt, int gm, int grid, size_t smem, cudaStream_t s);
 // perm (may be null): perm[sorted position] = index of the record in `in`
 cudaError_t launch_bwd_sort(const HitRec* in, long long n, unsigned int* key_count, unsigned int* key_off,
                             unsigned int* key_cursor, HitRec* out, unsigned int* perm, cudaStream_t s);
@@ -191,14 +191,14 @@ cudaError_t launch_heads_sort(const RayHead* in, long long n, unsigned int* cnt,
 cudaError_t launch_exits_sort(const ExitRec* in, long long n, unsigned int* cnt, ExitRec* out, cudaStream_t s);
 // reflection-probability pre-optimization: geometric trace of the rays of a
 // (a.tally, a.G; grad_omega [n_mir] FP64 sums, may be null)
-cudaError_t launch_omega_trace(const TraceArgs& a, double* grad_omega, int sm_count, cudaStream_t s);
+cudaError_t launch_omega_trace(const TraceArgs& a, double* grad_omega, int gm, int sm_count, cudaStream_t s);
 // mirror-tilt gradient of the a.n_heads rays a tilt replay recorded, one
 // pass per group of 8 mirrors starting at a.tilt_k0
-cudaError_t launch_tilt_grad(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_tilt_grad(const TraceArgs& a, int F, int P, int gm, int grid, size_t smem, cudaStream_t s);
 size_t tilt_smem_bytes(int blob_bytes, int F);
-int tilt_blocks_per_sm(int F, int P, size_t smem);
-int trace_fwd_blocks_per_sm(int F, int P, size_t smem);
-int bwd_replay_blocks_per_sm(int F, int P, bool tilt, size_t smem);
+int tilt_blocks_per_sm(int F, int P, int gm, size_t smem);
+int trace_fwd_blocks_per_sm(int F, int P, int gm, size_t smem);
+int bwd_replay_blocks_per_sm(int F, int P, bool tilt, int gm, size_t smem);
 int bwd_adjoint_blocks_per_sm(int P, size_t smem);
 // dynamic shared memory of the adjoint kernel (blob, per-layer sums, segment buffers)
 size_t adj_smem_bytes(int blob_bytes, int n_layers, int P);

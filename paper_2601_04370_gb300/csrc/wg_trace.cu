@@ -775,7 +775,8 @@ __device__ __forceinline__ int q_get(const uint32_t* q, unsigned i, Ray<F>& R, l
   return (int)(c >> 30);
 }
 
-template <int F, int P>
+// GM: geometry mode of next_surface (0 PRMA, 1 general, 2 either: fused launches)
+template <int F, int P, int GM>
 __global__ void __launch_bounds__(kBlock, 2)
     k_trace_fwd(const TraceArgs A0, const TraceArgs* __restrict__ jobs, const int* __restrict__ cta_job) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -891,7 +892,7 @@ __global__ void __launch_bounds__(kBlock, 2)
       bool fin = false, to_mir = false;
       if (has) {
         float t;
-        const int sid = next_surface(B, R.p, R.d, R.last, R.reg, t);
+        const int sid = next_surface<GM>(B, R.p, R.d, R.last, R.reg, t);
         ++R.ev;
         Outcome o;
         o.term = 0;
@@ -1116,7 +1117,7 @@ struct TapeE {
 // T: the replay also serves the tilt gradient: each emitted record gets its
 // TiltAux (the applied coefficients; the adjoint kernel adds dL/d(cos t0))
 // and its ray a RayHead.
-template <int F, int P, bool T>
+template <int F, int P, bool T, int GM>
 __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_mbar;
@@ -1210,7 +1211,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
           o.term = 0;
           if (adv) {
             float t;
-            const int sid = next_surface(B, R.p, R.d, R.last, R.reg, t);
+            const int sid = next_surface<GM>(B, R.p, R.d, R.last, R.reg, t);
             ++R.ev;
             if (sid < 0) {
               o.term = 1;
@@ -1558,7 +1559,7 @@ __device__ void mirror_event_tilt(Ray<F>& R, int k, const Blob& B, const TraceAr
   R.hits = m + 1;
 }
 
-template <int F>
+template <int F, int GM>
 __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_mbar;
@@ -1584,7 +1585,7 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
     unsigned live = 0u;
     for (;;) {
       float tt;
-      const int sid = next_surface(B, R.p, R.d, R.last, R.reg, tt);
+      const int sid = next_surface<GM>(B, R.p, R.d, R.last, R.reg, tt);
       ++R.ev;
       if (sid < 0) break;
       R.p = v3(fmaf(tt, R.d.x, R.p.x), fmaf(tt, R.d.y, R.p.y), fmaf(tt, R.d.z, R.p.z));
@@ -1702,6 +1703,7 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
 // One ray per thread; the gradient is summed per CTA in shared memory.
 // ---------------------------------------------------------------------------
 constexpr int kOmegaBlock = 256;
+template <int GM>
 __global__ void __launch_bounds__(kOmegaBlock) k_omega_trace(const TraceArgs A, double* grad_omega) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_mbar;
@@ -1729,7 +1731,7 @@ __global__ void __launch_bounds__(kOmegaBlock) k_omega_trace(const TraceArgs A, 
     ++c_rays;
     for (;;) {
       float t;
-      const int sid = next_surface(B, R.p, R.d, R.last, R.reg, t);
+      const int sid = next_surface<GM>(B, R.p, R.d, R.last, R.reg, t);
       ++R.ev;
       if (sid < 0) break;
       R.p = v3(fmaf(t, R.d.x, R.p.x), fmaf(t, R.d.y, R.p.y), fmaf(t, R.d.z, R.p.z));
@@ -1793,13 +1795,14 @@ __global__ void __launch_bounds__(kOmegaBlock) k_omega_trace(const TraceArgs A, 
   if (threadIdx.x == 2 && s_cnt[2]) atomicAdd(A.counters + 5, s_cnt[2]);
 }
 
-cudaError_t launch_omega_trace(const TraceArgs& a, double* grad_omega, int sm_count, cudaStream_t s) {
+cudaError_t launch_omega_trace(const TraceArgs& a, double* grad_omega, int gm, int sm_count, cudaStream_t s) {
   const long long n = a.ray_end - a.ray_begin;
   if (n <= 0) return cudaSuccess;
   const int grid = (int)std::max<long long>(1, std::min<long long>((n + kOmegaBlock - 1) / kOmegaBlock, 8ll * sm_count));
-  cudaFuncSetAttribute(k_omega_trace, cudaFuncAttributeMaxDynamicSharedMemorySize, a.blob_bytes);
+  auto k = gm == 1 ? k_omega_trace<1> : k_omega_trace<0>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, a.blob_bytes);
   note_launches(1);
-  k_omega_trace<<<grid, kOmegaBlock, a.blob_bytes, s>>>(a, grad_omega);
+  k<<<grid, kOmegaBlock, a.blob_bytes, s>>>(a, grad_omega);
   return cudaGetLastError();
 }
 
@@ -2218,45 +2221,58 @@ static int occupancy(K kernel, size_t smem) {
   return n;
 }
 
-// kernel instance for (fields F, material period P)
-#define WG_PICK_FP(K, F, P) \
-  ((F) == 2 ? ((P) == 3 ? K<2, 3> : (P) == 2 ? K<2, 2> : K<2, 0>) : ((P) == 3 ? K<1, 3> : (P) == 2 ? K<1, 2> : K<1, 0>))
+// kernel instance for (fields F, material period P, geometry mode GM)
 #define WG_PICK_P(K, P) ((P) == 3 ? K<3> : (P) == 2 ? K<2> : K<0>)
 
-int trace_fwd_blocks_per_sm(int F, int P, size_t smem) { return occupancy(WG_PICK_FP(k_trace_fwd, F, P), smem); }
-template <bool T>
-static void (*pick_replay(int F, int P))(const TraceArgs) {
-  return F == 2 ? (P == 3 ? k_bwd_replay<2, 3, T> : P == 2 ? k_bwd_replay<2, 2, T> : k_bwd_replay<2, 0, T>)
-                : (P == 3 ? k_bwd_replay<1, 3, T> : P == 2 ? k_bwd_replay<1, 2, T> : k_bwd_replay<1, 0, T>);
+template <int GM>
+static void (*pick_fwd_gm(int F, int P))(const TraceArgs, const TraceArgs*, const int*) {
+  return F == 2 ? (P == 3 ? k_trace_fwd<2, 3, GM> : P == 2 ? k_trace_fwd<2, 2, GM> : k_trace_fwd<2, 0, GM>)
+                : (P == 3 ? k_trace_fwd<1, 3, GM> : P == 2 ? k_trace_fwd<1, 2, GM> : k_trace_fwd<1, 0, GM>);
 }
-int bwd_replay_blocks_per_sm(int F, int P, bool tilt, size_t smem) {
-  return occupancy(tilt ? pick_replay<true>(F, P) : pick_replay<false>(F, P), smem);
+static void (*pick_fwd(int F, int P, int gm))(const TraceArgs, const TraceArgs*, const int*) {
+  return gm == 1 ? pick_fwd_gm<1>(F, P) : gm == 2 ? pick_fwd_gm<2>(F, P) : pick_fwd_gm<0>(F, P);
+}
+int trace_fwd_blocks_per_sm(int F, int P, int gm, size_t smem) { return occupancy(pick_fwd(F, P, gm), smem); }
+template <bool T, int GM>
+static void (*pick_replay_gm(int F, int P))(const TraceArgs) {
+  return F == 2 ? (P == 3 ? k_bwd_replay<2, 3, T, GM> : P == 2 ? k_bwd_replay<2, 2, T, GM> : k_bwd_replay<2, 0, T, GM>)
+                : (P == 3 ? k_bwd_replay<1, 3, T, GM> : P == 2 ? k_bwd_replay<1, 2, T, GM> : k_bwd_replay<1, 0, T, GM>);
+}
+template <bool T>
+static void (*pick_replay(int F, int P, int gm))(const TraceArgs) {
+  return gm == 1 ? pick_replay_gm<T, 1>(F, P) : pick_replay_gm<T, 0>(F, P);
+}
+int bwd_replay_blocks_per_sm(int F, int P, bool tilt, int gm, size_t smem) {
+  return occupancy(tilt ? pick_replay<true>(F, P, gm) : pick_replay<false>(F, P, gm), smem);
 }
 template <bool T>
 static void (*pick_adjoint(int P))(const AdjArgs) {
   return P == 3 ? k_bwd_adjoint<3, T> : P == 2 ? k_bwd_adjoint<2, T> : k_bwd_adjoint<0, T>;
 }
 int bwd_adjoint_blocks_per_sm(int P, size_t smem) { return occupancy(pick_adjoint<false>(P), smem); }
-int tilt_blocks_per_sm(int F, int P, size_t smem) {
+static void (*pick_tilt(int F, int gm))(const TraceArgs) {
+  return gm == 1 ? (F == 2 ? k_tilt_grad<2, 1> : k_tilt_grad<1, 1>) : (F == 2 ? k_tilt_grad<2, 0> : k_tilt_grad<1, 0>);
+}
+int tilt_blocks_per_sm(int F, int P, int gm, size_t smem) {
   (void)P;
-  auto k = F == 2 ? k_tilt_grad<2> : k_tilt_grad<1>;
+  auto k = pick_tilt(F, gm);
   int n = 0;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kTiltBlock, smem);
   return n;
 }
 
-cudaError_t launch_tilt_grad(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_tilt_grad(const TraceArgs& a, int F, int P, int gm, int grid, size_t smem, cudaStream_t s) {
   (void)P;
-  auto k = F == 2 ? k_tilt_grad<2> : k_tilt_grad<1>;
+  auto k = pick_tilt(F, gm);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   note_launches(1);
   k<<<grid, kTiltBlock, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int grid, size_t smem, cudaStream_t s) {
-  auto k = WG_PICK_FP(k_trace_fwd, F, P);
+cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int gm, int grid, size_t smem, cudaStream_t s) {
+  auto k = pick_fwd(F, P, gm);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   note_launches(1);
   TraceArgs a1 = a;
@@ -2267,7 +2283,7 @@ cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int grid, size_t 
 
 cudaError_t launch_trace_fwd_fused(const TraceArgs* jobs_dev, const int* cta_job_dev, int F, int P, int grid,
                                    size_t smem, cudaStream_t s) {
-  auto k = WG_PICK_FP(k_trace_fwd, F, P);
+  auto k = pick_fwd(F, P, 2);  // the jobs of a fused launch may mix PRMA and general designs
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   note_launches(1);
   TraceArgs unused;
@@ -2276,8 +2292,9 @@ cudaError_t launch_trace_fwd_fused(const TraceArgs* jobs_dev, const int* cta_job
   return cudaGetLastError();
 }
 
-cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, bool tilt, int grid, size_t smem, cudaStream_t s) {
-  auto k = tilt ? pick_replay<true>(F, P) : pick_replay<false>(F, P);
+cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, bool tilt, int gm, int grid, size_t smem,
+                              cudaStream_t s) {
+  auto k = tilt ? pick_replay<true>(F, P, gm) : pick_replay<false>(F, P, gm);
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   note_launches(1);
   k<<<grid, kBlock, smem, s>>>(a);
