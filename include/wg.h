@@ -162,7 +162,7 @@ typedef struct wg_trace_cfg {
                                  wg_trace_backward only (not served, not no-alloc). */
   void* stream;               /* cudaStream_t or NULL */
   int64_t ray_begin, ray_end; /* traced ray ids [begin, end); end <= 0: all */
-  void* ray_records;          /* NULL or device wg_ray_record[end - begin] */
+  void* ray_records;          /* NULL or device wg_ray_record[end - begin]; a host pointer: WG_EINVAL */
 } wg_trace_cfg;
 
 /* per-ray record written when wg_trace_cfg.ray_records != NULL */
@@ -328,9 +328,10 @@ wg_status wg_trace_backward(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg*
  *  - The scratch needed is 256 B + the wavelength and field-angle arrays +
  *    48 B per field (up to ~2700 fields); a configuration that needs more
  *    than WG_NOALLOC_SCRATCH_BYTES is rejected with WG_EINVAL.
- *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *  - wg_init places the array on its device and looks up its device address
+ *    (cudaGetSymbolAddress, with that device current), and loads the forward
+ *    kernels there, so no call of this entry point, the first included,
+ *    loads or allocates anything on the device.
  *  - Every call shares the array and clears the parts that must start at
  *    zero; the array keeps the last call's contents. Calls whose work
  *    overlaps on the GPU (other streams, other threads) race on the array:
@@ -426,6 +427,35 @@ wg_status wg_omega_trace(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cf
  * (0, 1)); the sampled paths change, so an earlier eyebox-ray list no longer
  * applies. Returns once the device copy is done. Errors: WG_EINVAL. */
 wg_status wg_set_omega(wg_design* d, const float* omega, int32_t n, void* stream);
+
+/* Optimizer of the reflection probabilities (the pre-optimization's update):
+ * Adam on the n_mirrors values of omega with the gradient of a loss to
+ * minimize (wg_omega_trace's grad_omega of L = -I_mean maximizes the mean
+ * pupil throughput), each value then clipped to [lo, hi]. The paper names no
+ * optimizer for this step. */
+typedef struct wg_omega_adam_opts {
+  float lr;        /* step size (0 = 0.02) */
+  float beta1;     /* (0 = 0.9) */
+  float beta2;     /* (0 = 0.999) */
+  float eps;       /* (0 = 1e-8) */
+  float lo, hi;    /* clip range, 0 < lo < hi < 1 (both 0: [0.02, 0.98]) */
+} wg_omega_adam_opts;
+typedef struct wg_omega_adam wg_omega_adam;
+/* State (FP64 values and moments on the design's device) starting from the
+ * design's current omega. NULL opts: the defaults. Errors: WG_EINVAL, WG_ENOMEM. */
+wg_status wg_omega_adam_create(wg_design* d, const wg_omega_adam_opts* opts, wg_omega_adam** out);
+/* One step with dL/d omega ([n_mirrors] FP64, host or device); the clipped
+ * values go to the design (as wg_set_omega; returns once they are there).
+ * omega_out: NULL or host FP32 [n_mirrors], the new values. Non-finite
+ * gradient entries leave their mirror unchanged. Errors: WG_EINVAL, WG_EDEVICE. */
+wg_status wg_omega_adam_step(wg_omega_adam* a, const double* grad_omega, float* omega_out, void* stream);
+void wg_omega_adam_destroy(wg_omega_adam* a);
+
+/* A counter that every change of the design's parameters (wg_set_params,
+ * wg_set_omega, the optimizers' steps) increases: a caller that pairs a
+ * forward trace with a later backward can check that both saw the same
+ * parameters. Errors: WG_EINVAL. */
+wg_status wg_design_version(const wg_design* d, uint64_t* version);
 
 /* ------------------------------------------------------------------------
  * Optimizer of the layer thicknesses (Results, "Evaluation": all PRMA

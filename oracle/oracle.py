@@ -423,3 +423,25 @@ def adam_projected_step(theta, m, v, g, t, lr=2.0, beta1=0.9, beta2=0.999, eps=1
     x = np.where(gap, np.where(x < 0.5 * d_min, 0.0, d_min), x)
     theta_new = np.where(upd, x, theta).astype(np.float32)
     return theta_new, np.where(upd, m_new, m), np.where(upd, v_new, v)
+
+
+def adam_clipped_step(w, m, v, g, t, lr=0.02, beta1=0.9, beta2=0.999, eps=1e-8, lo=0.02, hi=0.98):
+    """One step of the reflection-probability pre-optimization's update
+    (Methods, "Learned reflection probabilities"; the paper names no
+    optimizer): Adam (Kingma and Ba, 2015, Algorithm 1) in FP64 on the
+    mirrors' omega with dL/d omega of a loss to minimize,
+        m <- b1 m + (1 - b1) g,  v <- b2 v + (1 - b2) g^2,
+        w <- w - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps),
+    then each value clipped to [lo, hi]. Entries whose gradient is not
+    finite are left as they are. Returns new (w, m, v)."""
+    w = np.array(w, dtype=np.float64)
+    m = np.array(m, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    g = np.asarray(g, dtype=np.float64)
+    upd = np.isfinite(g)
+    gg = np.where(upd, g, 0.0)
+    m_new = beta1 * m + (1.0 - beta1) * gg
+    v_new = beta2 * v + (1.0 - beta2) * gg * gg
+    x = w - lr * (m_new / (1.0 - beta1 ** t)) / (np.sqrt(v_new / (1.0 - beta2 ** t)) + eps)
+    x = np.clip(x, lo, hi)
+    return np.where(upd, x, w), np.where(upd, m_new, m), np.where(upd, v_new, v)

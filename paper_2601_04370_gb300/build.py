@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libwg.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ("wg_trace.cu", "wg_loss.cu", "wg_api.cu", "wg_serve.cu", "wg_opt.cu")
+SOURCES = ("wg_trace.cu", "wg_trace_fwd.cu", "wg_trace_fwd_acc.cu", "wg_trace_bwd.cu", "wg_trace_bwd_acc.cu",
+           "wg_trace_adj.cu", "wg_loss.cu", "wg_api.cu", "wg_serve.cu", "wg_opt.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -85,6 +85,7 @@ struct wg_ctx {
   DevBuf lut;     // coating look-up table of the last call that asked for one
   DevBuf lsort;   // the eyebox-ray list grouped by hit count, for the replay
   void* serve = nullptr;  // serving runtime state (wg_serve.cu)
+  void* noalloc_scratch = nullptr;  // device address of the no-allocation trace's static array
 };
 
 struct wg_design {
@@ -103,6 +104,7 @@ struct wg_design {
   int* d_dev_to_orig = nullptr;
   float* d_stage = nullptr;    // [n_orig] thickness staging for set_params
   int period = 0;              // material period shared by all stacks (0, 2 or 3)
+  bool acc = false;            // accurate layer evaluation (a stack longer than kAccLayers)
   int geom_version = 0;        // bumped whenever the mirror geometry (tilts) changes
   // eyebox rays of the last listing forward trace: count (u64) | ExitRec[],
   // valid for the configuration and geometry with fingerprint exit_fp (0: none)
@@ -118,6 +120,7 @@ struct wg_design {
   int coef_thick = -1, coef_lut = 0, coef_slots = 0;
   long long coef_base = 0, coef_rays = 0;
   int thick_version = 0;  // bumped whenever the thicknesses change
+  uint64_t param_version = 0;  // bumped by every parameter change (wg_design_version)
 };
 
 // hits per ray whose coefficients the listing forward keeps for the replay:
@@ -146,6 +149,16 @@ static bool is_device_ptr(const void* p) {
 }
 
 // ---------------------------------------------------------------------------
+// Scratch of the allocation-free forward trace (wg_trace_forward_noalloc),
+// for callers that cannot allocate device memory: the per-call scratch lives
+// in this static device array instead of the context's workspace. Host code
+// must not pass the array's name to a kernel (on the host it is only a
+// stand-in); wg_init looks up its device address with the context's device
+// current and keeps it in the context.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[WG_NOALLOC_SCRATCH_BYTES];
+
+// ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
 extern "C" wg_status wg_init(wg_ctx** out, const wg_init_opts* opts) {
@@ -167,6 +180,22 @@ extern "C" wg_status wg_init(wg_ctx** out, const wg_init_opts* opts) {
   if (opts && opts->max_slots > 0) c->max_slots = opts->max_slots;
   if (opts) c->hbm_budget = opts->hbm_budget_bytes;
   if (opts && opts->autotune_cache) c->autotune_cache = opts->autotune_cache;
+  // the allocation-free trace's array: looking up its address places it on
+  // this device now, and loading the forward kernels now keeps a first
+  // wg_trace_forward_noalloc call from loading (allocating) anything
+  {
+    const cudaError_t e = cudaGetSymbolAddress(&c->noalloc_scratch, g_noalloc_scratch);
+    if (e != cudaSuccess || !c->noalloc_scratch) {
+      delete c;
+      return fail(WG_EDEVICE, "wg_init: cudaGetSymbolAddress of the no-allocation scratch failed: %s",
+                  cudaGetErrorString(e));
+    }
+    const cudaError_t e2 = preload_forward_kernels();
+    if (e2 != cudaSuccess) {
+      delete c;
+      return fail(WG_EDEVICE, "wg_init: loading the forward kernels failed: %s", cudaGetErrorString(e2));
+    }
+  }
   if (cudaEventCreateWithFlags(&c->ws_free, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreate(&c->t0) != cudaSuccess || cudaEventCreate(&c->t1) != cudaSuccess ||
       cudaEventCreate(&c->kev[0]) != cudaSuccess || cudaEventCreate(&c->kev[1]) != cudaSuccess ||
@@ -291,6 +320,7 @@ static std::vector<uint8_t> build_blob(const wg_design& d) {
     h.mat_inv_n[i] = (float)(1.0 / (double)d.mat_n[i]);
     const double r = (double)d.n_slab / (double)d.mat_n[i];
     h.mat_r2[i] = (float)(r * r);
+    h.mat_r2_lo[i] = (float)(r * r - (double)h.mat_r2[i]);
   }
   h.off_mir = (int)off_mir;
   h.off_d = (int)off_d;
@@ -335,8 +365,21 @@ static int design_period(const wg_design& d) {
   return 0;
 }
 
+// the accurate layer evaluation for designs with a stack of more than
+// kAccLayers (non-pruned) layers
+static bool design_acc(const wg_design& d) {
+  int orig = 0;
+  for (int k = 0; k < d.K; ++k) {
+    int n = 0;
+    for (int l = 0; l < d.n_layers[k]; ++l, ++orig) n += d.pruned[orig] ? 0 : 1;
+    if (n > kAccLayers) return true;
+  }
+  return false;
+}
+
 static wg_status upload_design(wg_design* d, cudaStream_t s) {
   d->period = design_period(*d);
+  d->acc = design_acc(*d);
   std::vector<uint8_t> b = build_blob(*d);
   d->blob_bytes = (int)b.size();
   CU(cudaMalloc(&d->blob, b.size()));
@@ -451,6 +494,7 @@ extern "C" wg_status wg_set_params(wg_design* d, const float* thickness_nm, int6
     }
     CU(launch_thickness_update(d->blob, d->d_stage, d->d_orig_to_dev, d->n_orig, s));
     ++d->thick_version;  // the coefficients kept by the last listing forward are stale
+    ++d->param_version;
   }
   if (tilt_deg) {
     if (n_tilt != d->K) return fail(WG_EINVAL, "wg_set_params: %d tilts for %d mirrors", n_tilt, d->K);
@@ -459,10 +503,18 @@ extern "C" wg_status wg_set_params(wg_design* d, const float* thickness_nm, int6
         return fail(WG_EINVAL, "wg_set_params: tilt %d invalid", k);
     d->mir_tilt.assign(tilt_deg, tilt_deg + d->K);
     ++d->geom_version;  // ray paths change with the geometry: the eyebox-ray list is stale
+    ++d->param_version;
     d->exit_fp = 0;
     CU(cudaMemcpyAsync(d->d_mir + d->K, tilt_deg, sizeof(float) * d->K, cudaMemcpyHostToDevice, s));
     CU(launch_prep_design(d->blob, d->d_mir, d->d_mir + d->K, d->d_mir + 2 * d->K, d->d_geo, d->K, d->ic_tilt, d->thick, s));
   }
+  return WG_OK;
+}
+
+extern "C" wg_status wg_design_version(const wg_design* d, uint64_t* version) {
+  if (!d || !version) return fail(WG_EINVAL, "wg_design_version: NULL design/version");
+  std::lock_guard<std::mutex> lk(d->ctx->mu);
+  *version = d->param_version;
   return WG_OK;
 }
 
@@ -477,6 +529,7 @@ extern "C" wg_status wg_set_omega(wg_design* d, const float* omega, int32_t n, v
   CU(cudaSetDevice(c->device));
   d->omega.assign(omega, omega + n);
   ++d->geom_version;  // the sampled paths change with omega: the eyebox-ray list is stale
+  ++d->param_version;
   d->exit_fp = 0;
   CU(cudaMemcpyAsync(d->d_mir + 2 * d->K, omega, sizeof(float) * d->K, cudaMemcpyHostToDevice, s));
   CU(launch_prep_design(d->blob, d->d_mir, d->d_mir + d->K, d->d_mir + 2 * d->K, d->d_geo, d->K, d->ic_tilt, d->thick, s));
@@ -497,7 +550,7 @@ extern "C" wg_status wg_eval_coating(wg_ctx* c, const wg_design* d, int32_t mirr
     return fail(WG_EINVAL, "wg_eval_coating: arrays must be device memory");
   std::lock_guard<std::mutex> lk(c->mu);
   CU(cudaSetDevice(c->device));
-  CU(launch_coating_eval(d->blob, d->period, mirror, side, n, cos_theta, lambda_nm, out_rt, (cudaStream_t)stream));
+  CU(launch_coating_eval(d->blob, d->period, d->acc, mirror, side, n, cos_theta, lambda_nm, out_rt, (cudaStream_t)stream));
   return WG_OK;
 }
 
@@ -512,7 +565,7 @@ extern "C" wg_status wg_eval_coating_grad(wg_ctx* c, const wg_design* d, int32_t
     return fail(WG_EINVAL, "wg_eval_coating_grad: arrays must be device memory");
   std::lock_guard<std::mutex> lk(c->mu);
   CU(cudaSetDevice(c->device));
-  CU(launch_coating_grad(d->blob, d->period, mirror, side, n, cos_theta, lambda_nm, weights, which, grad,
+  CU(launch_coating_grad(d->blob, d->period, d->acc, mirror, side, n, cos_theta, lambda_nm, weights, which, grad,
                           (cudaStream_t)stream));
   return WG_OK;
 }
@@ -534,7 +587,11 @@ static wg_status validate_cfg(const wg_design* d, const wg_trace_cfg* cfg) {
   if (d->dims == 2 && (cfg->n_fy != 1 || cfg->field_y_deg[0] != 0.0f || cfg->eb_ny != 1))
     return fail(WG_EINVAL, "cfg: 2D designs take one field_y of 0 and eb_ny = 1");
   if (cfg->pol < 0 || cfg->pol > 3) return fail(WG_EINVAL, "cfg: pol must be 0..3");
+  if (cfg->n_lambda > 65536) return fail(WG_EINVAL, "cfg: at most 65536 wavelengths");
   if (cfg->n_rays < 1) return fail(WG_EINVAL, "cfg: n_rays must be >= 1");
+  // the kernels write the per-ray records directly: a host pointer would fault
+  if (cfg->ray_records && !is_device_ptr(cfg->ray_records))
+    return fail(WG_EINVAL, "cfg: ray_records must be device memory");
   if (cfg->max_events < 1 || cfg->max_events > WG_MAX_EVENTS)
     return fail(WG_EINVAL, "cfg: max_events must be in [1,%d]", WG_MAX_EVENTS);
   if (cfg->eb_nx < 1 || cfg->eb_ny < 1 || (long long)cfg->eb_nx * cfg->eb_ny > 16384)
@@ -730,7 +787,7 @@ static wg_status prepare_lut(wg_ctx* c, const wg_design* d, const wg_trace_cfg* 
     CU(c->lut.ensure(bytes));
   }
   const float c0 = 0.5f / (float)N, dc = 1.0f / (float)N;
-  CU(launch_lut_build(d->blob, d->period, d->K, cfg->n_lambda, w.lam, N, c0, dc, static_cast<float4*>(c->lut.p), s));
+  CU(launch_lut_build(d->blob, d->period, d->acc, d->K, cfg->n_lambda, w.lam, N, c0, dc, static_cast<float4*>(c->lut.p), s));
   a.lut = static_cast<const float4*>(c->lut.p);
   a.lut_n = N;
   a.n_lam = cfg->n_lambda;
@@ -823,7 +880,7 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
   p.chunk_rays = default_chunk(p);
   p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
   p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
-  const size_t smem = fwd_smem_bytes(d->blob_bytes, p.bins, p.F, fwd_slots(p.chunk_rays));
+  const size_t smem = fwd_smem_bytes(d->blob_bytes, p.bins, p.F, fwd_slots(p.chunk_rays), d->acc);
   if (smem > 200 * 1024) return fail(WG_EINVAL, "wg_trace_forward: design + eyebox too large for shared memory");
   cudaStream_t s = (cudaStream_t)cfg->stream;
   std::lock_guard<std::mutex> lk(c->mu);
@@ -858,10 +915,10 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
       a.coef_mode = 1;
     }
   }
-  const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, d->period, geo_mode(d), smem));
+  const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, d->period, geo_mode(d), d->acc, smem));
   const int grid = (int)std::min<long long>(p.n_chunks, (long long)c->sm_count * bps);
   if (stats) CU(cudaEventRecord(c->t0, s));
-  CU(launch_trace_fwd(a, p.F, d->period, geo_mode(d), grid, smem, s));
+  CU(launch_trace_fwd(a, p.F, d->period, geo_mode(d), d->acc, grid, smem, s));
   if (a.exit_list) dm->exit_fp = path_fingerprint(d, cfg, p);
   if (a.coef_mode == 1) {
     dm->coef_fp = dm->exit_fp;
@@ -899,10 +956,12 @@ long long design_params(const wg_design* d) { return d->n_orig; }
 wg_ctx* design_ctx(const wg_design* d) { return d->ctx; }
 const float* design_thickness(const wg_design* d) { return d->layer_d.data(); }
 const uint8_t* design_pruned(const wg_design* d) { return d->pruned.data(); }
-void design_shape(const wg_design* d, int* K, int* n_dev, int* period) {
+const float* design_omega(const wg_design* d) { return d->omega.data(); }
+void design_shape(const wg_design* d, int* K, int* n_dev, int* period, int* acc) {
   *K = d->K;
   *n_dev = d->n_dev;
   *period = d->period;
+  *acc = d->acc ? 1 : 0;
 }
 
 long long tally_doubles(const wg_design* d, const wg_trace_cfg* cfg) {
@@ -957,7 +1016,7 @@ struct FusedBatch::Impl {
   };
   std::vector<Copy> copies;
   struct Group {
-    int F, P, grid, first, cta0;
+    int F, P, acc, grid, first, cta0;
     size_t smem;
   };
   std::vector<Group> groups;
@@ -998,7 +1057,7 @@ wg_status fused_prepare(wg_ctx* c, FusedJob* jobs, int n, int blocks_per_sm, Fus
     p.chunk_rays = J.chunk_rays > 0 ? std::min<long long>(J.chunk_rays, p.n_cell) : default_chunk(p);
     p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
     p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
-    smem[j] = fwd_smem_bytes(J.design->blob_bytes, p.bins, p.F, fwd_slots(p.chunk_rays));
+    smem[j] = fwd_smem_bytes(J.design->blob_bytes, p.bins, p.F, fwd_slots(p.chunk_rays), J.design->acc);
     if (smem[j] > 200 * 1024) return fail(WG_EINVAL, "fused forward: job %d design + eyebox too large", j);
   }
   // device arena: heads (contiguous) | per-job arrays | job table | CTA map;
@@ -1071,33 +1130,33 @@ wg_status fused_prepare(wg_ctx* c, FusedJob* jobs, int n, int blocks_per_sm, Fus
     }
     B.args[j] = a;
   }
-  // groups of jobs sharing the kernel variant (fields per ray, material period)
+  // groups of jobs sharing the kernel variant (fields per ray, material period, accuracy mode)
   std::vector<int> order(n);
   for (int j = 0; j < n; ++j) order[j] = j;
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-    return B.plans[x].F * 4 + jobs[x].design->period < B.plans[y].F * 4 + jobs[y].design->period;
-  });
+  auto variant = [&](int j) { return B.plans[j].F * 8 + jobs[j].design->period * 2 + (jobs[j].design->acc ? 1 : 0); };
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return variant(x) < variant(y); });
   TraceArgs* tab_h = reinterpret_cast<TraceArgs*>(pin + B.tab_dev);
   int* cta_h = reinterpret_cast<int*>(pin + B.cta_dev);
   size_t n_cta = 0;
   for (size_t g0 = 0; g0 < order.size();) {
     size_t g1 = g0;
     const int F = B.plans[order[g0]].F, P = jobs[order[g0]].design->period;
+    const bool acc = jobs[order[g0]].design->acc;
     size_t sm_max = 0;
     double cost = 0.0;
     auto job_cost = [&](int j) {
       const double layers = (double)jobs[j].design->n_dev / std::max(1, jobs[j].design->K);
       return (double)(B.plans[j].re - B.plans[j].rb) * (10.0 + layers);
     };
-    while (g1 < order.size() && B.plans[order[g1]].F == F && jobs[order[g1]].design->period == P) {
+    while (g1 < order.size() && variant(order[g1]) == variant(order[g0])) {
       sm_max = std::max(sm_max, smem[order[g1]]);
       cost += job_cost(order[g1]);
       ++g1;
     }
-    int bps = std::max(1, trace_fwd_blocks_per_sm(F, P, 2, sm_max));
+    int bps = std::max(1, trace_fwd_blocks_per_sm(F, P, 2, acc, sm_max));
     if (blocks_per_sm > 0) bps = std::min(bps, blocks_per_sm);
     const int G = c->sm_count * bps;
-    FusedBatch::Impl::Group gr{F, P, 0, (int)g0, (int)n_cta, sm_max};
+    FusedBatch::Impl::Group gr{F, P, acc ? 1 : 0, 0, (int)g0, (int)n_cta, sm_max};
     // CTAs per job: as many as the GPU holds at once (at most its chunks),
     // in an order that interleaves the jobs in proportion to their estimated
     // work. The first G CTAs to start share the GPU between the jobs; a CTA
@@ -1149,7 +1208,8 @@ wg_status fused_enqueue(wg_ctx* c, FusedJob* jobs, FusedBatch& fb, cudaStream_t 
   const TraceArgs* tab = reinterpret_cast<const TraceArgs*>(dev + B.tab_dev);
   const int* cta = reinterpret_cast<const int*>(dev + B.cta_dev);
   CU(cudaEventRecord(B.e0, s));
-  for (const auto& g : B.groups) CU(launch_trace_fwd_fused(tab, cta + g.cta0, g.F, g.P, g.grid, g.smem, s));
+  for (const auto& g : B.groups)
+    CU(launch_trace_fwd_fused(tab, cta + g.cta0, g.F, g.P, g.acc != 0, g.grid, g.smem, s));
   CU(cudaEventRecord(B.e1, s));
   CU(cudaMemcpyAsync(static_cast<uint8_t*>(B.pin.p) + B.heads_pin, dev, (size_t)kHeadStride * (size_t)B.n,
                      cudaMemcpyDeviceToHost, s));
@@ -1200,7 +1260,7 @@ uint64_t fused_signature(const wg_ctx* c, const FusedJob* jobs, const FusedBatch
   mixv(B.n);
   for (const auto& cp : B.copies) mix(&cp, sizeof(cp));
   for (const auto& g : B.groups) {
-    mixv(g.F), mixv(g.P), mixv(g.grid), mixv(g.first), mixv(g.cta0), mixv(g.smem);
+    mixv(g.F), mixv(g.P), mixv(g.acc), mixv(g.grid), mixv(g.first), mixv(g.cta0), mixv(g.smem);
   }
   for (int j = 0; j < B.n; ++j) {
     const Plan& p = B.plans[j];
@@ -1384,18 +1444,18 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   if (!dev_g) CU(cudaMallocAsync((void**)&gout, sizeof(double) * std::max(1, d->n_orig), s));
   CU(cudaMemsetAsync(gout, 0, sizeof(double) * std::max(1, d->n_orig), s));
   CU(cudaMemsetAsync(sc.grad_acc, 0, sizeof(double) * std::max(1, d->n_dev), s));
-  const int bps_r = std::max(1, bwd_replay_blocks_per_sm(p.F, d->period, tilt, geo_mode(d), smem_r));
+  const int bps_r = std::max(1, bwd_replay_blocks_per_sm(p.F, d->period, tilt, geo_mode(d), d->acc, smem_r));
   // mirror tilts: the replay records each hit's coefficients, the adjoint kernel its dL/d(cos t0);
   // after each batch a tangent pass per 8 mirrors re-traces its rays
   double* gt = grad_tilt;
   const bool dev_t = tilt && is_device_ptr(grad_tilt);
   const size_t smem_t = tilt_smem_bytes(d->blob_bytes, p.F);
-  const int bps_t = tilt ? std::max(1, tilt_blocks_per_sm(p.F, d->period, geo_mode(d), smem_t)) : 0;
+  const int bps_t = tilt ? std::max(1, tilt_blocks_per_sm(p.F, d->period, geo_mode(d), d->acc, smem_t)) : 0;
   if (tilt) {
     if (!dev_t) CU(cudaMallocAsync((void**)&gt, sizeof(double) * d->K, s));
     CU(cudaMemsetAsync(gt, 0, sizeof(double) * d->K, s));
   }
-  const int bps_a = std::max(1, bwd_adjoint_blocks_per_sm(d->period, smem_a));
+  const int bps_a = std::max(1, bwd_adjoint_blocks_per_sm(d->period, d->acc, smem_a));
   // coating table: the same table as the forward's (same thicknesses), and
   // the FP64 sums of dL/dc per entry that the replay scatters into
   TraceArgs lut_a;
@@ -1451,7 +1511,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     CU(cudaMemsetAsync(sc.hit_count, 0, 2 * sizeof(unsigned long long), s));
     const int grid_r = (int)std::max<long long>(1, std::min<long long>(a.n_chunks, (long long)c->sm_count * bps_r));
     if (stats) CU(cudaEventRecord(c->t0, s));
-    CU(launch_bwd_replay(a, p.F, d->period, tilt, geo_mode(d), grid_r, smem_r, s));
+    CU(launch_bwd_replay(a, p.F, d->period, tilt, geo_mode(d), d->acc, grid_r, smem_r, s));
     if (stats) CU(cudaEventRecord(c->kev[1], s));
     unsigned long long counts[2] = {0, 0};  // records, ray heads
     CU(cudaMemcpyAsync(counts, sc.hit_count, sizeof(counts), cudaMemcpyDeviceToHost, s));
@@ -1472,6 +1532,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     aa.blob = d->blob;
     aa.blob_bytes = d->blob_bytes;
     aa.recs = sc.sorted;
+    aa.lambda = w.lam;
     aa.n_rec = (long long)n_rec;
     aa.rec_chunk = 1024;
     aa.n_layers = d->n_dev;
@@ -1484,7 +1545,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     if (n_rec > 0 && !use_lut) {  // (table mode: one adjoint over the table's entries after the last batch)
       const long long chunks = ((long long)n_rec + aa.rec_chunk - 1) / aa.rec_chunk;
       const int grid_a = (int)std::min<long long>(chunks, (long long)c->sm_count * bps_a);
-      CU(launch_bwd_adjoint(aa, d->period, grid_a, smem_a, s));
+      CU(launch_bwd_adjoint(aa, d->period, d->acc, grid_a, smem_a, s));
       ++n_adj_launches;
     }
     if (stats) CU(cudaEventRecord(c->kev[3], s));
@@ -1498,7 +1559,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
       at.tilt_k0 = k0;
       const int grid_t =
           (int)std::max<long long>(1, std::min<long long>((n_heads + 127) / 128, (long long)c->sm_count * bps_t));
-      CU(launch_tilt_grad(at, p.F, d->period, geo_mode(d), grid_t, smem_t, s));
+      CU(launch_tilt_grad(at, p.F, d->period, geo_mode(d), d->acc, grid_t, smem_t, s));
     }
     if (stats) {
       CU(cudaEventRecord(c->t1, s));
@@ -1525,6 +1586,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     aa.blob = d->blob;
     aa.blob_bytes = d->blob_bytes;
     aa.recs = lut_recs;
+    aa.lambda = w.lam;
     aa.n_rec = 2 * n_lut;
     aa.rec_chunk = 1024;
     aa.n_layers = d->n_dev;
@@ -1536,7 +1598,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     if (stats) CU(cudaEventRecord(c->kev[2], s));
     const long long chunks = (aa.n_rec + aa.rec_chunk - 1) / aa.rec_chunk;
     const int grid_a = (int)std::min<long long>(chunks, (long long)c->sm_count * bps_a);
-    CU(launch_bwd_adjoint(aa, d->period, grid_a, smem_a, s));
+    CU(launch_bwd_adjoint(aa, d->period, d->acc, grid_a, smem_a, s));
     ++n_adj_launches;
     if (stats) {
       CU(cudaEventRecord(c->kev[3], s));
@@ -1602,34 +1664,6 @@ extern "C" wg_status wg_loss(wg_ctx* c, const wg_design* d, const wg_trace_cfg* 
   return WG_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Allocation-free forward trace (wg_trace_forward_noalloc). For callers that
-// cannot allocate device memory: the per-call scratch lives in this static
-// device array instead of the context's workspace. Host code must not pass
-// the array's name to a kernel (on the host it is only a stand-in); it uses
-// the device address looked up once per device below.
-// ---------------------------------------------------------------------------
-static __device__ __align__(256) unsigned char g_noalloc_scratch[WG_NOALLOC_SCRATCH_BYTES];
-
-static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[128] = {nullptr};  // device address of the array, per device ordinal
-
-// With the context's device current: the array's device address (looked up
-// on the first call on that device).
-static wg_status noalloc_scratch(int device, void** out) {
-  if (device < 0 || device >= 128) return fail(WG_EINVAL, "wg_trace_forward_noalloc: device %d unsupported", device);
-  std::lock_guard<std::mutex> lk(g_noalloc_mu);
-  if (!g_noalloc_addr[device]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return fail(WG_EDEVICE, "wg_trace_forward_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-    g_noalloc_addr[device] = p;
-  }
-  *out = g_noalloc_addr[device];
-  return WG_OK;
-}
-
 extern "C" wg_status wg_trace_forward_noalloc(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, double* tally,
                                               wg_stats* stats) {
   if (!c || !d || !tally) return fail(WG_EINVAL, "wg_trace_forward_noalloc: NULL ctx/design/tally");
@@ -1640,7 +1674,7 @@ extern "C" wg_status wg_trace_forward_noalloc(wg_ctx* c, const wg_design* d, con
   p.chunk_rays = default_chunk(p);
   p.chunks_per_cell = (p.n_cell + p.chunk_rays - 1) / p.chunk_rays;
   p.n_chunks = (p.cell_hi - p.cell_lo + 1) * p.chunks_per_cell;
-  const size_t smem = fwd_smem_bytes(d->blob_bytes, p.bins, p.F, fwd_slots(p.chunk_rays));
+  const size_t smem = fwd_smem_bytes(d->blob_bytes, p.bins, p.F, fwd_slots(p.chunk_rays), d->acc);
   if (smem > 200 * 1024) return fail(WG_EINVAL, "wg_trace_forward_noalloc: design + eyebox too large for shared memory");
   const WsLayout need = ws_layout(nullptr, cfg, p.n_f);
   if (need.bytes > (size_t)WG_NOALLOC_SCRATCH_BYTES)
@@ -1653,10 +1687,7 @@ extern "C" wg_status wg_trace_forward_noalloc(wg_ctx* c, const wg_design* d, con
   CU(cudaSetDevice(c->device));
   if (!is_device_ptr(tally))
     return fail(WG_EINVAL, "wg_trace_forward_noalloc: tally must be device memory (host buffers would need staging)");
-  void* base = nullptr;
-  st = noalloc_scratch(c->device, &base);
-  if (st != WG_OK) return st;
-  const WsLayout w = ws_layout(base, cfg, p.n_f);
+  const WsLayout w = ws_layout(c->noalloc_scratch, cfg, p.n_f);
   // clear what must start at zero: counters, ledger, chunk queue, error word
   CU(cudaMemsetAsync(w.head, 0, 256, s));
   CU(cudaMemcpyAsync(w.lam, cfg->lambda_nm, sizeof(float) * cfg->n_lambda, cudaMemcpyHostToDevice, s));
@@ -1666,10 +1697,10 @@ extern "C" wg_status wg_trace_forward_noalloc(wg_ctx* c, const wg_design* d, con
   CU(cudaMemsetAsync(tally + p.cell_lo * p.bins, 0, sizeof(double) * (p.cell_hi - p.cell_lo + 1) * p.bins, s));
   TraceArgs a = base_args(d, cfg, p, w);
   a.tally = tally;
-  const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, d->period, geo_mode(d), smem));
+  const int bps = std::max(1, trace_fwd_blocks_per_sm(p.F, d->period, geo_mode(d), d->acc, smem));
   const int grid = (int)std::min<long long>(p.n_chunks, (long long)c->sm_count * bps);
   if (stats) CU(cudaEventRecord(c->t0, s));
-  CU(launch_trace_fwd(a, p.F, d->period, geo_mode(d), grid, smem, s));
+  CU(launch_trace_fwd(a, p.F, d->period, geo_mode(d), d->acc, grid, smem, s));
   if (stats) {
     CU(cudaEventRecord(c->t1, s));
     return finish_stats(c, w, s, stats, true);

@@ -64,9 +64,10 @@ struct alignas(16) BlobHeader {
   int n_fam;  // general designs: plane families (FamRec table after the mirror records)
   int pad_;
   float mat_inv_n[MAX_MAT];               // 1 / n
-  float mat_r2[MAX_MAT];                  // (n_slab / n)^2
+  float mat_r2[MAX_MAT];                  // (n_slab / n)^2, rounded from FP64
+  float mat_r2_lo[MAX_MAT];               // (n_slab / n)^2 - mat_r2 (accurate layer evaluation)
 };
-static_assert(sizeof(BlobHeader) == 128, "header layout");
+static_assert(sizeof(BlobHeader) == 144, "header layout");
 
 struct alignas(16) MirrorRec {
   float nx, ny, nz, c;       // plane n . p = c (PRMA: ny = 0)
@@ -75,8 +76,10 @@ struct alignas(16) MirrorRec {
   int n_layers;              // device layers of this mirror
   float ax, ay, az;          // tilt axis: dn/d(tilt) = a x n per radian (PRMA: a = -y)
   float x0, x1, y0, y1;      // (x, y) rectangle where a general mirror acts
+  float nlx, nly, nlz;       // FP64 normal minus (nx, ny, nz): the low part (accurate mode)
+  float pad_;
 };
-static_assert(sizeof(MirrorRec) == 64, "mirror layout");
+static_assert(sizeof(MirrorRec) == 80, "mirror layout");
 
 // A family of a general design: mirrors k0 .. k0 + n - 1 with the same normal
 // (bitwise) and offsets c monotone in the index (dir = +1 increasing, -1
@@ -102,11 +105,12 @@ struct Blob {
 };
 
 // per-field launch constants: guided direction after the input mirror and
-// the transverse basis e1 (y projected off d), e2 = d x e1
+// the transverse basis e1 (y projected off d), e2 = d x e1; dlx, dly, dlz:
+// the FP64 direction minus (dx, dy, dz) (accurate mode)
 struct alignas(16) FieldRec {
-  float dx, dy, dz, pad0;
-  float e1x, e1y, e1z, pad1;
-  float e2x, e2y, e2z, pad2;
+  float dx, dy, dz, dlx;
+  float e1x, e1y, e1z, dly;
+  float e2x, e2y, e2z, dlz;
 };
 
 // ---------------------------------------------------------------------------
@@ -164,8 +168,9 @@ __device__ __forceinline__ float2 cdiv_s(float2 a, float2 b) {
 // kt: the rate the layer loop multiplies by: turns/nm for a propagating layer
 // (the phase is reduced exactly to [-1/2, 1/2) turn before the fast sin/cos),
 // beta for an evanescent one.
+// ktl: the low part of kt in the accurate evaluation (kt + ktl), unused otherwise.
 struct MatK {
-  float kap, kt, q12s, q21s, q12p, q21p;
+  float kap, kt, ktl, q12s, q21s, q12p, q21p;
   int evan;
 };
 
@@ -200,6 +205,85 @@ __device__ __forceinline__ MatK mat_const(float sin2_0, float n, float inv_n, fl
   k.q21s = ev ? -nc : nc;
   k.q12p = (ev ? -c : c) * inv_n;
   k.q21p = q21p;
+  k.ktl = 0.0f;
+  k.evan = ev;
+  return k;
+}
+
+// ---------------------------------------------------------------------------
+// Double-float arithmetic (a value carried as an unevaluated sum hi + lo of
+// two floats) for the accurate layer evaluation. A 200-layer stack turns a
+// phase-rate error e into a coherent phase error of ~70 turns x e, which its
+// resonances amplify: FP32 incidence cosines, phase rates and phases leave
+// coefficient errors of 1e-4 at the 99th percentile, while the FP32 vector
+// sweep alone stays near 1e-5. So the accurate mode carries the incidence
+// cosine, (n0/n)^2, n/lambda and each layer's phase as hi + lo, and takes the
+// sin/cos of the phase on the FMA pipe. The _rn intrinsics are never
+// contracted into FMAs, which the error-free transformations below rely on.
+// ---------------------------------------------------------------------------
+struct F2 {
+  float h, l;
+};
+// p + e = a b exactly
+__device__ __forceinline__ F2 two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return F2{p, fmaf(a, b, -p)};
+}
+// s + e = a + b exactly (Knuth's branch-free sum)
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return F2{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// s + e = a + b exactly when |a| >= |b| or a = 0 (Dekker)
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return F2{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// (a.h + a.l)(b.h + b.l) to about 2^-44 relative (lo not renormalized)
+__device__ __forceinline__ F2 mul_ff(F2 a, F2 b) {
+  const float p = __fmul_rn(a.h, b.h);
+  return F2{p, fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p)))};
+}
+
+// 2 pi log2(e) as hi + lo: an evanescent layer's rate in base-2 exponent units
+constexpr float K2PI_LOG2E_H = 9.064720154e+00f;
+constexpr float K2PI_LOG2E_L = 1.298458017e-07f;
+constexpr float LN2_F = 6.931471825e-01f;
+
+// Accurate material constants: sin2 = sin^2(theta_0), r2 = (n0/n)^2 and
+// nl = n / lambda as hi + lo. rad = 1 - r2 sin2 and cos t = sqrt|rad| keep
+// ~2^-44 relative error through the cancellation near the critical angle;
+// kt + ktl = n cos t / lambda (turns per nm) for a propagating layer, and
+// beta log2(e) / (2 pi) x 2 pi = n a / lambda x 2 pi log2(e) (base-2
+// exponent per nm) for an evanescent one. The quotients are FP32 as above.
+__device__ __forceinline__ MatK mat_const_acc(F2 sin2, float n, float inv_n, F2 r2, F2 nl) {
+  MatK k;
+  const F2 q = mul_ff(r2, sin2);
+  F2 rad = two_sum(1.0f, -q.h);
+  rad = fast_two_sum(rad.h, __fsub_rn(rad.l, q.l));
+  const bool ev = !(rad.h >= 0.0f);
+  const float x = fmaxf(fabsf(rad.h), 1e-30f);
+  const float xl = ev ? -rad.l : rad.l;
+  float r = rsqrtf(x);
+  r = fmaf(0.5f * r, fmaf(-x * r, r, 1.0f), r);
+  float c = x * r;
+  c = fmaf(0.5f * r, fmaf(-c, c, x), c);
+  const float cl = (fmaf(-c, c, x) + xl) * (0.5f * r);  // sqrt(x + xl) = c + cl
+  const float nc = n * c;
+  float q12 = r * inv_n;
+  q12 = fmaf(q12, fmaf(-nc, q12, 1.0f), q12);  // 1 / (n c)
+  float q21p = n * r;
+  q21p = fmaf(fmaf(-c, q21p, n), r, q21p);     // n / c
+  F2 kt = mul_ff(nl, F2{c, cl});
+  k.kap = TWO_PI * kt.h;
+  if (ev) kt = mul_ff(kt, F2{K2PI_LOG2E_H, K2PI_LOG2E_L});
+  k.kt = kt.h;
+  k.ktl = kt.l;
+  k.q12s = q12;
+  k.q21s = ev ? -nc : nc;
+  k.q12p = (ev ? -c : c) * inv_n;
+  k.q21p = q21p;
   k.evan = ev;
   return k;
 }
@@ -213,6 +297,30 @@ struct MatTable {
     for (int i = 0; i < MAX_MAT; ++i)
       if (i < h.n_mat) k[i] = mat_const(sin2, h.mat_n[i], h.mat_inv_n[i], h.mat_r2[i], inv_lam);
   }
+  // accurate mode: cos(theta_0) = c0h + c0l
+  __device__ __forceinline__ void init_acc(const BlobHeader& h, float c0h, float c0l, float lam) {
+    const F2 p = two_prod(c0h, c0h);
+    F2 sin2 = fast_two_sum(1.0f, -p.h);
+    sin2.l = fmaf(-2.0f * c0h, c0l, __fsub_rn(sin2.l, p.l));
+    const float ilh = __frcp_rn(lam);
+    const float ill = fmaf(-ilh, lam, 1.0f) * ilh;  // 1/lam = ilh + ill
+#pragma unroll
+    for (int i = 0; i < MAX_MAT; ++i)
+      if (i < h.n_mat) {
+        const float n = h.mat_n[i];
+        const F2 nl = two_prod(n, ilh);
+        k[i] = mat_const_acc(sin2, n, h.mat_inv_n[i], F2{h.mat_r2[i], h.mat_r2_lo[i]},
+                             F2{nl.h, fmaf(n, ill, nl.l)});
+      }
+  }
+  template <bool ACC>
+  __device__ __forceinline__ void init_sel(const BlobHeader& h, float c0h, float c0l, float lam) {
+    if constexpr (ACC) {
+      init_acc(h, c0h, c0l, lam);
+    } else {
+      init(h, c0h, lam);
+    }
+  }
   // register select by material id (no local-memory indexing)
   __device__ __forceinline__ MatK get(int m) const {
     MatK r = k[0];
@@ -223,19 +331,67 @@ struct MatTable {
   }
 };
 
-// c, s of one layer; sigma = d(c)/dx sign (-1 propagating, +1 evanescent)
+// sin and cos of 2 pi (p + pl) turns on the FMA pipe (accurate mode), with
+// |pl| << 1e-6. p is reduced exactly to r = p - q/4, |r| <= 1/8 turn, with
+// q = round(4 p) (from the bits of p 4 + 1.5 2^23); sin(2 pi r) and
+// cos(2 pi r) are minimax polynomials in r (max error 5e-9 and 4e-10 on
+// |r| <= 1/8, fitted by Lawson's iteratively reweighted least squares with
+// the coefficients rounded to FP32 one at a time and the rest refitted);
+// pl enters to first order (its square is below 1e-12); the quadrant q mod 4
+// then rotates (s, c) by q pi/2.
+constexpr float SC_S1 = 6.283185005e+00f, SC_S3 = -4.134150696e+01f, SC_S5 = 8.157170105e+01f,
+                SC_S7 = -7.461544800e+01f;
+constexpr float SC_C2 = -1.973920822e+01f, SC_C4 = 6.493914032e+01f, SC_C6 = -8.542311859e+01f,
+                SC_C8 = 5.856121445e+01f;
+__device__ __forceinline__ void sincos_turns_acc(float p, float pl, float& s, float& c) {
+  constexpr float MAGIC = 12582912.0f;  // 1.5 x 2^23: the sum's unit is 1
+  const float t = fmaf(p, 4.0f, MAGIC);
+  const float q = __fsub_rn(t, MAGIC);
+  const int qb = __float_as_int(t);
+  const float r = fmaf(-0.25f, q, p);  // exact (Sterbenz)
+  const float r2 = r * r;
+  const float sp = r * fmaf(fmaf(fmaf(SC_S7, r2, SC_S5), r2, SC_S3), r2, SC_S1);
+  const float cp = fmaf(fmaf(fmaf(fmaf(SC_C8, r2, SC_C6), r2, SC_C4), r2, SC_C2), r2, 1.0f);
+  const float da = TWO_PI * pl;
+  const float s1 = fmaf(da, cp, sp), c1 = fmaf(-da, sp, cp);
+  const bool sw = qb & 1;
+  const float so = sw ? c1 : s1, co = sw ? s1 : c1;
+  s = (qb & 2) ? -so : so;          // quadrants 2, 3
+  c = ((qb + 1) & 2) ? -co : co;    // quadrants 1, 2
+}
+
+// c, s of one layer. Fast mode: the phase reduced exactly to [-1/2, 1/2)
+// turn, hardware sin/cos; e^x and e^-x from two independent hardware
+// exponentials. Accurate mode: the phase as kt d + (ktl d + the rounding
+// error of kt d) turns, sin/cos on the FMA pipe; an evanescent layer's
+// exponent in base 2 with the same split, 2^(y + yl) = 2^y (1 + ln2 yl).
+template <bool ACC = false>
 __device__ __forceinline__ void layer_cs(const MatK& k, float d, float& c, float& s) {
-  const float x = k.kt * d;
-  if (!k.evan) {
-    const float f = x - rintf(x);  // exact reduction in turns
-    __sincosf(f * TWO_PI, &s, &c);
+  if constexpr (!ACC) {
+    const float x = k.kt * d;
+    if (!k.evan) {
+      const float f = x - rintf(x);  // exact reduction in turns
+      __sincosf(f * TWO_PI, &s, &c);
+    } else {
+      // e^x and e^-x from two independent hardware exponentials (no
+      // dependent reciprocal; both with the same relative accuracy)
+      const float e = __expf(x);
+      const float ei = __expf(-x);
+      c = 0.5f * (e + ei);
+      s = 0.5f * (e - ei);
+    }
   } else {
-    // e^x and e^-x from two independent hardware exponentials (no
-    // dependent reciprocal; both with the same relative accuracy)
-    const float e = __expf(x);
-    const float ei = __expf(-x);
-    c = 0.5f * (e + ei);
-    s = 0.5f * (e - ei);
+    const float p = __fmul_rn(k.kt, d);
+    const float pl = fmaf(k.ktl, d, fmaf(k.kt, d, -p));
+    if (!k.evan) {
+      sincos_turns_acc(p, pl, s, c);
+    } else {
+      const float t = LN2_F * pl;
+      const float e0 = exp2f(p), ei0 = exp2f(-p);
+      const float e = fmaf(e0, t, e0), ei = fmaf(-ei0, t, ei0);
+      c = 0.5f * (e + ei);
+      s = 0.5f * (e - ei);
+    }
   }
 }
 
@@ -346,7 +502,7 @@ __device__ __forceinline__ void stack_slots(const StackView& st, bool front, con
 }
 
 // Effective coefficients in the paper's convention (r_p = -r_p(Abeles)).
-template <int P>
+template <int P, bool ACC = false>
 __device__ __forceinline__ Coef tmm_forward(const StackView& st, bool front, const MatTable& mt, float n0,
                                             float cos0, int& layer_steps) {
   constexpr int CKP = Seg<P>::CKP;
@@ -369,7 +525,7 @@ __device__ __forceinline__ Coef tmm_forward(const StackView& st, bool front, con
           k = mt.get(st.m[i]);
         }
         float c, s;
-        layer_cs(k, st.d[i], c, s);
+        layer_cs<ACC>(k, st.d[i], c, s);
         cv_step(vs, c, s * k.q12s, s * k.q21s);
         cv_step(vp, c, s * k.q12p, s * k.q21p);
       }
@@ -480,7 +636,7 @@ __device__ __forceinline__ void cv_rescale_d(CV& v, CV& dv, int& e) {
 // the layer loop of tmm_forward (segments of the material period, material
 // constants and their derivatives in registers) carrying the dual vector
 // (the coating look-up table's entries).
-template <int P>
+template <int P, bool ACC = false>
 __device__ __forceinline__ void tmm_forward_dual(const StackView& st, bool front, const MatTable& mt,
                                                  const MatTableD& mtd, float n0, float cos0, Coef& cf, Coef& dcf) {
   constexpr int CKP = Seg<P>::CKP;
@@ -520,7 +676,7 @@ __device__ __forceinline__ void tmm_forward_dual(const StackView& st, bool front
         }
         const float dthk = st.d[i];
         float c, s, dc, ds;
-        layer_cs(k, dthk, c, s);
+        layer_cs<ACC>(k, dthk, c, s);
         if (!k.evan) {
           const float dth = TWO_PI * dthk * kd.dkt;  // d(phase)
           dc = -s * dth;
@@ -697,7 +853,7 @@ __device__ __forceinline__ void row_guard_fold(CRow& a, int& e, float& acc, floa
 // thickness term's product, times dphi/dcos) + s a dK(dq) v_{j+1} (the same
 // two products on v_{j+1} with the quotients' derivatives); both scale with
 // the material's rho (tt).
-template <int P, class Sink, bool DUAL = false>
+template <int P, class Sink, bool DUAL = false, bool ACC = false>
 __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, const MatTable& mt, float n0,
                                             float cos0, float2 A_s, float2 A_p, int which, Sink& sink,
                                             float* seg, int eA = 0, const TiltTable* tt = nullptr,
@@ -727,7 +883,7 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
           k = mt.get(st.m[i]);
         }
         float c, s;
-        layer_cs(k, st.d[i], c, s);
+        layer_cs<ACC>(k, st.d[i], c, s);
         cv_step(vs, c, s * k.q12s, s * k.q21s);
         cv_step(vp, c, s * k.q12p, s * k.q21p);
       }
@@ -779,7 +935,7 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         } else {
           k = mt.get(st.m[i]);
         }
-        layer_cs(k, st.d[i], c, s);
+        layer_cs<ACC>(k, st.d[i], c, s);
         cv_step(ws, c, s * k.q12s, s * k.q21s);
         cv_step(wp, c, s * k.q12p, s * k.q21p);
       }
@@ -876,6 +1032,33 @@ __device__ __forceinline__ V3 v3(float x, float y, float z) { return V3{x, y, z}
 __device__ __forceinline__ float dot3(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
 __device__ __forceinline__ V3 cross3(V3 a, V3 b) {
   return V3{fmaf(a.y, b.z, -a.z * b.y), fmaf(a.z, b.x, -a.x * b.z), fmaf(a.x, b.y, -a.y * b.x)};
+}
+
+// Accurate mode: a direction is carried as d + dl (dl the low parts), a
+// mirror normal as N + Nl (FP64 rounded to hi + lo). d . N as hi + lo: the
+// three exact products summed with exact sums, then the cross terms.
+__device__ __forceinline__ F2 dot3_df(V3 d, V3 dl, V3 N, V3 Nl) {
+  const F2 a = two_prod(d.x, N.x), b = two_prod(d.y, N.y), c = two_prod(d.z, N.z);
+  const F2 s1 = two_sum(a.h, b.h);
+  const F2 s2 = two_sum(s1.h, c.h);
+  float lo = __fadd_rn(__fadd_rn(a.l, b.l), __fadd_rn(c.l, __fadd_rn(s1.l, s2.l)));
+  lo = fmaf(d.x, Nl.x, fmaf(d.y, Nl.y, fmaf(d.z, Nl.z, lo)));
+  lo = fmaf(dl.x, N.x, fmaf(dl.y, N.y, fmaf(dl.z, N.z, lo)));
+  return fast_two_sum(s2.h, lo);
+}
+// one component of d - 2 (d . N) N as hi + lo (m = -2 d . N)
+__device__ __forceinline__ F2 reflect1_df(float d, float dl, float n, float nl, F2 m) {
+  const F2 p = mul_ff(m, F2{n, nl});
+  const F2 s = two_sum(d, p.h);
+  return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(dl, p.l)));
+}
+__device__ __forceinline__ void reflect_df(V3& d, V3& dl, V3 N, V3 Nl, F2 cd) {
+  const F2 m{-2.0f * cd.h, -2.0f * cd.l};
+  const F2 x = reflect1_df(d.x, dl.x, N.x, Nl.x, m);
+  const F2 y = reflect1_df(d.y, dl.y, N.y, Nl.y, m);
+  const F2 z = reflect1_df(d.z, dl.z, N.z, Nl.z, m);
+  d = V3{x.h, y.h, z.h};
+  dl = V3{x.l, y.l, z.l};
 }
 
 // s/p basis of the slab faces for direction d: s = (d_y, -d_x, 0)/|.|, p = s x d

@@ -58,12 +58,14 @@ uint64_t fused_signature(const wg_ctx* c, const FusedJob* jobs, const FusedBatch
 long long tally_doubles(const wg_design* d, const wg_trace_cfg* cfg);
 long long design_params(const wg_design* d);
 // mirrors, device (non-pruned) layers, material period of the stacks
-void design_shape(const wg_design* d, int* K, int* n_dev, int* period);
+void design_shape(const wg_design* d, int* K, int* n_dev, int* period, int* acc);
 // the design's context; its thicknesses as last set from the host (nm, 0 for
 // layers the design prunes) and its pruned mask, both [design_params]
 wg_ctx* design_ctx(const wg_design* d);
 const float* design_thickness(const wg_design* d);
 const uint8_t* design_pruned(const wg_design* d);
+// the mirrors' reflection probabilities as last set [K]
+const float* design_omega(const wg_design* d);
 // Device bytes a forward (and a backward) evaluation of cfg holds while it
 // runs, for admission against the HBM budget.
 size_t eval_device_bytes(const wg_design* d, const wg_trace_cfg* cfg, bool backward);

@@ -111,6 +111,7 @@ struct AdjArgs {
   const uint8_t* blob;
   int blob_bytes;
   const HitRec* recs;         // sorted by stack
+  const float* lambda;        // [n_lam]: the records carry wavelength indices
   long long n_rec;
   int rec_chunk;              // records per CTA work item
   int n_layers;
@@ -133,7 +134,7 @@ constexpr int kBlock = 256;
 constexpr int kFwdSlots = 3;
 inline int fwd_slots(long long chunk_rays) { return chunk_rays >= 1536 ? 2 : 3; }
 // rays a warp of the forward kernel owns at a time (its lanes plus its two
-// shared-memory queues); a queued ray takes 9 + 4 F words
+// shared-memory queues); a queued ray takes 9 + 4 F words (+ 3 in accurate mode)
 constexpr int kFwdQCap = 48;
 // a warp of the forward kernel reserves eyebox-ray list slots this many at a
 // time (one global atomic per chunk); slots it leaves unused are holes
@@ -142,45 +143,60 @@ constexpr int kExitChunk = 64;
 inline long long exit_list_cap(long long rays, int sm_count) {
   return rays + (long long)sm_count * 64 * kExitChunk;
 }
-inline size_t fwd_smem_bytes(int blob_bytes, long long bins, int F, int n_slots) {
+inline size_t fwd_smem_bytes(int blob_bytes, long long bins, int F, int n_slots, bool acc) {
   return (size_t)blob_bytes + sizeof(float) * (size_t)n_slots * (size_t)bins +
-         sizeof(uint32_t) * (size_t)(kBlock / 32) * 2 * (size_t)kFwdQCap * (size_t)(9 + 4 * F);
+         sizeof(uint32_t) * (size_t)(kBlock / 32) * 2 * (size_t)kFwdQCap * (size_t)(9 + 4 * F + (acc ? 3 : 0));
 }
+// Accurate layer evaluation (direction, incidence cosine, material constants
+// and layer phases carried as hi + lo; sin/cos on the FMA pipe) for designs
+// whose longest stack has more than this many layers: the FP32 evaluation's
+// error grows with the stack length and passes 1e-4 on long stacks.
+constexpr int kAccLayers = 48;
+
+// loads every instance of the forward trace kernel and the field preparation
+// kernel onto the current device (under lazy loading a kernel is otherwise
+// loaded, and its code placed in device memory, at its first launch)
+cudaError_t preload_forward_kernels();
 
 // number of kernels this library has launched (all launchers add to it)
 void note_launches(unsigned long long n);
 unsigned long long launches();
 
 // launchers (return cudaError_t of the launch). P: material period of the
-// design's stacks (0 = any, 2, 3); F: fields per ray (2 = s+p pair).
+// design's stacks (0 = any, 2, 3); F: fields per ray (2 = s+p pair); acc:
+// the accurate layer evaluation (designs with stacks longer than kAccLayers).
 cudaError_t launch_prep_design(uint8_t* blob, const float* mir_x, const float* mir_tilt, const float* mir_omega,
                                const float* geo, int n_mir, float ic_tilt_deg, float thick, cudaStream_t s);
 cudaError_t launch_prep_fields(FieldRec* out, const float* fx, const float* fy, int n_fx, int n_fy,
                                float n_slab, float ic_tilt_deg, int dims, cudaStream_t s);
-cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int gm, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int gm, bool acc, int grid, size_t smem,
+                             cudaStream_t s);
 // several jobs (designs / configurations with the same F and P) in one
 // launch: CTA b works on job cta_job[b] (device arrays; each job's n_cta set)
-cudaError_t launch_trace_fwd_fused(const TraceArgs* jobs_dev, const int* cta_job_dev, int F, int P, int grid,
-                                   size_t smem, cudaStream_t s);
+cudaError_t launch_trace_fwd_fused(const TraceArgs* jobs_dev, const int* cta_job_dev, int F, int P, bool acc,
+                                   int grid, size_t smem, cudaStream_t s);
 // tilt: also record TiltAux per hit and a RayHead per ray (a.tilt_aux, a.ray_heads)
-cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, bool tilt, int gm, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, bool tilt, int gm, bool acc, int grid, size_t smem,
+                              cudaStream_t s);
 // perm (may be null): perm[sorted position] = index of the record in `in`
 cudaError_t launch_bwd_sort(const HitRec* in, long long n, unsigned int* key_count, unsigned int* key_off,
                             unsigned int* key_cursor, HitRec* out, unsigned int* perm, cudaStream_t s);
-cudaError_t launch_bwd_adjoint(const AdjArgs& a, int P, int grid, size_t smem, cudaStream_t s);  // a.tilt_aux picks the variant
+cudaError_t launch_bwd_adjoint(const AdjArgs& a, int P, bool acc, int grid, size_t smem,
+                               cudaStream_t s);  // a.tilt_aux picks the variant
 cudaError_t launch_scatter_grad(const double* acc, int n_layers, const int* dev_to_orig, double* out,
                                 cudaStream_t s);
-cudaError_t launch_coating_eval(const uint8_t* blob, int P, int mirror, int side, long long n, const float* cos0,
-                                const float* lam, float* out, cudaStream_t s);
-cudaError_t launch_coating_grad(const uint8_t* blob, int P, int mirror, int side, long long n, const float* cos0,
-                                const float* lam, const float* w, int which, float* grad, cudaStream_t s);
+cudaError_t launch_coating_eval(const uint8_t* blob, int P, bool acc, int mirror, int side, long long n,
+                                const float* cos0, const float* lam, float* out, cudaStream_t s);
+cudaError_t launch_coating_grad(const uint8_t* blob, int P, bool acc, int mirror, int side, long long n,
+                                const float* cos0, const float* lam, const float* w, int which, float* grad,
+                                cudaStream_t s);
 cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const int* orig_to_dev, int n_orig,
                                     cudaStream_t s);
 // coating look-up table: entries for every (mirror, side, wavelength, bin)
 // of the design (lam: device [n_lam]); records: one hit record per (entry,
 // r or t) carrying the entry's accumulated FP64 weights, in stack order
-cudaError_t launch_lut_build(const uint8_t* blob, int P, int n_mir, int n_lam, const float* lam, int n, float c0,
-                             float dc, float4* out, cudaStream_t s);
+cudaError_t launch_lut_build(const uint8_t* blob, int P, bool acc, int n_mir, int n_lam, const float* lam, int n,
+                             float c0, float dc, float4* out, cudaStream_t s);
 cudaError_t launch_lut_records(const double* grad, int n_mir, int n_lam, const float* lam, int n, float c0, float dc,
                                HitRec* out, cudaStream_t s);
 // ray heads / listed eyebox rays grouped by their mirror-hit count (cnt: device
@@ -194,12 +210,13 @@ cudaError_t launch_exits_sort(const ExitRec* in, long long n, unsigned int* cnt,
 cudaError_t launch_omega_trace(const TraceArgs& a, double* grad_omega, int gm, int sm_count, cudaStream_t s);
 // mirror-tilt gradient of the a.n_heads rays a tilt replay recorded, one
 // pass per group of 8 mirrors starting at a.tilt_k0
-cudaError_t launch_tilt_grad(const TraceArgs& a, int F, int P, int gm, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_tilt_grad(const TraceArgs& a, int F, int P, int gm, bool acc, int grid, size_t smem,
+                             cudaStream_t s);
 size_t tilt_smem_bytes(int blob_bytes, int F);
-int tilt_blocks_per_sm(int F, int P, int gm, size_t smem);
-int trace_fwd_blocks_per_sm(int F, int P, int gm, size_t smem);
-int bwd_replay_blocks_per_sm(int F, int P, bool tilt, int gm, size_t smem);
-int bwd_adjoint_blocks_per_sm(int P, size_t smem);
+int tilt_blocks_per_sm(int F, int P, int gm, bool acc, size_t smem);
+int trace_fwd_blocks_per_sm(int F, int P, int gm, bool acc, size_t smem);
+int bwd_replay_blocks_per_sm(int F, int P, bool tilt, int gm, bool acc, size_t smem);
+int bwd_adjoint_blocks_per_sm(int P, bool acc, size_t smem);
 // dynamic shared memory of the adjoint kernel (blob, per-layer sums, segment buffers)
 size_t adj_smem_bytes(int blob_bytes, int n_layers, int P);
 size_t hit_rec_bytes();

@@ -117,14 +117,14 @@ constexpr size_t kMaxSeen = 256;
 
 // class of an evaluation for the autotuned table
 uint64_t tune_key(const wg_design* d, const wg_trace_cfg* cfg) {
-  int K = 1, n_dev = 0, period = 0;
-  wgh::design_shape(d, &K, &n_dev, &period);
+  int K = 1, n_dev = 0, period = 0, acc = 0;
+  wgh::design_shape(d, &K, &n_dev, &period, &acc);
   const int F = cfg->pol == WG_POL_PAIR ? 2 : 1;
   const int lbin = std::min(7, (n_dev / std::max(1, K)) / 32);
   const long long cells = (long long)cfg->n_lambda * cfg->n_fx * cfg->n_fy;
   const long long per_cell = (cfg->n_rays + cells - 1) / std::max(1ll, cells);
   const int rbin = per_cell < 512 ? 0 : per_cell < 4096 ? 1 : 2;
-  return (uint64_t)F * 1000 + (uint64_t)period * 100 + (uint64_t)lbin * 10 + (uint64_t)rbin;
+  return (uint64_t)acc * 10000 + (uint64_t)F * 1000 + (uint64_t)period * 100 + (uint64_t)lbin * 10 + (uint64_t)rbin;
 }
 
 void load_tune_cache(Serve& S) {

@@ -138,9 +138,16 @@ def lib():
         L.wg_adam_params.argtypes = [vp, vp, vp]
         L.wg_adam_destroy.argtypes = [vp]
         L.wg_adam_destroy.restype = None
+        L.wg_omega_adam_create.argtypes = [vp, C.POINTER(OmegaAdamOpts), C.POINTER(vp)]
+        L.wg_omega_adam_step.argtypes = [vp, vp, vp, vp]
+        L.wg_omega_adam_destroy.argtypes = [vp]
+        L.wg_omega_adam_destroy.restype = None
+        L.wg_design_version.argtypes = [vp, C.POINTER(C.c_uint64)]
         for name in ("wg_init", "wg_create_design", "wg_set_params", "wg_eval_coating", "wg_eval_coating_grad",
                      "wg_trace_forward", "wg_trace_backward", "wg_loss", "wg_trace_forward_noalloc",
-                     "wg_submit", "wg_poll", "wg_cancel", "wg_autotune"):
+                     "wg_submit", "wg_poll", "wg_cancel", "wg_autotune", "wg_omega_trace", "wg_set_omega",
+                     "wg_adam_create", "wg_adam_step", "wg_adam_params", "wg_omega_adam_create",
+                     "wg_omega_adam_step", "wg_design_version"):
             getattr(L, name).restype = C.c_int32
         _lib = L
     return _lib
@@ -189,6 +196,42 @@ class _CfgHolder:
 class AdamOpts(C.Structure):
     _fields_ = [("lr_nm", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
                 ("d_min_nm", C.c_float), ("d_max_nm", C.c_float)]
+
+
+class OmegaAdamOpts(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("lo", C.c_float), ("hi", C.c_float)]
+
+
+class OmegaAdam:
+    """Optimizer of a design's reflection probabilities (wg_omega_adam_*):
+    Adam on omega with the gradient of a loss to minimize, clipped to
+    [lo, hi]; each step writes omega to the design."""
+
+    def __init__(self, dh, lr=0.02, beta1=0.9, beta2=0.999, eps=1e-8, lo=0.02, hi=0.98):
+        self.n = dh.design.n_mirrors
+        o = OmegaAdamOpts(lr, beta1, beta2, eps, lo, hi)
+        h = C.c_void_p()
+        _check(lib().wg_omega_adam_create(dh.h, C.byref(o), C.byref(h)))
+        self.h = h
+
+    def step(self, grad_omega, stream=None):
+        """grad_omega: FP64 [K] (torch CUDA tensor or numpy array). Returns the new omega (FP32)."""
+        out = np.zeros(self.n, dtype=np.float32)
+        _check(lib().wg_omega_adam_step(self.h, _ptr(grad_omega), out.ctypes.data,
+                                        stream if stream is not None else _current_stream()))
+        return out
+
+    def close(self):
+        if self.h:
+            lib().wg_omega_adam_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Adam:
@@ -262,27 +305,24 @@ def optimize_omega(ctx, dh, cfg, n_iter, lr=0.02, lo=0.02, hi=0.98, beta1=0.9, b
     brightness term of Eq. 1) of the scalar-reflectance geometric model over
     the mirrors' omega. Each iteration traces cfg's rays (wg_omega_trace,
     fixed Philox keys), takes the score-function gradient and one Adam step
-    on the K values (here on the host), clipped to [lo, hi], and sets omega.
-    Returns the per-iteration I_mean and the final omega."""
+    on the K values (wg_omega_adam_step, on the GPU), clipped to [lo, hi],
+    which sets omega. Returns the per-iteration I_mean and the final omega."""
     import torch
     tally = torch.zeros(cfg.tally_shape, dtype=torch.float64, device="cuda")
     G = torch.zeros_like(tally)
     ctx.loss(dh, cfg, tally, G, w_f=0.0, w_e=0.0)  # dL/dtally of L = -I_mean: the pupil masks, any tally
-    om = np.asarray(dh.design.mirror_omega, dtype=np.float64).copy()
-    m = np.zeros_like(om)
-    v = np.zeros_like(om)
-    g = np.zeros_like(om)
+    g = torch.zeros(dh.design.n_mirrors, dtype=torch.float64, device="cuda")
+    opt = OmegaAdam(dh, lr=lr, beta1=beta1, beta2=beta2, eps=eps, lo=lo, hi=hi)
+    om = np.asarray(dh.design.mirror_omega, dtype=np.float32).copy()
     hist = []
-    for t in range(1, n_iter + 1):
+    for _ in range(n_iter):
         ctx.omega_trace(dh, cfg, tally, G, g)
         hist.append(ctx.loss(dh, cfg, tally, w_f=0.0, w_e=0.0)[1])
-        m = beta1 * m + (1.0 - beta1) * g
-        v = beta2 * v + (1.0 - beta2) * g * g
-        om = np.clip(om - lr * (m / (1.0 - beta1 ** t)) / (np.sqrt(v / (1.0 - beta2 ** t)) + eps), lo, hi)
-        dh.set_omega(om)
+        om = opt.step(g)
+    opt.close()
     ctx.omega_trace(dh, cfg, tally)
     hist.append(ctx.loss(dh, cfg, tally, w_f=0.0, w_e=0.0)[1])
-    return np.array(hist), om.astype(np.float32)
+    return np.array(hist), om
 
 
 class DesignHandle:
@@ -318,6 +358,12 @@ class DesignHandle:
             keep.append(a)
             tl, ntl = a.ctypes.data, a.size
         _check(lib().wg_set_params(self.h, th, nth, tl, ntl, stream if stream is not None else _current_stream()))
+
+    def version(self):
+        """wg_design_version: increases with every change of the parameters."""
+        v = C.c_uint64()
+        _check(lib().wg_design_version(self.h, C.byref(v)))
+        return int(v.value)
 
     def destroy(self):
         if self.h:
@@ -469,7 +515,10 @@ def _torch_autograd():
         forward: wg_set_params (thicknesses, and the mirror tilts in degrees
         when given) + wg_trace_forward; backward: wg_trace_backward with
         grad_output as dL/dtally, returning dL/dthickness and, for a tilt
-        tensor, dL/dtilt per degree (FP64 -> the inputs' dtypes)."""
+        tensor, dL/dtilt per degree (FP64 -> the inputs' dtypes). The
+        backward differentiates the design as it is when it runs, so it
+        refuses (RuntimeError) when the design's parameters changed after its
+        forward (another forward or an optimizer step on the same handle)."""
 
         @staticmethod
         def forward(actx, thickness, ctx, dh, cfg, tilt_deg=None):
@@ -478,6 +527,7 @@ def _torch_autograd():
             tally = torch.empty(cfg.tally_shape, dtype=torch.float64, device=thickness.device)
             ctx.trace_forward(dh, cfg, tally, stats=False)
             actx.wg = (ctx, dh, cfg)
+            actx.version = dh.version()
             actx.n = thickness.numel()
             actx.dtype = thickness.dtype
             actx.tilt = None if tilt_deg is None else (tilt_deg.numel(), tilt_deg.dtype, tilt_deg.device)
@@ -486,6 +536,10 @@ def _torch_autograd():
         @staticmethod
         def backward(actx, grad_tally):
             ctx, dh, cfg = actx.wg
+            if dh.version() != actx.version:
+                raise RuntimeError("WGTrace.backward: the design's parameters changed after this forward "
+                                   "(another forward or an optimizer step on the same design handle); "
+                                   "its gradient would be taken at other parameters")
             g = torch.empty(actx.n, dtype=torch.float64, device=grad_tally.device)
             gt = None
             if actx.tilt is not None and actx.needs_input_grad[4]:

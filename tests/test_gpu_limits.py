@@ -9,7 +9,7 @@ import torch
 
 from paper_2601_04370_gb300 import workloads as W
 
-from test_gpu_parity import _grad_compare, compare, ctx, run_gpu  # noqa: F401 (fixture)
+from test_gpu_parity import tilt_compare, _grad_compare, compare, ctx, run_gpu  # noqa: F401 (fixture)
 
 pytestmark = pytest.mark.gpu
 
@@ -37,26 +37,30 @@ def test_64_mirrors(ctx, ora):
     assert st["overflow"] == 0 and st["n_nonfinite"] == 0
     ref_d, ref_t = ora.trace_grad(D, C, G)
     _grad_compare(gd, ref_d)
-    assert np.linalg.norm(gt - ref_t) <= 1e-3 * np.linalg.norm(ref_t)
+    tilt_compare(gt, ref_t)
 
 
 def test_512_layers_per_mirror(ctx, ora):
-    """Tallies hold 1e-4. Gradients: the 1e-3 bound holds to 200 layers (the
-    largest configuration, tests in test_gpu_parity.py); at 512 layers the FP32
-    conditioning of single coatings widens (per-hit relative error p99 3e-3 to
-    7e-3 against 1e-3 to 3e-3 at 200 layers, measured against the oracle), and
-    the traced gradient sits near 1e-2, so the bound here is 3e-2."""
+    """The longest stacks a mirror may carry (the accurate layer evaluation):
+    paths, tallies and per-ray intensities hold the configurations' bounds.
+    The gradients hold 3e-2, not 1e-3. In total-reflection bands of 512-layer
+    stacks a hit's |dr/dd| reaches ~6 per nm while the ray's intensity
+    gradient 2 Re(A dr/dd) is ~300 times smaller than its terms (measured on
+    single rays of this case, 630 nm, |t| ~ 7e-7). The FP32 vector sweep
+    leaves ~1e-5 on r there even with exact inputs, and the cancellation
+    turns that into 1-3 % on those rays (relative L2 of the whole gradient:
+    thicknesses 1.2e-2, tilts 2.0e-2). Every configuration (up to 200
+    layers) holds 1e-3 (test_gpu_differentiation.py: 2.2e-4)."""
     D = W._prma_design(3, 1.71, 1.5, 2, 512, [W.N_SIO2, W.N_TIO2, W.N_TA2O5], seed=5)
     _, C = W.representative(n_rays=3000, n_layers=8)
     C = C.replace(fx_deg=[-12.0, 0.5, 9.0], fy_deg=[-6.0, 4.0], eb_nx=16, eb_ny=12, n_rays=3000,
                   eb_cx_mm=float(D.mirror_x_mm.mean()))
     g, G, gd, gt, st = _fwd_bwd(ctx, D, C)
-    compare(C, g, ora.trace(D, C, records=True), ray_tol=1e-3)
+    compare(C, g, ora.trace(D, C, records=True))
     assert st["overflow"] == 0 and st["n_nonfinite"] == 0
     ref_d, ref_t = ora.trace_grad(D, C, G)
-    assert np.all(np.isfinite(gd))
-    assert np.linalg.norm(gd - ref_d) <= 3e-2 * np.linalg.norm(ref_d)
-    assert np.linalg.norm(gt - ref_t) <= 3e-2 * np.linalg.norm(ref_t)
+    _grad_compare(gd, ref_d, tol=3e-2)
+    tilt_compare(gt, ref_t, tol=3e-2)
 
 
 @pytest.mark.parametrize("kind", ["no_layers", "all_pruned"])
@@ -75,6 +79,6 @@ def test_bare_mirror(ctx, ora, kind):
     compare(C, g, ora.trace(D, C, records=True))
     ref_d, ref_t = ora.trace_grad(D, C, G)
     _grad_compare(gd, ref_d)
-    assert np.linalg.norm(gt - ref_t) <= 1e-3 * np.linalg.norm(ref_t)
+    tilt_compare(gt, ref_t)
     if kind == "all_pruned":
         assert np.all(gd[:8] == 0.0)

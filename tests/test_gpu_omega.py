@@ -54,3 +54,33 @@ def test_omega_optimization_raises_throughput(wg):
     assert hist[-1] > hist[0] * 1.02, hist
     dh.destroy()
     ctx.close()
+
+
+def test_omega_adam_steps_match_the_oracle(wg, ora):
+    """Five steps of wg_omega_adam_step on gradients spanning many decades,
+    with values driven into both clip bounds, a non-finite entry, host and
+    device gradients: the omega the design takes equals the oracle's step
+    (FP64 state on both sides, FP32 in the design)."""
+    D, _ = W.representative(n_rays=1000)
+    ctx = wg.Context(0)
+    dh = ctx.create_design(D)
+    K = D.n_mirrors
+    w0 = np.array([0.5, 0.03, 0.97, 0.2, 0.6, 0.45], dtype=np.float32)[:K]
+    dh.set_omega(w0)
+    opt = wg.OmegaAdam(dh, lr=0.02)
+    rng = np.random.default_rng(3)
+    w, m, v = w0.astype(np.float64), np.zeros(K), np.zeros(K)
+    for t in range(1, 6):
+        g = rng.normal(size=K) * 10.0 ** rng.uniform(-5, 4, size=K)
+        g[1] = 3.0    # pushes omega_1 below lo
+        g[2] = -3.0   # pushes omega_2 above hi
+        if t == 3:
+            g[4] = np.nan
+        gd = torch.as_tensor(g, device="cuda") if t % 2 else g
+        got = opt.step(gd)
+        w, m, v = ora.adam_clipped_step(w, m, v, g, t, lr=0.02)
+        assert np.allclose(got, w.astype(np.float32), rtol=0, atol=1e-7), (t, got, w)
+    assert got[1] == np.float32(0.02) and got[2] == np.float32(0.98)
+    opt.close()
+    dh.destroy()
+    ctx.close()

@@ -53,7 +53,7 @@ def run_gpu(ctx, D, C, records=True, rays=None, dh=None):
     return out
 
 
-def compare(C, g, o, frac_max=1e-4, tol=1e-4, ray_tol=1e-4):
+def compare(C, g, o, frac_max=1e-4, tol=1e-4, ray_tol=1e-4, bin_tol=1e-4, bin_min=100):
     rg, ro = g["records"], o["records"]
     mism = (rg["hash"] != ro["hash"]) | (rg["bin"] != ro["bin"]) | (rg["n_events"] != ro["n_events"])
     n = len(rg)
@@ -67,7 +67,13 @@ def compare(C, g, o, frac_max=1e-4, tol=1e-4, ray_tol=1e-4):
             to[ro["bin"][i]] -= ro["I"][i]
     rel = np.linalg.norm(tg - to) / max(np.linalg.norm(to), 1e-300)
     assert rel <= tol, rel
+    # per bin, for bins that at least bin_min matched rays reach
     ok = ~mism
+    cnt = np.bincount(ro["bin"][ok & (ro["bin"] >= 0)], minlength=to.size)
+    full = cnt >= bin_min
+    if full.any():
+        bin_rel = np.abs(tg[full] - to[full]) / np.abs(to[full])
+        assert bin_rel.max() <= bin_tol, (bin_rel.max(), int(full.sum()))
     # per-ray intensities of matched rays (FP32 vs FP64): relative to the
     # ray's launched power (1) or its weight if larger. Single rays inherit
     # the FP32 conditioning of their coating hits (up to ~1e-3 near thin-film
@@ -108,11 +114,19 @@ def test_coating_coefficients(ctx, ora, L, side):
         nm, dd = nm[::-1], dd[::-1]
     err = np.array([np.abs(got[i] - np.array(ora.tmm(D.n_slab, D.n_slab, nm, dd, float(lam[i]), float(cos0[i]))))
                     .max() for i in range(n)])
-    # FP32 conditioning (an exactly rounded FP32 evaluation of the same chain
-    # reaches median 2.5e-6, p99 1.1e-4, max 6.7e-4 at 200 layers on these inputs)
-    assert np.median(err) <= 1e-5, np.median(err)
-    assert np.quantile(err, 0.99) <= 3e-4, np.quantile(err, 0.99)
-    assert err.max() <= 5e-3, err.max()   # the fast sin/cos adds ~2^-21 per layer
+    if L > 48:
+        # the accurate layer evaluation (stacks longer than 48 layers):
+        # measured median 5e-7, p99 1.6e-5, max 1e-4 at 200 layers; an exactly
+        # rounded FP32 evaluation of the plain chain reaches p99 1.1e-4
+        assert np.median(err) <= 2e-6, np.median(err)
+        assert np.quantile(err, 0.99) <= 5e-5, np.quantile(err, 0.99)
+        assert err.max() <= 5e-4, err.max()
+    else:
+        # FP32 conditioning of the fast evaluation (measured median 2.5e-6,
+        # p99 2.8e-5, max 6.8e-4 at 40 layers)
+        assert np.median(err) <= 1e-5, np.median(err)
+        assert np.quantile(err, 0.99) <= 3e-4, np.quantile(err, 0.99)
+        assert err.max() <= 5e-3, err.max()   # the fast sin/cos adds ~2^-21 per layer
     dh.destroy()
 
 
@@ -178,14 +192,14 @@ def test_trace_3d_matches_oracle(ctx, ora, pol):
 
 
 def test_trace_200_layer_stacks_match_oracle(ctx, ora):
-    """200-layer stacks: FP32 geometry fixes each incidence angle to ~1e-7
-    and a 200-layer stack's coefficients amplify that (an exactly rounded FP32
-    evaluation of the chain alone has p99 error 1e-4 per coefficient), so the
-    tally bound is 2.5e-4 here; the 40-layer representative design holds 1e-4."""
+    """200-layer stacks run the accurate layer evaluation (incidence cosine,
+    phase rates and phases as hi + lo): they hold the same bounds as the
+    40-layer design (measured: no path flips, tally 5e-6, per-ray 1.6e-5 at
+    the 99.9th percentile)."""
     D, C = W.differentiation(n_rays=1728 * 40)
     g = run_gpu(ctx, D, C)
     o = ora.trace(D, C, records=True)
-    compare(C, g, o, tol=2.5e-4, ray_tol=1e-3)
+    compare(C, g, o)
 
 
 def test_trace_ragged_and_tiny_cells(ctx, ora):
@@ -242,22 +256,10 @@ def test_full_size_representative_sampled(ctx, ora):
     rg = g["records"]
     N = C.total_rays
     assert g["stats"]["n_rays"] == N and len(rg) == N
-    rng = np.random.default_rng(0)
-    starts = np.sort(rng.choice(N - 64, 48, replace=False))
-    mism = 0
-    tot = 0
-    dI = []
-    for s in starts:
-        o = ora.trace(D, C, rays=(int(s), int(s) + 64), records=True, nthreads=4)["records"]
-        gg = rg[s:s + 64]
-        bad = (gg["hash"] != o["hash"]) | (gg["bin"] != o["bin"])
-        mism += int(bad.sum())
-        tot += 64
-        ok = ~bad
-        assert np.all(np.abs(gg["I"][ok] - o["I"][ok]) <= 1e-2 * np.maximum(1, o["I"][ok]))
-        dI.append(np.abs(gg["I"][ok] - o["I"][ok]) / np.maximum(1, o["I"][ok]))
-    assert mism <= max(1, int(1e-4 * tot) + 1)
-    assert np.quantile(np.concatenate(dI), 0.99) <= 1e-4
+    mism, tot, dI = sampled_rays(ora, D, C, rg, seed=0)
+    assert mism <= max(1, int(1e-4 * tot)), (mism, tot)
+    assert np.quantile(dI, 0.999) <= 1e-4, np.quantile(dI, 0.999)
+    assert dI.max() <= 1e-2
     # tally equals the records' eyebox contributions; ledger sums to launched power in expectation
     t = g["tally"].reshape(-1)
     ok = rg["bin"] >= 0
@@ -286,6 +288,36 @@ def test_loss_matches_oracle(ctx, ora, cfg, kind):
     g = G.cpu().numpy()
     assert np.abs(g - Gr).max() <= 1e-12 * np.abs(Gr).max()
     dh.destroy()
+
+
+def sampled_rays(ora, D, C, rg, seed, n_runs=100, run=1000):
+    """n_runs runs of `run` consecutive rays at seeded starts across the
+    whole launch (1e5 rays), traced by the oracle one by one and compared with
+    the GPU records rg: (rays on another path, rays compared, per-ray
+    intensity errors of the others relative to max(1, I))."""
+    N = len(rg)
+    rng = np.random.default_rng(seed)
+    starts = np.sort(rng.choice(N // run, n_runs, replace=False)) * run
+    mism, tot, dI = 0, 0, []
+    for s in starts:
+        o = ora.trace(D, C, rays=(int(s), int(s) + run), records=True, nthreads=0)["records"]
+        gg = rg[s:s + run]
+        bad = (gg["hash"] != o["hash"]) | (gg["bin"] != o["bin"]) | (gg["n_events"] != o["n_events"])
+        mism += int(bad.sum())
+        tot += run
+        ok = ~bad
+        dI.append(np.abs(gg["I"][ok] - o["I"][ok]) / np.maximum(1, o["I"][ok]))
+    return mism, tot, np.concatenate(dI)
+
+
+def tilt_compare(gt, ref, tol=1e-3):
+    """Tilt gradients: relative L2 error <= tol, and per mirror
+    |g_k - ref_k| <= tol (|ref_k| + 0.1 max|ref|)."""
+    assert np.all(np.isfinite(gt)), "non-finite tilt gradient"
+    assert np.linalg.norm(gt - ref) <= tol * np.linalg.norm(ref), np.linalg.norm(gt - ref) / np.linalg.norm(ref)
+    err = np.abs(gt - ref)
+    bound = tol * (np.abs(ref) + 0.1 * np.abs(ref).max())
+    assert np.all(err <= bound), (np.nonzero(err > bound)[0], gt, ref)
 
 
 def _grad_compare(g, ref, tol=1e-3, n_pick=20):
@@ -351,7 +383,7 @@ def test_tilt_gradient_matches_oracle_adjoint(ctx, ora, cfg):
     ref_d, ref_t = ora.trace_grad(D, C, G.cpu().numpy())
     _grad_compare(g.cpu().numpy(), ref_d)
     assert np.all(np.isfinite(gt))
-    assert np.linalg.norm(gt - ref_t) <= 1e-3 * np.linalg.norm(ref_t), (gt, ref_t)
+    tilt_compare(gt, ref_t)
     dh.destroy()
 
 
@@ -426,7 +458,7 @@ def test_autograd_function_with_tilts(ctx, ora):
     ref_d, ref_t = ora.trace_grad(D, C, G.cpu().numpy())
     _grad_compare(th.grad.double().cpu().numpy(), ref_d)
     gt = tl.grad.double().cpu().numpy()
-    assert np.linalg.norm(gt - ref_t) <= 1e-3 * np.linalg.norm(ref_t), (gt, ref_t)
+    tilt_compare(gt, ref_t)
     dh.destroy()
 
 

@@ -49,3 +49,30 @@ def test_adam_converges_to_the_minimum_of_a_quadratic():
         g = 2.0 * (th.astype(np.float64) - a)
         th, m, v = O.adam_projected_step(th, m, v, g, t, lr=0.5)
     assert np.max(np.abs(th - a)) < 0.3
+
+
+# ---------------------------------------------------------------------------
+# the reflection probabilities' step (Adam on omega, clipped to [lo, hi])
+# ---------------------------------------------------------------------------
+
+def test_omega_first_step_is_lr_against_the_gradient_and_clipped():
+    w = np.array([0.5, 0.5, 0.03, 0.97, 0.4])
+    g = np.array([2.0, -1e-3, 5.0, -7.0, np.nan])
+    w1, m, v = O.adam_clipped_step(w, np.zeros(5), np.zeros(5), g, 1, lr=0.02, lo=0.02, hi=0.98)
+    # bias-corrected first step: lr g / (|g| + eps); then the clip
+    assert np.allclose(w1[:2], [0.48, 0.52], atol=1e-9)
+    assert w1[2] == 0.02 and w1[3] == 0.98   # 0.03 - 0.02 and 0.97 + 0.02 leave [lo, hi]
+    assert w1[4] == 0.4 and m[4] == 0.0 and v[4] == 0.0   # non-finite gradient: untouched
+    assert np.allclose(m[:4], 0.1 * g[:4]) and np.allclose(v[:4], 0.001 * g[:4] ** 2)
+
+
+def test_omega_adam_converges_to_an_interior_minimum():
+    # f = sum (w - a)^2 with a inside (lo, hi): a sign error or a dropped bias
+    # correction would not settle near a
+    a = np.array([0.1, 0.35, 0.6, 0.9])
+    w = np.full(4, 0.5)
+    m = np.zeros(4)
+    v = np.zeros(4)
+    for t in range(1, 3001):
+        w, m, v = O.adam_clipped_step(w, m, v, 2.0 * (w - a), t, lr=0.005)
+    assert np.max(np.abs(w - a)) < 2e-3
