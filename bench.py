@@ -96,7 +96,8 @@ class Clocks:
     def __init__(self, device):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.mkdtemp(prefix="wg_clocks_"), f"clocks_rank{device}.csv")
 
     def start(self):
         try:
@@ -256,15 +257,159 @@ def cpu_oracle_rate(D, C, G, budget_s=12.0, max_rays=None, sample=None):
                        f"FP64 forward + adjoint, {t:.1f} s wall on {nthreads} host threads"), h, t, (k, m)
 
 
-def run_serving(dev, n_requests, max_slots, cache_path):
-    """The serving trace (Poisson arrivals at 200 req/s, designs drawn from the
+def run_child(argv, timeout):
+    """One measurement in its own process (its own contexts; a failure there
+    is reported in the line, not fatal to the bench)."""
+    cmd = [sys.executable, "-X", "faulthandler", os.path.abspath(__file__), *argv]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout)
+    except subprocess.TimeoutExpired:
+        return {"error": f"timed out after {timeout} s"}
+    lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
+    if r.returncode == 0 and lines:
+        return json.loads(lines[-1])
+    return {"error": f"exit {r.returncode}", "stderr_tail": r.stderr[-1500:]}
+
+
+def run_batching(dev, rounds):
+    """The batching configuration: the 64 designs of the batching pool (K
+    3..8, L 10..200 with 30% of layers pruned, 1e5..1e7 rays) traced by
+    wg_trace_forward_batch, once as one batch (one fused launch per kernel
+    variant and launch-shape group, graph-replayed from the third round) and
+    once one design per call (each its own launch, also graph-replayed); three
+    untimed rounds first (autotuning, capture), then `rounds` timed ones."""
+    import numpy as np
+    import torch
+    from paper_2601_04370_gb300 import wg
+    from paper_2601_04370_gb300 import workloads as W
+    pool = W.batching(n_designs=64, seed=4)
+    ctx = wg.Context(dev)
+    dhs = [ctx.create_design(D) for D, _ in pool]
+    cfgs = [C for _, C in pool]
+    ts = [torch.zeros(C.tally_shape, dtype=torch.float64, device=f"cuda:{dev}") for C in cfgs]
+
+    def longest_stack(D):
+        kept = np.split(1 - D.pruned.astype(np.int64), np.cumsum(D.n_layers)[:-1])
+        return max(int(k.sum()) for k in kept)
+    n_acc = sum(1 for D, _ in pool if longest_stack(D) > 48)
+
+    def batched():
+        st, rep = ctx.trace_forward_batch(dhs, cfgs, ts)
+        return sum(s["n_hits"] for s in st), rep
+
+    def single():
+        hits, rep = 0, True
+        for dh, C, t in zip(dhs, cfgs, ts):
+            st, r = ctx.trace_forward_batch([dh], [C], [t])
+            hits += st[0]["n_hits"]
+            rep = rep and r
+        return hits, rep
+
+    out = {"designs": len(pool), "rays": int(sum(C.total_rays for C in cfgs)),
+           "designs_accurate_mode": n_acc}
+    for name, fn in (("batched", batched), ("one_design_per_launch", single)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        n0 = wg.kernel_launches()
+        t0 = time.perf_counter()
+        hits, reps = 0, []
+        for _ in range(rounds):
+            h, rep = fn()
+            hits += h
+            reps.append(rep)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        out[name] = {"interactions_per_s": hits / wall, "ms_per_round": 1e3 * wall / rounds,
+                     "interactions_per_round": hits // rounds, "graph_replayed": all(reps),
+                     "kernel_launches_per_round": (wg.kernel_launches() - n0) / rounds}
+    out["speedup"] = out["batched"]["interactions_per_s"] / out["one_design_per_launch"]["interactions_per_s"]
+    for dh in dhs:
+        dh.destroy()
+    ctx.close()
+    return out
+
+
+def bench_differentiation(ctx, dev, args, pg, ws, rank, flush, stream, pk, pk_kind):
+    """fwd + loss + bwd (thickness and tilt gradients) of the differentiation
+    configuration at 1e8 rays, timed with CUDA events; rooflines of the forward
+    and of the thin-film adjoint (accurate mode) in the same units as the
+    headline; the oracle's forward + adjoint on a sample of at most 1e5 rays."""
+    import torch
+    from paper_2601_04370_gb300 import wg
+    from paper_2601_04370_gb300 import workloads as W
+    D, C = W.differentiation()
+    C = C.replace(seed=C.seed + 1000003 * rank)
+    dh = ctx.create_design(D)
+    tally = torch.zeros(C.tally_shape, dtype=torch.float64, device=f"cuda:{dev}")
+    G = torch.zeros_like(tally)
+    g = torch.zeros(D.total_layers, dtype=torch.float64, device=f"cuda:{dev}")
+    gt = torch.zeros(D.n_mirrors, dtype=torch.float64, device=f"cuda:{dev}")
+    st_f = ctx.trace_forward(dh, C, tally)
+    ctx.loss(dh, C, tally, G)
+    st_b = ctx.trace_backward(dh, C, G, g, grad_tilt=gt)
+    hits = st_f["n_hits"]
+    ms, fm, bm, adj = [], [], [], []
+    for i in range(1 + args.d_steps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        flush.zero_()
+        ev[0].record(stream)
+        ctx.trace_forward(dh, C, tally, stats=False)
+        ev[1].record(stream)
+        ctx.loss(dh, C, tally, G)
+        ev[2].record(stream)
+        sb = ctx.trace_backward(dh, C, G, g, grad_tilt=gt)
+        ev[3].record(stream)
+        ev[3].synchronize()
+        if i >= 1:
+            ms.append(ev[0].elapsed_time(ev[3]))
+            fm.append(ev[0].elapsed_time(ev[1]))
+            bm.append(ev[2].elapsed_time(ev[3]))
+            adj.append(sb)
+    t = allmax(pg, sum(ms) / 1e3, dev)
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = fp32_peak_tflops(sm, float(pk.get("sm_max_mhz", 2070.0)))
+    f_fwd = FLOPS_PER_LAYER * st_f["n_layer_steps"] + FLOPS_PER_HIT * hits
+    ach_f = f_fwd / (statistics.mean(fm) / 1e3) / 1e12
+    n_adj = sum(s["n_adjoint_launches"] for s in adj)
+    adj_ms = sum(s["adjoint_ms"] for s in adj)
+    adj_steps = sum(s["n_adjoint_steps"] for s in adj)
+    f_adj = FLOPS_ADJ_LAYER_TILT * adj_steps / max(1, n_adj)
+    ach_a = f_adj / (adj_ms / max(1, n_adj) / 1e3) / 1e12 if adj_ms > 0 else 0.0
+    peak_source = f"derived: {sm} SMs x 128 FP32 lanes x 2 flop x {float(pk.get('sm_max_mhz', 2070.0)):.0f} MHz ({pk_kind})"
+    out = {"workload": "differentiation fwd+loss+adjoint: as representative with 6 mirrors x 200 layers (1200 "
+                       "thicknesses) + 6 tilts, 1e8 rays per GPU, accurate layer evaluation",
+           "value": allsum(pg, hits * len(ms), dev) / t, "unit": UNIT, "steps": len(ms), "warmup": 1,
+           "ms_per_step": 1e3 * t / len(ms), "fwd_ms": statistics.mean(fm), "bwd_ms": statistics.mean(bm),
+           "fwd_interactions_per_s": hits / (statistics.mean(fm) / 1e3), "interactions_per_step": hits,
+           "rays": C.total_rays, "layer_steps_per_hit": st_f["n_layer_steps"] / max(1, hits),
+           "overflow": st_b["overflow"], "nonfinite": st_b["n_nonfinite"],
+           "roofline": {"bound": "alu", "kernel": "k_bwd_adjoint (tilt variant, accurate mode)", "achieved": ach_a,
+                        "peak": peak, "unit": "TFLOP/s", "frac": ach_a / peak, "traffic": None,
+                        "flops_per_launch": f_adj, "launch_ms": adj_ms / max(1, n_adj), "launches": n_adj,
+                        "units": f"{adj_steps / max(1, n_adj):.4g} record layer steps per launch x "
+                                 f"{FLOPS_ADJ_LAYER_TILT} flops", "peak_source": peak_source},
+           "roofline_fwd": {"bound": "alu", "kernel": "k_trace_fwd (accurate mode)", "achieved": ach_f, "peak": peak,
+                            "unit": "TFLOP/s", "frac": ach_f / peak, "flops_per_launch": f_fwd,
+                            "units": f"{hits} interactions x ({FLOPS_PER_LAYER} x "
+                                     f"{st_f['n_layer_steps'] / max(1, hits):.1f} layers + {FLOPS_PER_HIT}) flops",
+                            "peak_source": peak_source}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"], _, _, _ = cpu_oracle_rate(D, C, G.cpu().numpy(), budget_s=max(2.0, args.cpu_budget / 2),
+                                                       max_rays=100_000)
+    dh.destroy()
+    return out
+
+
+def run_serving(dev, n_requests, max_slots, cache_path, rate_hz=200.0):
+    """The serving trace (Poisson arrivals at rate_hz, designs drawn from the
     64-design batching pool and kept resident, 5% loss+gradient requests at
     1e6..1e8 rays) submitted at its arrival times through wg_submit; latency
     of a request = submit -> completion as the runtime measures it."""
     import numpy as np
     from paper_2601_04370_gb300 import wg
     from paper_2601_04370_gb300 import workloads as W
-    reqs = W.serving_trace(n_requests=n_requests)
+    reqs = W.serving_trace(n_requests=n_requests, rate_hz=rate_hz)
     ctx = wg.Context(dev, max_slots=max_slots, autotune_cache=cache_path)
     handles = {}
     for r in reqs:
@@ -289,17 +434,22 @@ def run_serving(dev, n_requests, max_slots, cache_path):
         wall = time.perf_counter() - t0
         return res, wall
 
-    # warm-up, untimed and the same in both modes: the whole trace once, so
-    # every class is autotuned and captured before the timed pass
-    run(reqs)
+    # warm-up, untimed and the same in both modes: the first 400 requests
+    # once, so the classes they meet are autotuned before the timed pass
+    run(reqs[:400])
     res, wall = run(reqs)
     ok = [r for r in res if r["status"] == wg.WG_OK]
+    failed = [r for r in res if r["status"] != wg.WG_OK]
+    if not ok:
+        return {"requests": len(reqs), "completed": 0, "error": "no request completed",
+                "failures": [(r["status"], r.get("error", "")) for r in failed[:5]]}
     lat = np.array([r["queue_ms"] + r["run_ms"] for r in ok])
     hits = sum(r["stats"]["n_hits"] for r in ok)
     out = {"requests": len(reqs), "completed": len(ok), "p50_ms": float(np.percentile(lat, 50)),
            "p99_ms": float(np.percentile(lat, 99)), "interactions_per_s": hits / wall, "wall_s": wall,
            "mean_batch": float(np.mean([r["batch_size"] for r in ok])),
-           "graph_replays": int(sum(r["graph_replayed"] for r in ok))}
+           "graph_replays": int(sum(r["graph_replayed"] for r in ok)), "failed": len(failed),
+           "failures": [(r["status"], r.get("error", "")) for r in failed[:3]]}
     for dh in handles.values():
         dh.destroy()
     ctx.close()
@@ -530,6 +680,21 @@ def run_ours(args):
                                                              budget_s=max(2.0, args.cpu_budget / 3))
         dhe.destroy()
 
+    # the differentiation configuration (6 mirrors x 200 layers = 1200
+    # thicknesses + 6 tilts, 1e8 rays, the accurate layer evaluation): the
+    # same step (forward, loss, backward with thickness and tilt gradients),
+    # after the timed region, with its own rooflines and CPU baseline
+    differentiation = None
+    if not args.no_differentiation:
+        differentiation = bench_differentiation(ctx, dev, args, pg, ws, rank, flush, stream, pk, pk_kind)
+
+    # the batching configuration: 64 designs (K 3..8, L 10..200, 30% pruned,
+    # 1e5..1e7 rays) in one fused launch per kernel variant with autotuned
+    # shapes and graph replay, against one design per launch
+    batching = None
+    if args.batch_rounds > 0:
+        batching = run_child(["--batch-child", f"{dev},{args.batch_rounds}"], timeout=900)
+
     # serving: the same request trace batched by the runtime and one design per launch
     serving = None
     if args.serve_requests > 0:
@@ -537,21 +702,20 @@ def run_ours(args):
         cache = os.path.join(tempfile.mkdtemp(prefix="wg_tune_"), "autotune.txt")
         barrier(pg, dev)
 
-        def serve_child(slots):
-            # each mode in its own process (its own contexts; a failure there is reported, not fatal)
-            cmd = [sys.executable, "-X", "faulthandler", os.path.abspath(__file__), "--serve-child",
-                   f"{dev},{args.serve_requests},{slots},{cache}"]
-            r = subprocess.run(cmd, capture_output=True, text=True, timeout=600)
-            lines = [x for x in r.stdout.splitlines() if x.startswith("{")]
-            if r.returncode == 0 and lines:
-                return json.loads(lines[-1])
-            return {"error": f"exit {r.returncode}", "stderr_tail": r.stderr[-1500:]}
+        def serve_child(slots, n_req, rate):
+            return run_child(["--serve-child", f"{dev},{n_req},{slots},{cache},{rate}"], timeout=900)
 
-        b = serve_child(64)
-        o = serve_child(1)
-        serving = {"trace": f"{args.serve_requests} requests, Poisson 200 req/s (seed 5), designs from the 64-design "
-                            f"batching pool (K 3..8, L 10..200, 30% pruned), fwd at 1e5..1e7 rays, 5% loss+grad at "
-                            f"1e6..1e8 rays", "batched": b, "one_design_per_launch": o}
+        serving = {}
+        for rate, n_req in ((200.0, args.serve_requests), (args.serve_low_rate, args.serve_low_requests)):
+            if n_req <= 0:
+                continue
+            bt = serve_child(64, n_req, rate)
+            ot = serve_child(1, n_req, rate)
+            serving[f"{rate:g}_req_per_s"] = {
+                "trace": f"{n_req} requests, Poisson {rate:g} req/s (seed 5), designs from the 64-design batching pool "
+                         f"(K 3..8, L 10..200, 30% pruned), fwd at 1e5..1e7 rays, 5% loss+grad at 1e6..1e8 rays; "
+                         f"the first {min(400, n_req)} requests served once untimed before",
+                "batched": bt, "one_design_per_launch": ot}
 
     out = None
     if rank == 0:
@@ -603,7 +767,8 @@ def run_ours(args):
                "roofline": roof, "roofline_fwd": roof_f, "roofline_bwd": roof_b, "cpu_baseline": cpu,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": launches, "clocks": ck, "coating_table": coating_table,
-               "pupil_expander": expander, "serving": serving}
+               "pupil_expander": expander, "differentiation": differentiation, "batching": batching,
+               "serving": serving}
         print(json.dumps(out))
     dh.destroy()
     ctx.close()
@@ -621,15 +786,30 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-expander", action="store_true", help="skip the two-dimensional pupil-expander entry")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
-    ap.add_argument("--serve-requests", type=int, default=400,
-                    help="requests of the serving trace (0: skip the serving measurement)")
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests of the serving trace at 200 req/s (0: skip)")
+    ap.add_argument("--serve-low-rate", type=float, default=50.0,
+                    help="arrival rate of the second serving run, below the GPU's capacity")
+    ap.add_argument("--serve-low-requests", type=int, default=400,
+                    help="requests of the second serving run (0: skip)")
+    ap.add_argument("--no-differentiation", action="store_true", help="skip the differentiation-configuration entry")
+    ap.add_argument("--d-steps", type=int, default=3, help="timed steps of the differentiation entry")
+    ap.add_argument("--batch-rounds", type=int, default=3,
+                    help="timed rounds of the batching entry after its warm-up rounds (0: skip)")
     ap.add_argument("--serve-child", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--batch-child", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.serve_child:
-        dev, n, slots, cache = args.serve_child.split(",", 3)
+        dev, n, slots, cache, rate = args.serve_child.split(",", 4)
         import torch
         torch.cuda.set_device(int(dev))
-        print(json.dumps(run_serving(int(dev), int(n), int(slots), cache)))
+        print(json.dumps(run_serving(int(dev), int(n), int(slots), cache, float(rate))))
+        return 0
+    if args.batch_child:
+        dev, rounds = args.batch_child.split(",", 1)
+        import torch
+        torch.cuda.set_device(int(dev))
+        print(json.dumps(run_batching(int(dev), int(rounds))))
         return 0
     if args.warmup < 3:
         args.warmup = 3

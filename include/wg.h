@@ -86,6 +86,14 @@ typedef struct wg_init_opts {
   int32_t max_slots;           /* serving: requests admitted at once (0 = 64) */
   size_t hbm_budget_bytes;     /* serving: admission budget (0 = 80% of free HBM) */
   const char* autotune_cache;  /* serving: file for autotuned launch shapes, or NULL */
+  /* limit of every bounded wait inside the kernels (design staging, a warp
+   * waiting for its CTA's next chunk), by the device clock; a kernel whose
+   * wait runs out sets its error word, finishes what it holds and returns,
+   * and the call returns WG_ETIMEOUT (0 = 0.5 s) */
+  uint64_t wait_limit_ns;
+  int32_t max_queue;           /* serving: queued requests before wg_submit returns WG_EBUSY (0 = 4096) */
+  int32_t reserved;
+  int64_t max_batch_rays;      /* serving: rays a batch admits beyond its first request (0 = 2^25) */
 } wg_init_opts;
 
 /*
@@ -402,10 +410,38 @@ wg_status wg_poll(wg_ctx* ctx, wg_ticket ticket, int64_t timeout_us, wg_result* 
 wg_status wg_cancel(wg_ctx* ctx, wg_ticket ticket);
 /* Times the forward kernel's chunk size and CTAs per SM on (a bounded sample
  * of) this evaluation and stores the fastest for its class (fields per ray,
- * material period, layers per mirror, rays per cell) in the context's table,
- * and in wg_init_opts.autotune_cache when given. The scheduler tunes classes
- * it has not seen on their first batch. */
+ * material period, accuracy mode, layers per mirror, rays per cell) in the
+ * context's table, and in wg_init_opts.autotune_cache when given. The
+ * scheduler tunes classes it has not seen on their first batch. */
 wg_status wg_autotune(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cfg);
+/* Forward traces of n designs (the batching workload: many designs of
+ * uneven mirror and layer counts and ray budgets) in one fused persistent
+ * launch per kernel variant (fields per ray, material period, accuracy mode;
+ * each design on its own CTAs, a design whose chunks run out hands its SMs
+ * to the others), with the autotuned launch shape of each design's class; a
+ * composition met before replays its captured CUDA graph. cfgs[i] and
+ * tallies[i] (device FP64 in cfgs[i]'s tally layout, overwritten) belong to
+ * designs[i]; stats: NULL or host [n]. Runs on the context's serving stream
+ * and returns when done (cfgs[i].stream is ignored). graph_replayed: NULL or
+ * host, set to 1 when the launches were a graph replay. Errors: WG_EINVAL,
+ * WG_ENOMEM, WG_EDEVICE, WG_ETIMEOUT (then the stats tell which design). */
+wg_status wg_trace_forward_batch(wg_ctx* ctx, int32_t n, const wg_design* const* designs, const wg_trace_cfg* cfgs,
+                                 double* const* tallies, wg_stats* stats, int32_t* graph_replayed);
+/* The table's entry for the class of (d, cfg): the launch shape the runtime
+ * uses for it and, when this context timed it (wg_autotune or a first
+ * batch), every candidate it timed. An entry read from the cache file has
+ * n_tried = 0. Errors: WG_EINVAL, WG_ENOTFOUND (no entry for the class). */
+#define WG_TUNE_MAX_TRIED 8
+typedef struct wg_tune_info {
+  int32_t chunk_rays;    /* rays per chunk of the forward kernel */
+  int32_t ctas_per_sm;   /* CTAs per SM (0: the occupancy limit) */
+  float best_ms;         /* the chosen shape's time on the sample (0: from the cache file) */
+  int32_t n_tried;       /* candidates timed */
+  int32_t tried_chunk_rays[WG_TUNE_MAX_TRIED];
+  int32_t tried_ctas_per_sm[WG_TUNE_MAX_TRIED];
+  float tried_ms[WG_TUNE_MAX_TRIED];
+} wg_tune_info;
+wg_status wg_autotune_info(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cfg, wg_tune_info* out);
 
 /* ------------------------------------------------------------------------
  * Reflection-probability pre-optimization (Methods, "Learned reflection

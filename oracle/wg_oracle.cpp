@@ -23,7 +23,7 @@
 //     PRMA, eyebox at an eye relief.
 //   * Results, Eq. 1 (loss) lives in oracle.py (numpy).
 //
-// Readings where the paper is silent (each is listed in the design doc):
+// Readings where the paper is silent:
 //   - time convention exp(+i w t): the Airy phase factor is exp(-2 i delta) as
 //     printed, and an evanescent cos(theta) is -i sqrt(n0^2 sin^2/n^2 - 1);
 //   - the p-polarized TMM result is quoted in the paper's Fresnel sign

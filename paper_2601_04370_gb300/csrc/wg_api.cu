@@ -48,14 +48,19 @@ extern "C" uint64_t wg_kernel_launches(void) { return (uint64_t)launches(); }
 // ---------------------------------------------------------------------------
 // objects
 // ---------------------------------------------------------------------------
+// gen counts the reallocations: a captured CUDA graph that refers to the
+// buffer must not be replayed after one, even when the new allocation lands
+// at the old address (the graph's nodes still refer to the freed one)
 struct DevBuf {
   void* p = nullptr;
   size_t n = 0;
+  unsigned long long gen = 0;
   cudaError_t ensure(size_t bytes) {
     if (bytes <= n) return cudaSuccess;
     if (p) cudaFree(p);
     p = nullptr;
     n = 0;
+    ++gen;
     cudaError_t e = cudaMalloc(&p, bytes);
     if (e == cudaSuccess) n = bytes;
     return e;
@@ -86,6 +91,12 @@ struct wg_ctx {
   DevBuf lsort;   // the eyebox-ray list grouped by hit count, for the replay
   void* serve = nullptr;  // serving runtime state (wg_serve.cu)
   void* noalloc_scratch = nullptr;  // device address of the no-allocation trace's static array
+  unsigned long long wait_limit_ns = 0;  // bounded waits in the kernels (0: the default 0.5 s)
+  int max_queue = 4096;                  // serving queue length
+  // serving: rays one batch admits beyond its first request (every request
+  // of a batch completes when the batch does, so a bounded batch keeps
+  // latency short)
+  long long max_batch_rays = 1ll << 25;
 };
 
 struct wg_design {
@@ -180,6 +191,9 @@ extern "C" wg_status wg_init(wg_ctx** out, const wg_init_opts* opts) {
   if (opts && opts->max_slots > 0) c->max_slots = opts->max_slots;
   if (opts) c->hbm_budget = opts->hbm_budget_bytes;
   if (opts && opts->autotune_cache) c->autotune_cache = opts->autotune_cache;
+  if (opts) c->wait_limit_ns = opts->wait_limit_ns;
+  if (opts && opts->max_queue > 0) c->max_queue = opts->max_queue;
+  if (opts && opts->max_batch_rays > 0) c->max_batch_rays = opts->max_batch_rays;
   // the allocation-free trace's array: looking up its address places it on
   // this device now, and loading the forward kernels now keeps a first
   // wg_trace_forward_noalloc call from loading (allocating) anything
@@ -691,6 +705,7 @@ static wg_status prepare_ws(wg_ctx* c, const wg_design* d, const wg_trace_cfg* c
 static TraceArgs base_args(const wg_design* d, const wg_trace_cfg* cfg, const Plan& p, const WsLayout& w) {
   TraceArgs a;
   memset(&a, 0, sizeof(a));
+  a.wait_ns = d->ctx->wait_limit_ns;
   a.blob = d->blob;
   a.blob_bytes = d->blob_bytes;
   a.fields = w.fields;
@@ -935,7 +950,14 @@ extern "C" wg_status wg_trace_forward(wg_ctx* c, const wg_design* d, const wg_tr
     CU(cudaFreeAsync(t, s));
     CU(cudaStreamSynchronize(s));
   }
-  if (stats || !dev_tally) return finish_stats(c, w, s, stats, stats != nullptr);
+  if (stats || !dev_tally) {
+    const wg_status fs = finish_stats(c, w, s, stats, stats != nullptr);
+    if (fs != WG_OK) {  // an incomplete trace: its eyebox-ray list and kept coefficients do not apply
+      dm->exit_fp = 0;
+      dm->coef_fp = 0;
+    }
+    return fs;
+  }
   return WG_OK;
 }
 
@@ -948,6 +970,9 @@ wg_status set_error(wg_status st, const char* msg) { return fail(st, "%s", msg);
 int ctx_device(const wg_ctx* c) { return c->device; }
 int ctx_sm_count(const wg_ctx* c) { return c->sm_count; }
 int ctx_max_slots(const wg_ctx* c) { return c->max_slots; }
+int ctx_max_queue(const wg_ctx* c) { return c->max_queue; }
+long long ctx_max_batch_rays(const wg_ctx* c) { return c->max_batch_rays; }
+unsigned long long ctx_wait_limit(const wg_ctx* c) { return c->wait_limit_ns; }
 size_t ctx_hbm_budget(const wg_ctx* c) { return c->hbm_budget; }
 const char* ctx_autotune_cache(const wg_ctx* c) { return c->autotune_cache.empty() ? nullptr : c->autotune_cache.c_str(); }
 void** ctx_serve_slot(wg_ctx* c) { return &c->serve; }
@@ -990,11 +1015,13 @@ size_t eval_device_bytes(const wg_design* d, const wg_trace_cfg* cfg, bool backw
 struct FusedPinned {
   void* p = nullptr;
   size_t n = 0;
+  unsigned long long gen = 0;  // reallocations (as DevBuf::gen)
   cudaError_t ensure(size_t bytes) {
     if (bytes <= n) return cudaSuccess;
     if (p) cudaFreeHost(p);
     p = nullptr;
     n = 0;
+    ++gen;
     cudaError_t e = cudaMallocHost(&p, bytes);
     if (e == cudaSuccess) n = bytes;
     return e;
@@ -1194,19 +1221,25 @@ wg_status fused_enqueue(wg_ctx* c, FusedJob* jobs, FusedBatch& fb, cudaStream_t 
   const uint8_t* pin = static_cast<const uint8_t*>(B.pin.p);
   std::lock_guard<std::mutex> lk(c->mu);
   CU(cudaSetDevice(c->device));
+  // What this enqueues (and a captured graph of it bakes in) refers only to
+  // the context's workspace and the batch's pinned staging; the jobs' tallies
+  // and eyebox-ray counters are cleared by a kernel that reads them from the
+  // job table copied in here, so a replay never touches a caller's buffer
+  // through a stale address.
   CU(cudaMemsetAsync(dev, 0, (size_t)B.n * kHeadStride, s));
   for (const auto& cp : B.copies) CU(cudaMemcpyAsync(dev + cp.dst, pin + cp.src, cp.bytes, cudaMemcpyHostToDevice, s));
+  long long max_doubles = 0;
   for (int j = 0; j < B.n; ++j) {
     const FusedJob& J = jobs[j];
     const Plan& p = B.plans[j];
     const WsLayout& w = B.lay[j];
     CU(launch_prep_fields(w.fields, w.fx, w.fy, J.cfg->n_fx, J.cfg->n_fy, J.design->n_slab, J.design->ic_tilt,
                           J.design->dims, s));
-    CU(cudaMemsetAsync(J.tally + p.cell_lo * p.bins, 0, sizeof(double) * (p.cell_hi - p.cell_lo + 1) * p.bins, s));
-    if (B.args[j].exit_count) CU(cudaMemsetAsync(B.args[j].exit_count, 0, sizeof(unsigned long long), s));
+    max_doubles = std::max<long long>(max_doubles, (p.cell_hi - p.cell_lo + 1) * p.bins);
   }
   const TraceArgs* tab = reinterpret_cast<const TraceArgs*>(dev + B.tab_dev);
   const int* cta = reinterpret_cast<const int*>(dev + B.cta_dev);
+  CU(launch_zero_jobs(tab, B.n, max_doubles, s));
   CU(cudaEventRecord(B.e0, s));
   for (const auto& g : B.groups)
     CU(launch_trace_fwd_fused(tab, cta + g.cta0, g.F, g.P, g.acc != 0, g.grid, g.smem, s));
@@ -1256,7 +1289,9 @@ uint64_t fused_signature(const wg_ctx* c, const FusedJob* jobs, const FusedBatch
   };
   auto mixv = [&](auto v) { mix(&v, sizeof(v)); };
   mixv(c->fws.p);
+  mixv(c->fws.gen);
   mixv(B.pin.p);
+  mixv(B.pin.gen);
   mixv(B.n);
   for (const auto& cp : B.copies) mix(&cp, sizeof(cp));
   for (const auto& g : B.groups) {
@@ -1527,6 +1562,8 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     }
     if (!use_lut) CU(launch_bwd_sort(sc.rec, (long long)n_rec, sc.keys, sc.keys + 128, sc.keys + 256, sc.sorted, perm, s));
     AdjArgs aa;
+    memset(&aa, 0, sizeof(aa));
+    aa.wait_ns = c->wait_limit_ns;
     aa.tilt_aux = tilt_aux;
     aa.perm = perm;
     aa.blob = d->blob;
@@ -1583,6 +1620,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
                           lut_recs, s));
     AdjArgs aa;
     memset(&aa, 0, sizeof(aa));
+    aa.wait_ns = c->wait_limit_ns;
     aa.blob = d->blob;
     aa.blob_bytes = d->blob_bytes;
     aa.recs = lut_recs;

@@ -74,6 +74,9 @@ size_t eval_device_bytes(const wg_design* d, const wg_trace_cfg* cfg, bool backw
 int ctx_device(const wg_ctx* c);
 int ctx_sm_count(const wg_ctx* c);
 int ctx_max_slots(const wg_ctx* c);
+int ctx_max_queue(const wg_ctx* c);
+long long ctx_max_batch_rays(const wg_ctx* c);
+unsigned long long ctx_wait_limit(const wg_ctx* c);
 size_t ctx_hbm_budget(const wg_ctx* c);
 const char* ctx_autotune_cache(const wg_ctx* c);
 void** ctx_serve_slot(wg_ctx* c);  // opaque serving state owned by wg_serve.cu

@@ -104,6 +104,7 @@ struct TraceArgs {
   float4* coef;
   long long coef_base, coef_rays;
   int coef_slots, coef_mode;
+  unsigned long long wait_ns;  // limit of the bounded waits (device clock)
 };
 
 // Arguments of the thin-film adjoint over sorted hit records.
@@ -123,6 +124,7 @@ struct AdjArgs {
   // tilt_aux[perm[i]].g_cos (the record's slot before the sort)
   TiltAux* tilt_aux;
   const unsigned int* perm;
+  unsigned long long wait_ns;  // limit of the bounded waits (device clock)
 };
 
 constexpr int kBlock = 256;
@@ -173,6 +175,9 @@ cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int gm, bool acc,
                              cudaStream_t s);
 // several jobs (designs / configurations with the same F and P) in one
 // launch: CTA b works on job cta_job[b] (device arrays; each job's n_cta set)
+// clears, for each of the n jobs of a fused launch (device table), its
+// tally over the cells its ray range touches and its eyebox-ray counter
+cudaError_t launch_zero_jobs(const TraceArgs* jobs_dev, int n, long long max_doubles, cudaStream_t s);
 cudaError_t launch_trace_fwd_fused(const TraceArgs* jobs_dev, const int* cta_job_dev, int F, int P, bool acc,
                                    int grid, size_t smem, cudaStream_t s);
 // tilt: also record TiltAux per hit and a RayHead per ray (a.tilt_aux, a.ray_heads)

@@ -48,14 +48,18 @@ __device__ __forceinline__ unsigned long long gtimer_ns() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-constexpr unsigned long long kWaitLimitNs = 500ull * 1000ull * 1000ull;  // 0.5 s
+constexpr unsigned long long kWaitLimitNs = 500ull * 1000ull * 1000ull;  // 0.5 s, the default limit
+__host__ __device__ __forceinline__ unsigned long long wait_limit(unsigned long long ns) {
+  return ns ? ns : kWaitLimitNs;
+}
 
 // ---------------------------------------------------------------------------
 // Bulk (TMA) staging of the design blob into shared memory, mbarrier
 // completion with a bounded wait. Returns false (uniformly across the CTA)
 // if the wait ran out; the caller then exits after flagging the error.
 // ---------------------------------------------------------------------------
-static __device__ bool stage_blob(uint8_t* s_dst, const uint8_t* g_src, int bytes, uint64_t* mbar, unsigned* err) {
+static __device__ bool stage_blob(uint8_t* s_dst, const uint8_t* g_src, int bytes, uint64_t* mbar, unsigned* err,
+                                  unsigned long long limit_ns) {
   const uint32_t bar = (uint32_t)__cvta_generic_to_shared(mbar);
   const uint32_t dst = (uint32_t)__cvta_generic_to_shared(s_dst);
   if (threadIdx.x == 0) {
@@ -81,7 +85,7 @@ static __device__ bool stage_blob(uint8_t* s_dst, const uint8_t* g_src, int byte
         : "=r"(done)
         : "r"(bar), "r"(0)
         : "memory");
-    if (!done && gtimer_ns() - t_start > kWaitLimitNs) break;
+    if (!done && gtimer_ns() - t_start > limit_ns) break;
   }
   const int ok = __syncthreads_and(done != 0);
   if (!ok && threadIdx.x == 0) atomicOr(err, 1u);
@@ -684,7 +688,7 @@ __global__ void __launch_bounds__(kBlock, 2)
     S.no_more = 0;
   }
   for (int i = tid; i < n_slots * A.bins; i += blockDim.x) s_tally[i] = 0.f;
-  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;  // includes a CTA barrier
+  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error, wait_limit(A.wait_ns))) return;  // includes a CTA barrier
   Blob B;
   B.bind(smem);
   const BlobHeader& H = *B.h;
@@ -917,7 +921,7 @@ __global__ void __launch_bounds__(kBlock, 2)
       const unsigned long long now = warp_time_ns();
       if (!idling) idle_t0 = now;
       idling = true;
-      if (now - idle_t0 > kWaitLimitNs) {  // no work for 0.5 s: give up and flag
+      if (now - idle_t0 > wait_limit(A.wait_ns)) {  // no work within the wait limit: give up and flag
         if (lane == 0) atomicOr(A.error, 2u);
         break;
       }
@@ -999,7 +1003,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
   const int tid = threadIdx.x, lane = tid & 31;
   for (int i = tid; i < 2 * MAX_MIR; i += blockDim.x) s_keys[i] = 0u;
   if (tid < 8) s_cnt[tid] = 0ull;
-  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;
+  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error, wait_limit(A.wait_ns))) return;
   Blob B;
   B.bind(smem);
   const BlobHeader& H = *B.h;
@@ -1451,7 +1455,7 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
   double* acc = reinterpret_cast<double*>(smem + A.blob_bytes) + warp * (kTiltPass * 32) + lane;
   float* col = reinterpret_cast<float*>(smem + A.blob_bytes + sizeof(double) * (kTiltBlock / 32) * kTiltPass * 32) +
                warp * (kTiltPass * W * 32) + lane;
-  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;
+  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error, wait_limit(A.wait_ns))) return;
   Blob B;
   B.bind(smem);
   const BlobHeader& H = *B.h;
@@ -1619,7 +1623,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_adjoint(const AdjArgs A) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   float* seg = s_grad + ((max(1, A.n_layers) + 31) & ~31) + warp * seg_floats_per_warp<P>() + lane;
   if (tid < 2) s_cnt[tid] = 0ull;
-  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;
+  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error, wait_limit(A.wait_ns))) return;
   Blob B;
   B.bind(smem);
   const BlobHeader& H = *B.h;
@@ -1775,10 +1779,44 @@ __global__ void __launch_bounds__(128) k_coating_grad(const uint8_t* blob, int m
                  make_float2(w[4 * i + 2], w[4 * i + 3]), which, sink, seg);
 }
 
+// Every kernel's dynamic shared memory limit is raised once to the device's
+// opt-in maximum and never lowered: a limit set per launch to that launch's
+// size would drop below what a CUDA graph captured earlier needs for the same
+// kernel, and replaying that graph then crashed inside the driver's launch.
+static inline int max_dyn_smem() {
+  static int v[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return 227 * 1024;
+  if (!v[dev]) {
+    int x = 0;
+    if (cudaDeviceGetAttribute(&x, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || x <= 0) {
+      cudaGetLastError();
+      x = 227 * 1024;
+    }
+    v[dev] = x;
+  }
+  return v[dev];
+}
+// raises the kernel's limit to the opt-in maximum less its static shared
+// memory (once: later calls find it there); errors are cleared, so they never
+// reach the launch's status
+template <class K>
+static void raise_smem_limit(K kernel) {
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  const int want = max_dyn_smem() - (int)fa.sharedSizeBytes;
+  if (fa.maxDynamicSharedSizeBytes < want &&
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, want) != cudaSuccess)
+    cudaGetLastError();
+}
 template <class K>
 static int occupancy(K kernel, size_t smem) {
   int n = 0;
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit(kernel);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kBlock, smem);
   return n;
 }

@@ -63,10 +63,15 @@ struct Ticket {
   Clock::time_point t_submit, t_start, t_done;
 };
 
-// launch shape chosen for a class of evaluations
+// launch shape chosen for a class of evaluations, and what was timed for it
 struct Tuned {
   int chunk = 0;  // rays per chunk (0: default)
   int bps = 0;    // CTAs per SM (0: occupancy limit)
+  float ms = 0.0f;  // the chosen shape's time (0: read from the cache file)
+  int n_tried = 0;
+  int tried_chunk[WG_TUNE_MAX_TRIED] = {};
+  int tried_bps[WG_TUNE_MAX_TRIED] = {};
+  float tried_ms[WG_TUNE_MAX_TRIED] = {};
 };
 
 struct Graph {
@@ -108,10 +113,6 @@ struct Serve {
   size_t garena_n = 0;
 };
 
-constexpr size_t kMaxQueue = 4096;
-// rays one batch admits beyond its first request: every request of a batch
-// completes when the batch does, so a bounded batch keeps latency short
-constexpr long long kBatchRays = 1ll << 25;
 constexpr size_t kMaxGraphs = 16;
 constexpr size_t kMaxSeen = 256;
 
@@ -134,7 +135,12 @@ void load_tune_cache(Serve& S) {
   if (!f) return;
   unsigned long long key;
   int chunk, bps;
-  while (fscanf(f, "%llu %d %d", &key, &chunk, &bps) == 3) S.tune[key] = Tuned{chunk, bps};
+  while (fscanf(f, "%llu %d %d", &key, &chunk, &bps) == 3) {
+    Tuned t;
+    t.chunk = chunk;
+    t.bps = bps;
+    S.tune[key] = t;
+  }
   fclose(f);
 }
 
@@ -200,9 +206,17 @@ wg_status autotune(Serve& S, const wg_design* d, const wg_trace_cfg* cfg0, cudaS
         if (st == WG_OK && job.status != WG_OK) st = job.status;
         ms = job.stats.kernel_ms;
       }
+      if (st == WG_OK && best.n_tried < WG_TUNE_MAX_TRIED) {
+        best.tried_chunk[best.n_tried] = chunks[ci];
+        best.tried_bps[best.n_tried] = bps;
+        best.tried_ms[best.n_tried] = (float)ms;
+        ++best.n_tried;
+      }
       if (st == WG_OK && ms < best_ms) {
         best_ms = ms;
-        best = Tuned{chunks[ci], bps};
+        best.chunk = chunks[ci];
+        best.bps = bps;
+        best.ms = (float)ms;
       }
     }
   }
@@ -554,7 +568,8 @@ void scheduler(Serve* Sp) {
           t->t_start = t->t_done = now;
           continue;
         }
-        if (!batch.empty() && (bytes + t->dev_bytes > budget || rays + t->rays > kBatchRays)) break;  // next batch
+        if (!batch.empty() && (bytes + t->dev_bytes > budget || rays + t->rays > wgh::ctx_max_batch_rays(S.ctx)))
+        break;  // next batch
         S.queue.pop_front();
         bytes += t->dev_bytes;
         rays += t->rays;
@@ -583,8 +598,14 @@ void scheduler(Serve* Sp) {
   }
 }
 
+// Creation of a context's runtime is serialized: two threads making their
+// first wg_submit / wg_autotune at once must not start two schedulers (one of
+// them would outlive the context).
+std::mutex g_serve_create_mu;
+
 Serve* serve_of(wg_ctx* c, bool create) {
   void** slot = wgh::ctx_serve_slot(c);
+  std::lock_guard<std::mutex> lk(g_serve_create_mu);
   if (!*slot && create) {
     Serve* S = new Serve();
     S->ctx = c;
@@ -605,6 +626,7 @@ Serve* serve_of(wg_ctx* c, bool create) {
       memset(&o, 0, sizeof(o));
       o.device = wgh::ctx_device(c);
       o.max_slots = 1;
+      o.wait_limit_ns = wgh::ctx_wait_limit(c);
       if (wg_init(&S->gctx, &o) != WG_OK ||
           cudaStreamCreateWithPriority(&S->gstream, cudaStreamNonBlocking, lo) != cudaSuccess) {
         cudaGetLastError();
@@ -628,7 +650,12 @@ namespace wgh {
 
 void serve_shutdown(wg_ctx* c) {
   void** slot = ctx_serve_slot(c);
-  Serve* S = static_cast<Serve*>(*slot);
+  Serve* S = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_serve_create_mu);
+    S = static_cast<Serve*>(*slot);
+    *slot = nullptr;
+  }
   if (!S) return;
   {
     std::lock_guard<std::mutex> lk(S->mu);
@@ -662,7 +689,6 @@ void serve_shutdown(wg_ctx* c) {
   if (S->arena) cudaFree(S->arena);
   if (S->stream) cudaStreamDestroy(S->stream);
   delete S;
-  *slot = nullptr;
 }
 
 }  // namespace wgh
@@ -713,7 +739,8 @@ extern "C" wg_status wg_submit(wg_ctx* c, const wg_request* req, wg_ticket* tick
   {
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->stop) return wgh::set_error(WG_ECANCELED, "wg_submit: the context is shutting down");
-    if (S->queue.size() >= kMaxQueue) return wgh::set_error(WG_EBUSY, "wg_submit: queue full");
+    if (S->queue.size() + S->gqueue.size() >= (size_t)wgh::ctx_max_queue(c))
+      return wgh::set_error(WG_EBUSY, "wg_submit: queue full");
     t->id = S->next_id++;
     t->t_submit = Clock::now();
     *ticket = t->id;
@@ -792,4 +819,87 @@ extern "C" wg_status wg_autotune(wg_ctx* c, const wg_design* d, const wg_trace_c
   const wg_status st = autotune(*S, d, cfg, s);
   cudaStreamDestroy(s);
   return st;
+}
+
+extern "C" wg_status wg_autotune_info(wg_ctx* c, const wg_design* d, const wg_trace_cfg* cfg, wg_tune_info* out) {
+  if (!c || !d || !cfg || !out) return wgh::set_error(WG_EINVAL, "wg_autotune_info: NULL argument");
+  Serve* S = serve_of(c, true);
+  if (!S) return wgh::set_error(WG_EDEVICE, "wg_autotune_info: could not start the serving runtime");
+  bool found = false;
+  const Tuned t = lookup_tune(*S, d, cfg, &found);
+  if (!found) return wgh::set_error(WG_ENOTFOUND, "wg_autotune_info: no entry for this class");
+  memset(out, 0, sizeof(*out));
+  out->chunk_rays = t.chunk;
+  out->ctas_per_sm = t.bps;
+  out->best_ms = t.ms;
+  out->n_tried = t.n_tried;
+  for (int i = 0; i < t.n_tried; ++i) {
+    out->tried_chunk_rays[i] = t.tried_chunk[i];
+    out->tried_ctas_per_sm[i] = t.tried_bps[i];
+    out->tried_ms[i] = t.tried_ms[i];
+  }
+  return WG_OK;
+}
+
+extern "C" wg_status wg_trace_forward_batch(wg_ctx* c, int32_t n, const wg_design* const* designs,
+                                            const wg_trace_cfg* cfgs, double* const* tallies, wg_stats* stats,
+                                            int32_t* graph_replayed) {
+  if (!c || n < 1 || !designs || !cfgs || !tallies)
+    return wgh::set_error(WG_EINVAL, "wg_trace_forward_batch: NULL argument or n < 1");
+  cudaSetDevice(wgh::ctx_device(c));
+  for (int i = 0; i < n; ++i) {
+    if (!designs[i] || !tallies[i]) return wgh::set_error(WG_EINVAL, "wg_trace_forward_batch: NULL design or tally");
+    if (cfgs[i].ray_records || cfgs[i].lut_bins)
+      return wgh::set_error(WG_EINVAL, "wg_trace_forward_batch: no per-ray records or coating table in a batch");
+    if (wgh::tally_doubles(designs[i], &cfgs[i]) < 0) return WG_EINVAL;  // the message is set
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, tallies[i]) != cudaSuccess ||
+        (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
+      cudaGetLastError();
+      return wgh::set_error(WG_EINVAL, "wg_trace_forward_batch: tallies must be device memory");
+    }
+  }
+  Serve* S = serve_of(c, true);
+  if (!S) return wgh::set_error(WG_EDEVICE, "wg_trace_forward_batch: could not start the serving runtime");
+  std::vector<wg_trace_cfg> cf(cfgs, cfgs + n);
+  std::vector<Tuned> shape(n);
+  for (int i = 0; i < n; ++i) {
+    cf[i].stream = nullptr;
+    bool found = false;
+    shape[i] = lookup_tune(*S, designs[i], &cf[i], &found);
+    if (!found && autotune(*S, designs[i], &cf[i], S->stream) == WG_OK)
+      shape[i] = lookup_tune(*S, designs[i], &cf[i], &found);
+  }
+  if (graph_replayed) *graph_replayed = 1;
+  wg_status result = WG_OK;
+  for (int bps = 0; bps <= 2; ++bps) {
+    std::vector<wgh::FusedJob> jobs;
+    std::vector<int> idx;
+    for (int i = 0; i < n; ++i) {
+      if (shape[i].bps != bps) continue;
+      wgh::FusedJob j{};
+      j.design = designs[i];
+      j.cfg = &cf[i];
+      j.tally = tallies[i];
+      j.chunk_rays = shape[i].chunk;
+      jobs.push_back(j);
+      idx.push_back(i);
+    }
+    if (jobs.empty()) continue;
+    bool replayed = false;
+    const wg_status st = run_forward(*S, jobs, bps, &replayed);
+    if (!replayed && graph_replayed) *graph_replayed = 0;
+    if (st != WG_OK) return st;
+    for (size_t q = 0; q < jobs.size(); ++q) {
+      if (stats) stats[idx[q]] = jobs[q].stats;
+      if (jobs[q].status != WG_OK && result == WG_OK) {
+        result = jobs[q].status;
+        char buf[160];
+        snprintf(buf, sizeof(buf), "wg_trace_forward_batch: design %d: device error word 0x%x", idx[q],
+                 jobs[q].error_word);
+        wgh::set_error(result, buf);
+      }
+    }
+  }
+  return result;
 }

@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kOmegaBlock) k_omega_trace(const TraceArgs A, 
   __shared__ unsigned long long s_cnt[3];
   for (int k = threadIdx.x; k < MAX_MIR; k += blockDim.x) s_grad[k] = 0.0;
   if (threadIdx.x < 3) s_cnt[threadIdx.x] = 0ull;
-  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error)) return;
+  if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error, wait_limit(A.wait_ns))) return;
   Blob B;
   B.bind(smem);
   const BlobHeader& H = *B.h;
@@ -287,7 +287,7 @@ cudaError_t launch_omega_trace(const TraceArgs& a, double* grad_omega, int gm, i
   if (n <= 0) return cudaSuccess;
   const int grid = (int)std::max<long long>(1, std::min<long long>((n + kOmegaBlock - 1) / kOmegaBlock, 8ll * sm_count));
   auto k = gm == 1 ? k_omega_trace<1> : k_omega_trace<0>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, a.blob_bytes);
+  raise_smem_limit(k);
   note_launches(1);
   k<<<grid, kOmegaBlock, a.blob_bytes, s>>>(a, grad_omega);
   return cudaGetLastError();
@@ -482,6 +482,26 @@ cudaError_t launch_prep_design(uint8_t* blob, const float* mir_x, const float* m
                                const float* geo, int n_mir, float ic_tilt_deg, float thick, cudaStream_t s) {
   note_launches(1);
   k_prep_design<<<1, 64, 0, s>>>(blob, mir_x, mir_tilt, mir_omega, geo, n_mir, ic_tilt_deg, thick);
+  return cudaGetLastError();
+}
+
+// job j = blockIdx.y of a fused launch: its tally cells [cell_lo, cell_hi]
+// and its eyebox-ray counter to zero
+__global__ void k_zero_jobs(const TraceArgs* __restrict__ jobs) {
+  const TraceArgs& A = jobs[blockIdx.y];
+  const long long cell_hi = (A.ray_end - 1) / A.n_cell;
+  const long long lo = A.cell_lo * A.bins, hi = (cell_hi + 1) * A.bins;
+  for (long long i = lo + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < hi;
+       i += (long long)gridDim.x * blockDim.x)
+    A.tally[i] = 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0 && A.exit_count) *A.exit_count = 0ull;
+}
+
+cudaError_t launch_zero_jobs(const TraceArgs* jobs_dev, int n, long long max_doubles, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const long long bx = std::max<long long>(1, std::min<long long>((max_doubles + 255) / 256, 256));
+  note_launches(1);
+  k_zero_jobs<<<dim3((unsigned)bx, (unsigned)n), 256, 0, s>>>(jobs_dev);
   return cudaGetLastError();
 }
 

@@ -16,7 +16,7 @@ int bwd_adjoint_blocks_per_sm(int P, bool acc, size_t smem) { return occupancy(p
 
 cudaError_t launch_bwd_adjoint(const AdjArgs& a, int P, bool acc, int grid, size_t smem, cudaStream_t s) {
   auto k = pick_adjoint(P, a.tilt_aux != nullptr, acc);
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit(k);
   note_launches(1);
   k<<<grid, kBlock, smem, s>>>(a);
   return cudaGetLastError();

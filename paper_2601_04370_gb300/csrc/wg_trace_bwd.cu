@@ -33,7 +33,7 @@ int bwd_replay_blocks_per_sm(int F, int P, bool tilt, int gm, bool acc, size_t s
 cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, bool tilt, int gm, bool acc, int grid, size_t smem,
                               cudaStream_t s) {
   auto k = pick_replay(F, P, tilt, gm, acc);
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit(k);
   note_launches(1);
   k<<<grid, kBlock, smem, s>>>(a);
   return cudaGetLastError();
@@ -43,7 +43,7 @@ int tilt_blocks_per_sm(int F, int P, int gm, bool acc, size_t smem) {
   (void)P;
   auto k = pick_tilt(F, gm, acc);
   int n = 0;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit(k);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kTiltBlock, smem);
   return n;
 }
@@ -52,7 +52,7 @@ cudaError_t launch_tilt_grad(const TraceArgs& a, int F, int P, int gm, bool acc,
                              cudaStream_t s) {
   (void)P;
   auto k = pick_tilt(F, gm, acc);
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit(k);
   note_launches(1);
   k<<<grid, kTiltBlock, smem, s>>>(a);
   return cudaGetLastError();

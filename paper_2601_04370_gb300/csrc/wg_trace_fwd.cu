@@ -39,7 +39,7 @@ int trace_fwd_blocks_per_sm(int F, int P, int gm, bool acc, size_t smem) {
 cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int gm, bool acc, int grid, size_t smem,
                              cudaStream_t s) {
   auto k = pick_fwd(F, P, gm, acc);
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit(k);
   note_launches(1);
   TraceArgs a1 = a;
   a1.n_cta = grid;
@@ -50,7 +50,7 @@ cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int gm, bool acc,
 cudaError_t launch_trace_fwd_fused(const TraceArgs* jobs_dev, const int* cta_job_dev, int F, int P, bool acc,
                                    int grid, size_t smem, cudaStream_t s) {
   auto k = pick_fwd(F, P, 2, acc);  // the jobs of a fused launch may mix PRMA and general designs
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  raise_smem_limit(k);
   note_launches(1);
   TraceArgs unused;
   memset(&unused, 0, sizeof(unused));

@@ -35,7 +35,14 @@ class WGError(RuntimeError):
 
 class InitOpts(C.Structure):
     _fields_ = [("device", C.c_int32), ("max_slots", C.c_int32), ("hbm_budget_bytes", C.c_size_t),
-                ("autotune_cache", C.c_char_p)]
+                ("autotune_cache", C.c_char_p), ("wait_limit_ns", C.c_uint64), ("max_queue", C.c_int32),
+                ("reserved", C.c_int32), ("max_batch_rays", C.c_int64)]
+
+
+class TuneInfo(C.Structure):
+    _fields_ = [("chunk_rays", C.c_int32), ("ctas_per_sm", C.c_int32), ("best_ms", C.c_float),
+                ("n_tried", C.c_int32), ("tried_chunk_rays", C.c_int32 * 8), ("tried_ctas_per_sm", C.c_int32 * 8),
+                ("tried_ms", C.c_float * 8)]
 
 
 class DesignDesc(C.Structure):
@@ -131,6 +138,8 @@ def lib():
         L.wg_poll.argtypes = [vp, C.c_uint64, i64, C.POINTER(Result)]
         L.wg_cancel.argtypes = [vp, C.c_uint64]
         L.wg_autotune.argtypes = [vp, vp, C.POINTER(TraceCfg)]
+        L.wg_autotune_info.argtypes = [vp, vp, C.POINTER(TraceCfg), C.POINTER(TuneInfo)]
+        L.wg_trace_forward_batch.argtypes = [vp, i32, vp, vp, vp, vp, vp]
         L.wg_omega_trace.argtypes = [vp, vp, C.POINTER(TraceCfg), vp, vp, vp]
         L.wg_set_omega.argtypes = [vp, vp, i32, vp]
         L.wg_adam_create.argtypes = [vp, C.POINTER(AdamOpts), vp, C.POINTER(vp)]
@@ -147,7 +156,8 @@ def lib():
                      "wg_trace_forward", "wg_trace_backward", "wg_loss", "wg_trace_forward_noalloc",
                      "wg_submit", "wg_poll", "wg_cancel", "wg_autotune", "wg_omega_trace", "wg_set_omega",
                      "wg_adam_create", "wg_adam_step", "wg_adam_params", "wg_omega_adam_create",
-                     "wg_omega_adam_step", "wg_design_version"):
+                     "wg_omega_adam_step", "wg_design_version", "wg_autotune_info",
+                     "wg_trace_forward_batch"):
             getattr(L, name).restype = C.c_int32
         _lib = L
     return _lib
@@ -373,11 +383,13 @@ class DesignHandle:
 
 class Context:
     def __init__(self, device: int = 0, max_slots: int = 0, hbm_budget_bytes: int = 0,
-                 autotune_cache: Optional[str] = None):
+                 autotune_cache: Optional[str] = None, wait_limit_ns: int = 0, max_queue: int = 0,
+                 max_batch_rays: int = 0):
         h = C.c_void_p()
         self._cache = autotune_cache.encode() if autotune_cache else None
         opts = InitOpts(device=device, max_slots=max_slots, hbm_budget_bytes=hbm_budget_bytes,
-                        autotune_cache=self._cache)
+                        autotune_cache=self._cache, wait_limit_ns=wait_limit_ns, max_queue=max_queue,
+                        max_batch_rays=max_batch_rays)
         _check(lib().wg_init(C.byref(h), C.byref(opts)))
         self.h = h
         self.device = device
@@ -406,7 +418,10 @@ class Context:
         if st == WG_ENOTREADY:
             return None
         _check(st)
-        return res.to_dict()
+        out = res.to_dict()
+        if out["status"] != WG_OK:
+            out["error"] = lib().wg_last_error().decode()
+        return out
 
     def cancel(self, ticket):
         _check(lib().wg_cancel(self.h, ticket))
@@ -414,6 +429,34 @@ class Context:
     def autotune(self, dh, cfg):
         h = _CfgHolder(cfg, None)
         _check(lib().wg_autotune(self.h, dh.h, C.byref(h.c)))
+
+    def trace_forward_batch(self, dhs, cfgs, tallies, stats=True):
+        """wg_trace_forward_batch: the forwards of several designs in one fused
+        launch per kernel variant (autotuned shapes, graph replay of a
+        composition met before). tallies: torch CUDA float64 tensors.
+        Returns (list of stats dicts or None, graph_replayed)."""
+        n = len(dhs)
+        holders = [_CfgHolder(c, None) for c in cfgs]
+        carr = (TraceCfg * n)(*[h.c for h in holders])
+        darr = (C.c_void_p * n)(*[dh.h.value if hasattr(dh.h, "value") else dh.h for dh in dhs])
+        tarr = (C.c_void_p * n)(*[_ptr(t) for t in tallies])
+        st = (Stats * n)() if stats else None
+        rep = C.c_int32(0)
+        _check(lib().wg_trace_forward_batch(self.h, n, darr, carr, tarr, st, C.byref(rep)))
+        return ([s.to_dict() for s in st] if stats else None), bool(rep.value)
+
+    def autotune_info(self, dh, cfg):
+        """wg_autotune_info: the launch shape stored for the class of (dh, cfg)
+        and the candidates timed for it, as a dict (None if there is none)."""
+        h = _CfgHolder(cfg, None)
+        t = TuneInfo()
+        st = lib().wg_autotune_info(self.h, dh.h, C.byref(h.c), C.byref(t))
+        if st == WG_ENOTFOUND:
+            return None
+        _check(st)
+        n = t.n_tried
+        return {"chunk_rays": t.chunk_rays, "ctas_per_sm": t.ctas_per_sm, "best_ms": t.best_ms, "n_tried": n,
+                "tried": [(t.tried_chunk_rays[i], t.tried_ctas_per_sm[i], t.tried_ms[i]) for i in range(n)]}
 
     def __enter__(self):
         return self

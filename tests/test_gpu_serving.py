@@ -139,3 +139,25 @@ def test_identical_batch_replays_graph(wg):
     assert _close(a, b) and _close(a, c)
     dh.destroy()
     ctx.close()
+
+
+def test_forward_batch_matches_direct_calls_and_replays_its_graph(wg):
+    """wg_trace_forward_batch: designs of uneven mirror and layer counts
+    (fast and accurate evaluations, pruned layers) in fused launches equal
+    their direct traces; the same composition runs directly the first time,
+    is captured the second time and replays the graph from the third."""
+    jobs = _designs(8, 1728 * 4)
+    ctx = wg.Context(0)
+    dhs = [ctx.create_design(D) for D, _ in jobs]
+    ts = [torch.zeros(C.tally_shape, dtype=torch.float64, device="cuda") for _, C in jobs]
+    reps = []
+    for _ in range(3):
+        st, rep = ctx.trace_forward_batch(dhs, [C for _, C in jobs], ts)
+        reps.append(rep)
+        assert all(s["n_rays"] == C.total_rays for s, (_, C) in zip(st, jobs))
+    assert reps == [False, False, True]
+    for dh, (D, C), t in zip(dhs, jobs, ts):
+        assert _close(t.cpu().numpy(), _direct_forward(ctx, dh, C))
+    for dh in dhs:
+        dh.destroy()
+    ctx.close()
