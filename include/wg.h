@@ -266,6 +266,14 @@ wg_status wg_eval_coating(wg_ctx* ctx, const wg_design* d, int32_t mirror, int32
 wg_status wg_eval_coating_grad(wg_ctx* ctx, const wg_design* d, int32_t mirror, int32_t side, int64_t n,
                                const float* cos_theta, const float* lambda_nm, const float* weights,
                                int32_t which, float* grad, void* stream);
+/*
+ * d f / d(cos theta_0) of the same f through the coating (the coating term of
+ * the mirror-tilt gradient), from the same reverse sweep: grad_cos device [n]
+ * FP32. Errors: WG_EINVAL.
+ */
+wg_status wg_eval_coating_dcos(wg_ctx* ctx, const wg_design* d, int32_t mirror, int32_t side, int64_t n,
+                               const float* cos_theta, const float* lambda_nm, const float* weights, int32_t which,
+                               float* grad_cos, void* stream);
 
 /* ---- trace, loss, adjoint --------------------------------------------- */
 

@@ -584,6 +584,22 @@ extern "C" wg_status wg_eval_coating_grad(wg_ctx* c, const wg_design* d, int32_t
   return WG_OK;
 }
 
+extern "C" wg_status wg_eval_coating_dcos(wg_ctx* c, const wg_design* d, int32_t mirror, int32_t side, int64_t n,
+                                          const float* cos_theta, const float* lambda_nm, const float* weights,
+                                          int32_t which, float* grad_cos, void* stream) {
+  if (!c || !d) return fail(WG_EINVAL, "wg_eval_coating_dcos: NULL ctx/design");
+  if (mirror < 0 || mirror >= d->K || (side != 0 && side != 1) || n < 0 || (which != 0 && which != 1))
+    return fail(WG_EINVAL, "wg_eval_coating_dcos: bad mirror/side/which/n");
+  if (n == 0) return WG_OK;
+  if (!is_device_ptr(cos_theta) || !is_device_ptr(lambda_nm) || !is_device_ptr(weights) || !is_device_ptr(grad_cos))
+    return fail(WG_EINVAL, "wg_eval_coating_dcos: arrays must be device memory");
+  std::lock_guard<std::mutex> lk(c->mu);
+  CU(cudaSetDevice(c->device));
+  CU(launch_coating_dcos(d->blob, d->period, d->acc, mirror, side, n, cos_theta, lambda_nm, weights, which, grad_cos,
+                         (cudaStream_t)stream));
+  return WG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // trace plumbing
 // ---------------------------------------------------------------------------

@@ -843,8 +843,82 @@ __device__ __forceinline__ void row_guard_fold(CRow& a, int& e, float& acc, floa
   }
 }
 
+// Exact power-of-two scaling for the adjoint's range management.
+// floor(log2 m) of a normal positive float
+__device__ __forceinline__ int exp_of(float m) { return ((__float_as_int(m) >> 23) & 0xff) - 127; }
+// 2^e for e in [-126, 127]
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((e + 127) << 23); }
+// x 2^k for any k in [-252, 254] (two exact factors)
+__device__ __forceinline__ float mul_pow2(float x, int k) {
+  const int k1 = k / 2;
+  return (x * pow2f(k1)) * pow2f(k - k1);
+}
+// v scaled in one exact step into [1, 2) once its largest entry passes 2^8:
+// checkpoints stay small, so that the products of a segment (a vector grown
+// by up to 2^31 times a row) leave room below the FP32 range even after the
+// tilt terms' factor rho = d ln cos(theta_j)/d cos(theta_0), large near the
+// critical angle
+constexpr float CK_HI = 256.0f;
+__device__ __forceinline__ void cv_fit(CV& v, int& e) {
+  const float m = cv_maxabs(v);
+  if (m > CK_HI) {
+    const int sh = min(exp_of(m), 127);  // m 2^-sh in [1, 2); non-finite stays non-finite
+    const float f = pow2f(-sh);
+    v.xr *= f;
+    v.xi *= f;
+    v.yr *= f;
+    v.yi *= f;
+    e += sh;
+  }
+}
+// the row scaled in one exact step into [2^7, 2^8) when outside [2^-8, 2^8]
+constexpr float ROW_HI = 256.0f, ROW_LO = 0.00390625f;
+__device__ __forceinline__ void row_fit8(CRow& a, int& e) {
+  const float m = row_maxabs(a);
+  if ((m > ROW_HI || m < ROW_LO) && m > 0.0f) {
+    const int em = m >= 1.17549435e-38f ? exp_of(m) : -126;  // a subnormal row counts as 2^-126
+    const int sh = min(em, 127) - 7;
+    a.a0 = make_float2(mul_pow2(a.a0.x, -sh), mul_pow2(a.a0.y, -sh));
+    a.a1 = make_float2(mul_pow2(a.a1.x, -sh), mul_pow2(a.a1.y, -sh));
+    e += sh;
+  }
+}
+
+// Sum over the warp's 32 lanes of R = 8 values per lane, one result per
+// value: three transposing exchanges (16, 8, 4 lanes apart) halve the values
+// a lane holds while summing pairs, two plain exchanges finish the sums.
+// Afterwards lane l holds the sum of value ((l >> 4) & 1) 4 + ((l >> 3) & 1) 2
+// + ((l >> 2) & 1), and every lane of a quad holds the same sum.
+__device__ __forceinline__ float warp_transpose_sum8(const float (&t)[8], int lane) {
+  const bool b16 = lane & 16, b8 = lane & 8, b4 = lane & 4;
+  float h[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float send = b16 ? t[k] : t[k + 4];
+    h[k] = (b16 ? t[k + 4] : t[k]) + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  float q[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float send = b8 ? h[k] : h[k + 2];
+    q[k] = (b8 ? h[k + 2] : h[k]) + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float r = (b4 ? q[1] : q[0]) + __shfl_xor_sync(0xffffffffu, b4 ? q[0] : q[1], 4);
+  r += __shfl_xor_sync(0xffffffffu, r, 2);
+  r += __shfl_xor_sync(0xffffffffu, r, 1);
+  return r;
+}
+
 // seg: this lane's column of its warp's segment buffer (element (u, w) at
 // seg[(u * kSegWords + w) * 32]; the 32 lanes' columns interleave).
+// The sink receives each segment's gradient terms at once:
+// sink.segment(t, n, i0, di): t[u] = df/dd of layer i0 + u di (per nm), u < n.
+// Range management (exact powers of two): the first sweep keeps every
+// checkpoint at or below 2^8, the row is brought into [2^-8, 2^8] at each
+// segment start; a segment grows either by less than 2^31, so a . v (< 2^78)
+// stays far below the FP32 range inside the segment, and each segment's
+// terms take one scale factor 2^(e_row + e_v) (computed once; out of the
+// normal range the terms are scaled one by one).
 // DUAL: *g_cos also receives df/d(cos t0) of the record through its coating,
 // without 2^eA, from the same reverse sweep (reverse-mode, no derivative
 // chain): with v_j = M_j v_{j+1} (substrate side) and the row a_j,
@@ -865,6 +939,8 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
   Ckpt ck[MAX_CK];
   const int L = st.L;
   const int nseg = (L + CKP - 1) / CKP;
+  // device index of traversal step j: i0 + j di
+  const int i0 = front ? st.off : st.off + L - 1, di = front ? 1 : -1;
   const float eta_s = n0 * cos0, eta_p = n0 / cos0;
   CV vs{1.0f, 0.0f, eta_s, 0.0f}, vp{1.0f, 0.0f, eta_p, 0.0f};
   int es = 0, ep = 0;
@@ -875,7 +951,7 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
     for (int u = CKP - 1; u >= 0; --u) {
       const int j = j0 + u;
       if (j < L) {
-        const int i = st.idx(front, j);
+        const int i = i0 + j * di;
         MatK k;
         if constexpr (P > 0) {
           k = kb[u % P];
@@ -888,11 +964,8 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         cv_step(vp, c, s * k.q12p, s * k.q21p);
       }
     }
-#pragma unroll
-    for (int t = 0; t < 3; ++t) {
-      cv_rescale32(vs, es);
-      cv_rescale32(vp, ep);
-    }
+    cv_fit(vs, es);
+    cv_fit(vp, ep);
     ck[sg] = Ckpt{vs, vp, es, ep};
   }
   // paper convention r_p = -r_p(Abeles): flip A_p for reflection
@@ -918,6 +991,8 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
   eap += eA;
   for (int sg = 0; sg < nseg; ++sg) {
     const int j0 = sg * CKP;
+    row_fit8(as, eas);
+    row_fit8(ap, eap);
     const Ckpt c1 = ck[sg + 1];
     CV ws = c1.s, wp = c1.p;
     // the segment's substrate-side vectors and (c, s), recomputed from the
@@ -928,7 +1003,7 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
       const int j = j0 + u;
       float c = 1.0f, s = 0.0f;
       if (j < L) {
-        const int i = st.idx(front, j);
+        const int i = i0 + j * di;
         MatK k;
         if constexpr (P > 0) {
           k = kb[u % P];
@@ -951,6 +1026,10 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
       b[8 * 32] = c;
       b[9 * 32] = s;
     }
+    // one scale factor per segment for the terms (exact; else per term)
+    const int xs = eas + c1.es, xp = eap + c1.ep;
+    const bool in_range = xs >= -126 && xs <= 127 && xp >= -126 && xp <= 127;
+    const float fs = in_range ? pow2f(xs) : 0.0f, fp = in_range ? pow2f(xp) : 0.0f;
     // v_j of step u (the row's products with v_{j+1} read the next slot,
     // or the checkpoint for the segment's last step)
     CV x{seg[0], seg[32], seg[2 * 32], seg[3 * 32]};
@@ -967,23 +1046,24 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
       if (j < L) {
         MatK k;
         float rho = 0.0f;
+        const int i = i0 + j * di;
         if constexpr (P > 0) {
           k = kb[u % P];
           if constexpr (DUAL) rho = rb[u % P];
         } else {
-          const int m = st.m[st.idx(front, j)];
+          const int m = st.m[i];
           k = mt.get(m);
           if constexpr (DUAL) rho = tt->get(m);
         }
-        const float* b = seg + u * kSegWords * 32;
+        float* b = seg + u * kSegWords * 32;
         const float c = b[8 * 32], s = b[9 * 32];
         const float gs = fmaf(k.q12s, fmaf(as.a0.x, x.yi, as.a0.y * x.yr), k.q21s * fmaf(as.a1.x, x.xi, as.a1.y * x.xr));
         const float gp = fmaf(k.q12p, fmaf(ap.a0.x, y.yi, ap.a0.y * y.yr), k.q21p * fmaf(ap.a1.x, y.xi, ap.a1.y * y.xr));
-        const int i = st.idx(front, j);
-        sink(i, -2.0f * k.kap * (scale2(gs, eas + c1.es) + scale2(gp, eap + c1.ep)));
+        // the step's term goes to its (c) slot, no longer needed
+        b[8 * 32] = -2.0f * k.kap * (in_range ? fmaf(gs, fs, gp * fp) : scale2(gs, xs) + scale2(gp, xp));
         if constexpr (DUAL) {
           // rho (phase term kap d g + quotient term on v_{j+1}), at this
-          // step's exponents
+          // segment's exponents
           const float kd = k.kap * st.d[i];
           const float qs = fmaf(k.q21s, fmaf(as.a1.x, xn.xi, as.a1.y * xn.xr),
                                 -k.q12s * fmaf(as.a0.x, xn.yi, as.a0.y * xn.yr));
@@ -994,16 +1074,15 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         }
         row_step(as, c, s * k.q12s, s * k.q21s);
         row_step(ap, c, s * k.q12p, s * k.q21p);
-        if constexpr (DUAL) {
-          row_guard_fold(as, eas, acc_s, gc, c1.es - eA);
-          row_guard_fold(ap, eap, acc_p, gc, c1.ep - eA);
-        } else {
-          row_guard(as, eas);
-          row_guard(ap, eap);
-        }
       }
       x = xn;
       y = yn;
+    }
+    {
+      float t[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = u < CKP ? seg[(u * kSegWords + 8) * 32] : 0.0f;
+      sink.segment(t, min(CKP, L - j0), i0 + j0 * di, di);
     }
     if constexpr (DUAL) {
       gc = fmaf(-2.0f, scale2(acc_s, eas + c1.es - eA), gc);
@@ -1011,8 +1090,6 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
       acc_s = 0.0f;
       acc_p = 0.0f;
     }
-    row_renorm(as, eas);
-    row_renorm(ap, eap);
   }
   if constexpr (DUAL) {
     // a_L (0, deta0)^T: v_L = (1, eta0) at exponent 0

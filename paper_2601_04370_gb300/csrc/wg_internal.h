@@ -200,6 +200,10 @@ cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const in
 // coating look-up table: entries for every (mirror, side, wavelength, bin)
 // of the design (lam: device [n_lam]); records: one hit record per (entry,
 // r or t) carrying the entry's accumulated FP64 weights, in stack order
+// d f / d(cos theta_0) per sample through the coating (the adjoint's dual reverse sweep)
+cudaError_t launch_coating_dcos(const uint8_t* blob, int P, bool acc, int mirror, int side, long long n,
+                                const float* cos0, const float* lam, const float* w, int which, float* out,
+                                cudaStream_t s);
 cudaError_t launch_lut_build(const uint8_t* blob, int P, bool acc, int n_mir, int n_lam, const float* lam, int n,
                              float c0, float dc, float4* out, cudaStream_t s);
 cudaError_t launch_lut_records(const double* grad, int n_mir, int n_lam, const float* lam, int n, float c0, float dc,

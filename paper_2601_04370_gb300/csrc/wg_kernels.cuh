@@ -1580,26 +1580,37 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
 
 __device__ __forceinline__ int rec_key(int kfw) { return ((kfw & 0xff) << 1) | ((kfw >> 8) & 1); }
 
-// Per-layer gradient terms of one record per lane. When all 32 lanes hold
-// records of the same stack (uniform, warp-uniform flag) every step touches
-// the same entry in all lanes: reduced with shuffles and added once; else
-// added per lane. Non-finite terms are counted (wg_stats) and never added.
+// Gradient terms of one record per lane, a segment (up to 8 layers) at a
+// time. When all 32 lanes hold records of the same stack (uniform, a
+// warp-uniform flag) their terms go to the same layers: summed across the
+// warp with one transposing reduction per segment and added once per layer;
+// else added per lane. Non-finite sums are counted (wg_stats) and not added.
 struct GradSink {
   float* s_grad;
   int* bad;
   int lane;
   bool uniform;
-  __device__ __forceinline__ void operator()(int idx, float g) const {
-    if (!isfinite(g)) {
-      ++*bad;
-      g = 0.f;
-    }
+  __device__ __forceinline__ void segment(const float (&t)[8], int n, int i0, int di) const {
     if (uniform) {
+      const float r = warp_transpose_sum8(t, lane);
+      const int u = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+      if ((lane & 3) == 0 && u < n) {
+        if (isfinite(r)) {
+          atomicAdd(s_grad + i0 + u * di, r);
+        } else {
+          ++*bad;
+        }
+      }
+    } else {
 #pragma unroll
-      for (int o = 16; o; o >>= 1) g += __shfl_xor_sync(FULL, g, o);
-      if (lane == 0) atomicAdd(s_grad + idx, g);
-    } else if (g != 0.f) {
-      atomicAdd(s_grad + idx, g);
+      for (int u = 0; u < 8; ++u)
+        if (u < n) {
+          if (!isfinite(t[u])) {
+            ++*bad;
+          } else if (t[u] != 0.f) {
+            atomicAdd(s_grad + i0 + u * di, t[u]);
+          }
+        }
     }
   }
 };
@@ -1753,9 +1764,13 @@ struct RowSink {
   float* row;
   int off, L;
   bool front;
-  __device__ __forceinline__ void operator()(int idx, float g) const {
-    const int j = front ? idx - off : off + L - 1 - idx;
-    row[j] = g;
+  __device__ __forceinline__ void segment(const float (&t)[8], int n, int i0, int di) const {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (u < n) {
+        const int idx = i0 + u * di;
+        row[front ? idx - off : off + L - 1 - idx] = t[u];
+      }
   }
 };
 
@@ -1777,6 +1792,35 @@ __global__ void __launch_bounds__(128) k_coating_grad(const uint8_t* blob, int m
   RowSink sink{grad + i * M.n_layers, M.layer_off, M.n_layers, side == 0};
   tmm_adjoint<P, RowSink, false, ACC>(sv, side == 0, mt, H.n_slab, cos0[i], make_float2(w[4 * i], w[4 * i + 1]),
                  make_float2(w[4 * i + 2], w[4 * i + 3]), which, sink, seg);
+}
+
+struct NullSink {
+  __device__ __forceinline__ void segment(const float (&)[8], int, int, int) const {}
+};
+
+// d f / d(cos theta_0) of single coatings (test hook of the adjoint's dual sweep)
+template <int P, bool ACC>
+__global__ void __launch_bounds__(128) k_coating_dcos(const uint8_t* blob, int mirror, int side, long long n,
+                                                       const float* cos0, const float* lam, const float* w, int which,
+                                                       float* out) {
+  __shared__ float s_seg[4 * seg_floats_per_warp<P>()];
+  float* seg = s_seg + (threadIdx.x >> 5) * seg_floats_per_warp<P>() + (threadIdx.x & 31);
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  Blob B;
+  B.bind(blob);
+  const BlobHeader& H = *B.h;
+  const MirrorRec& M = B.mir[mirror];
+  MatTable mt;
+  mt.init_sel<ACC>(H, cos0[i], 0.0f, lam[i]);
+  TiltTable tt;
+  tt.init(H, cos0[i]);
+  const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+  NullSink sink;
+  float g = 0.f;
+  tmm_adjoint<P, NullSink, true, ACC>(sv, side == 0, mt, H.n_slab, cos0[i], make_float2(w[4 * i], w[4 * i + 1]),
+                                       make_float2(w[4 * i + 2], w[4 * i + 3]), which, sink, seg, 0, &tt, &g);
+  out[i] = g;
 }
 
 // Every kernel's dynamic shared memory limit is raised once to the device's

@@ -55,4 +55,14 @@ cudaError_t launch_coating_grad(const uint8_t* blob, int P, bool acc, int mirror
   return cudaGetLastError();
 }
 
+cudaError_t launch_coating_dcos(const uint8_t* blob, int P, bool acc, int mirror, int side, long long n,
+                                const float* cos0, const float* lam, const float* w, int which, float* out,
+                                cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  note_launches(1);
+  WG_PICK_PA(k_coating_dcos, P, acc)<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(blob, mirror, side, n, cos0, lam,
+                                                                                 w, which, out);
+  return cudaGetLastError();
+}
+
 }  // namespace wgk

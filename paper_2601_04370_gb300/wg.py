@@ -130,6 +130,7 @@ def lib():
         L.wg_destroy_design.restype = None
         L.wg_eval_coating.argtypes = [vp, vp, i32, i32, i64, fp, fp, fp, vp]
         L.wg_eval_coating_grad.argtypes = [vp, vp, i32, i32, i64, fp, fp, fp, i32, fp, vp]
+        L.wg_eval_coating_dcos.argtypes = [vp, vp, i32, i32, i64, fp, fp, fp, i32, fp, vp]
         L.wg_trace_forward.argtypes = [vp, vp, C.POINTER(TraceCfg), vp, C.POINTER(Stats)]
         L.wg_trace_backward.argtypes = [vp, vp, C.POINTER(TraceCfg), vp, vp, vp, C.POINTER(Stats)]
         L.wg_loss.argtypes = [vp, vp, C.POINTER(TraceCfg), i32, C.c_double, C.c_double, vp, dp, vp]
@@ -157,7 +158,7 @@ def lib():
                      "wg_submit", "wg_poll", "wg_cancel", "wg_autotune", "wg_omega_trace", "wg_set_omega",
                      "wg_adam_create", "wg_adam_step", "wg_adam_params", "wg_omega_adam_create",
                      "wg_omega_adam_step", "wg_design_version", "wg_autotune_info",
-                     "wg_trace_forward_batch"):
+                     "wg_trace_forward_batch", "wg_eval_coating_dcos"):
             getattr(L, name).restype = C.c_int32
         _lib = L
     return _lib
@@ -496,6 +497,12 @@ class Context:
                                           stream if stream is not None else _current_stream()))
 
     # ---- trace ----
+    def eval_coating_dcos(self, dh, mirror, side, cos_theta, lambda_nm, weights, which, grad_cos, stream=None):
+        """wg_eval_coating_dcos: d f / d(cos theta_0) through the coating (device FP32 [n])."""
+        _check(lib().wg_eval_coating_dcos(self.h, dh.h, mirror, side, cos_theta.numel(), _ptr(cos_theta),
+                                          _ptr(lambda_nm), _ptr(weights), which, _ptr(grad_cos),
+                                          stream if stream is not None else _current_stream()))
+
     def trace_forward(self, dh, cfg, tally, stats=True, stream=None, rays=None, records=None, flags=0):
         """tally: torch CUDA float64 tensor (device path) or numpy float64 array
         (host path, copies inside the call). flags: TRACE_* bits. Returns the

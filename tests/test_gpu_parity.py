@@ -490,3 +490,35 @@ def test_invalid_inputs_are_rejected(ctx):
     with pytest.raises(wg.WGError):
         ctx.trace_forward(dh, C.replace(fy_deg=[3.0]), tally)
     dh.destroy()
+
+
+@pytest.mark.parametrize("L", [40, 200])
+@pytest.mark.parametrize("which", [0, 1])
+def test_coating_dcos_matches_oracle(ctx, ora, L, which):
+    """d f / d(cos theta_0) through single coatings (the coating term of the
+    mirror-tilt gradient, formed by the adjoint's reverse sweep) against the
+    oracle's reverse-mode tape, both sides of the stack. Measured: median
+    3e-6, p90 4e-5, max 3e-3 (relative)."""
+    D, _ = W.representative(n_rays=1000, n_layers=L)
+    dh = ctx.create_design(D)
+    for side in (0, 1):
+        rng = np.random.default_rng(11 * L + which + 2 * side)
+        n = 128
+        cos0 = rng.uniform(0.05, 1.0, n).astype(np.float32)
+        lam = rng.choice([460.0, 532.0, 630.0], n).astype(np.float32)
+        w = rng.normal(size=(n, 4)).astype(np.float32)
+        gc = torch.zeros(n, dtype=torch.float32, device="cuda")
+        ctx.eval_coating_dcos(dh, 1, side, _dev(cos0), _dev(lam), _dev(w), which, gc)
+        g = gc.cpu().numpy().astype(np.float64)
+        off = D.layer_offsets()
+        nm = D.mat_n.astype(np.float64)[D.layer_mat[off[1]:off[2]]]
+        dd = D.layer_d_nm.astype(np.float64)[off[1]:off[2]]
+        if side == 1:
+            nm, dd = nm[::-1], dd[::-1]
+        ref = np.array([ora.tmm_grad(D.n_slab, nm, dd, float(lam[i]), float(cos0[i]), complex(w[i, 0], w[i, 1]),
+                                     complex(w[i, 2], w[i, 3]), "r" if which == 0 else "t")[1] for i in range(n)])
+        rel = np.abs(g - ref) / np.maximum(np.abs(ref), 1e-30)
+        assert np.median(rel) <= 2e-5, np.median(rel)
+        assert np.quantile(rel, 0.9) <= 3e-4, np.quantile(rel, 0.9)
+        assert rel.max() <= 2e-2, rel.max()
+    dh.destroy()
