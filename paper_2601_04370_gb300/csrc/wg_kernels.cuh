@@ -981,13 +981,26 @@ __global__ void __launch_bounds__(kBlock, 2)
 //   With the tilt gradient the reverse sweep also forms each record's
 //   dL/d(cos theta_0) (tmm_adjoint<..., DUAL>).
 // ---------------------------------------------------------------------------
-template <int F>
-struct TapeE {
+// the low part of a hit's incidence cosine: kept in the tape in accurate
+// mode only (the fast mode's tape stays as small as before)
+template <bool ACC>
+struct TapeLo {
+  float cos0l_;
+  __device__ __forceinline__ float cos0l() const { return cos0l_; }
+  __device__ __forceinline__ void set_cos0l(float v) { cos0l_ = v; }
+};
+template <>
+struct TapeLo<false> {
+  __device__ __forceinline__ float cos0l() const { return 0.0f; }
+  __device__ __forceinline__ void set_cos0l(float) {}
+};
+template <int F, bool ACC>
+struct TapeE : TapeLo<ACC> {
   float2 cs, cp;
   float2 Es[F], Ep[F];
   float cphi, sphi, cpsi, spsi;
   float2 seg_s, seg_p;
-  float cos0, cos0l;
+  float cos0;
   int kfw;
 };
 
@@ -1012,7 +1025,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
   const long long cap = A.hit_cap;
 
   int c_rays = 0, c_hits = 0, c_overflow = 0, c_tallied = 0, c_steps = 0;
-  TapeE<F> tape[TAPE_HITS];
+  TapeE<F, ACC> tape[TAPE_HITS];
 
   // warp-private work unit (a short ray range of one cell, warp-uniform)
   long long u_cell = 0, u_next = 0, u_end = 0;
@@ -1174,7 +1187,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                   gb[f] = cmulc(seg_p, cscale(R.b[f], sc * o.Tp));
                 }
                 for (int h = emit - 1; h >= 0; --h) {
-                  const TapeE<F>& E = tape[h];
+                  const TapeE<F, ACC>& E = tape[h];
                   float2 gs[F], gp[F];
                   float2 As = make_float2(0.f, 0.f), Ap = make_float2(0.f, 0.f);
                   const int k = E.kfw & 0xff;
@@ -1223,7 +1236,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                     HitRec rec;
                     rec.kfw = E.kfw | ((int)(cell_l / A.n_f) << 10);
                     rec.cos0 = E.cos0;
-                    rec.cos0l = E.cos0l;
+                    rec.cos0l = E.cos0l();
                     rec.eA = eG;
                     rec.As = cscale(As, scl);
                     rec.Ap = cscale(Ap, scl);
@@ -1256,7 +1269,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
           float2 Es[F], Ep[F];
           const MirrorStep ms = mirror_event<F, P, 2, ACC>(R, hit_k, B, lam_l, (int)(cell_l / A.n_f), A, c_steps, Es, Ep);
           if (h < TAPE_HITS) {
-            TapeE<F>& E = tape[h];
+            TapeE<F, ACC>& E = tape[h];
             E.cs = ms.cs;
             E.cp = ms.cp;
 #pragma unroll
@@ -1271,7 +1284,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
             E.seg_s = seg_s;
             E.seg_p = seg_p;
             E.cos0 = ms.cos0;
-            E.cos0l = ms.cos0l;
+            E.set_cos0l(ms.cos0l);
             E.kfw = hit_k | (ms.front << 8) | ((ms.refl ? 0 : 1) << 9);
           }
           seg_s = make_float2(1.f, 0.f);
