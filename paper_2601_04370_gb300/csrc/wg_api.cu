@@ -1358,7 +1358,7 @@ static void plan_range(Plan& p, long long rb, long long re) {
 struct BwdScratch {
   HitRec* rec;
   HitRec* sorted;
-  unsigned int* keys;   // [3][128]: counts, offsets, cursors
+  unsigned int* keys;   // [3][kSortKeys]: counts, offsets, cursors
   unsigned long long* hit_count;
   double* grad_acc;
   long long cap;
@@ -1448,7 +1448,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   const bool use_lut = cfg->lut_bins > 0;
   const long long n_lut = use_lut ? lut_entries(d, cfg) : 0;
   const size_t lut_bytes = use_lut ? (size_t)n_lut * (8 * sizeof(double) + 2 * hit_rec_bytes()) : 0;
-  const size_t need = 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + acc_bytes + aux_bytes + lut_bytes;
+  const size_t need = 2 * rec_bytes + 3 * kSortKeys * sizeof(unsigned int) + 64 + acc_bytes + aux_bytes + lut_bytes;
   if (need > c->bwd.n) {
     CU(cudaEventSynchronize(c->ws_free));
     CU(c->bwd.ensure(need));
@@ -1458,14 +1458,14 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   sc.rec = (HitRec*)bw;
   sc.sorted = (HitRec*)(bw + rec_bytes);
   sc.keys = (unsigned int*)(bw + 2 * rec_bytes);
-  sc.hit_count = (unsigned long long*)(bw + 2 * rec_bytes + 3 * 128 * sizeof(unsigned int));
-  sc.grad_acc = (double*)(bw + 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64);
+  sc.hit_count = (unsigned long long*)(bw + 2 * rec_bytes + 3 * kSortKeys * sizeof(unsigned int));
+  sc.grad_acc = (double*)(bw + 2 * rec_bytes + 3 * kSortKeys * sizeof(unsigned int) + 64);
   sc.cap = cap;
   TiltAux* tilt_aux = nullptr;
   RayHead* heads = nullptr;
   unsigned int* perm = nullptr;  // sorted record -> its slot in tilt_aux
   if (tilt) {
-    tilt_aux = (TiltAux*)(bw + 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + acc_bytes);
+    tilt_aux = (TiltAux*)(bw + 2 * rec_bytes + 3 * kSortKeys * sizeof(unsigned int) + 64 + acc_bytes);
     heads = (RayHead*)((uint8_t*)tilt_aux + (size_t)cap * sizeof(TiltAux));
     perm = (unsigned int*)((uint8_t*)heads + (size_t)batch * sizeof(RayHead));
   }
@@ -1479,7 +1479,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
   double* lut_grad = nullptr;
   HitRec* lut_recs = nullptr;
   if (use_lut) {
-    lut_grad = (double*)(bw + 2 * rec_bytes + 3 * 128 * sizeof(unsigned int) + 64 + acc_bytes + aux_bytes);
+    lut_grad = (double*)(bw + 2 * rec_bytes + 3 * kSortKeys * sizeof(unsigned int) + 64 + acc_bytes + aux_bytes);
     lut_recs = (HitRec*)((uint8_t*)lut_grad + (size_t)n_lut * 8 * sizeof(double));
   }
   const bool dev_G = is_device_ptr(dL_dtally);
@@ -1546,7 +1546,6 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     a.hit_buf = sc.rec;
     a.hit_cap = cap;
     a.hit_count = sc.hit_count;
-    a.key_count = sc.keys;
     a.tilt_aux = tilt_aux;
     a.ray_heads = heads;
     a.head_cap = b1 - b0;
@@ -1558,7 +1557,7 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
     a.lut_inv_dc = lut_a.lut_inv_dc;
     a.lut_grad = lut_a.lut_grad;
     CU(cudaMemsetAsync(&w.head->work, 0, sizeof(unsigned long long), s));
-    CU(cudaMemsetAsync(sc.keys, 0, 128 * sizeof(unsigned int), s));
+    CU(cudaMemsetAsync(sc.keys, 0, kSortKeys * sizeof(unsigned int), s));
     CU(cudaMemsetAsync(sc.hit_count, 0, 2 * sizeof(unsigned long long), s));
     const int grid_r = (int)std::max<long long>(1, std::min<long long>(a.n_chunks, (long long)c->sm_count * bps_r));
     if (stats) CU(cudaEventRecord(c->t0, s));
@@ -1576,7 +1575,8 @@ extern "C" wg_status wg_trace_backward(wg_ctx* c, const wg_design* d, const wg_t
       batch = std::max<long long>(1, (b1 - b0) / 2);
       continue;
     }
-    if (!use_lut) CU(launch_bwd_sort(sc.rec, (long long)n_rec, sc.keys, sc.keys + 128, sc.keys + 256, sc.sorted, perm, s));
+    if (!use_lut) CU(launch_bwd_sort(sc.rec, (long long)n_rec, d->blob, sc.keys, sc.keys + kSortKeys, sc.keys + 2 * kSortKeys,
+                                         sc.sorted, perm, s));
     AdjArgs aa;
     memset(&aa, 0, sizeof(aa));
     aa.wait_ns = c->wait_limit_ns;

@@ -64,7 +64,6 @@ struct TraceArgs {
   HitRec* hit_buf;            // [hit_cap] hit records
   long long hit_cap;
   unsigned long long* hit_count;  // records reserved (may exceed hit_cap: overflow)
-  unsigned int* key_count;    // [2 * 64] records per stack (mirror, side)
   int n_layers;               // device layers
   // forward: list of eyebox rays (null: not recorded)
   ExitRec* exit_list;
@@ -128,6 +127,10 @@ struct AdjArgs {
 };
 
 constexpr int kBlock = 256;
+// sort keys of the adjoint's hit records: stack (mirror, side; 2 x 64) x
+// evanescence class (how many of the design's materials are evanescent at
+// the hit's incidence angle, 0..7)
+constexpr int kStackKeys = 128, kClsPerStack = 8, kSortKeys = kStackKeys * kClsPerStack;
 // the forward kernel keeps up to this many chunks (cells) in flight per CTA,
 // each with its own FP32 shared tally. Large chunks take two: a CTA then
 // draws its rays from fewer cells at a time (same wavelength and field, so
@@ -184,7 +187,7 @@ cudaError_t launch_trace_fwd_fused(const TraceArgs* jobs_dev, const int* cta_job
 cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, bool tilt, int gm, bool acc, int grid, size_t smem,
                               cudaStream_t s);
 // perm (may be null): perm[sorted position] = index of the record in `in`
-cudaError_t launch_bwd_sort(const HitRec* in, long long n, unsigned int* key_count, unsigned int* key_off,
+cudaError_t launch_bwd_sort(const HitRec* in, long long n, const uint8_t* blob, unsigned int* key_count, unsigned int* key_off,
                             unsigned int* key_cursor, HitRec* out, unsigned int* perm, cudaStream_t s);
 cudaError_t launch_bwd_adjoint(const AdjArgs& a, int P, bool acc, int grid, size_t smem,
                                cudaStream_t s);  // a.tilt_aux picks the variant

@@ -33,6 +33,25 @@ struct alignas(16) HitRec {
   float2 As, Ap;
 };
 __device__ __forceinline__ int kfw_lam(int kfw) { return (kfw >> 10) & 0xffff; }
+static_assert(kStackKeys == 2 * MAX_MIR, "stack keys");
+// stack of a hit record: (mirror, side)
+__device__ __forceinline__ int stack_key(int kfw) { return ((kfw & 0xff) << 1) | ((kfw >> 8) & 1); }
+// evanescence class of an incidence cosine: the number of the design's
+// materials with (n0/n)^2 sin^2 t0 > 1. The adjoint's records are sorted by
+// it within their stack, so that the lanes of a warp agree on which layers
+// are evanescent (a divergent branch in the layer loop otherwise runs both
+// of its sides); it decides nothing else.
+__device__ __forceinline__ int evan_class(const BlobHeader& H, float cos0) {
+  const float sin2 = fmaf(-cos0, cos0, 1.0f);
+  int n = 0;
+#pragma unroll
+  for (int i = 0; i < MAX_MAT; ++i) n += (i < H.n_mat && H.mat_r2[i] * sin2 > 1.0f) ? 1 : 0;
+  return min(n, kClsPerStack - 1);
+}
+// sort key of a record: its stack, then its evanescence class
+__device__ __forceinline__ int sort_key(const HitRec& r, const BlobHeader& H) {
+  return stack_key(r.kfw) * kClsPerStack + evan_class(H, r.cos0);
+}
 static_assert(sizeof(HitRec) == 32, "hit record");
 // per-ray record (layout of wg_ray_record)
 struct RayRec {
@@ -1011,10 +1030,8 @@ template <int F, int P, bool T, int GM, bool ACC>
 __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_mbar;
-  __shared__ unsigned int s_keys[2 * MAX_MIR];
   __shared__ unsigned long long s_cnt[8];
   const int tid = threadIdx.x, lane = tid & 31;
-  for (int i = tid; i < 2 * MAX_MIR; i += blockDim.x) s_keys[i] = 0u;
   if (tid < 8) s_cnt[tid] = 0ull;
   if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error, wait_limit(A.wait_ns))) return;
   Blob B;
@@ -1241,7 +1258,6 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                     rec.As = cscale(As, scl);
                     rec.Ap = cscale(Ap, scl);
                     hb[first + h] = rec;
-                    atomicAdd(&s_keys[((E.kfw & 0xff) << 1) | ((E.kfw >> 8) & 1)], 1u);  // stack (mirror, side)
                   }
                   if constexpr (T) {
                     TiltAux ta;
@@ -1312,8 +1328,6 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
   }
   __syncthreads();
   if (tid < 7 && s_cnt[tid]) atomicAdd(A.counters + tid, s_cnt[tid]);
-  for (int i = tid; i < 2 * MAX_MIR; i += blockDim.x)
-    if (s_keys[i]) atomicAdd(A.key_count + i, s_keys[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1591,8 +1605,6 @@ __global__ void __launch_bounds__(kTiltBlock) k_tilt_grad(const TraceArgs A) {
   }
 }
 
-__device__ __forceinline__ int rec_key(int kfw) { return ((kfw & 0xff) << 1) | ((kfw >> 8) & 1); }
-
 // Gradient terms of one record per lane, a segment (up to 8 layers) at a
 // time. When all 32 lanes hold records of the same stack (uniform, a
 // warp-uniform flag) their terms go to the same layers: summed across the
@@ -1666,7 +1678,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_adjoint(const AdjArgs A) {
       HitRec rec;
       rec.kfw = -1;
       if (valid) rec = A.recs[i];
-      const int key = valid ? rec_key(rec.kfw) : -1 - lane;
+      const int key = valid ? stack_key(rec.kfw) : -1 - lane;
       const int key0 = __shfl_sync(FULL, key, 0);
       const bool uniform = __all_sync(FULL, key == key0);
       if (valid) {

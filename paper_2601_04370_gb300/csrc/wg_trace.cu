@@ -368,37 +368,73 @@ size_t tilt_smem_bytes(int blob_bytes, int F) {
          sizeof(float) * (size_t)(kTiltBlock / 32) * kTiltPass * (3 + 4 * F) * 32;
 }
 
-// exclusive prefix of the per-stack record counts (one block)
+// exclusive prefix of the per-key record counts (one block of kSortKeys
+// threads: warp-level inclusive scans, then the scan of the warp totals)
 __global__ void k_bwd_scan(const unsigned int* key_count, unsigned int* key_off, unsigned int* key_cursor) {
-  __shared__ unsigned int s[2 * MAX_MIR];
-  const int t = threadIdx.x;
-  if (t < 2 * MAX_MIR) s[t] = key_count[t];
+  constexpr int NW = kSortKeys / 32;
+  __shared__ unsigned int s_w[NW];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const unsigned int c = key_count[t];
+  unsigned int x = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned int y = __shfl_up_sync(FULL, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_w[w] = x;
   __syncthreads();
-  if (t == 0) {
-    unsigned int acc = 0;
-    for (int i = 0; i < 2 * MAX_MIR; ++i) {
-      const unsigned int c = s[i];
-      s[i] = acc;
-      acc += c;
+  if (w == 0) {
+    unsigned int v = lane < NW ? s_w[lane] : 0u;
+    const unsigned int own = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned int y = __shfl_up_sync(FULL, v, o);
+      if (lane >= o) v += y;
     }
+    if (lane < NW) s_w[lane] = v - own;  // exclusive prefix of the warp totals
   }
   __syncthreads();
-  if (t < 2 * MAX_MIR) {
-    key_off[t] = s[t];
-    key_cursor[t] = s[t];
-  }
+  const unsigned int off = s_w[w] + x - c;
+  key_off[t] = off;
+  key_cursor[t] = off;
 }
 
-// Scatter into stack order. A block takes a tile of kScatterItems records per
-// thread, ranks them per stack in shared memory (warp-aggregated), reserves
-// one range per stack with a single global atomic, then writes.
+// Records per sort key (stack, then evanescence class), counted per block in
+// shared memory (warp-aggregated) and added to the global counts.
 constexpr int kScatterItems = 8;
-// perm (optional): perm[sorted position] = record index before the sort
-__global__ void k_bwd_scatter(const HitRec* in, long long n, unsigned int* key_cursor, HitRec* out,
-                              unsigned int* perm) {
-  __shared__ unsigned int s_cnt[2 * MAX_MIR], s_base[2 * MAX_MIR];
+__global__ void k_bwd_count(const HitRec* in, long long n, const uint8_t* blob, unsigned int* key_count) {
+  __shared__ unsigned int s_cnt[kSortKeys];
+  const BlobHeader& H = *reinterpret_cast<const BlobHeader*>(blob);
   const int tid = threadIdx.x, lane = tid & 31;
-  for (int k = tid; k < 2 * MAX_MIR; k += blockDim.x) s_cnt[k] = 0u;
+  for (int k = tid; k < kSortKeys; k += blockDim.x) s_cnt[k] = 0u;
+  __syncthreads();
+  const long long tile = (long long)blockIdx.x * blockDim.x * kScatterItems;
+#pragma unroll
+  for (int t = 0; t < kScatterItems; ++t) {
+    const long long i = tile + (long long)t * blockDim.x + tid;
+    int key = -1;
+    if (i < n) {
+      const HitRec r = in[i];
+      if (r.kfw >= 0) key = sort_key(r, H);
+    }
+    const unsigned peers = __match_any_sync(FULL, key);
+    if (key >= 0 && lane == __ffs(peers) - 1) atomicAdd(&s_cnt[key], (unsigned)__popc(peers));
+  }
+  __syncthreads();
+  for (int k = tid; k < kSortKeys; k += blockDim.x)
+    if (s_cnt[k]) atomicAdd(key_count + k, s_cnt[k]);
+}
+
+// Scatter into key order. A block takes a tile of kScatterItems records per
+// thread, ranks them per key in shared memory (warp-aggregated), reserves
+// one range per key with a single global atomic, then writes.
+// perm (optional): perm[sorted position] = record index before the sort
+__global__ void k_bwd_scatter(const HitRec* in, long long n, const uint8_t* blob, unsigned int* key_cursor,
+                              HitRec* out, unsigned int* perm) {
+  const BlobHeader& H = *reinterpret_cast<const BlobHeader*>(blob);
+  __shared__ unsigned int s_cnt[kSortKeys], s_base[kSortKeys];
+  const int tid = threadIdx.x, lane = tid & 31;
+  for (int k = tid; k < kSortKeys; k += blockDim.x) s_cnt[k] = 0u;
   __syncthreads();
   const long long tile = (long long)blockIdx.x * blockDim.x * kScatterItems;
   HitRec r[kScatterItems];
@@ -410,7 +446,7 @@ __global__ void k_bwd_scatter(const HitRec* in, long long n, unsigned int* key_c
     key[t] = -1;
     if (i < n) {
       r[t] = in[i];
-      if (r[t].kfw >= 0) key[t] = rec_key(r[t].kfw);
+      if (r[t].kfw >= 0) key[t] = sort_key(r[t], H);
     }
     const unsigned peers = __match_any_sync(FULL, key[t]);
     const int leader = __ffs(peers) - 1;
@@ -420,7 +456,7 @@ __global__ void k_bwd_scatter(const HitRec* in, long long n, unsigned int* key_c
     rank[t] = base + __popc(peers & ((1u << lane) - 1u));
   }
   __syncthreads();
-  for (int k = tid; k < 2 * MAX_MIR; k += blockDim.x)
+  for (int k = tid; k < kSortKeys; k += blockDim.x)
     if (s_cnt[k]) s_base[k] = atomicAdd(key_cursor + k, s_cnt[k]);
   __syncthreads();
 #pragma unroll
@@ -525,14 +561,22 @@ cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const in
   return cudaGetLastError();
 }
 
-cudaError_t launch_bwd_sort(const HitRec* in, long long n, unsigned int* key_count, unsigned int* key_off,
-                            unsigned int* key_cursor, HitRec* out, unsigned int* perm, cudaStream_t s) {
-  note_launches(1);
-  k_bwd_scan<<<1, 2 * MAX_MIR, 0, s>>>(key_count, key_off, key_cursor);
+// counting sort of the records by key: key_count must be zero on entry
+cudaError_t launch_bwd_sort(const HitRec* in, long long n, const uint8_t* blob, unsigned int* key_count,
+                            unsigned int* key_off, unsigned int* key_cursor, HitRec* out, unsigned int* perm,
+                            cudaStream_t s) {
+  const long long per_block = 256ll * kScatterItems;
+  const unsigned grid = (unsigned)((n + per_block - 1) / per_block);
   if (n > 0) {
     note_launches(1);
-    const long long per_block = 256ll * kScatterItems;
-    k_bwd_scatter<<<(unsigned)((n + per_block - 1) / per_block), 256, 0, s>>>(in, n, key_cursor, out, perm);
+    k_bwd_count<<<grid, 256, 0, s>>>(in, n, blob, key_count);
+  }
+  note_launches(1);
+  static_assert(kSortKeys % 32 == 0 && kSortKeys / 32 <= 32 && kSortKeys <= 1024, "one scan block");
+  k_bwd_scan<<<1, kSortKeys, 0, s>>>(key_count, key_off, key_cursor);
+  if (n > 0) {
+    note_launches(1);
+    k_bwd_scatter<<<grid, 256, 0, s>>>(in, n, blob, key_cursor, out, perm);
   }
   return cudaGetLastError();
 }
