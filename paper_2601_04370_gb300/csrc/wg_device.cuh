@@ -402,24 +402,32 @@ __device__ __forceinline__ void layer_cs(const MatK& k, float d, float& c, float
 // error at ~1 ulp (the left-to-right matrix product loses the
 // subdominant part behind evanescent barriers). v = (x, y) complex,
 // M_j = [[c, i m12], [i m21, c]] real-structured:
-//   x' = c x + i m12 y,  y' = i m21 x + c y            (8 FMA-pipe ops)
+//   x' = c x + i m12 y,  y' = i m21 x + c y.
+// The vector is carried as (x, z) with z = i y: the step then has real
+// coefficients only, x' = c x + m12 z, z' = c z - m21 x, two complex
+// multiply-adds per entry that map onto the paired FP32 instructions
+// (one issue for the real and imaginary parts; per component the same
+// fmaf and product as the scalar form, so the same values).
 // ---------------------------------------------------------------------------
 struct CV {
-  float xr, xi, yr, yi;
+  float xr, xi;  // x
+  float zr, zi;  // z = i y, i.e. y = (zi, -zr)
 };
+__device__ __forceinline__ float2 f2b(float a) { return make_float2(a, a); }
 __device__ __forceinline__ void cv_step(CV& v, float c, float m12, float m21) {
-  const float xr = fmaf(c, v.xr, -m12 * v.yi);
-  const float xi = fmaf(c, v.xi, m12 * v.yr);
-  const float yr = fmaf(c, v.yr, -m21 * v.xi);
-  const float yi = fmaf(c, v.yi, m21 * v.xr);
-  v.xr = xr;
-  v.xi = xi;
-  v.yr = yr;
-  v.yi = yi;
+  const float2 X = make_float2(v.xr, v.xi), Z = make_float2(v.zr, v.zi), cc = f2b(c);
+  const float2 X2 = __ffma2_rn(cc, X, __fmul2_rn(f2b(m12), Z));
+  const float2 Z2 = __ffma2_rn(cc, Z, __fmul2_rn(f2b(-m21), X));
+  v.xr = X2.x;
+  v.xi = X2.y;
+  v.zr = Z2.x;
+  v.zi = Z2.y;
 }
 __device__ __forceinline__ float cv_maxabs(const CV& v) {
-  return fmaxf(fmaxf(fabsf(v.xr), fabsf(v.xi)), fmaxf(fabsf(v.yr), fabsf(v.yi)));
+  return fmaxf(fmaxf(fabsf(v.xr), fabsf(v.xi)), fmaxf(fabsf(v.zi), fabsf(v.zr)));
 }
+// the initial vector (1, eta) of the substrate side: z = i eta
+__device__ __forceinline__ CV cv_init(float eta) { return CV{1.0f, 0.0f, 0.0f, eta}; }
 constexpr float TWO_P64 = 1.8446744073709552e19f;   // 2^64
 constexpr float TWO_M64 = 5.421010862427522e-20f;   // 2^-64
 // keep entries below 2^64 by exact power-of-two scaling; e counts the scale
@@ -427,8 +435,8 @@ __device__ __forceinline__ void cv_rescale(CV& v, int& e) {
   if (cv_maxabs(v) > TWO_P64) {
     v.xr *= TWO_M64;
     v.xi *= TWO_M64;
-    v.yr *= TWO_M64;
-    v.yi *= TWO_M64;
+    v.zr *= TWO_M64;
+    v.zi *= TWO_M64;
     e += 64;
   }
 }
@@ -473,8 +481,9 @@ __device__ __forceinline__ float2 crcp_s(float2 b) {
 // r = (eta0 B - C)/(eta0 B + C), t = 2 eta0/(eta0 B + C) (Macleod); the
 // scale 2^e of v cancels in r and multiplies t by 2^-e.
 __device__ __forceinline__ void coef_from_v(const CV& v, float eta0, int e, float2& r, float2& t) {
-  const float2 den = make_float2(fmaf(eta0, v.xr, v.yr), fmaf(eta0, v.xi, v.yi));
-  const float2 num = make_float2(fmaf(eta0, v.xr, -v.yr), fmaf(eta0, v.xi, -v.yi));
+  // B = x, C = y = (zi, -zr)
+  const float2 den = make_float2(fmaf(eta0, v.xr, v.zi), fmaf(eta0, v.xi, -v.zr));
+  const float2 num = make_float2(fmaf(eta0, v.xr, -v.zi), fmaf(eta0, v.xi, v.zr));
   const float2 q = crcp_s(den);
   r = cmul(num, q);
   t = cscale(cscale(q, 2.0f * eta0), pow2i(-e));
@@ -509,7 +518,7 @@ __device__ __forceinline__ Coef tmm_forward(const StackView& st, bool front, con
   MatK kb[Seg<P>::NSLOT];
   if constexpr (P > 0) stack_slots<P>(st, front, mt, kb);
   const float eta_s = n0 * cos0, eta_p = n0 / cos0;
-  CV vs{1.0f, 0.0f, eta_s, 0.0f}, vp{1.0f, 0.0f, eta_p, 0.0f};
+  CV vs = cv_init(eta_s), vp = cv_init(eta_p);
   int es = 0, ep = 0;
   const int L = st.L;
   for (int j0 = L > 0 ? ((L - 1) / CKP) * CKP : -1; j0 >= 0; j0 -= CKP) {
@@ -594,23 +603,24 @@ struct MatTableD {
 // v' = M v and its derivative dv' = dM v + M dv (M = [[c, i m12], [i m21, c]])
 __device__ __forceinline__ void cv_step_d(CV& v, CV& dv, float c, float m12, float m21, float dc, float dm12,
                                           float dm21) {
+  // in (x, z) form: dx' = dc x + c dx + dm12 z + m12 dz, dz' = dc z + c dz - dm21 x - m21 dx
   const CV o = v;
   cv_step(v, c, m12, m21);
-  const float xr = fmaf(dc, o.xr, fmaf(c, dv.xr, -fmaf(dm12, o.yi, m12 * dv.yi)));
-  const float xi = fmaf(dc, o.xi, fmaf(c, dv.xi, fmaf(dm12, o.yr, m12 * dv.yr)));
-  const float yr = fmaf(dc, o.yr, fmaf(c, dv.yr, -fmaf(dm21, o.xi, m21 * dv.xi)));
-  const float yi = fmaf(dc, o.yi, fmaf(c, dv.yi, fmaf(dm21, o.xr, m21 * dv.xr)));
+  const float xr = fmaf(dc, o.xr, fmaf(c, dv.xr, fmaf(dm12, o.zr, m12 * dv.zr)));
+  const float xi = fmaf(dc, o.xi, fmaf(c, dv.xi, fmaf(dm12, o.zi, m12 * dv.zi)));
+  const float zr = fmaf(dc, o.zr, fmaf(c, dv.zr, -fmaf(dm21, o.xr, m21 * dv.xr)));
+  const float zi = fmaf(dc, o.zi, fmaf(c, dv.zi, -fmaf(dm21, o.xi, m21 * dv.xi)));
   dv.xr = xr;
   dv.xi = xi;
-  dv.yr = yr;
-  dv.yi = yi;
+  dv.zr = zr;
+  dv.zi = zi;
 }
 
 // r, t and their derivatives from the (scaled) vector and its derivative
 __device__ __forceinline__ void coef_from_v_d(const CV& v, const CV& dv, float eta0, float deta0, int e, float2& r,
                                               float2& t, float2& dr, float2& dt) {
-  const float2 B = make_float2(v.xr, v.xi), C = make_float2(v.yr, v.yi);
-  const float2 dB = make_float2(dv.xr, dv.xi), dC = make_float2(dv.yr, dv.yi);
+  const float2 B = make_float2(v.xr, v.xi), C = make_float2(v.zi, -v.zr);
+  const float2 dB = make_float2(dv.xr, dv.xi), dC = make_float2(dv.zi, -dv.zr);
   const float2 den = make_float2(fmaf(eta0, B.x, C.x), fmaf(eta0, B.y, C.y));
   const float2 num = make_float2(fmaf(eta0, B.x, -C.x), fmaf(eta0, B.y, -C.y));
   const float2 dden = make_float2(fmaf(deta0, B.x, fmaf(eta0, dB.x, dC.x)), fmaf(deta0, B.y, fmaf(eta0, dB.y, dC.y)));
@@ -626,8 +636,8 @@ __device__ __forceinline__ void coef_from_v_d(const CV& v, const CV& dv, float e
 // v and its derivative scaled by the same exact power of two
 __device__ __forceinline__ void cv_rescale_d(CV& v, CV& dv, int& e) {
   if (fmaxf(cv_maxabs(v), cv_maxabs(dv)) > TWO_P64) {
-    v = CV{v.xr * TWO_M64, v.xi * TWO_M64, v.yr * TWO_M64, v.yi * TWO_M64};
-    dv = CV{dv.xr * TWO_M64, dv.xi * TWO_M64, dv.yr * TWO_M64, dv.yi * TWO_M64};
+    v = CV{v.xr * TWO_M64, v.xi * TWO_M64, v.zr * TWO_M64, v.zi * TWO_M64};
+    dv = CV{dv.xr * TWO_M64, dv.xi * TWO_M64, dv.zr * TWO_M64, dv.zi * TWO_M64};
     e += 64;
   }
 }
@@ -654,8 +664,8 @@ __device__ __forceinline__ void tmm_forward_dual(const StackView& st, bool front
   }
   const float eta_s = n0 * cos0, eta_p = n0 / cos0;
   const float deta_s = n0, deta_p = -eta_p / cos0;
-  CV vs{1.0f, 0.0f, eta_s, 0.0f}, vp{1.0f, 0.0f, eta_p, 0.0f};
-  CV dvs{0.0f, 0.0f, deta_s, 0.0f}, dvp{0.0f, 0.0f, deta_p, 0.0f};
+  CV vs = cv_init(eta_s), vp = cv_init(eta_p);
+  CV dvs{0.0f, 0.0f, 0.0f, deta_s}, dvp{0.0f, 0.0f, 0.0f, deta_p};
   int es = 0, ep = 0;
   const int L = st.L;
   for (int j0 = L > 0 ? ((L - 1) / CKP) * CKP : -1; j0 >= 0; j0 -= CKP) {
@@ -718,14 +728,19 @@ struct Ckpt {
   int es, ep;
 };
 
+// The row a = (a0, a1) is carried as (a0, b) with b = i a1, i.e. a1 =
+// (b.y, -b.x): the step a' = a M, a0' = c a0 + i m21 a1, a1' = i m12 a0 +
+// c a1, becomes a0' = c a0 + m21 b, b' = c b - m12 a0 (real coefficients,
+// the paired FP32 instructions; per component the scalar form's values).
 struct CRow {
-  float2 a0, a1;
+  float2 a0, b;
 };
 __device__ __forceinline__ void row_step(CRow& a, float c, float m12, float m21) {
-  const float2 a0 = make_float2(fmaf(c, a.a0.x, -m21 * a.a1.y), fmaf(c, a.a0.y, m21 * a.a1.x));
-  const float2 a1 = make_float2(fmaf(c, a.a1.x, -m12 * a.a0.y), fmaf(c, a.a1.y, m12 * a.a0.x));
+  const float2 cc = f2b(c);
+  const float2 a0 = __ffma2_rn(cc, a.a0, __fmul2_rn(f2b(m21), a.b));
+  const float2 b = __ffma2_rn(cc, a.b, __fmul2_rn(f2b(-m12), a.a0));
   a.a0 = a0;
-  a.a1 = a1;
+  a.b = b;
 }
 // The adjoint keeps both factors of its products a_j . v_j within 2^32 (a:
 // checked every layer; v: checkpoints <= 2^32, and a segment of CK layers
@@ -734,12 +749,12 @@ __device__ __forceinline__ void row_step(CRow& a, float c, float m12, float m21)
 constexpr float TWO_P32 = 4294967296.0f;
 constexpr float TWO_M32 = 2.3283064365386963e-10f;
 __device__ __forceinline__ float row_maxabs(const CRow& a) {
-  return fmaxf(fmaxf(fabsf(a.a0.x), fabsf(a.a0.y)), fmaxf(fabsf(a.a1.x), fabsf(a.a1.y)));
+  return fmaxf(fmaxf(fabsf(a.a0.x), fabsf(a.a0.y)), fmaxf(fabsf(a.b.y), fabsf(a.b.x)));
 }
 __device__ __forceinline__ void row_guard(CRow& a, int& e) {
   if (row_maxabs(a) > TWO_P32) {
     a.a0 = cscale(a.a0, TWO_M32);
-    a.a1 = cscale(a.a1, TWO_M32);
+    a.b = cscale(a.b, TWO_M32);
     e += 32;
   }
 }
@@ -747,11 +762,11 @@ __device__ __forceinline__ void row_renorm(CRow& a, int& e) {
   const float m = row_maxabs(a);
   if (m > TWO_P32) {
     a.a0 = cscale(a.a0, TWO_M32);
-    a.a1 = cscale(a.a1, TWO_M32);
+    a.b = cscale(a.b, TWO_M32);
     e += 32;
   } else if (m < TWO_M32 && m > 0.0f) {
     a.a0 = cscale(a.a0, TWO_P32);
-    a.a1 = cscale(a.a1, TWO_P32);
+    a.b = cscale(a.b, TWO_P32);
     e -= 32;
   }
 }
@@ -759,32 +774,34 @@ __device__ __forceinline__ void cv_rescale32(CV& v, int& e) {
   if (cv_maxabs(v) > TWO_P32) {
     v.xr *= TWO_M32;
     v.xi *= TWO_M32;
-    v.yr *= TWO_M32;
-    v.yi *= TWO_M32;
+    v.zr *= TWO_M32;
+    v.zi *= TWO_M32;
     e += 32;
   }
 }
 
 // rho for one polarization (scaled v, exponent e): returns the row and its exponent
 __device__ __forceinline__ CRow coef_row(const CV& v, float eta0, int e, float2 A, int which, int& ea) {
-  const float2 B = make_float2(v.xr, v.xi), C = make_float2(v.yr, v.yi);
+  const float2 B = make_float2(v.xr, v.xi), C = make_float2(v.zi, -v.zr);
   const float2 den = make_float2(fmaf(eta0, B.x, C.x), fmaf(eta0, B.y, C.y));
   CRow a;
+  float2 a1;
   if (which == 0) {
     // dr/dB = 2 eta0 C / den^2, dr/dC = -2 eta0 B / den^2
     const float2 dB = cscale(cdiv_s(cdiv_s(C, den), den), 2.0f * eta0);
     const float2 dC = cscale(cdiv_s(cdiv_s(B, den), den), -2.0f * eta0);
     a.a0 = cmul(A, dB);
-    a.a1 = cmul(A, dC);
+    a1 = cmul(A, dC);
     ea = -e;
   } else {
     // t = 2 eta0 / den: dt/dB = -eta0 t / den, dt/dC = -t / den
     const float2 t = cdiv_s(make_float2(2.0f * eta0, 0.0f), den);
     const float2 td = cdiv_s(t, den);
     a.a0 = cmul(A, cscale(td, -eta0));
-    a.a1 = cmul(A, cscale(td, -1.0f));
+    a1 = cmul(A, cscale(td, -1.0f));
     ea = -2 * e;
   }
+  a.b = make_float2(-a1.y, a1.x);  // b = i a1
   return a;
 }
 
@@ -825,7 +842,7 @@ struct TiltTable {
 // gives 2 B C / den^2, t = 2 eta0 2^-e / den gives 2 C 2^-e / den^2
 // (den = eta0 B + C on the scaled vector; A already carries the r_p sign).
 __device__ __forceinline__ float coef_deta(const CV& v, float eta0, int e, float2 A, int which) {
-  const float2 B = make_float2(v.xr, v.xi), C = make_float2(v.yr, v.yi);
+  const float2 B = make_float2(v.xr, v.xi), C = make_float2(v.zi, -v.zr);
   const float2 den = make_float2(fmaf(eta0, B.x, C.x), fmaf(eta0, B.y, C.y));
   const float2 cd = cdiv_s(C, den);
   const float2 x = which == 0 ? cmul(cdiv_s(B, den), cd) : cscale(cdiv_s(cd, den), pow2i(-e));
@@ -838,7 +855,7 @@ __device__ __forceinline__ void row_guard_fold(CRow& a, int& e, float& acc, floa
     g = fmaf(-2.0f, scale2(acc, e + e_off), g);
     acc = 0.0f;
     a.a0 = cscale(a.a0, TWO_M32);
-    a.a1 = cscale(a.a1, TWO_M32);
+    a.b = cscale(a.b, TWO_M32);
     e += 32;
   }
 }
@@ -866,8 +883,8 @@ __device__ __forceinline__ void cv_fit(CV& v, int& e) {
     const float f = pow2f(-sh);
     v.xr *= f;
     v.xi *= f;
-    v.yr *= f;
-    v.yi *= f;
+    v.zr *= f;
+    v.zi *= f;
     e += sh;
   }
 }
@@ -879,7 +896,7 @@ __device__ __forceinline__ void row_fit8(CRow& a, int& e) {
     const int em = m >= 1.17549435e-38f ? exp_of(m) : -126;  // a subnormal row counts as 2^-126
     const int sh = min(em, 127) - 7;
     a.a0 = make_float2(mul_pow2(a.a0.x, -sh), mul_pow2(a.a0.y, -sh));
-    a.a1 = make_float2(mul_pow2(a.a1.x, -sh), mul_pow2(a.a1.y, -sh));
+    a.b = make_float2(mul_pow2(a.b.x, -sh), mul_pow2(a.b.y, -sh));
     e += sh;
   }
 }
@@ -942,7 +959,7 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
   // device index of traversal step j: i0 + j di
   const int i0 = front ? st.off : st.off + L - 1, di = front ? 1 : -1;
   const float eta_s = n0 * cos0, eta_p = n0 / cos0;
-  CV vs{1.0f, 0.0f, eta_s, 0.0f}, vp{1.0f, 0.0f, eta_p, 0.0f};
+  CV vs = cv_init(eta_s), vp = cv_init(eta_p);
   int es = 0, ep = 0;
   ck[nseg] = Ckpt{vs, vp, 0, 0};
   for (int sg = nseg - 1; sg >= 0; --sg) {
@@ -1017,12 +1034,12 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
       float* b = seg + u * kSegWords * 32;
       b[0 * 32] = ws.xr;
       b[1 * 32] = ws.xi;
-      b[2 * 32] = ws.yr;
-      b[3 * 32] = ws.yi;
+      b[2 * 32] = ws.zr;
+      b[3 * 32] = ws.zi;
       b[4 * 32] = wp.xr;
       b[5 * 32] = wp.xi;
-      b[6 * 32] = wp.yr;
-      b[7 * 32] = wp.yi;
+      b[6 * 32] = wp.zr;
+      b[7 * 32] = wp.zi;
       b[8 * 32] = c;
       b[9 * 32] = s;
     }
@@ -1057,18 +1074,21 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         }
         float* b = seg + u * kSegWords * 32;
         const float c = b[8 * 32], s = b[9 * 32];
-        const float gs = fmaf(k.q12s, fmaf(as.a0.x, x.yi, as.a0.y * x.yr), k.q21s * fmaf(as.a1.x, x.xi, as.a1.y * x.xr));
-        const float gp = fmaf(k.q12p, fmaf(ap.a0.x, y.yi, ap.a0.y * y.yr), k.q21p * fmaf(ap.a1.x, y.xi, ap.a1.y * y.xr));
+        // Im(a0 y) and Im(a1 x) with y = (zi, -zr), a1 = (b.y, -b.x)
+        const float gs = fmaf(k.q12s, fmaf(-as.a0.x, x.zr, as.a0.y * x.zi),
+                              k.q21s * fmaf(as.b.y, x.xi, -as.b.x * x.xr));
+        const float gp = fmaf(k.q12p, fmaf(-ap.a0.x, y.zr, ap.a0.y * y.zi),
+                              k.q21p * fmaf(ap.b.y, y.xi, -ap.b.x * y.xr));
         // the step's term goes to its (c) slot, no longer needed
         b[8 * 32] = -2.0f * k.kap * (in_range ? fmaf(gs, fs, gp * fp) : scale2(gs, xs) + scale2(gp, xp));
         if constexpr (DUAL) {
           // rho (phase term kap d g + quotient term on v_{j+1}), at this
           // segment's exponents
           const float kd = k.kap * st.d[i];
-          const float qs = fmaf(k.q21s, fmaf(as.a1.x, xn.xi, as.a1.y * xn.xr),
-                                -k.q12s * fmaf(as.a0.x, xn.yi, as.a0.y * xn.yr));
-          const float qp = fmaf(k.q12p, fmaf(ap.a0.x, yn.yi, ap.a0.y * yn.yr),
-                                -k.q21p * fmaf(ap.a1.x, yn.xi, ap.a1.y * yn.xr));
+          const float qs = fmaf(k.q21s, fmaf(as.b.y, xn.xi, -as.b.x * xn.xr),
+                                -k.q12s * fmaf(-as.a0.x, xn.zr, as.a0.y * xn.zi));
+          const float qp = fmaf(k.q12p, fmaf(-ap.a0.x, yn.zr, ap.a0.y * yn.zi),
+                                -k.q21p * fmaf(ap.b.y, yn.xi, -ap.b.x * yn.xr));
           acc_s = fmaf(rho, fmaf(kd, gs, s * qs), acc_s);
           acc_p = fmaf(rho, fmaf(kd, gp, s * qp), acc_p);
         }
@@ -1093,8 +1113,8 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
   }
   if constexpr (DUAL) {
     // a_L (0, deta0)^T: v_L = (1, eta0) at exponent 0
-    gc = fmaf(2.0f * deta_s, scale2(as.a1.x, eas - eA), gc);
-    gc = fmaf(2.0f * deta_p, scale2(ap.a1.x, eap - eA), gc);
+    gc = fmaf(2.0f * deta_s, scale2(as.b.y, eas - eA), gc);
+    gc = fmaf(2.0f * deta_p, scale2(ap.b.y, eap - eA), gc);
     *g_cos = gc;
   }
 }
