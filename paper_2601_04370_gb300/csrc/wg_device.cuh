@@ -805,8 +805,14 @@ __device__ __forceinline__ CRow coef_row(const CV& v, float eta0, int e, float2 
   return a;
 }
 
-// Words per layer of the segment buffer (s and p substrate-side vectors, c, s).
-constexpr int kSegWords = 10;
+// Words per layer of the segment buffer (s and p substrate-side vectors, c, s),
+// and the same as pairs of floats
+constexpr int kSegWords = 10, kSegPairs = kSegWords / 2;
+// a vector from two pairs of a segment-buffer column
+__device__ __forceinline__ CV seg_cv(const float2* b) {
+  const float2 x = b[0], z = b[32];
+  return CV{x.x, x.y, z.x, z.y};
+}
 // Shared-memory floats of one warp's segment buffers for material period P.
 template <int P>
 __host__ __device__ constexpr int seg_floats_per_warp() {
@@ -926,8 +932,11 @@ __device__ __forceinline__ float warp_transpose_sum8(const float (&t)[8], int la
   return r;
 }
 
-// seg: this lane's column of its warp's segment buffer (element (u, w) at
-// seg[(u * kSegWords + w) * 32]; the 32 lanes' columns interleave).
+// seg: this lane's column of its warp's segment buffer, in pairs of floats
+// (pair (u, q) of step u at seg[(u * kSegPairs + q) * 32]; the 32 lanes'
+// columns interleave, 8-byte aligned): q = 0, 1: the s vector (x, z); 2, 3:
+// the p vector; 4: (c, s) of the layer, whose c word takes the step's term
+// once it is used.
 // The sink receives each segment's gradient terms at once:
 // sink.segment(t, n, i0, di): t[u] = df/dd of layer i0 + u di (per nm), u < n.
 // Range management (exact powers of two): the first sweep keeps every
@@ -947,7 +956,7 @@ __device__ __forceinline__ float warp_transpose_sum8(const float (&t)[8], int la
 template <int P, class Sink, bool DUAL = false, bool ACC = false>
 __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, const MatTable& mt, float n0,
                                             float cos0, float2 A_s, float2 A_p, int which, Sink& sink,
-                                            float* seg, int eA = 0, const TiltTable* tt = nullptr,
+                                            float2* seg, int eA = 0, const TiltTable* tt = nullptr,
                                             float* g_cos = nullptr) {
   // (A_s, A_p) * 2^eA are the weights; eA carries the range of dL/dtally
   constexpr int CKP = Seg<P>::CKP;
@@ -1031,17 +1040,12 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         cv_step(ws, c, s * k.q12s, s * k.q21s);
         cv_step(wp, c, s * k.q12p, s * k.q21p);
       }
-      float* b = seg + u * kSegWords * 32;
-      b[0 * 32] = ws.xr;
-      b[1 * 32] = ws.xi;
-      b[2 * 32] = ws.zr;
-      b[3 * 32] = ws.zi;
-      b[4 * 32] = wp.xr;
-      b[5 * 32] = wp.xi;
-      b[6 * 32] = wp.zr;
-      b[7 * 32] = wp.zi;
-      b[8 * 32] = c;
-      b[9 * 32] = s;
+      float2* b = seg + u * kSegPairs * 32;
+      b[0 * 32] = make_float2(ws.xr, ws.xi);
+      b[1 * 32] = make_float2(ws.zr, ws.zi);
+      b[2 * 32] = make_float2(wp.xr, wp.xi);
+      b[3 * 32] = make_float2(wp.zr, wp.zi);
+      b[4 * 32] = make_float2(c, s);
     }
     // one scale factor per segment for the terms (exact; else per term)
     const int xs = eas + c1.es, xp = eap + c1.ep;
@@ -1049,16 +1053,15 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
     const float fs = in_range ? pow2f(xs) : 0.0f, fp = in_range ? pow2f(xp) : 0.0f;
     // v_j of step u (the row's products with v_{j+1} read the next slot,
     // or the checkpoint for the segment's last step)
-    CV x{seg[0], seg[32], seg[2 * 32], seg[3 * 32]};
-    CV y{seg[4 * 32], seg[5 * 32], seg[6 * 32], seg[7 * 32]};
+    CV x = seg_cv(seg), y = seg_cv(seg + 2 * 32);
 #pragma unroll
     for (int u = 0; u < CKP; ++u) {
       const int j = j0 + u;
       CV xn = c1.s, yn = c1.p;
       if (u + 1 < CKP) {
-        const float* bn = seg + (u + 1) * kSegWords * 32;
-        xn = CV{bn[0 * 32], bn[1 * 32], bn[2 * 32], bn[3 * 32]};
-        yn = CV{bn[4 * 32], bn[5 * 32], bn[6 * 32], bn[7 * 32]};
+        const float2* bn = seg + (u + 1) * kSegPairs * 32;
+        xn = seg_cv(bn);
+        yn = seg_cv(bn + 2 * 32);
       }
       if (j < L) {
         MatK k;
@@ -1072,15 +1075,17 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
           k = mt.get(m);
           if constexpr (DUAL) rho = tt->get(m);
         }
-        float* b = seg + u * kSegWords * 32;
-        const float c = b[8 * 32], s = b[9 * 32];
+        float2* b = seg + u * kSegPairs * 32;
+        const float2 cs = b[4 * 32];
+        const float c = cs.x, s = cs.y;
         // Im(a0 y) and Im(a1 x) with y = (zi, -zr), a1 = (b.y, -b.x)
         const float gs = fmaf(k.q12s, fmaf(-as.a0.x, x.zr, as.a0.y * x.zi),
                               k.q21s * fmaf(as.b.y, x.xi, -as.b.x * x.xr));
         const float gp = fmaf(k.q12p, fmaf(-ap.a0.x, y.zr, ap.a0.y * y.zi),
                               k.q21p * fmaf(ap.b.y, y.xi, -ap.b.x * y.xr));
         // the step's term goes to its (c) slot, no longer needed
-        b[8 * 32] = -2.0f * k.kap * (in_range ? fmaf(gs, fs, gp * fp) : scale2(gs, xs) + scale2(gp, xp));
+        reinterpret_cast<float*>(b + 4 * 32)[0] =
+            -2.0f * k.kap * (in_range ? fmaf(gs, fs, gp * fp) : scale2(gs, xs) + scale2(gp, xp));
         if constexpr (DUAL) {
           // rho (phase term kap d g + quotient term on v_{j+1}), at this
           // segment's exponents
@@ -1101,7 +1106,7 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
     {
       float t[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) t[u] = u < CKP ? seg[(u * kSegWords + 8) * 32] : 0.0f;
+      for (int u = 0; u < 8; ++u) t[u] = u < CKP ? seg[(u * kSegPairs + 4) * 32].x : 0.0f;
       sink.segment(t, min(CKP, L - j0), i0 + j0 * di, di);
     }
     if constexpr (DUAL) {

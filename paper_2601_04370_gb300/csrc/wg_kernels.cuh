@@ -1657,7 +1657,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_adjoint(const AdjArgs A) {
   __shared__ unsigned long long s_cnt[2];
   float* s_grad = reinterpret_cast<float*>(smem + A.blob_bytes);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  float* seg = s_grad + ((max(1, A.n_layers) + 31) & ~31) + warp * seg_floats_per_warp<P>() + lane;
+  // (8-byte aligned: the blob's size is a multiple of 16 bytes, the other offsets even)
+  float2* seg = reinterpret_cast<float2*>(s_grad + ((max(1, A.n_layers) + 31) & ~31) + warp * seg_floats_per_warp<P>()) +
+                lane;
   if (tid < 2) s_cnt[tid] = 0ull;
   if (!stage_blob(smem, A.blob, A.blob_bytes, &s_mbar, A.error, wait_limit(A.wait_ns))) return;
   Blob B;
@@ -1803,8 +1805,8 @@ template <int P, bool ACC>
 __global__ void __launch_bounds__(128) k_coating_grad(const uint8_t* blob, int mirror, int side, long long n,
                                                        const float* cos0, const float* lam, const float* w, int which,
                                                        float* grad) {
-  __shared__ float s_seg[4 * seg_floats_per_warp<P>()];
-  float* seg = s_seg + (threadIdx.x >> 5) * seg_floats_per_warp<P>() + (threadIdx.x & 31);
+  __shared__ __align__(16) float s_seg[4 * seg_floats_per_warp<P>()];
+  float2* seg = reinterpret_cast<float2*>(s_seg + (threadIdx.x >> 5) * seg_floats_per_warp<P>()) + (threadIdx.x & 31);
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   Blob B;
@@ -1828,8 +1830,8 @@ template <int P, bool ACC>
 __global__ void __launch_bounds__(128) k_coating_dcos(const uint8_t* blob, int mirror, int side, long long n,
                                                        const float* cos0, const float* lam, const float* w, int which,
                                                        float* out) {
-  __shared__ float s_seg[4 * seg_floats_per_warp<P>()];
-  float* seg = s_seg + (threadIdx.x >> 5) * seg_floats_per_warp<P>() + (threadIdx.x & 31);
+  __shared__ __align__(16) float s_seg[4 * seg_floats_per_warp<P>()];
+  float2* seg = reinterpret_cast<float2*>(s_seg + (threadIdx.x >> 5) * seg_floats_per_warp<P>()) + (threadIdx.x & 31);
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= n) return;
   Blob B;
