@@ -944,7 +944,7 @@ __device__ __forceinline__ float warp_transpose_sum8(const float (&t)[8], int la
 // segment start; a segment grows either by less than 2^31, so a . v (< 2^78)
 // stays far below the FP32 range inside the segment, and each segment's
 // terms take one scale factor 2^(e_row + e_v) (computed once; out of the
-// normal range the terms are scaled one by one).
+// normal range a common part is applied to the terms after the segment).
 // DUAL: *g_cos also receives df/d(cos t0) of the record through its coating,
 // without 2^eA, from the same reverse sweep (reverse-mode, no derivative
 // chain): with v_j = M_j v_{j+1} (substrate side) and the row a_j,
@@ -1047,10 +1047,22 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
       b[3 * 32] = make_float2(wp.zr, wp.zi);
       b[4 * 32] = make_float2(c, s);
     }
-    // one scale factor per segment for the terms (exact; else per term)
+    // the segment's scale factors of the terms, 2^xs (s) and 2^xp (p), exact
+    // powers of two. When either lies outside the normal range the loop
+    // applies 2^(xs - xr) and 2^(xp - xr) instead, with xr the larger
+    // exponent of the non-zero rows (a row is in [2^7, 2^8) at the segment
+    // start unless it is zero, when its exponent means nothing), the other
+    // factor clamped to the normal range (a term more than 2^126 below its
+    // partner's scale, or a zero row's), and the terms take 2^xr when they
+    // are read out: the loop itself never branches on the range
     const int xs = eas + c1.es, xp = eap + c1.ep;
     const bool in_range = xs >= -126 && xs <= 127 && xp >= -126 && xp <= 127;
-    const float fs = in_range ? pow2f(xs) : 0.0f, fp = in_range ? pow2f(xp) : 0.0f;
+    int xr = 0;
+    if (!in_range) {
+      const bool ns = row_maxabs(as) > 0.0f, np = row_maxabs(ap) > 0.0f;
+      xr = ns ? (np ? max(xs, xp) : xs) : (np ? xp : 0);
+    }
+    const float fs = pow2f(min(max(xs - xr, -126), 127)), fp = pow2f(min(max(xp - xr, -126), 127));
     // v_j of step u (the row's products with v_{j+1} read the next slot,
     // or the checkpoint for the segment's last step)
     CV x = seg_cv(seg), y = seg_cv(seg + 2 * 32);
@@ -1084,8 +1096,7 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         const float gp = fmaf(k.q12p, fmaf(-ap.a0.x, y.zr, ap.a0.y * y.zi),
                               k.q21p * fmaf(ap.b.y, y.xi, -ap.b.x * y.xr));
         // the step's term goes to its (c) slot, no longer needed
-        reinterpret_cast<float*>(b + 4 * 32)[0] =
-            -2.0f * k.kap * (in_range ? fmaf(gs, fs, gp * fp) : scale2(gs, xs) + scale2(gp, xp));
+        reinterpret_cast<float*>(b + 4 * 32)[0] = -2.0f * k.kap * fmaf(gs, fs, gp * fp);
         if constexpr (DUAL) {
           // rho (phase term kap d g + quotient term on v_{j+1}), at this
           // segment's exponents
@@ -1107,6 +1118,11 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
       float t[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) t[u] = u < CKP ? seg[(u * kSegPairs + 4) * 32].x : 0.0f;
+      if (xr != 0) {
+        const int k = min(max(xr, -252), 254);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = mul_pow2(t[u], k);
+      }
       sink.segment(t, min(CKP, L - j0), i0 + j0 * di, di);
     }
     if constexpr (DUAL) {

@@ -363,6 +363,35 @@ def test_backward_3d_matches_oracle_adjoint(ctx, ora, L):
     dh.destroy()
 
 
+@pytest.mark.parametrize("k", [100, -60])
+def test_backward_is_linear_across_the_exponent_range(ctx, k):
+    """The backward is linear in dL/dtally: scaling it by 2^k scales the
+    thickness and tilt gradients by 2^k. The exponent of dL/dtally travels
+    beside the FP32 weights of the hit records, and k = 100 puts the scale
+    factors of many of the adjoint's layer segments outside the FP32
+    normal range (the path where the terms take a common power of two
+    after the segment); k = -60 moves them down. Both sides sum FP32
+    partials per chunk in a different order (2^-24 per term)."""
+    D, C = W.representative(n_rays=1728 * 4)
+    dh = ctx.create_design(D)
+    tally = torch.zeros(C.tally_shape, dtype=torch.float64, device="cuda")
+    ctx.trace_forward(dh, C, tally)
+    rng = np.random.default_rng(8)
+    G0 = rng.normal(size=C.tally_shape)
+    out = []
+    for scale in (1.0, 2.0 ** k):
+        g = torch.zeros(D.total_layers, dtype=torch.float64, device="cuda")
+        gt = np.zeros(len(D.mirror_x_mm))
+        st = ctx.trace_backward(dh, C, _dev(G0 * scale, torch.float64), g, grad_tilt=gt)
+        assert st["overflow"] == 0 and st["n_nonfinite"] == 0
+        out.append((g.cpu().numpy() / scale, gt / scale))
+    (a, at), (b, bt) = out
+    assert np.abs(a).max() > 0 and np.abs(at).max() > 0
+    assert np.abs(a - b).max() <= 1e-5 * np.abs(a).max(), np.abs(a - b).max() / np.abs(a).max()
+    assert np.abs(at - bt).max() <= 1e-5 * np.abs(at).max(), np.abs(at - bt).max() / np.abs(at).max()
+    dh.destroy()
+
+
 @pytest.mark.parametrize("cfg", ["rep", "tiny"])
 def test_tilt_gradient_matches_oracle_adjoint(ctx, ora, cfg):
     """dL/d(tilt) per degree along the fixed sampled paths (forward-mode
