@@ -510,6 +510,28 @@ __device__ __forceinline__ void stack_slots(const StackView& st, bool front, con
   }
 }
 
+// Traversal step j of a stack (device index i0 + j di), or past the stack's
+// end (j >= L) an identity step: thickness 0 and (c, s) = (1, 0), exactly
+// the identity matrix. Loops over whole segments then take no branch on the
+// stack length (a branch per unrolled step costs more than the identity
+// steps of a stack's last segment). The material of a periodic stack's step
+// comes from its register slot; a general stack reads it (index clamped).
+template <int P, bool ACC>
+__device__ __forceinline__ void layer_at(const StackView& st, const MatTable& mt, const MatK* kb, int i0, int di,
+                                         int j, int u, MatK& k, float& d, float& c, float& s) {
+  const bool in = j < st.L;
+  const int i = i0 + min(j, st.L - 1) * di;
+  if constexpr (P > 0) {
+    k = kb[u % P];
+  } else {
+    k = mt.get(st.m[i]);
+  }
+  d = in ? st.d[i] : 0.0f;
+  layer_cs<ACC>(k, d, c, s);
+  c = in ? c : 1.0f;
+  s = in ? s : 0.0f;
+}
+
 // Effective coefficients in the paper's convention (r_p = -r_p(Abeles)).
 template <int P, bool ACC = false>
 __device__ __forceinline__ Coef tmm_forward(const StackView& st, bool front, const MatTable& mt, float n0,
@@ -521,23 +543,15 @@ __device__ __forceinline__ Coef tmm_forward(const StackView& st, bool front, con
   CV vs = cv_init(eta_s), vp = cv_init(eta_p);
   int es = 0, ep = 0;
   const int L = st.L;
+  const int i0 = front ? st.off : st.off + L - 1, di = front ? 1 : -1;
   for (int j0 = L > 0 ? ((L - 1) / CKP) * CKP : -1; j0 >= 0; j0 -= CKP) {
 #pragma unroll
     for (int u = CKP - 1; u >= 0; --u) {
-      const int j = j0 + u;
-      if (j < L) {
-        const int i = st.idx(front, j);
-        MatK k;
-        if constexpr (P > 0) {
-          k = kb[u % P];
-        } else {
-          k = mt.get(st.m[i]);
-        }
-        float c, s;
-        layer_cs<ACC>(k, st.d[i], c, s);
-        cv_step(vs, c, s * k.q12s, s * k.q21s);
-        cv_step(vp, c, s * k.q12p, s * k.q21p);
-      }
+      MatK k;
+      float d, c, s;
+      layer_at<P, ACC>(st, mt, kb, i0, di, j0 + u, u, k, d, c, s);
+      cv_step(vs, c, s * k.q12s, s * k.q21s);
+      cv_step(vp, c, s * k.q12p, s * k.q21p);
     }
     cv_rescale(vs, es);
     cv_rescale(vp, ep);
@@ -975,20 +989,11 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
     const int j0 = sg * CKP;
 #pragma unroll
     for (int u = CKP - 1; u >= 0; --u) {
-      const int j = j0 + u;
-      if (j < L) {
-        const int i = i0 + j * di;
-        MatK k;
-        if constexpr (P > 0) {
-          k = kb[u % P];
-        } else {
-          k = mt.get(st.m[i]);
-        }
-        float c, s;
-        layer_cs<ACC>(k, st.d[i], c, s);
-        cv_step(vs, c, s * k.q12s, s * k.q21s);
-        cv_step(vp, c, s * k.q12p, s * k.q21p);
-      }
+      MatK k;
+      float d, c, s;
+      layer_at<P, ACC>(st, mt, kb, i0, di, j0 + u, u, k, d, c, s);
+      cv_step(vs, c, s * k.q12s, s * k.q21s);
+      cv_step(vp, c, s * k.q12p, s * k.q21p);
     }
     cv_fit(vs, es);
     cv_fit(vp, ep);
@@ -1026,20 +1031,11 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
     // (slots past the stack's end hold the checkpoint itself, v_L)
 #pragma unroll
     for (int u = CKP - 1; u >= 0; --u) {
-      const int j = j0 + u;
-      float c = 1.0f, s = 0.0f;
-      if (j < L) {
-        const int i = i0 + j * di;
-        MatK k;
-        if constexpr (P > 0) {
-          k = kb[u % P];
-        } else {
-          k = mt.get(st.m[i]);
-        }
-        layer_cs<ACC>(k, st.d[i], c, s);
-        cv_step(ws, c, s * k.q12s, s * k.q21s);
-        cv_step(wp, c, s * k.q12p, s * k.q21p);
-      }
+      MatK k;
+      float d, c, s;
+      layer_at<P, ACC>(st, mt, kb, i0, di, j0 + u, u, k, d, c, s);
+      cv_step(ws, c, s * k.q12s, s * k.q21s);
+      cv_step(wp, c, s * k.q12p, s * k.q21p);
       float2* b = seg + u * kSegPairs * 32;
       b[0 * 32] = make_float2(ws.xr, ws.xi);
       b[1 * 32] = make_float2(ws.zr, ws.zi);
@@ -1075,10 +1071,13 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         xn = seg_cv(bn);
         yn = seg_cv(bn + 2 * 32);
       }
-      if (j < L) {
+      {
+        // past the stack's end an identity step (the buffer holds c = 1,
+        // s = 0 there, the thickness is taken as 0): its term is not read,
+        // the row and the tilt sums do not change
         MatK k;
         float rho = 0.0f;
-        const int i = i0 + j * di;
+        const int i = i0 + min(j, L - 1) * di;
         if constexpr (P > 0) {
           k = kb[u % P];
           if constexpr (DUAL) rho = rb[u % P];
@@ -1100,7 +1099,7 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         if constexpr (DUAL) {
           // rho (phase term kap d g + quotient term on v_{j+1}), at this
           // segment's exponents
-          const float kd = k.kap * st.d[i];
+          const float kd = k.kap * (j < L ? st.d[i] : 0.0f);
           const float qs = fmaf(k.q21s, fmaf(as.b.y, xn.xi, -as.b.x * xn.xr),
                                 -k.q12s * fmaf(-as.a0.x, xn.zr, as.a0.y * xn.zi));
           const float qp = fmaf(k.q12p, fmaf(-ap.a0.x, yn.zr, ap.a0.y * yn.zi),
