@@ -756,42 +756,8 @@ __device__ __forceinline__ void row_step(CRow& a, float c, float m12, float m21)
   a.a0 = a0;
   a.b = b;
 }
-// The adjoint keeps both factors of its products a_j . v_j within 2^32 (a:
-// checked every layer; v: checkpoints <= 2^32, and a segment of CK layers
-// grows v by < 2^31), so a . v stays far below the FP32 range whatever the
-// scale factor 2^(e_a + e_v) applied afterwards.
-constexpr float TWO_P32 = 4294967296.0f;
-constexpr float TWO_M32 = 2.3283064365386963e-10f;
 __device__ __forceinline__ float row_maxabs(const CRow& a) {
   return fmaxf(fmaxf(fabsf(a.a0.x), fabsf(a.a0.y)), fmaxf(fabsf(a.b.y), fabsf(a.b.x)));
-}
-__device__ __forceinline__ void row_guard(CRow& a, int& e) {
-  if (row_maxabs(a) > TWO_P32) {
-    a.a0 = cscale(a.a0, TWO_M32);
-    a.b = cscale(a.b, TWO_M32);
-    e += 32;
-  }
-}
-__device__ __forceinline__ void row_renorm(CRow& a, int& e) {
-  const float m = row_maxabs(a);
-  if (m > TWO_P32) {
-    a.a0 = cscale(a.a0, TWO_M32);
-    a.b = cscale(a.b, TWO_M32);
-    e += 32;
-  } else if (m < TWO_M32 && m > 0.0f) {
-    a.a0 = cscale(a.a0, TWO_P32);
-    a.b = cscale(a.b, TWO_P32);
-    e -= 32;
-  }
-}
-__device__ __forceinline__ void cv_rescale32(CV& v, int& e) {
-  if (cv_maxabs(v) > TWO_P32) {
-    v.xr *= TWO_M32;
-    v.xi *= TWO_M32;
-    v.zr *= TWO_M32;
-    v.zi *= TWO_M32;
-    e += 32;
-  }
 }
 
 // rho for one polarization (scaled v, exponent e): returns the row and its exponent
@@ -869,16 +835,6 @@ __device__ __forceinline__ float coef_deta(const CV& v, float eta0, int e, float
   return 4.0f * fmaf(A.x, x.x, -A.y * x.y);
 }
 
-// the row's guard, first folding the tilt partial sum kept at its exponent
-__device__ __forceinline__ void row_guard_fold(CRow& a, int& e, float& acc, float& g, int e_off) {
-  if (row_maxabs(a) > TWO_P32) {
-    g = fmaf(-2.0f, scale2(acc, e + e_off), g);
-    acc = 0.0f;
-    a.a0 = cscale(a.a0, TWO_M32);
-    a.b = cscale(a.b, TWO_M32);
-    e += 32;
-  }
-}
 
 // Exact power-of-two scaling for the adjoint's range management.
 // floor(log2 m) of a normal positive float
