@@ -31,7 +31,7 @@ struct RayHead {
   int cell;
   int first;
   int emit;
-  int pad;
+  int events;  // surface events of the replayed path (the tangent pass groups its rays by it)
 };
 
 // Arguments of the trace kernels (passed by value).

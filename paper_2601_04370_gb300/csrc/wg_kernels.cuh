@@ -1183,7 +1183,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                   rh.cell = (int)cell_l;
                   rh.first = (int)f0;
                   rh.emit = emit;
-                  rh.pad = 0;
+                  rh.events = R.ev;
                   A.ray_heads[hi] = rh;
                 }
               }
