@@ -61,9 +61,10 @@ def src_hash():
     their argument layout)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2601_04370_gb300", "csrc")
-    for f in ("wg_device.cuh", "wg_internal.h", "wg_trace.cu"):
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(fh.read())
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
@@ -377,6 +378,8 @@ def bench_differentiation(ctx, dev, args, pg, ws, rank, flush, stream, pk, pk_ki
     f_adj = FLOPS_ADJ_LAYER_TILT * adj_steps / max(1, n_adj)
     ach_a = f_adj / (adj_ms / max(1, n_adj) / 1e3) / 1e12 if adj_ms > 0 else 0.0
     peak_source = f"derived: {sm} SMs x 128 FP32 lanes x 2 flop x {float(pk.get('sm_max_mhz', 2070.0)):.0f} MHz ({pk_kind})"
+    step_ms = 1e3 * t / len(ms)
+    adj_step_ms = adj_ms / max(1, len(adj))
     out = {"workload": "differentiation fwd+loss+adjoint: as representative with 6 mirrors x 200 layers (1200 "
                        "thicknesses) + 6 tilts, 1e8 rays per GPU, accurate layer evaluation",
            "value": allsum(pg, hits * len(ms), dev) / t, "unit": UNIT, "steps": len(ms), "warmup": 1,
@@ -388,9 +391,11 @@ def bench_differentiation(ctx, dev, args, pg, ws, rank, flush, stream, pk, pk_ki
                         "peak": peak, "unit": "TFLOP/s", "frac": ach_a / peak, "traffic": None,
                         "flops_per_launch": f_adj, "launch_ms": adj_ms / max(1, n_adj), "launches": n_adj,
                         "units": f"{adj_steps / max(1, n_adj):.4g} record layer steps per launch x "
-                                 f"{FLOPS_ADJ_LAYER_TILT} flops", "peak_source": peak_source},
+                                 f"{FLOPS_ADJ_LAYER_TILT} flops", "peak_source": peak_source,
+                        "ms_per_step": adj_step_ms, "share_of_step": adj_step_ms / step_ms},
            "roofline_fwd": {"bound": "alu", "kernel": "k_trace_fwd (accurate mode)", "achieved": ach_f, "peak": peak,
                             "unit": "TFLOP/s", "frac": ach_f / peak, "flops_per_launch": f_fwd,
+                            "ms_per_step": statistics.mean(fm), "share_of_step": statistics.mean(fm) / step_ms,
                             "units": f"{hits} interactions x ({FLOPS_PER_LAYER} x "
                                      f"{st_f['n_layer_steps'] / max(1, hits):.1f} layers + {FLOPS_PER_HIT}) flops",
                             "peak_source": peak_source}}
@@ -728,8 +733,7 @@ def run_ours(args):
         ach_f = flops_fwd / fwd_s / 1e12
         peak_source = (f"derived: {sm} SMs x 128 FP32 lanes x 2 flop x {smax:.0f} MHz "
                        f"(sm_max_mhz of {pk_kind} peaks)")
-        # the dominant kernel of the step (largest share of the launch list) is
-        # the thin-film adjoint (tilt variant); its launches are timed by the
+        # the thin-film adjoint (tilt variant): its launches are timed by the
         # library with CUDA events on the launching stream during the timed
         # steps (wg_stats adjoint_ms / n_adjoint_launches)
         n_adj = sum(s["n_adjoint_launches"] for s in adj)
@@ -753,6 +757,16 @@ def run_ours(args):
                   "peak_source": peak_source}
         roof_b = {"bound": "alu", "kernels": "k_bwd_replay + sort + k_bwd_adjoint (tilt pass excluded)", "achieved": ach_b,
                   "peak": peak, "unit": "TFLOP/s", "frac": ach_b / peak, "flops_per_call": flops_bwd}
+        # "roofline" is the dominant kernel of the step: the one with the
+        # larger device time per step (the launch list's largest share)
+        step_ms_mean = 1e3 * t_max / args.steps
+        fwd_step_ms = fwd_s * 1e3
+        adj_step_ms = adj_ms / max(1, len(adj))
+        roof_f["ms_per_step"] = fwd_step_ms
+        roof_f["share_of_step"] = fwd_step_ms / step_ms_mean
+        roof["ms_per_step"] = adj_step_ms
+        roof["share_of_step"] = adj_step_ms / step_ms_mean
+        roof_dom = roof_f if fwd_step_ms >= adj_step_ms else roof
         cpu = None
         if ws == 1 and not args.no_cpu_baseline:
             cpu, _, _, _ = cpu_oracle_rate(D, C, G.cpu().numpy(), budget_s=args.cpu_budget)
@@ -764,7 +778,8 @@ def run_ours(args):
                           "parallelism": f"replicas x{ws} (rays sharded by seed, no collective)"},
                "fwd_interactions_per_s": fwd_rate, "fwd_ms": statistics.mean(fwd_ms),
                "bwd_ms": statistics.mean(bwd_ms), "tilt_pass_ms": tilt_ms, "loss": loss[0], "wall_s": t_wall,
-               "roofline": roof, "roofline_fwd": roof_f, "roofline_bwd": roof_b, "cpu_baseline": cpu,
+               "roofline": roof_dom, "roofline_fwd": roof_f, "roofline_adjoint": roof, "roofline_bwd": roof_b,
+               "cpu_baseline": cpu,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": launches, "clocks": ck, "coating_table": coating_table,
                "pupil_expander": expander, "differentiation": differentiation, "batching": batching,
