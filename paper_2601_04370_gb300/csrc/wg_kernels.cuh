@@ -437,9 +437,9 @@ __device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v) {
 // CTA-wide sequence that runs over the chunks (one cell, a range of rays)
 // the CTA has bound to its tally slots (A.n_slots <= kSlots). A warp advances its rays
 // through face events until every live ray sits on a mirror, then runs the
-// per-hit transfer-matrix chain together. Exits are aggregated per warp
-// (lanes with the same slot and bin) into the slot's FP32 shared tally; the
-// warp that finishes a chunk's last ray flushes the slot to the FP64 global
+// per-hit transfer-matrix chain together. Exits are added into the slot's
+// FP32 shared tally; the lane whose ray completes a chunk has its warp flush
+// the slot to the FP64 global
 // tally and frees it for the CTA's next chunk. No CTA barrier separates
 // chunks, so lanes never idle at a chunk's tail while rays remain.
 // ---------------------------------------------------------------------------
@@ -585,13 +585,11 @@ __device__ __forceinline__ void ring_finish(FwdRing& S, bool fin, int slot, floa
   if (!__any_sync(FULL, fin)) return;
   __threadfence_block();
   __syncwarp();  // every lane's tally adds ordered before the counts below
-  const int key = fin ? slot : -1 - lane;
-  const unsigned peers = __match_any_sync(FULL, key);
+  // one count per finished ray: the lane whose count completes the chunk flushes it
   bool complete = false;
-  if (fin && lane == __ffs(peers) - 1) {
-    const unsigned c = __popc(peers);
-    const unsigned old = atomicAdd(&S.slot[slot].done, c);
-    complete = old + c == (unsigned)(vload(S.slot[slot].range) & ((1ull << kSizeBits) - 1ull));
+  if (fin) {
+    const unsigned old = atomicAdd(&S.slot[slot].done, 1u);
+    complete = old + 1u == (unsigned)(vload(S.slot[slot].range) & ((1ull << kSizeBits) - 1ull));
   }
   unsigned cm = __ballot_sync(FULL, complete);
   while (cm) {
@@ -848,16 +846,12 @@ __global__ void __launch_bounds__(kBlock, 2)
       const unsigned pmask = __ballot_sync(FULL, to_mir);
       if (to_mir) q_put<F, ACC>(mq, (mt + __popc(pmask & lt_mask)) % kQCap, R, A.ray_begin, slot);
       mt += __popc(pmask);
-      // per-warp aggregation of exits into the slot tallies
+      // exits into the slot tallies: a few lanes per pass over thousands of
+      // bins rarely meet, so each adds its own (a warp-level aggregation by
+      // bin cost more than the collisions it saved)
       const unsigned pm = __ballot_sync(FULL, pend_bin >= 0);
       if (pm) {
-        const int key = pend_bin >= 0 ? slot * A.bins + pend_bin : -1 - lane;
-        const unsigned peers = __match_any_sync(FULL, key);
-        if (pend_bin >= 0) {
-          float sum = 0.f;
-          for (unsigned mm = peers; mm; mm &= mm - 1) sum += __shfl_sync(peers, pend_I, __ffs(mm) - 1);
-          if (lane == __ffs(peers) - 1) atomicAdd(&s_tally[key], sum);
-        }
+        if (pend_bin >= 0) atomicAdd(&s_tally[slot * A.bins + pend_bin], pend_I);
         // list of eyebox rays for the adjoint: slots from the warp's reserved
         // chunk, a new chunk of kExitChunk when it runs out
         if (A.exit_list) {
