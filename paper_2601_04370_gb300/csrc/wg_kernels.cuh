@@ -825,7 +825,10 @@ __global__ void __launch_bounds__(kBlock, 2)
             led[L_MISSED] += o.I;
             led[L_EXIT_REFL] += o.w - o.I;
           } else {
-            led[o.cat] += o.w;
+            // (a static index per category keeps the ledger in registers)
+#pragma unroll
+            for (int c = 0; c < 6; ++c)
+              if (c == o.cat) led[c] += o.w;
           }
           if (recs) {
             RayRec rr;
