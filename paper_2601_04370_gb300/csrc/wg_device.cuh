@@ -290,9 +290,10 @@ __device__ __forceinline__ MatK mat_const_acc(F2 sin2, float n, float inv_n, F2 
 
 struct MatTable {
   MatK k[MAX_MAT];
-  __device__ __forceinline__ void init(const BlobHeader& h, float cos0, float lam) {
+  __device__ __forceinline__ void init(const BlobHeader& h, float cos0, float lam) { init_inv(h, cos0, 1.0f / lam); }
+  // the same with 1/lambda given (computed once per cell by the trace kernels)
+  __device__ __forceinline__ void init_inv(const BlobHeader& h, float cos0, float inv_lam) {
     const float sin2 = fmaf(-cos0, cos0, 1.0f);
-    const float inv_lam = 1.0f / lam;
 #pragma unroll
     for (int i = 0; i < MAX_MAT; ++i)
       if (i < h.n_mat) k[i] = mat_const(sin2, h.mat_n[i], h.mat_inv_n[i], h.mat_r2[i], inv_lam);

@@ -129,7 +129,8 @@ struct ChunkConst {
   V3 fd;                  // guided launch direction
   V3 fdl;                 // its low parts (accurate mode)
   float a1, b1, a2, b2;   // e1, e2 in the face basis of fd
-  float lam;
+  float lam, inv_lam;     // the cell's wavelength and 1/lambda
+  int li;                 // its wavelength index
   long long cell;
 };
 
@@ -283,13 +284,14 @@ __device__ __forceinline__ float2 lerp2(float2 a, float2 b, float f) {
   return make_float2(fmaf(f, b.x - a.x, a.x), fmaf(f, b.y - a.y, a.y));
 }
 
-// li: wavelength index of the hit (the coating table's, when A.lut is set)
+// lam, inv_lam, li: the hit's wavelength, 1/lambda and wavelength index (the
+// coating table's, when A.lut is set), computed once per cell
 // CM: 1 in the forward (may keep the applied coefficients, TraceArgs::coef),
 // 2 in the replay (may read them back); the other direction is compiled out.
 // ACC: accurate mode (direction and incidence cosine as hi + lo, the
 // accurate layer evaluation), for long stacks.
 template <int F, int P, int CM, bool ACC>
-__device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob& B, float lam, int li,
+__device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob& B, float lam, float inv_lam, int li,
                                                    const TraceArgs& A, int& layer_steps, float2* Es_out,
                                                    float2* Ep_out) {
   const BlobHeader& H = *B.h;
@@ -321,7 +323,11 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
     cf.tp = lerp2(make_float2(a1.z, a1.w), make_float2(b1.z, b1.w), f);
   } else {
     MatTable mt;
-    mt.init_sel<ACC>(H, st.cos0, st.cos0l, lam);
+    if constexpr (ACC) {
+      mt.init_acc(H, st.cos0, st.cos0l, lam);
+    } else {
+      mt.init_inv(H, st.cos0, inv_lam);
+    }
     const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
     cf = tmm_forward<P, ACC>(sv, st.front, mt, H.n_slab, st.cos0, layer_steps);
   }
@@ -396,6 +402,8 @@ __device__ __forceinline__ ChunkConst chunk_const(const TraceArgs& A, long long 
   cc.cell = cell;
   const int li = (int)(cell / A.n_f), f = (int)(cell % A.n_f);
   cc.lam = __ldg(A.lambda + li);
+  cc.inv_lam = 1.0f / cc.lam;
+  cc.li = li;
   const FieldRec fr = A.fields[f];
   cc.fd = v3(fr.dx, fr.dy, fr.dz);
   cc.fdl = v3(fr.dlx, fr.dly, fr.dlz);
@@ -898,7 +906,8 @@ __global__ void __launch_bounds__(kBlock, 2)
       bool fin = false, keep = false;
       if ((unsigned)lane < n) {
         slot = q_get<F, ACC>(mq, (mh + lane) % kQCap, R, A.ray_begin);
-        mirror_event<F, P, 1, ACC>(R, R.last - S_MIR, B, S.slot[slot].cc.lam, (int)(S.slot[slot].cc.cell / A.n_f), A, c_steps,
+        const ChunkConst& scc = S.slot[slot].cc;
+        mirror_event<F, P, 1, ACC>(R, R.last - S_MIR, B, scc.lam, scc.inv_lam, scc.li, A, c_steps,
                            nullptr, nullptr);
         if (R.ev >= A.max_events) {
           fin = true;
@@ -1046,11 +1055,14 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
   bool u_more = true;
   ChunkConst ucc;
   ucc.lam = 0.f;
+  ucc.inv_lam = 0.f;
+  ucc.li = 0;
   Ray<F> R;
   bool has = false, at_mir = false;
   int hit_k = 0;
   long long cell_l = 0;  // cell and wavelength of this lane's ray
-  float lam_l = 0.f;
+  float lam_l = 0.f, inv_lam_l = 0.f;
+  int li_l = 0;
   float2 seg_s = make_float2(1.f, 0.f), seg_p = make_float2(1.f, 0.f);
   for (;;) {
         for (;;) {
@@ -1089,12 +1101,16 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                   const ChunkConst cc = chunk_const(A, cell_l);
                   gen_ray(R, e.id, cc, H, A);
                   lam_l = cc.lam;
+                  inv_lam_l = cc.inv_lam;
+                  li_l = cc.li;
                   has = true;
                 }
               } else {
                 gen_ray(R, u_next + rank, ucc, H, A);
                 cell_l = u_cell;
                 lam_l = ucc.lam;
+                inv_lam_l = ucc.inv_lam;
+                li_l = ucc.li;
                 has = true;
               }
               if (has) {
@@ -1222,7 +1238,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                     float f;
                     lut_locate(A, E.cos0, j, f);
                     const bool front = (E.kfw >> 8) & 1;
-                    const long long e = lut_entry(A, k, front, (int)(cell_l / A.n_f), j);
+                    const long long e = lut_entry(A, k, front, li_l, j);
                     // FP32 relative to the ray's exponent of dL/dtally; one exact
                     // power of two turns each value into FP64 for the sums
                     const double p2 = pow2d(eG);
@@ -1248,7 +1264,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                     }
                   } else {
                     HitRec rec;
-                    rec.kfw = E.kfw | ((int)(cell_l / A.n_f) << 10);
+                    rec.kfw = E.kfw | (li_l << 10);
                     rec.cos0 = E.cos0;
                     rec.cos0l = E.cos0l();
                     rec.eA = eG;
@@ -1280,7 +1296,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
         if (at_mir) {
           const int h = R.hits;
           float2 Es[F], Ep[F];
-          const MirrorStep ms = mirror_event<F, P, 2, ACC>(R, hit_k, B, lam_l, (int)(cell_l / A.n_f), A, c_steps, Es, Ep);
+          const MirrorStep ms = mirror_event<F, P, 2, ACC>(R, hit_k, B, lam_l, inv_lam_l, li_l, A, c_steps, Es, Ep);
           if (h < TAPE_HITS) {
             TapeE<F, ACC>& E = tape[h];
             E.cs = ms.cs;
