@@ -139,8 +139,12 @@ constexpr int kStackKeys = 128, kClsPerStack = 8, kSortKeys = kStackKeys * kClsP
 constexpr int kFwdSlots = 3;
 inline int fwd_slots(long long chunk_rays) { return chunk_rays >= 1536 ? 2 : 3; }
 // rays a warp of the forward kernel owns at a time (its lanes plus its two
-// shared-memory queues); a queued ray takes 9 + 4 F words (+ 3 in accurate mode)
+// shared-memory queues), and the slots of each queue's ring (a power of two,
+// so that a ring index is a mask; at least kFwdQCap); a queued ray takes
+// 9 + 4 F words (+ 3 in accurate mode)
 constexpr int kFwdQCap = 48;
+constexpr int kFwdQRing = 64;
+static_assert(kFwdQRing >= kFwdQCap && (kFwdQRing & (kFwdQRing - 1)) == 0, "queue ring");
 // a warp of the forward kernel reserves eyebox-ray list slots this many at a
 // time (one global atomic per chunk); slots it leaves unused are holes
 // (flat = -1). The list holds at most rays + 64 warps per SM x one chunk.
@@ -150,7 +154,7 @@ inline long long exit_list_cap(long long rays, int sm_count) {
 }
 inline size_t fwd_smem_bytes(int blob_bytes, long long bins, int F, int n_slots, bool acc) {
   return (size_t)blob_bytes + sizeof(float) * (size_t)n_slots * (size_t)bins +
-         sizeof(uint32_t) * (size_t)(kBlock / 32) * 2 * (size_t)kFwdQCap * (size_t)(9 + 4 * F + (acc ? 3 : 0));
+         sizeof(uint32_t) * (size_t)(kBlock / 32) * 2 * (size_t)kFwdQRing * (size_t)(9 + 4 * F + (acc ? 3 : 0));
 }
 // Accurate layer evaluation (direction, incidence cosine, material constants
 // and layer phases carried as hi + lo; sin/cos on the FMA pipe) for designs

@@ -615,7 +615,8 @@ __device__ __forceinline__ void ring_finish(FwdRing& S, bool fin, int slot, floa
 // the warp's next transfer-matrix round, and rays waiting for a geometry
 // lane. A warp owns at most kFwdQCap rays (lanes + both queues), so neither
 // queue can overflow.
-constexpr int kQCap = kFwdQCap;
+constexpr int kQCap = kFwdQCap;    // rays a warp owns at a time
+constexpr int kQRing = kFwdQRing;  // slots of a queue's ring
 
 // words of a queued ray (accurate mode: also the direction's low parts)
 template <int F, bool ACC>
@@ -624,7 +625,7 @@ __host__ __device__ constexpr int q_words() { return 9 + 4 * F + (ACC ? 3 : 0); 
 template <int F, bool ACC>
 __device__ __forceinline__ void q_put(uint32_t* q, unsigned i, const Ray<F>& R, long long ray_begin, int slot) {
   uint32_t* w = q + i;
-  constexpr int C = kQCap;
+  constexpr int C = kQRing;
   w[0 * C] = __float_as_uint(R.p.x);
   w[1 * C] = __float_as_uint(R.p.y);
   w[2 * C] = __float_as_uint(R.p.z);
@@ -653,7 +654,7 @@ __device__ __forceinline__ void q_put(uint32_t* q, unsigned i, const Ray<F>& R, 
 template <int F, bool ACC>
 __device__ __forceinline__ int q_get(const uint32_t* q, unsigned i, Ray<F>& R, long long ray_begin) {
   const uint32_t* w = q + i;
-  constexpr int C = kQCap;
+  constexpr int C = kQRing;
   R.p = v3(__uint_as_float(w[0 * C]), __uint_as_float(w[1 * C]), __uint_as_float(w[2 * C]));
   R.d = v3(__uint_as_float(w[3 * C]), __uint_as_float(w[4 * C]), __uint_as_float(w[5 * C]));
 #pragma unroll
@@ -696,8 +697,8 @@ __global__ void __launch_bounds__(kBlock, 2)
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int n_slots = min(max(A.n_slots, 1), kSlots);
   uint32_t* mq = reinterpret_cast<uint32_t*>(smem + A.blob_bytes + sizeof(float) * n_slots * A.bins) +
-                 wid * 2 * NW * kQCap;
-  uint32_t* gq = mq + NW * kQCap;
+                 wid * 2 * NW * kQRing;
+  uint32_t* gq = mq + NW * kQRing;
   if (tid < 6) s_led[tid] = 0.f;
   if (tid < 8) s_cnt[tid] = 0ull;
   if (tid < kSlots) {
@@ -749,7 +750,7 @@ __global__ void __launch_bounds__(kBlock, 2)
       const unsigned avail = gt - gh;
       const unsigned rank = __popc(need & lt_mask);
       if (!has && rank < avail) {
-        slot = q_get<F, ACC>(gq, (gh + rank) % kQCap, R, A.ray_begin);
+        slot = q_get<F, ACC>(gq, (gh + rank) & (kQRing - 1), R, A.ray_begin);
         has = true;
       }
       gh += min((unsigned)__popc(need), avail);
@@ -855,7 +856,7 @@ __global__ void __launch_bounds__(kBlock, 2)
       }
       // rays that reached a mirror wait in the mirror queue
       const unsigned pmask = __ballot_sync(FULL, to_mir);
-      if (to_mir) q_put<F, ACC>(mq, (mt + __popc(pmask & lt_mask)) % kQCap, R, A.ray_begin, slot);
+      if (to_mir) q_put<F, ACC>(mq, (mt + __popc(pmask & lt_mask)) & (kQRing - 1), R, A.ray_begin, slot);
       mt += __popc(pmask);
       // exits into the slot tallies: a few lanes per pass over thousands of
       // bins rarely meet, so each adds its own (a warp-level aggregation by
@@ -899,13 +900,13 @@ __global__ void __launch_bounds__(kBlock, 2)
     if (nm >= 32u || (nm > 0u && !__any_sync(FULL, has) && gt == gh)) {
       // the geometry rays wait in the geometry queue meanwhile
       const unsigned hm = __ballot_sync(FULL, has);
-      if (has) q_put<F, ACC>(gq, (gt + __popc(hm & lt_mask)) % kQCap, R, A.ray_begin, slot);
+      if (has) q_put<F, ACC>(gq, (gt + __popc(hm & lt_mask)) & (kQRing - 1), R, A.ray_begin, slot);
       gt += __popc(hm);
       has = false;
       const unsigned n = min(nm, 32u);
       bool fin = false, keep = false;
       if ((unsigned)lane < n) {
-        slot = q_get<F, ACC>(mq, (mh + lane) % kQCap, R, A.ray_begin);
+        slot = q_get<F, ACC>(mq, (mh + lane) & (kQRing - 1), R, A.ray_begin);
         const ChunkConst& scc = S.slot[slot].cc;
         mirror_event<F, P, 1, ACC>(R, R.last - S_MIR, B, scc.lam, scc.inv_lam, scc.li, A, c_steps,
                            nullptr, nullptr);
@@ -933,7 +934,7 @@ __global__ void __launch_bounds__(kBlock, 2)
       }
       mh += n;
       const unsigned km = __ballot_sync(FULL, keep);
-      if (keep) q_put<F, ACC>(gq, (gt + __popc(km & lt_mask)) % kQCap, R, A.ray_begin, slot);
+      if (keep) q_put<F, ACC>(gq, (gt + __popc(km & lt_mask)) & (kQRing - 1), R, A.ray_begin, slot);
       gt += __popc(km);
       ring_finish(S, fin, slot, s_tally, A, lane);
       n_fly -= __popc(__ballot_sync(FULL, fin));
