@@ -1265,7 +1265,9 @@ __device__ __forceinline__ int region_after(const Blob& B, int reg, int k, V3 d)
 // TIR at a slab face against air: r_s, r_p with u = n cos_i, a = sqrt(n^2 sin^2 - 1)
 //   r_s = (u + i a)/(u - i a), r_p = (c + i n a)/(c - i n a)   (cos_t = -i a)
 __device__ __forceinline__ void tir_coef(float n, float ci, float sin2, float2& rs, float2& rp) {
-  const float a = sqrtf(fmaxf(fmaf(n * n, sin2, -1.0f), 0.0f));
+  // a from the hardware reciprocal square root (TIR: a^2 > 0; the phase only)
+  const float a2 = fmaxf(fmaf(n * n, sin2, -1.0f), 1e-30f);
+  const float a = a2 * rsqrtf(a2);
   const float u = n * ci;
   const float iu = __fdividef(1.0f, fmaf(u, u, a * a));
   rs = make_float2(fmaf(u, u, -a * a) * iu, 2.0f * u * a * iu);

@@ -226,9 +226,11 @@ __device__ __forceinline__ Outcome face_event(Ray<F>& R, int sid, const BlobHead
     // eye-side exit: Fresnel power transmission glass -> air
     const float ct = sqrtf(fmaxf(1.0f - x, 0.0f));
     const float u = n * ci;
-    const float ts = 2.0f * u / (u + ct);
-    const float tp = 2.0f * u / fmaf(n, ct, ci);
-    const float tf = ct / u;
+    // the Fresnel factors only scale the intensity: fast quotients (the
+    // eye-plane distance below, which decides the bin, keeps the IEEE one)
+    const float ts = __fdividef(2.0f * u, u + ct);
+    const float tp = __fdividef(2.0f * u, fmaf(n, ct, ci));
+    const float tf = __fdividef(ct, u);
     o.Ts = tf * ts * ts;
     o.Tp = tf * tp * tp;
     float I = 0.f;
