@@ -501,6 +501,14 @@ void wg_omega_adam_destroy(wg_omega_adam* a);
  * parameters. Errors: WG_EINVAL. */
 wg_status wg_design_version(const wg_design* d, uint64_t* version);
 
+/* Failure-path test hook (no counterpart in the paper): one device thread
+ * waits for a flag that nothing sets, with the bounded wait the trace kernels
+ * use (device clock); after limit_ns (0 < limit_ns <= 1e9) it gives up, sets
+ * the error word and returns, and the call returns WG_ETIMEOUT with the
+ * context still usable. It allocates and frees 8 bytes of device memory and
+ * synchronizes the context's stream. Errors: WG_EINVAL, WG_EDEVICE. */
+wg_status wg_test_bounded_wait(wg_ctx* ctx, uint64_t limit_ns);
+
 /* ------------------------------------------------------------------------
  * Optimizer of the layer thicknesses (Results, "Evaluation": all PRMA
  * thicknesses optimized jointly within 20-200 nm; a soft gap between 0 and

@@ -600,6 +600,25 @@ extern "C" wg_status wg_eval_coating_dcos(wg_ctx* c, const wg_design* d, int32_t
   return WG_OK;
 }
 
+extern "C" wg_status wg_test_bounded_wait(wg_ctx* c, uint64_t limit_ns) {
+  if (!c) return fail(WG_EINVAL, "wg_test_bounded_wait: NULL ctx");
+  if (limit_ns == 0 || limit_ns > 1000000000ull) return fail(WG_EINVAL, "wg_test_bounded_wait: limit_ns must be in (0, 1e9]");
+  std::lock_guard<std::mutex> lk(c->mu);
+  CU(cudaSetDevice(c->device));
+  const cudaStream_t s = 0;  // the legacy default stream of the device
+  unsigned* dw = nullptr;
+  CU(cudaMalloc(&dw, 2 * sizeof(unsigned)));
+  unsigned h[2] = {0u, 0u};
+  cudaError_t e = cudaMemsetAsync(dw, 0, 2 * sizeof(unsigned), s);
+  if (e == cudaSuccess) e = launch_wait_flag(dw, dw + 1, (unsigned long long)limit_ns, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, dw, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(dw);
+  if (e != cudaSuccess) return fail(WG_EDEVICE, "wg_test_bounded_wait: %s", cudaGetErrorString(e));
+  if (h[1]) return fail(WG_ETIMEOUT, "a bounded device wait ran out (error word %u)", h[1]);
+  return WG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // trace plumbing
 // ---------------------------------------------------------------------------

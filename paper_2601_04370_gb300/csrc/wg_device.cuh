@@ -533,13 +533,50 @@ __device__ __forceinline__ void layer_at(const StackView& st, const MatTable& mt
   s = in ? s : 0.0f;
 }
 
+// The same slots evaluated directly from each slot's material, without a
+// table of every material and a select by material id (the values are those
+// of MatTable: the same function on the same inputs). inv_lam: 1/lambda of
+// the fast evaluation; the accurate one forms 1/lambda as hi + lo from lam.
+template <int P, bool ACC>
+__device__ __forceinline__ void slot_consts(const BlobHeader& h, const StackView& st, bool front, float c0h,
+                                            float c0l, float lam, float inv_lam, MatK* kb) {
+  int mv[P];
+#pragma unroll
+  for (int v = 0; v < P; ++v) {
+    int r = front ? v : (((st.L - 1 - v) % P) + P) % P;
+    r = r < st.L ? r : 0;
+    mv[v] = st.m[st.off + r];
+  }
+  if constexpr (ACC) {
+    const F2 p = two_prod(c0h, c0h);
+    F2 sin2 = fast_two_sum(1.0f, -p.h);
+    sin2.l = fmaf(-2.0f * c0h, c0l, __fsub_rn(sin2.l, p.l));
+    const float ilh = __frcp_rn(lam);
+    const float ill = fmaf(-ilh, lam, 1.0f) * ilh;  // 1/lam = ilh + ill
+#pragma unroll
+    for (int v = 0; v < P; ++v) {
+      const int m = mv[v];
+      const float n = h.mat_n[m];
+      const F2 nl = two_prod(n, ilh);
+      kb[v] = mat_const_acc(sin2, n, h.mat_inv_n[m], F2{h.mat_r2[m], h.mat_r2_lo[m]}, F2{nl.h, fmaf(n, ill, nl.l)});
+    }
+  } else {
+    const float sin2 = fmaf(-c0h, c0h, 1.0f);
+#pragma unroll
+    for (int v = 0; v < P; ++v) {
+      const int m = mv[v];
+      kb[v] = mat_const(sin2, h.mat_n[m], h.mat_inv_n[m], h.mat_r2[m], inv_lam);
+    }
+  }
+}
+
 // Effective coefficients in the paper's convention (r_p = -r_p(Abeles)).
+// kb: the material slots of a periodic stack (P > 0); mt: the material
+// table of a general one (P = 0)
 template <int P, bool ACC = false>
-__device__ __forceinline__ Coef tmm_forward(const StackView& st, bool front, const MatTable& mt, float n0,
-                                            float cos0, int& layer_steps) {
+__device__ __forceinline__ Coef tmm_forward_k(const StackView& st, bool front, const MatTable& mt, const MatK* kb,
+                                              float n0, float cos0, int& layer_steps) {
   constexpr int CKP = Seg<P>::CKP;
-  MatK kb[Seg<P>::NSLOT];
-  if constexpr (P > 0) stack_slots<P>(st, front, mt, kb);
   const float eta_s = n0 * cos0, eta_p = n0 / cos0;
   CV vs = cv_init(eta_s), vp = cv_init(eta_p);
   int es = 0, ep = 0;
@@ -564,6 +601,13 @@ __device__ __forceinline__ Coef tmm_forward(const StackView& st, bool front, con
   coef_from_v(vp, eta_p, ep, rpm, out.tp);
   out.rp = make_float2(-rpm.x, -rpm.y);
   return out;
+}
+template <int P, bool ACC = false>
+__device__ __forceinline__ Coef tmm_forward(const StackView& st, bool front, const MatTable& mt, float n0,
+                                            float cos0, int& layer_steps) {
+  MatK kb[Seg<P>::NSLOT];
+  if constexpr (P > 0) stack_slots<P>(st, front, mt, kb);
+  return tmm_forward_k<P, ACC>(st, front, mt, kb, n0, cos0, layer_steps);
 }
 
 // ---------------------------------------------------------------------------

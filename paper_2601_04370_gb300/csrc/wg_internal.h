@@ -191,6 +191,7 @@ cudaError_t launch_trace_fwd_fused(const TraceArgs* jobs_dev, const int* cta_job
 cudaError_t launch_bwd_replay(const TraceArgs& a, int F, int P, bool tilt, int gm, bool acc, int grid, size_t smem,
                               cudaStream_t s);
 // perm (may be null): perm[sorted position] = index of the record in `in`
+cudaError_t launch_wait_flag(const unsigned* flag, unsigned* err, unsigned long long limit_ns, cudaStream_t s);
 cudaError_t launch_bwd_sort(const HitRec* in, long long n, const uint8_t* blob, unsigned int* key_count, unsigned int* key_off,
                             unsigned int* key_cursor, HitRec* out, unsigned int* perm, cudaStream_t s);
 cudaError_t launch_bwd_adjoint(const AdjArgs& a, int P, bool acc, int grid, size_t smem,

@@ -324,14 +324,22 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
     cf.ts = lerp2(make_float2(a1.x, a1.y), make_float2(b1.x, b1.y), f);
     cf.tp = lerp2(make_float2(a1.z, a1.w), make_float2(b1.z, b1.w), f);
   } else {
-    MatTable mt;
-    if constexpr (ACC) {
-      mt.init_acc(H, st.cos0, st.cos0l, lam);
-    } else {
-      mt.init_inv(H, st.cos0, inv_lam);
-    }
     const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
-    cf = tmm_forward<P, ACC>(sv, st.front, mt, H.n_slab, st.cos0, layer_steps);
+    if constexpr (P > 0) {
+      // a periodic stack: each slot's material evaluated directly
+      MatK kb[P];
+      slot_consts<P, ACC>(H, sv, st.front, st.cos0, st.cos0l, lam, inv_lam, kb);
+      MatTable unused;
+      cf = tmm_forward_k<P, ACC>(sv, st.front, unused, kb, H.n_slab, st.cos0, layer_steps);
+    } else {
+      MatTable mt;
+      if constexpr (ACC) {
+        mt.init_acc(H, st.cos0, st.cos0l, lam);
+      } else {
+        mt.init_inv(H, st.cos0, inv_lam);
+      }
+      cf = tmm_forward<P, ACC>(sv, st.front, mt, H.n_slab, st.cos0, layer_steps);
+    }
   }
   // hit m draws word m & 3 of the block for counter (ray, m >> 2); the block
   // is recomputed per hit so the ray state needs no RNG words

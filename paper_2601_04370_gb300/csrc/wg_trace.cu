@@ -564,6 +564,26 @@ cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const in
   return cudaGetLastError();
 }
 
+// Failure-path test hook: one thread waits, with the trace kernels' bounded
+// wait (device clock, at most 2^24 polls), for a flag that nothing sets; when
+// the limit runs out it sets bit 2 of the error word (as an idle wait of the
+// forward trace does) and returns.
+__global__ void k_wait_flag(const unsigned* flag, unsigned* err, unsigned long long limit_ns) {
+  if (threadIdx.x != 0) return;
+  const unsigned long long t0 = gtimer_ns();
+  for (int it = 0; it < (1 << 24); ++it) {
+    if (*reinterpret_cast<const volatile unsigned*>(flag)) return;
+    if (gtimer_ns() - t0 > limit_ns) break;
+    __nanosleep(64);
+  }
+  atomicOr(err, 2u);
+}
+cudaError_t launch_wait_flag(const unsigned* flag, unsigned* err, unsigned long long limit_ns, cudaStream_t s) {
+  note_launches(1);
+  k_wait_flag<<<1, 32, 0, s>>>(flag, err, limit_ns);
+  return cudaGetLastError();
+}
+
 // counting sort of the records by key: key_count must be zero on entry
 cudaError_t launch_bwd_sort(const HitRec* in, long long n, const uint8_t* blob, unsigned int* key_count,
                             unsigned int* key_off, unsigned int* key_cursor, HitRec* out, unsigned int* perm,

@@ -153,12 +153,13 @@ def lib():
         L.wg_omega_adam_destroy.argtypes = [vp]
         L.wg_omega_adam_destroy.restype = None
         L.wg_design_version.argtypes = [vp, C.POINTER(C.c_uint64)]
+        L.wg_test_bounded_wait.argtypes = [vp, C.c_uint64]
         for name in ("wg_init", "wg_create_design", "wg_set_params", "wg_eval_coating", "wg_eval_coating_grad",
                      "wg_trace_forward", "wg_trace_backward", "wg_loss", "wg_trace_forward_noalloc",
                      "wg_submit", "wg_poll", "wg_cancel", "wg_autotune", "wg_omega_trace", "wg_set_omega",
                      "wg_adam_create", "wg_adam_step", "wg_adam_params", "wg_omega_adam_create",
                      "wg_omega_adam_step", "wg_design_version", "wg_autotune_info",
-                     "wg_trace_forward_batch", "wg_eval_coating_dcos"):
+                     "wg_trace_forward_batch", "wg_eval_coating_dcos", "wg_test_bounded_wait"):
             getattr(L, name).restype = C.c_int32
         _lib = L
     return _lib
@@ -426,6 +427,11 @@ class Context:
 
     def cancel(self, ticket):
         _check(lib().wg_cancel(self.h, ticket))
+
+    def test_bounded_wait(self, limit_ns: int):
+        """wg_test_bounded_wait: a device wait on a flag that nothing sets
+        gives up after limit_ns; raises WGError (WG_ETIMEOUT)."""
+        _check(lib().wg_test_bounded_wait(self.h, int(limit_ns)))
 
     def autotune(self, dh, cfg):
         h = _CfgHolder(cfg, None)
