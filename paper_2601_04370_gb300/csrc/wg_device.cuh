@@ -972,11 +972,20 @@ template <int P, class Sink, bool DUAL = false, bool ACC = false>
 __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, const MatTable& mt, float n0,
                                             float cos0, float2 A_s, float2 A_p, int which, Sink& sink,
                                             float2* seg, int eA = 0, const TiltTable* tt = nullptr,
-                                            float* g_cos = nullptr) {
-  // (A_s, A_p) * 2^eA are the weights; eA carries the range of dL/dtally
+                                            float* g_cos = nullptr, const MatK* slots = nullptr) {
+  // (A_s, A_p) * 2^eA are the weights; eA carries the range of dL/dtally;
+  // slots (P > 0): the stack slots' material constants when the caller
+  // evaluated them directly (else they come from mt)
   constexpr int CKP = Seg<P>::CKP;
   MatK kb[Seg<P>::NSLOT];
-  if constexpr (P > 0) stack_slots<P>(st, front, mt, kb);
+  if constexpr (P > 0) {
+    if (slots) {
+#pragma unroll
+      for (int v = 0; v < P; ++v) kb[v] = slots[v];
+    } else {
+      stack_slots<P>(st, front, mt, kb);
+    }
+  }
   Ckpt ck[MAX_CK];
   const int L = st.L;
   const int nseg = (L + CKP - 1) / CKP;

@@ -1712,20 +1712,28 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_adjoint(const AdjArgs A) {
         const bool front = (rec.kfw >> 8) & 1;
         const int which = (rec.kfw >> 9) & 1;
         const MirrorRec& M = B.mir[k];
-        MatTable mt;
-        mt.init_sel<ACC>(H, rec.cos0, rec.cos0l, __ldg(A.lambda + kfw_lam(rec.kfw)));
         const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+        const float lam = __ldg(A.lambda + kfw_lam(rec.kfw));
+        // a periodic stack's slots evaluated directly; a general stack's table
+        MatTable mt;
+        MatK kb[P > 0 ? P : 1];
+        if constexpr (P > 0) {
+          slot_consts<P, ACC>(H, sv, front, rec.cos0, rec.cos0l, lam, 1.0f / lam, kb);
+        } else {
+          mt.init_sel<ACC>(H, rec.cos0, rec.cos0l, lam);
+        }
+        const MatK* slots = P > 0 ? kb : nullptr;
         GradSink sink{s_grad, &bad, lane, uniform};
         if constexpr (T) {
           TiltTable tt;
           tt.init(H, rec.cos0);
           float g = 0.f;
           tmm_adjoint<P, GradSink, true, ACC>(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, seg,
-                                              rec.eA, &tt, &g);
+                                              rec.eA, &tt, &g, slots);
           A.tilt_aux[A.perm[i]].g_cos = (double)g * pow2d(rec.eA);
         } else {
           tmm_adjoint<P, GradSink, false, ACC>(sv, front, mt, H.n_slab, rec.cos0, rec.As, rec.Ap, which, sink, seg,
-                                               rec.eA);
+                                               rec.eA, nullptr, nullptr, slots);
         }
         c_steps += M.n_layers;
       }
