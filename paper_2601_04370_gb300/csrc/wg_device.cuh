@@ -1267,12 +1267,11 @@ __device__ __forceinline__ int next_surface(const Blob& B, V3 p, V3 d, int last,
       id = sid;
     }
   };
-  if (d.z < 0.0f) consider(S_BOT, __fdividef(-p.z, d.z));
-  if (d.z > 0.0f) consider(S_TOP, __fdividef(h.thick - p.z, d.z));
-  if (h.dims == 3) {
-    if (d.y > 0.0f) consider(S_YPOS, __fdividef(h.half_w - p.y, d.y));
-    if (d.y < 0.0f) consider(S_YNEG, __fdividef(-h.half_w - p.y, d.y));
-  }
+  // the face (and side) ahead: the numerator selected, one quotient each
+  // (the same values as testing both)
+  if (d.z != 0.0f) consider(d.z < 0.0f ? S_BOT : S_TOP, __fdividef(d.z < 0.0f ? -p.z : h.thick - p.z, d.z));
+  if (h.dims == 3 && d.y != 0.0f)
+    consider(d.y > 0.0f ? S_YPOS : S_YNEG, __fdividef(d.y > 0.0f ? h.half_w - p.y : -h.half_w - p.y, d.y));
   const int K = h.n_mir;
   int k0 = 0, k1 = K;
   bool left = true, right = true;
