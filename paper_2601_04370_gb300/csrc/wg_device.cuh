@@ -1286,12 +1286,18 @@ __device__ __forceinline__ int next_surface(const Blob& B, V3 p, V3 d, int last,
     if (dn > 0.0f) consider(S_LEFT, __fdividef(-fmaf(p.x, h.ic_nx, p.z * h.ic_nz), dn));
   }
   if (right && d.x > 0.0f) consider(S_RIGHT, __fdividef(h.x_end - p.x, d.x));
+  auto plane = [&](int k) {
+    const float4 m = *reinterpret_cast<const float4*>(&B.mir[k]);  // (nx, ny, nz, c)
+    const float den = fmaf(d.x, m.x, fmaf(d.y, m.y, d.z * m.z));
+    if (den != 0.0f) consider(S_MIR + k, __fdividef(m.w - fmaf(p.x, m.x, fmaf(p.y, m.y, p.z * m.z)), den));
+  };
   auto prma_planes = [&]() {
-    for (int k = k0; k < k1; ++k) {
-      const MirrorRec& m = B.mir[k];
-      const float den = fmaf(d.x, m.nx, fmaf(d.y, m.ny, d.z * m.nz));
-      if (den == 0.0f) continue;
-      consider(S_MIR + k, __fdividef(m.c - fmaf(p.x, m.nx, fmaf(p.y, m.ny, p.z * m.nz)), den));
+    if (reg >= 0) {
+      // the two planes bounding the region (one at either end), in order
+      if (reg > 0) plane(reg - 1);
+      if (reg < K) plane(reg);
+    } else {
+      for (int k = k0; k < k1; ++k) plane(k);
     }
   };
   if constexpr (GM == 0) {
