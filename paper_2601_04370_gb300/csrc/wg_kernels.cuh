@@ -943,9 +943,11 @@ __global__ void __launch_bounds__(kBlock, 2)
         }
       }
       mh += n;
-      const unsigned km = __ballot_sync(FULL, keep);
-      if (keep) q_put<F, ACC>(gq, (gt + __popc(km & lt_mask)) & (kQRing - 1), R, A.ray_begin, slot);
-      gt += __popc(km);
+      // a lane keeps the ray it took on through the mirror (its next event
+      // comes in the next pass); the rays parked in the geometry queue return
+      // to lanes as they free up (the order of the warp's work, not any ray's
+      // result, depends on this)
+      has = keep;
       ring_finish(S, fin, slot, s_tally, A, lane);
       n_fly -= __popc(__ballot_sync(FULL, fin));
       continue;
