@@ -583,13 +583,30 @@ __device__ __forceinline__ Coef tmm_forward_k(const StackView& st, bool front, c
   const int L = st.L;
   const int i0 = front ? st.off : st.off + L - 1, di = front ? 1 : -1;
   for (int j0 = L > 0 ? ((L - 1) / CKP) * CKP : -1; j0 >= 0; j0 -= CKP) {
+    if constexpr (P > 0) {
+      // one material period unrolled per iteration (the slots stay static):
+      // a shorter loop body for the instruction cache of a kernel whose
+      // warps run different phases at once
+#pragma unroll 1
+      for (int w = CKP / P - 1; w >= 0; --w) {
 #pragma unroll
-    for (int u = CKP - 1; u >= 0; --u) {
-      MatK k;
-      float d, c, s;
-      layer_at<P, ACC>(st, mt, kb, i0, di, j0 + u, u, k, d, c, s);
-      cv_step(vs, c, s * k.q12s, s * k.q21s);
-      cv_step(vp, c, s * k.q12p, s * k.q21p);
+        for (int v = P - 1; v >= 0; --v) {
+          MatK k;
+          float d, c, s;
+          layer_at<P, ACC>(st, mt, kb, i0, di, j0 + w * P + v, v, k, d, c, s);
+          cv_step(vs, c, s * k.q12s, s * k.q21s);
+          cv_step(vp, c, s * k.q12p, s * k.q21p);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int u = CKP - 1; u >= 0; --u) {
+        MatK k;
+        float d, c, s;
+        layer_at<P, ACC>(st, mt, kb, i0, di, j0 + u, u, k, d, c, s);
+        cv_step(vs, c, s * k.q12s, s * k.q21s);
+        cv_step(vp, c, s * k.q12p, s * k.q21p);
+      }
     }
     cv_rescale(vs, es);
     cv_rescale(vp, ep);
