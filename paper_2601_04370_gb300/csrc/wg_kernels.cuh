@@ -292,7 +292,10 @@ __device__ __forceinline__ float2 lerp2(float2 a, float2 b, float f) {
 // 2 in the replay (may read them back); the other direction is compiled out.
 // ACC: accurate mode (direction and incidence cosine as hi + lo, the
 // accurate layer evaluation), for long stacks.
-template <int F, int P, int CM, bool ACC>
+// LM: where the coefficients come from: 0 the layer chain (the coating
+// table's branch compiled out), 1 the coating table, 2 the table when A.lut
+// is set, else the chain.
+template <int F, int P, int CM, bool ACC, int LM = 2>
 __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob& B, float lam, float inv_lam, int li,
                                                    const TraceArgs& A, int& layer_steps, float2* Es_out,
                                                    float2* Ep_out) {
@@ -313,7 +316,7 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
   float4 kv;
   if (kept) {
     kv = A.coef[(R.id - A.coef_base) * A.coef_slots + m];
-  } else if (A.lut) {
+  } else if (LM == 1 || (LM == 2 && A.lut)) {
     int j;
     float f;
     lut_locate(A, st.cos0, j, f);
@@ -689,7 +692,9 @@ __device__ __forceinline__ int q_get(const uint32_t* q, unsigned i, Ray<F>& R, l
 }
 
 // GM: geometry mode of next_surface (0 PRMA, 1 general, 2 either: fused launches)
-template <int F, int P, int GM, bool ACC>
+// LUT: the coating table's instance (coefficients interpolated, no layer
+// chain); the exact instances carry no table code
+template <int F, int P, int GM, bool ACC, bool LUT = false>
 __global__ void __launch_bounds__(kBlock, 2)
     k_trace_fwd(const TraceArgs A0, const TraceArgs* __restrict__ jobs, const int* __restrict__ cta_job) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -918,7 +923,7 @@ __global__ void __launch_bounds__(kBlock, 2)
       if ((unsigned)lane < n) {
         slot = q_get<F, ACC>(mq, (mh + lane) & (kQRing - 1), R, A.ray_begin);
         const ChunkConst& scc = S.slot[slot].cc;
-        mirror_event<F, P, 1, ACC>(R, R.last - S_MIR, B, scc.lam, scc.inv_lam, scc.li, A, c_steps,
+        mirror_event<F, P, 1, ACC, LUT ? 1 : 0>(R, R.last - S_MIR, B, scc.lam, scc.inv_lam, scc.li, A, c_steps,
                            nullptr, nullptr);
         if (R.ev >= A.max_events) {
           fin = true;

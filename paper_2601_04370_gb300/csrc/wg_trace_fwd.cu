@@ -6,6 +6,7 @@ namespace wgk {
 
 using FwdKernel = void (*)(const TraceArgs, const TraceArgs*, const int*);
 FwdKernel pick_fwd_accurate(int F, int P, int gm);
+FwdKernel pick_fwd_table(int F, int gm, bool acc);
 
 template <int GM>
 static FwdKernel pick_fwd_gm(int F, int P) {
@@ -23,12 +24,16 @@ cudaError_t preload_field_kernel();
 cudaError_t preload_forward_kernels() {
   for (int acc = 0; acc < 2; ++acc)
     for (int gm = 0; gm < 3; ++gm)
-      for (int F = 1; F <= 2; ++F)
+      for (int F = 1; F <= 2; ++F) {
         for (int P : {0, 2, 3}) {
           cudaFuncAttributes fa;
           const cudaError_t e = cudaFuncGetAttributes(&fa, pick_fwd(F, P, gm, acc != 0));
           if (e != cudaSuccess) return e;
         }
+        cudaFuncAttributes fa;
+        const cudaError_t e = cudaFuncGetAttributes(&fa, pick_fwd_table(F, gm, acc != 0));
+        if (e != cudaSuccess) return e;
+      }
   return preload_field_kernel();
 }
 
@@ -38,7 +43,8 @@ int trace_fwd_blocks_per_sm(int F, int P, int gm, bool acc, size_t smem) {
 
 cudaError_t launch_trace_fwd(const TraceArgs& a, int F, int P, int gm, bool acc, int grid, size_t smem,
                              cudaStream_t s) {
-  auto k = pick_fwd(F, P, gm, acc);
+  // the coating table's instance when the call interpolates coefficients
+  auto k = a.lut ? pick_fwd_table(F, gm, acc) : pick_fwd(F, P, gm, acc);
   raise_smem_limit(k);
   note_launches(1);
   TraceArgs a1 = a;
