@@ -104,14 +104,14 @@ struct wg_design {
   int dims = 3, n_mat = 0, K = 0, n_orig = 0, n_dev = 0;
   float n_slab = 0, thick = 0, width = 0, x_end = 0, eye_relief = 0, ic_tilt = 0;
   std::vector<float> mat_n, mir_x, mir_tilt, omega, layer_d;
-  std::vector<int> n_layers, layer_mat, orig_to_dev, dev_to_orig;
+  std::vector<int> n_layers, layer_mat, orig_to_store, dev_to_orig;
   std::vector<uint8_t> pruned;
   uint8_t* blob = nullptr;
   int blob_bytes = 0;
   float* d_mir = nullptr;      // [3][K]: x, tilt, omega
   std::vector<float> geo;      // general mirrors: [K][14] as in the descriptor; empty: PRMA
   float* d_geo = nullptr;      // device copy of geo, or NULL
-  int* d_orig_to_dev = nullptr;
+  int* d_orig_to_store = nullptr;  // original layer -> index in the blob's padded layer arrays (-1 pruned)
   int* d_dev_to_orig = nullptr;
   float* d_stage = nullptr;    // [n_orig] thickness staging for set_params
   int period = 0;              // material period shared by all stacks (0, 2 or 3)
@@ -226,7 +226,7 @@ static void destroy_design_dev(wg_design* d) {
   if (d->blob) cudaFree(d->blob);
   if (d->d_mir) cudaFree(d->d_mir);
   if (d->d_geo) cudaFree(d->d_geo);
-  if (d->d_orig_to_dev) cudaFree(d->d_orig_to_dev);
+  if (d->d_orig_to_store) cudaFree(d->d_orig_to_store);
   if (d->d_dev_to_orig) cudaFree(d->d_dev_to_orig);
   if (d->d_stage) cudaFree(d->d_stage);
   d->exits.release();
@@ -314,9 +314,12 @@ static std::vector<uint8_t> build_blob(const wg_design& d) {
   const size_t off_mir = sizeof(BlobHeader);
   // general designs: the plane-family table follows the mirror records
   const size_t fam_bytes = d.geo.empty() ? 0 : sizeof(FamRec) * d.K;
+  // layer arrays: kStackPad zero-thickness layers (material 0) before each
+  // stack and after the last
+  const size_t n_store = (size_t)d.n_dev + (size_t)kStackPad * (d.K + 1);
   const size_t off_d = align16(off_mir + sizeof(MirrorRec) * d.K + fam_bytes);
-  const size_t off_m = align16(off_d + sizeof(float) * d.n_dev);
-  const size_t bytes = align16(off_m + (size_t)d.n_dev + 1);
+  const size_t off_m = align16(off_d + sizeof(float) * n_store);
+  const size_t bytes = align16(off_m + n_store + 1);
   std::vector<uint8_t> b(bytes, 0);
   BlobHeader h;
   memset(&h, 0, sizeof(h));
@@ -349,10 +352,11 @@ static std::vector<uint8_t> build_blob(const wg_design& d) {
     MirrorRec r;
     memset(&r, 0, sizeof(r));
     r.layer_off = dev;
+    r.store_off = dev + kStackPad * (k + 1);
     for (int l = 0; l < d.n_layers[k]; ++l, ++orig) {
       if (d.pruned[orig]) continue;
-      dd[dev] = d.layer_d[orig];
-      mm[dev] = (uint8_t)d.layer_mat[orig];
+      dd[dev + kStackPad * (k + 1)] = d.layer_d[orig];
+      mm[dev + kStackPad * (k + 1)] = (uint8_t)d.layer_mat[orig];
       ++dev;
     }
     r.n_layers = dev - r.layer_off;
@@ -410,11 +414,12 @@ static wg_status upload_design(wg_design* d, cudaStream_t s) {
     CU(cudaMalloc(&d->d_geo, sizeof(float) * d->geo.size()));
     CU(cudaMemcpyAsync(d->d_geo, d->geo.data(), sizeof(float) * d->geo.size(), cudaMemcpyHostToDevice, s));
   }
-  CU(cudaMalloc(&d->d_orig_to_dev, sizeof(int) * std::max(1, d->n_orig)));
+  CU(cudaMalloc(&d->d_orig_to_store, sizeof(int) * std::max(1, d->n_orig)));
   CU(cudaMalloc(&d->d_dev_to_orig, sizeof(int) * std::max(1, d->n_dev)));
   CU(cudaMalloc(&d->d_stage, sizeof(float) * std::max(1, d->n_orig)));
   if (d->n_orig)
-    CU(cudaMemcpyAsync(d->d_orig_to_dev, d->orig_to_dev.data(), sizeof(int) * d->n_orig, cudaMemcpyHostToDevice, s));
+    CU(cudaMemcpyAsync(d->d_orig_to_store, d->orig_to_store.data(), sizeof(int) * d->n_orig, cudaMemcpyHostToDevice,
+                       s));
   if (d->n_dev)
     CU(cudaMemcpyAsync(d->d_dev_to_orig, d->dev_to_orig.data(), sizeof(int) * d->n_dev, cudaMemcpyHostToDevice, s));
   CU(launch_prep_design(d->blob, d->d_mir, d->d_mir + d->K, d->d_mir + 2 * d->K, d->d_geo, d->K, d->ic_tilt, d->thick, s));
@@ -454,14 +459,18 @@ extern "C" wg_status wg_create_design(wg_ctx* c, const wg_design_desc* s, wg_des
   d->pruned.assign(total, 0);
   if (s->layer_pruned)
     for (int i = 0; i < total; ++i) d->pruned[i] = s->layer_pruned[i] ? 1 : 0;
-  d->orig_to_dev.assign(total, -1);
-  for (int i = 0; i < total; ++i) {
-    if (d->pruned[i]) {
-      d->layer_d[i] = 0.0f;
-      continue;
+  // device layers: the non-pruned ones in order; mirror k's stack sits in the
+  // blob's layer arrays after k + 1 pads of kStackPad
+  d->orig_to_store.assign(total, -1);
+  for (int k = 0, i = 0; k < d->K; ++k) {
+    for (int l = 0; l < d->n_layers[k]; ++l, ++i) {
+      if (d->pruned[i]) {
+        d->layer_d[i] = 0.0f;
+        continue;
+      }
+      d->orig_to_store[i] = (int)d->dev_to_orig.size() + kStackPad * (k + 1);
+      d->dev_to_orig.push_back(i);
     }
-    d->orig_to_dev[i] = (int)d->dev_to_orig.size();
-    d->dev_to_orig.push_back(i);
   }
   d->n_dev = (int)d->dev_to_orig.size();
   st = upload_design(d, 0);
@@ -506,7 +515,7 @@ extern "C" wg_status wg_set_params(wg_design* d, const float* thickness_nm, int6
       for (int i = 0; i < d->n_orig; ++i) d->layer_d[i] = d->pruned[i] ? 0.0f : thickness_nm[i];
       CU(cudaMemcpyAsync(d->d_stage, thickness_nm, sizeof(float) * d->n_orig, cudaMemcpyHostToDevice, s));
     }
-    CU(launch_thickness_update(d->blob, d->d_stage, d->d_orig_to_dev, d->n_orig, s));
+    CU(launch_thickness_update(d->blob, d->d_stage, d->d_orig_to_store, d->n_orig, s));
     ++d->thick_version;  // the coefficients kept by the last listing forward are stale
     ++d->param_version;
   }

@@ -35,6 +35,11 @@ constexpr int TAPE_HITS = 128;  // = WG_MAX_EVENTS: a ray's mirror hits always f
 constexpr int CK = 8;                 // checkpoint stride (layers)
 constexpr int MAX_LAYERS_MIRROR = 512;
 constexpr int MAX_CK = MAX_LAYERS_MIRROR / 6 + 2;  // checkpoints at the shortest segment (6 layers)
+// Zero-thickness layers stored before every stack and after the last one in
+// the blob's thickness and material arrays (material 0): at least the longest
+// segment minus one, so the steps of a stack's last segment that lie past its
+// end read thickness 0, an exact identity step, with no test of the index.
+constexpr int kStackPad = 8;
 constexpr float TWO_PI = 6.283185307179586f;
 
 enum { S_BOT = 0, S_TOP = 1, S_LEFT = 2, S_RIGHT = 3, S_YNEG = 4, S_YPOS = 5, S_MIR = 8 };
@@ -45,7 +50,9 @@ constexpr uint32_t TAG_GEN = 0x47454E30u;
 constexpr uint32_t TAG_EVT = 0x45565430u;
 
 // ---------------------------------------------------------------------------
-// Design blob: header | mirrors | layer thickness (FP32) | layer material (u8)
+// Design blob: header | mirrors | layer thickness (FP32) | layer material (u8);
+// the two layer arrays hold kStackPad zero-thickness layers before each
+// mirror's stack and after the last
 // Staged into shared memory per CTA with a bulk (TMA) copy.
 // ---------------------------------------------------------------------------
 struct alignas(16) BlobHeader {
@@ -77,7 +84,7 @@ struct alignas(16) MirrorRec {
   float ax, ay, az;          // tilt axis: dn/d(tilt) = a x n per radian (PRMA: a = -y)
   float x0, x1, y0, y1;      // (x, y) rectangle where a general mirror acts
   float nlx, nly, nlz;       // FP64 normal minus (nx, ny, nz): the low part (accurate mode)
-  float pad_;
+  int store_off;             // first layer in the blob's padded layer arrays
 };
 static_assert(sizeof(MirrorRec) == 80, "mirror layout");
 
@@ -461,11 +468,13 @@ struct Coef {
   float2 rs, rp, ts, tp;
 };
 
-// Stack view of one mirror in shared memory.
+// Stack view of one mirror in shared memory: off is the first layer's index
+// in the padded layer arrays, shift = off - the first layer's device index
+// (the index of the gradient sums).
 struct StackView {
   const float* d;
   const uint8_t* m;
-  int off, L;
+  int off, L, shift;
   __device__ __forceinline__ int idx(bool front, int j) const { return front ? off + j : off + L - 1 - j; }
 };
 
@@ -511,26 +520,24 @@ __device__ __forceinline__ void stack_slots(const StackView& st, bool front, con
   }
 }
 
-// Traversal step j of a stack (device index i0 + j di), or past the stack's
-// end (j >= L) an identity step: thickness 0 and (c, s) = (1, 0), exactly
-// the identity matrix. Loops over whole segments then take no branch on the
-// stack length (a branch per unrolled step costs more than the identity
-// steps of a stack's last segment). The material of a periodic stack's step
-// comes from its register slot; a general stack reads it (index clamped).
+// Traversal step j of a stack (array index i0 + j di), or past the stack's
+// end (j >= L, one of the stored pad layers) an identity step: thickness 0
+// gives phase 0 and (c, s) = (1, 0) exactly (sin 0 = 0, cos 0 = 1 and
+// e^0 = 1 in every evaluation of layer_cs), the identity matrix. Loops over
+// whole segments then take no branch and no bounds test on the stack length.
+// The material of a periodic stack's step comes from its register slot; a
+// general stack reads it.
 template <int P, bool ACC>
 __device__ __forceinline__ void layer_at(const StackView& st, const MatTable& mt, const MatK* kb, int i0, int di,
                                          int j, int u, MatK& k, float& d, float& c, float& s) {
-  const bool in = j < st.L;
-  const int i = i0 + min(j, st.L - 1) * di;
+  const int i = i0 + j * di;
   if constexpr (P > 0) {
     k = kb[u % P];
   } else {
     k = mt.get(st.m[i]);
   }
-  d = in ? st.d[i] : 0.0f;
+  d = st.d[i];
   layer_cs<ACC>(k, d, c, s);
-  c = in ? c : 1.0f;
-  s = in ? s : 0.0f;
 }
 
 // The same slots evaluated directly from each slot's material, without a
@@ -1006,7 +1013,8 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
   Ckpt ck[MAX_CK];
   const int L = st.L;
   const int nseg = (L + CKP - 1) / CKP;
-  // device index of traversal step j: i0 + j di
+  // layer-array index of traversal step j: i0 + j di (the gradient sums take
+  // the device index, i0 + j di - st.shift)
   const int i0 = front ? st.off : st.off + L - 1, di = front ? 1 : -1;
   const float eta_s = n0 * cos0, eta_p = n0 / cos0;
   CV vs = cv_init(eta_s), vp = cv_init(eta_p);
@@ -1104,7 +1112,7 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         // the row and the tilt sums do not change
         MatK k;
         float rho = 0.0f;
-        const int i = i0 + min(j, L - 1) * di;
+        const int i = i0 + j * di;
         if constexpr (P > 0) {
           k = kb[u % P];
           if constexpr (DUAL) rho = rb[u % P];
@@ -1126,7 +1134,7 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         if constexpr (DUAL) {
           // rho (phase term kap d g + quotient term on v_{j+1}), at this
           // segment's exponents
-          const float kd = k.kap * (j < L ? st.d[i] : 0.0f);
+          const float kd = k.kap * st.d[i];
           const float qs = fmaf(k.q21s, fmaf(as.b.y, xn.xi, -as.b.x * xn.xr),
                                 -k.q12s * fmaf(-as.a0.x, xn.zr, as.a0.y * xn.zi));
           const float qp = fmaf(k.q12p, fmaf(-ap.a0.x, yn.zr, ap.a0.y * yn.zi),
@@ -1149,7 +1157,7 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
 #pragma unroll
         for (int u = 0; u < 8; ++u) t[u] = mul_pow2(t[u], k);
       }
-      sink.segment(t, min(CKP, L - j0), i0 + j0 * di, di);
+      sink.segment(t, min(CKP, L - j0), i0 + j0 * di - st.shift, di);
     }
     if constexpr (DUAL) {
       gc = fmaf(-2.0f, scale2(acc_s, eas + c1.es - eA), gc);

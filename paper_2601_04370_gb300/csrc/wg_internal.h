@@ -203,7 +203,7 @@ cudaError_t launch_coating_eval(const uint8_t* blob, int P, bool acc, int mirror
 cudaError_t launch_coating_grad(const uint8_t* blob, int P, bool acc, int mirror, int side, long long n,
                                 const float* cos0, const float* lam, const float* w, int which, float* grad,
                                 cudaStream_t s);
-cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const int* orig_to_dev, int n_orig,
+cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const int* orig_to_store, int n_orig,
                                     cudaStream_t s);
 // coating look-up table: entries for every (mirror, side, wavelength, bin)
 // of the design (lam: device [n_lam]); records: one hit record per (entry,

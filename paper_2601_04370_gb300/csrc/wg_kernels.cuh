@@ -327,7 +327,7 @@ __device__ __forceinline__ MirrorStep mirror_event(Ray<F>& R, int k, const Blob&
     cf.ts = lerp2(make_float2(a1.x, a1.y), make_float2(b1.x, b1.y), f);
     cf.tp = lerp2(make_float2(a1.z, a1.w), make_float2(b1.z, b1.w), f);
   } else {
-    const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+    const StackView sv{B.d, B.m, M.store_off, M.n_layers, M.store_off - M.layer_off};
     if constexpr (P > 0) {
       // a periodic stack: each slot's material evaluated directly
       MatK kb[P];
@@ -1719,7 +1719,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_adjoint(const AdjArgs A) {
         const bool front = (rec.kfw >> 8) & 1;
         const int which = (rec.kfw >> 9) & 1;
         const MirrorRec& M = B.mir[k];
-        const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+        const StackView sv{B.d, B.m, M.store_off, M.n_layers, M.store_off - M.layer_off};
         const float lam = __ldg(A.lambda + kfw_lam(rec.kfw));
         // a periodic stack's slots evaluated directly; a general stack's table
         MatTable mt;
@@ -1792,7 +1792,7 @@ __global__ void k_lut_build(const uint8_t* blob, int n_mir, int n_lam, const flo
   mt.init_sel<ACC>(H, c, 0.0f, lam[li]);
   MatTableD mtd;
   mtd.init(H, c, lam[li], mt);
-  const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+  const StackView sv{B.d, B.m, M.store_off, M.n_layers, M.store_off - M.layer_off};
   Coef cf, dcf;
   tmm_forward_dual<P, ACC>(sv, side == 0, mt, mtd, H.n_slab, c, cf, dcf);
   out[4 * i] = make_float4(cf.rs.x, cf.rs.y, cf.rp.x, cf.rp.y);
@@ -1812,7 +1812,7 @@ __global__ void k_coating_eval(const uint8_t* blob, int mirror, int side, long l
   const MirrorRec& M = B.mir[mirror];
   MatTable mt;
   mt.init_sel<ACC>(H, cos0[i], 0.0f, lam[i]);
-  const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+  const StackView sv{B.d, B.m, M.store_off, M.n_layers, M.store_off - M.layer_off};
   int steps = 0;
   const Coef c = tmm_forward<P, ACC>(sv, side == 0, mt, H.n_slab, cos0[i], steps);
   float* o = out + i * 8;
@@ -1854,7 +1854,7 @@ __global__ void __launch_bounds__(128) k_coating_grad(const uint8_t* blob, int m
   const MirrorRec& M = B.mir[mirror];
   MatTable mt;
   mt.init_sel<ACC>(H, cos0[i], 0.0f, lam[i]);
-  const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+  const StackView sv{B.d, B.m, M.store_off, M.n_layers, M.store_off - M.layer_off};
   RowSink sink{grad + i * M.n_layers, M.layer_off, M.n_layers, side == 0};
   tmm_adjoint<P, RowSink, false, ACC>(sv, side == 0, mt, H.n_slab, cos0[i], make_float2(w[4 * i], w[4 * i + 1]),
                  make_float2(w[4 * i + 2], w[4 * i + 3]), which, sink, seg);
@@ -1881,7 +1881,7 @@ __global__ void __launch_bounds__(128) k_coating_dcos(const uint8_t* blob, int m
   mt.init_sel<ACC>(H, cos0[i], 0.0f, lam[i]);
   TiltTable tt;
   tt.init(H, cos0[i]);
-  const StackView sv{B.d, B.m, M.layer_off, M.n_layers};
+  const StackView sv{B.d, B.m, M.store_off, M.n_layers, M.store_off - M.layer_off};
   NullSink sink;
   float g = 0.f;
   tmm_adjoint<P, NullSink, true, ACC>(sv, side == 0, mt, H.n_slab, cos0[i], make_float2(w[4 * i], w[4 * i + 1]),

@@ -168,12 +168,12 @@ __global__ void k_prep_fields(FieldRec* out, const float* fx, const float* fy, i
   out[f] = r;
 }
 
-__global__ void k_thickness_update(uint8_t* blob, const float* d_orig, const int* orig_to_dev, int n_orig) {
+__global__ void k_thickness_update(uint8_t* blob, const float* d_orig, const int* orig_to_store, int n_orig) {
   const BlobHeader* h = reinterpret_cast<const BlobHeader*>(blob);
   float* d = reinterpret_cast<float*>(blob + h->off_d);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n_orig) {
-    const int j = orig_to_dev[i];
+    const int j = orig_to_store[i];
     if (j >= 0) d[j] = d_orig[i];
   }
 }
@@ -557,10 +557,10 @@ cudaError_t launch_prep_fields(FieldRec* out, const float* fx, const float* fy, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const int* orig_to_dev, int n_orig,
+cudaError_t launch_thickness_update(uint8_t* blob, const float* d_orig, const int* orig_to_store, int n_orig,
                                     cudaStream_t s) {
   note_launches(1);
-  k_thickness_update<<<(n_orig + 255) / 256, 256, 0, s>>>(blob, d_orig, orig_to_dev, n_orig);
+  k_thickness_update<<<(n_orig + 255) / 256, 256, 0, s>>>(blob, d_orig, orig_to_store, n_orig);
   return cudaGetLastError();
 }
 
