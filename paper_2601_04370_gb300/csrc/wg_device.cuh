@@ -1055,29 +1055,27 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
   }
   eas += eA;
   eap += eA;
+  // Stacks without an evanescent layer (P > 0: every slot propagating) take
+  // v_{j+1} = M_j^{-1} v_j from the checkpoint at the segment's incident-side
+  // end, in registers: M_j = c I + s K with K^2 = -I (q12 q21 = 1) has
+  // determinant c^2 + s^2 = 1, and its inverse is the same step with s
+  // negated. Its singular values are bounded by the quotients, so the
+  // segment's vectors keep about the forward sweep's relative accuracy.
+  // Through an evanescent layer (K^2 = I) the inverse would lose the decaying
+  // solution, so those stacks recompute each segment from its substrate-side
+  // checkpoint instead and keep it in the lane's shared-memory column.
+  bool inv = false;
+  if constexpr (P > 0) {
+    inv = true;
+#pragma unroll
+    for (int v = 0; v < P; ++v) inv = inv && !kb[v].evan;
+  }
   for (int sg = 0; sg < nseg; ++sg) {
     const int j0 = sg * CKP;
     row_fit8(as, eas);
     row_fit8(ap, eap);
-    const Ckpt c1 = ck[sg + 1];
-    CV ws = c1.s, wp = c1.p;
-    // the segment's substrate-side vectors and (c, s), recomputed from the
-    // checkpoint at its far end and kept in this lane's shared-memory column
-    // (slots past the stack's end hold the checkpoint itself, v_L)
-#pragma unroll
-    for (int u = CKP - 1; u >= 0; --u) {
-      MatK k;
-      float d, c, s;
-      layer_at<P, ACC>(st, mt, kb, i0, di, j0 + u, u, k, d, c, s);
-      cv_step(ws, c, s * k.q12s, s * k.q21s);
-      cv_step(wp, c, s * k.q12p, s * k.q21p);
-      float2* b = seg + u * kSegPairs * 32;
-      b[0 * 32] = make_float2(ws.xr, ws.xi);
-      b[1 * 32] = make_float2(ws.zr, ws.zi);
-      b[2 * 32] = make_float2(wp.xr, wp.xi);
-      b[3 * 32] = make_float2(wp.zr, wp.zi);
-      b[4 * 32] = make_float2(c, s);
-    }
+    // the checkpoint the segment's vectors come from; its exponents scale the terms
+    const Ckpt cb = ck[inv ? sg : sg + 1];
     // the segment's scale factors of the terms, 2^xs (s) and 2^xp (p), exact
     // powers of two. When either lies outside the normal range the loop
     // applies 2^(xs - xr) and 2^(xp - xr) instead, with xr the larger
@@ -1086,7 +1084,7 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
     // factor clamped to the normal range (a term more than 2^126 below its
     // partner's scale, or a zero row's), and the terms take 2^xr when they
     // are read out: the loop itself never branches on the range
-    const int xs = eas + c1.es, xp = eap + c1.ep;
+    const int xs = eas + cb.es, xp = eap + cb.ep;
     const bool in_range = xs >= -126 && xs <= 127 && xp >= -126 && xp <= 127;
     int xr = 0;
     if (!in_range) {
@@ -1094,47 +1092,30 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
       xr = ns ? (np ? max(xs, xp) : xs) : (np ? xp : 0);
     }
     const float fs = pow2f(min(max(xs - xr, -126), 127)), fp = pow2f(min(max(xp - xr, -126), 127));
-    // v_j of step u (the row's products with v_{j+1} read the next slot,
-    // or the checkpoint for the segment's last step)
-    CV x = seg_cv(seg), y = seg_cv(seg + 2 * 32);
+    float t[8];
 #pragma unroll
-    for (int u = 0; u < CKP; ++u) {
-      const int j = j0 + u;
-      CV xn = c1.s, yn = c1.p;
-      if (u + 1 < CKP) {
-        const float2* bn = seg + (u + 1) * kSegPairs * 32;
-        xn = seg_cv(bn);
-        yn = seg_cv(bn + 2 * 32);
-      }
-      {
-        // past the stack's end an identity step (the buffer holds c = 1,
-        // s = 0 there, the thickness is taken as 0): its term is not read,
-        // the row and the tilt sums do not change
+    for (int u = 0; u < 8; ++u) t[u] = 0.0f;
+    if (inv) {
+      CV x = cb.s, y = cb.p;  // v_j of step u
+#pragma unroll
+      for (int u = 0; u < CKP; ++u) {
         MatK k;
+        float d, c, s;
         float rho = 0.0f;
-        const int i = i0 + j * di;
-        if constexpr (P > 0) {
-          k = kb[u % P];
-          if constexpr (DUAL) rho = rb[u % P];
-        } else {
-          const int m = st.m[i];
-          k = mt.get(m);
-          if constexpr (DUAL) rho = tt->get(m);
-        }
-        float2* b = seg + u * kSegPairs * 32;
-        const float2 cs = b[4 * 32];
-        const float c = cs.x, s = cs.y;
-        // Im(a0 y) and Im(a1 x) with y = (zi, -zr), a1 = (b.y, -b.x)
+        layer_at<P, ACC>(st, mt, kb, i0, di, j0 + u, u, k, d, c, s);
+        if constexpr (DUAL) rho = rb[u % P];
+        const float m12s = s * k.q12s, m21s = s * k.q21s, m12p = s * k.q12p, m21p = s * k.q21p;
+        // v_{j+1} (past the stack's end the identity: v_L)
+        CV xn = x, yn = y;
+        cv_step(xn, c, -m12s, -m21s);
+        cv_step(yn, c, -m12p, -m21p);
         const float gs = fmaf(k.q12s, fmaf(-as.a0.x, x.zr, as.a0.y * x.zi),
                               k.q21s * fmaf(as.b.y, x.xi, -as.b.x * x.xr));
         const float gp = fmaf(k.q12p, fmaf(-ap.a0.x, y.zr, ap.a0.y * y.zi),
                               k.q21p * fmaf(ap.b.y, y.xi, -ap.b.x * y.xr));
-        // the step's term goes to its (c) slot, no longer needed
-        reinterpret_cast<float*>(b + 4 * 32)[0] = -2.0f * k.kap * fmaf(gs, fs, gp * fp);
+        t[u] = -2.0f * k.kap * fmaf(gs, fs, gp * fp);
         if constexpr (DUAL) {
-          // rho (phase term kap d g + quotient term on v_{j+1}), at this
-          // segment's exponents
-          const float kd = k.kap * st.d[i];
+          const float kd = k.kap * d;
           const float qs = fmaf(k.q21s, fmaf(as.b.y, xn.xi, -as.b.x * xn.xr),
                                 -k.q12s * fmaf(-as.a0.x, xn.zr, as.a0.y * xn.zi));
           const float qp = fmaf(k.q12p, fmaf(-ap.a0.x, yn.zr, ap.a0.y * yn.zi),
@@ -1142,26 +1123,92 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
           acc_s = fmaf(rho, fmaf(kd, gs, s * qs), acc_s);
           acc_p = fmaf(rho, fmaf(kd, gp, s * qp), acc_p);
         }
-        row_step(as, c, s * k.q12s, s * k.q21s);
-        row_step(ap, c, s * k.q12p, s * k.q21p);
+        row_step(as, c, m12s, m21s);
+        row_step(ap, c, m12p, m21p);
+        x = xn;
+        y = yn;
       }
-      x = xn;
-      y = yn;
-    }
-    {
-      float t[8];
+    } else {
+      CV ws = cb.s, wp = cb.p;
+      // the segment's substrate-side vectors and (c, s), recomputed from the
+      // checkpoint at its far end and kept in this lane's shared-memory column
+      // (slots past the stack's end hold the checkpoint itself, v_L)
 #pragma unroll
-      for (int u = 0; u < 8; ++u) t[u] = u < CKP ? seg[(u * kSegPairs + 4) * 32].x : 0.0f;
-      if (xr != 0) {
-        const int k = min(max(xr, -252), 254);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) t[u] = mul_pow2(t[u], k);
+      for (int u = CKP - 1; u >= 0; --u) {
+        MatK k;
+        float d, c, s;
+        layer_at<P, ACC>(st, mt, kb, i0, di, j0 + u, u, k, d, c, s);
+        cv_step(ws, c, s * k.q12s, s * k.q21s);
+        cv_step(wp, c, s * k.q12p, s * k.q21p);
+        float2* b = seg + u * kSegPairs * 32;
+        b[0 * 32] = make_float2(ws.xr, ws.xi);
+        b[1 * 32] = make_float2(ws.zr, ws.zi);
+        b[2 * 32] = make_float2(wp.xr, wp.xi);
+        b[3 * 32] = make_float2(wp.zr, wp.zi);
+        b[4 * 32] = make_float2(c, s);
       }
-      sink.segment(t, min(CKP, L - j0), i0 + j0 * di - st.shift, di);
+      // v_j of step u (the row's products with v_{j+1} read the next slot,
+      // or the checkpoint for the segment's last step)
+      CV x = seg_cv(seg), y = seg_cv(seg + 2 * 32);
+#pragma unroll
+      for (int u = 0; u < CKP; ++u) {
+        const int j = j0 + u;
+        CV xn = cb.s, yn = cb.p;
+        if (u + 1 < CKP) {
+          const float2* bn = seg + (u + 1) * kSegPairs * 32;
+          xn = seg_cv(bn);
+          yn = seg_cv(bn + 2 * 32);
+        }
+        {
+          // past the stack's end an identity step (the buffer holds c = 1,
+          // s = 0 there, the stored thickness is 0): its term is not read,
+          // the row and the tilt sums do not change
+          MatK k;
+          float rho = 0.0f;
+          const int i = i0 + j * di;
+          if constexpr (P > 0) {
+            k = kb[u % P];
+            if constexpr (DUAL) rho = rb[u % P];
+          } else {
+            const int m = st.m[i];
+            k = mt.get(m);
+            if constexpr (DUAL) rho = tt->get(m);
+          }
+          const float2 cs = seg[(u * kSegPairs + 4) * 32];
+          const float c = cs.x, s = cs.y;
+          // Im(a0 y) and Im(a1 x) with y = (zi, -zr), a1 = (b.y, -b.x)
+          const float gs = fmaf(k.q12s, fmaf(-as.a0.x, x.zr, as.a0.y * x.zi),
+                                k.q21s * fmaf(as.b.y, x.xi, -as.b.x * x.xr));
+          const float gp = fmaf(k.q12p, fmaf(-ap.a0.x, y.zr, ap.a0.y * y.zi),
+                                k.q21p * fmaf(ap.b.y, y.xi, -ap.b.x * y.xr));
+          t[u] = -2.0f * k.kap * fmaf(gs, fs, gp * fp);
+          if constexpr (DUAL) {
+            // rho (phase term kap d g + quotient term on v_{j+1}), at this
+            // segment's exponents
+            const float kd = k.kap * st.d[i];
+            const float qs = fmaf(k.q21s, fmaf(as.b.y, xn.xi, -as.b.x * xn.xr),
+                                  -k.q12s * fmaf(-as.a0.x, xn.zr, as.a0.y * xn.zi));
+            const float qp = fmaf(k.q12p, fmaf(-ap.a0.x, yn.zr, ap.a0.y * yn.zi),
+                                  -k.q21p * fmaf(ap.b.y, yn.xi, -ap.b.x * yn.xr));
+            acc_s = fmaf(rho, fmaf(kd, gs, s * qs), acc_s);
+            acc_p = fmaf(rho, fmaf(kd, gp, s * qp), acc_p);
+          }
+          row_step(as, c, s * k.q12s, s * k.q21s);
+          row_step(ap, c, s * k.q12p, s * k.q21p);
+        }
+        x = xn;
+        y = yn;
+      }
     }
+    if (xr != 0) {
+      const int k = min(max(xr, -252), 254);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) t[u] = mul_pow2(t[u], k);
+    }
+    sink.segment(t, min(CKP, L - j0), i0 + j0 * di - st.shift, di);
     if constexpr (DUAL) {
-      gc = fmaf(-2.0f, scale2(acc_s, eas + c1.es - eA), gc);
-      gc = fmaf(-2.0f, scale2(acc_p, eap + c1.ep - eA), gc);
+      gc = fmaf(-2.0f, scale2(acc_s, eas + cb.es - eA), gc);
+      gc = fmaf(-2.0f, scale2(acc_p, eap + cb.ep - eA), gc);
       acc_s = 0.0f;
       acc_p = 0.0f;
     }

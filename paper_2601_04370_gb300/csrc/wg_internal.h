@@ -142,7 +142,7 @@ inline int fwd_slots(long long chunk_rays) { return chunk_rays >= 1536 ? 2 : 3; 
 // shared-memory queues), and the slots of each queue's ring (a power of two,
 // so that a ring index is a mask; at least kFwdQCap); a queued ray takes
 // 9 + 4 F words (+ 3 in accurate mode)
-constexpr int kFwdQCap = 48;
+constexpr int kFwdQCap = 64;
 constexpr int kFwdQRing = 64;
 static_assert(kFwdQRing >= kFwdQCap && (kFwdQRing & (kFwdQRing - 1)) == 0, "queue ring");
 // a warp of the forward kernel reserves eyebox-ray list slots this many at a

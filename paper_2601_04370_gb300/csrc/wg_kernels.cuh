@@ -630,6 +630,7 @@ __device__ __forceinline__ void ring_finish(FwdRing& S, bool fin, int slot, floa
 // queue can overflow.
 constexpr int kQCap = kFwdQCap;    // rays a warp owns at a time
 constexpr int kQRing = kFwdQRing;  // slots of a queue's ring
+constexpr int kGenBatch = 16;      // fewest new rays a warp generates at once
 
 // words of a queued ray (accurate mode: also the direction's low parts)
 template <int F, bool ACC>
@@ -771,18 +772,23 @@ __global__ void __launch_bounds__(kBlock, 2)
       gh += min((unsigned)__popc(need), avail);
       need = __ballot_sync(FULL, !has);
     }
-    if (need && n_fly < kQCap) {
-      const int leader = __ffs(need) - 1;
+    // New rays in batches: with no parked ray left, and room for at least
+    // kGenBatch, every lane generates one ray (the generation runs once for
+    // up to 32 rays instead of once per pass for the few lanes that freed
+    // up); a free lane keeps its own, a busy lane parks its in the geometry
+    // queue, from which lanes take them as they free up
+    if (need && gt == gh && n_fly <= kQCap - kGenBatch) {
       unsigned long long base = 0;
       int got = 0;
-      if (lane == leader) base = ring_fetch(S, A, min(__popc(need), kQCap - n_fly), got);
-      base = __shfl_sync(FULL, base, leader);
-      got = __shfl_sync(FULL, got, leader);
+      if (lane == 0) base = ring_fetch(S, A, min(32, kQCap - n_fly), got);
+      base = __shfl_sync(FULL, base, 0);
+      got = __shfl_sync(FULL, got, 0);
       __threadfence_block();
-      const int rank = __popc(need & lt_mask);
       bool mapped = false;
-      if (!has && rank < got) {
-        const unsigned long long v = base + (unsigned long long)rank;
+      int tsl = 0;
+      Ray<F> T;
+      if (lane < got) {
+        const unsigned long long v = base + (unsigned long long)lane;
         int sl = -1;
 #pragma unroll
         for (int s = 0; s < kSlots; ++s) {
@@ -793,13 +799,21 @@ __global__ void __launch_bounds__(kBlock, 2)
         if (sl < 0) {
           atomicOr(A.error, 4u);  // a handed-out ray outside every bound chunk: never traced
         } else {
-          slot = sl;
-          const SlotState& st = S.slot[slot];
-          gen_ray(R, st.r0 + (long long)(v - (st.range >> kSizeBits)), st.cc, H, A);
-          has = true;
+          tsl = sl;
+          const SlotState& st = S.slot[sl];
+          gen_ray(T, st.r0 + (long long)(v - (st.range >> kSizeBits)), st.cc, H, A);
           mapped = true;
           ++c_rays;
         }
+      }
+      const bool park = mapped && has;
+      const unsigned pk = __ballot_sync(FULL, park);
+      if (park) q_put<F, ACC>(gq, (gt + __popc(pk & lt_mask)) & (kQRing - 1), T, A.ray_begin, tsl);
+      gt += __popc(pk);
+      if (mapped && !has) {
+        R = T;
+        slot = tsl;
+        has = true;
       }
       n_fly += __popc(__ballot_sync(FULL, mapped));
     }

@@ -168,6 +168,50 @@ def test_coating_gradient(ctx, ora, L, which):
     dh.destroy()
 
 
+@pytest.mark.parametrize("L", [40, 200])
+@pytest.mark.parametrize("which", [0, 1])
+def test_coating_gradient_near_the_critical_angle(ctx, ora, L, which):
+    """Incidence just inside the low-index material's critical angle: every
+    layer propagates, and the SiO2 layers run at grazing angles where the
+    layer quotients 1/(n cos t) and n/cos t reach ~30x their normal size.
+    The adjoint rebuilds these stacks' vectors by inverting the layer steps,
+    whose conditioning is worst here; the gradient must keep the accuracy of
+    the general test."""
+    D, _ = W.representative(n_rays=1000, n_layers=L)
+    dh = ctx.create_design(D)
+    n_lo = float(np.min(D.mat_n))
+    c_crit = np.sqrt(1.0 - (n_lo / D.n_slab) ** 2)   # cos(theta_0) where SiO2 turns evanescent
+    rng = np.random.default_rng(11 * L + which)
+    n = 96
+    cos0 = (c_crit + rng.uniform(1e-3, 4e-2, n)).astype(np.float32)
+    lam = rng.choice([460.0, 532.0, 630.0], n).astype(np.float32)
+    w = rng.normal(size=(n, 4)).astype(np.float32)
+    grad = torch.zeros((n, L), dtype=torch.float32, device="cuda")
+    k, side = 3, int(which)
+    ctx.eval_coating_grad(dh, k, side, _dev(cos0), _dev(lam), _dev(w), which, grad)
+    g = grad.cpu().numpy().astype(np.float64)
+    off = D.layer_offsets()
+    nm = D.mat_n.astype(np.float64)[D.layer_mat[off[k]:off[k + 1]]]
+    dd = D.layer_d_nm.astype(np.float64)[off[k]:off[k + 1]]
+    if side == 1:
+        nm, dd = nm[::-1], dd[::-1]
+    rel = []
+    for i in range(n):
+        ref, _, _ = ora.tmm_grad(D.n_slab, nm, dd, float(lam[i]), float(cos0[i]),
+                                 complex(w[i, 0], w[i, 1]), complex(w[i, 2], w[i, 3]), "r" if which == 0 else "t")
+        nr = np.linalg.norm(ref)
+        if nr < 1e-12:
+            assert np.linalg.norm(g[i]) < 1e-6
+            continue
+        rel.append(np.linalg.norm(g[i] - ref) / nr)
+    rel = np.array(rel)
+    assert rel.size > n // 2
+    assert np.median(rel) <= 1e-4, np.median(rel)
+    assert np.quantile(rel, 0.9) <= 5e-4, np.quantile(rel, 0.9)
+    assert rel.max() <= 1e-2, rel.max()
+    dh.destroy()
+
+
 # ---------------------------------------------------------------------------
 # forward trace
 # ---------------------------------------------------------------------------
