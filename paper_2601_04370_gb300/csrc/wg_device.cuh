@@ -589,18 +589,32 @@ __device__ __forceinline__ Coef tmm_forward_k(const StackView& st, bool front, c
   int es = 0, ep = 0;
   const int L = st.L;
   const int i0 = front ? st.off : st.off + L - 1, di = front ? 1 : -1;
-  for (int j0 = L > 0 ? ((L - 1) / CKP) * CKP : -1; j0 >= 0; j0 -= CKP) {
+  const int jtop = L > 0 ? ((L - 1) / CKP) * CKP : -1;
+  // P > 0: the thicknesses of the period ahead are loaded one iteration early
+  // (the period after the last reads stored pad layers)
+  float dn[Seg<P>::NSLOT];
+  if constexpr (P > 0) {
+#pragma unroll
+    for (int v = 0; v < P; ++v) dn[v] = st.d[i0 + (jtop + CKP - P + v) * di];
+  }
+  for (int j0 = jtop; j0 >= 0; j0 -= CKP) {
     if constexpr (P > 0) {
       // one material period unrolled per iteration (the slots stay static):
       // a shorter loop body for the instruction cache of a kernel whose
       // warps run different phases at once
 #pragma unroll 1
       for (int w = CKP / P - 1; w >= 0; --w) {
+        float dc[P];
+#pragma unroll
+        for (int v = 0; v < P; ++v) {
+          dc[v] = dn[v];
+          dn[v] = st.d[i0 + (j0 + (w - 1) * P + v) * di];
+        }
 #pragma unroll
         for (int v = P - 1; v >= 0; --v) {
-          MatK k;
-          float d, c, s;
-          layer_at<P, ACC>(st, mt, kb, i0, di, j0 + w * P + v, v, k, d, c, s);
+          float c, s;
+          const MatK& k = kb[v];
+          layer_cs<ACC>(k, dc[v], c, s);
           cv_step(vs, c, s * k.q12s, s * k.q21s);
           cv_step(vp, c, s * k.q12p, s * k.q21p);
         }

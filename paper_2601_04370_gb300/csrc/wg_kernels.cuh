@@ -630,7 +630,7 @@ __device__ __forceinline__ void ring_finish(FwdRing& S, bool fin, int slot, floa
 // queue can overflow.
 constexpr int kQCap = kFwdQCap;    // rays a warp owns at a time
 constexpr int kQRing = kFwdQRing;  // slots of a queue's ring
-constexpr int kGenBatch = 16;      // fewest new rays a warp generates at once
+constexpr int kGenBatch = 24;      // fewest new rays a warp generates at once
 
 // words of a queued ray (accurate mode: also the direction's low parts)
 template <int F, bool ACC>
