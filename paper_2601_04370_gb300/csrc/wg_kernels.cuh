@@ -1061,6 +1061,10 @@ struct TapeE : TapeLo<ACC> {
   int kfw;
 };
 
+// fewest eyebox rays whose reverse sweeps a warp of the replay runs together
+// (fewer when the warp has no live ray left)
+constexpr int kSweepMin = 16;
+
 // T: the replay also serves the tilt gradient: each emitted record gets its
 // TiltAux (the applied coefficients; the adjoint kernel adds dL/d(cos t0))
 // and its ray a RayHead.
@@ -1096,11 +1100,16 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
   float lam_l = 0.f, inv_lam_l = 0.f;
   int li_l = 0;
   float2 seg_s = make_float2(1.f, 0.f), seg_p = make_float2(1.f, 0.f);
+  // a ray that ended in the eyebox waits in its lane (which takes no new ray
+  // meanwhile) for the warp's next reverse sweep: emit hits, dL/dtally as
+  // g0 2^eG, its exit transmittances
+  int emit = 0, eG = 0;
+  float g0 = 0.f, x_Ts = 0.f, x_Tp = 0.f;
   for (;;) {
         for (;;) {
           // lanes without a ray take the next rays of the warp's unit; the
           // warp claims units from the global queue as they run out
-          unsigned fm = __ballot_sync(FULL, !has);
+          unsigned fm = __ballot_sync(FULL, !has && emit == 0);
           while (fm && u_more) {
             if (u_next >= u_end) {
               long long c = 0;
@@ -1124,7 +1133,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
             }
             const int take = (int)min((long long)__popc(fm), u_end - u_next);
             const int rank = __popc(fm & lt_mask);
-            if (!has && rank < take) {
+            if (!has && emit == 0 && rank < take) {  // a waiting lane keeps its ray until its sweep
               if (A.replay_list) {
                 // listed ray: replayed only if its bin carries gradient
                 const ExitRec e = A.replay_list[u_next + rank];
@@ -1152,13 +1161,14 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
               }
             }
             u_next += take;
-            fm = __ballot_sync(FULL, !has);
+            fm = __ballot_sync(FULL, !has && emit == 0);
           }
           const bool adv = has && !at_mir;
-          if (!__any_sync(FULL, adv)) break;
-          int emit = 0;  // hits to emit for a ray that ended in the eyebox
-          float g0 = 0.f;  // mantissa of G[bin] in [0.5, 1), exponent eG
-          int eG = 0;
+          // leave for the mirror step when no lane can advance, unless
+          // waiting lanes are left with no live ray in the warp: their sweep
+          // runs first (below; every pass either advances a ray or empties
+          // the waiting lanes)
+          if (!__any_sync(FULL, adv) && !(__any_sync(FULL, emit > 0) && !__any_sync(FULL, has))) break;
           Outcome o;
           o.term = 0;
           if (adv) {
@@ -1191,7 +1201,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                 if (g != 0.0) {
                   if (R.hits <= TAPE_HITS) {
                     emit = R.hits;
-                    g0 = (float)frexp(g, &eG);
+                    g0 = (float)frexp(g, &eG);  // mantissa in [0.5, 1), exponent eG
+                    x_Ts = o.Ts;
+                    x_Tp = o.Tp;
                   } else {
                     ++c_overflow;
                   }
@@ -1200,6 +1212,11 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
               }
             }
           }
+          // the reverse sweeps run for the waiting lanes together: once
+          // kSweepMin wait, or when no live ray is left in the warp (the
+          // sweep of one or two lanes at a time left the rest of the warp idle)
+          const unsigned wm = __ballot_sync(FULL, emit > 0);
+          if (!wm || (__popc(wm) < kSweepMin && __any_sync(FULL, has))) continue;
           // warp-aggregated reservation of record slots in the global buffer
           int incl = emit;
 #pragma unroll
@@ -1245,8 +1262,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
                 float2 ga[F], gb[F];
 #pragma unroll
                 for (int f = 0; f < F; ++f) {
-                  ga[f] = cmulc(seg_s, cscale(R.a[f], sc * o.Ts));
-                  gb[f] = cmulc(seg_p, cscale(R.b[f], sc * o.Tp));
+                  ga[f] = cmulc(seg_s, cscale(R.a[f], sc * x_Ts));
+                  gb[f] = cmulc(seg_p, cscale(R.b[f], sc * x_Tp));
                 }
                 for (int h = emit - 1; h >= 0; --h) {
                   const TapeE<F, ACC>& E = tape[h];
@@ -1323,6 +1340,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_bwd_replay(const TraceArgs A) {
               }
             }
           }
+          emit = 0;  // swept: the lane takes a new ray
         }
         if (!__any_sync(FULL, at_mir)) break;  // no ray left in this warp and no unit to claim
         if (at_mir) {

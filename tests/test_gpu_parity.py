@@ -489,6 +489,34 @@ def test_backward_eyebox_list_matches_full_replay(ctx):
     dh.destroy()
 
 
+def test_backward_replays_each_listed_ray_once(ctx):
+    """At a size where every warp of the replay takes many rays, the adjoint
+    gets exactly one record per mirror hit of every eyebox ray whose bin
+    carries gradient: a ray replayed twice, or dropped, changes the count.
+    Expected count from the forward's per-ray records; the adjoint's layer
+    steps are records x layers (every stack has 40)."""
+    from paper_2601_04370_gb300 import wg
+    D, C = W.representative(n_rays=2_000_000)
+    dh = ctx.create_design(D)
+    tally = torch.zeros(C.tally_shape, dtype=torch.float64, device="cuda")
+    rec = torch.zeros(C.total_rays * 8, dtype=torch.int32, device="cuda")
+    ctx.trace_forward(dh, C, tally, records=rec)
+    G = torch.zeros_like(tally)
+    ctx.loss(dh, C, tally, G)
+    r = rec.cpu().numpy().view(wg.RAY_RECORD_DTYPE)
+    g_flat = G.cpu().numpy().reshape(-1)
+    eb = (r["cat"] == 0) & (r["bin"] >= 0)
+    eb[eb] = g_flat[r["bin"][eb]] != 0.0
+    expected = int(r["n_hits"][eb].sum())
+    for tilt in (False, True):
+        g = torch.zeros(D.total_layers, dtype=torch.float64, device="cuda")
+        gt = torch.zeros(D.n_mirrors, dtype=torch.float64, device="cuda") if tilt else None
+        st = ctx.trace_backward(dh, C, G, g, grad_tilt=gt)
+        assert st["overflow"] == 0 and st["n_nonfinite"] == 0
+        assert st["n_adjoint_steps"] == 40 * expected, (st["n_adjoint_steps"] // 40, expected)
+    dh.destroy()
+
+
 def test_backward_pruned_layers_zero(ctx, ora):
     D, C = W.batching(n_designs=2, seed=4)[0]
     C = C.replace(n_rays=1728 * 4)
