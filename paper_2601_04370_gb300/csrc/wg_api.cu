@@ -1730,7 +1730,7 @@ extern "C" wg_status wg_loss(wg_ctx* c, const wg_design* d, const wg_trace_cfg* 
   cudaStream_t s = (cudaStream_t)cfg->stream;
   std::lock_guard<std::mutex> lk(c->mu);
   CU(cudaSetDevice(c->device));
-  const size_t need = sizeof(double) * (2 * p.n_cells * 9 + 8) + sizeof(unsigned short) * p.bins + 16;
+  const size_t need = sizeof(double) * (size_t)loss_ws_doubles(p.n_cells, p.bins, cfg->n_lambda) + 16;
   CU(cudaStreamWaitEvent(s, c->ws_free, 0));
   if (need > c->loss.n) {
     CU(cudaEventSynchronize(c->ws_free));

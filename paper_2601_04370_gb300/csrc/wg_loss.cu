@@ -46,7 +46,9 @@ __global__ void k_pupil_masks(LossGeom g, unsigned short* mask) {
   mask[b] = m;
 }
 
-// I[cell, p]
+// I[cell, p]. FP64 adds are scarce on this part: a warp's 32 consecutive
+// bins lie in 2-4 pupils, so the add of a pupil that none of them is in is
+// skipped for the whole warp (the loop runs in whole warps).
 __global__ void k_pupil_sums(const double* tally, LossGeom g, const unsigned short* mask, double inv_ncell,
                              double* I) {
   const long long cell = blockIdx.x;
@@ -55,13 +57,13 @@ __global__ void k_pupil_sums(const double* tally, LossGeom g, const unsigned sho
   double acc[9];
   for (int p = 0; p < 9; ++p) acc[p] = 0.0;
   const double* t = tally + cell * bins;
-  for (int b = threadIdx.x; b < bins; b += blockDim.x) {
-    const double v = t[b];
-    if (v == 0.0) continue;
-    const unsigned m = mask[b];
+  for (int b0 = threadIdx.x & ~31; b0 < bins; b0 += blockDim.x) {
+    const int b = b0 + (threadIdx.x & 31);
+    const double v = b < bins ? t[b] : 0.0;
+    const unsigned m = b < bins ? mask[b] : 0u;
 #pragma unroll
     for (int p = 0; p < 9; ++p)
-      if (m & (1u << p)) acc[p] += v;
+      if (__any_sync(0xffffffffu, m & (1u << p)) && (m & (1u << p))) acc[p] += v;
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int p = 0; p < g.n_pupil; ++p) {
@@ -77,50 +79,22 @@ __global__ void k_pupil_sums(const double* tally, LossGeom g, const unsigned sho
   }
 }
 
-// Spread statistic of x[0..n) with stride: CV (kind 0) or variance (kind 1),
-// and its gradient written to dx (scaled by `scale`).
-__device__ void spread_grad(const double* x, int n, long long stride, int kind, double scale, double* dx,
-                            double& val) {
-  double mu = 0.0;
-  for (int i = 0; i < n; ++i) mu += x[i * stride];
-  mu /= n;
-  double var = 0.0;
-  for (int i = 0; i < n; ++i) {
-    const double d = x[i * stride] - mu;
-    var += d * d;
-  }
-  var /= n;
-  if (kind == 1) {
-    val = var;
-    for (int i = 0; i < n; ++i) dx[i * stride] += scale * 2.0 * (x[i * stride] - mu) / n;
-    return;
-  }
-  const double sd = sqrt(var);
-  if (mu == 0.0) {
-    val = 0.0;
-    return;
-  }
-  val = sd / mu;
-  if (sd <= 0.0) return;
-  for (int i = 0; i < n; ++i) {
-    const double dsd = (x[i * stride] - mu) / (n * sd);
-    dx[i * stride] += scale * (dsd / mu - (val / mu) / n);
-  }
-}
-
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-// spread_grad for one group with a whole warp (n values, stride): the sums
-// are warp reductions; val is returned in every lane
-__device__ void spread_grad_warp(const double* x, int n, long long stride, int kind, double scale, double* dx,
-                                 double& val, int lane) {
-  double mu = 0.0;
-  for (int i = lane; i < n; i += 32) mu += x[i * stride];
-  mu = warp_sum_d(mu) / n;
+// The statistic of one group of n values x[i stride] with a whole warp and
+// its gradient, scaled, written to dx (every entry: 0 where the statistic has
+// none); returns the statistic and the group's sum. The per-group quotients
+// are taken once (FP64 divides are slow here) and the entries multiplied.
+__device__ void spread_group(const double* x, int n, long long stride, int kind, double scale, double* dx,
+                             double& val, double& sum, int lane) {
+  double su = 0.0;
+  for (int i = lane; i < n; i += 32) su += x[i * stride];
+  sum = warp_sum_d(su);
+  const double mu = sum / n;
   double var = 0.0;
   for (int i = lane; i < n; i += 32) {
     const double d = x[i * stride] - mu;
@@ -129,56 +103,64 @@ __device__ void spread_grad_warp(const double* x, int n, long long stride, int k
   var = warp_sum_d(var) / n;
   if (kind == 1) {
     val = var;
-    for (int i = lane; i < n; i += 32) dx[i * stride] += scale * 2.0 * (x[i * stride] - mu) / n;
+    const double c = scale * 2.0 / n;
+    for (int i = lane; i < n; i += 32) dx[i * stride] = c * (x[i * stride] - mu);
     return;
   }
   const double sd = sqrt(var);
-  if (mu == 0.0) {
-    val = 0.0;
+  val = mu == 0.0 ? 0.0 : sd / mu;
+  if (mu == 0.0 || sd <= 0.0) {
+    for (int i = lane; i < n; i += 32) dx[i * stride] = 0.0;
     return;
   }
-  val = sd / mu;
-  if (sd <= 0.0) return;
-  for (int i = lane; i < n; i += 32) {
-    const double dsd = (x[i * stride] - mu) / (n * sd);
-    dx[i * stride] += scale * (dsd / mu - (val / mu) / n);
+  // d(sd/mu)/dx_i = (x_i - mu)/(n sd mu) - (sd/mu)/(n mu)
+  const double a = scale / (n * sd * mu), b = scale * (val / mu) / n;
+  for (int i = lane; i < n; i += 32) dx[i * stride] = fma(a, x[i * stride] - mu, -b);
+}
+
+// One warp per group: U_FoV groups q < n_lam P ((lambda, pupil): the n_f
+// fields at stride P) into dIf, then U_eyebox groups ((lambda, field): its P
+// pupils) into dIe; the groups of one kind touch disjoint entries. Each
+// group's statistic goes to gval[q] and, for U_FoV (which covers every
+// entry once), its sum of I to gsum[q]; k_loss_final adds them up.
+__global__ void k_loss_groups(const double* I, int n_lam, int n_f, int P, int kind, double w_f, double w_e,
+                              double* dIf, double* dIe, double* gval, double* gsum) {
+  const int lane = threadIdx.x & 31;
+  const long long q = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;  // the same in a warp
+  const long long nfov = (long long)n_lam * P, neb = (long long)n_lam * n_f;
+  if (q >= nfov + neb) return;
+  double v, sum;
+  if (q < nfov) {
+    const long long off = (q / P) * n_f * P + q % P;
+    spread_group(I + off, n_f, P, kind, w_f / (double)nfov, dIf + off, v, sum, lane);
+    if (lane == 0) {
+      gval[q] = v;
+      gsum[q] = sum;
+    }
+  } else {
+    const long long off = (q - nfov) * P;
+    spread_group(I + off, P, 1, kind, w_e / (double)neb, dIe + off, v, sum, lane);
+    if (lane == 0) gval[q] = v;
   }
 }
 
-// One block: scalars and dL/dI. I is [n_lam][n_f][P]; dI same layout. The
-// field-uniformity groups (long: n_f values) take a warp each; the
-// eyebox-uniformity groups (P values) a thread each.
-__global__ void k_loss_scalar(const double* I, int n_lam, int n_f, int P, int kind, double w_f, double w_e, double* dI,
-                              double* out) {
-  const long long N = (long long)n_lam * n_f * P;
+// One block: dL/dI = -1/N + the two spread parts, and the scalars
+// L = -mean + w_f U_FoV + w_e U_eyebox, sums in a fixed order
+__global__ void k_loss_final(int n_lam, int n_f, int P, double w_f, double w_e, const double* dIf, const double* dIe,
+                             const double* gval, const double* gsum, double* dI, double* out) {
+  const long long N = (long long)n_lam * n_f * P, nfov = (long long)n_lam * P, neb = (long long)n_lam * n_f;
+  for (long long i = threadIdx.x; i < N; i += blockDim.x) dI[i] = (-1.0 / (double)N + dIf[i]) + dIe[i];
   __shared__ double s_red[3][32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   double sum = 0.0, uf = 0.0, ue = 0.0;
-  for (long long i = threadIdx.x; i < N; i += blockDim.x) {
-    sum += I[i];
-    dI[i] = -1.0 / (double)N;
+  for (long long q = threadIdx.x; q < nfov; q += blockDim.x) {
+    sum += gsum[q];
+    uf += gval[q];
   }
-  __syncthreads();
-  // U_FoV: over fields for each (lambda, p); gradients touch disjoint entries
-  const int nfov = n_lam * P;
-  for (int q = wid; q < nfov; q += nw) {
-    const int l = q / P, p = q % P;
-    double v;
-    spread_grad_warp(I + (long long)l * n_f * P + p, n_f, P, kind, w_f / nfov, dI + (long long)l * n_f * P + p, v,
-                     lane);
-    if (lane == 0) uf += v;
-  }
-  __syncthreads();
-  const int neb = n_lam * n_f;
-  for (int q = threadIdx.x; q < neb; q += blockDim.x) {
-    double v;
-    spread_grad(I + (long long)q * P, P, 1, kind, w_e / neb, dI + (long long)q * P, v);
-    ue += v;
-  }
+  for (long long q = threadIdx.x; q < neb; q += blockDim.x) ue += gval[nfov + q];
   double vals[3] = {sum, uf, ue};
   for (int k = 0; k < 3; ++k) {
-    double v = vals[k];
-    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const double v = warp_sum_d(vals[k]);
     if (lane == 0) s_red[k][wid] = v;
   }
   __syncthreads();
@@ -195,17 +177,18 @@ __global__ void k_loss_scalar(const double* I, int n_lam, int n_f, int P, int ki
 }
 
 // dL/dtally[cell, bin] = sum_{p containing bin} dL/dI[cell, p] / rays per cell
+// (whole warps; a pupil none of the warp's bins is in is skipped for it)
 __global__ void k_loss_scatter(const double* dI, LossGeom g, const unsigned short* mask, double inv_ncell,
                                long long n_cells, double* dL) {
   const long long bins = (long long)g.nx * g.ny;
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= n_cells * bins) return;
-  const long long cell = i / bins;
-  const unsigned m = mask[i % bins];
+  const bool in = i < n_cells * bins;
+  const long long cell = in ? i / bins : 0;
+  const unsigned m = in ? mask[i % bins] : 0u;
   double v = 0.0;
   for (int p = 0; p < g.n_pupil; ++p)
-    if (m & (1u << p)) v += dI[cell * g.n_pupil + p];
-  dL[i] = v * inv_ncell;
+    if (__any_sync(0xffffffffu, m & (1u << p)) && (m & (1u << p))) v += dI[cell * g.n_pupil + p];
+  if (in) dL[i] = v * inv_ncell;
 }
 
 cudaError_t launch_loss_impl(const double* tally, int dims, int n_lam, int n_f, int nx, int ny, double cx, double cy,
@@ -213,14 +196,21 @@ cudaError_t launch_loss_impl(const double* tally, int dims, int n_lam, int n_f, 
                              double* out_dev, double* dL, cudaStream_t s) {
   LossGeom g{dims, nx, ny, dims == 2 ? 3 : 9, cx, cy, w, h};
   const long long n_cells = (long long)n_lam * n_f;
+  const int bins = nx * ny;
   double* I = ws;
   double* dI = ws + n_cells * g.n_pupil;
   unsigned short* mask = reinterpret_cast<unsigned short*>(ws + 2 * n_cells * 9 + 8);
-  const int bins = nx * ny;
-  note_launches(dL ? 4 : 3);
+  double* dIf = ws + loss_ws_extra(n_cells, bins);
+  double* dIe = dIf + n_cells * 9;
+  double* gval = dIe + n_cells * 9;
+  double* gsum = gval + n_cells + 9 * (long long)n_lam;
+  const long long n_groups = (long long)n_lam * g.n_pupil + n_cells;
+  note_launches(dL ? 5 : 4);
   k_pupil_masks<<<(bins + 255) / 256, 256, 0, s>>>(g, mask);
   k_pupil_sums<<<(unsigned)n_cells, 256, 0, s>>>(tally, g, mask, inv_ncell, I);
-  k_loss_scalar<<<1, 512, 0, s>>>(I, n_lam, n_f, g.n_pupil, kind, w_f, w_e, dI, out_dev);
+  k_loss_groups<<<(unsigned)((n_groups * 32 + 255) / 256), 256, 0, s>>>(I, n_lam, n_f, g.n_pupil, kind, w_f, w_e, dIf,
+                                                                         dIe, gval, gsum);
+  k_loss_final<<<1, 256, 0, s>>>(n_lam, n_f, g.n_pupil, w_f, w_e, dIf, dIe, gval, gsum, dI, out_dev);
   if (dL) {
     const long long n = n_cells * nx * ny;
     k_loss_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dI, g, mask, inv_ncell, n_cells, dL);
