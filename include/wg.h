@@ -312,7 +312,8 @@ wg_status wg_loss(wg_ctx* ctx, const wg_design* d, const wg_trace_cfg* cfg, int3
  * WG_TRACE_NO_EXIT_LIST; every ray otherwise), propagates G[bin] dI/dE
  * backwards through each ray's Jones maps and back-propagates each hit's
  * coefficient sensitivity through the characteristic-matrix chain
- * (checkpointed forward products, no matrix inversion). The sampled path
+ * (checkpointed forward products; a stack whose layers all propagate is
+ * walked back by inverse layer steps between checkpoints). The sampled path
  * (keys, surfaces, decisions, TIR counts, bin) is held fixed: exact for the
  * thicknesses, which the sampling does not depend on; for the tilts it is
  * the derivative along the fixed path (a ray whose path or bin would change

@@ -816,8 +816,10 @@ __device__ __forceinline__ void tmm_forward_dual(const StackView& st, bool front
 //   df/dx_j = 2 Re(a_j G_j v_j) = -2 (q12 Im(a_j0 y_j) + q21 Im(a_j1 x_j)),
 //   G_j = [[0, i q12], [i q21, 0]] (dM_j/dx = M_j G_j), df/dd_j = kappa_j df/dx_j.
 // Sweep 1 runs v from the substrate side and keeps a checkpoint every CK
-// layers; sweep 2 runs a from the incident side, recomputing each segment's
-// v_j from the checkpoint at its far end. No layer matrix is inverted.
+// layers; sweep 2 runs a from the incident side and takes each segment's v_j
+// from a checkpoint: by inverse layer steps from the segment's incident-side
+// checkpoint when no layer of the stack is evanescent, else recomputed from
+// the checkpoint at its far end.
 // sink(layer index, df/dd) receives the gradient (per nm).
 // ---------------------------------------------------------------------------
 struct Ckpt {
