@@ -373,11 +373,13 @@ __device__ __forceinline__ void sincos_turns_acc(float p, float pl, float& s, fl
 // exponentials. Accurate mode: the phase as kt d + (ktl d + the rounding
 // error of kt d) turns, sin/cos on the FMA pipe; an evanescent layer's
 // exponent in base 2 with the same split, 2^(y + yl) = 2^y (1 + ln2 yl).
-template <bool ACC = false>
+// PROP: the caller knows the layer propagates (its evanescent form is
+// compiled out; the same values as the general evaluation of such a layer)
+template <bool ACC = false, bool PROP = false>
 __device__ __forceinline__ void layer_cs(const MatK& k, float d, float& c, float& s) {
   if constexpr (!ACC) {
     const float x = k.kt * d;
-    if (!k.evan) {
+    if (PROP || !k.evan) {
       const float f = x - rintf(x);  // exact reduction in turns
       __sincosf(f * TWO_PI, &s, &c);
     } else {
@@ -391,7 +393,7 @@ __device__ __forceinline__ void layer_cs(const MatK& k, float d, float& c, float
   } else {
     const float p = __fmul_rn(k.kt, d);
     const float pl = fmaf(k.ktl, d, fmaf(k.kt, d, -p));
-    if (!k.evan) {
+    if (PROP || !k.evan) {
       sincos_turns_acc(p, pl, s, c);
     } else {
       const float t = LN2_F * pl;
@@ -527,7 +529,7 @@ __device__ __forceinline__ void stack_slots(const StackView& st, bool front, con
 // whole segments then take no branch and no bounds test on the stack length.
 // The material of a periodic stack's step comes from its register slot; a
 // general stack reads it.
-template <int P, bool ACC>
+template <int P, bool ACC, bool PROP = false>
 __device__ __forceinline__ void layer_at(const StackView& st, const MatTable& mt, const MatK* kb, int i0, int di,
                                          int j, int u, MatK& k, float& d, float& c, float& s) {
   const int i = i0 + j * di;
@@ -537,7 +539,7 @@ __device__ __forceinline__ void layer_at(const StackView& st, const MatTable& mt
     k = mt.get(st.m[i]);
   }
   d = st.d[i];
-  layer_cs<ACC>(k, d, c, s);
+  layer_cs<ACC, PROP>(k, d, c, s);
 }
 
 // The same slots evaluated directly from each slot's material, without a
@@ -1033,18 +1035,45 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
   // the device index, i0 + j di - st.shift)
   const int i0 = front ? st.off : st.off + L - 1, di = front ? 1 : -1;
   const float eta_s = n0 * cos0, eta_p = n0 / cos0;
+  // Stacks without an evanescent layer (P > 0: every slot propagating) take
+  // v_{j+1} = M_j^{-1} v_j from the checkpoint at the segment's incident-side
+  // end, in registers: M_j = c I + s K with K^2 = -I (q12 q21 = 1) has
+  // determinant c^2 + s^2 = 1, and its inverse is the same step with s
+  // negated. Its singular values are bounded by the quotients, so the
+  // segment's vectors keep about the forward sweep's relative accuracy.
+  // Through an evanescent layer (K^2 = I) the inverse would lose the decaying
+  // solution, so those stacks recompute each segment from its substrate-side
+  // checkpoint instead and keep it in the lane's shared-memory column. The
+  // propagating stacks' sweeps also take the layers' propagating form only.
+  bool inv = false;
+  if constexpr (P > 0) {
+    inv = true;
+#pragma unroll
+    for (int v = 0; v < P; ++v) inv = inv && !kb[v].evan;
+  }
   CV vs = cv_init(eta_s), vp = cv_init(eta_p);
   int es = 0, ep = 0;
   ck[nseg] = Ckpt{vs, vp, 0, 0};
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int j0 = sg * CKP;
+    if (inv) {
 #pragma unroll
-    for (int u = CKP - 1; u >= 0; --u) {
-      MatK k;
-      float d, c, s;
-      layer_at<P, ACC>(st, mt, kb, i0, di, j0 + u, u, k, d, c, s);
-      cv_step(vs, c, s * k.q12s, s * k.q21s);
-      cv_step(vp, c, s * k.q12p, s * k.q21p);
+      for (int u = CKP - 1; u >= 0; --u) {
+        MatK k;
+        float d, c, s;
+        layer_at<P, ACC, true>(st, mt, kb, i0, di, j0 + u, u, k, d, c, s);
+        cv_step(vs, c, s * k.q12s, s * k.q21s);
+        cv_step(vp, c, s * k.q12p, s * k.q21p);
+      }
+    } else {
+#pragma unroll
+      for (int u = CKP - 1; u >= 0; --u) {
+        MatK k;
+        float d, c, s;
+        layer_at<P, ACC>(st, mt, kb, i0, di, j0 + u, u, k, d, c, s);
+        cv_step(vs, c, s * k.q12s, s * k.q21s);
+        cv_step(vp, c, s * k.q12p, s * k.q21p);
+      }
     }
     cv_fit(vs, es);
     cv_fit(vp, ep);
@@ -1071,21 +1100,6 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
   }
   eas += eA;
   eap += eA;
-  // Stacks without an evanescent layer (P > 0: every slot propagating) take
-  // v_{j+1} = M_j^{-1} v_j from the checkpoint at the segment's incident-side
-  // end, in registers: M_j = c I + s K with K^2 = -I (q12 q21 = 1) has
-  // determinant c^2 + s^2 = 1, and its inverse is the same step with s
-  // negated. Its singular values are bounded by the quotients, so the
-  // segment's vectors keep about the forward sweep's relative accuracy.
-  // Through an evanescent layer (K^2 = I) the inverse would lose the decaying
-  // solution, so those stacks recompute each segment from its substrate-side
-  // checkpoint instead and keep it in the lane's shared-memory column.
-  bool inv = false;
-  if constexpr (P > 0) {
-    inv = true;
-#pragma unroll
-    for (int v = 0; v < P; ++v) inv = inv && !kb[v].evan;
-  }
   for (int sg = 0; sg < nseg; ++sg) {
     const int j0 = sg * CKP;
     row_fit8(as, eas);
@@ -1118,7 +1132,7 @@ __device__ __forceinline__ void tmm_adjoint(const StackView& st, bool front, con
         MatK k;
         float d, c, s;
         float rho = 0.0f;
-        layer_at<P, ACC>(st, mt, kb, i0, di, j0 + u, u, k, d, c, s);
+        layer_at<P, ACC, true>(st, mt, kb, i0, di, j0 + u, u, k, d, c, s);
         if constexpr (DUAL) rho = rb[u % P];
         const float m12s = s * k.q12s, m21s = s * k.q21s, m12p = s * k.q12p, m21p = s * k.q21p;
         // v_{j+1} (past the stack's end the identity: v_L)
