@@ -241,12 +241,15 @@ size_t hit_rec_bytes();
 // loss (workspace: 2 * cells * 9 + 8 doubles, then one u16 pupil mask per eyebox bin)
 // loss workspace (doubles): I and dL/dI (9 per cell each), 8 result words,
 // the pupil masks of the bins (u16), then the two spread parts of dL/dI, the
-// statistic of every group and the sums of the field groups
+// statistic of every group and the sums of the field groups, the per-cell
+// table over the 512 possible pupil masks, the masks that occur (512 ints and
+// their count) and each bin's index among them (u16)
 inline long long loss_ws_extra(long long n_cells, long long bins) {
   return 2 * n_cells * 9 + 8 + (bins * 2 + 7) / 8;
 }
 inline long long loss_ws_doubles(long long n_cells, long long bins, int n_lam) {
-  return loss_ws_extra(n_cells, bins) + 2 * n_cells * 9 + 2 * (n_cells + 9 * (long long)n_lam);
+  return loss_ws_extra(n_cells, bins) + 2 * n_cells * 9 + 2 * (n_cells + 9 * (long long)n_lam) + n_cells * 512 +
+         (512 * 4 + 16 + bins * 2 + 7) / 8;
 }
 cudaError_t launch_loss_impl(const double* tally, int dims, int n_lam, int n_f, int nx, int ny, double cx, double cy,
                              double w, double h, double inv_ncell, int kind, double w_f, double w_e, double* ws,

@@ -176,19 +176,54 @@ __global__ void k_loss_final(int n_lam, int n_f, int P, double w_f, double w_e, 
   }
 }
 
-// dL/dtally[cell, bin] = sum_{p containing bin} dL/dI[cell, p] / rays per cell
-// (whole warps; a pupil none of the warp's bins is in is skipped for it)
-__global__ void k_loss_scatter(const double* dI, LossGeom g, const unsigned short* mask, double inv_ncell,
-                               long long n_cells, double* dL) {
-  const long long bins = (long long)g.nx * g.ny;
-  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const bool in = i < n_cells * bins;
-  const long long cell = in ? i / bins : 0;
-  const unsigned m = in ? mask[i % bins] : 0u;
-  double v = 0.0;
-  for (int p = 0; p < g.n_pupil; ++p)
-    if (__any_sync(0xffffffffu, m & (1u << p)) && (m & (1u << p))) v += dI[cell * g.n_pupil + p];
-  if (in) dL[i] = v * inv_ncell;
+// dL/dtally[cell, bin] = sum_{p containing bin} dL/dI[cell, p] / rays per cell.
+// The bins take few distinct pupil masks (2-4 pupils overlap at most), so the
+// sum is formed once per (cell, mask that occurs) and the bins copy it: no
+// FP64 arithmetic per bin (scarce on this part), the same value per bin.
+constexpr int kMaskValues = 512;  // 2^9 pupil masks
+// one block: the masks that occur, in increasing order, and each bin's index
+// among them
+__global__ void k_mask_ids(const unsigned short* mask, int bins, int* occ_list, int* n_occ,
+                           unsigned short* mid) {
+  __shared__ unsigned s_bits[kMaskValues / 32];
+  __shared__ unsigned short s_id[kMaskValues];
+  for (int i = threadIdx.x; i < kMaskValues / 32; i += blockDim.x) s_bits[i] = 0u;
+  __syncthreads();
+  for (int b = threadIdx.x; b < bins; b += blockDim.x) atomicOr(&s_bits[mask[b] >> 5], 1u << (mask[b] & 31));
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int m = 0; m < kMaskValues; ++m)
+      if (s_bits[m >> 5] & (1u << (m & 31))) {
+        s_id[m] = (unsigned short)n;
+        occ_list[n++] = m;
+      }
+    *n_occ = n;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < bins; b += blockDim.x) mid[b] = s_id[mask[b]];
+}
+
+// table[cell, j] = sum over the pupils p of mask occ_list[j] (increasing p) of
+// dL/dI[cell, p], times 1 / rays per cell
+__global__ void k_loss_table(const double* dI, int n_pupil, const int* occ_list, const int* n_occ, double inv_ncell,
+                             double* table) {
+  const long long cell = blockIdx.x;
+  const int n = *n_occ;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const unsigned m = (unsigned)occ_list[j];
+    double v = 0.0;
+    for (int p = 0; p < n_pupil; ++p)
+      if (m & (1u << p)) v += dI[cell * n_pupil + p];
+    table[cell * kMaskValues + j] = v * inv_ncell;
+  }
+}
+
+// dL/dtally[cell, bin] (grid: bins in x, cells in y)
+__global__ void k_loss_scatter(const double* table, const unsigned short* mid, int bins, double* dL) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long cell = blockIdx.y;
+  if (b < bins) dL[cell * bins + b] = table[cell * kMaskValues + mid[b]];
 }
 
 cudaError_t launch_loss_impl(const double* tally, int dims, int n_lam, int n_f, int nx, int ny, double cx, double cy,
@@ -204,16 +239,21 @@ cudaError_t launch_loss_impl(const double* tally, int dims, int n_lam, int n_f, 
   double* dIe = dIf + n_cells * 9;
   double* gval = dIe + n_cells * 9;
   double* gsum = gval + n_cells + 9 * (long long)n_lam;
+  double* table = gsum + n_cells + 9 * (long long)n_lam;
+  int* occ_list = reinterpret_cast<int*>(table + n_cells * kMaskValues);
+  int* n_occ = occ_list + kMaskValues;
+  unsigned short* mid = reinterpret_cast<unsigned short*>(n_occ + 4);
   const long long n_groups = (long long)n_lam * g.n_pupil + n_cells;
-  note_launches(dL ? 5 : 4);
+  note_launches(dL ? 7 : 4);
   k_pupil_masks<<<(bins + 255) / 256, 256, 0, s>>>(g, mask);
   k_pupil_sums<<<(unsigned)n_cells, 256, 0, s>>>(tally, g, mask, inv_ncell, I);
   k_loss_groups<<<(unsigned)((n_groups * 32 + 255) / 256), 256, 0, s>>>(I, n_lam, n_f, g.n_pupil, kind, w_f, w_e, dIf,
                                                                          dIe, gval, gsum);
   k_loss_final<<<1, 256, 0, s>>>(n_lam, n_f, g.n_pupil, w_f, w_e, dIf, dIe, gval, gsum, dI, out_dev);
   if (dL) {
-    const long long n = n_cells * nx * ny;
-    k_loss_scatter<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dI, g, mask, inv_ncell, n_cells, dL);
+    k_mask_ids<<<1, 1024, 0, s>>>(mask, bins, occ_list, n_occ, mid);
+    k_loss_table<<<(unsigned)n_cells, 64, 0, s>>>(dI, g.n_pupil, occ_list, n_occ, inv_ncell, table);
+    k_loss_scatter<<<dim3((unsigned)((bins + 255) / 256), (unsigned)n_cells), 256, 0, s>>>(table, mid, bins, dL);
   }
   return cudaGetLastError();
 }
